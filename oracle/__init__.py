@@ -1,0 +1,470 @@
+"""FP64 CPU oracle for planewave-orbital splines (arXiv:1309.6250).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and the
+benchmark's CPU-baseline leg may import this package.  The product path (the CUDA
+library and its Python binding) never imports, links or calls anything here, and the
+two share no code: the only thing both sides consume is the seeded input generator.
+
+What the oracle computes, in the paper's order:
+
+1. Grid values of a planewave orbital, Eq. (pw_orbital) sampled at the grid points
+   s = l/N: the coefficients are folded onto the N-periodic frequency grid and summed
+   with an inverse FFT (a library step; numpy.fft).  `direct_grid_sum` is the same sum
+   written out term by term for small cases and for sampled grid points.
+2. Spline coefficients (Appendix "B-splines"):
+   * interpolating: three stages of cyclic tridiagonal solves with the rows
+     [b(1), b(0), b(1)] = [1/4, 1, 1/4] of Eq. (bsplinegridcenteredbasis), solved by
+     the Thomas algorithm with a Sherman-Morrison correction for the corners;
+   * smoothing: Eq. (b-splinecoefficients), beta = sum_G c_G/gamma_G exp(iG.x);
+   * separate Laplacian table (Sec. III A, III C): the same with -|G|^2 c_G.
+3. Lagrange tables (Appendix "Lagrange interpolation", Sec. III C): grid values of
+   phi, d_x phi, d_y phi, d_z phi and lap phi.
+4. pp-spline tables (Appendix "Piecewise-polynomial-form splines"): periodic
+   [4 1 ... 1] solves with right-hand side 6 x second differences, applied along each
+   axis of the coefficient's label, Eq. (pp-splinecoefficients3).
+5. Evaluation and adjoint: plain C loops in qmcspl_oracle.c.
+
+Readings of the paper that the code depends on:
+* gamma_G (Eq. b-splinecoefficients) is a product over axes of
+  3(3 - 4 cos th + cos 2 th)/th^4 with th = 2 pi n_m / N_m the phase per grid step;
+  that equals 24 sin^4(th/2)/th^4 = (3/2) sinc^4(th/2) per axis and 3/2 at th = 0.
+  The second and third printed forms put the constant outside the product; they are
+  read as misprints.
+* The pp right-hand side 6/h^2 is taken with h = 1 (reduced units).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qmcspl_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+GCC_FLAGS = ["-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC"]
+
+
+def build(force: bool = False) -> str:
+    """Compile qmcspl_oracle.c into liboracle.so (plain gcc, no CUDA)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.run(["gcc", *GCC_FLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            ip = ctypes.POINTER(ctypes.c_int)
+            L = ctypes.c_long
+            I = ctypes.c_int
+            lib.orc_bspline_eval.argtypes = [dp, dp, ip, I, dp, L, dp, dp, dp, dp]
+            lib.orc_bspline_reduced_derivative.argtypes = [dp, ip, I, dp, L, dp, I, I, I, dp]
+            lib.orc_lagrange_eval.argtypes = [dp, ip, I, dp, L, dp, dp, dp, dp]
+            lib.orc_lagrange_reduced_derivative.argtypes = [dp, ip, I, dp, L, dp, I, I, I, dp]
+            lib.orc_pp_eval.argtypes = [dp, ip, I, dp, L, dp, dp, dp, dp]
+            lib.orc_pw_eval.argtypes = [I, ip, I, dp, dp, L, dp, dp, dp, dp, dp]
+            lib.orc_bspline_adjoint.argtypes = [dp, dp, ip, I, dp, L, dp, dp, dp, dp, dp, dp, dp]
+            for name in ("orc_bspline_basis", "orc_lagrange_basis", "orc_pp_basis"):
+                getattr(lib, name).argtypes = [ctypes.c_double, I, dp]
+                getattr(lib, name).restype = None
+            _lib = lib
+    return _lib
+
+
+def _d(a: Optional[np.ndarray]):
+    if a is None:
+        return ctypes.POINTER(ctypes.c_double)()
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i(a: np.ndarray):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _dims(dims) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# ---------------------------------------------------------------------------
+# basis polynomials (for pins)
+# ---------------------------------------------------------------------------
+
+def basis(kind: str, t: float, d: int = 0) -> np.ndarray:
+    """Basis weights at reduced coordinate t: kind in {bspline, lagrange, pp}."""
+    lib = _load()
+    w = np.zeros(4)
+    fn = {"bspline": lib.orc_bspline_basis, "lagrange": lib.orc_lagrange_basis,
+          "pp": lib.orc_pp_basis}[kind]
+    fn(float(t), int(d), _d(w))
+    return w
+
+
+# ---------------------------------------------------------------------------
+# planewave side, Eq. (pw_orbital)
+# ---------------------------------------------------------------------------
+
+def reciprocal(lattice: np.ndarray) -> np.ndarray:
+    """Matrix whose columns are the reciprocal vectors b_i = 2 pi (a^-T)_i."""
+    return 2.0 * np.pi * np.linalg.inv(_f64(lattice)).T
+
+
+def g_vectors(lattice: np.ndarray, miller: np.ndarray) -> np.ndarray:
+    """Cartesian G = 2 pi a^-T n for every Miller triple, [n_pw, 3]."""
+    return miller.astype(np.float64) @ reciprocal(lattice).T
+
+
+def pw_eval(lattice, miller, coef, pos) -> Tuple[np.ndarray, np.ndarray, np.ndarray, float]:
+    """Direct planewave sums: (val [P,O], grad [P,3,O], lap [P,O], max |Im val|)."""
+    lib = _load()
+    miller = np.ascontiguousarray(miller, dtype=np.int32)
+    coef = np.ascontiguousarray(coef, dtype=np.complex128)
+    n_orb, n_pw = coef.shape
+    c2 = np.ascontiguousarray(coef.view(np.float64).reshape(n_orb, n_pw, 2))
+    pos = _f64(pos).reshape(-1, 3)
+    P = pos.shape[0]
+    val = np.zeros((P, n_orb))
+    grad = np.zeros((P, 3, n_orb))
+    lap = np.zeros((P, n_orb))
+    mi = np.zeros(1)
+    rc = lib.orc_pw_eval(n_pw, _i(miller), n_orb, _d(c2), _d(_f64(lattice)), P, _d(pos),
+                         _d(val), _d(grad), _d(lap), _d(mi))
+    if rc != 0:
+        raise RuntimeError("orc_pw_eval failed (%d)" % rc)
+    return val, grad, lap, float(mi[0])
+
+
+def fold(miller: np.ndarray, weighted: np.ndarray, dims) -> np.ndarray:
+    """X[o, k1, k2, k3] = sum over G with n = k (mod N) of weighted[o, G]."""
+    n_orb = weighted.shape[0]
+    X = np.zeros((n_orb,) + tuple(int(d) for d in dims), dtype=np.complex128)
+    k = np.mod(miller.astype(np.int64), np.asarray(dims, dtype=np.int64))
+    for o in range(n_orb):
+        np.add.at(X[o], (k[:, 0], k[:, 1], k[:, 2]), weighted[o])
+    return X
+
+
+def grid_sum(X: np.ndarray) -> Tuple[np.ndarray, float]:
+    """f(x_l) = sum_k X_k exp(2 pi i k.l / N) on the grid, canonical [Nx,Ny,Nz,O].
+
+    The inverse FFT computes the sum divided by N1 N2 N3; it is multiplied back.
+    Returns the real part and the largest |imaginary part| (zero for Hermitian input).
+    """
+    n = X.shape[1] * X.shape[2] * X.shape[3]
+    f = np.fft.ifftn(X, axes=(1, 2, 3)) * n
+    im = float(np.max(np.abs(f.imag))) if f.size else 0.0
+    return np.ascontiguousarray(np.moveaxis(f.real, 0, -1)), im
+
+
+def direct_grid_sum(miller: np.ndarray, weighted: np.ndarray, dims, points: np.ndarray) -> np.ndarray:
+    """The same sum written out: f[l, o] = sum_G weighted[o,G] exp(2 pi i n.l/N).
+
+    `points` are integer grid indices [M, 3].  Returns the real part [M, O].
+    """
+    frac = points.astype(np.float64) / np.asarray(dims, dtype=np.float64)
+    ph = 2.0 * np.pi * (frac @ miller.astype(np.float64).T)     # [M, n_pw]
+    return np.real(np.exp(1j * ph) @ weighted.T)
+
+
+def grid_values(lattice, miller, coef, dims, what: str = "value") -> np.ndarray:
+    """Grid values [Nx,Ny,Nz,O] of phi_PW or one of its derivatives.
+
+    what: 'value', 'dx', 'dy', 'dz' (Cartesian derivative) or 'lap'.
+    """
+    G = g_vectors(lattice, miller)
+    if what == "value":
+        w = coef
+    elif what in ("dx", "dy", "dz"):
+        a = "xyz".index(what[1])
+        w = coef * (1j * G[:, a])[None, :]
+    elif what == "lap":
+        w = coef * (-np.einsum("ij,ij->i", G, G))[None, :]
+    else:
+        raise ValueError(what)
+    f, _ = grid_sum(fold(miller, w, dims))
+    return f
+
+
+# ---------------------------------------------------------------------------
+# smoothing B-spline, Eq. (b-splinecoefficients)
+# ---------------------------------------------------------------------------
+
+def gamma_axis(theta: np.ndarray) -> np.ndarray:
+    """One axis of gamma_G: 3(3 - 4 cos th + cos 2th)/th^4, written as 24 sin^4(th/2)/th^4
+    (the same function; this form has no cancellation at small th), 3/2 at th = 0."""
+    theta = np.asarray(theta, dtype=np.float64)
+    out = np.full(theta.shape, 1.5)
+    nz = theta != 0.0
+    th = theta[nz]
+    out[nz] = 24.0 * np.sin(0.5 * th) ** 4 / th ** 4
+    return out
+
+
+def gamma(miller: np.ndarray, dims) -> np.ndarray:
+    """gamma_G for every planewave: product over axes of gamma_axis(2 pi n_m / N_m)."""
+    th = 2.0 * np.pi * miller.astype(np.float64) / np.asarray(dims, dtype=np.float64)
+    return gamma_axis(th[:, 0]) * gamma_axis(th[:, 1]) * gamma_axis(th[:, 2])
+
+
+def smoothing_coefficients(lattice, miller, coef, dims, laplacian: bool = False) -> np.ndarray:
+    """beta [Nx,Ny,Nz,O] = sum_G c_G / gamma_G exp(i G.x_lmn); with laplacian=True the
+    coefficients of the separate Laplacian spline (c_G -> -|G|^2 c_G)."""
+    w = coef / gamma(miller, dims)[None, :]
+    if laplacian:
+        G = g_vectors(lattice, miller)
+        w = w * (-np.einsum("ij,ij->i", G, G))[None, :]
+    f, _ = grid_sum(fold(miller, w, dims))
+    return f
+
+
+def smoothing_coefficients_at(lattice, miller, coef, dims, points, laplacian: bool = False):
+    """Eq. (b-splinecoefficients) summed directly at selected grid points [M,3] -> [M,O]."""
+    w = coef / gamma(miller, dims)[None, :]
+    if laplacian:
+        G = g_vectors(lattice, miller)
+        w = w * (-np.einsum("ij,ij->i", G, G))[None, :]
+    return direct_grid_sum(miller, w, dims, points)
+
+
+# ---------------------------------------------------------------------------
+# interpolating B-spline: three stages of cyclic tridiagonal solves
+# ---------------------------------------------------------------------------
+
+def cyclic_tridiagonal_solve(rhs: np.ndarray, axis: int, diag: float, off: float) -> np.ndarray:
+    """Solve off*x[i-1] + diag*x[i] + off*x[i+1] = rhs[i] (indices mod n) along `axis`.
+
+    Thomas algorithm on the tridiagonal part with a Sherman-Morrison rank-one
+    correction for the two corner entries, vectorised over all other axes.
+    """
+    r = np.moveaxis(np.asarray(rhs, dtype=np.float64), axis, 0)
+    n = r.shape[0]
+    if n < 3:
+        raise ValueError("cyclic solve needs at least 3 points")
+    gam = -diag
+    dmod = np.full(n, diag)
+    dmod[0] = diag - gam
+    dmod[-1] = diag - off * off / gam
+
+    def thomas(d):
+        cp = np.empty(n)
+        dp = np.empty_like(d)
+        cp[0] = off / dmod[0]
+        dp[0] = d[0] / dmod[0]
+        for i in range(1, n):
+            m = dmod[i] - off * cp[i - 1]
+            cp[i] = off / m
+            dp[i] = (d[i] - off * dp[i - 1]) / m
+        x = np.empty_like(d)
+        x[-1] = dp[-1]
+        for i in range(n - 2, -1, -1):
+            x[i] = dp[i] - cp[i] * x[i + 1]
+        return x
+
+    y = thomas(r)
+    u = np.zeros(n)
+    u[0] = gam
+    u[-1] = off
+    q = thomas(u)
+    # v = (1, 0, ..., 0, off/gam)
+    vy = y[0] + (off / gam) * y[-1]
+    vq = q[0] + (off / gam) * q[-1]
+    x = y - (vy / (1.0 + vq)) * q.reshape((n,) + (1,) * (y.ndim - 1))
+    return np.moveaxis(x, 0, axis)
+
+
+def interpolating_coefficients(values: np.ndarray) -> np.ndarray:
+    """beta with sum_lmn B^x_il B^y_jm B^z_kn beta_lmn = values_ijk (Appendix, interpolating
+    B-spline coefficients), solved in three stages along x, y and z."""
+    b0, b1 = 1.0, 0.25      # b(0) and b(+-1) of Eq. (bsplinegridcenteredbasis)
+    beta = np.asarray(values, dtype=np.float64)
+    for axis in range(3):
+        beta = cyclic_tridiagonal_solve(beta, axis, b0, b1)
+    return np.ascontiguousarray(beta)
+
+
+def interpolating_tables(lattice, miller, coef, dims, laplacian: bool = False):
+    """(beta, beta_lap or None) of the interpolating B-spline."""
+    beta = interpolating_coefficients(grid_values(lattice, miller, coef, dims, "value"))
+    lap = None
+    if laplacian:
+        lap = interpolating_coefficients(grid_values(lattice, miller, coef, dims, "lap"))
+    return beta, lap
+
+
+def smoothing_tables(lattice, miller, coef, dims, laplacian: bool = False):
+    beta = smoothing_coefficients(lattice, miller, coef, dims)
+    lap = smoothing_coefficients(lattice, miller, coef, dims, laplacian=True) if laplacian else None
+    return beta, lap
+
+
+# ---------------------------------------------------------------------------
+# Lagrange and pp-spline tables
+# ---------------------------------------------------------------------------
+
+def lagrange_tables(lattice, miller, coef, dims) -> np.ndarray:
+    """[5, Nx, Ny, Nz, O]: grid values of phi, d_x phi, d_y phi, d_z phi, lap phi."""
+    return np.ascontiguousarray(np.stack(
+        [grid_values(lattice, miller, coef, dims, w) for w in ("value", "dx", "dy", "dz", "lap")]))
+
+
+def pp_second_derivative(f: np.ndarray, axis: int) -> np.ndarray:
+    """Periodic cubic-spline second derivatives along `axis`:
+    [4 1 ... 1; 1 4 1 ...; ...; 1 ... 1 4] sigma = 6/h^2 (f[i-1] - 2 f[i] + f[i+1]), h = 1."""
+    rhs = 6.0 * (np.roll(f, 1, axis=axis) - 2.0 * f + np.roll(f, -1, axis=axis))
+    return cyclic_tridiagonal_solve(rhs, axis, 4.0, 1.0)
+
+
+def pp_tables(values: np.ndarray) -> np.ndarray:
+    """[8, Nx, Ny, Nz, O] sigma^{kappa mu nu}, index 4(kappa-1) + 2(mu-1) + (nu-1):
+    the 1-D operator is applied along every axis whose label is 2."""
+    out = []
+    for kappa in (1, 2):
+        for mu in (1, 2):
+            for nu in (1, 2):
+                s = np.asarray(values, dtype=np.float64)
+                for axis, lab in enumerate((kappa, mu, nu)):
+                    if lab == 2:
+                        s = pp_second_derivative(s, axis)
+                out.append(s)
+    return np.ascontiguousarray(np.stack(out))
+
+
+# ---------------------------------------------------------------------------
+# evaluation (C loops)
+# ---------------------------------------------------------------------------
+
+def _outputs(P, n_orb):
+    return np.zeros((P, n_orb)), np.zeros((P, 3, n_orb)), np.zeros((P, n_orb))
+
+
+def bspline_eval(beta, lattice, pos, beta_lap=None):
+    """Tricubic B-spline value, Cartesian gradient and Laplacian, [P,O], [P,3,O], [P,O]."""
+    lib = _load()
+    beta = _f64(beta)
+    dims = _dims(beta.shape[:3])
+    n_orb = beta.shape[3]
+    pos = _f64(pos).reshape(-1, 3)
+    val, grad, lap = _outputs(pos.shape[0], n_orb)
+    bl = None if beta_lap is None else _f64(beta_lap)
+    rc = lib.orc_bspline_eval(_d(beta), _d(bl), _i(dims), n_orb, _d(_f64(lattice)),
+                              pos.shape[0], _d(pos), _d(val), _d(grad), _d(lap))
+    if rc:
+        raise RuntimeError("orc_bspline_eval failed (%d)" % rc)
+    return val, grad, lap
+
+
+def bspline_reduced_derivative(beta, lattice, pos, order):
+    lib = _load()
+    beta = _f64(beta)
+    dims = _dims(beta.shape[:3])
+    n_orb = beta.shape[3]
+    pos = _f64(pos).reshape(-1, 3)
+    out = np.zeros((pos.shape[0], n_orb))
+    rc = lib.orc_bspline_reduced_derivative(_d(beta), _i(dims), n_orb, _d(_f64(lattice)),
+                                            pos.shape[0], _d(pos), *[int(x) for x in order], _d(out))
+    if rc:
+        raise RuntimeError("orc_bspline_reduced_derivative failed")
+    return out
+
+
+def lagrange_eval(tabs, lattice, pos):
+    lib = _load()
+    tabs = _f64(tabs)
+    dims = _dims(tabs.shape[1:4])
+    n_orb = tabs.shape[4]
+    pos = _f64(pos).reshape(-1, 3)
+    val, grad, lap = _outputs(pos.shape[0], n_orb)
+    rc = lib.orc_lagrange_eval(_d(tabs), _i(dims), n_orb, _d(_f64(lattice)), pos.shape[0],
+                               _d(pos), _d(val), _d(grad), _d(lap))
+    if rc:
+        raise RuntimeError("orc_lagrange_eval failed")
+    return val, grad, lap
+
+
+def lagrange_reduced_derivative(tab, lattice, pos, order):
+    lib = _load()
+    tab = _f64(tab)
+    dims = _dims(tab.shape[:3])
+    n_orb = tab.shape[3]
+    pos = _f64(pos).reshape(-1, 3)
+    out = np.zeros((pos.shape[0], n_orb))
+    rc = lib.orc_lagrange_reduced_derivative(_d(tab), _i(dims), n_orb, _d(_f64(lattice)),
+                                             pos.shape[0], _d(pos), *[int(x) for x in order], _d(out))
+    if rc:
+        raise RuntimeError("orc_lagrange_reduced_derivative failed")
+    return out
+
+
+def pp_eval(sig, lattice, pos):
+    lib = _load()
+    sig = _f64(sig)
+    dims = _dims(sig.shape[1:4])
+    n_orb = sig.shape[4]
+    pos = _f64(pos).reshape(-1, 3)
+    val, grad, lap = _outputs(pos.shape[0], n_orb)
+    rc = lib.orc_pp_eval(_d(sig), _i(dims), n_orb, _d(_f64(lattice)), pos.shape[0], _d(pos),
+                         _d(val), _d(grad), _d(lap))
+    if rc:
+        raise RuntimeError("orc_pp_eval failed")
+    return val, grad, lap
+
+
+def bspline_adjoint(beta, lattice, pos, gv, gg, gl, beta_lap=None):
+    """(dbeta [Nx,Ny,Nz,O], dbeta_lap or None, dpos [P,3]) for loss = <gv,val>+<gg,grad>+<gl,lap>."""
+    lib = _load()
+    beta = _f64(beta)
+    dims = _dims(beta.shape[:3])
+    n_orb = beta.shape[3]
+    pos = _f64(pos).reshape(-1, 3)
+    P = pos.shape[0]
+    dbeta = np.zeros_like(beta)
+    bl = None if beta_lap is None else _f64(beta_lap)
+    dbl = None if beta_lap is None else np.zeros_like(beta)
+    dpos = np.zeros((P, 3))
+    rc = lib.orc_bspline_adjoint(_d(beta), _d(bl), _i(dims), n_orb, _d(_f64(lattice)), P, _d(pos),
+                                 _d(_f64(gv)), _d(_f64(gg)), _d(_f64(gl)), _d(dbeta), _d(dbl),
+                                 _d(dpos))
+    if rc:
+        raise RuntimeError("orc_bspline_adjoint failed")
+    return dbeta, dbl, dpos
+
+
+# ---------------------------------------------------------------------------
+# error metrics
+# ---------------------------------------------------------------------------
+
+def relative_error(test: np.ndarray, ref: np.ndarray) -> float:
+    """max |test - ref| / max |ref| (per output, relative to its largest magnitude)."""
+    scale = float(np.max(np.abs(ref))) if ref.size else 0.0
+    if scale == 0.0:
+        return float(np.max(np.abs(test))) if test.size else 0.0
+    return float(np.max(np.abs(np.asarray(test, dtype=np.float64) - ref))) / scale
+
+
+def relative_mean_absolute_error(test: np.ndarray, ref: np.ndarray) -> float:
+    """The paper's accuracy metric (Sec. III A): mean |error| / mean |planewave value|."""
+    return float(np.mean(np.abs(test - ref)) / np.mean(np.abs(ref)))
+
+
+def kinetic_energy(val: np.ndarray, lap: np.ndarray) -> np.ndarray:
+    """Per-orbital kinetic-energy estimate over the sampled positions:
+    T_n = -1/2 sum_p phi_n lap phi_n / sum_p phi_n^2 (Hartree)."""
+    return -0.5 * np.sum(val * lap, axis=0) / np.sum(val * val, axis=0)
