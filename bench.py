@@ -1,0 +1,363 @@
+"""Benchmark: orbital x position evaluations per second (value + gradient + Laplacian).
+
+Workload (default): the MgO-like 64-atom cell -- cubic a = 15.9 bohr, 128 real
+orbitals with |G|^2/2 <= 40 Ha and coefficient envelope exp(-|G|^2/8), smoothing
+B-spline on a 96^3 grid with the separate Laplacian table, 2048 walkers x 256
+electrons (524,288 positions) uniform in the cell.  A step is one evaluation of every
+orbital at every position (table construction is setup, reported separately).
+
+`value` is timed with CUDA events on the launching stream with positions already in
+HBM; `e2e` goes through the host-buffer entry point (pinned host positions in,
+host outputs back) every step.  The table (934 MB for FP32) and the outputs
+(1.34 GB) are both far larger than the 129 MB L2, so no extra flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1309_6250_gb300 import inputs  # noqa: E402
+
+METRIC = "orbital x position evals/s (val+grad+lap)"
+UNIT = "evals/s"
+KERNEL_SOURCES = ["paper_1309_6250_gb300/csrc/eval_bspline.cu", "paper_1309_6250_gb300/csrc/eval_common.cuh"]
+
+
+def out_bytes(storage):
+    return 8 if storage == "f64" else 4
+
+
+def elem_bytes(storage):
+    return {"f64": 8, "f32": 4, "bf16": 2}[storage]
+
+
+def algorithmic_bytes_per_eval(storage, n_tables, n_orb):
+    """Gathered table bytes (64 coefficients per table) + 5 outputs per orbital-eval
+    + the position (24 B) shared by the orbitals."""
+    return n_tables * 64 * elem_bytes(storage) + 5 * out_bytes(storage) + 24.0 / n_orb
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(key)
+    if not e or e.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    import torch
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, ws, dist
+
+
+def time_steps(fn, steps, warmup, torch, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def cpu_baseline(w, storage, sep, budget_s=12.0):
+    """The FP64 oracle's evaluation, as it stands, on the host cores: sized to about
+    `budget_s` seconds of work on a prefix of the positions."""
+    import oracle
+    n_orb = w.coef.shape[0]
+    beta, blap = oracle.smoothing_tables(w.lattice, w.miller, w.coef, w.cell.grid, laplacian=sep)
+    n = 256
+    t0 = time.perf_counter()
+    oracle.bspline_eval(beta, w.lattice, w.pos[:n], beta_lap=blap)
+    dt = time.perf_counter() - t0
+    n2 = int(min(w.pos.shape[0], max(n, n * budget_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.bspline_eval(beta, w.lattice, w.pos[:n2], beta_lap=blap)
+    dt2 = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n2 * n_orb / dt2, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d positions x %d orbitals, FP64 oracle evaluation (tables prebuilt)"
+                      % (n2, w.pos.shape[0], n_orb), "seconds": dt2}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = inputs.make_workload(args.workload)
+    import oracle
+    n_orb = w.coef.shape[0]
+    beta, blap = oracle.smoothing_tables(w.lattice, w.miller, w.coef, w.cell.grid, laplacian=True)
+    n = args.ref_sample
+    for i in range(args.warmup):
+        oracle.bspline_eval(beta, w.lattice, w.pos[:min(n, 64)], beta_lap=blap)
+    times = []
+    for i in range(args.steps):
+        s0 = (i * n) % max(1, w.pos.shape[0] - n)
+        t0 = time.perf_counter()
+        oracle.bspline_eval(beta, w.lattice, w.pos[s0:s0 + n], beta_lap=blap)
+        times.append(time.perf_counter() - t0)
+    t = sum(times)
+    value = n * n_orb * args.steps / t
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.cell.name, "n_orb": n_orb,
+                                            "grid": list(w.cell.grid), "positions_per_step": n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d positions x %d orbitals per step" % (n, n_orb)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    rank, ws, dist = dist_setup()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1309_6250_gb300.api import OrbitalSplines
+
+    w = inputs.make_workload(args.workload, n_pos=args.n_pos)
+    if rank > 0:   # weak scaling: every rank its own walkers
+        w.pos[:] = inputs.positions(w.lattice, w.pos.shape[0], w.cell.pos_seed + 7919 * rank)
+    n_pos, n_orb = w.pos.shape[0], w.coef.shape[0]
+    stream = torch.cuda.current_stream()
+
+    def build(storage):
+        t0 = time.perf_counter()
+        s = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth",
+                           storage=storage, separate_lap=True, device=dev)
+        return s, time.perf_counter() - t0
+
+    spl, setup_s = build(args.storage)
+    info = spl.info()
+    pos_d = torch.from_numpy(w.pos).to(dev)
+    outs = spl.alloc_outputs(n_pos)
+    step = lambda: spl.eval_vgl(pos_d, out=outs)
+
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ms = time_steps(step, args.steps, 0, torch, stream)
+    clocks = sampler.stop()
+    spl.sync()
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    evals_per_step = n_pos * n_orb
+    value = evals_per_step * ws * args.steps / (total_ms * 1e-3)
+
+    # end to end through the host-buffer entry point: pinned positions in, outputs back
+    pos_h = torch.from_numpy(w.pos).pin_memory()
+    host_out = tuple(torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs)
+    e2e_step = lambda: spl.eval_vgl_host(pos_h, out=host_out)
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = evals_per_step * ws * args.steps / e2e_s
+    d2h = sum(o.numel() * o.element_size() for o in host_out)
+
+    # roofline of the (only) kernel of a step
+    hbm, peak_kind = load_peaks()
+    bpe = algorithmic_bytes_per_eval(args.storage, info["n_tables"], n_orb)
+    launch_s = total_ms * 1e-3 / args.steps
+    achieved = bpe * evals_per_step / launch_s / 1e9
+    key = "bspline_vgl/%s/%s" % (w.cell.name, args.storage)
+    traffic = load_traffic(key)
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for st in [s for s in ("f32", "bf16", "f64") if s != args.storage]:
+            del outs
+            spl.close()
+            torch.cuda.empty_cache()
+            spl, _ = build(st)
+            outs = spl.alloc_outputs(n_pos)
+            vstep = lambda: spl.eval_vgl(pos_d, out=outs)
+            vms = time_steps(vstep, max(3, args.steps // 2), 2, torch, stream)
+            spl.sync()
+            vt = sum(vms) / len(vms) * 1e-3
+            vb = algorithmic_bytes_per_eval(st, spl.info()["n_tables"], n_orb)
+            variants[st] = {"value": evals_per_step / vt, "ms_per_step": vt * 1e3,
+                            "algorithmic_gbs": vb * evals_per_step / vt / 1e9,
+                            "frac_of_hbm": vb * evals_per_step / vt / 1e9 / hbm}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.storage, True)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": w.cell.name, "method": "smoothing B-spline + separate Laplacian table",
+                   "n_orb": n_orb, "grid": list(w.cell.grid), "walkers": w.cell.n_walkers,
+                   "electrons": w.cell.n_elec, "positions": n_pos, "storage": args.storage,
+                   "accumulate": "f64" if args.storage == "f64" else "f32",
+                   "table_bytes": info["table_bytes"], "lanes": info["lanes"], "tiles": info["tiles"],
+                   "l2": "table and outputs larger than L2 (no flush needed)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "bspline_vgl_kernel", "bytes_per_eval": bpe},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pos_h.numel() * 8),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "setup_s": setup_s,
+        "variants": variants,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3")
+    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--ref-sample", type=int, default=2048)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-pos", type=int, default=None, help="use only the first N positions (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

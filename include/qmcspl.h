@@ -1,0 +1,221 @@
+/*
+ * qmcspl.h -- C ABI of the GB300 (sm_103a) planewave-orbital spline library.
+ *
+ * The library evaluates single-particle orbitals given as planewave sums
+ *     phi_n(r) = sum_G c_{G n} exp(i G.r)                        (paper Eq. pw_orbital)
+ * with their Cartesian gradients and Laplacians at many electron positions, through
+ * a tricubic polynomial basis on a periodic grid (Parker, Umrigar, Alfe, Hennig,
+ * Wilkins, arXiv:1309.6250, Sec. II and the Appendix):
+ *   - smoothing B-splines, Eq. (b-splinecoefficients)          QMCSPL_BSPLINE_SMOOTH
+ *   - interpolating B-splines, Appendix "Interpolating ..."    QMCSPL_BSPLINE_INTERP
+ *   - cubic Lagrange interpolation, Eq. (lagrangeinterpolation3), with the separate
+ *     gradient and Laplacian tables of Sec. III C            QMCSPL_LAGRANGE
+ *   - cubic pp-splines, Eq. (pp-splineinterpolation3)          QMCSPL_PPSPLINE
+ * B-splines may carry the separate Laplacian table recommended in Sec. III A / IV.
+ *
+ * Conventions shared by every call
+ *   - Status: every call returns QMCSPL_OK (0) or one of the QMCSPL_ERR_* codes;
+ *     qmcspl_last_error() then gives a message (per calling thread).  Arguments are
+ *     validated before anything is launched; on an error nothing is written.
+ *   - Pointers named *_host are host memory; all other array pointers of the eval
+ *     calls are device memory of the device the handle was created on.  The caller
+ *     owns every buffer it passes; the library owns the coefficient tables.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Device work is
+ *     asynchronous on that stream unless a call says otherwise.  Errors a kernel
+ *     detects on the device (a non-finite position) are recorded in the handle and
+ *     reported by qmcspl_sync().
+ *   - Lattice: row-major 3x3 with the lattice vectors a_1, a_2, a_3 as COLUMNS (bohr),
+ *     so r = a s for crystal coordinates s.  Positions may lie anywhere; they are
+ *     wrapped into the cell (Eq. reducedcoordinate).
+ *   - Output dtype: double for QMCSPL_F64 tables, float for QMCSPL_F32 / QMCSPL_BF16.
+ *     Output layouts (P positions, O orbitals, row-major):
+ *         val [P][O],   grad [P][3][O] (Cartesian x, y, z),   lap [P][O].
+ */
+#ifndef QMCSPL_H
+#define QMCSPL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qmcspl_s* qmcspl_t;   /* opaque handle owning the coefficient tables */
+
+enum qmcspl_status {
+    QMCSPL_OK = 0,
+    QMCSPL_ERR_ARG = 1,            /* invalid argument (null pointer, size, enum value) */
+    QMCSPL_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    QMCSPL_ERR_OOM = 3,            /* device or host allocation failed */
+    QMCSPL_ERR_UNSUPPORTED = 4,    /* combination not supported (e.g. backward of pp) */
+    QMCSPL_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
+    QMCSPL_ERR_NOT_HERMITIAN = 6,  /* coefficients do not give a real (Gamma-point) orbital */
+    QMCSPL_ERR_DEVICE = 7          /* a kernel flagged bad input (non-finite position) */
+};
+
+enum qmcspl_method {
+    QMCSPL_BSPLINE_SMOOTH = 0,     /* Eq. (b-splinecoefficients): beta = sum c_G/gamma_G e^{iG.x} */
+    QMCSPL_BSPLINE_INTERP = 1,     /* interpolating B-spline (cyclic tridiagonal system) */
+    QMCSPL_LAGRANGE = 2,           /* cubic Lagrange, five tables (phi, grad phi, lap phi) */
+    QMCSPL_PPSPLINE = 3            /* cubic pp-spline, eight coefficients per grid point */
+};
+
+enum qmcspl_storage {
+    QMCSPL_F64 = 0,                /* tables and arithmetic in double */
+    QMCSPL_F32 = 1,                /* float tables, float accumulation */
+    QMCSPL_BF16 = 2                /* bfloat16 tables, float accumulation */
+};
+
+typedef struct {
+    int method;        /* enum qmcspl_method */
+    int storage;       /* enum qmcspl_storage */
+    int separate_lap;  /* B-splines: 1 = also build the Laplacian table (Sec. III C,
+                          memory x2) and return its value as the Laplacian; 0 = the
+                          Laplacian of the spline itself.  Ignored by Lagrange (always
+                          its own Laplacian table) and pp (always the spline's own). */
+} qmcspl_opts;
+
+typedef struct {
+    int dims[3];             /* grid points along a_1, a_2, a_3 */
+    int n_orb;               /* orbitals */
+    int n_orb_padded;        /* orbitals per stored row (zero padded) */
+    int method, storage, separate_lap;
+    int n_tables;            /* value tables stored: 1, 2 (B-spline + Laplacian), 5, or 1 pp table of 8 entries */
+    int entries_per_point;   /* stored values per grid point per orbital row: 1, or 8 (pp) */
+    int rows_z;              /* stored z planes per (x, y) column (periodic ghost planes included) */
+    int lanes;               /* threads sharing one position in the eval kernel */
+    int tiles;               /* orbital tiles per position */
+    long long table_bytes;   /* device bytes of all coefficient tables */
+    long long n_pw;          /* planewaves the tables were built from */
+} qmcspl_info_t;
+
+/*
+ * qmcspl_create -- build the coefficient tables of n_orb real orbitals.
+ *
+ * Paper: Eq. (pw_orbital) defines the input; the Appendix defines the tables:
+ * smoothing coefficients by Eq. (b-splinecoefficients), interpolating coefficients by
+ * the periodic system of "Interpolating B-spline coefficients", Lagrange tables as the
+ * grid values of phi, its gradient and Laplacian, pp tables by
+ * Eq. (pp-splinecoefficients3).
+ *
+ *   out      [out] receives the handle (set to NULL on failure)
+ *   lattice  host double[9], row-major, columns = lattice vectors (bohr); non-singular
+ *   dims     host int[3], grid points per lattice vector, each in [4, 4096]
+ *   n_pw     number of planewaves, >= 1
+ *   miller   host int[n_pw][3], integer Miller indices n of G = 2 pi a^{-T} n; each
+ *            G must appear once and -G must be present (real orbitals)
+ *   n_orb    number of orbitals, >= 1
+ *   coef     host double[n_orb][n_pw][2], (re, im) of c_{G n}; must satisfy
+ *            c_{-G} = conj(c_G) to 1e-12 relative, else QMCSPL_ERR_NOT_HERMITIAN
+ *   opts     host pointer to the options (method, storage, separate_lap)
+ *   stream   cudaStream_t the construction runs on; the call blocks until the tables
+ *            are complete, then frees its temporaries
+ *
+ * The tables live on the current CUDA device.  The construction arithmetic (frequency
+ * grid, symbol division, inverse transforms) is FP64 whatever the storage type.
+ */
+int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int n_pw,
+                  const int* miller, int n_orb, const double* coef, const qmcspl_opts* opts,
+                  void* stream);
+
+/* qmcspl_destroy -- synchronise the device and free the handle and its tables.
+ * NULL is accepted. */
+int qmcspl_destroy(qmcspl_t h);
+
+/* qmcspl_info -- describe a handle (host struct filled in). */
+int qmcspl_info(qmcspl_t h, qmcspl_info_t* out);
+
+/*
+ * qmcspl_eval_vgl -- value, Cartesian gradient and Laplacian of every orbital at
+ * every position.
+ *
+ * Paper: Eq. (reducedcoordinate) maps r to a grid cell and t in [0,1)^3; the tricubic
+ * sum of Eq. (b-splineapproximation) / (lagrangeinterpolation3) /
+ * (pp-splineinterpolation3) gives the value and reduced derivatives; the chain rule
+ * of Sec. II (Coordinates) gives grad = N_i (a^-1)^T grad_t and
+ * lap = sum_ij N_i N_j (a^-1 a^-T)_ij d2/dt_i dt_j.  With a separate Laplacian table
+ * (B-splines) or for Lagrange, lap (and for Lagrange grad) is the interpolated table.
+ *
+ *   pos    device double[n_pos][3], Cartesian (bohr); non-finite entries give NaN
+ *          outputs for that position and QMCSPL_ERR_DEVICE at qmcspl_sync
+ *   n_pos  >= 0 (0 is a no-op)
+ *   val, grad, lap  device outputs in the layouts above (double for F64 tables, float
+ *          otherwise); any of them may be NULL to skip it
+ *   stream cudaStream_t; asynchronous
+ */
+int qmcspl_eval_vgl(qmcspl_t h, const double* pos, long long n_pos, void* val, void* grad,
+                    void* lap, void* stream);
+
+/*
+ * qmcspl_eval_vgl_host -- qmcspl_eval_vgl from and to HOST memory.
+ *
+ * Same computation; the library stages the positions to the device and the outputs
+ * back in chunks, overlapping copies and kernels on internal streams ordered after
+ * `stream`.  Blocking: on return the host outputs are complete.  For full copy speed
+ * the host buffers should be page-locked (cudaHostAlloc / pinned torch tensors).
+ * Device staging buffers are allocated on first use and kept by the handle.
+ */
+int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, void* val_host,
+                         void* grad_host, void* lap_host, void* stream);
+
+/*
+ * qmcspl_eval_vgl_backward -- adjoint of qmcspl_eval_vgl for the B-spline methods.
+ *
+ * Not in the paper: for a scalar loss L with upstream gradients gv = dL/dval,
+ * gg = dL/dgrad, gl = dL/dlap (same layouts and dtype as the outputs; any may be NULL
+ * meaning zero) it gives
+ *   dcoef     device, canonical layout [Nx][Ny][Nz][O] (unpadded, no ghost planes),
+ *             output dtype; ACCUMULATED (+=) with dL/dbeta of the value table.
+ *             NULL skips the coefficient adjoint.
+ *   dcoef_lap same for the separate Laplacian table (required iff separate_lap and
+ *             dcoef is given; must be NULL otherwise).
+ *   dpos      device double[n_pos][3], WRITTEN with dL/dr.  NULL skips it.
+ * The coefficient adjoint scatters into 64 stencil rows per position with atomic
+ * adds, so its summation order (and last bits) vary from run to run.
+ * QMCSPL_ERR_UNSUPPORTED for Lagrange and pp handles.
+ */
+int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, const void* gv,
+                             const void* gg, const void* gl, void* dcoef, void* dcoef_lap,
+                             double* dpos, void* stream);
+
+/*
+ * qmcspl_eval_batched -- qmcspl_eval_vgl for several handles in ONE kernel launch.
+ *
+ * Walkers of cells with different orbital counts and grids (same storage type, all
+ * B-spline methods) go through one launch whose work list balances the cells.
+ *   n_cells   1..QMCSPL_MAX_BATCH
+ *   h         host array of n_cells handles (same device, same storage type)
+ *   pos, val, grad, lap   host arrays of n_cells DEVICE pointers (layouts as above;
+ *             val/grad/lap entries may be NULL)
+ *   n_pos     host array of n_cells position counts
+ * Asynchronous on `stream`.  The call uploads its descriptors with a copy on `stream`
+ * from a buffer owned by the first handle, so calls on that handle are ordered by
+ * the stream.
+ */
+#define QMCSPL_MAX_BATCH 64
+int qmcspl_eval_batched(int n_cells, const qmcspl_t* h, const double* const* pos,
+                        const long long* n_pos, void* const* val, void* const* grad,
+                        void* const* lap, void* stream);
+
+/*
+ * qmcspl_get_table -- copy one stored table back to the host in canonical layout
+ * double[Nx][Ny][Nz][O] (padding and ghost planes removed, converted to double).
+ *   table  B-splines: 0 = coefficients, 1 = Laplacian coefficients (separate_lap);
+ *          Lagrange: 0..4 = phi, d_x phi, d_y phi, d_z phi, lap phi;
+ *          pp: 0..7 = sigma^{kappa mu nu} with index 4(kappa-1) + 2(mu-1) + (nu-1).
+ * Blocking.
+ */
+int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream);
+
+/* qmcspl_sync -- synchronise `stream` and report (then clear) any device-side error the
+ * handle's kernels recorded: QMCSPL_ERR_DEVICE for non-finite positions. */
+int qmcspl_sync(qmcspl_t h, void* stream);
+
+/* qmcspl_last_error -- message of the last failed call on this thread ("" if none). */
+const char* qmcspl_last_error(void);
+
+/* qmcspl_version -- library version as 10000*major + 100*minor + patch. */
+int qmcspl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QMCSPL_H */

@@ -1,0 +1,99 @@
+"""ctypes loader for libqmcspl.so, the CUDA C-ABI library declared in include/qmcspl.h.
+
+Argument marshalling only.  There is no fallback: if the library cannot be found or
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqmcspl.so")
+
+OK = 0
+ERR_ARG = 1
+ERR_CUDA = 2
+ERR_OOM = 3
+ERR_UNSUPPORTED = 4
+ERR_TIMEOUT = 5
+ERR_NOT_HERMITIAN = 6
+ERR_DEVICE = 7
+
+BSPLINE_SMOOTH = 0
+BSPLINE_INTERP = 1
+LAGRANGE = 2
+PPSPLINE = 3
+
+F64 = 0
+F32 = 1
+BF16 = 2
+
+MAX_BATCH = 64
+
+METHODS = {"smooth": BSPLINE_SMOOTH, "interp": BSPLINE_INTERP, "lagrange": LAGRANGE, "pp": PPSPLINE}
+STORAGE = {"f64": F64, "f32": F32, "bf16": BF16}
+
+
+class QmcsplError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("qmcspl error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("storage", ctypes.c_int), ("separate_lap", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 3), ("n_orb", ctypes.c_int), ("n_orb_padded", ctypes.c_int),
+                ("method", ctypes.c_int), ("storage", ctypes.c_int), ("separate_lap", ctypes.c_int),
+                ("n_tables", ctypes.c_int), ("entries_per_point", ctypes.c_int),
+                ("rows_z", ctypes.c_int), ("lanes", ctypes.c_int), ("tiles", ctypes.c_int),
+                ("table_bytes", ctypes.c_longlong), ("n_pw", ctypes.c_longlong)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+VP = ctypes.c_void_p
+LL = ctypes.c_longlong
+I = ctypes.c_int
+
+# (name, restype, argtypes) of every entry point of include/qmcspl.h
+PROTOTYPES = [
+    ("qmcspl_create", I, [ctypes.POINTER(VP), VP, VP, I, VP, I, VP, ctypes.POINTER(Opts), VP]),
+    ("qmcspl_destroy", I, [VP]),
+    ("qmcspl_info", I, [VP, ctypes.POINTER(Info)]),
+    ("qmcspl_eval_vgl", I, [VP, VP, LL, VP, VP, VP, VP]),
+    ("qmcspl_eval_vgl_host", I, [VP, VP, LL, VP, VP, VP, VP]),
+    ("qmcspl_eval_vgl_backward", I, [VP, VP, LL, VP, VP, VP, VP, VP, VP, VP]),
+    ("qmcspl_eval_batched", I, [I, VP, VP, VP, VP, VP, VP, VP]),
+    ("qmcspl_get_table", I, [VP, I, VP, VP]),
+    ("qmcspl_sync", I, [VP, VP]),
+    ("qmcspl_last_error", ctypes.c_char_p, []),
+    ("qmcspl_version", I, []),
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load the library (once) and attach the prototypes.  Raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise QmcsplError(ERR_UNSUPPORTED,
+                                  "libqmcspl.so not built (run __graft_entry__.build()): %s" % path)
+            lib = ctypes.CDLL(path)
+            for name, res, args in PROTOTYPES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def check(rc: int) -> None:
+    if rc != OK:
+        raise QmcsplError(rc, load().qmcspl_last_error().decode(errors="replace"))

@@ -1,0 +1,169 @@
+"""Python face of the qmcspl C ABI: device memory and streams from PyTorch, all
+arithmetic in the CUDA library.
+
+    spl = OrbitalSplines(lattice, dims, miller, coef, method="smooth", storage="f32",
+                         separate_lap=True)
+    val, grad, lap = spl.eval_vgl(pos)          # pos: float64 CUDA tensor [P, 3]
+
+Output layouts: val [P, O], grad [P, 3, O] (Cartesian), lap [P, O]; float64 for "f64"
+tables, float32 otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib
+
+
+def _stream_handle(stream: Optional[torch.cuda.Stream]) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+class OrbitalSplines:
+    """Coefficient tables of n_orb real planewave orbitals on one CUDA device."""
+
+    def __init__(self, lattice, dims: Sequence[int], miller, coef, method: str = "smooth",
+                 storage: str = "f32", separate_lap: bool = True,
+                 device: Optional[torch.device] = None,
+                 stream: Optional[torch.cuda.Stream] = None):
+        self.lib = _lib.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(3, 3))
+        dm = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(3))
+        mil = np.ascontiguousarray(np.asarray(miller, dtype=np.int32).reshape(-1, 3))
+        c = np.asarray(coef)
+        if c.ndim == 1:
+            c = c[None, :]
+        c = np.ascontiguousarray(c.astype(np.complex128))
+        n_orb, n_pw = c.shape
+        if mil.shape[0] != n_pw:
+            raise ValueError("miller and coef disagree on the number of planewaves")
+        craw = np.ascontiguousarray(c.view(np.float64).reshape(n_orb, n_pw, 2))
+        opts = _lib.Opts(_lib.METHODS[method], _lib.STORAGE[storage], int(bool(separate_lap)))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = _stream_handle(stream)
+            _lib.check(self.lib.qmcspl_create(ctypes.byref(h), lat.ctypes.data, dm.ctypes.data, n_pw,
+                                              mil.ctypes.data, n_orb, craw.ctypes.data,
+                                              ctypes.byref(opts), st))
+        self.handle = h
+        self.method = method
+        self.storage = storage
+        self.n_orb = n_orb
+        self.dims = tuple(int(x) for x in dm)
+        self.lattice = lat
+        self.out_dtype = torch.float64 if storage == "f64" else torch.float32
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.qmcspl_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- queries -----------------------------------------------------------
+    def info(self) -> dict:
+        inf = _lib.Info()
+        _lib.check(self.lib.qmcspl_info(self.handle, ctypes.byref(inf)))
+        return {k: (list(getattr(inf, k)) if k == "dims" else getattr(inf, k)) for k, _ in inf._fields_}
+
+    def get_table(self, index: int = 0, stream=None) -> np.ndarray:
+        """Stored table `index` in canonical layout [Nx, Ny, Nz, O] as float64."""
+        out = np.zeros(self.dims + (self.n_orb,), dtype=np.float64)
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.qmcspl_get_table(self.handle, int(index), out.ctypes.data,
+                                                 _stream_handle(stream)))
+        return out
+
+    def sync(self, stream=None) -> None:
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.qmcspl_sync(self.handle, _stream_handle(stream)))
+
+    # -- evaluation --------------------------------------------------------
+    def alloc_outputs(self, n_pos: int):
+        kw = dict(dtype=self.out_dtype, device=self.device)
+        return (torch.empty((n_pos, self.n_orb), **kw), torch.empty((n_pos, 3, self.n_orb), **kw),
+                torch.empty((n_pos, self.n_orb), **kw))
+
+    def _check_pos(self, pos: torch.Tensor) -> torch.Tensor:
+        if pos.device != self.device or pos.dtype != torch.float64:
+            raise ValueError("positions must be a float64 tensor on %s" % self.device)
+        return pos.reshape(-1, 3).contiguous()
+
+    def eval_vgl(self, pos: torch.Tensor, out=None, stream=None,
+                 want: Tuple[bool, bool, bool] = (True, True, True)):
+        """Value, Cartesian gradient and Laplacian at positions pos [P, 3] (device)."""
+        pos = self._check_pos(pos)
+        n = pos.shape[0]
+        val, grad, lap = out if out is not None else self.alloc_outputs(n)
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.qmcspl_eval_vgl(
+                self.handle, _ptr(pos), n, _ptr(val if want[0] else None),
+                _ptr(grad if want[1] else None), _ptr(lap if want[2] else None), _stream_handle(stream)))
+        return val, grad, lap
+
+    def eval_vgl_host(self, pos: torch.Tensor, out=None, stream=None):
+        """Same computation from and to host memory (pinned tensors for full speed)."""
+        if pos.device.type != "cpu" or pos.dtype != torch.float64:
+            raise ValueError("positions must be a float64 CPU tensor")
+        pos = pos.reshape(-1, 3).contiguous()
+        n = pos.shape[0]
+        if out is None:
+            out = (torch.empty((n, self.n_orb), dtype=self.out_dtype),
+                   torch.empty((n, 3, self.n_orb), dtype=self.out_dtype),
+                   torch.empty((n, self.n_orb), dtype=self.out_dtype))
+        val, grad, lap = out
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.qmcspl_eval_vgl_host(self.handle, _ptr(pos), n, _ptr(val), _ptr(grad),
+                                                     _ptr(lap), _stream_handle(stream)))
+        return val, grad, lap
+
+    def backward(self, pos: torch.Tensor, gv=None, gg=None, gl=None, dcoef=None, dcoef_lap=None,
+                 want_dpos: bool = True, stream=None):
+        """Adjoint of eval_vgl: accumulates dL/dbeta into dcoef (and dcoef_lap) and
+        returns dL/dr [P, 3] (float64) when want_dpos."""
+        pos = self._check_pos(pos)
+        n = pos.shape[0]
+        dpos = torch.empty((n, 3), dtype=torch.float64, device=self.device) if want_dpos else None
+        c = lambda t: None if t is None else t.contiguous()
+        gv, gg, gl = c(gv), c(gg), c(gl)
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.qmcspl_eval_vgl_backward(
+                self.handle, _ptr(pos), n, _ptr(gv), _ptr(gg), _ptr(gl), _ptr(dcoef), _ptr(dcoef_lap),
+                _ptr(dpos), _stream_handle(stream)))
+        return dpos
+
+    def coef_shape(self) -> Tuple[int, int, int, int]:
+        return self.dims + (self.n_orb,)
+
+
+def eval_batched(splines: Sequence[OrbitalSplines], positions: Sequence[torch.Tensor],
+                 outs=None, stream=None):
+    """One kernel launch evaluating several cells (handles of one storage type)."""
+    lib = _lib.load()
+    n = len(splines)
+    if outs is None:
+        outs = [s.alloc_outputs(p.reshape(-1, 3).shape[0]) for s, p in zip(splines, positions)]
+    H = (ctypes.c_void_p * n)(*[s.handle.value for s in splines])
+    P = (ctypes.c_void_p * n)(*[p.data_ptr() for p in positions])
+    NP = (ctypes.c_longlong * n)(*[p.reshape(-1, 3).shape[0] for p in positions])
+    V = (ctypes.c_void_p * n)(*[o[0].data_ptr() for o in outs])
+    G = (ctypes.c_void_p * n)(*[o[1].data_ptr() for o in outs])
+    L = (ctypes.c_void_p * n)(*[o[2].data_ptr() for o in outs])
+    with torch.cuda.device(splines[0].device):
+        _lib.check(lib.qmcspl_eval_batched(n, H, P, NP, V, G, L, _stream_handle(stream)))
+    return outs

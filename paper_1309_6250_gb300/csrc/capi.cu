@@ -1,0 +1,520 @@
+// capi.cu -- the extern "C" entry points declared in include/qmcspl.h.
+//
+// Host-side work only: argument validation, the Hermitian check of the planewave
+// coefficients (real Gamma-point orbitals, Sec. III), the chain-rule matrices of
+// Sec. II (Coordinates), table sizing, and dispatch to the kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_map>
+
+#include "qmcspl_internal.cuh"
+
+namespace qmcspl {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return QMCSPL_OK;
+    cudaGetLastError();   // clear a sticky launch error so later calls can proceed
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? QMCSPL_ERR_OOM : QMCSPL_ERR_CUDA;
+}
+
+int sm_count()
+{
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 152;
+    }
+    return cached[dev];
+}
+
+void fill_eval_args(const Handle* h, EvalArgs* a)
+{
+    std::memset(a, 0, sizeof(*a));
+    for (int t = 0; t < 5; ++t) a->tab[t] = t < h->n_tables ? h->table(t) : nullptr;
+    a->row_stride = h->n_orb_p * h->entries;
+    a->col_stride = (long long)h->rows_z * a->row_stride;
+    a->nx = h->dims[0];
+    a->ny = h->dims[1];
+    a->nz = h->dims[2];
+    a->n_orb = h->n_orb;
+    a->lanes_log2 = h->lanes_log2;
+    a->tiles = h->tiles;
+    std::memcpy(a->ainv, h->ainv, sizeof(a->ainv));
+    std::memcpy(a->mg, h->mg, sizeof(a->mg));
+    std::memcpy(a->ml, h->ml, sizeof(a->ml));
+    a->err = h->d_err;
+}
+
+namespace {
+
+bool inv3(const double m[9], double out[9])
+{
+    const double c00 = m[4] * m[8] - m[5] * m[7];
+    const double c01 = m[5] * m[6] - m[3] * m[8];
+    const double c02 = m[3] * m[7] - m[4] * m[6];
+    const double det = m[0] * c00 + m[1] * c01 + m[2] * c02;
+    // singular (or nearly) relative to the product of the column lengths
+    double vol = 1.0;
+    for (int j = 0; j < 3; ++j) vol *= std::sqrt(m[j] * m[j] + m[3 + j] * m[3 + j] + m[6 + j] * m[6 + j]);
+    if (!std::isfinite(det) || std::fabs(det) <= 1e-12 * vol) return false;
+    const double id = 1.0 / det;
+    out[0] = c00 * id;
+    out[1] = (m[2] * m[7] - m[1] * m[8]) * id;
+    out[2] = (m[1] * m[5] - m[2] * m[4]) * id;
+    out[3] = c01 * id;
+    out[4] = (m[0] * m[8] - m[2] * m[6]) * id;
+    out[5] = (m[2] * m[3] - m[0] * m[5]) * id;
+    out[6] = c02 * id;
+    out[7] = (m[1] * m[6] - m[0] * m[7]) * id;
+    out[8] = (m[0] * m[4] - m[1] * m[3]) * id;
+    return true;
+}
+
+inline long long miller_key(int a, int b, int c)
+{
+    const long long off = 1LL << 20;
+    return ((a + off) << 42) | ((b + off) << 21) | (c + off);
+}
+
+// Real (Gamma-point) orbitals need every -G and c_{-G} = conj(c_G).
+int check_hermitian(int n_pw, const int* miller, int n_orb, const double* coef)
+{
+    std::unordered_map<long long, int> index;
+    index.reserve((size_t)n_pw * 2);
+    for (int g = 0; g < n_pw; ++g) {
+        const int a = miller[3 * g], b = miller[3 * g + 1], c = miller[3 * g + 2];
+        if (std::abs(a) >= (1 << 20) || std::abs(b) >= (1 << 20) || std::abs(c) >= (1 << 20))
+            return set_error(QMCSPL_ERR_ARG, "Miller index out of range");
+        if (!index.emplace(miller_key(a, b, c), g).second)
+            return set_error(QMCSPL_ERR_ARG, "duplicate Miller index " + std::to_string(g));
+    }
+    double cmax = 0.0;
+    for (long long i = 0; i < 2LL * n_pw * n_orb; ++i) {
+        if (!std::isfinite(coef[i])) return set_error(QMCSPL_ERR_ARG, "non-finite coefficient");
+        cmax = std::fmax(cmax, std::fabs(coef[i]));
+    }
+    const double tol = 1e-12 * (cmax > 0 ? cmax : 1.0);
+    for (int g = 0; g < n_pw; ++g) {
+        auto it = index.find(miller_key(-miller[3 * g], -miller[3 * g + 1], -miller[3 * g + 2]));
+        if (it == index.end())
+            return set_error(QMCSPL_ERR_NOT_HERMITIAN, "planewave " + std::to_string(g) + " has no -G partner");
+        const int m = it->second;
+        for (int o = 0; o < n_orb; ++o) {
+            const double* c1 = coef + 2 * ((size_t)o * n_pw + g);
+            const double* c2 = coef + 2 * ((size_t)o * n_pw + m);
+            if (std::fabs(c1[0] - c2[0]) > tol || std::fabs(c1[1] + c2[1]) > tol)
+                return set_error(QMCSPL_ERR_NOT_HERMITIAN,
+                                 "c_{-G} != conj(c_G) for planewave " + std::to_string(g) +
+                                     ", orbital " + std::to_string(o));
+        }
+    }
+    return QMCSPL_OK;
+}
+
+// Lanes per position and orbital tiles: rows of n 16-byte chunks are split over
+// L = 2^k lanes and ceil(n / L) tiles, taking the widest L whose padding stays
+// within 1/8 of the row.
+void choose_lanes(int n_chunks, int& lanes_log2, int& tiles)
+{
+    for (int lg = 5; lg >= 0; --lg) {
+        const int L = 1 << lg;
+        const long long padded = (long long)((n_chunks + L - 1) / L) * L;
+        if (L == 1 || padded * 8 <= (long long)n_chunks * 9) {
+            lanes_log2 = lg;
+            tiles = (n_chunks + L - 1) / L;
+            return;
+        }
+    }
+}
+
+void free_handle(Handle* h)
+{
+    if (!h) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    if (h->tables) cudaFree(h->tables);
+    if (h->d_err) cudaFree(h->d_err);
+    for (int b = 0; b < 2; ++b) {
+        if (h->st_pos[b]) cudaFree(h->st_pos[b]);
+        if (h->st_out[b]) cudaFree(h->st_out[b]);
+        if (h->st_stream[b]) cudaStreamDestroy(h->st_stream[b]);
+    }
+    if (h->st_ready)
+        for (int i = 0; i < 6; ++i) cudaEventDestroy(h->st_ev[i]);
+    if (h->batch_desc) cudaFree(h->batch_desc);
+    delete h;
+    cudaSetDevice(prev);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+}  // namespace qmcspl
+
+using namespace qmcspl;
+
+extern "C" {
+
+int qmcspl_version(void) { return 10000 * 1 + 100 * 0 + 0; }
+
+const char* qmcspl_last_error(void) { return g_err.c_str(); }
+
+int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int n_pw,
+                  const int* miller, int n_orb, const double* coef, const qmcspl_opts* opts,
+                  void* stream)
+{
+    g_err.clear();
+    if (!out) return set_error(QMCSPL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!lattice || !dims || !miller || !coef || !opts)
+        return set_error(QMCSPL_ERR_ARG, "NULL argument");
+    if (n_pw < 1) return set_error(QMCSPL_ERR_ARG, "n_pw must be >= 1");
+    if (n_orb < 1) return set_error(QMCSPL_ERR_ARG, "n_orb must be >= 1");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 4 || dims[a] > kMaxDim)
+            return set_error(QMCSPL_ERR_ARG, "grid dims must be in [4, 512]");
+    if (opts->method < QMCSPL_BSPLINE_SMOOTH || opts->method > QMCSPL_PPSPLINE)
+        return set_error(QMCSPL_ERR_ARG, "unknown method");
+    if (opts->storage < QMCSPL_F64 || opts->storage > QMCSPL_BF16)
+        return set_error(QMCSPL_ERR_ARG, "unknown storage type");
+    for (int i = 0; i < 9; ++i)
+        if (!std::isfinite(lattice[i])) return set_error(QMCSPL_ERR_ARG, "non-finite lattice");
+    double ainv[9];
+    if (!inv3(lattice, ainv)) return set_error(QMCSPL_ERR_ARG, "singular lattice");
+    int rc = check_hermitian(n_pw, miller, n_orb, coef);
+    if (rc != QMCSPL_OK) return rc;
+
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) return set_error(QMCSPL_ERR_OOM, "host allocation failed");
+    cudaGetDevice(&h->device);
+    h->method = opts->method;
+    h->storage = opts->storage;
+    const bool bspline = h->method == QMCSPL_BSPLINE_SMOOTH || h->method == QMCSPL_BSPLINE_INTERP;
+    h->separate_lap = bspline ? (opts->separate_lap != 0) : (h->method == QMCSPL_LAGRANGE);
+    for (int a = 0; a < 3; ++a) h->dims[a] = dims[a];
+    h->n_orb = n_orb;
+    h->n_pw = n_pw;
+    std::memcpy(h->lattice, lattice, sizeof(h->lattice));
+    std::memcpy(h->ainv, ainv, sizeof(h->ainv));
+    // chain rule: grad_cart[a] = sum_i N_i ainv[i][a] grad_t[i];
+    // lap = sum_ij N_i N_j (a^-1 a^-T)_ij H_ij, off-diagonal terms counted twice
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < 3; ++i) h->mg[3 * a + i] = dims[i] * ainv[3 * i + a];
+    double M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int a = 0; a < 3; ++a) s += ainv[3 * i + a] * ainv[3 * j + a];
+            M[3 * i + j] = (double)dims[i] * dims[j] * s;
+        }
+    h->ml[0] = M[0];
+    h->ml[1] = M[4];
+    h->ml[2] = M[8];
+    h->ml[3] = 2.0 * M[1];
+    h->ml[4] = 2.0 * M[2];
+    h->ml[5] = 2.0 * M[5];
+
+    h->elem_bytes = h->storage == QMCSPL_F64 ? 8 : (h->storage == QMCSPL_F32 ? 4 : 2);
+    const int E = (int)(16 / h->elem_bytes);
+    const int n_chunks = (n_orb + E - 1) / E;
+    choose_lanes(n_chunks, h->lanes_log2, h->tiles);
+    h->n_orb_p = h->tiles * (1 << h->lanes_log2) * E;
+    switch (h->method) {
+    case QMCSPL_LAGRANGE: h->n_tables = 5; h->entries = 1; h->rows_z = dims[2] + 3; break;
+    case QMCSPL_PPSPLINE: h->n_tables = 1; h->entries = 8; h->rows_z = dims[2] + 1; break;
+    default: h->n_tables = h->separate_lap ? 2 : 1; h->entries = 1; h->rows_z = dims[2] + 3; break;
+    }
+    h->table_elems = (size_t)dims[0] * dims[1] * h->rows_z * h->entries * h->n_orb_p;
+
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t bytes = h->table_elems * h->elem_bytes * h->n_tables;
+    cudaError_t e = cudaMalloc(&h->tables, bytes);
+    if (e != cudaSuccess) {
+        rc = cuda_error(e, "cudaMalloc(tables)");
+        free_handle(h);
+        return rc;
+    }
+    e = cudaMalloc((void**)&h->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->tables, 0, bytes, st);
+    if (e != cudaSuccess) {
+        rc = cuda_error(e, "table initialisation");
+        free_handle(h);
+        return rc;
+    }
+    rc = build_tables(h, n_pw, miller, coef, st);
+    if (rc != QMCSPL_OK) {
+        free_handle(h);
+        return rc;
+    }
+    *out = h;
+    return QMCSPL_OK;
+}
+
+int qmcspl_destroy(qmcspl_t h)
+{
+    g_err.clear();
+    free_handle(h);
+    return QMCSPL_OK;
+}
+
+int qmcspl_info(qmcspl_t h, qmcspl_info_t* out)
+{
+    g_err.clear();
+    if (!h || !out) return set_error(QMCSPL_ERR_ARG, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    for (int a = 0; a < 3; ++a) out->dims[a] = h->dims[a];
+    out->n_orb = h->n_orb;
+    out->n_orb_padded = h->n_orb_p;
+    out->method = h->method;
+    out->storage = h->storage;
+    out->separate_lap = h->separate_lap;
+    out->n_tables = h->n_tables;
+    out->entries_per_point = h->entries;
+    out->rows_z = h->rows_z;
+    out->lanes = 1 << h->lanes_log2;
+    out->tiles = h->tiles;
+    out->table_bytes = (long long)(h->table_elems * h->elem_bytes * h->n_tables);
+    out->n_pw = h->n_pw;
+    return QMCSPL_OK;
+}
+
+static int eval_dispatch(Handle* h, const double* pos, long long n_pos, void* val, void* grad,
+                         void* lap, cudaStream_t st)
+{
+    switch (h->method) {
+    case QMCSPL_LAGRANGE: return launch_lagrange_vgl(h, pos, n_pos, val, grad, lap, st);
+    case QMCSPL_PPSPLINE: return launch_pp_vgl(h, pos, n_pos, val, grad, lap, st);
+    default: return launch_bspline_vgl(h, pos, n_pos, val, grad, lap, st);
+    }
+}
+
+int qmcspl_eval_vgl(qmcspl_t h, const double* pos, long long n_pos, void* val, void* grad,
+                    void* lap, void* stream)
+{
+    g_err.clear();
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
+    if (n_pos == 0) return QMCSPL_OK;
+    if (!pos) return set_error(QMCSPL_ERR_ARG, "pos is NULL");
+    if (n_pos > (1LL << 40)) return set_error(QMCSPL_ERR_ARG, "n_pos too large");
+    DeviceGuard dg(h->device);
+    return eval_dispatch(h, pos, n_pos, val, grad, lap, static_cast<cudaStream_t>(stream));
+}
+
+int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, void* val_host,
+                         void* grad_host, void* lap_host, void* stream)
+{
+    g_err.clear();
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
+    if (n_pos == 0) return QMCSPL_OK;
+    if (!pos_host) return set_error(QMCSPL_ERR_ARG, "pos_host is NULL");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t ob = (h->storage == QMCSPL_F64) ? 8 : 4;
+    const size_t row = (size_t)h->n_orb * ob;          // bytes of one output row
+    const long long cap = 1LL << 16;                   // positions per chunk
+    cudaError_t e;
+    if (!h->st_ready) {
+        for (int b = 0; b < 2; ++b) {
+            e = cudaStreamCreateWithFlags(&h->st_stream[b], cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate");
+        }
+        for (int i = 0; i < 6; ++i) {
+            e = cudaEventCreateWithFlags(&h->st_ev[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_error(e, "cudaEventCreate");
+        }
+        for (int b = 0; b < 2; ++b) {
+            e = cudaMalloc((void**)&h->st_pos[b], sizeof(double) * 3 * cap);
+            if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(staging)");
+            e = cudaMalloc(&h->st_out[b], row * 5 * cap);
+            if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(staging)");
+        }
+        h->st_cap = cap;
+        h->st_ready = true;
+    }
+    cudaStream_t s_in = h->st_stream[0], s_out = h->st_stream[1];
+    cudaEvent_t* ev_in = h->st_ev;          // positions of buffer b are on the device
+    cudaEvent_t* ev_done = h->st_ev + 2;    // kernel writing buffer b finished
+    cudaEvent_t* ev_free = h->st_ev + 4;    // outputs of buffer b copied out
+    // order the staging streams after the work already queued on `stream`
+    e = cudaEventRecord(ev_free[0], st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_free[1], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev_free[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_free[0], 0);
+    if (e != cudaSuccess) return cuda_error(e, "stream ordering");
+    char* hv = static_cast<char*>(val_host);
+    char* hg = static_cast<char*>(grad_host);
+    char* hl = static_cast<char*>(lap_host);
+    int rc = QMCSPL_OK;
+    int chunk_i = 0;
+    for (long long p0 = 0; p0 < n_pos; p0 += h->st_cap, ++chunk_i) {
+        const int b = chunk_i & 1;
+        const long long n = (n_pos - p0 < h->st_cap) ? n_pos - p0 : h->st_cap;
+        char* dv = static_cast<char*>(h->st_out[b]);
+        char* dg_ = dv + row * n;
+        char* dl = dg_ + row * 3 * n;
+        if ((e = cudaStreamWaitEvent(s_in, ev_free[b], 0)) != cudaSuccess) break;
+        if ((e = cudaMemcpyAsync(h->st_pos[b], pos_host + 3 * p0, sizeof(double) * 3 * n,
+                                 cudaMemcpyHostToDevice, s_in)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(ev_in[b], s_in)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(st, ev_in[b], 0)) != cudaSuccess) break;
+        rc = eval_dispatch(h, h->st_pos[b], n, hv ? dv : nullptr, hg ? dg_ : nullptr,
+                           hl ? dl : nullptr, st);
+        if (rc != QMCSPL_OK) break;
+        if ((e = cudaEventRecord(ev_done[b], st)) != cudaSuccess) break;
+        if ((e = cudaStreamWaitEvent(s_out, ev_done[b], 0)) != cudaSuccess) break;
+        if (hv && (e = cudaMemcpyAsync(hv + row * p0, dv, row * n, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) break;
+        if (hg && (e = cudaMemcpyAsync(hg + row * 3 * p0, dg_, row * 3 * n, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) break;
+        if (hl && (e = cudaMemcpyAsync(hl + row * p0, dl, row * n, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) break;
+        if ((e = cudaEventRecord(ev_free[b], s_out)) != cudaSuccess) break;
+    }
+    if (rc == QMCSPL_OK && e != cudaSuccess) rc = cuda_error(e, "host staging pipeline");
+    cudaError_t e2 = cudaStreamSynchronize(s_out);
+    cudaError_t e3 = cudaStreamSynchronize(st);
+    if (rc == QMCSPL_OK && e2 != cudaSuccess) rc = cuda_error(e2, "host staging copy-out");
+    if (rc == QMCSPL_OK && e3 != cudaSuccess) rc = cuda_error(e3, "host staging kernels");
+    return rc;
+}
+
+int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, const void* gv,
+                             const void* gg, const void* gl, void* dcoef, void* dcoef_lap,
+                             double* dpos, void* stream)
+{
+    g_err.clear();
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    if (h->method != QMCSPL_BSPLINE_SMOOTH && h->method != QMCSPL_BSPLINE_INTERP)
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is implemented for B-spline handles");
+    if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
+    if (dcoef_lap && !(h->separate_lap && dcoef))
+        return set_error(QMCSPL_ERR_ARG, "dcoef_lap needs a separate-Laplacian handle and dcoef");
+    if (dcoef && h->separate_lap && !dcoef_lap)
+        return set_error(QMCSPL_ERR_ARG, "separate-Laplacian handle: dcoef_lap is required with dcoef");
+    if (n_pos == 0) return QMCSPL_OK;
+    if (!pos) return set_error(QMCSPL_ERR_ARG, "pos is NULL");
+    DeviceGuard dg(h->device);
+    return launch_bspline_backward(h, pos, n_pos, gv, gg, gl, dcoef, dcoef_lap, dpos,
+                                   static_cast<cudaStream_t>(stream));
+}
+
+int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* pos,
+                        const long long* n_pos, void* const* val, void* const* grad,
+                        void* const* lap, void* stream)
+{
+    g_err.clear();
+    if (n_cells < 1 || n_cells > QMCSPL_MAX_BATCH)
+        return set_error(QMCSPL_ERR_ARG, "n_cells must be in [1, QMCSPL_MAX_BATCH]");
+    if (!hs || !pos || !n_pos || !val || !grad || !lap) return set_error(QMCSPL_ERR_ARG, "NULL argument");
+    for (int c = 0; c < n_cells; ++c) {
+        if (!hs[c]) return set_error(QMCSPL_ERR_ARG, "NULL handle in batch");
+        if (hs[c]->device != hs[0]->device) return set_error(QMCSPL_ERR_ARG, "handles on different devices");
+        if (hs[c]->storage != hs[0]->storage)
+            return set_error(QMCSPL_ERR_ARG, "handles of a batch must share the storage type");
+        if (hs[c]->method != QMCSPL_BSPLINE_SMOOTH && hs[c]->method != QMCSPL_BSPLINE_INTERP)
+            return set_error(QMCSPL_ERR_UNSUPPORTED, "batched evaluation is for B-spline handles");
+        if (n_pos[c] < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
+        if (n_pos[c] > 0 && !pos[c]) return set_error(QMCSPL_ERR_ARG, "pos is NULL");
+    }
+    DeviceGuard dg(hs[0]->device);
+    return launch_batched(n_cells, reinterpret_cast<const Handle* const*>(hs), pos, n_pos, val, grad,
+                          lap, static_cast<cudaStream_t>(stream));
+}
+
+int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream)
+{
+    g_err.clear();
+    if (!h || !out_host) return set_error(QMCSPL_ERR_ARG, "NULL argument");
+    const int n_avail = (h->method == QMCSPL_PPSPLINE) ? 8 : h->n_tables;
+    if (table < 0 || table >= n_avail) return set_error(QMCSPL_ERR_ARG, "table index out of range");
+    DeviceGuard dg(h->device);
+    const int tab = (h->method == QMCSPL_PPSPLINE) ? 0 : table;
+    const int entry = (h->method == QMCSPL_PPSPLINE) ? table : 0;
+    const size_t bytes = h->table_elems * h->elem_bytes;
+    char* raw = new (std::nothrow) char[bytes];
+    if (!raw) return set_error(QMCSPL_ERR_OOM, "host allocation failed");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(raw, h->table(tab), bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        delete[] raw;
+        return cuda_error(e, "table copy");
+    }
+    const int N1 = h->dims[0], N2 = h->dims[1], N3 = h->dims[2];
+    const int zshift = (h->method == QMCSPL_PPSPLINE) ? 0 : 1;
+    for (int x = 0; x < N1; ++x)
+        for (int y = 0; y < N2; ++y)
+            for (int z = 0; z < N3; ++z) {
+                const size_t src = ((((size_t)x * N2 + y) * h->rows_z + z + zshift) * h->entries + entry) *
+                                   h->n_orb_p;
+                double* dst = out_host + (((size_t)x * N2 + y) * N3 + z) * h->n_orb;
+                for (int o = 0; o < h->n_orb; ++o) {
+                    double v;
+                    if (h->storage == QMCSPL_F64) {
+                        std::memcpy(&v, raw + (src + o) * 8, 8);
+                    } else if (h->storage == QMCSPL_F32) {
+                        float f;
+                        std::memcpy(&f, raw + (src + o) * 4, 4);
+                        v = f;
+                    } else {
+                        uint16_t b;
+                        std::memcpy(&b, raw + (src + o) * 2, 2);
+                        const uint32_t u = (uint32_t)b << 16;
+                        float f;
+                        std::memcpy(&f, &u, 4);
+                        v = f;
+                    }
+                    dst[o] = v;
+                }
+            }
+    delete[] raw;
+    return QMCSPL_OK;
+}
+
+int qmcspl_sync(qmcspl_t h, void* stream)
+{
+    g_err.clear();
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    DeviceGuard dg(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+    int flag = 0;
+    e = cudaMemcpy(&flag, h->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "error word read");
+    if (flag) {
+        cudaMemset(h->d_err, 0, sizeof(int));
+        return set_error(QMCSPL_ERR_DEVICE, "a kernel saw a non-finite position");
+    }
+    return QMCSPL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,415 @@
+// construct.cu -- coefficient-table construction (FP64) for every method.
+//
+// Every table of the paper is a real-space sum over the planewave set,
+//     T(x_l) = sum_G w(G) c_G exp(i G.x_l),       x_l = grid point l (s = l / N),
+// with a per-planewave multiplier w(G):
+//   smoothing B-spline   1/gamma_G                        Eq. (b-splinecoefficients)
+//   interpolating        1/prod_m (1 + cos(th_m)/2)       the periodic [1/4 1 1/4] system
+//                                                         of "Interpolating B-spline
+//                                                         coefficients", diagonalised
+//   separate Laplacian   -|G|^2 times the above           Sec. III A / III C
+//   Lagrange tables      1, i G_x, i G_y, i G_z, -|G|^2   Sec. III C, Appendix A
+//   pp-spline sigma      prod over the axes labelled 2 of the periodic [4 1 .. 1]
+//                        second-derivative system, diagonalised:
+//                        6 (cos th - 1) / (2 + cos th)   Eq. (pp-splinecoefficients3)
+// with th_m = 2 pi n_m / N_m.  The cyclic systems are circulant, so dividing the folded
+// spectrum by their eigenvalues is their exact solution.
+//
+// Steps (all FP64, all in this file's kernels):
+//   1. scatter_kernel: fold c_G w(G) onto the N1 x N2 x N3 frequency grid
+//      F[k1][k2][k3][o] (aliases add up, as in the sum above);
+//   2. dft_pass_kernel x 3: separable inverse DFT along z, y, x, skipping frequency
+//      lines outside the planewave band and summing only over in-band frequencies;
+//   3. layout_kernel: real part -> stored dtype, orbital-innermost rows, ghost planes.
+// Orbitals are processed in chunks so the complex grids stay below a fixed budget.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "qmcspl_internal.cuh"
+
+namespace qmcspl {
+namespace {
+
+constexpr int kDftInner = 16;          // inner elements per DFT block (threads x)
+constexpr int kDftRows = 16;           // output rows in flight per DFT block (threads y)
+constexpr size_t kGridBudget = size_t(2) << 30;   // bytes per complex work grid
+
+struct ScatterArgs {
+    const int* miller;        // [n_pw][3]
+    const double2* coef;      // [n_orb][n_pw]
+    int n_pw;
+    int o0, oc;               // orbital chunk
+    int dims[3];
+    double bmat[9];           // G_a = sum_i bmat[3a+i] n_i
+    int kind;
+    int pp_axes;              // bit 2: x, bit 1: y, bit 0: z carry label 2
+    double2* F;               // [N1][N2][N3][oc]
+};
+
+__device__ __forceinline__ int fold(int n, int N)
+{
+    int k = n % N;
+    return k < 0 ? k + N : k;
+}
+
+// One axis of gamma_G: 3(3 - 4 cos th + cos 2th)/th^4 = 24 sin^4(th/2)/th^4, 3/2 at 0.
+__device__ __forceinline__ double gamma_axis(int n, int N)
+{
+    if (n == 0) return 1.5;
+    const double th = 6.283185307179586476925286766559 * (double)n / (double)N;
+    const double s = sinpi((double)n / (double)N);          // sin(th / 2)
+    const double s2 = s * s, th2 = th * th;
+    return 24.0 * s2 * s2 / (th2 * th2);
+}
+
+// Eigenvalue of the periodic interpolation matrix rows [1/4, 1, 1/4].
+__device__ __forceinline__ double interp_axis(int k, int N)
+{
+    return 1.0 + 0.5 * cospi(2.0 * (double)k / (double)N);
+}
+
+// Eigenvalue ratio of the pp system: rhs 6(f[i-1] - 2 f[i] + f[i+1]) over rows
+// [1, 4, 1]: 12 (cos th - 1)/(4 + 2 cos th) = -12 sin^2(th/2)/(2 + cos th).
+__device__ __forceinline__ double pp_axis(int k, int N)
+{
+    const double s = sinpi((double)k / (double)N);
+    return -12.0 * s * s / (2.0 + cospi(2.0 * (double)k / (double)N));
+}
+
+__global__ void scatter_kernel(const ScatterArgs a)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)a.oc * a.n_pw;
+    if (idx >= total) return;
+    const int oc = (int)(idx / a.n_pw);
+    const int g = (int)(idx - (long long)oc * a.n_pw);
+    const int n0 = a.miller[3 * g], n1 = a.miller[3 * g + 1], n2 = a.miller[3 * g + 2];
+    const int k0 = fold(n0, a.dims[0]), k1 = fold(n1, a.dims[1]), k2 = fold(n2, a.dims[2]);
+    const double2 c = a.coef[(long long)(a.o0 + oc) * a.n_pw + g];
+    const double G0 = a.bmat[0] * n0 + a.bmat[1] * n1 + a.bmat[2] * n2;
+    const double G1 = a.bmat[3] * n0 + a.bmat[4] * n1 + a.bmat[5] * n2;
+    const double G2 = a.bmat[6] * n0 + a.bmat[7] * n1 + a.bmat[8] * n2;
+    const double g2 = G0 * G0 + G1 * G1 + G2 * G2;
+    double wr = 1.0, wi = 0.0;   // complex multiplier w(G)
+    switch (a.kind) {
+    case kBuildSmoothValue:
+        wr = 1.0 / (gamma_axis(n0, a.dims[0]) * gamma_axis(n1, a.dims[1]) * gamma_axis(n2, a.dims[2]));
+        break;
+    case kBuildSmoothLap:
+        wr = -g2 / (gamma_axis(n0, a.dims[0]) * gamma_axis(n1, a.dims[1]) * gamma_axis(n2, a.dims[2]));
+        break;
+    case kBuildInterpValue:
+        wr = 1.0 / (interp_axis(k0, a.dims[0]) * interp_axis(k1, a.dims[1]) * interp_axis(k2, a.dims[2]));
+        break;
+    case kBuildInterpLap:
+        wr = -g2 / (interp_axis(k0, a.dims[0]) * interp_axis(k1, a.dims[1]) * interp_axis(k2, a.dims[2]));
+        break;
+    case kBuildGridValue: break;
+    case kBuildGridDx: wr = 0.0; wi = G0; break;
+    case kBuildGridDy: wr = 0.0; wi = G1; break;
+    case kBuildGridDz: wr = 0.0; wi = G2; break;
+    case kBuildGridLap: wr = -g2; break;
+    case kBuildPP:
+        if (a.pp_axes & 4) wr *= pp_axis(k0, a.dims[0]);
+        if (a.pp_axes & 2) wr *= pp_axis(k1, a.dims[1]);
+        if (a.pp_axes & 1) wr *= pp_axis(k2, a.dims[2]);
+        break;
+    default: break;
+    }
+    const double vr = c.x * wr - c.y * wi;
+    const double vi = c.x * wi + c.y * wr;
+    double2* dst = a.F + ((((long long)k0 * a.dims[1] + k1) * a.dims[2] + k2) * a.oc + oc);
+    atomicAdd(&dst->x, vr);
+    atomicAdd(&dst->y, vi);
+}
+
+struct DftArgs {
+    const double2* in;
+    double2* out;
+    long long outer;          // array viewed as [outer][N][inner]
+    long long inner;
+    int N;
+    int kmax;                 // nonzero input rows: k <= kmax or k >= N - kmax; -1 = all
+    int skip_mode;            // 0: every line; 1: outer = k1; 2: outer = k1 * D2 + k2
+    int D1, kmax1, D2, kmax2; // band of the outer index (skip_mode 1, 2)
+};
+
+__device__ __forceinline__ bool in_band(int k, int kmax, int N)
+{
+    return kmax < 0 || k <= kmax || k >= N - kmax;
+}
+
+// out[o][l][i] = sum_k in[o][k][i] exp(+2 pi i k l / N), k over the input band.
+__global__ void __launch_bounds__(kDftInner * kDftRows) dft_pass_kernel(const DftArgs a)
+{
+    extern __shared__ double2 smem[];
+    const long long tiles_inner = (a.inner + kDftInner - 1) / kDftInner;
+    const long long b = blockIdx.x;
+    const long long outer = b / tiles_inner;
+    const long long i = (b - outer * tiles_inner) * kDftInner + (threadIdx.x % kDftInner);
+    const int ty = threadIdx.x / kDftInner;
+    const int N = a.N;
+
+    bool zero = false;
+    if (a.skip_mode == 1) {
+        zero = !in_band((int)outer, a.kmax1, a.D1);
+    } else if (a.skip_mode == 2) {
+        const int q1 = (int)(outer / a.D2), q2 = (int)(outer % a.D2);
+        zero = !(in_band(q1, a.kmax1, a.D1) && in_band(q2, a.kmax2, a.D2));
+    }
+    if (zero) {   // every input row of this line is zero
+        if (i < a.inner)
+            for (int l = ty; l < N; l += kDftRows)
+                a.out[((long long)outer * N + l) * a.inner + i] = make_double2(0.0, 0.0);
+        return;
+    }
+    const int full = (a.kmax < 0 || 2 * a.kmax + 1 >= N);
+    const int nlo = full ? N : a.kmax + 1;           // rows k = 0 .. nlo-1
+    const int nhi = full ? 0 : a.kmax;               // rows k = N-kmax .. N-1
+    const int nb = nlo + nhi;
+    double2* rows = smem;                            // [nb][kDftInner]
+    double2* tw = smem + (size_t)nb * kDftInner;     // [N]
+    for (int m = threadIdx.x; m < N; m += blockDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)m / (double)N, &s, &c);
+        tw[m] = make_double2(c, s);
+    }
+    for (int j = ty; j < nb; j += kDftRows) {
+        const int k = j < nlo ? j : N - nhi + (j - nlo);
+        rows[j * kDftInner + (threadIdx.x % kDftInner)] =
+            (i < a.inner) ? a.in[((long long)outer * N + k) * a.inner + i] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (i >= a.inner) return;
+    const int tx = threadIdx.x % kDftInner;
+    for (int l = ty; l < N; l += kDftRows) {
+        double re = 0.0, im = 0.0;
+        int idx = 0;                                  // (k l) mod N for k = 0, 1, ...
+        for (int j = 0; j < nlo; ++j) {
+            const double2 v = rows[j * kDftInner + tx];
+            const double2 w = tw[idx];
+            re = fma(v.x, w.x, fma(-v.y, w.y, re));
+            im = fma(v.x, w.y, fma(v.y, w.x, im));
+            idx += l;
+            if (idx >= N) idx -= N;
+        }
+        if (nhi) {
+            idx = (int)(((long long)(N - nhi) * l) % N);
+            for (int j = nlo; j < nb; ++j) {
+                const double2 v = rows[j * kDftInner + tx];
+                const double2 w = tw[idx];
+                re = fma(v.x, w.x, fma(-v.y, w.y, re));
+                im = fma(v.x, w.y, fma(v.y, w.x, im));
+                idx += l;
+                if (idx >= N) idx -= N;
+            }
+        }
+        a.out[((long long)outer * N + l) * a.inner + i] = make_double2(re, im);
+    }
+}
+
+template <typename T> __device__ __forceinline__ T from_double(double v);
+template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_double<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v)
+{
+    return __double2bfloat16(v);
+}
+
+struct LayoutArgs {
+    const double2* F;         // [N1][N2][N3][oc]
+    void* tab;                // this table
+    int N1, N2, N3;
+    int oc, o0;
+    int o_p;
+    int rows_z;
+    int entries, entry;
+    int zshift;               // 1: zz = z + 1 (B-spline / Lagrange); 0: zz = z (pp)
+};
+
+// table[x][y][zz][entry][o0 + o] = Re F[x][y][(zz - zshift) mod N3][o]
+template <typename T>
+__global__ void layout_kernel(const LayoutArgs a)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)a.N1 * a.N2 * a.rows_z * a.oc;
+    if (idx >= total) return;
+    const int o = (int)(idx % a.oc);
+    long long r = idx / a.oc;
+    const int zz = (int)(r % a.rows_z);
+    r /= a.rows_z;
+    const int y = (int)(r % a.N2);
+    const int x = (int)(r / a.N2);
+    int z = zz - a.zshift;
+    z = z < 0 ? z + a.N3 : (z >= a.N3 ? z - a.N3 : z);
+    const double v = a.F[(((long long)x * a.N2 + y) * a.N3 + z) * a.oc + o].x;
+    T* t = static_cast<T*>(a.tab);
+    t[((((long long)x * a.N2 + y) * a.rows_z + zz) * a.entries + a.entry) * a.o_p + a.o0 + o] =
+        from_double<T>(v);
+}
+
+int launch_layout(const Handle* h, const double2* F, int tab, int entry, int o0, int oc,
+                  cudaStream_t st)
+{
+    LayoutArgs a;
+    a.F = F;
+    a.tab = const_cast<Handle*>(h)->table(tab);
+    a.N1 = h->dims[0];
+    a.N2 = h->dims[1];
+    a.N3 = h->dims[2];
+    a.oc = oc;
+    a.o0 = o0;
+    a.o_p = h->n_orb_p;
+    a.rows_z = h->rows_z;
+    a.entries = h->entries;
+    a.entry = entry;
+    a.zshift = (h->method == QMCSPL_PPSPLINE) ? 0 : 1;
+    const long long total = (long long)a.N1 * a.N2 * a.rows_z * a.oc;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    switch (h->storage) {
+    case QMCSPL_F64: layout_kernel<double><<<blocks, 256, 0, st>>>(a); break;
+    case QMCSPL_F32: layout_kernel<float><<<blocks, 256, 0, st>>>(a); break;
+    default: layout_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(a); break;
+    }
+    return cuda_error(cudaGetLastError(), "layout_kernel launch");
+}
+
+int launch_dft(const DftArgs& a, cudaStream_t st)
+{
+    const int full = (a.kmax < 0 || 2 * a.kmax + 1 >= a.N);
+    const int nb = full ? a.N : 2 * a.kmax + 1;
+    const size_t smem = ((size_t)nb * kDftInner + a.N) * sizeof(double2);
+    const long long tiles_inner = (a.inner + kDftInner - 1) / kDftInner;
+    const long long blocks = a.outer * tiles_inner;
+    if (blocks <= 0) return QMCSPL_OK;
+    if (blocks > 0x7fffffffLL) return set_error(QMCSPL_ERR_UNSUPPORTED, "DFT grid too large");
+    cudaError_t e = cudaFuncSetAttribute(dft_pass_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(dft_pass_kernel)");
+    dft_pass_kernel<<<(unsigned)blocks, kDftInner * kDftRows, smem, st>>>(a);
+    return cuda_error(cudaGetLastError(), "dft_pass_kernel launch");
+}
+
+struct TableJob {
+    int tab, entry, kind, pp_axes;
+};
+
+}  // namespace
+
+int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef_host,
+                 cudaStream_t st)
+{
+    const int N1 = h->dims[0], N2 = h->dims[1], N3 = h->dims[2];
+    int kmax[3] = {0, 0, 0};
+    for (int g = 0; g < n_pw; ++g)
+        for (int a = 0; a < 3; ++a) {
+            int v = miller_host[3 * g + a];
+            v = v < 0 ? -v : v;
+            if (v > kmax[a]) kmax[a] = v;
+        }
+    for (int a = 0; a < 3; ++a)
+        if (2 * kmax[a] + 1 >= h->dims[a]) kmax[a] = -1;   // band covers the whole axis
+
+    std::vector<TableJob> jobs;
+    switch (h->method) {
+    case QMCSPL_BSPLINE_SMOOTH:
+        jobs.push_back({0, 0, kBuildSmoothValue, 0});
+        if (h->separate_lap) jobs.push_back({1, 0, kBuildSmoothLap, 0});
+        break;
+    case QMCSPL_BSPLINE_INTERP:
+        jobs.push_back({0, 0, kBuildInterpValue, 0});
+        if (h->separate_lap) jobs.push_back({1, 0, kBuildInterpLap, 0});
+        break;
+    case QMCSPL_LAGRANGE:
+        jobs.push_back({0, 0, kBuildGridValue, 0});
+        jobs.push_back({1, 0, kBuildGridDx, 0});
+        jobs.push_back({2, 0, kBuildGridDy, 0});
+        jobs.push_back({3, 0, kBuildGridDz, 0});
+        jobs.push_back({4, 0, kBuildGridLap, 0});
+        break;
+    default:   // pp: entry e = 4(kappa-1) + 2(mu-1) + (nu-1); label 2 <=> bit set
+        for (int e = 0; e < 8; ++e) jobs.push_back({0, e, kBuildPP, e});
+        break;
+    }
+
+    const size_t per_orb = (size_t)N1 * N2 * N3 * sizeof(double2);
+    int oc_max = (int)(kGridBudget / per_orb);
+    if (oc_max < 1) oc_max = 1;
+    if (oc_max > h->n_orb) oc_max = h->n_orb;
+
+    int* d_miller = nullptr;
+    double2* d_coef = nullptr;
+    double2* F[2] = {nullptr, nullptr};
+    int rc = QMCSPL_OK;
+    cudaError_t e;
+    do {
+        e = cudaMallocAsync((void**)&d_miller, sizeof(int) * 3 * (size_t)n_pw, st);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(miller)"); break; }
+        e = cudaMallocAsync((void**)&d_coef, sizeof(double2) * (size_t)n_pw * h->n_orb, st);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(coef)"); break; }
+        e = cudaMallocAsync((void**)&F[0], per_orb * oc_max, st);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(grid)"); break; }
+        e = cudaMallocAsync((void**)&F[1], per_orb * oc_max, st);
+        if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(grid)"); break; }
+        e = cudaMemcpyAsync(d_miller, miller_host, sizeof(int) * 3 * (size_t)n_pw,
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { rc = cuda_error(e, "upload miller"); break; }
+        e = cudaMemcpyAsync(d_coef, coef_host, sizeof(double2) * (size_t)n_pw * h->n_orb,
+                            cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) { rc = cuda_error(e, "upload coefficients"); break; }
+
+        double bmat[9];
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < 3; ++i) bmat[3 * a + i] = 2.0 * M_PI * h->ainv[3 * i + a];
+
+        for (int o0 = 0; o0 < h->n_orb && rc == QMCSPL_OK; o0 += oc_max) {
+            const int oc = (h->n_orb - o0 < oc_max) ? h->n_orb - o0 : oc_max;
+            for (const TableJob& job : jobs) {
+                e = cudaMemsetAsync(F[0], 0, per_orb * oc, st);
+                if (e != cudaSuccess) { rc = cuda_error(e, "cudaMemsetAsync(grid)"); break; }
+                ScatterArgs s;
+                s.miller = d_miller;
+                s.coef = d_coef;
+                s.n_pw = n_pw;
+                s.o0 = o0;
+                s.oc = oc;
+                for (int a = 0; a < 3; ++a) s.dims[a] = h->dims[a];
+                std::memcpy(s.bmat, bmat, sizeof(bmat));
+                s.kind = job.kind;
+                s.pp_axes = job.pp_axes;
+                s.F = F[0];
+                const long long tot = (long long)oc * n_pw;
+                scatter_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(s);
+                if ((rc = cuda_error(cudaGetLastError(), "scatter_kernel launch")) != QMCSPL_OK) break;
+
+                DftArgs d;
+                // z: [N1*N2][N3][oc], lines outside the (k1, k2) band are zero
+                d.in = F[0]; d.out = F[1];
+                d.outer = (long long)N1 * N2; d.N = N3; d.inner = oc; d.kmax = kmax[2];
+                d.skip_mode = 2; d.D1 = N1; d.kmax1 = kmax[0]; d.D2 = N2; d.kmax2 = kmax[1];
+                if ((rc = launch_dft(d, st)) != QMCSPL_OK) break;
+                // y: [N1][N2][N3*oc], lines outside the k1 band are zero
+                d.in = F[1]; d.out = F[0];
+                d.outer = N1; d.N = N2; d.inner = (long long)N3 * oc; d.kmax = kmax[1];
+                d.skip_mode = 1; d.D1 = N1; d.kmax1 = kmax[0]; d.D2 = 1; d.kmax2 = -1;
+                if ((rc = launch_dft(d, st)) != QMCSPL_OK) break;
+                // x: [1][N1][N2*N3*oc]
+                d.in = F[0]; d.out = F[1];
+                d.outer = 1; d.N = N1; d.inner = (long long)N2 * N3 * oc; d.kmax = kmax[0];
+                d.skip_mode = 0;
+                if ((rc = launch_dft(d, st)) != QMCSPL_OK) break;
+                if ((rc = launch_layout(h, F[1], job.tab, job.entry, o0, oc, st)) != QMCSPL_OK) break;
+            }
+        }
+    } while (0);
+    if (F[0]) cudaFreeAsync(F[0], st);
+    if (F[1]) cudaFreeAsync(F[1], st);
+    if (d_coef) cudaFreeAsync(d_coef, st);
+    if (d_miller) cudaFreeAsync(d_miller, st);
+    e = cudaStreamSynchronize(st);
+    if (rc == QMCSPL_OK && e != cudaSuccess) rc = cuda_error(e, "table construction");
+    return rc;
+}
+
+}  // namespace qmcspl

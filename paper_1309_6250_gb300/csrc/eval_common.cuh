@@ -1,0 +1,149 @@
+// eval_common.cuh -- device helpers shared by the evaluation kernels of this library.
+#pragma once
+
+#include "qmcspl_internal.cuh"
+
+namespace qmcspl {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+
+// Storage type traits: accumulation type A and elements per 16-byte chunk E.
+template <typename T> struct Traits;
+template <> struct Traits<double> { using A = double; static constexpr int E = 2; };
+template <> struct Traits<float> { using A = float; static constexpr int E = 4; };
+template <> struct Traits<__nv_bfloat16> { using A = float; static constexpr int E = 8; };
+
+// 16-byte read-only load of table data.
+__device__ __forceinline__ uint4 ldg16(const void* p)
+{
+    return __ldg(reinterpret_cast<const uint4*>(p));
+}
+
+template <typename T>
+__device__ __forceinline__ void unpack(const uint4& r, typename Traits<T>::A* v);
+
+template <> __device__ __forceinline__ void unpack<double>(const uint4& r, double* v)
+{
+    v[0] = __hiloint2double((int)r.y, (int)r.x);
+    v[1] = __hiloint2double((int)r.w, (int)r.z);
+}
+template <> __device__ __forceinline__ void unpack<float>(const uint4& r, float* v)
+{
+    v[0] = __uint_as_float(r.x);
+    v[1] = __uint_as_float(r.y);
+    v[2] = __uint_as_float(r.z);
+    v[3] = __uint_as_float(r.w);
+}
+// bfloat16 is the top half of a float: widen by shifting into the high 16 bits.
+template <> __device__ __forceinline__ void unpack<__nv_bfloat16>(const uint4& r, float* v)
+{
+    const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        v[2 * j] = __uint_as_float(w[j] << 16);
+        v[2 * j + 1] = __uint_as_float(w[j] & 0xffff0000u);
+    }
+}
+
+// Eq. (reducedcoordinate) for one axis: s -> (grid index below the point, t in [0,1)).
+// `ok` is false for a non-finite coordinate (then i = 0 and t = NaN).
+__device__ __forceinline__ void reduce_axis(double s, int N, int& i, double& t, bool& ok)
+{
+    const double f = s - floor(s);
+    ok = isfinite(f);
+    const double u = (double)N * f;
+    const double fl = floor(u);
+    t = u - fl;
+    int k = ok ? (int)fl : 0;
+    if (k >= N) k -= N;        // f rounded up to 1.0
+    i = k;
+    if (!ok) t = __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// Reduced coordinates of position r for every lane of a group of L lanes.  With
+// L >= 4 lane j < 3 of the group reduces axis j and the results are broadcast by
+// shuffles; smaller groups reduce all three axes in every lane.  Must be called by
+// all 32 lanes of the warp.
+__device__ __forceinline__ void reduced_coordinates(const EvalArgs& p, const double* r, int L,
+                                                    int sub, int gbase, int& ix, int& iy,
+                                                    int& iz, double& tx, double& ty,
+                                                    double& tz, bool& ok)
+{
+    if (L >= 4) {
+        const int ax = sub < 3 ? sub : 2;
+        const double a0 = ax == 0 ? p.ainv[0] : (ax == 1 ? p.ainv[3] : p.ainv[6]);
+        const double a1 = ax == 0 ? p.ainv[1] : (ax == 1 ? p.ainv[4] : p.ainv[7]);
+        const double a2 = ax == 0 ? p.ainv[2] : (ax == 1 ? p.ainv[5] : p.ainv[8]);
+        const int N = ax == 0 ? p.nx : (ax == 1 ? p.ny : p.nz);
+        int i;
+        double t;
+        bool o;
+        reduce_axis(a0 * r[0] + a1 * r[1] + a2 * r[2], N, i, t, o);
+        ix = __shfl_sync(kFullMask, i, gbase);
+        iy = __shfl_sync(kFullMask, i, gbase + 1);
+        iz = __shfl_sync(kFullMask, i, gbase + 2);
+        tx = __shfl_sync(kFullMask, t, gbase);
+        ty = __shfl_sync(kFullMask, t, gbase + 1);
+        tz = __shfl_sync(kFullMask, t, gbase + 2);
+        const int okb = o ? 1 : 0;
+        ok = (__shfl_sync(kFullMask, okb, gbase) & __shfl_sync(kFullMask, okb, gbase + 1) &
+              __shfl_sync(kFullMask, okb, gbase + 2)) != 0;
+    } else {
+        bool o0, o1, o2;
+        reduce_axis(p.ainv[0] * r[0] + p.ainv[1] * r[1] + p.ainv[2] * r[2], p.nx, ix, tx, o0);
+        reduce_axis(p.ainv[3] * r[0] + p.ainv[4] * r[1] + p.ainv[5] * r[2], p.ny, iy, ty, o1);
+        reduce_axis(p.ainv[6] * r[0] + p.ainv[7] * r[1] + p.ainv[8] * r[2], p.nz, iz, tz, o2);
+        ok = o0 && o1 && o2;
+    }
+}
+
+__device__ __forceinline__ int wrap1(int x, int n)
+{
+    return x < 0 ? x + n : (x >= n ? x - n : x);
+}
+
+// Cubic B-spline weights of the Appendix, Eq. (b-splinebasis), for stencil offsets
+// -1..2 (index 0..3), and their first and second t-derivatives.
+template <typename A>
+__device__ __forceinline__ void bspline_weights(A t, A* w, A* dw, A* d2w)
+{
+    const A s = A(1) - t;
+    const A t2 = t * t;
+    w[0] = A(0.25) * s * s * s;
+    w[1] = (A(0.75) * t - A(1.5)) * t2 + A(1);
+    w[2] = ((A(-0.75) * t + A(0.75)) * t + A(0.75)) * t + A(0.25);
+    w[3] = A(0.25) * t2 * t;
+    dw[0] = A(-0.75) * s * s;
+    dw[1] = (A(2.25) * t - A(3)) * t;
+    dw[2] = (A(-2.25) * t + A(1.5)) * t + A(0.75);
+    dw[3] = A(0.75) * t2;
+    if (d2w) {
+        d2w[0] = A(1.5) * s;
+        d2w[1] = A(4.5) * t - A(3);
+        d2w[2] = A(-4.5) * t + A(1.5);
+        d2w[3] = A(1.5) * t;
+    }
+}
+
+// Streaming stores of E consecutive outputs (vector when allowed).
+template <typename A, int E>
+__device__ __forceinline__ void store_run(A* dst, const A* v, int o0, int n_orb, bool vec)
+{
+    if (vec && o0 + E <= n_orb) {
+        if constexpr (sizeof(A) == 8) {
+#pragma unroll
+            for (int j = 0; j < E; j += 2)
+                __stcs(reinterpret_cast<double2*>(dst + j), make_double2(v[j], v[j + 1]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < E; j += 4)
+                __stcs(reinterpret_cast<float4*>(dst + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < E; ++j)
+            if (o0 + j < n_orb) __stcs(dst + j, v[j]);
+    }
+}
+
+}  // namespace qmcspl

@@ -1,0 +1,137 @@
+// qmcspl_internal.cuh -- private declarations of the qmcspl CUDA library.
+//
+// Stored table layout (all methods), orbital-innermost so that one position's stencil
+// is a handful of long contiguous runs:
+//
+//   B-spline, Lagrange:  T[x][y][zz][O_p],     zz = z + 1, z in [-1, Nz + 1]
+//   pp-spline:           T[x][y][zz][8][O_p],  zz = z,     z in [0, Nz]
+//
+// The z ghost planes repeat planes Nz-1, 0 and 1 (pp: plane 0), so the four (two)
+// z rows of a stencil column are contiguous and only x and y need a periodic wrap.
+// O_p pads the orbital count so that each row is a whole number of 16-byte chunks
+// split evenly over the lanes that share a position.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/qmcspl.h"
+
+struct qmcspl_s;
+
+namespace qmcspl {
+
+using Handle = ::qmcspl_s;
+
+constexpr int kMaxDim = 512;          // grid points per axis accepted by qmcspl_create
+constexpr int kEvalThreads = 256;     // eval kernels: 8 warps per block
+
+enum BuildKind : int {
+    kBuildSmoothValue = 0,   // c_G / gamma_G
+    kBuildSmoothLap = 1,     // -|G|^2 c_G / gamma_G
+    kBuildInterpValue = 2,   // c_G / prod(1 + cos(th)/2)
+    kBuildInterpLap = 3,     // -|G|^2 c_G / prod(1 + cos(th)/2)
+    kBuildGridValue = 4,     // c_G                (Lagrange phi)
+    kBuildGridDx = 5,        // i G_x c_G          (Lagrange d_x phi)
+    kBuildGridDy = 6,
+    kBuildGridDz = 7,
+    kBuildGridLap = 8,       // -|G|^2 c_G         (Lagrange lap phi)
+    kBuildPP = 9,            // c_G prod_{axes with label 2} 6(cos th - 1)/(2 + cos th)
+};
+
+// Eval parameters shared by the B-spline, Lagrange and pp kernels (passed by value).
+struct EvalArgs {
+    const void* tab[5];       // tables (B-spline: value, Laplacian; Lagrange: 5; pp: 1)
+    long long col_stride;     // elements between successive (x, y) columns
+    int row_stride;           // elements between successive z rows (O_p, or 8 O_p for pp)
+    int nx, ny, nz;
+    int n_orb;
+    int lanes_log2;           // lanes sharing one position
+    int tiles;                // orbital tiles per position
+    double ainv[9];           // s = a^-1 r (row-major)
+    double mg[9];             // grad_cart[a] = sum_i mg[3a+i] grad_t[i]
+    double ml[6];             // lap = ml0 Hxx + ml1 Hyy + ml2 Hzz + ml3 Hxy + ml4 Hxz + ml5 Hyz
+    const double* pos;
+    long long n_pos;
+    void* val;
+    void* grad;
+    void* lap;
+    int vec_out;              // outputs may use 16-byte vector stores
+    int* err;                 // device error word (bit 0: non-finite position)
+};
+
+}  // namespace qmcspl
+
+// The handle behind the opaque qmcspl_t of the C ABI.
+struct qmcspl_s {
+    int device = 0;
+    int method = 0, storage = 0, separate_lap = 0;
+    int dims[3] = {0, 0, 0};
+    int n_orb = 0, n_orb_p = 0;
+    int n_tables = 0;
+    int entries = 1;          // 8 for pp
+    int rows_z = 0;
+    int lanes_log2 = 0, tiles = 1;
+    long long n_pw = 0;
+    double lattice[9];
+    double ainv[9];
+    double mg[9];
+    double ml[6];
+    size_t elem_bytes = 4;
+    size_t table_elems = 0;   // elements per table
+    void* tables = nullptr;   // one allocation, n_tables * table_elems elements
+    int* d_err = nullptr;
+    // staging for qmcspl_eval_vgl_host
+    double* st_pos[2] = {nullptr, nullptr};
+    void* st_out[2] = {nullptr, nullptr};
+    long long st_cap = 0;     // positions per staging chunk
+    cudaStream_t st_stream[2] = {nullptr, nullptr};
+    cudaEvent_t st_ev[6] = {};
+    bool st_ready = false;
+    // batched-call descriptor buffer (device)
+    void* batch_desc = nullptr;
+
+    const void* table(int t) const
+    {
+        return static_cast<const char*>(tables) + (size_t)t * table_elems * elem_bytes;
+    }
+    void* table(int t)
+    {
+        return static_cast<char*>(tables) + (size_t)t * table_elems * elem_bytes;
+    }
+};
+
+namespace qmcspl {
+
+// ---- error reporting (thread-local message) ----
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+
+// ---- construction (construct.cu) ----
+int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef_host,
+                 cudaStream_t stream);
+
+// ---- evaluation launchers ----
+int launch_bspline_vgl(const Handle* h, const double* pos, long long n_pos, void* val,
+                       void* grad, void* lap, cudaStream_t stream);
+int launch_lagrange_vgl(const Handle* h, const double* pos, long long n_pos, void* val,
+                        void* grad, void* lap, cudaStream_t stream);
+int launch_pp_vgl(const Handle* h, const double* pos, long long n_pos, void* val, void* grad,
+                  void* lap, cudaStream_t stream);
+int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
+                            const void* gv, const void* gg, const void* gl, void* dcoef,
+                            void* dcoef_lap, double* dpos, cudaStream_t stream);
+int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos,
+                   const long long* n_pos, void* const* val, void* const* grad,
+                   void* const* lap, cudaStream_t stream);
+
+// fill the common part of EvalArgs from a handle
+void fill_eval_args(const Handle* h, EvalArgs* a);
+
+// number of SMs of the current device (cached)
+int sm_count();
+
+}  // namespace qmcspl

@@ -1,0 +1,80 @@
+"""The C-ABI library loads and exports every entry point of include/qmcspl.h; host-side
+validation answers without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1309_6250_gb300 import _lib, build as pkg_build, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pkg_build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "qmcspl.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qmcspl_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "qmcspl_create" in names and "qmcspl_eval_vgl_backward" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert {p[0] for p in _lib.PROTOTYPES} == set(names)
+
+
+def test_version_and_empty_error(lib):
+    assert lib.qmcspl_version() >= 10000
+    assert lib.qmcspl_last_error() == b""
+
+
+def _create(lib, lattice, dims, miller, coef, method=0, storage=0, sep=0):
+    h = ctypes.c_void_p()
+    lat = np.ascontiguousarray(lattice, dtype=np.float64)
+    dm = np.ascontiguousarray(dims, dtype=np.int32)
+    mil = np.ascontiguousarray(miller, dtype=np.int32)
+    c = np.ascontiguousarray(np.asarray(coef, dtype=np.complex128)).view(np.float64)
+    opts = _lib.Opts(method, storage, sep)
+    rc = lib.qmcspl_create(ctypes.byref(h), lat.ctypes.data, dm.ctypes.data, mil.shape[0],
+                           mil.ctypes.data, c.shape[0], c.ctypes.data, ctypes.byref(opts), None)
+    return rc, h
+
+
+def test_validation_without_gpu(lib):
+    lat, mil, coef = inputs.random_cell(1, (8, 8, 8), 2, 4.0, 4.0, np.eye(3) * 6.0)
+    # bad grid
+    rc, h = _create(lib, lat, (3, 8, 8), mil, coef)
+    assert rc == _lib.ERR_ARG and h.value is None
+    # singular lattice
+    rc, _ = _create(lib, np.zeros((3, 3)), (8, 8, 8), mil, coef)
+    assert rc == _lib.ERR_ARG and b"singular" in lib.qmcspl_last_error()
+    # unknown method / storage
+    assert _create(lib, lat, (8, 8, 8), mil, coef, method=9)[0] == _lib.ERR_ARG
+    assert _create(lib, lat, (8, 8, 8), mil, coef, storage=7)[0] == _lib.ERR_ARG
+    # non-Hermitian: break c_{-G} = conj(c_G)
+    bad = coef.copy()
+    k = int(np.nonzero(np.any(mil != 0, axis=1))[0][0])
+    bad[0, k] += 0.1
+    rc, _ = _create(lib, lat, (8, 8, 8), mil, bad)
+    assert rc == _lib.ERR_NOT_HERMITIAN
+    # a planewave without its -G partner
+    k = int(np.nonzero(np.any(mil != 0, axis=1))[0][0])
+    keep = np.arange(mil.shape[0]) != k
+    rc, _ = _create(lib, lat, (8, 8, 8), mil[keep], coef[:, keep])
+    assert rc == _lib.ERR_NOT_HERMITIAN and b"partner" in lib.qmcspl_last_error()
+    # duplicated G
+    rc, _ = _create(lib, lat, (8, 8, 8), np.vstack([mil, mil[:1]]), np.hstack([coef, coef[:, :1]]))
+    assert rc == _lib.ERR_ARG and b"duplicate" in lib.qmcspl_last_error()
+    # NULL handle calls
+    assert lib.qmcspl_eval_vgl(None, None, 0, None, None, None, None) == _lib.ERR_ARG
+    assert lib.qmcspl_sync(None, None) == _lib.ERR_ARG
+    assert lib.qmcspl_destroy(None) == _lib.OK
