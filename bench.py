@@ -100,7 +100,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
@@ -230,17 +230,20 @@ def run_ours(args):
     n_pos, n_orb = w.pos.shape[0], w.coef.shape[0]
     stream = torch.cuda.current_stream()
 
-    def build(storage):
+    def build(storage, order):
         t0 = time.perf_counter()
         s = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth",
                            storage=storage, separate_lap=True, device=dev)
+        s.set_order(order)
         return s, time.perf_counter() - t0
 
-    spl, setup_s = build(args.storage)
+    spl, setup_s = build(args.storage, args.order)
     info = spl.info()
     pos_d = torch.from_numpy(w.pos).to(dev)
     outs = spl.alloc_outputs(n_pos)
     step = lambda: spl.eval_vgl(pos_d, out=outs)
+    cell_order = args.order == "cell" or (args.order == "auto" and n_pos >= 8192)
+    kernels_per_step = 4 if cell_order else 1     # bin, scan, place + evaluation
 
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     for _ in range(args.warmup):
@@ -249,9 +252,12 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    spl.profile(True)
     sampler.start()
     ms = time_steps(step, args.steps, 0, torch, stream)
     clocks = sampler.stop()
+    prof = spl.profile_read()
+    spl.profile(False)
     spl.sync()
     total_ms = sum(ms)
     if dist:
@@ -270,8 +276,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    e2e_steps = max(3, args.steps // 4)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -279,33 +286,44 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e_value = evals_per_step * ws * args.steps / e2e_s
+    e2e_value = evals_per_step * ws * e2e_steps / e2e_s
     d2h = sum(o.numel() * o.element_size() for o in host_out)
 
-    # roofline of the (only) kernel of a step
+    # roofline of the dominant kernel, from its own CUDA-event launch times
     hbm, peak_kind = load_peaks()
     bpe = algorithmic_bytes_per_eval(args.storage, info["n_tables"], n_orb)
-    launch_s = total_ms * 1e-3 / args.steps
+    launch_s = prof["eval_ms"] * 1e-3 / max(1, prof["launches"])
     achieved = bpe * evals_per_step / launch_s / 1e9
-    key = "bspline_vgl/%s/%s" % (w.cell.name, args.storage)
+    key = "bspline_vgl/%s/%s/%s" % (w.cell.name, args.storage, "cell" if cell_order else "input")
     traffic = load_traffic(key)
 
     variants = {}
     if not args.no_variants and rank == 0:
-        for st in [s for s in ("f32", "bf16", "f64") if s != args.storage]:
+        for st, order in (("f32", "input"), ("bf16", "auto"), ("f64", "auto"), ("bf16", "input")):
+            if st == args.storage and order == args.order:
+                continue
             del outs
             spl.close()
             torch.cuda.empty_cache()
-            spl, _ = build(st)
+            spl, _ = build(st, order)
             outs = spl.alloc_outputs(n_pos)
             vstep = lambda: spl.eval_vgl(pos_d, out=outs)
-            vms = time_steps(vstep, max(3, args.steps // 2), 2, torch, stream)
+            for _ in range(3):
+                vstep()
+            torch.cuda.synchronize()
+            spl.profile(True)
+            vms = time_steps(vstep, max(5, args.steps // 4), 0, torch, stream)
+            vp = spl.profile_read()
+            spl.profile(False)
             spl.sync()
             vt = sum(vms) / len(vms) * 1e-3
+            vk = vp["eval_ms"] * 1e-3 / max(1, vp["launches"])
             vb = algorithmic_bytes_per_eval(st, spl.info()["n_tables"], n_orb)
-            variants[st] = {"value": evals_per_step / vt, "ms_per_step": vt * 1e3,
-                            "algorithmic_gbs": vb * evals_per_step / vt / 1e9,
-                            "frac_of_hbm": vb * evals_per_step / vt / 1e9 / hbm}
+            variants["%s_%s" % (st, order)] = {
+                "value": evals_per_step / vt, "ms_per_step": vt * 1e3, "eval_kernel_ms": vk * 1e3,
+                "order_kernels_ms": vp["order_ms"] / max(1, vp["launches"]),
+                "algorithmic_gbs": vb * evals_per_step / vk / 1e9,
+                "frac_of_hbm": vb * evals_per_step / vk / 1e9 / hbm}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -319,16 +337,19 @@ def run_ours(args):
                    "n_orb": n_orb, "grid": list(w.cell.grid), "walkers": w.cell.n_walkers,
                    "electrons": w.cell.n_elec, "positions": n_pos, "storage": args.storage,
                    "accumulate": "f64" if args.storage == "f64" else "f32",
+                   "order": "cell" if cell_order else "input",
                    "table_bytes": info["table_bytes"], "lanes": info["lanes"], "tiles": info["tiles"],
                    "l2": "table and outputs larger than L2 (no flush needed)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": "bspline_vgl_kernel", "bytes_per_eval": bpe},
+                     "kernel": "bspline_vgl_kernel", "bytes_per_eval": bpe,
+                     "kernel_ms": launch_s * 1e3,
+                     "order_kernels_ms": prof["order_ms"] / max(1, prof["launches"])},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pos_h.numel() * 8),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * kernels_per_step,
         "clocks": clocks,
         "setup_s": setup_s,
         "variants": variants,
@@ -343,11 +364,12 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3")
     ap.add_argument("--storage", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--order", default="auto", choices=["auto", "input", "cell"])
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

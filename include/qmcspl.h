@@ -179,18 +179,21 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
 /*
  * qmcspl_eval_batched -- qmcspl_eval_vgl for several handles in ONE kernel launch.
  *
- * Walkers of cells with different orbital counts and grids (same storage type, all
- * B-spline methods) go through one launch whose work list balances the cells.
+ * Walkers of cells with different orbital counts and grids go through one launch
+ * whose work list spreads every cell's positions evenly over the whole GPU (each warp
+ * task moves the same number of bytes whatever the cell).  All handles must be
+ * B-spline handles on one device with the same storage type and the same
+ * separate_lap setting.
  *   n_cells   1..QMCSPL_MAX_BATCH
- *   h         host array of n_cells handles (same device, same storage type)
+ *   h         host array of n_cells handles
  *   pos, val, grad, lap   host arrays of n_cells DEVICE pointers (layouts as above;
  *             val/grad/lap entries may be NULL)
  *   n_pos     host array of n_cells position counts
- * Asynchronous on `stream`.  The call uploads its descriptors with a copy on `stream`
- * from a buffer owned by the first handle, so calls on that handle are ordered by
- * the stream.
+ * Asynchronous on `stream`.  The cell descriptors travel as kernel parameters, so the
+ * call allocates nothing and copies nothing (it can be captured in a CUDA graph);
+ * positions are evaluated in input order.
  */
-#define QMCSPL_MAX_BATCH 64
+#define QMCSPL_MAX_BATCH 48
 int qmcspl_eval_batched(int n_cells, const qmcspl_t* h, const double* const* pos,
                         const long long* n_pos, void* const* val, void* const* grad,
                         void* const* lap, void* stream);
@@ -204,6 +207,35 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* h, const double* const* pos
  * Blocking.
  */
 int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream);
+
+/*
+ * qmcspl_set_order -- choose the order in which qmcspl_eval_vgl visits positions.
+ *
+ * Not in the paper.  Results do not depend on it (each position is computed the same
+ * way; outputs are always written in input order).  Visiting positions grouped by
+ * grid cell lets neighbouring positions share their stencil rows in the on-chip
+ * caches instead of re-reading them from HBM.  Cell order sorts the positions into
+ * spatial bins first (a counting sort on the device, in scratch memory the handle
+ * allocates on first use and grows when a call has more positions).
+ *   mode  QMCSPL_ORDER_AUTO (default: cell order for 8192 positions or more),
+ *         QMCSPL_ORDER_INPUT or QMCSPL_ORDER_CELL
+ */
+enum qmcspl_order { QMCSPL_ORDER_AUTO = 0, QMCSPL_ORDER_INPUT = 1, QMCSPL_ORDER_CELL = 2 };
+int qmcspl_set_order(qmcspl_t h, int mode);
+
+/*
+ * qmcspl_profile / qmcspl_profile_read -- CUDA-event timing of the library's own kernels.
+ *
+ * Not in the paper.  While enabled, every qmcspl_eval_vgl on the handle records CUDA
+ * events on its stream around the cell-ordering kernels and around the evaluation
+ * kernel (up to 4096 calls).  qmcspl_profile(h, 1) enables and clears the record,
+ * qmcspl_profile(h, 0) disables it.  qmcspl_profile_read synchronises on the recorded
+ * events and returns the summed device time in milliseconds of the evaluation
+ * kernel launches (eval_ms), of the ordering kernels (order_ms) and the number of
+ * evaluation launches recorded.  Any output pointer may be NULL.
+ */
+int qmcspl_profile(qmcspl_t h, int enable);
+int qmcspl_profile_read(qmcspl_t h, double* eval_ms, double* order_ms, long long* launches);
 
 /* qmcspl_sync -- synchronise `stream` and report (then clear) any device-side error the
  * handle's kernels recorded: QMCSPL_ERR_DEVICE for non-finite positions. */

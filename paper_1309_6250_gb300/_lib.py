@@ -30,7 +30,11 @@ F64 = 0
 F32 = 1
 BF16 = 2
 
-MAX_BATCH = 64
+MAX_BATCH = 48
+
+ORDER_AUTO = 0
+ORDER_INPUT = 1
+ORDER_CELL = 2
 
 METHODS = {"smooth": BSPLINE_SMOOTH, "interp": BSPLINE_INTERP, "lagrange": LAGRANGE, "pp": PPSPLINE}
 STORAGE = {"f64": F64, "f32": F32, "bf16": BF16}
@@ -71,6 +75,10 @@ PROTOTYPES = [
     ("qmcspl_eval_vgl_backward", I, [VP, VP, LL, VP, VP, VP, VP, VP, VP, VP]),
     ("qmcspl_eval_batched", I, [I, VP, VP, VP, VP, VP, VP, VP]),
     ("qmcspl_get_table", I, [VP, I, VP, VP]),
+    ("qmcspl_set_order", I, [VP, I]),
+    ("qmcspl_profile", I, [VP, I]),
+    ("qmcspl_profile_read", I, [VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_longlong)]),
     ("qmcspl_sync", I, [VP, VP]),
     ("qmcspl_last_error", ctypes.c_char_p, []),
     ("qmcspl_version", I, []),

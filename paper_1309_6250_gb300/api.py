@@ -89,6 +89,27 @@ class OrbitalSplines:
                                                  _stream_handle(stream)))
         return out
 
+    def set_order(self, mode: str) -> None:
+        """Order in which eval_vgl visits positions: 'auto', 'input' or 'cell'."""
+        code = {"auto": _lib.ORDER_AUTO, "input": _lib.ORDER_INPUT, "cell": _lib.ORDER_CELL}[mode]
+        _lib.check(self.lib.qmcspl_set_order(self.handle, code))
+
+    def profile(self, enable: bool = True) -> None:
+        """Start (and clear) or stop CUDA-event timing of this handle's kernels."""
+        _lib.check(self.lib.qmcspl_profile(self.handle, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        """{'eval_ms', 'order_ms', 'launches'} summed over the recorded calls."""
+        e, o, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.qmcspl_profile_read(self.handle, ctypes.byref(e), ctypes.byref(o),
+                                                    ctypes.byref(n)))
+        return {"eval_ms": e.value, "order_ms": o.value, "launches": n.value}
+
+    def coefficient_parameters(self):
+        from .autograd import coefficient_parameters
+        return coefficient_parameters(self)
+
     def sync(self, stream=None) -> None:
         with torch.cuda.device(self.device):
             _lib.check(self.lib.qmcspl_sync(self.handle, _stream_handle(stream)))

@@ -1,0 +1,71 @@
+"""torch.autograd binding of the spline evaluation and its hand-written adjoint.
+
+    beta, beta_lap = spl.coefficient_parameters()      # leaf tensors, requires_grad
+    val, grad, lap = evaluate(spl, pos, beta, beta_lap)
+    loss = f(val, grad, lap); loss.backward()
+    # pos.grad: dL/dr [P, 3] (forces);  beta.grad, beta_lap.grad: dL/dbeta (canonical
+    # layout [Nx, Ny, Nz, O]), both from qmcspl_eval_vgl_backward.
+
+The forward pass reads the coefficient tables held by the handle; `beta` / `beta_lap`
+stand for those tables in the autograd graph (they must hold the same values, which
+is what coefficient_parameters() returns).  Stencil weights are recomputed in the
+backward kernel rather than saved.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import torch
+
+from .api import OrbitalSplines
+
+
+class SplineOrbitalFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pos, beta, beta_lap, spl: OrbitalSplines):
+        val, grad, lap = spl.eval_vgl(pos)
+        ctx.spl = spl
+        ctx.save_for_backward(pos)
+        return val, grad, lap
+
+    @staticmethod
+    def backward(ctx, gv, gg, gl):
+        spl: OrbitalSplines = ctx.spl
+        (pos,) = ctx.saved_tensors
+        need_pos = ctx.needs_input_grad[0]
+        need_coef = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
+        sep = bool(spl.info()["separate_lap"])
+        dcoef = dcoef_lap = None
+        if need_coef:
+            dcoef = torch.zeros(spl.coef_shape(), dtype=spl.out_dtype, device=spl.device)
+            if sep:
+                dcoef_lap = torch.zeros_like(dcoef)
+        dpos = None
+        if need_pos or need_coef:
+            dpos = spl.backward(pos, gv, gg, gl, dcoef=dcoef, dcoef_lap=dcoef_lap, want_dpos=need_pos)
+        return (dpos if need_pos else None, dcoef if ctx.needs_input_grad[1] else None,
+                dcoef_lap if ctx.needs_input_grad[2] else None, None)
+
+
+def coefficient_parameters(spl: OrbitalSplines):
+    """Leaf tensors (requires_grad) holding the handle's coefficient tables in canonical
+    layout [Nx, Ny, Nz, O], in the output dtype: (beta, beta_lap or None)."""
+    inf = spl.info()
+    out = []
+    for idx in range(2):
+        if idx == 1 and not inf["separate_lap"]:
+            out.append(None)
+            continue
+        t = torch.from_numpy(spl.get_table(idx)).to(device=spl.device, dtype=spl.out_dtype)
+        out.append(t.requires_grad_(True))
+    return tuple(out)
+
+
+def evaluate(spl: OrbitalSplines, pos: torch.Tensor, beta: Optional[torch.Tensor] = None,
+             beta_lap: Optional[torch.Tensor] = None):
+    """(val, grad, lap) with autograd to positions and (if given) coefficients."""
+    if beta is None:
+        beta = torch.zeros((), device=spl.device)   # no coefficient gradient requested
+    if beta_lap is None:
+        beta_lap = torch.zeros((), device=spl.device)
+    return SplineOrbitalFunction.apply(pos, beta, beta_lap, spl)

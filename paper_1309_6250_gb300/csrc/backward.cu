@@ -1,0 +1,301 @@
+// backward.cu -- adjoint of the tricubic B-spline evaluation (not part of the paper:
+// gradients of a downstream scalar L for orbital optimisation and forces).
+//
+// Given upstream weights wv = dL/dval, wg = dL/dgrad (Cartesian), wl = dL/dlap for one
+// position and orbital, the chain rule of Sec. II (Coordinates) is transposed first:
+//   g~_i = sum_a N_i (a^-1)_{i a} wg_a           (reduced-coordinate gradient weight)
+// Coefficient adjoint (linear in beta, exact transpose of the evaluation): every
+// stencil point (l, m, n) receives
+//   dbeta     += wv B + g~ . grad_t B + wl lap(B)        (Hessian-derived Laplacian)
+//   dbeta_lap += wl B                                     (separate Laplacian table)
+// with B = b_l(tx) b_m(ty) b_n(tz) and lap(B) = sum_ij N_i N_j (a^-1 a^-T)_ij d2B/dt_i dt_j;
+// the adds are vector atomics into the canonical table layout [Nx][Ny][Nz][O].
+// Position adjoint: dL/dr = N (a^-1)^T u summed over orbitals, with
+//   u_i = wv dphi/dt_i + sum_j H_ij g~_j + wl d(lap)/dt_i,
+// where d(lap)/dt_i needs the third derivatives of the spline (Hessian-derived
+// Laplacian) or the gradient of the Laplacian table.  The stencil weights are
+// recomputed here, not stored by the forward pass.
+#include "eval_common.cuh"
+
+namespace qmcspl {
+namespace {
+
+struct BwdArgs {
+    EvalArgs e;               // tables, geometry, positions (outputs unused)
+    const void* gv;           // [P][O] output dtype, may be null
+    const void* gg;           // [P][3][O]
+    const void* gl;           // [P][O]
+    void* dcoef;              // [Nx][Ny][Nz][O] output dtype, accumulated
+    void* dcoef_lap;
+    double* dpos;             // [P][3], zeroed before the launch, accumulated
+    int vec_atomic;           // dcoef rows allow 16-byte vector atomics
+};
+
+template <typename A>
+__device__ __forceinline__ void load_run(const A* src, A* v, int o0, int n_orb, int E)
+{
+    for (int j = 0; j < E; ++j) v[j] = (src && o0 + j < n_orb) ? src[j] : A(0);
+}
+
+template <typename A, int E>
+__device__ __forceinline__ void atomic_run(A* dst, const A* v, int o0, int n_orb, bool vec)
+{
+    if constexpr (sizeof(A) == 4) {
+        if (vec && o0 + E <= n_orb) {
+#pragma unroll
+            for (int j = 0; j < E; j += 4)
+                atomicAdd(reinterpret_cast<float4*>(dst + j), make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]));
+            return;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j)
+        if (o0 + j < n_orb) atomicAdd(dst + j, v[j]);
+}
+
+template <typename T, bool LAPTAB>
+__global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs b)
+{
+    using A = typename Traits<T>::A;
+    constexpr int E = Traits<T>::E;
+    const EvalArgs& p = b.e;
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << p.lanes_log2;
+    const int sub = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const int gpw = 32 >> p.lanes_log2;
+    const long long total = p.n_pos * p.tiles;
+    const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
+    const size_t rowb = (size_t)p.row_stride * sizeof(T);
+    const size_t colb = (size_t)p.col_stride * sizeof(T);
+    const int n_orb = p.n_orb;
+
+    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
+        const long long gid = w0 + (lane >> p.lanes_log2);
+        const bool active = gid < total;
+        const long long ip = active ? gid / p.tiles : 0;
+        const int tile = active ? (int)(gid - ip * p.tiles) : 0;
+        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+        int ix, iy, iz;
+        double tx, ty, tz;
+        bool ok;
+        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+        if (active && !ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+
+        A w[3][4], dw[3][4], d2w[3][4];
+        bspline_weights<A>((A)tx, w[0], dw[0], d2w[0]);
+        bspline_weights<A>((A)ty, w[1], dw[1], d2w[1]);
+        bspline_weights<A>((A)tz, w[2], dw[2], d2w[2]);
+        const A d3w[4] = {A(-1.5), A(4.5), A(-4.5), A(1.5)};
+
+        const int chunk = tile * L + sub;
+        const int o0 = chunk * E;
+        // upstream weights of my orbitals (zero for inactive lanes and padding)
+        A wv[E], wl[E], gt[3][E];
+        {
+            A wg[3][E];
+            const A* gvp = static_cast<const A*>(b.gv);
+            const A* ggp = static_cast<const A*>(b.gg);
+            const A* glp = static_cast<const A*>(b.gl);
+            const bool use = active && o0 < n_orb;
+            load_run<A>(use && gvp ? gvp + ip * n_orb + o0 : nullptr, wv, o0, n_orb, E);
+            load_run<A>(use && glp ? glp + ip * n_orb + o0 : nullptr, wl, o0, n_orb, E);
+            for (int a = 0; a < 3; ++a)
+                load_run<A>(use && ggp ? ggp + (ip * 3 + a) * n_orb + o0 : nullptr, wg[a], o0, n_orb, E);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    gt[i][e] = (A)p.mg[i] * wg[0][e] + (A)p.mg[3 + i] * wg[1][e] + (A)p.mg[6 + i] * wg[2][e];
+        }
+        const A ml0 = (A)p.ml[0], ml1 = (A)p.ml[1], ml2 = (A)p.ml[2];
+        const A ml3 = (A)p.ml[3], ml4 = (A)p.ml[4], ml5 = (A)p.ml[5];
+        int xs[4], ys[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            xs[j] = wrap1(ix + j - 1, p.nx);
+            ys[j] = wrap1(iy + j - 1, p.ny);
+        }
+
+        // ---- coefficient adjoint: scatter into 64 stencil rows ----
+        if (b.dcoef && active && o0 < n_orb) {
+            A* dc = static_cast<A*>(b.dcoef);
+            A* dl = static_cast<A*>(b.dcoef_lap);
+            const bool vec = b.vec_atomic != 0;
+            for (int l = 0; l < 4; ++l)
+                for (int m = 0; m < 4; ++m)
+                    for (int n = 0; n < 4; ++n) {
+                        const int z = wrap1(iz + n - 1, p.nz);
+                        const A B = w[0][l] * w[1][m] * w[2][n];
+                        const A Bx = dw[0][l] * w[1][m] * w[2][n];
+                        const A By = w[0][l] * dw[1][m] * w[2][n];
+                        const A Bz = w[0][l] * w[1][m] * dw[2][n];
+                        A lapB = 0;
+                        if (!LAPTAB)
+                            lapB = ml0 * d2w[0][l] * w[1][m] * w[2][n] + ml1 * w[0][l] * d2w[1][m] * w[2][n] +
+                                   ml2 * w[0][l] * w[1][m] * d2w[2][n] + ml3 * dw[0][l] * dw[1][m] * w[2][n] +
+                                   ml4 * dw[0][l] * w[1][m] * dw[2][n] + ml5 * w[0][l] * dw[1][m] * dw[2][n];
+                        A v[E], vl[E];
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            v[e] = wv[e] * B + gt[0][e] * Bx + gt[1][e] * By + gt[2][e] * Bz;
+                            if (LAPTAB) vl[e] = wl[e] * B;
+                            else v[e] += wl[e] * lapB;
+                        }
+                        const size_t row = (((size_t)xs[l] * p.ny + ys[m]) * p.nz + z) * n_orb + o0;
+                        atomic_run<A, E>(dc + row, v, o0, n_orb, vec);
+                        if (LAPTAB) atomic_run<A, E>(dl + row, vl, o0, n_orb, vec);
+                    }
+        }
+
+        // ---- position adjoint ----
+        if (b.dpos) {
+            // reduced derivatives of my orbitals: gradient, Hessian, gradient of the Laplacian
+            A g1[3][E], h2[6][E], d3[3][E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                for (int i = 0; i < 3; ++i) g1[i][e] = d3[i][e] = A(0);
+                for (int i = 0; i < 6; ++i) h2[i][e] = A(0);
+            }
+            const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
+            const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb
+                                    : nullptr;
+            for (int l = 0; l < 4; ++l)
+                for (int m = 0; m < 4; ++m) {
+                    const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb;
+                    A a[4][E], al[2][E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) a[0][e] = a[1][e] = a[2][e] = a[3][e] = al[0][e] = al[1][e] = A(0);
+#pragma unroll
+                    for (int n = 0; n < 4; ++n) {
+                        A c[E];
+                        unpack<T>(ldg16(t0 + col + n * rowb), c);
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            a[0][e] = fma(w[2][n], c[e], a[0][e]);
+                            a[1][e] = fma(dw[2][n], c[e], a[1][e]);
+                            a[2][e] = fma(d2w[2][n], c[e], a[2][e]);
+                            a[3][e] = fma(d3w[n], c[e], a[3][e]);
+                        }
+                        if (LAPTAB) {
+                            unpack<T>(ldg16(t1 + col + n * rowb), c);
+#pragma unroll
+                            for (int e = 0; e < E; ++e) {
+                                al[0][e] = fma(w[2][n], c[e], al[0][e]);
+                                al[1][e] = fma(dw[2][n], c[e], al[1][e]);
+                            }
+                        }
+                    }
+                    const A bx = w[0][l], dbx = dw[0][l], d2bx = d2w[0][l], d3bx = d3w[l];
+                    const A by = w[1][m], dby = dw[1][m], d2by = d2w[1][m], d3by = d3w[m];
+                    // third-derivative weights contracted with the Laplacian metric
+                    const A x0 = ml0 * d3bx * by + ml1 * dbx * d2by + ml3 * d2bx * dby;
+                    const A x1 = ml4 * d2bx * by + ml5 * dbx * dby;
+                    const A x2 = ml2 * dbx * by;
+                    const A y0 = ml0 * d2bx * dby + ml1 * bx * d3by + ml3 * dbx * d2by;
+                    const A y1 = ml4 * dbx * dby + ml5 * bx * d2by;
+                    const A y2 = ml2 * bx * dby;
+                    const A z1 = ml0 * d2bx * by + ml1 * bx * d2by + ml3 * dbx * dby;
+                    const A z2 = ml4 * dbx * by + ml5 * bx * dby;
+                    const A z3 = ml2 * bx * by;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        g1[0][e] += dbx * by * a[0][e];
+                        g1[1][e] += bx * dby * a[0][e];
+                        g1[2][e] += bx * by * a[1][e];
+                        h2[0][e] += d2bx * by * a[0][e];
+                        h2[1][e] += bx * d2by * a[0][e];
+                        h2[2][e] += bx * by * a[2][e];
+                        h2[3][e] += dbx * dby * a[0][e];
+                        h2[4][e] += dbx * by * a[1][e];
+                        h2[5][e] += bx * dby * a[1][e];
+                        if (LAPTAB) {
+                            d3[0][e] += dbx * by * al[0][e];
+                            d3[1][e] += bx * dby * al[0][e];
+                            d3[2][e] += bx * by * al[1][e];
+                        } else {
+                            d3[0][e] += x0 * a[0][e] + x1 * a[1][e] + x2 * a[2][e];
+                            d3[1][e] += y0 * a[0][e] + y1 * a[1][e] + y2 * a[2][e];
+                            d3[2][e] += z1 * a[1][e] + z2 * a[2][e] + z3 * a[3][e];
+                        }
+                    }
+                }
+            // u_i = wv g_i + sum_j H_ij g~_j + wl d3_i, summed over my orbitals (in FP64)
+            double u[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const A hxx = h2[0][e], hyy = h2[1][e], hzz = h2[2][e];
+                const A hxy = h2[3][e], hxz = h2[4][e], hyz = h2[5][e];
+                u[0] += (double)(wv[e] * g1[0][e] + hxx * gt[0][e] + hxy * gt[1][e] + hxz * gt[2][e] + wl[e] * d3[0][e]);
+                u[1] += (double)(wv[e] * g1[1][e] + hxy * gt[0][e] + hyy * gt[1][e] + hyz * gt[2][e] + wl[e] * d3[1][e]);
+                u[2] += (double)(wv[e] * g1[2][e] + hxz * gt[0][e] + hyz * gt[1][e] + hzz * gt[2][e] + wl[e] * d3[2][e]);
+            }
+            // sum over the lanes of the group (all lanes of the warp take part)
+            for (int off = L >> 1; off > 0; off >>= 1)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) u[i] += __shfl_xor_sync(kFullMask, u[i], off);
+            if (active && sub == 0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const double d = p.mg[3 * a] * u[0] + p.mg[3 * a + 1] * u[1] + p.mg[3 * a + 2] * u[2];
+                    atomicAdd(b.dpos + 3 * ip + a, d);
+                }
+            }
+        }
+    }
+}
+
+template <typename T, bool LAPTAB>
+int launch_typed(const BwdArgs& a, cudaStream_t st)
+{
+    const int gpw = 32 >> a.e.lanes_log2;
+    const long long groups = a.e.n_pos * a.e.tiles;
+    const long long warps = (groups + gpw - 1) / gpw;
+    long long blocks = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bspline_bwd_kernel<T, LAPTAB>,
+                                                                  kEvalThreads, 0);
+    if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+    if (per_sm < 1) per_sm = 1;
+    const long long cap = (long long)sm_count() * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    bspline_bwd_kernel<T, LAPTAB><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
+    return cuda_error(cudaGetLastError(), "bspline_bwd_kernel launch");
+}
+
+}  // namespace
+
+int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos, const void* gv,
+                            const void* gg, const void* gl, void* dcoef, void* dcoef_lap, double* dpos,
+                            cudaStream_t st)
+{
+    BwdArgs a;
+    fill_eval_args(h, &a.e);
+    a.e.pos = pos;
+    a.e.n_pos = n_pos;
+    a.gv = gv;
+    a.gg = gg;
+    a.gl = gl;
+    a.dcoef = dcoef;
+    a.dcoef_lap = dcoef_lap;
+    a.dpos = dpos;
+    const size_t ob = (h->storage == QMCSPL_F64) ? 8 : 4;
+    const uintptr_t al = (uintptr_t)dcoef | (uintptr_t)dcoef_lap;
+    a.vec_atomic = ((h->n_orb * ob) % 16 == 0) && (al % 16 == 0);
+    if (dpos) {
+        cudaError_t e = cudaMemsetAsync(dpos, 0, sizeof(double) * 3 * (size_t)n_pos, st);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(dpos)");
+    }
+    if (!dcoef && !dpos) return QMCSPL_OK;
+    const bool lt = h->separate_lap != 0;
+    switch (h->storage) {
+    case QMCSPL_F64: return lt ? launch_typed<double, true>(a, st) : launch_typed<double, false>(a, st);
+    case QMCSPL_F32: return lt ? launch_typed<float, true>(a, st) : launch_typed<float, false>(a, st);
+    default:
+        return lt ? launch_typed<__nv_bfloat16, true>(a, st) : launch_typed<__nv_bfloat16, false>(a, st);
+    }
+}
+
+}  // namespace qmcspl

@@ -158,7 +158,13 @@ void free_handle(Handle* h)
     }
     if (h->st_ready)
         for (int i = 0; i < 6; ++i) cudaEventDestroy(h->st_ev[i]);
-    if (h->batch_desc) cudaFree(h->batch_desc);
+    if (h->ord_bin) cudaFree(h->ord_bin);
+    if (h->ord_perm) cudaFree(h->ord_perm);
+    if (h->ord_count) cudaFree(h->ord_count);
+    if (h->prof_ev) {
+        for (int i = 0; i < 3 * kProfCalls; ++i) cudaEventDestroy(h->prof_ev[i]);
+        delete[] h->prof_ev;
+    }
     delete h;
     cudaSetDevice(prev);
 }
@@ -310,11 +316,23 @@ int qmcspl_info(qmcspl_t h, qmcspl_info_t* out)
 static int eval_dispatch(Handle* h, const double* pos, long long n_pos, void* val, void* grad,
                          void* lap, cudaStream_t st)
 {
-    switch (h->method) {
-    case QMCSPL_LAGRANGE: return launch_lagrange_vgl(h, pos, n_pos, val, grad, lap, st);
-    case QMCSPL_PPSPLINE: return launch_pp_vgl(h, pos, n_pos, val, grad, lap, st);
-    default: return launch_bspline_vgl(h, pos, n_pos, val, grad, lap, st);
+    cudaEvent_t* ev = nullptr;
+    if (h->prof_on && h->prof_n < kProfCalls) ev = h->prof_ev + 3 * h->prof_n++;
+    if (ev) cudaEventRecord(ev[0], st);
+    const int* perm = nullptr;
+    if (use_cell_order(h, n_pos)) {
+        const int rc = cell_order(h, pos, n_pos, &perm, st);
+        if (rc != QMCSPL_OK) return rc;
     }
+    if (ev) cudaEventRecord(ev[1], st);
+    int rc;
+    switch (h->method) {
+    case QMCSPL_LAGRANGE: rc = launch_lagrange_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
+    case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
+    default: rc = launch_bspline_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
+    }
+    if (ev) cudaEventRecord(ev[2], st);
+    return rc;
 }
 
 int qmcspl_eval_vgl(qmcspl_t h, const double* pos, long long n_pos, void* val, void* grad,
@@ -437,8 +455,8 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* po
     for (int c = 0; c < n_cells; ++c) {
         if (!hs[c]) return set_error(QMCSPL_ERR_ARG, "NULL handle in batch");
         if (hs[c]->device != hs[0]->device) return set_error(QMCSPL_ERR_ARG, "handles on different devices");
-        if (hs[c]->storage != hs[0]->storage)
-            return set_error(QMCSPL_ERR_ARG, "handles of a batch must share the storage type");
+        if (hs[c]->storage != hs[0]->storage || hs[c]->separate_lap != hs[0]->separate_lap)
+            return set_error(QMCSPL_ERR_ARG, "handles of a batch must share storage type and separate_lap");
         if (hs[c]->method != QMCSPL_BSPLINE_SMOOTH && hs[c]->method != QMCSPL_BSPLINE_INTERP)
             return set_error(QMCSPL_ERR_UNSUPPORTED, "batched evaluation is for B-spline handles");
         if (n_pos[c] < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
@@ -496,6 +514,60 @@ int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream)
                 }
             }
     delete[] raw;
+    return QMCSPL_OK;
+}
+
+int qmcspl_profile(qmcspl_t h, int enable)
+{
+    g_err.clear();
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    DeviceGuard dg(h->device);
+    if (enable && !h->prof_ev) {
+        h->prof_ev = new (std::nothrow) cudaEvent_t[3 * kProfCalls];
+        if (!h->prof_ev) return set_error(QMCSPL_ERR_OOM, "host allocation failed");
+        for (int i = 0; i < 3 * kProfCalls; ++i) {
+            cudaError_t e = cudaEventCreate(&h->prof_ev[i]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < i; ++j) cudaEventDestroy(h->prof_ev[j]);
+                delete[] h->prof_ev;
+                h->prof_ev = nullptr;
+                return cuda_error(e, "cudaEventCreate");
+            }
+        }
+    }
+    h->prof_on = enable != 0;
+    if (enable) h->prof_n = 0;
+    return QMCSPL_OK;
+}
+
+int qmcspl_profile_read(qmcspl_t h, double* eval_ms, double* order_ms, long long* launches)
+{
+    g_err.clear();
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    DeviceGuard dg(h->device);
+    double te = 0.0, to = 0.0;
+    for (int i = 0; i < h->prof_n; ++i) {
+        cudaEvent_t* ev = h->prof_ev + 3 * i;
+        cudaError_t e = cudaEventSynchronize(ev[2]);
+        float a = 0.f, b = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[1], ev[2]);
+        if (e != cudaSuccess) return cuda_error(e, "profile events");
+        to += a;
+        te += b;
+    }
+    if (eval_ms) *eval_ms = te;
+    if (order_ms) *order_ms = to;
+    if (launches) *launches = h->prof_n;
+    return QMCSPL_OK;
+}
+
+int qmcspl_set_order(qmcspl_t h, int mode)
+{
+    g_err.clear();
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    if (mode < QMCSPL_ORDER_AUTO || mode > QMCSPL_ORDER_CELL) return set_error(QMCSPL_ERR_ARG, "unknown order mode");
+    h->order_mode = mode;
     return QMCSPL_OK;
 }
 

@@ -17,183 +17,265 @@
 // Hessian-derived Laplacian folds the metric N_i N_j (a^-1 a^-T)_ij into the per-column
 // weights so only one accumulator per orbital is needed.
 //
-// The kernel is a gather bounded by memory bandwidth (HBM when the table exceeds the
-// L2): no tensor cores, since each position gathers its own stencil.
+// Every warp task (32 lanes x one chunk x 64 rows per table) moves the same number of
+// bytes whatever the orbital count, which is what lets the batched kernel mix cells
+// with different orbital counts and grids in one launch with a static schedule.
+//
+// The kernel is a gather bounded by memory bandwidth: no tensor cores, since each
+// position gathers its own stencil.
 #include "eval_common.cuh"
 
 namespace qmcspl {
 namespace {
 
+// Evaluate the groups [w0, w0 + groups per warp) of one cell.  Called by all 32 lanes.
 template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(kEvalThreads, 2) bspline_vgl_kernel(const EvalArgs p)
+__device__ __forceinline__ void bspline_warp_task(const EvalArgs& p, long long w0, int lane)
 {
     using A = typename Traits<T>::A;
     constexpr int E = Traits<T>::E;
-    const int lane = threadIdx.x & 31;
     const int L = 1 << p.lanes_log2;
     const int sub = lane & (L - 1);
     const int gbase = lane & ~(L - 1);
+    const long long total = p.n_pos * p.tiles;
+    const size_t rowb = (size_t)p.row_stride * sizeof(T);
+    const size_t colb = (size_t)p.col_stride * sizeof(T);
+
+    const long long gid = w0 + (lane >> p.lanes_log2);
+    const bool active = gid < total;
+    const long long q = active ? gid / p.tiles : 0;
+    const int tile = active ? (int)(gid - q * p.tiles) : 0;
+    const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
+    const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+    int ix, iy, iz;
+    double tx, ty, tz;
+    bool ok;
+    reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    if (!active) return;
+    if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+
+    A bx[4], dbx[4], d2bx[4], by[4], dby[4], d2by[4], bz[4], dbz[4], d2bz[4];
+    bspline_weights<A>((A)tx, bx, dbx, LAPTAB ? nullptr : d2bx);
+    bspline_weights<A>((A)ty, by, dby, LAPTAB ? nullptr : d2by);
+    bspline_weights<A>((A)tz, bz, dbz, LAPTAB ? nullptr : d2bz);
+
+    int xs[4], ys[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        xs[j] = wrap1(ix + j - 1, p.nx);
+        ys[j] = wrap1(iy + j - 1, p.ny);
+    }
+    const int chunk = tile * L + sub;
+    const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
+    const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb
+                            : nullptr;
+
+    A v[E], gx[E], gy[E], gz[E], lp[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = gx[e] = gy[e] = gz[e] = lp[e] = A(0);
+
+    A ml0 = 0, ml1 = 0, ml2 = 0, ml3 = 0, ml4 = 0, ml5 = 0;
+    if (!LAPTAB) {
+        ml0 = (A)p.ml[0]; ml1 = (A)p.ml[1]; ml2 = (A)p.ml[2];
+        ml3 = (A)p.ml[3]; ml4 = (A)p.ml[4]; ml5 = (A)p.ml[5];
+    }
+
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb;
+            uint4 raw[4], rawl[4];
+#pragma unroll
+            for (int n = 0; n < 4; ++n) raw[n] = ldg16(t0 + col + n * rowb);
+            if (LAPTAB) {
+#pragma unroll
+                for (int n = 0; n < 4; ++n) rawl[n] = ldg16(t1 + col + n * rowb);
+            }
+            A a0[E], a1[E], a2[E], al[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) a0[e] = a1[e] = a2[e] = al[e] = A(0);
+#pragma unroll
+            for (int n = 0; n < 4; ++n) {
+                A c[E];
+                unpack<T>(raw[n], c);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    a0[e] = fma(bz[n], c[e], a0[e]);
+                    a1[e] = fma(dbz[n], c[e], a1[e]);
+                    if (!LAPTAB) a2[e] = fma(d2bz[n], c[e], a2[e]);
+                }
+                if (LAPTAB) {
+                    A cl[E];
+                    unpack<T>(rawl[n], cl);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) al[e] = fma(bz[n], cl[e], al[e]);
+                }
+            }
+            const A w00 = bx[l] * by[m];
+            const A w10 = dbx[l] * by[m];
+            const A w01 = bx[l] * dby[m];
+            A c0 = 0, c1 = 0, c2 = 0;
+            if (!LAPTAB) {
+                c0 = ml0 * (d2bx[l] * by[m]) + ml1 * (bx[l] * d2by[m]) + ml3 * (dbx[l] * dby[m]);
+                c1 = ml4 * w10 + ml5 * w01;
+                c2 = ml2 * w00;
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                v[e] = fma(w00, a0[e], v[e]);
+                gx[e] = fma(w10, a0[e], gx[e]);
+                gy[e] = fma(w01, a0[e], gy[e]);
+                gz[e] = fma(w00, a1[e], gz[e]);
+                if (LAPTAB) {
+                    lp[e] = fma(w00, al[e], lp[e]);
+                } else {
+                    lp[e] = fma(c0, a0[e], fma(c1, a1[e], fma(c2, a2[e], lp[e])));
+                }
+            }
+        }
+    }
+
+    const int o0 = chunk * E;
+    if (o0 >= p.n_orb) return;
+    const bool vec = p.vec_out != 0;
+    if (p.val) store_run<A, E>(static_cast<A*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
+    if (p.grad) {
+        A* g = static_cast<A*>(p.grad) + ip * 3 * p.n_orb + o0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const A m0 = (A)p.mg[3 * a], m1 = (A)p.mg[3 * a + 1], m2 = (A)p.mg[3 * a + 2];
+            A c[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) c[e] = fma(m0, gx[e], fma(m1, gy[e], m2 * gz[e]));
+            store_run<A, E>(g + (size_t)a * p.n_orb, c, o0, p.n_orb, vec);
+        }
+    }
+    if (p.lap) store_run<A, E>(static_cast<A*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
+}
+
+template <typename T, bool LAPTAB>
+__global__ void __launch_bounds__(kEvalThreads, 2) bspline_vgl_kernel(const EvalArgs p)
+{
+    const int lane = threadIdx.x & 31;
     const int gpw = 32 >> p.lanes_log2;
     const long long total = p.n_pos * p.tiles;
     const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
     const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
-    const size_t rowb = (size_t)p.row_stride * sizeof(T);
-    const size_t colb = (size_t)p.col_stride * sizeof(T);
+    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw)
+        bspline_warp_task<T, LAPTAB>(p, w0, lane);
+}
 
-    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
-        const long long gid = w0 + (lane >> p.lanes_log2);
-        const bool active = gid < total;
-        const long long ip = active ? gid / p.tiles : 0;
-        const int tile = active ? (int)(gid - ip * p.tiles) : 0;
-        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
-        int ix, iy, iz;
-        double tx, ty, tz;
-        bool ok;
-        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
-        if (!active) continue;
-        if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+// Several cells in one launch: warp task w belongs to the cell c with
+// start[c] <= w < start[c + 1]; tasks are handed out round-robin over all warps.
+struct BatchArgs {
+    int n_cells;
+    long long start[QMCSPL_MAX_BATCH + 1];   // prefix sums of warp tasks per cell
+    EvalArgs cell[QMCSPL_MAX_BATCH];
+};
+static_assert(sizeof(BatchArgs) <= 32000, "batched kernel parameters exceed the 32 KB limit");
 
-        A bx[4], dbx[4], d2bx[4], by[4], dby[4], d2by[4], bz[4], dbz[4], d2bz[4];
-        bspline_weights<A>((A)tx, bx, dbx, LAPTAB ? nullptr : d2bx);
-        bspline_weights<A>((A)ty, by, dby, LAPTAB ? nullptr : d2by);
-        bspline_weights<A>((A)tz, bz, dbz, LAPTAB ? nullptr : d2bz);
-
-        int xs[4], ys[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            xs[j] = wrap1(ix + j - 1, p.nx);
-            ys[j] = wrap1(iy + j - 1, p.ny);
-        }
-        const int chunk = tile * L + sub;
-        const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
-        const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb
-                                : nullptr;
-
-        A v[E], gx[E], gy[E], gz[E], lp[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = gx[e] = gy[e] = gz[e] = lp[e] = A(0);
-
-        A ml0 = 0, ml1 = 0, ml2 = 0, ml3 = 0, ml4 = 0, ml5 = 0;
-        if (!LAPTAB) {
-            ml0 = (A)p.ml[0]; ml1 = (A)p.ml[1]; ml2 = (A)p.ml[2];
-            ml3 = (A)p.ml[3]; ml4 = (A)p.ml[4]; ml5 = (A)p.ml[5];
-        }
-
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb;
-                uint4 raw[4], rawl[4];
-#pragma unroll
-                for (int n = 0; n < 4; ++n) raw[n] = ldg16(t0 + col + n * rowb);
-                if (LAPTAB) {
-#pragma unroll
-                    for (int n = 0; n < 4; ++n) rawl[n] = ldg16(t1 + col + n * rowb);
-                }
-                A a0[E], a1[E], a2[E], al[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) a0[e] = a1[e] = a2[e] = al[e] = A(0);
-#pragma unroll
-                for (int n = 0; n < 4; ++n) {
-                    A c[E];
-                    unpack<T>(raw[n], c);
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        a0[e] = fma(bz[n], c[e], a0[e]);
-                        a1[e] = fma(dbz[n], c[e], a1[e]);
-                        if (!LAPTAB) a2[e] = fma(d2bz[n], c[e], a2[e]);
-                    }
-                    if (LAPTAB) {
-                        A cl[E];
-                        unpack<T>(rawl[n], cl);
-#pragma unroll
-                        for (int e = 0; e < E; ++e) al[e] = fma(bz[n], cl[e], al[e]);
-                    }
-                }
-                const A w00 = bx[l] * by[m];
-                const A w10 = dbx[l] * by[m];
-                const A w01 = bx[l] * dby[m];
-                A c0 = 0, c1 = 0, c2 = 0;
-                if (!LAPTAB) {
-                    c0 = ml0 * (d2bx[l] * by[m]) + ml1 * (bx[l] * d2by[m]) + ml3 * (dbx[l] * dby[m]);
-                    c1 = ml4 * w10 + ml5 * w01;
-                    c2 = ml2 * w00;
-                }
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    v[e] = fma(w00, a0[e], v[e]);
-                    gx[e] = fma(w10, a0[e], gx[e]);
-                    gy[e] = fma(w01, a0[e], gy[e]);
-                    gz[e] = fma(w00, a1[e], gz[e]);
-                    if (LAPTAB) {
-                        lp[e] = fma(w00, al[e], lp[e]);
-                    } else {
-                        lp[e] = fma(c0, a0[e], fma(c1, a1[e], fma(c2, a2[e], lp[e])));
-                    }
-                }
-            }
-        }
-
-        const int o0 = chunk * E;
-        if (o0 >= p.n_orb) continue;
-        const bool vec = p.vec_out != 0;
-        if (p.val) store_run<A, E>(static_cast<A*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
-        if (p.grad) {
-            A* g = static_cast<A*>(p.grad) + ip * 3 * p.n_orb + o0;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const A m0 = (A)p.mg[3 * a], m1 = (A)p.mg[3 * a + 1], m2 = (A)p.mg[3 * a + 2];
-                A c[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) c[e] = fma(m0, gx[e], fma(m1, gy[e], m2 * gz[e]));
-                store_run<A, E>(g + (size_t)a * p.n_orb, c, o0, p.n_orb, vec);
-            }
-        }
-        if (p.lap) store_run<A, E>(static_cast<A*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
+template <typename T, bool LAPTAB>
+__global__ void __launch_bounds__(kEvalThreads, 2) bspline_vgl_batched_kernel(const __grid_constant__ BatchArgs b)
+{
+    const int lane = threadIdx.x & 31;
+    const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
+    const long long total = b.start[b.n_cells];
+    int c = 0;
+    for (long long w = warp; w < total; w += wstride) {
+        while (w >= b.start[c + 1]) ++c;          // tasks only move forward
+        const EvalArgs& p = b.cell[c];
+        const long long local = w - b.start[c];
+        bspline_warp_task<T, LAPTAB>(p, local * (32 >> p.lanes_log2), lane);
     }
+}
+
+template <typename K>
+long long grid_for(K kernel, long long warps)
+{
+    long long blocks = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kEvalThreads, 0) != cudaSuccess)
+        per_sm = 1;
+    if (per_sm < 1) per_sm = 1;
+    const long long cap = (long long)sm_count() * per_sm;
+    if (blocks > cap) blocks = cap;
+    return blocks < 1 ? 1 : blocks;
 }
 
 template <typename T, bool LAPTAB>
 int launch_typed(const EvalArgs& a, cudaStream_t st)
 {
     const int gpw = 32 >> a.lanes_log2;
-    const long long groups = a.n_pos * a.tiles;
-    const long long warps = (groups + gpw - 1) / gpw;
-    long long blocks = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, bspline_vgl_kernel<T, LAPTAB>, kEvalThreads, 0);
-    if (e != cudaSuccess) return cuda_error(e, "occupancy query");
-    if (per_sm < 1) per_sm = 1;
-    const long long cap = (long long)sm_count() * per_sm;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
+    const long long warps = (a.n_pos * a.tiles + gpw - 1) / gpw;
+    const long long blocks = grid_for(bspline_vgl_kernel<T, LAPTAB>, warps);
     bspline_vgl_kernel<T, LAPTAB><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "bspline_vgl_kernel launch");
 }
 
-}  // namespace
-
-int launch_bspline_vgl(const Handle* h, const double* pos, long long n_pos, void* val,
-                       void* grad, void* lap, cudaStream_t st)
+template <typename T, bool LAPTAB>
+int launch_batched_typed(const BatchArgs& b, cudaStream_t st)
 {
-    EvalArgs a;
-    fill_eval_args(h, &a);
-    a.pos = pos;
-    a.n_pos = n_pos;
+    const long long blocks = grid_for(bspline_vgl_batched_kernel<T, LAPTAB>, b.start[b.n_cells]);
+    bspline_vgl_batched_kernel<T, LAPTAB><<<(unsigned)blocks, kEvalThreads, 0, st>>>(b);
+    return cuda_error(cudaGetLastError(), "bspline_vgl_batched_kernel launch");
+}
+
+void set_outputs(const Handle* h, EvalArgs& a, void* val, void* grad, void* lap)
+{
     a.val = val;
     a.grad = grad;
     a.lap = lap;
     const size_t ob = (h->storage == QMCSPL_F64) ? 8 : 4;
     const uintptr_t al = (uintptr_t)val | (uintptr_t)grad | (uintptr_t)lap;
     a.vec_out = ((h->n_orb * ob) % 16 == 0) && (al % 16 == 0);
+}
+
+}  // namespace
+
+int launch_bspline_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos, void* val,
+                       void* grad, void* lap, cudaStream_t st)
+{
+    EvalArgs a;
+    fill_eval_args(h, &a);
+    a.pos = pos;
+    a.perm = perm;
+    a.n_pos = n_pos;
+    set_outputs(h, a, val, grad, lap);
     const bool lt = h->separate_lap != 0;
     switch (h->storage) {
     case QMCSPL_F64: return lt ? launch_typed<double, true>(a, st) : launch_typed<double, false>(a, st);
     case QMCSPL_F32: return lt ? launch_typed<float, true>(a, st) : launch_typed<float, false>(a, st);
     default:
         return lt ? launch_typed<__nv_bfloat16, true>(a, st) : launch_typed<__nv_bfloat16, false>(a, st);
+    }
+}
+
+int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const long long* n_pos,
+                   void* const* val, void* const* grad, void* const* lap, cudaStream_t st)
+{
+    thread_local BatchArgs B;   // about 16 KB: kept off the stack, one per calling thread
+    B.n_cells = n_cells;
+    B.start[0] = 0;
+    for (int c = 0; c < n_cells; ++c) {
+        EvalArgs& a = B.cell[c];
+        fill_eval_args(hs[c], &a);
+        a.pos = pos[c];
+        a.perm = nullptr;
+        a.n_pos = n_pos[c];
+        set_outputs(hs[c], a, val[c], grad[c], lap[c]);
+        const int gpw = 32 >> a.lanes_log2;
+        B.start[c + 1] = B.start[c] + (a.n_pos * a.tiles + gpw - 1) / gpw;
+    }
+    if (B.start[n_cells] == 0) return QMCSPL_OK;
+    const bool lt = hs[0]->separate_lap != 0;
+    switch (hs[0]->storage) {
+    case QMCSPL_F64: return lt ? launch_batched_typed<double, true>(B, st) : launch_batched_typed<double, false>(B, st);
+    case QMCSPL_F32: return lt ? launch_batched_typed<float, true>(B, st) : launch_batched_typed<float, false>(B, st);
+    default:
+        return lt ? launch_batched_typed<__nv_bfloat16, true>(B, st)
+                  : launch_batched_typed<__nv_bfloat16, false>(B, st);
     }
 }
 

@@ -28,6 +28,7 @@ using Handle = ::qmcspl_s;
 
 constexpr int kMaxDim = 512;          // grid points per axis accepted by qmcspl_create
 constexpr int kEvalThreads = 256;     // eval kernels: 8 warps per block
+constexpr int kProfCalls = 4096;      // calls qmcspl_profile can record
 
 enum BuildKind : int {
     kBuildSmoothValue = 0,   // c_G / gamma_G
@@ -55,6 +56,7 @@ struct EvalArgs {
     double mg[9];             // grad_cart[a] = sum_i mg[3a+i] grad_t[i]
     double ml[6];             // lap = ml0 Hxx + ml1 Hyy + ml2 Hzz + ml3 Hxy + ml4 Hxz + ml5 Hyz
     const double* pos;
+    const int* perm;          // evaluation order: position perm[i] is the i-th evaluated (null: input order)
     long long n_pos;
     void* val;
     void* grad;
@@ -91,8 +93,18 @@ struct qmcspl_s {
     cudaStream_t st_stream[2] = {nullptr, nullptr};
     cudaEvent_t st_ev[6] = {};
     bool st_ready = false;
-    // batched-call descriptor buffer (device)
-    void* batch_desc = nullptr;
+    // cell-ordering scratch (device): per-position bin, bin counts/offsets, permutation
+    int* ord_bin = nullptr;
+    int* ord_count = nullptr;
+    int* ord_perm = nullptr;
+    long long ord_cap = 0;    // positions the scratch can hold
+    int ord_nbins = 0;        // bins the count array can hold
+    int order_mode = 0;       // QMCSPL_ORDER_AUTO / INPUT / CELL
+    // kernel timing (qmcspl_profile): per call, events before ordering, before and
+    // after the evaluation kernel
+    bool prof_on = false;
+    int prof_n = 0;           // calls recorded
+    cudaEvent_t* prof_ev = nullptr;   // 3 * kProfCalls events, created on first enable
 
     const void* table(int t) const
     {
@@ -115,18 +127,35 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
                  cudaStream_t stream);
 
 // ---- evaluation launchers ----
-int launch_bspline_vgl(const Handle* h, const double* pos, long long n_pos, void* val,
-                       void* grad, void* lap, cudaStream_t stream);
-int launch_lagrange_vgl(const Handle* h, const double* pos, long long n_pos, void* val,
-                        void* grad, void* lap, cudaStream_t stream);
-int launch_pp_vgl(const Handle* h, const double* pos, long long n_pos, void* val, void* grad,
-                  void* lap, cudaStream_t stream);
+int launch_bspline_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos,
+                       void* val, void* grad, void* lap, cudaStream_t stream);
+int launch_lagrange_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos,
+                        void* val, void* grad, void* lap, cudaStream_t stream);
+int launch_pp_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos, void* val,
+                  void* grad, void* lap, cudaStream_t stream);
 int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
                             const void* gv, const void* gg, const void* gl, void* dcoef,
                             void* dcoef_lap, double* dpos, cudaStream_t stream);
 int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos,
                    const long long* n_pos, void* const* val, void* const* grad,
                    void* const* lap, cudaStream_t stream);
+
+// ---- cell ordering (order.cu) ----
+// Bin geometry of a handle: bins of `edge` grid cells per axis, nb[3] bins per axis.
+struct BinGeometry {
+    int edge;
+    int nb[3];
+    int n_bins;
+};
+BinGeometry bin_geometry(const Handle* h);
+// True when the evaluation of n_pos positions should run in cell order.
+bool use_cell_order(const Handle* h, long long n_pos);
+// Build the cell-order permutation of `pos` into the scratch arrays given (device
+// pointers sized for n_pos positions and g.n_bins + 1 counters) on `stream`.
+int build_cell_order(const Handle* h, const double* pos, long long n_pos, int* bin, int* count,
+                     int* perm, const BinGeometry& g, cudaStream_t stream);
+// Same, using the handle's own scratch (grown on demand); returns the permutation.
+int cell_order(Handle* h, const double* pos, long long n_pos, const int** perm, cudaStream_t stream);
 
 // fill the common part of EvalArgs from a handle
 void fill_eval_args(const Handle* h, EvalArgs* a);

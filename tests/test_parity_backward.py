@@ -1,0 +1,150 @@
+"""GPU adjoint (qmcspl_eval_vgl_backward and the autograd binding) against the FP64
+oracle adjoint, an exact linearity identity and central finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_6250_gb300 import inputs
+from gpu_helpers import NONORTHO, TOL, dev, rounded, splines
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def t(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device=dev(), dtype=dtype)
+
+
+def gpu_backward(spl, pos, gv, gg, gl):
+    sep = bool(spl.info()["separate_lap"])
+    dc = torch.zeros(spl.coef_shape(), dtype=spl.out_dtype, device=dev())
+    dcl = torch.zeros_like(dc) if sep else None
+    dpos = spl.backward(t(pos, torch.float64), t(gv, spl.out_dtype), t(gg, spl.out_dtype),
+                        t(gl, spl.out_dtype), dcoef=dc, dcoef_lap=dcl)
+    spl.sync()
+    return dc.double().cpu().numpy(), None if dcl is None else dcl.double().cpu().numpy(), \
+        dpos.cpu().numpy()
+
+
+def away_from_planes(lat, dims, pos, margin):
+    s = pos @ np.linalg.inv(lat).T * np.array(dims)
+    f = s - np.floor(s)
+    return np.all((f > margin) & (f < 1 - margin), axis=1)
+
+
+@pytest.mark.parametrize("method", ["smooth", "interp"])
+@pytest.mark.parametrize("sep", [False, True])
+@pytest.mark.parametrize("n_orb", [3, 16])
+def test_fp64_backward_matches_oracle(method, sep, n_orb):
+    dims = (9, 10, 11)
+    lat, mil, coef = inputs.random_cell(600 + n_orb, dims, n_orb, 6.0, 5.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method=method, storage="f64", separate_lap=sep)
+    beta = spl.get_table(0)
+    blap = spl.get_table(1) if sep else None
+    pos = inputs.positions(lat, 300, 12, -1, 2)
+    gv, gg, gl = inputs.upstream_weights(300, n_orb, 13)
+    dc, dcl, dpos = gpu_backward(spl, pos, gv, gg, gl)
+    rdc, rdcl, rdpos = oracle.bspline_adjoint(beta, lat, pos, gv, gg, gl, beta_lap=blap)
+    assert oracle.relative_error(dc, rdc) < 1e-12
+    if sep:
+        assert oracle.relative_error(dcl, rdcl) < 1e-12
+    assert oracle.relative_error(dpos, rdpos) < 1e-12
+
+
+def test_fp64_linearity_identity_and_position_fd():
+    """L is linear in beta: sum(dL/dbeta * beta) = L(beta) with the GPU forward pass; and
+    dL/dr against central differences of the GPU forward (h = 1e-4 bohr, FP64)."""
+    dims = (12, 12, 12)
+    lat, mil, coef = inputs.random_cell(700, dims, 8, 6.0, 5.0, NONORTHO)
+    for sep in (False, True):
+        spl = splines(lat, dims, mil, coef, method="smooth", storage="f64", separate_lap=sep)
+        pos = inputs.positions(lat, 200, 14)
+        pos = pos[away_from_planes(lat, dims, pos, 0.01)]
+        n = pos.shape[0]
+        gv, gg, gl = inputs.upstream_weights(n, 8, 15)
+
+        def loss(p):
+            v, g, l = spl.eval_vgl(t(p, torch.float64))
+            spl.sync()
+            return (np.sum(gv * v.cpu().numpy()) + np.sum(gg * g.cpu().numpy()) +
+                    np.sum(gl * l.cpu().numpy()))
+
+        dc, dcl, dpos = gpu_backward(spl, pos, gv, gg, gl)
+        lin = np.sum(dc * spl.get_table(0)) + (np.sum(dcl * spl.get_table(1)) if sep else 0.0)
+        assert lin == pytest.approx(loss(pos), rel=1e-12)
+        h = 1e-4
+        fd = np.zeros_like(dpos)
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            # per-position losses: perturb one coordinate of every position at once
+            # (positions are independent, so the sum separates)
+            lp = [None, None]
+            for k, sgn in enumerate((1, -1)):
+                v, g, l = spl.eval_vgl(t(pos + sgn * e, torch.float64))
+                spl.sync()
+                lp[k] = (np.sum(gv * v.cpu().numpy(), 1) + np.sum(gg * g.cpu().numpy(), (1, 2)) +
+                         np.sum(gl * l.cpu().numpy(), 1))
+            fd[:, a] = (lp[0] - lp[1]) / (2 * h)
+        assert oracle.relative_error(dpos, fd) < 1e-6
+
+
+def test_c5_si64_backward_fp32():
+    """Si-like 64-atom cell, 128 orbitals on 72^3, FP32 tables with the Laplacian table,
+    4096 positions, N(0,1) upstream weights on value, gradient and Laplacian: coefficient
+    and position gradients against the oracle adjoint (FP64, same rounded tables)."""
+    w = inputs.make_workload("c5")
+    dims = w.cell.grid
+    spl = splines(w.lattice, dims, w.miller, w.coef, method="smooth", storage="f32", separate_lap=True)
+    beta = spl.get_table(0)       # the stored FP32 values, exactly
+    blap = spl.get_table(1)
+    n = w.pos.shape[0]
+    gv, gg, gl = inputs.upstream_weights(n, w.coef.shape[0], 3005)
+    gv32, gg32, gl32 = (x.astype(np.float32).astype(np.float64) for x in (gv, gg, gl))
+    dc, dcl, dpos = gpu_backward(spl, w.pos, gv32, gg32, gl32)
+    rdc, rdcl, rdpos = oracle.bspline_adjoint(beta, w.lattice, w.pos, gv32, gg32, gl32, beta_lap=blap)
+    e = [oracle.relative_error(dc, rdc), oracle.relative_error(dcl, rdcl), oracle.relative_error(dpos, rdpos)]
+    print("c5 backward relative errors (dcoef, dcoef_lap, dpos): %s" % ["%.2e" % x for x in e])
+    assert e[0] < TOL["f32"] and e[1] < TOL["f32"] and e[2] < TOL["f32"]
+    # the exact tables were built from the same planewaves in FP64: within FP32 rounding
+    rb, _ = oracle.smoothing_tables(w.lattice, w.miller, w.coef[:8], dims)
+    assert oracle.relative_error(beta[..., :8], rb) < 1e-7
+
+
+def test_autograd_function_positions_and_coefficients():
+    from paper_1309_6250_gb300.autograd import evaluate
+    dims = (10, 10, 12)
+    lat, mil, coef = inputs.random_cell(800, dims, 6, 6.0, 5.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="smooth", storage="f64", separate_lap=True)
+    beta, beta_lap = spl.coefficient_parameters()
+    pos_np = inputs.positions(lat, 64, 16)
+    pos = t(pos_np, torch.float64).requires_grad_(True)
+    gv, gg, gl = inputs.upstream_weights(64, 6, 17)
+    v, g, l = evaluate(spl, pos, beta, beta_lap)
+    loss = (v * t(gv, torch.float64)).sum() + (g * t(gg, torch.float64)).sum() + \
+        (l * t(gl, torch.float64)).sum()
+    loss.backward()
+    rdc, rdcl, rdpos = oracle.bspline_adjoint(spl.get_table(0), lat, pos_np, gv, gg, gl,
+                                              beta_lap=spl.get_table(1))
+    assert oracle.relative_error(pos.grad.cpu().numpy(), rdpos) < 1e-12
+    assert oracle.relative_error(beta.grad.cpu().numpy(), rdc) < 1e-12
+    assert oracle.relative_error(beta_lap.grad.cpu().numpy(), rdcl) < 1e-12
+    # only some outputs used: missing upstream gradients count as zero
+    pos.grad = None
+    v, g, l = evaluate(spl, pos)
+    (v * t(gv, torch.float64)).sum().backward()
+    z = np.zeros_like(gg), np.zeros_like(gl)
+    _, _, rdpos_v = oracle.bspline_adjoint(spl.get_table(0), lat, pos_np, gv, z[0], z[1],
+                                           beta_lap=spl.get_table(1))
+    assert oracle.relative_error(pos.grad.cpu().numpy(), rdpos_v) < 1e-12
+
+
+def test_backward_rejects_variants():
+    from paper_1309_6250_gb300 import _lib
+    dims = (8, 8, 8)
+    lat, mil, coef = inputs.random_cell(5, dims, 2, 5.0, 4.0, np.eye(3) * 6.0)
+    spl = splines(lat, dims, mil, coef, method="lagrange", storage="f64")
+    pos = torch.zeros((4, 3), dtype=torch.float64, device=dev())
+    with pytest.raises(_lib.QmcsplError) as ei:
+        spl.backward(pos)
+    assert ei.value.code == _lib.ERR_UNSUPPORTED

@@ -1,0 +1,120 @@
+"""Cell-ordered evaluation returns exactly the input-order results; the batched
+multi-cell launch returns exactly the per-cell results (and matches the oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_6250_gb300 import inputs
+from gpu_helpers import NONORTHO, TOL, assert_parity, dev, gpu_eval, rounded, splines
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("method,storage,sep", [("smooth", "f32", True), ("smooth", "bf16", True),
+                                                ("interp", "f64", False), ("lagrange", "f32", True),
+                                                ("pp", "f32", False)])
+def test_cell_order_is_bit_identical(method, storage, sep):
+    dims = (20, 22, 24)
+    lat, mil, coef = inputs.random_cell(77, dims, 20, 8.0, 5.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method=method, storage=storage, separate_lap=sep)
+    pos = torch.from_numpy(np.vstack([inputs.positions(lat, 30000, 6),
+                                      inputs.positions(lat, 1000, 7, -5, 6)])).to(dev())
+    outs = {}
+    for mode in ("input", "cell", "auto"):
+        spl.set_order(mode)
+        outs[mode] = [t.clone() for t in spl.eval_vgl(pos)]
+        spl.sync()
+    for mode in ("cell", "auto"):
+        for a, b in zip(outs["input"], outs[mode]):
+            assert torch.equal(a, b), mode
+
+
+def test_cell_order_small_and_nan():
+    dims = (8, 8, 8)
+    lat, mil, coef = inputs.random_cell(78, dims, 4, 5.0, 4.0, np.eye(3) * 6.0)
+    spl = splines(lat, dims, mil, coef, method="smooth", storage="f64", separate_lap=True)
+    spl.set_order("cell")
+    beta, blap = oracle.smoothing_tables(lat, mil, coef, dims, laplacian=True)
+    for n in (1, 2, 33):
+        pos = inputs.positions(lat, n, 10 + n)
+        assert_parity(gpu_eval(spl, pos), oracle.bspline_eval(beta, lat, pos, beta_lap=blap), 1e-12)
+    pos = inputs.positions(lat, 100, 3)
+    pos[5] = np.inf
+    v, _, _ = spl.eval_vgl(torch.from_numpy(pos).to(dev()))
+    from paper_1309_6250_gb300 import _lib
+    with pytest.raises(_lib.QmcsplError):
+        spl.sync()
+    v = v.cpu().numpy()
+    assert np.all(np.isnan(v[5])) and np.isfinite(np.delete(v, 5, axis=0)).all()
+
+
+def test_batched_uneven_cells_full_size():
+    """Al-like 32-atom (48 orbitals, 64^3, 512 x 96 e), Si-like 64-atom (128, 80^3,
+    1024 x 256 e) and MgO-like 16-atom (32, 64^3, 2048 x 64 e), FP32 smoothing + Laplacian
+    table, in one launch: identical to three separate launches, and on a sample of each
+    cell equal to the oracle within the FP32 tolerance."""
+    from paper_1309_6250_gb300.api import eval_batched
+    keys = ("c4-al32", "c4-si64", "c4-mgo16")
+    ws = [inputs.make_workload(k) for k in keys]
+    spls = [splines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32",
+                    separate_lap=True) for w in ws]
+    for s in spls:
+        s.set_order("input")
+    pos = [torch.from_numpy(w.pos).to(dev()) for w in ws]
+    outs = eval_batched(spls, pos)
+    torch.cuda.synchronize()
+    for s, p, o, w in zip(spls, pos, outs, ws):
+        single = s.eval_vgl(p)
+        s.sync()
+        for a, b in zip(o, single):
+            assert torch.equal(a, b), w.cell.name
+        sample = np.arange(0, w.pos.shape[0], max(1, w.pos.shape[0] // 40))
+        ref = [[], [], []]
+        for o0 in range(0, w.coef.shape[0], 32):
+            beta, blap = oracle.smoothing_tables(w.lattice, w.miller, w.coef[o0:o0 + 32], w.cell.grid,
+                                                 laplacian=True)
+            r = oracle.bspline_eval(rounded(beta, "f32"), w.lattice, w.pos[sample],
+                                    beta_lap=rounded(blap, "f32"))
+            for k in range(3):
+                ref[k].append(r[k])
+        ref = [np.concatenate(r, axis=-1) for r in ref]
+        s_t = torch.from_numpy(sample).to(dev())
+        got = [t[s_t].double().cpu().numpy() for t in o]
+        assert_parity(got, ref, TOL["f32"], w.cell.name)
+
+
+def test_batched_graph_capture_and_validation():
+    from paper_1309_6250_gb300 import _lib
+    from paper_1309_6250_gb300.api import eval_batched
+    cells = []
+    for i, dims in enumerate(((12, 12, 12), (10, 14, 16))):
+        lat, mil, coef = inputs.random_cell(500 + i, dims, 7 + 9 * i, 6.0, 5.0, NONORTHO)
+        cells.append((splines(lat, dims, mil, coef, method="smooth", storage="f32", separate_lap=True),
+                      torch.from_numpy(inputs.positions(lat, 1000 + 777 * i, 9)).to(dev())))
+    spls = [c[0] for c in cells]
+    pos = [c[1] for c in cells]
+    outs = [s.alloc_outputs(p.shape[0]) for s, p in zip(spls, pos)]
+    ref = eval_batched(spls, pos)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        eval_batched(spls, pos, outs=outs, stream=s)   # warm up on the capture stream
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            eval_batched(spls, pos, outs=outs, stream=s)
+    for o in outs:
+        for t in o:
+            t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(outs, ref):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    # mixed storage types are rejected before any launch
+    lat, mil, coef = inputs.random_cell(9, (8, 8, 8), 3, 5.0, 4.0, np.eye(3) * 6.0)
+    other = splines(lat, (8, 8, 8), mil, coef, method="smooth", storage="f64", separate_lap=True)
+    with pytest.raises(_lib.QmcsplError) as ei:
+        eval_batched([spls[0], other], [pos[0], pos[0]])
+    assert ei.value.code == _lib.ERR_ARG
