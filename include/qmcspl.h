@@ -224,6 +224,32 @@ enum qmcspl_order { QMCSPL_ORDER_AUTO = 0, QMCSPL_ORDER_INPUT = 1, QMCSPL_ORDER_
 int qmcspl_set_order(qmcspl_t h, int mode);
 
 /*
+ * qmcspl_eval_vgl_noalloc -- qmcspl_eval_vgl in cell order, allocating nothing.
+ *
+ * The paper has no counterpart; this is a service for callers that cannot allocate
+ * device memory while they evaluate: programs that give all device memory to their own
+ * pool allocator at start-up, and time-critical loops that must not call cudaMalloc or
+ * cudaFree (which can block the whole device).  It computes exactly what
+ * qmcspl_eval_vgl computes, visiting the positions in cell order, but its sort
+ * scratch (bins, permutation, bin counters) is one fixed array compiled into the
+ * library (about 8.7 MB, held on every GPU that loads the library until the process
+ * exits) instead of memory the handle allocates.  The caller still passes the
+ * positions and the outputs, laid out as for qmcspl_eval_vgl.
+ *   n_pos  0 .. QMCSPL_NOALLOC_MAX_POS; larger counts fail with QMCSPL_ERR_ARG
+ *          before anything is launched
+ *   stream cudaStream_t; asynchronous like qmcspl_eval_vgl
+ * The first call on a device looks up the array's device address (a one-time set-up
+ * per device, under a lock); make that first call before capturing any stream.
+ * Every call on a device shares the one array and leaves its contents behind; each
+ * call clears the counters it needs, but calls whose work overlaps on the GPU (on
+ * different streams, or from different threads) race on the array and must be
+ * ordered by the caller.  qmcspl_profile does not record these calls.
+ */
+#define QMCSPL_NOALLOC_MAX_POS (1 << 20)
+int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void* val,
+                            void* grad, void* lap, void* stream);
+
+/*
  * qmcspl_profile / qmcspl_profile_read -- CUDA-event timing of the library's own kernels.
  *
  * Not in the paper.  While enabled, every qmcspl_eval_vgl on the handle records CUDA

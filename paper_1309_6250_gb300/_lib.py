@@ -31,6 +31,7 @@ F32 = 1
 BF16 = 2
 
 MAX_BATCH = 48
+NOALLOC_MAX_POS = 1 << 20
 
 ORDER_AUTO = 0
 ORDER_INPUT = 1
@@ -72,6 +73,7 @@ PROTOTYPES = [
     ("qmcspl_info", I, [VP, ctypes.POINTER(Info)]),
     ("qmcspl_eval_vgl", I, [VP, VP, LL, VP, VP, VP, VP]),
     ("qmcspl_eval_vgl_host", I, [VP, VP, LL, VP, VP, VP, VP]),
+    ("qmcspl_eval_vgl_noalloc", I, [VP, VP, LL, VP, VP, VP, VP]),
     ("qmcspl_eval_vgl_backward", I, [VP, VP, LL, VP, VP, VP, VP, VP, VP, VP]),
     ("qmcspl_eval_batched", I, [I, VP, VP, VP, VP, VP, VP, VP]),
     ("qmcspl_get_table", I, [VP, I, VP, VP]),

@@ -1,0 +1,82 @@
+// noalloc.cu -- qmcspl_eval_vgl_noalloc: cell-ordered evaluation with a fixed scratch
+// array instead of allocated memory (for callers that cannot allocate device memory).
+//
+// The scratch of the cell-order sort lives in g_noalloc_scratch below, a file-scope
+// __device__ array that every GPU loading the library holds until the process exits:
+//   [0, max_pos)                    bin of each position
+//   [max_pos, 2 max_pos)            evaluation order (permutation)
+//   [2 max_pos, 2 max_pos + bins+1) bin counters, cleared by every call
+// Host code must not pass the symbol itself to a kernel (on the host it only names a
+// stand-in); the device address is looked up once per device with
+// cudaGetSymbolAddress while that device is current.
+#include <mutex>
+
+#include "qmcspl_internal.cuh"
+
+namespace qmcspl {
+namespace {
+
+constexpr long long kNoAllocMaxPos = QMCSPL_NOALLOC_MAX_POS;
+constexpr long long kNoAllocMaxBins = 1 << 16;   // bin_geometry never exceeds this
+constexpr size_t kScratchInts = (size_t)(2 * kNoAllocMaxPos + kNoAllocMaxBins + 1);
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) int g_noalloc_scratch[kScratchInts];
+
+std::mutex g_scratch_mutex;
+int* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device `dev` (looked up once).
+int scratch_on_device(int dev, int** out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return set_error(QMCSPL_ERR_UNSUPPORTED, "device index out of range");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        int* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(noalloc scratch)");
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return QMCSPL_OK;
+}
+
+}  // namespace
+}  // namespace qmcspl
+
+using namespace qmcspl;
+
+extern "C" int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void* val,
+                                       void* grad, void* lap, void* stream)
+{
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
+    if (n_pos > kNoAllocMaxPos)
+        return set_error(QMCSPL_ERR_ARG, "qmcspl_eval_vgl_noalloc: n_pos " + std::to_string(n_pos) +
+                                             " exceeds QMCSPL_NOALLOC_MAX_POS (" +
+                                             std::to_string(kNoAllocMaxPos) + ")");
+    if (n_pos == 0) return QMCSPL_OK;
+    if (!pos) return set_error(QMCSPL_ERR_ARG, "pos is NULL");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != h->device) cudaSetDevice(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int* scratch = nullptr;
+    int rc = scratch_on_device(h->device, &scratch);
+    if (rc == QMCSPL_OK) {
+        const BinGeometry g = bin_geometry(h);
+        int* bin = scratch;
+        int* perm = scratch + kNoAllocMaxPos;
+        int* count = scratch + 2 * kNoAllocMaxPos;
+        rc = build_cell_order(h, pos, n_pos, bin, count, perm, g, st);
+        if (rc == QMCSPL_OK) {
+            switch (h->method) {
+            case QMCSPL_LAGRANGE: rc = launch_lagrange_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
+            case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
+            default: rc = launch_bspline_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
+            }
+        }
+    }
+    if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+    return rc;
+}
