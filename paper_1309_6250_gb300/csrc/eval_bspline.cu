@@ -154,8 +154,175 @@ __device__ __forceinline__ void bspline_warp_task(const EvalArgs& p, long long w
     if (p.lap) store_run<A, E>(static_cast<A*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
 }
 
+// The same computation for float and bfloat16 tables with packed FP32 arithmetic
+// (fma.rn.f32x2: two orbitals per instruction) and the next stencil column's rows
+// loaded before the current column is contracted.
 template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(kEvalThreads, 2) bspline_vgl_kernel(const EvalArgs p)
+__device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long long w0, int lane)
+{
+    constexpr int E = Traits<T>::E;          // orbitals per lane (4 float, 8 bfloat16)
+    constexpr int NP = Pairs<T>::N;          // packed pairs per lane
+    constexpr int R = LAPTAB ? 8 : 4;        // rows loaded per column
+    const int L = 1 << p.lanes_log2;
+    const int sub = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const long long total = p.n_pos * p.tiles;
+    const size_t rowb = (size_t)p.row_stride * sizeof(T);
+    const size_t colb = (size_t)p.col_stride * sizeof(T);
+
+    const long long gid = w0 + (lane >> p.lanes_log2);
+    const bool active = gid < total;
+    const long long q = active ? gid / p.tiles : 0;
+    const int tile = active ? (int)(gid - q * p.tiles) : 0;
+    const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
+    const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+    int ix, iy, iz;
+    double tx, ty, tz;
+    bool ok;
+    reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    if (!active) return;
+    if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+
+    float bx[4], dbx[4], d2bx[4], by[4], dby[4], d2by[4], bz[4], dbz[4], d2bz[4];
+    bspline_weights<float>((float)tx, bx, dbx, LAPTAB ? nullptr : d2bx);
+    bspline_weights<float>((float)ty, by, dby, LAPTAB ? nullptr : d2by);
+    bspline_weights<float>((float)tz, bz, dbz, LAPTAB ? nullptr : d2bz);
+    f32x2 bz2[4], dbz2[4], d2bz2[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        bz2[n] = pack2(bz[n], bz[n]);
+        dbz2[n] = pack2(dbz[n], dbz[n]);
+        if (!LAPTAB) d2bz2[n] = pack2(d2bz[n], d2bz[n]);
+    }
+    float ml0 = 0.f, ml1 = 0.f, ml2 = 0.f, ml3 = 0.f, ml4 = 0.f, ml5 = 0.f;
+    if (!LAPTAB) {
+        ml0 = (float)p.ml[0]; ml1 = (float)p.ml[1]; ml2 = (float)p.ml[2];
+        ml3 = (float)p.ml[3]; ml4 = (float)p.ml[4]; ml5 = (float)p.ml[5];
+    }
+    int xs[4], ys[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        xs[j] = wrap1(ix + j - 1, p.nx);
+        ys[j] = wrap1(iy + j - 1, p.ny);
+    }
+    const int chunk = tile * L + sub;
+    const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
+    const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb
+                            : nullptr;
+
+    f32x2 V[NP], GX[NP], GY[NP], GZ[NP], LP[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) V[j] = GX[j] = GY[j] = GZ[j] = LP[j] = 0ull;
+
+    uint4 cur[R], nxt[R];
+    {
+        const size_t col = (size_t)(xs[0] * p.ny + ys[0]) * colb;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) cur[n] = ldg16(t0 + col + n * rowb);
+        if (LAPTAB) {
+#pragma unroll
+            for (int n = 0; n < 4; ++n) cur[4 + n] = ldg16(t1 + col + n * rowb);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        const int l = c >> 2, m = c & 3;
+        if (c < 15) {   // next column's rows in flight while this one is contracted
+            const int ln = (c + 1) >> 2, mn = (c + 1) & 3;
+            const size_t col = (size_t)(xs[ln] * p.ny + ys[mn]) * colb;
+#pragma unroll
+            for (int n = 0; n < 4; ++n) nxt[n] = ldg16(t0 + col + n * rowb);
+            if (LAPTAB) {
+#pragma unroll
+                for (int n = 0; n < 4; ++n) nxt[4 + n] = ldg16(t1 + col + n * rowb);
+            }
+        }
+        f32x2 A0[NP], A1[NP], A2[NP], AL[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) A0[j] = A1[j] = A2[j] = AL[j] = 0ull;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            f32x2 cv[NP];
+            Pairs<T>::get(cur[n], cv);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                A0[j] = ffma2(bz2[n], cv[j], A0[j]);
+                A1[j] = ffma2(dbz2[n], cv[j], A1[j]);
+                if (!LAPTAB) A2[j] = ffma2(d2bz2[n], cv[j], A2[j]);
+            }
+            if (LAPTAB) {
+                Pairs<T>::get(cur[4 + n], cv);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) AL[j] = ffma2(bz2[n], cv[j], AL[j]);
+            }
+        }
+        const float w00 = bx[l] * by[m], w10 = dbx[l] * by[m], w01 = bx[l] * dby[m];
+        const f32x2 W00 = pack2(w00, w00), W10 = pack2(w10, w10), W01 = pack2(w01, w01);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            V[j] = ffma2(W00, A0[j], V[j]);
+            GX[j] = ffma2(W10, A0[j], GX[j]);
+            GY[j] = ffma2(W01, A0[j], GY[j]);
+            GZ[j] = ffma2(W00, A1[j], GZ[j]);
+        }
+        if (LAPTAB) {
+#pragma unroll
+            for (int j = 0; j < NP; ++j) LP[j] = ffma2(W00, AL[j], LP[j]);
+        } else {
+            const float c0 = ml0 * (d2bx[l] * by[m]) + ml1 * (bx[l] * d2by[m]) + ml3 * (dbx[l] * dby[m]);
+            const float c1 = ml4 * w10 + ml5 * w01;
+            const float c2 = ml2 * w00;
+            const f32x2 C0 = pack2(c0, c0), C1 = pack2(c1, c1), C2 = pack2(c2, c2);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) LP[j] = ffma2(C0, A0[j], ffma2(C1, A1[j], ffma2(C2, A2[j], LP[j])));
+        }
+        if (c < 15) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) cur[k] = nxt[k];
+        }
+    }
+
+    const int o0 = chunk * E;
+    if (o0 >= p.n_orb) return;
+    const bool vec = p.vec_out != 0;
+    float v[E], gx[E], gy[E], gz[E], lp[E];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        unpack2(V[j], v[2 * j], v[2 * j + 1]);
+        unpack2(GX[j], gx[2 * j], gx[2 * j + 1]);
+        unpack2(GY[j], gy[2 * j], gy[2 * j + 1]);
+        unpack2(GZ[j], gz[2 * j], gz[2 * j + 1]);
+        unpack2(LP[j], lp[2 * j], lp[2 * j + 1]);
+    }
+    if (p.val) store_run<float, E>(static_cast<float*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
+    if (p.grad) {
+        float* g = static_cast<float*>(p.grad) + ip * 3 * p.n_orb + o0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float m0 = (float)p.mg[3 * a], m1 = (float)p.mg[3 * a + 1], m2 = (float)p.mg[3 * a + 2];
+            float cg[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) cg[e] = fmaf(m0, gx[e], fmaf(m1, gy[e], m2 * gz[e]));
+            store_run<float, E>(g + (size_t)a * p.n_orb, cg, o0, p.n_orb, vec);
+        }
+    }
+    if (p.lap) store_run<float, E>(static_cast<float*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
+}
+
+// float and bfloat16 tables take the packed path, double tables the scalar one
+template <typename T, bool LAPTAB>
+__device__ __forceinline__ void warp_task(const EvalArgs& p, long long w0, int lane)
+{
+    if constexpr (sizeof(T) == 8) bspline_warp_task<T, LAPTAB>(p, w0, lane);
+    else bspline_warp_task_x2<T, LAPTAB>(p, w0, lane);
+}
+
+#ifndef QMCSPL_EVAL_MINBLOCKS
+#define QMCSPL_EVAL_MINBLOCKS 2
+#endif
+
+template <typename T, bool LAPTAB>
+__global__ void __launch_bounds__(kEvalThreads, QMCSPL_EVAL_MINBLOCKS) bspline_vgl_kernel(const EvalArgs p)
 {
     const int lane = threadIdx.x & 31;
     const int gpw = 32 >> p.lanes_log2;
@@ -163,7 +330,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) bspline_vgl_kernel(const Eval
     const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
     const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
     for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw)
-        bspline_warp_task<T, LAPTAB>(p, w0, lane);
+        warp_task<T, LAPTAB>(p, w0, lane);
 }
 
 // Several cells in one launch: warp task w belongs to the cell c with
@@ -176,7 +343,7 @@ struct BatchArgs {
 static_assert(sizeof(BatchArgs) <= 32000, "batched kernel parameters exceed the 32 KB limit");
 
 template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(kEvalThreads, 2) bspline_vgl_batched_kernel(const __grid_constant__ BatchArgs b)
+__global__ void __launch_bounds__(kEvalThreads, QMCSPL_EVAL_MINBLOCKS) bspline_vgl_batched_kernel(const __grid_constant__ BatchArgs b)
 {
     const int lane = threadIdx.x & 31;
     const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
@@ -187,7 +354,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) bspline_vgl_batched_kernel(co
         while (w >= b.start[c + 1]) ++c;          // tasks only move forward
         const EvalArgs& p = b.cell[c];
         const long long local = w - b.start[c];
-        bspline_warp_task<T, LAPTAB>(p, local * (32 >> p.lanes_log2), lane);
+        warp_task<T, LAPTAB>(p, local * (32 >> p.lanes_log2), lane);
     }
 }
 

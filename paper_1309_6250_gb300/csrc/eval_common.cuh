@@ -125,6 +125,54 @@ __device__ __forceinline__ void bspline_weights(A t, A* w, A* dw, A* d2w)
     }
 }
 
+// ---- packed FP32 pairs (fma.rn.f32x2 on sm_100+): two orbitals per instruction ----
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ f32x2 pack2u(unsigned lo, unsigned hi)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float& lo, float& hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// d = a * b + c, lane-wise on the two halves, round to nearest
+__device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// A 16-byte chunk as float pairs: 2 pairs (4 floats) or 4 pairs (8 bfloat16 widened).
+template <typename T> struct Pairs;
+template <> struct Pairs<float> {
+    static constexpr int N = 2;
+    __device__ __forceinline__ static void get(const uint4& r, f32x2* c)
+    {
+        c[0] = pack2u(r.x, r.y);
+        c[1] = pack2u(r.z, r.w);
+    }
+};
+template <> struct Pairs<__nv_bfloat16> {
+    static constexpr int N = 4;
+    __device__ __forceinline__ static void get(const uint4& r, f32x2* c)
+    {
+        c[0] = pack2u(r.x << 16, r.x & 0xffff0000u);
+        c[1] = pack2u(r.y << 16, r.y & 0xffff0000u);
+        c[2] = pack2u(r.z << 16, r.z & 0xffff0000u);
+        c[3] = pack2u(r.w << 16, r.w & 0xffff0000u);
+    }
+};
+
 // Streaming stores of E consecutive outputs (vector when allowed).
 template <typename A, int E>
 __device__ __forceinline__ void store_run(A* dst, const A* v, int o0, int n_orb, bool vec)
