@@ -218,6 +218,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_batched(args, dev, stream):
+    """The uneven three-cell workload (Al-like 32-atom: 48 orbitals, 64^3, 512 x 96 e;
+    Si-like 64-atom: 128 orbitals, 80^3, 1024 x 256 e; MgO-like 16-atom: 32 orbitals,
+    64^3, 2048 x 64 e; FP32 smoothing + Laplacian tables) through one batched launch
+    per step, each cell with the autotuner's tile shape and order."""
+    import torch
+    from paper_1309_6250_gb300 import autotune
+    from paper_1309_6250_gb300.api import eval_batched
+    cache = os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) \
+        else None
+    cells, shapes, evals = [], {}, 0
+    for key in ("c4-al32", "c4-si64", "c4-mgo16"):
+        w = inputs.make_workload(key)
+        spl, t = autotune.tuned_splines(w.lattice, w.cell.grid, w.miller, w.coef, w.pos, storage="f32",
+                                        separate_lap=True, device=dev, cache_path=cache, repeats=5)
+        shapes[w.cell.name] = {"lanes": t["lanes"], "order": t["order"]}
+        p = torch.from_numpy(w.pos).to(dev)
+        cells.append((spl, p, spl.alloc_outputs(p.shape[0])))
+        evals += w.pos.shape[0] * w.coef.shape[0]
+    spls = [c[0] for c in cells]
+    pos = [c[1] for c in cells]
+    outs = [c[2] for c in cells]
+    step = lambda: eval_batched(spls, pos, outs=outs)
+    ms = time_steps(step, max(10, args.steps // 2), 3, torch, stream)
+    t = sum(ms) / len(ms)
+    for s in spls:
+        s.sync()
+        s.close()
+    return {"workload": "c4 uneven batch (Al-32 48 orb 64^3, Si-64 128 orb 80^3, MgO-16 32 orb 64^3)",
+            "value": evals / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "evals_per_step": evals,
+            "storage": "f32", "shapes": shapes}
+
+
 def run_ours(args):
     import torch
     rank, ws, dist = dist_setup()
@@ -325,6 +358,13 @@ def run_ours(args):
                 "algorithmic_gbs": vb * evals_per_step / vk / 1e9,
                 "frac_of_hbm": vb * evals_per_step / vk / 1e9 / hbm}
 
+    batched = None
+    if not args.no_variants and rank == 0:
+        del outs
+        spl.close()
+        torch.cuda.empty_cache()
+        batched = bench_batched(args, dev, stream)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w, args.storage, True)
@@ -353,6 +393,7 @@ def run_ours(args):
         "clocks": clocks,
         "setup_s": setup_s,
         "variants": variants,
+        "batched": batched,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -71,6 +71,10 @@ typedef struct {
                           memory x2) and return its value as the Laplacian; 0 = the
                           Laplacian of the spline itself.  Ignored by Lagrange (always
                           its own Laplacian table) and pp (always the spline's own). */
+    int lanes;         /* threads that share one position in the evaluation kernels,
+                          each owning one 16-byte chunk of every stored row: 0 = choose
+                          automatically, else 1, 2, 4, 8, 16 or 32.  Rows are padded to
+                          a multiple of lanes x 16 bytes. */
 } qmcspl_opts;
 
 typedef struct {
@@ -189,9 +193,12 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
  *   pos, val, grad, lap   host arrays of n_cells DEVICE pointers (layouts as above;
  *             val/grad/lap entries may be NULL)
  *   n_pos     host array of n_cells position counts
- * Asynchronous on `stream`.  The cell descriptors travel as kernel parameters, so the
- * call allocates nothing and copies nothing (it can be captured in a CUDA graph);
- * positions are evaluated in input order.
+ * Asynchronous on `stream`.  The cell descriptors travel as kernel parameters (no
+ * copy).  Each handle's evaluation order applies (qmcspl_set_order): cells evaluated
+ * in cell order are sorted first by three small kernels per cell, in the handle's
+ * scratch memory, which a call allocates only when a cell has more positions than
+ * any earlier call on that handle.  After one call at the largest sizes the call
+ * allocates nothing and can be captured in a CUDA graph.
  */
 #define QMCSPL_MAX_BATCH 48
 int qmcspl_eval_batched(int n_cells, const qmcspl_t* h, const double* const* pos,

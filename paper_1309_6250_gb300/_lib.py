@@ -48,7 +48,8 @@ class QmcsplError(RuntimeError):
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [("method", ctypes.c_int), ("storage", ctypes.c_int), ("separate_lap", ctypes.c_int)]
+    _fields_ = [("method", ctypes.c_int), ("storage", ctypes.c_int), ("separate_lap", ctypes.c_int),
+                ("lanes", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

@@ -34,7 +34,7 @@ class OrbitalSplines:
     def __init__(self, lattice, dims: Sequence[int], miller, coef, method: str = "smooth",
                  storage: str = "f32", separate_lap: bool = True,
                  device: Optional[torch.device] = None,
-                 stream: Optional[torch.cuda.Stream] = None):
+                 stream: Optional[torch.cuda.Stream] = None, lanes: int = 0):
         self.lib = _lib.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(3, 3))
@@ -48,7 +48,7 @@ class OrbitalSplines:
         if mil.shape[0] != n_pw:
             raise ValueError("miller and coef disagree on the number of planewaves")
         craw = np.ascontiguousarray(c.view(np.float64).reshape(n_orb, n_pw, 2))
-        opts = _lib.Opts(_lib.METHODS[method], _lib.STORAGE[storage], int(bool(separate_lap)))
+        opts = _lib.Opts(_lib.METHODS[method], _lib.STORAGE[storage], int(bool(separate_lap)), int(lanes))
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = _stream_handle(stream)

@@ -251,7 +251,19 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
     h->elem_bytes = h->storage == QMCSPL_F64 ? 8 : (h->storage == QMCSPL_F32 ? 4 : 2);
     const int E = (int)(16 / h->elem_bytes);
     const int n_chunks = (n_orb + E - 1) / E;
-    choose_lanes(n_chunks, h->lanes_log2, h->tiles);
+    if (opts->lanes == 0) {
+        choose_lanes(n_chunks, h->lanes_log2, h->tiles);
+    } else {
+        int lg = -1;
+        for (int k = 0; k <= 5; ++k)
+            if (opts->lanes == (1 << k)) lg = k;
+        if (lg < 0) {
+            delete h;
+            return set_error(QMCSPL_ERR_ARG, "lanes must be 0, 1, 2, 4, 8, 16 or 32");
+        }
+        h->lanes_log2 = lg;
+        h->tiles = (n_chunks + (1 << lg) - 1) >> lg;
+    }
     h->n_orb_p = h->tiles * (1 << h->lanes_log2) * E;
     switch (h->method) {
     case QMCSPL_LAGRANGE: h->n_tables = 5; h->entries = 1; h->rows_z = dims[2] + 3; break;
@@ -463,8 +475,17 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* po
         if (n_pos[c] > 0 && !pos[c]) return set_error(QMCSPL_ERR_ARG, "pos is NULL");
     }
     DeviceGuard dg(hs[0]->device);
-    return launch_batched(n_cells, reinterpret_cast<const Handle* const*>(hs), pos, n_pos, val, grad,
-                          lap, static_cast<cudaStream_t>(stream));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int* perms[QMCSPL_MAX_BATCH];
+    for (int c = 0; c < n_cells; ++c) {
+        perms[c] = nullptr;
+        if (n_pos[c] > 0 && use_cell_order(hs[c], n_pos[c])) {
+            const int rc = cell_order(hs[c], pos[c], n_pos[c], &perms[c], st);
+            if (rc != QMCSPL_OK) return rc;
+        }
+    }
+    return launch_batched(n_cells, reinterpret_cast<const Handle* const*>(hs), pos, perms, n_pos, val,
+                          grad, lap, st);
 }
 
 int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream)

@@ -419,8 +419,9 @@ int launch_bspline_vgl(const Handle* h, const double* pos, const int* perm, long
     }
 }
 
-int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const long long* n_pos,
-                   void* const* val, void* const* grad, void* const* lap, cudaStream_t st)
+int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const int* const* perm,
+                   const long long* n_pos, void* const* val, void* const* grad, void* const* lap,
+                   cudaStream_t st)
 {
     thread_local BatchArgs B;   // about 16 KB: kept off the stack, one per calling thread
     B.n_cells = n_cells;
@@ -429,7 +430,7 @@ int launch_batched(int n_cells, const Handle* const* hs, const double* const* po
         EvalArgs& a = B.cell[c];
         fill_eval_args(hs[c], &a);
         a.pos = pos[c];
-        a.perm = nullptr;
+        a.perm = perm[c];
         a.n_pos = n_pos[c];
         set_outputs(hs[c], a, val[c], grad[c], lap[c]);
         const int gpw = 32 >> a.lanes_log2;

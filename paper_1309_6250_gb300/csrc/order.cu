@@ -12,6 +12,9 @@
 namespace qmcspl {
 namespace {
 
+#ifndef QMCSPL_BIN_EDGE
+#define QMCSPL_BIN_EDGE 4      // grid cells per bin edge (a bin is edge^3 cells)
+#endif
 constexpr int kMaxBins = 1 << 16;
 constexpr int kScanThreads = 1024;
 
@@ -96,7 +99,7 @@ __global__ void place_kernel(const int* bin, long long n, int* offset, int* perm
 BinGeometry bin_geometry(const Handle* h)
 {
     BinGeometry g;
-    g.edge = 4;
+    g.edge = QMCSPL_BIN_EDGE;
     for (;;) {
         long long nb = 1;
         for (int a = 0; a < 3; ++a) {

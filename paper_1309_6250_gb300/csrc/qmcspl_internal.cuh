@@ -137,8 +137,8 @@ int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
                             const void* gv, const void* gg, const void* gl, void* dcoef,
                             void* dcoef_lap, double* dpos, cudaStream_t stream);
 int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos,
-                   const long long* n_pos, void* const* val, void* const* grad,
-                   void* const* lap, cudaStream_t stream);
+                   const int* const* perm, const long long* n_pos, void* const* val,
+                   void* const* grad, void* const* lap, cudaStream_t stream);
 
 // ---- cell ordering (order.cu) ----
 // Bin geometry of a handle: bins of `edge` grid cells per axis, nb[3] bins per axis.

@@ -43,7 +43,7 @@ def _create(lib, lattice, dims, miller, coef, method=0, storage=0, sep=0):
     dm = np.ascontiguousarray(dims, dtype=np.int32)
     mil = np.ascontiguousarray(miller, dtype=np.int32)
     c = np.ascontiguousarray(np.asarray(coef, dtype=np.complex128)).view(np.float64)
-    opts = _lib.Opts(method, storage, sep)
+    opts = _lib.Opts(method, storage, sep, 0)
     rc = lib.qmcspl_create(ctypes.byref(h), lat.ctypes.data, dm.ctypes.data, mil.shape[0],
                            mil.ctypes.data, c.shape[0], c.ctypes.data, ctypes.byref(opts), None)
     return rc, h
