@@ -39,11 +39,11 @@ KERNEL_SOURCES = ["paper_1309_6250_gb300/csrc/eval_bspline.cu", "paper_1309_6250
 
 
 def out_bytes(storage):
-    return 8 if storage == "f64" else 4
+    return 8 if storage in ("f64", "df64") else 4
 
 
 def elem_bytes(storage):
-    return {"f64": 8, "f32": 4, "bf16": 2}[storage]
+    return {"f64": 8, "df64": 8, "f32": 4, "bf16": 2}[storage]
 
 
 def algorithmic_bytes_per_eval(storage, n_tables, n_orb):
@@ -332,7 +332,8 @@ def run_ours(args):
 
     variants = {}
     if not args.no_variants and rank == 0:
-        for st, order in (("f32", "input"), ("bf16", "auto"), ("f64", "auto"), ("bf16", "input")):
+        for st, order in (("f32", "input"), ("bf16", "auto"), ("f64", "auto"), ("df64", "auto"),
+                          ("bf16", "input")):
             if st == args.storage and order == args.order:
                 continue
             del outs
@@ -376,7 +377,7 @@ def run_ours(args):
         "config": {"workload": w.cell.name, "method": "smoothing B-spline + separate Laplacian table",
                    "n_orb": n_orb, "grid": list(w.cell.grid), "walkers": w.cell.n_walkers,
                    "electrons": w.cell.n_elec, "positions": n_pos, "storage": args.storage,
-                   "accumulate": "f64" if args.storage == "f64" else "f32",
+                   "accumulate": {"f64": "f64", "df64": "double-float (f32 pairs)"}.get(args.storage, "f32"),
                    "order": "cell" if cell_order else "input",
                    "table_bytes": info["table_bytes"], "lanes": info["lanes"], "tiles": info["tiles"],
                    "l2": "table and outputs larger than L2 (no flush needed)",
@@ -409,7 +410,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3")
-    ap.add_argument("--storage", default="f32", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--storage", default="f32", choices=["f64", "df64", "f32", "bf16"])
     ap.add_argument("--order", default="auto", choices=["auto", "input", "cell"])
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--no-variants", action="store_true")

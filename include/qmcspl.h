@@ -27,7 +27,8 @@
  *   - Lattice: row-major 3x3 with the lattice vectors a_1, a_2, a_3 as COLUMNS (bohr),
  *     so r = a s for crystal coordinates s.  Positions may lie anywhere; they are
  *     wrapped into the cell (Eq. reducedcoordinate).
- *   - Output dtype: double for QMCSPL_F64 tables, float for QMCSPL_F32 / QMCSPL_BF16.
+ *   - Output dtype: double for QMCSPL_F64 and QMCSPL_DF64 tables, float for QMCSPL_F32 /
+ *     QMCSPL_BF16.
  *     Output layouts (P positions, O orbitals, row-major):
  *         val [P][O],   grad [P][3][O] (Cartesian x, y, z),   lap [P][O].
  */
@@ -61,7 +62,12 @@ enum qmcspl_method {
 enum qmcspl_storage {
     QMCSPL_F64 = 0,                /* tables and arithmetic in double */
     QMCSPL_F32 = 1,                /* float tables, float accumulation */
-    QMCSPL_BF16 = 2                /* bfloat16 tables, float accumulation */
+    QMCSPL_BF16 = 2,               /* bfloat16 tables, float accumulation */
+    QMCSPL_DF64 = 3                /* double-float: each coefficient a pair of floats whose
+                                      sum carries ~48 significant bits, arithmetic in
+                                      error-free FP32 pair operations, double outputs; the
+                                      accuracy class of FP64 at FP32-pipe speed.  B-spline
+                                      evaluation only (no backward, Lagrange or pp). */
 };
 
 typedef struct {

@@ -29,6 +29,7 @@ PPSPLINE = 3
 F64 = 0
 F32 = 1
 BF16 = 2
+DF64 = 3
 
 MAX_BATCH = 48
 NOALLOC_MAX_POS = 1 << 20
@@ -38,7 +39,7 @@ ORDER_INPUT = 1
 ORDER_CELL = 2
 
 METHODS = {"smooth": BSPLINE_SMOOTH, "interp": BSPLINE_INTERP, "lagrange": LAGRANGE, "pp": PPSPLINE}
-STORAGE = {"f64": F64, "f32": F32, "bf16": BF16}
+STORAGE = {"f64": F64, "f32": F32, "bf16": BF16, "df64": DF64}
 
 
 class QmcsplError(RuntimeError):

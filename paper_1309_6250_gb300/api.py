@@ -61,7 +61,7 @@ class OrbitalSplines:
         self.n_orb = n_orb
         self.dims = tuple(int(x) for x in dm)
         self.lattice = lat
-        self.out_dtype = torch.float64 if storage == "f64" else torch.float32
+        self.out_dtype = torch.float64 if storage in ("f64", "df64") else torch.float32
 
     # -- lifecycle ---------------------------------------------------------
     def close(self) -> None:

@@ -23,7 +23,7 @@ import numpy as np
 
 _lock = threading.Lock()
 
-ELEM_BYTES = {"f64": 8, "f32": 4, "bf16": 2}
+ELEM_BYTES = {"f64": 8, "df64": 8, "f32": 4, "bf16": 2}
 
 
 def default_cache_path() -> str:

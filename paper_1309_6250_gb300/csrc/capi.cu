@@ -209,8 +209,11 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
             return set_error(QMCSPL_ERR_ARG, "grid dims must be in [4, 512]");
     if (opts->method < QMCSPL_BSPLINE_SMOOTH || opts->method > QMCSPL_PPSPLINE)
         return set_error(QMCSPL_ERR_ARG, "unknown method");
-    if (opts->storage < QMCSPL_F64 || opts->storage > QMCSPL_BF16)
+    if (opts->storage < QMCSPL_F64 || opts->storage > QMCSPL_DF64)
         return set_error(QMCSPL_ERR_ARG, "unknown storage type");
+    if (opts->storage == QMCSPL_DF64 && opts->method != QMCSPL_BSPLINE_SMOOTH &&
+        opts->method != QMCSPL_BSPLINE_INTERP)
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "double-float tables are for the B-spline methods");
     for (int i = 0; i < 9; ++i)
         if (!std::isfinite(lattice[i])) return set_error(QMCSPL_ERR_ARG, "non-finite lattice");
     double ainv[9];
@@ -248,7 +251,7 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
     h->ml[4] = 2.0 * M[2];
     h->ml[5] = 2.0 * M[5];
 
-    h->elem_bytes = h->storage == QMCSPL_F64 ? 8 : (h->storage == QMCSPL_F32 ? 4 : 2);
+    h->elem_bytes = (h->storage == QMCSPL_F64 || h->storage == QMCSPL_DF64) ? 8 : (h->storage == QMCSPL_F32 ? 4 : 2);
     const int E = (int)(16 / h->elem_bytes);
     const int n_chunks = (n_orb + E - 1) / E;
     if (opts->lanes == 0) {
@@ -370,7 +373,7 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
     if (!pos_host) return set_error(QMCSPL_ERR_ARG, "pos_host is NULL");
     DeviceGuard dg(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t ob = (h->storage == QMCSPL_F64) ? 8 : 4;
+    const size_t ob = (h->storage == QMCSPL_F64 || h->storage == QMCSPL_DF64) ? 8 : 4;
     const size_t row = (size_t)h->n_orb * ob;          // bytes of one output row
     const long long cap = 1LL << 16;                   // positions per chunk
     cudaError_t e;
@@ -444,6 +447,8 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
     if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
     if (h->method != QMCSPL_BSPLINE_SMOOTH && h->method != QMCSPL_BSPLINE_INTERP)
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is implemented for B-spline handles");
+    if (h->storage == QMCSPL_DF64)
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for double-float tables");
     if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
     if (dcoef_lap && !(h->separate_lap && dcoef))
         return set_error(QMCSPL_ERR_ARG, "dcoef_lap needs a separate-Laplacian handle and dcoef");
@@ -517,7 +522,14 @@ int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream)
                 double* dst = out_host + (((size_t)x * N2 + y) * N3 + z) * h->n_orb;
                 for (int o = 0; o < h->n_orb; ++o) {
                     double v;
-                    if (h->storage == QMCSPL_F64) {
+                    if (h->storage == QMCSPL_DF64) {
+                        // 16-byte chunk of two orbitals: hi0, hi1, lo0, lo1
+                        const size_t fl = (src + (o & ~1)) * 2 + (o & 1);
+                        float hi, lo;
+                        std::memcpy(&hi, raw + fl * 4, 4);
+                        std::memcpy(&lo, raw + (fl + 2) * 4, 4);
+                        v = (double)hi + (double)lo;
+                    } else if (h->storage == QMCSPL_F64) {
                         std::memcpy(&v, raw + (src + o) * 8, 8);
                     } else if (h->storage == QMCSPL_F32) {
                         float f;

@@ -249,6 +249,31 @@ __global__ void layout_kernel(const LayoutArgs a)
         from_double<T>(v);
 }
 
+// Double-float tables: orbital o of a row lives in the 16-byte chunk o/2 as
+// (hi0, hi1, lo0, lo1), hi = v rounded to float, lo = (v - hi) rounded to float.
+__global__ void layout_df_kernel(const LayoutArgs a)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)a.N1 * a.N2 * a.rows_z * a.oc;
+    if (idx >= total) return;
+    const int o = (int)(idx % a.oc);
+    long long r = idx / a.oc;
+    const int zz = (int)(r % a.rows_z);
+    r /= a.rows_z;
+    const int y = (int)(r % a.N2);
+    const int x = (int)(r / a.N2);
+    int z = zz - a.zshift;
+    z = z < 0 ? z + a.N3 : (z >= a.N3 ? z - a.N3 : z);
+    const double v = a.F[(((long long)x * a.N2 + y) * a.N3 + z) * a.oc + o].x;
+    const float hi = __double2float_rn(v);
+    const float lo = __double2float_rn(v - (double)hi);
+    const long long row = (((long long)x * a.N2 + y) * a.rows_z + zz) * a.o_p;   // in 8-byte elements
+    const int oo = a.o0 + o;
+    float* f = static_cast<float*>(a.tab) + 2 * (row + (oo & ~1)) + (oo & 1);
+    f[0] = hi;
+    f[2] = lo;
+}
+
 int launch_layout(const Handle* h, const double2* F, int tab, int entry, int o0, int oc,
                   cudaStream_t st)
 {
@@ -268,6 +293,7 @@ int launch_layout(const Handle* h, const double2* F, int tab, int entry, int o0,
     const long long total = (long long)a.N1 * a.N2 * a.rows_z * a.oc;
     const unsigned blocks = (unsigned)((total + 255) / 256);
     switch (h->storage) {
+    case QMCSPL_DF64: layout_df_kernel<<<blocks, 256, 0, st>>>(a); break;
     case QMCSPL_F64: layout_kernel<double><<<blocks, 256, 0, st>>>(a); break;
     case QMCSPL_F32: layout_kernel<float><<<blocks, 256, 0, st>>>(a); break;
     default: layout_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(a); break;

@@ -23,6 +23,8 @@
 //
 // The kernel is a gather bounded by memory bandwidth: no tensor cores, since each
 // position gathers its own stencil.
+#include <type_traits>
+
 #include "eval_common.cuh"
 
 namespace qmcspl {
@@ -309,11 +311,144 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
     if (p.lap) store_run<float, E>(static_cast<float*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
 }
 
+// Double-float tables (16-byte chunk = two orbitals as hi0, hi1, lo0, lo1): the same
+// stencil walk with every product and sum carried as a double-float pair on the FP32
+// pipe (see df_fma2), results converted to double at the store.
+struct DF64Tag {
+    float v[2];   // 8 bytes per stored coefficient
+};
+
+template <bool LAPTAB>
+__device__ __forceinline__ void bspline_warp_task_df(const EvalArgs& p, long long w0, int lane)
+{
+    const int L = 1 << p.lanes_log2;
+    const int sub = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const long long total = p.n_pos * p.tiles;
+    const size_t rowb = (size_t)p.row_stride * 8;
+    const size_t colb = (size_t)p.col_stride * 8;
+
+    const long long gid = w0 + (lane >> p.lanes_log2);
+    const bool active = gid < total;
+    const long long q = active ? gid / p.tiles : 0;
+    const int tile = active ? (int)(gid - q * p.tiles) : 0;
+    const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
+    const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+    int ix, iy, iz;
+    double tx, ty, tz;
+    bool ok;
+    reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    if (!active) return;
+    if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+
+    dfloat bx[4], dbx[4], d2bx[4], by[4], dby[4], d2by[4], bz[4], dbz[4], d2bz[4];
+    bspline_weights_df(tx, bx, dbx, LAPTAB ? nullptr : d2bx);
+    bspline_weights_df(ty, by, dby, LAPTAB ? nullptr : d2by);
+    bspline_weights_df(tz, bz, dbz, LAPTAB ? nullptr : d2bz);
+    dfloat ml[6];
+    if (!LAPTAB)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ml[k] = df_from_double(p.ml[k]);
+    int xs[4], ys[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        xs[j] = wrap1(ix + j - 1, p.nx);
+        ys[j] = wrap1(iy + j - 1, p.ny);
+    }
+    const int chunk = tile * L + sub;
+    const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
+    const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb
+                            : nullptr;
+    // accumulators (h, l) for value, reduced gradient, Laplacian-table value
+    f32x2 Vh = 0, Vl = 0, Xh = 0, Xl = 0, Yh = 0, Yl = 0, Zh = 0, Zl = 0, Lh = 0, Ll = 0;
+#pragma unroll 1
+    for (int c = 0; c < 16; ++c) {
+        const int l = c >> 2, m = c & 3;
+        const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb;
+        uint4 raw[4], rawl[4];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) raw[n] = ldg16(t0 + col + n * rowb);
+        if (LAPTAB) {
+#pragma unroll
+            for (int n = 0; n < 4; ++n) rawl[n] = ldg16(t1 + col + n * rowb);
+        }
+        f32x2 A0h = 0, A0l = 0, A1h = 0, A1l = 0, A2h = 0, A2l = 0, ALh = 0, ALl = 0;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const f32x2 Bh = pack2u(raw[n].x, raw[n].y), Bl = pack2u(raw[n].z, raw[n].w);
+            const f32x2 wh = pack2(bz[n].h, bz[n].h), wl = pack2(bz[n].l, bz[n].l), nwh = pack2(-bz[n].h, -bz[n].h);
+            df_fma2(A0h, A0l, wh, wl, nwh, Bh, Bl);
+            const f32x2 dh = pack2(dbz[n].h, dbz[n].h), dl = pack2(dbz[n].l, dbz[n].l),
+                        ndh = pack2(-dbz[n].h, -dbz[n].h);
+            df_fma2(A1h, A1l, dh, dl, ndh, Bh, Bl);
+            if (!LAPTAB) {
+                const f32x2 eh = pack2(d2bz[n].h, d2bz[n].h), el = pack2(d2bz[n].l, d2bz[n].l),
+                            neh = pack2(-d2bz[n].h, -d2bz[n].h);
+                df_fma2(A2h, A2l, eh, el, neh, Bh, Bl);
+            }
+            if (LAPTAB) {
+                const f32x2 Ch = pack2u(rawl[n].x, rawl[n].y), Cl = pack2u(rawl[n].z, rawl[n].w);
+                df_fma2(ALh, ALl, wh, wl, nwh, Ch, Cl);
+            }
+        }
+        const dfloat w00 = df_mul(bx[l], by[m]), w10 = df_mul(dbx[l], by[m]), w01 = df_mul(bx[l], dby[m]);
+        const f32x2 h00 = pack2(w00.h, w00.h), l00 = pack2(w00.l, w00.l), n00 = pack2(-w00.h, -w00.h);
+        const f32x2 h10 = pack2(w10.h, w10.h), l10 = pack2(w10.l, w10.l), n10 = pack2(-w10.h, -w10.h);
+        const f32x2 h01 = pack2(w01.h, w01.h), l01 = pack2(w01.l, w01.l), n01 = pack2(-w01.h, -w01.h);
+        df_fma2(Vh, Vl, h00, l00, n00, A0h, A0l);
+        df_fma2(Xh, Xl, h10, l10, n10, A0h, A0l);
+        df_fma2(Yh, Yl, h01, l01, n01, A0h, A0l);
+        df_fma2(Zh, Zl, h00, l00, n00, A1h, A1l);
+        if (LAPTAB) {
+            df_fma2(Lh, Ll, h00, l00, n00, ALh, ALl);
+        } else {
+            // metric folded into per-column weights: lap += c0 A0 + c1 A1 + c2 A2
+            const dfloat c0 = df_add(df_add(df_mul(ml[0], df_mul(d2bx[l], by[m])), df_mul(ml[1], df_mul(bx[l], d2by[m]))),
+                                     df_mul(ml[3], df_mul(dbx[l], dby[m])));
+            const dfloat c1 = df_add(df_mul(ml[4], w10), df_mul(ml[5], w01));
+            const dfloat c2 = df_mul(ml[2], w00);
+            df_fma2(Lh, Ll, pack2(c0.h, c0.h), pack2(c0.l, c0.l), pack2(-c0.h, -c0.h), A0h, A0l);
+            df_fma2(Lh, Ll, pack2(c1.h, c1.h), pack2(c1.l, c1.l), pack2(-c1.h, -c1.h), A1h, A1l);
+            df_fma2(Lh, Ll, pack2(c2.h, c2.h), pack2(c2.l, c2.l), pack2(-c2.h, -c2.h), A2h, A2l);
+        }
+    }
+
+    constexpr int E = 2;
+    const int o0 = chunk * E;
+    if (o0 >= p.n_orb) return;
+    const bool vec = p.vec_out != 0;
+    float a0, a1, b0, b1;
+    double v[E], gx[E], gy[E], gz[E], lp[E];
+    unpack2(Vh, a0, a1); unpack2(Vl, b0, b1);
+    v[0] = df_to_double(a0, b0); v[1] = df_to_double(a1, b1);
+    unpack2(Xh, a0, a1); unpack2(Xl, b0, b1);
+    gx[0] = df_to_double(a0, b0); gx[1] = df_to_double(a1, b1);
+    unpack2(Yh, a0, a1); unpack2(Yl, b0, b1);
+    gy[0] = df_to_double(a0, b0); gy[1] = df_to_double(a1, b1);
+    unpack2(Zh, a0, a1); unpack2(Zl, b0, b1);
+    gz[0] = df_to_double(a0, b0); gz[1] = df_to_double(a1, b1);
+    unpack2(Lh, a0, a1); unpack2(Ll, b0, b1);
+    lp[0] = df_to_double(a0, b0); lp[1] = df_to_double(a1, b1);
+    if (p.val) store_run<double, E>(static_cast<double*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
+    if (p.grad) {
+        double* g = static_cast<double*>(p.grad) + ip * 3 * p.n_orb + o0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double cg[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) cg[e] = p.mg[3 * a] * gx[e] + p.mg[3 * a + 1] * gy[e] + p.mg[3 * a + 2] * gz[e];
+            store_run<double, E>(g + (size_t)a * p.n_orb, cg, o0, p.n_orb, vec);
+        }
+    }
+    if (p.lap) store_run<double, E>(static_cast<double*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
+}
+
 // float and bfloat16 tables take the packed path, double tables the scalar one
 template <typename T, bool LAPTAB>
 __device__ __forceinline__ void warp_task(const EvalArgs& p, long long w0, int lane)
 {
-    if constexpr (sizeof(T) == 8) bspline_warp_task<T, LAPTAB>(p, w0, lane);
+    if constexpr (std::is_same<T, DF64Tag>::value) bspline_warp_task_df<LAPTAB>(p, w0, lane);
+    else if constexpr (sizeof(T) == 8) bspline_warp_task<T, LAPTAB>(p, w0, lane);
     else bspline_warp_task_x2<T, LAPTAB>(p, w0, lane);
 }
 
@@ -394,7 +529,7 @@ void set_outputs(const Handle* h, EvalArgs& a, void* val, void* grad, void* lap)
     a.val = val;
     a.grad = grad;
     a.lap = lap;
-    const size_t ob = (h->storage == QMCSPL_F64) ? 8 : 4;
+    const size_t ob = (h->storage == QMCSPL_F64 || h->storage == QMCSPL_DF64) ? 8 : 4;
     const uintptr_t al = (uintptr_t)val | (uintptr_t)grad | (uintptr_t)lap;
     a.vec_out = ((h->n_orb * ob) % 16 == 0) && (al % 16 == 0);
 }
@@ -414,6 +549,7 @@ int launch_bspline_vgl(const Handle* h, const double* pos, const int* perm, long
     switch (h->storage) {
     case QMCSPL_F64: return lt ? launch_typed<double, true>(a, st) : launch_typed<double, false>(a, st);
     case QMCSPL_F32: return lt ? launch_typed<float, true>(a, st) : launch_typed<float, false>(a, st);
+    case QMCSPL_DF64: return lt ? launch_typed<DF64Tag, true>(a, st) : launch_typed<DF64Tag, false>(a, st);
     default:
         return lt ? launch_typed<__nv_bfloat16, true>(a, st) : launch_typed<__nv_bfloat16, false>(a, st);
     }
@@ -439,6 +575,8 @@ int launch_batched(int n_cells, const Handle* const* hs, const double* const* po
     if (B.start[n_cells] == 0) return QMCSPL_OK;
     const bool lt = hs[0]->separate_lap != 0;
     switch (hs[0]->storage) {
+    case QMCSPL_DF64:
+        return lt ? launch_batched_typed<DF64Tag, true>(B, st) : launch_batched_typed<DF64Tag, false>(B, st);
     case QMCSPL_F64: return lt ? launch_batched_typed<double, true>(B, st) : launch_batched_typed<double, false>(B, st);
     case QMCSPL_F32: return lt ? launch_batched_typed<float, true>(B, st) : launch_batched_typed<float, false>(B, st);
     default:

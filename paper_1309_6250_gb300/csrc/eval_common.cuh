@@ -173,6 +173,112 @@ template <> struct Pairs<__nv_bfloat16> {
     }
 };
 
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// ---- double-float numbers x = h + l (two floats, ~48 significant bits) ----
+// Error-free transformations (Dekker / Knuth): the rounded product or sum plus its
+// exact rounding error.  Only the _rn intrinsics and explicit fma are used, so the
+// compiler cannot contract or reassociate them.
+struct dfloat {
+    float h, l;
+};
+
+__device__ __forceinline__ dfloat df_from_double(double x)
+{
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+__device__ __forceinline__ double df_to_double(float h, float l) { return (double)h + (double)l; }
+// renormalise so that |l| <= ulp(h)/2 (requires |h| >= |l|)
+__device__ __forceinline__ dfloat df_norm(float h, float l)
+{
+    const float s = __fadd_rn(h, l);
+    return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return df_norm(p, e);
+}
+__device__ __forceinline__ dfloat df_mulf(dfloat a, float c)
+{
+    const float p = __fmul_rn(a.h, c);
+    float e = fmaf(a.h, c, -p);
+    e = fmaf(a.l, c, e);
+    return df_norm(p, e);
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    return df_norm(s, e);
+}
+__device__ __forceinline__ dfloat df_neg(dfloat a) { return {-a.h, -a.l}; }
+
+// Cubic B-spline weights (Eq. b-splinebasis) and first derivatives in double-float
+// from a reduced coordinate given in double.
+__device__ __forceinline__ void bspline_weights_df(double td, dfloat* w, dfloat* dw, dfloat* d2w)
+{
+    const dfloat t = df_from_double(td);
+    const dfloat s = df_add({1.0f, 0.0f}, df_neg(t));
+    const dfloat t2 = df_mul(t, t), t3 = df_mul(t2, t);
+    const dfloat s2 = df_mul(s, s), s3 = df_mul(s2, s);
+    w[0] = {0.25f * s3.h, 0.25f * s3.l};                                        // (1-t)^3/4
+    w[1] = df_add(df_add(df_mulf(t3, 0.75f), df_mulf(t2, -1.5f)), {1.0f, 0.0f});
+    w[2] = df_add(df_add(df_mulf(t3, -0.75f), df_mulf(t2, 0.75f)), df_add(df_mulf(t, 0.75f), {0.25f, 0.0f}));
+    w[3] = {0.25f * t3.h, 0.25f * t3.l};
+    dw[0] = df_mulf(s2, -0.75f);
+    dw[1] = df_add(df_mulf(t2, 2.25f), df_mulf(t, -3.0f));
+    dw[2] = df_add(df_add(df_mulf(t2, -2.25f), df_mulf(t, 1.5f)), {0.75f, 0.0f});
+    dw[3] = df_mulf(t2, 0.75f);
+    if (d2w) {
+        d2w[0] = df_mulf(s, 1.5f);
+        d2w[1] = df_add(df_mulf(t, 4.5f), {-3.0f, 0.0f});
+        d2w[2] = df_add(df_mulf(t, -4.5f), {1.5f, 0.0f});
+        d2w[3] = df_mulf(t, 1.5f);
+    }
+}
+
+// Packed double-float accumulation of two orbitals: (Ah, Al) += w * (Bh, Bl), where w is
+// a double-float scalar given as the packed pairs wh = (w.h, w.h), wl = (w.l, w.l) and
+// nwh = -wh.  The rounded products enter Ah through an exact two-sum; the product's
+// rounding error, the cross terms and the sum's rounding error go to Al.
+__device__ __forceinline__ void df_fma2(f32x2& Ah, f32x2& Al, f32x2 wh, f32x2 wl, f32x2 nwh, f32x2 Bh, f32x2 Bl)
+{
+    const f32x2 nP = mul2(nwh, Bh);                 // -(rounded w.h * Bh)
+    f32x2 E = ffma2(wh, Bh, nP);                     // its exact rounding error
+    E = ffma2(wh, Bl, E);
+    E = ffma2(wl, Bh, E);
+    const f32x2 S = sub2(Ah, nP);                    // Ah + P
+    const f32x2 BB = sub2(S, Ah);
+    const f32x2 T1 = sub2(Ah, sub2(S, BB));
+    const f32x2 T2 = add2(nP, BB);                   // -(P - BB)
+    Al = add2(Al, add2(sub2(T1, T2), E));
+    Ah = S;
+}
+
 // Streaming stores of E consecutive outputs (vector when allowed).
 template <typename A, int E>
 __device__ __forceinline__ void store_run(A* dst, const A* v, int o0, int n_orb, bool vec)

@@ -3,7 +3,7 @@ import numpy as np
 
 import oracle
 
-TOL = {"f64": 1e-12, "f32": 2e-6, "bf16": 1e-2}
+TOL = {"f64": 1e-12, "df64": 1e-12, "f32": 2e-6, "bf16": 1e-2}
 NONORTHO = np.array([[5.0, 1.0, 0.5],
                      [0.0, 6.0, 0.3],
                      [0.0, 0.0, 7.0]])
@@ -21,7 +21,7 @@ def splines(*a, **k):
 
 def rounded(a, storage):
     import torch
-    if a is None or storage == "f64":
+    if a is None or storage in ("f64", "df64"):
         return a
     if storage == "f32":
         return a.astype(np.float32).astype(np.float64)

@@ -11,7 +11,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "df64", "f32", "bf16"])
 def test_every_lane_count_gives_identical_results(storage):
     dims = (10, 11, 12)
     lat, mil, coef = inputs.random_cell(910, dims, 37, 6.0, 5.0, NONORTHO)

@@ -148,3 +148,11 @@ def test_backward_rejects_variants():
     with pytest.raises(_lib.QmcsplError) as ei:
         spl.backward(pos)
     assert ei.value.code == _lib.ERR_UNSUPPORTED
+    spl = splines(lat, dims, mil, coef, method="smooth", storage="df64")
+    with pytest.raises(_lib.QmcsplError) as ei:
+        spl.backward(pos)
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
+    for method in ("lagrange", "pp"):
+        with pytest.raises(_lib.QmcsplError) as ei:
+            splines(lat, dims, mil, coef, method=method, storage="df64")
+        assert ei.value.code == _lib.ERR_UNSUPPORTED

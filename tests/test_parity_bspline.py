@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32": 2e-6, "bf16": 1e-2}
+TOL = {"f64": 1e-12, "df64": 1e-12, "f32": 2e-6, "bf16": 1e-2}
 NONORTHO = np.array([[5.0, 1.0, 0.5],
                      [0.0, 6.0, 0.3],
                      [0.0, 0.0, 7.0]])
@@ -36,7 +36,7 @@ def oracle_tables(method, lattice, miller, coef, dims, sep):
 
 
 def rounded(a, storage):
-    if storage == "f64":
+    if storage in ("f64", "df64"):
         return a
     if storage == "f32":
         return a.astype(np.float32).astype(np.float64)
@@ -58,7 +58,7 @@ def assert_parity(got, ref, tol, what=""):
 
 
 @pytest.mark.parametrize("method", ["smooth", "interp"])
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "df64", "f32", "bf16"])
 def test_tables_match_oracle(method, storage):
     """Construction (frequency grid, symbol division, inverse DFT, layout) against the
     oracle's tables: FP64 to 1e-13, lower precisions to their rounding."""
@@ -68,7 +68,7 @@ def test_tables_match_oracle(method, storage):
     beta, blap = oracle_tables(method, lat, mil, coef, dims, True)
     for idx, ref in ((0, beta), (1, blap)):
         got = spl.get_table(idx)
-        tol = {"f64": 1e-13, "f32": 1e-7, "bf16": 8e-3}[storage]
+        tol = {"f64": 1e-13, "df64": 1e-13, "f32": 1e-7, "bf16": 8e-3}[storage]
         assert oracle.relative_error(got, ref) <= tol
     info = spl.info()
     assert info["n_tables"] == 2 and info["table_bytes"] > 0
@@ -93,7 +93,7 @@ def test_c1_fp64_interpolating_16cube():
 
 
 @pytest.mark.parametrize("method", ["smooth", "interp"])
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "df64", "f32", "bf16"])
 @pytest.mark.parametrize("sep", [False, True])
 @pytest.mark.parametrize("n_orb", [1, 3, 13, 40])
 def test_eval_ragged_nonorthogonal(method, storage, sep, n_orb):
@@ -143,7 +143,7 @@ def test_edge_cases_empty_single_nan_and_far():
     assert oracle.relative_error(v[ok], ref[0]) < 1e-12
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "df64", "f32", "bf16"])
 def test_c2_si8_smoothing_with_laplacian_table(storage):
     """Si-like 8-atom cell, 16 orbitals on 48^3, smoothing B-spline + separate Laplacian
     table; 4096 of the 1024 x 32 positions.  Also reports the kinetic-energy effect of
@@ -157,7 +157,7 @@ def test_c2_si8_smoothing_with_laplacian_table(storage):
     assert_parity(got, ref, TOL[storage], "c2/" + storage)
     dT = np.abs(oracle.kinetic_energy(got[0], got[2]) - oracle.kinetic_energy(ref[0], ref[2]))
     print("c2 %s: max |dT_n| = %.3e mHa" % (storage, 1e3 * dT.max()))
-    assert 1e3 * dT.max() < {"f64": 1e-9, "f32": 1e-2, "bf16": 50.0}[storage]
+    assert 1e3 * dT.max() < {"f64": 1e-9, "df64": 1e-9, "f32": 1e-2, "bf16": 50.0}[storage]
 
 
 def test_host_buffers_match_device_path():
@@ -195,7 +195,7 @@ def test_c3_mgo64_full_size_sampled():
     sample = np.unique(np.concatenate([np.arange(0, P, 8191), np.arange(P - 5, P)]))
     ref = _oracle_c3_sample(w, sample)
     pos = torch.from_numpy(w.pos).to(dev())
-    for storage in ("f32", "bf16"):
+    for storage in ("f32", "bf16", "df64"):
         spl = splines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage=storage,
                       separate_lap=True)
         v, g, l = spl.eval_vgl(pos)

@@ -12,6 +12,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("method,storage,sep", [("smooth", "f32", True), ("smooth", "bf16", True),
+                                                ("smooth", "df64", True), ("interp", "df64", False),
                                                 ("interp", "f64", False), ("lagrange", "f32", True),
                                                 ("pp", "f32", False)])
 def test_cell_order_is_bit_identical(method, storage, sep):
