@@ -161,6 +161,7 @@ void free_handle(Handle* h)
     if (h->ord_bin) cudaFree(h->ord_bin);
     if (h->ord_perm) cudaFree(h->ord_perm);
     if (h->ord_count) cudaFree(h->ord_count);
+    if (h->ord_rec) cudaFree(h->ord_rec);
     if (h->prof_ev) {
         for (int i = 0; i < 3 * kProfCalls; ++i) cudaEventDestroy(h->prof_ev[i]);
         delete[] h->prof_ev;
@@ -335,16 +336,18 @@ static int eval_dispatch(Handle* h, const double* pos, long long n_pos, void* va
     if (h->prof_on && h->prof_n < kProfCalls) ev = h->prof_ev + 3 * h->prof_n++;
     if (ev) cudaEventRecord(ev[0], st);
     const int* perm = nullptr;
-    if (use_cell_order(h, n_pos)) {
-        const int rc = cell_order(h, pos, n_pos, &perm, st);
+    const void* rec = nullptr;
+    const bool sort = use_cell_order(h, n_pos);
+    if (sort || n_pos >= kRecordMinPositions) {
+        const int rc = prepare_positions(h, pos, n_pos, sort, &rec, &perm, st);
         if (rc != QMCSPL_OK) return rc;
     }
     if (ev) cudaEventRecord(ev[1], st);
     int rc;
     switch (h->method) {
-    case QMCSPL_LAGRANGE: rc = launch_lagrange_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
-    case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
-    default: rc = launch_bspline_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
+    case QMCSPL_LAGRANGE: rc = launch_lagrange_vgl(h, pos, rec, perm, n_pos, val, grad, lap, st); break;
+    case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, rec, perm, n_pos, val, grad, lap, st); break;
+    default: rc = launch_bspline_vgl(h, pos, rec, perm, n_pos, val, grad, lap, st); break;
     }
     if (ev) cudaEventRecord(ev[2], st);
     return rc;
@@ -482,14 +485,17 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* po
     DeviceGuard dg(hs[0]->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int* perms[QMCSPL_MAX_BATCH];
+    const void* recs[QMCSPL_MAX_BATCH];
     for (int c = 0; c < n_cells; ++c) {
         perms[c] = nullptr;
-        if (n_pos[c] > 0 && use_cell_order(hs[c], n_pos[c])) {
-            const int rc = cell_order(hs[c], pos[c], n_pos[c], &perms[c], st);
+        recs[c] = nullptr;
+        const bool sort = n_pos[c] > 0 && use_cell_order(hs[c], n_pos[c]);
+        if (sort || n_pos[c] >= kRecordMinPositions) {
+            const int rc = prepare_positions(hs[c], pos[c], n_pos[c], sort, &recs[c], &perms[c], st);
             if (rc != QMCSPL_OK) return rc;
         }
     }
-    return launch_batched(n_cells, reinterpret_cast<const Handle* const*>(hs), pos, perms, n_pos, val,
+    return launch_batched(n_cells, reinterpret_cast<const Handle* const*>(hs), pos, recs, perms, n_pos, val,
                           grad, lap, st);
 }
 

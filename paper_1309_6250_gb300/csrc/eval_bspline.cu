@@ -48,11 +48,10 @@ __device__ __forceinline__ void bspline_warp_task(const EvalArgs& p, long long w
     const long long q = active ? gid / p.tiles : 0;
     const int tile = active ? (int)(gid - q * p.tiles) : 0;
     const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
-    const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
     int ix, iy, iz;
     double tx, ty, tz;
     bool ok;
-    reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    coords_double(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
     if (!active) return;
     if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
 
@@ -177,18 +176,17 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
     const long long q = active ? gid / p.tiles : 0;
     const int tile = active ? (int)(gid - q * p.tiles) : 0;
     const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
-    const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
     int ix, iy, iz;
-    double tx, ty, tz;
+    float tx, ty, tz;
     bool ok;
-    reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    coords_float(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
     if (!active) return;
     if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
 
     float bx[4], dbx[4], d2bx[4], by[4], dby[4], d2by[4], bz[4], dbz[4], d2bz[4];
-    bspline_weights<float>((float)tx, bx, dbx, LAPTAB ? nullptr : d2bx);
-    bspline_weights<float>((float)ty, by, dby, LAPTAB ? nullptr : d2by);
-    bspline_weights<float>((float)tz, bz, dbz, LAPTAB ? nullptr : d2bz);
+    bspline_weights<float>(tx, bx, dbx, LAPTAB ? nullptr : d2bx);
+    bspline_weights<float>(ty, by, dby, LAPTAB ? nullptr : d2by);
+    bspline_weights<float>(tz, bz, dbz, LAPTAB ? nullptr : d2bz);
     f32x2 bz2[4], dbz2[4], d2bz2[4];
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
@@ -333,11 +331,24 @@ __device__ __forceinline__ void bspline_warp_task_df(const EvalArgs& p, long lon
     const long long q = active ? gid / p.tiles : 0;
     const int tile = active ? (int)(gid - q * p.tiles) : 0;
     const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
-    const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
     int ix, iy, iz;
-    double tx, ty, tz;
+    dfloat tx, ty, tz;
     bool ok;
-    reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    if (p.rec) {   // kind-3 record: cell and double-float t, no FP64 work here
+        const float4* qr = static_cast<const float4*>(p.rec) + 2 * ip;
+        const float4 a = __ldg(qr), b = __ldg(qr + 1);
+        unpack_cell(__float_as_int(a.x), ix, iy, iz, ok);
+        tx = {a.y, a.z};
+        ty = {a.w, b.x};
+        tz = {b.y, b.z};
+    } else {
+        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+        double dx, dy, dz;
+        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, dx, dy, dz, ok);
+        tx = df_from_double(dx);
+        ty = df_from_double(dy);
+        tz = df_from_double(dz);
+    }
     if (!active) return;
     if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
 
@@ -536,12 +547,13 @@ void set_outputs(const Handle* h, EvalArgs& a, void* val, void* grad, void* lap)
 
 }  // namespace
 
-int launch_bspline_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos, void* val,
-                       void* grad, void* lap, cudaStream_t st)
+int launch_bspline_vgl(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
+                       void* val, void* grad, void* lap, cudaStream_t st)
 {
     EvalArgs a;
     fill_eval_args(h, &a);
     a.pos = pos;
+    a.rec = rec;
     a.perm = perm;
     a.n_pos = n_pos;
     set_outputs(h, a, val, grad, lap);
@@ -555,9 +567,9 @@ int launch_bspline_vgl(const Handle* h, const double* pos, const int* perm, long
     }
 }
 
-int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const int* const* perm,
-                   const long long* n_pos, void* const* val, void* const* grad, void* const* lap,
-                   cudaStream_t st)
+int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const void* const* rec,
+                   const int* const* perm, const long long* n_pos, void* const* val, void* const* grad,
+                   void* const* lap, cudaStream_t st)
 {
     thread_local BatchArgs B;   // about 16 KB: kept off the stack, one per calling thread
     B.n_cells = n_cells;
@@ -566,6 +578,7 @@ int launch_batched(int n_cells, const Handle* const* hs, const double* const* po
         EvalArgs& a = B.cell[c];
         fill_eval_args(hs[c], &a);
         a.pos = pos[c];
+        a.rec = rec[c];
         a.perm = perm[c];
         a.n_pos = n_pos[c];
         set_outputs(hs[c], a, val[c], grad[c], lap[c]);

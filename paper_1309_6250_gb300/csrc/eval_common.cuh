@@ -60,6 +60,13 @@ __device__ __forceinline__ void reduce_axis(double s, int N, int& i, double& t, 
     if (!ok) t = __longlong_as_double(0x7ff8000000000000LL);
 }
 
+// Crystal coordinate s_i = sum_j ainv[i][j] r_j with a fixed rounding sequence, so that
+// every kernel that reduces a position gets the same bits.
+__device__ __forceinline__ double crystal(double a0, double a1, double a2, const double* r)
+{
+    return __fma_rn(a0, r[0], __fma_rn(a1, r[1], __dmul_rn(a2, r[2])));
+}
+
 // Reduced coordinates of position r for every lane of a group of L lanes.  With
 // L >= 4 lane j < 3 of the group reduces axis j and the results are broadcast by
 // shuffles; smaller groups reduce all three axes in every lane.  Must be called by
@@ -78,7 +85,7 @@ __device__ __forceinline__ void reduced_coordinates(const EvalArgs& p, const dou
         int i;
         double t;
         bool o;
-        reduce_axis(a0 * r[0] + a1 * r[1] + a2 * r[2], N, i, t, o);
+        reduce_axis(crystal(a0, a1, a2, r), N, i, t, o);
         ix = __shfl_sync(kFullMask, i, gbase);
         iy = __shfl_sync(kFullMask, i, gbase + 1);
         iz = __shfl_sync(kFullMask, i, gbase + 2);
@@ -90,10 +97,58 @@ __device__ __forceinline__ void reduced_coordinates(const EvalArgs& p, const dou
               __shfl_sync(kFullMask, okb, gbase + 2)) != 0;
     } else {
         bool o0, o1, o2;
-        reduce_axis(p.ainv[0] * r[0] + p.ainv[1] * r[1] + p.ainv[2] * r[2], p.nx, ix, tx, o0);
-        reduce_axis(p.ainv[3] * r[0] + p.ainv[4] * r[1] + p.ainv[5] * r[2], p.ny, iy, ty, o1);
-        reduce_axis(p.ainv[6] * r[0] + p.ainv[7] * r[1] + p.ainv[8] * r[2], p.nz, iz, tz, o2);
+        reduce_axis(crystal(p.ainv[0], p.ainv[1], p.ainv[2], r), p.nx, ix, tx, o0);
+        reduce_axis(crystal(p.ainv[3], p.ainv[4], p.ainv[5], r), p.ny, iy, ty, o1);
+        reduce_axis(crystal(p.ainv[6], p.ainv[7], p.ainv[8], r), p.nz, iz, tz, o2);
         ok = o0 && o1 && o2;
+    }
+}
+
+// ---- coordinates of position ip: from its record when the launch has records,
+// otherwise reduced here (all 32 lanes must call these) ----
+__device__ __forceinline__ void unpack_cell(int c, int& ix, int& iy, int& iz, bool& ok)
+{
+    ok = c >= 0;
+    const int cc = ok ? c : 0;
+    ix = cc & 1023;
+    iy = (cc >> 10) & 1023;
+    iz = (cc >> 20) & 1023;
+}
+
+__device__ __forceinline__ void coords_float(const EvalArgs& p, long long ip, int L, int sub, int gbase,
+                                             int& ix, int& iy, int& iz, float& tx, float& ty, float& tz,
+                                             bool& ok)
+{
+    if (p.rec) {
+        const float4 q = __ldg(static_cast<const float4*>(p.rec) + ip);
+        unpack_cell(__float_as_int(q.x), ix, iy, iz, ok);
+        tx = q.y;
+        ty = q.z;
+        tz = q.w;
+    } else {
+        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+        double dx, dy, dz;
+        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, dx, dy, dz, ok);
+        tx = (float)dx;
+        ty = (float)dy;
+        tz = (float)dz;
+    }
+}
+
+__device__ __forceinline__ void coords_double(const EvalArgs& p, long long ip, int L, int sub, int gbase,
+                                              int& ix, int& iy, int& iz, double& tx, double& ty, double& tz,
+                                              bool& ok)
+{
+    if (p.rec) {
+        const double2* q = static_cast<const double2*>(p.rec) + 2 * ip;
+        const double2 a = __ldg(q), b = __ldg(q + 1);
+        tx = a.x;
+        ty = a.y;
+        tz = b.x;
+        unpack_cell(__double2loint(b.y), ix, iy, iz, ok);
+    } else {
+        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
     }
 }
 
@@ -239,9 +294,8 @@ __device__ __forceinline__ dfloat df_neg(dfloat a) { return {-a.h, -a.l}; }
 
 // Cubic B-spline weights (Eq. b-splinebasis) and first derivatives in double-float
 // from a reduced coordinate given in double.
-__device__ __forceinline__ void bspline_weights_df(double td, dfloat* w, dfloat* dw, dfloat* d2w)
+__device__ __forceinline__ void bspline_weights_df(dfloat t, dfloat* w, dfloat* dw, dfloat* d2w)
 {
-    const dfloat t = df_from_double(td);
     const dfloat s = df_add({1.0f, 0.0f}, df_neg(t));
     const dfloat t2 = df_mul(t, t), t3 = df_mul(t2, t);
     const dfloat s2 = df_mul(s, s), s3 = df_mul(s2, s);

@@ -51,11 +51,11 @@ __global__ void __launch_bounds__(kEvalThreads, 2) lagrange_vgl_kernel(const Eva
         const long long q = active ? gid / p.tiles : 0;
         const int tile = active ? (int)(gid - q * p.tiles) : 0;
         const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
-        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
         int ix, iy, iz;
-        double tx, ty, tz;
+        A tx, ty, tz;
         bool ok;
-        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+        if constexpr (sizeof(A) == 8) coords_double(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+        else coords_float(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
         if (!active) continue;
         if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
         A lx[4], ly[4], lz[4];
@@ -152,11 +152,11 @@ __global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs 
         const long long q = active ? gid / p.tiles : 0;
         const int tile = active ? (int)(gid - q * p.tiles) : 0;
         const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
-        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
         int ix, iy, iz;
-        double tx, ty, tz;
+        A tx, ty, tz;
         bool ok;
-        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+        if constexpr (sizeof(A) == 8) coords_double(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+        else coords_float(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
         if (!active) continue;
         if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
         A wx[2][2], dwx[2][2], d2wx[2][2], wy[2][2], dwy[2][2], d2wy[2][2], wz[2][2], dwz[2][2], d2wz[2][2];
@@ -254,12 +254,13 @@ int launch_variant(void (*kernel)(EvalArgs), const EvalArgs& a, cudaStream_t st,
 template <typename T> struct LagrangeK {};
 template <typename T> struct PPK {};
 
-EvalArgs make_args(const Handle* h, const double* pos, const int* perm, long long n_pos, void* val,
-                   void* grad, void* lap)
+EvalArgs make_args(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
+                   void* val, void* grad, void* lap)
 {
     EvalArgs a;
     fill_eval_args(h, &a);
     a.pos = pos;
+    a.rec = rec;
     a.perm = perm;
     a.n_pos = n_pos;
     a.val = val;
@@ -273,10 +274,10 @@ EvalArgs make_args(const Handle* h, const double* pos, const int* perm, long lon
 
 }  // namespace
 
-int launch_lagrange_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos, void* val,
-                        void* grad, void* lap, cudaStream_t st)
+int launch_lagrange_vgl(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
+                        void* val, void* grad, void* lap, cudaStream_t st)
 {
-    const EvalArgs a = make_args(h, pos, perm, n_pos, val, grad, lap);
+    const EvalArgs a = make_args(h, pos, rec, perm, n_pos, val, grad, lap);
     switch (h->storage) {
     case QMCSPL_F64: return launch_variant<LagrangeK, double>(lagrange_vgl_kernel<double>, a, st, "lagrange_vgl_kernel");
     case QMCSPL_F32: return launch_variant<LagrangeK, float>(lagrange_vgl_kernel<float>, a, st, "lagrange_vgl_kernel");
@@ -286,10 +287,10 @@ int launch_lagrange_vgl(const Handle* h, const double* pos, const int* perm, lon
     }
 }
 
-int launch_pp_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos, void* val,
-                  void* grad, void* lap, cudaStream_t st)
+int launch_pp_vgl(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
+                  void* val, void* grad, void* lap, cudaStream_t st)
 {
-    const EvalArgs a = make_args(h, pos, perm, n_pos, val, grad, lap);
+    const EvalArgs a = make_args(h, pos, rec, perm, n_pos, val, grad, lap);
     switch (h->storage) {
     case QMCSPL_F64: return launch_variant<PPK, double>(pp_vgl_kernel<double>, a, st, "pp_vgl_kernel");
     case QMCSPL_F32: return launch_variant<PPK, float>(pp_vgl_kernel<float>, a, st, "pp_vgl_kernel");

@@ -71,9 +71,9 @@ extern "C" int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long 
         rc = build_cell_order(h, pos, n_pos, bin, count, perm, g, st);
         if (rc == QMCSPL_OK) {
             switch (h->method) {
-            case QMCSPL_LAGRANGE: rc = launch_lagrange_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
-            case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
-            default: rc = launch_bspline_vgl(h, pos, perm, n_pos, val, grad, lap, st); break;
+            case QMCSPL_LAGRANGE: rc = launch_lagrange_vgl(h, pos, nullptr, perm, n_pos, val, grad, lap, st); break;
+            case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, nullptr, perm, n_pos, val, grad, lap, st); break;
+            default: rc = launch_bspline_vgl(h, pos, nullptr, perm, n_pos, val, grad, lap, st); break;
             }
         }
     }

@@ -1,13 +1,20 @@
-// order.cu -- cell ordering of positions (not in the paper; a memory-locality step).
+// order.cu -- per-position preparation before evaluation (not in the paper).
 //
-// Each position's stencil touches 4 x 4 x 4 grid points; positions in nearby grid cells
-// share most of them.  Evaluating the positions grouped by cell lets those shared rows
-// be served by L1/L2 instead of HBM.  The order is a counting sort of the positions
-// into bins of `edge`^3 grid cells, bins swept x-major (z fastest), so the warps
-// resident on the GPU at any moment cover a compact slab of the cell.  Within a bin
-// the order is whatever the atomics give; it does not change any result, since each
-// position is computed the same way and written to its own output rows.
-#include "qmcspl_internal.cuh"
+// 1. Coordinate records.  Eq. (reducedcoordinate) needs FP64 (an FP32 product N*s
+//    loses ~N*6e-8 of t), and GB300 runs FP64 at a small fraction of its FP32 rate.
+//    Inside the evaluation kernels a group of lanes shares one position, so a warp-wide
+//    FP64 instruction there serves one position; here one thread reduces one position,
+//    so the same instruction serves 32.  The result (grid cell and t, see
+//    record_kind) is read by the evaluation kernels, which then do no FP64 work.
+// 2. Cell order.  Each position's stencil touches 4 x 4 x 4 grid points; positions in
+//    nearby grid cells share most of them.  Evaluating the positions grouped by cell
+//    lets those shared rows be served by L1/L2 instead of HBM.  The order is a counting
+//    sort of the positions into bins of edge^3 grid cells, bins swept x-major (z
+//    fastest), so the warps resident on the GPU at any moment cover a compact slab of
+//    the cell.  Within a bin the order is whatever the atomics give; it does not change
+//    any result, since each position is computed the same way and written to its own
+//    output rows.
+#include "eval_common.cuh"
 
 namespace qmcspl {
 namespace {
@@ -18,36 +25,57 @@ namespace {
 constexpr int kMaxBins = 1 << 16;
 constexpr int kScanThreads = 1024;
 
-__device__ __forceinline__ int cell_index(double s, int N)
-{
-    const double f = s - floor(s);
-    if (!isfinite(f)) return 0;
-    int k = (int)floor((double)N * f);
-    return k >= N ? k - N : (k < 0 ? 0 : k);
-}
-
-struct BinArgs {
+struct PrepArgs {
     const double* pos;
     long long n;
     double ainv[9];
     int dims[3];
     int edge;
     int nb[3];
-    int* bin;
-    int* count;
+    void* rec;                // records (kind 1, 2 or 3), may be null
+    int* bin;                 // per-position bin (with count)
+    int* count;               // bin counters, null: no binning
 };
 
-__global__ void bin_kernel(const BinArgs a)
+// Reduce position i; the same arithmetic as reduced_coordinates() in the kernels.
+__device__ __forceinline__ void reduce_position(const PrepArgs& a, long long i, int& ix, int& iy, int& iz,
+                                                double& tx, double& ty, double& tz, bool& ok)
+{
+    const double r[3] = {a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2]};
+    bool o0, o1, o2;
+    reduce_axis(crystal(a.ainv[0], a.ainv[1], a.ainv[2], r), a.dims[0], ix, tx, o0);
+    reduce_axis(crystal(a.ainv[3], a.ainv[4], a.ainv[5], r), a.dims[1], iy, ty, o1);
+    reduce_axis(crystal(a.ainv[6], a.ainv[7], a.ainv[8], r), a.dims[2], iz, tz, o2);
+    ok = o0 && o1 && o2;
+}
+
+template <int KIND>
+__global__ void prepare_kernel(const PrepArgs a)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
-    const double r0 = a.pos[3 * i], r1 = a.pos[3 * i + 1], r2 = a.pos[3 * i + 2];
-    const int ix = cell_index(a.ainv[0] * r0 + a.ainv[1] * r1 + a.ainv[2] * r2, a.dims[0]);
-    const int iy = cell_index(a.ainv[3] * r0 + a.ainv[4] * r1 + a.ainv[5] * r2, a.dims[1]);
-    const int iz = cell_index(a.ainv[6] * r0 + a.ainv[7] * r1 + a.ainv[8] * r2, a.dims[2]);
-    const int b = ((ix / a.edge) * a.nb[1] + iy / a.edge) * a.nb[2] + iz / a.edge;
-    a.bin[i] = b;
-    atomicAdd(a.count + b, 1);
+    int ix, iy, iz;
+    double tx, ty, tz;
+    bool ok;
+    reduce_position(a, i, ix, iy, iz, tx, ty, tz, ok);
+    const int cell = ok ? (ix | (iy << 10) | (iz << 20)) : -1;
+    if (KIND == 1) {
+        static_cast<float4*>(a.rec)[i] = make_float4(__int_as_float(cell), (float)tx, (float)ty, (float)tz);
+    } else if (KIND == 2) {
+        double2* q = static_cast<double2*>(a.rec) + 2 * i;
+        q[0] = make_double2(tx, ty);
+        q[1] = make_double2(tz, __hiloint2double(0, cell));
+    } else if (KIND == 3) {
+        const dfloat x = df_from_double(tx), y = df_from_double(ty), z = df_from_double(tz);
+        float4* q = static_cast<float4*>(a.rec) + 2 * i;
+        q[0] = make_float4(__int_as_float(cell), x.h, x.l, y.h);
+        q[1] = make_float4(y.l, z.h, z.l, 0.0f);
+    }
+    if (a.count) {
+        const int b = ((ix / a.edge) * a.nb[1] + iy / a.edge) * a.nb[2] + iz / a.edge;
+        a.bin[i] = b;
+        atomicAdd(a.count + b, 1);
+    }
 }
 
 // In-place exclusive scan of count[0 .. n) by one block; count[n] receives the total.
@@ -94,6 +122,36 @@ __global__ void place_kernel(const int* bin, long long n, int* offset, int* perm
     perm[slot] = (int)i;
 }
 
+PrepArgs prep_args(const Handle* h, const double* pos, long long n, void* rec, int* bin, int* count,
+                   const BinGeometry* g)
+{
+    PrepArgs a;
+    a.pos = pos;
+    a.n = n;
+    for (int i = 0; i < 9; ++i) a.ainv[i] = h->ainv[i];
+    for (int i = 0; i < 3; ++i) {
+        a.dims[i] = h->dims[i];
+        a.nb[i] = g ? g->nb[i] : 1;
+    }
+    a.edge = g ? g->edge : 1;
+    a.rec = rec;
+    a.bin = bin;
+    a.count = count;
+    return a;
+}
+
+int launch_prepare(const PrepArgs& a, int kind, cudaStream_t st)
+{
+    const unsigned blocks = (unsigned)((a.n + 255) / 256);
+    switch (kind) {
+    case 1: prepare_kernel<1><<<blocks, 256, 0, st>>>(a); break;
+    case 2: prepare_kernel<2><<<blocks, 256, 0, st>>>(a); break;
+    case 3: prepare_kernel<3><<<blocks, 256, 0, st>>>(a); break;
+    default: prepare_kernel<0><<<blocks, 256, 0, st>>>(a); break;
+    }
+    return cuda_error(cudaGetLastError(), "prepare_kernel launch");
+}
+
 }  // namespace
 
 BinGeometry bin_geometry(const Handle* h)
@@ -124,51 +182,85 @@ bool use_cell_order(const Handle* h, long long n_pos)
     }
 }
 
+int record_kind(const Handle* h)
+{
+    if (h->storage == QMCSPL_DF64) return 3;
+    if (h->storage == QMCSPL_F64) return 2;
+    return 1;
+}
+
+int build_records(const Handle* h, const double* pos, long long n_pos, void* rec, int* bin, int* count,
+                  const BinGeometry* g, cudaStream_t st)
+{
+    if (count) {
+        cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(g->n_bins + 1), st);
+        if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(bin counts)");
+    }
+    return launch_prepare(prep_args(h, pos, n_pos, rec, bin, count, g), rec ? record_kind(h) : 0, st);
+}
+
+// Cell order without records (the positions are reduced again by the evaluation kernel).
 int build_cell_order(const Handle* h, const double* pos, long long n_pos, int* bin, int* count,
                      int* perm, const BinGeometry& g, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(g.n_bins + 1), st);
-    if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(bin counts)");
-    BinArgs a;
-    a.pos = pos;
-    a.n = n_pos;
-    for (int i = 0; i < 9; ++i) a.ainv[i] = h->ainv[i];
-    for (int i = 0; i < 3; ++i) {
-        a.dims[i] = h->dims[i];
-        a.nb[i] = g.nb[i];
-    }
-    a.edge = g.edge;
-    a.bin = bin;
-    a.count = count;
+    int rc = build_records(h, pos, n_pos, nullptr, bin, count, &g, st);
+    if (rc != QMCSPL_OK) return rc;
     const unsigned blocks = (unsigned)((n_pos + 255) / 256);
-    bin_kernel<<<blocks, 256, 0, st>>>(a);
     scan_kernel<<<1, kScanThreads, 0, st>>>(count, g.n_bins);
     place_kernel<<<blocks, 256, 0, st>>>(bin, n_pos, count, perm);
     return cuda_error(cudaGetLastError(), "cell-order kernels");
 }
 
+static int grow_scratch(Handle* h, long long n_pos, int n_bins)
+{
+    if (n_pos <= h->ord_cap && n_bins + 1 <= h->ord_nbins) return QMCSPL_OK;
+    // cudaFree waits for kernels that may still read the old arrays
+    const long long cap = n_pos > h->ord_cap ? n_pos : h->ord_cap;
+    const int nb = n_bins + 1 > h->ord_nbins ? n_bins + 1 : h->ord_nbins;
+    if (h->ord_bin) cudaFree(h->ord_bin);
+    if (h->ord_perm) cudaFree(h->ord_perm);
+    if (h->ord_count) cudaFree(h->ord_count);
+    if (h->ord_rec) cudaFree(h->ord_rec);
+    h->ord_bin = h->ord_perm = h->ord_count = nullptr;
+    h->ord_rec = nullptr;
+    h->ord_cap = 0;
+    h->ord_nbins = 0;
+    cudaError_t e = cudaMalloc((void**)&h->ord_bin, sizeof(int) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->ord_perm, sizeof(int) * (size_t)cap);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->ord_count, sizeof(int) * (size_t)nb);
+    if (e == cudaSuccess) e = cudaMalloc(&h->ord_rec, 32 * (size_t)cap);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(position scratch)");
+    h->ord_cap = cap;
+    h->ord_nbins = nb;
+    return QMCSPL_OK;
+}
+
 int cell_order(Handle* h, const double* pos, long long n_pos, const int** perm, cudaStream_t st)
 {
     const BinGeometry g = bin_geometry(h);
-    if (n_pos > h->ord_cap || g.n_bins + 1 > h->ord_nbins) {
-        // grow the scratch; cudaFree waits for kernels that may still read the old arrays
-        if (h->ord_bin) cudaFree(h->ord_bin);
-        if (h->ord_perm) cudaFree(h->ord_perm);
-        if (h->ord_count) cudaFree(h->ord_count);
-        h->ord_bin = h->ord_perm = h->ord_count = nullptr;
-        h->ord_cap = 0;
-        h->ord_nbins = 0;
-        const long long cap = n_pos > h->ord_cap ? n_pos : h->ord_cap;
-        cudaError_t e = cudaMalloc((void**)&h->ord_bin, sizeof(int) * (size_t)cap);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&h->ord_perm, sizeof(int) * (size_t)cap);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&h->ord_count, sizeof(int) * (size_t)(g.n_bins + 1));
-        if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(cell-order scratch)");
-        h->ord_cap = cap;
-        h->ord_nbins = g.n_bins + 1;
-    }
-    const int rc = build_cell_order(h, pos, n_pos, h->ord_bin, h->ord_count, h->ord_perm, g, st);
+    int rc = grow_scratch(h, n_pos, g.n_bins);
+    if (rc != QMCSPL_OK) return rc;
+    rc = build_cell_order(h, pos, n_pos, h->ord_bin, h->ord_count, h->ord_perm, g, st);
     *perm = h->ord_perm;
     return rc;
+}
+
+int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, const void** rec,
+                      const int** perm, cudaStream_t st)
+{
+    const BinGeometry g = bin_geometry(h);
+    int rc = grow_scratch(h, n_pos, g.n_bins);
+    if (rc != QMCSPL_OK) return rc;
+    *rec = h->ord_rec;
+    *perm = nullptr;
+    if (!sort) return build_records(h, pos, n_pos, h->ord_rec, nullptr, nullptr, nullptr, st);
+    rc = build_records(h, pos, n_pos, h->ord_rec, h->ord_bin, h->ord_count, &g, st);
+    if (rc != QMCSPL_OK) return rc;
+    const unsigned blocks = (unsigned)((n_pos + 255) / 256);
+    scan_kernel<<<1, kScanThreads, 0, st>>>(h->ord_count, g.n_bins);
+    place_kernel<<<blocks, 256, 0, st>>>(h->ord_bin, n_pos, h->ord_count, h->ord_perm);
+    *perm = h->ord_perm;
+    return cuda_error(cudaGetLastError(), "cell-order kernels");
 }
 
 }  // namespace qmcspl

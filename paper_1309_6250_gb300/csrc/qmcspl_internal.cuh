@@ -29,6 +29,7 @@ using Handle = ::qmcspl_s;
 constexpr int kMaxDim = 512;          // grid points per axis accepted by qmcspl_create
 constexpr int kEvalThreads = 256;     // eval kernels: 8 warps per block
 constexpr int kProfCalls = 4096;      // calls qmcspl_profile can record
+constexpr long long kRecordMinPositions = 8192;   // from here on positions are reduced in a pass of their own
 
 enum BuildKind : int {
     kBuildSmoothValue = 0,   // c_G / gamma_G
@@ -56,6 +57,7 @@ struct EvalArgs {
     double mg[9];             // grad_cart[a] = sum_i mg[3a+i] grad_t[i]
     double ml[6];             // lap = ml0 Hxx + ml1 Hyy + ml2 Hzz + ml3 Hxy + ml4 Hxz + ml5 Hyz
     const double* pos;
+    const void* rec;          // per-position coordinate records (null: compute from pos), see order.cu
     const int* perm;          // evaluation order: position perm[i] is the i-th evaluated (null: input order)
     long long n_pos;
     void* val;
@@ -97,6 +99,7 @@ struct qmcspl_s {
     int* ord_bin = nullptr;
     int* ord_count = nullptr;
     int* ord_perm = nullptr;
+    void* ord_rec = nullptr;  // per-position coordinate records (32 bytes each)
     long long ord_cap = 0;    // positions the scratch can hold
     int ord_nbins = 0;        // bins the count array can hold
     int order_mode = 0;       // QMCSPL_ORDER_AUTO / INPUT / CELL
@@ -127,18 +130,18 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
                  cudaStream_t stream);
 
 // ---- evaluation launchers ----
-int launch_bspline_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos,
-                       void* val, void* grad, void* lap, cudaStream_t stream);
-int launch_lagrange_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos,
-                        void* val, void* grad, void* lap, cudaStream_t stream);
-int launch_pp_vgl(const Handle* h, const double* pos, const int* perm, long long n_pos, void* val,
-                  void* grad, void* lap, cudaStream_t stream);
+int launch_bspline_vgl(const Handle* h, const double* pos, const void* rec, const int* perm,
+                       long long n_pos, void* val, void* grad, void* lap, cudaStream_t stream);
+int launch_lagrange_vgl(const Handle* h, const double* pos, const void* rec, const int* perm,
+                        long long n_pos, void* val, void* grad, void* lap, cudaStream_t stream);
+int launch_pp_vgl(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
+                  void* val, void* grad, void* lap, cudaStream_t stream);
 int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
                             const void* gv, const void* gg, const void* gl, void* dcoef,
                             void* dcoef_lap, double* dpos, cudaStream_t stream);
 int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos,
-                   const int* const* perm, const long long* n_pos, void* const* val,
-                   void* const* grad, void* const* lap, cudaStream_t stream);
+                   const void* const* rec, const int* const* perm, const long long* n_pos,
+                   void* const* val, void* const* grad, void* const* lap, cudaStream_t stream);
 
 // ---- cell ordering (order.cu) ----
 // Bin geometry of a handle: bins of `edge` grid cells per axis, nb[3] bins per axis.
@@ -156,6 +159,20 @@ int build_cell_order(const Handle* h, const double* pos, long long n_pos, int* b
                      int* perm, const BinGeometry& g, cudaStream_t stream);
 // Same, using the handle's own scratch (grown on demand); returns the permutation.
 int cell_order(Handle* h, const double* pos, long long n_pos, const int** perm, cudaStream_t stream);
+
+// Per-position coordinate records: the grid cell and reduced coordinate t of every
+// position, computed once (FP64) so that the evaluation kernels need no FP64 work.
+//   kind 1 (float / bfloat16 tables): 16 bytes {int cell, float tx, ty, tz}
+//   kind 2 (double tables):           32 bytes {double tx, ty, tz; int cell, pad}
+//   kind 3 (double-float tables):     32 bytes {int cell, float txh, txl, tyh, tyl, tzh, tzl, pad}
+// cell = ix | iy << 10 | iz << 20, or -1 for a non-finite position.
+// With `count` non-null the kernel also bins the positions for the cell order.
+int record_kind(const Handle* h);
+int build_records(const Handle* h, const double* pos, long long n_pos, void* rec, int* bin, int* count,
+                  const BinGeometry* g, cudaStream_t stream);
+// Records (and, when sorting, the cell order) in the handle's scratch.
+int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, const void** rec,
+                      const int** perm, cudaStream_t stream);
 
 // fill the common part of EvalArgs from a handle
 void fill_eval_args(const Handle* h, EvalArgs* a);
