@@ -218,6 +218,73 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def l1_roofline(gather_bytes, launch_s, clocks):
+    """Every gathered stencil byte passes through the SM's L1/LSU data path, which moves
+    at most one 128-byte wavefront per clock per SM: 128 B x 152 SMs x the SM clock
+    (2070 MHz maximum, or the median clock sampled under load).  In cell order this path,
+    not HBM, bounds the gather."""
+    mhz = 2070.0
+    if clocks and clocks.get("sm_mhz"):
+        mhz = float(clocks["sm_mhz"])
+    peak = 128.0 * 152 * mhz * 1e6 / 1e9
+    achieved = gather_bytes / launch_s / 1e9
+    return {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_kind": "derived: 128 B/clk/SM x 152 SMs x %.0f MHz" % mhz}
+
+
+def _time_handle(spl, pos, torch, stream, steps):
+    out = spl.alloc_outputs(pos.shape[0])
+    step = lambda: spl.eval_vgl(pos, out=out)
+    ms = time_steps(step, steps, 3, torch, stream)
+    spl.sync()
+    return sum(ms) / len(ms)
+
+
+def bench_methods(args, dev, stream):
+    """The four bases of the paper on the Si-like 8-atom cell (16 orbitals, 48^3 grid,
+    1024 walkers x 32 electrons, same planewaves), FP32 tables: evaluations per second."""
+    import torch
+    from paper_1309_6250_gb300.api import OrbitalSplines
+    w = inputs.make_workload("c2")
+    pos = torch.from_numpy(w.pos).to(dev)
+    evals = w.pos.shape[0] * w.coef.shape[0]
+    out = {}
+    for name, method, sep in (("smooth_lap", "smooth", True), ("smooth", "smooth", False),
+                              ("interp_lap", "interp", True), ("interp", "interp", False),
+                              ("lagrange", "lagrange", True), ("pp", "pp", False)):
+        spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method=method, storage="f32",
+                             separate_lap=sep, device=dev)
+        t = _time_handle(spl, pos, torch, stream, max(10, args.steps // 4))
+        out[name] = {"value": evals / (t * 1e-3), "ms_per_step": t, "table_bytes": spl.info()["table_bytes"]}
+        spl.close()
+    return {"workload": "c2 Si-like 8-atom, 16 orbitals, 48^3, 32768 positions, f32 tables", "unit": UNIT,
+            "results": out}
+
+
+def bench_backward(args, dev, stream):
+    """Adjoint pass on the Si-like 64-atom cell (128 orbitals, 72^3, FP32 tables with the
+    Laplacian table, 4096 positions, N(0,1) upstream weights): coefficient scatter and
+    position gradient together, per second of positions x orbitals."""
+    import torch
+    from paper_1309_6250_gb300.api import OrbitalSplines
+    w = inputs.make_workload("c5")
+    spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32",
+                         separate_lap=True, device=dev)
+    n, o = w.pos.shape[0], w.coef.shape[0]
+    gv, gg, gl = (torch.from_numpy(x).to(device=dev, dtype=torch.float32)
+                  for x in inputs.upstream_weights(n, o, 3005))
+    pos = torch.from_numpy(w.pos).to(dev)
+    dc = torch.zeros(spl.coef_shape(), dtype=torch.float32, device=dev)
+    dcl = torch.zeros_like(dc)
+    step = lambda: spl.backward(pos, gv, gg, gl, dcoef=dc, dcoef_lap=dcl)
+    ms = time_steps(step, max(10, args.steps // 4), 3, torch, stream)
+    spl.sync()
+    t = sum(ms) / len(ms)
+    spl.close()
+    return {"workload": "c5 Si-like 64-atom, 128 orbitals, 72^3, 4096 positions, f32", "unit": UNIT,
+            "value": n * o / (t * 1e-3), "ms_per_step": t}
+
+
 def bench_batched(args, dev, stream):
     """The uneven three-cell workload (Al-like 32-atom: 48 orbitals, 64^3, 512 x 96 e;
     Si-like 64-atom: 128 orbitals, 80^3, 1024 x 256 e; MgO-like 16-atom: 32 orbitals,
@@ -359,12 +426,14 @@ def run_ours(args):
                 "algorithmic_gbs": vb * evals_per_step / vk / 1e9,
                 "frac_of_hbm": vb * evals_per_step / vk / 1e9 / hbm}
 
-    batched = None
+    batched = methods = backward = None
     if not args.no_variants and rank == 0:
         del outs
         spl.close()
         torch.cuda.empty_cache()
         batched = bench_batched(args, dev, stream)
+        methods = bench_methods(args, dev, stream)
+        backward = bench_backward(args, dev, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -387,6 +456,7 @@ def run_ours(args):
                      "kernel": "bspline_vgl_kernel", "bytes_per_eval": bpe,
                      "kernel_ms": launch_s * 1e3,
                      "order_kernels_ms": prof["order_ms"] / max(1, prof["launches"])},
+        "roofline_l1": l1_roofline(bpe * evals_per_step, launch_s, clocks),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pos_h.numel() * 8),
                 "d2h_bytes_per_step": int(d2h)},
@@ -395,6 +465,8 @@ def run_ours(args):
         "setup_s": setup_s,
         "variants": variants,
         "batched": batched,
+        "methods_si8_48": methods,
+        "backward_si64_72": backward,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

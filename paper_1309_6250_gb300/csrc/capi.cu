@@ -57,6 +57,16 @@ void fill_eval_args(const Handle* h, EvalArgs* a)
     std::memcpy(a->ainv, h->ainv, sizeof(a->ainv));
     std::memcpy(a->mg, h->mg, sizeof(a->mg));
     std::memcpy(a->ml, h->ml, sizeof(a->ml));
+    for (int i = 0; i < 9; ++i) {
+        a->mgf[i] = (float)h->mg[i];
+        a->mgh[i] = (float)h->mg[i];
+        a->mgl[i] = (float)(h->mg[i] - (double)a->mgh[i]);
+    }
+    for (int i = 0; i < 6; ++i) {
+        a->mlf[i] = (float)h->ml[i];
+        a->mlh[i] = (float)h->ml[i];
+        a->mll[i] = (float)(h->ml[i] - (double)a->mlh[i]);
+    }
     a->err = h->d_err;
 }
 

@@ -196,8 +196,8 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
     }
     float ml0 = 0.f, ml1 = 0.f, ml2 = 0.f, ml3 = 0.f, ml4 = 0.f, ml5 = 0.f;
     if (!LAPTAB) {
-        ml0 = (float)p.ml[0]; ml1 = (float)p.ml[1]; ml2 = (float)p.ml[2];
-        ml3 = (float)p.ml[3]; ml4 = (float)p.ml[4]; ml5 = (float)p.ml[5];
+        ml0 = p.mlf[0]; ml1 = p.mlf[1]; ml2 = p.mlf[2];
+        ml3 = p.mlf[3]; ml4 = p.mlf[4]; ml5 = p.mlf[5];
     }
     int xs[4], ys[4];
 #pragma unroll
@@ -299,7 +299,7 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
         float* g = static_cast<float*>(p.grad) + ip * 3 * p.n_orb + o0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float m0 = (float)p.mg[3 * a], m1 = (float)p.mg[3 * a + 1], m2 = (float)p.mg[3 * a + 2];
+            const float m0 = p.mgf[3 * a], m1 = p.mgf[3 * a + 1], m2 = p.mgf[3 * a + 2];
             float cg[E];
 #pragma unroll
             for (int e = 0; e < E; ++e) cg[e] = fmaf(m0, gx[e], fmaf(m1, gy[e], m2 * gz[e]));
@@ -359,7 +359,7 @@ __device__ __forceinline__ void bspline_warp_task_df(const EvalArgs& p, long lon
     dfloat ml[6];
     if (!LAPTAB)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) ml[k] = df_from_double(p.ml[k]);
+        for (int k = 0; k < 6; ++k) ml[k] = {p.mlh[k], p.mll[k]};
     int xs[4], ys[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -429,25 +429,27 @@ __device__ __forceinline__ void bspline_warp_task_df(const EvalArgs& p, long lon
     if (o0 >= p.n_orb) return;
     const bool vec = p.vec_out != 0;
     float a0, a1, b0, b1;
-    double v[E], gx[E], gy[E], gz[E], lp[E];
+    double v[E], lp[E];
     unpack2(Vh, a0, a1); unpack2(Vl, b0, b1);
     v[0] = df_to_double(a0, b0); v[1] = df_to_double(a1, b1);
-    unpack2(Xh, a0, a1); unpack2(Xl, b0, b1);
-    gx[0] = df_to_double(a0, b0); gx[1] = df_to_double(a1, b1);
-    unpack2(Yh, a0, a1); unpack2(Yl, b0, b1);
-    gy[0] = df_to_double(a0, b0); gy[1] = df_to_double(a1, b1);
-    unpack2(Zh, a0, a1); unpack2(Zl, b0, b1);
-    gz[0] = df_to_double(a0, b0); gz[1] = df_to_double(a1, b1);
     unpack2(Lh, a0, a1); unpack2(Ll, b0, b1);
     lp[0] = df_to_double(a0, b0); lp[1] = df_to_double(a1, b1);
     if (p.val) store_run<double, E>(static_cast<double*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
     if (p.grad) {
+        // chain rule in double-float: grad_a = sum_i mg[a][i] grad_t[i]
         double* g = static_cast<double*>(p.grad) + ip * 3 * p.n_orb + o0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
+            f32x2 Gh = 0, Gl = 0;
+            const float m0h = p.mgh[3 * a], m1h = p.mgh[3 * a + 1], m2h = p.mgh[3 * a + 2];
+            const float m0l = p.mgl[3 * a], m1l = p.mgl[3 * a + 1], m2l = p.mgl[3 * a + 2];
+            df_fma2(Gh, Gl, pack2(m0h, m0h), pack2(m0l, m0l), pack2(-m0h, -m0h), Xh, Xl);
+            df_fma2(Gh, Gl, pack2(m1h, m1h), pack2(m1l, m1l), pack2(-m1h, -m1h), Yh, Yl);
+            df_fma2(Gh, Gl, pack2(m2h, m2h), pack2(m2l, m2l), pack2(-m2h, -m2h), Zh, Zl);
             double cg[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) cg[e] = p.mg[3 * a] * gx[e] + p.mg[3 * a + 1] * gy[e] + p.mg[3 * a + 2] * gz[e];
+            unpack2(Gh, a0, a1); unpack2(Gl, b0, b1);
+            cg[0] = df_to_double(a0, b0);
+            cg[1] = df_to_double(a1, b1);
             store_run<double, E>(g + (size_t)a * p.n_orb, cg, o0, p.n_orb, vec);
         }
     }

@@ -163,8 +163,10 @@ __global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs 
         pp_weights<A>((A)tx, wx, dwx, d2wx);
         pp_weights<A>((A)ty, wy, dwy, d2wy);
         pp_weights<A>((A)tz, wz, dwz, d2wz);
-        const A ml0 = (A)p.ml[0], ml1 = (A)p.ml[1], ml2 = (A)p.ml[2];
-        const A ml3 = (A)p.ml[3], ml4 = (A)p.ml[4], ml5 = (A)p.ml[5];
+        const A* mlv = nullptr;
+        if constexpr (sizeof(A) == 8) mlv = p.ml; else mlv = p.mlf;
+        const A ml0 = mlv[0], ml1 = mlv[1], ml2 = mlv[2];
+        const A ml3 = mlv[3], ml4 = mlv[4], ml5 = mlv[5];
         const int chunk = tile * L + sub;
         const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
         A v[E], gx[E], gy[E], gz[E], lp[E];
@@ -222,7 +224,9 @@ __global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs 
             A* g = static_cast<A*>(p.grad) + ip * 3 * p.n_orb + o0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const A m0 = (A)p.mg[3 * a], m1 = (A)p.mg[3 * a + 1], m2 = (A)p.mg[3 * a + 2];
+                const A* mgv = nullptr;
+                if constexpr (sizeof(A) == 8) mgv = p.mg; else mgv = p.mgf;
+                const A m0 = mgv[3 * a], m1 = mgv[3 * a + 1], m2 = mgv[3 * a + 2];
                 A c[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) c[e] = fma(m0, gx[e], fma(m1, gy[e], m2 * gz[e]));

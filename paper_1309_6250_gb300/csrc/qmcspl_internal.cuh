@@ -56,6 +56,9 @@ struct EvalArgs {
     double ainv[9];           // s = a^-1 r (row-major)
     double mg[9];             // grad_cart[a] = sum_i mg[3a+i] grad_t[i]
     double ml[6];             // lap = ml0 Hxx + ml1 Hyy + ml2 Hzz + ml3 Hxy + ml4 Hxz + ml5 Hyz
+    float mgf[9], mlf[6];     // the same rounded to float (float kernels)
+    float mgh[9], mgl[9];     // double-float split of mg: mg = mgh + mgl
+    float mlh[6], mll[6];     // double-float split of ml
     const double* pos;
     const void* rec;          // per-position coordinate records (null: compute from pos), see order.cu
     const int* perm;          // evaluation order: position perm[i] is the i-th evaluated (null: input order)

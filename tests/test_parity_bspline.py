@@ -205,3 +205,21 @@ def test_c3_mgo64_full_size_sampled():
         errs = assert_parity(got, ref, TOL[storage], "c3/" + storage)
         print("c3 %s sampled errors: %s" % (storage, ["%.2e" % e for e in errs]))
         spl.close()
+
+
+def test_out_of_memory_is_reported_not_faulted():
+    """A table far larger than the device reports QMCSPL_ERR_OOM (or a CUDA error) from
+    qmcspl_create and leaves the context usable."""
+    from paper_1309_6250_gb300 import _lib
+    mil = np.zeros((1, 3), dtype=np.int32)
+    coef = np.ones((4096, 1))
+    with pytest.raises(_lib.QmcsplError) as ei:
+        splines(np.eye(3) * 10.0, (512, 512, 512), mil, coef, method="smooth", storage="f64",
+                separate_lap=True)
+    assert ei.value.code in (_lib.ERR_OOM, _lib.ERR_CUDA)
+    # the device still works
+    lat, mil, coef = inputs.random_cell(1, (8, 8, 8), 2, 4.0, 4.0, np.eye(3) * 6.0)
+    spl = splines(lat, (8, 8, 8), mil, coef, method="smooth", storage="f64", separate_lap=False)
+    beta, _ = oracle.smoothing_tables(lat, mil, coef, (8, 8, 8))
+    pos = inputs.positions(lat, 10, 1)
+    assert_parity(gpu_eval(spl, pos), oracle.bspline_eval(beta, lat, pos), 1e-12)
