@@ -466,17 +466,25 @@ __device__ __forceinline__ void warp_task(const EvalArgs& p, long long w0, int l
 }
 
 #ifndef QMCSPL_EVAL_MINBLOCKS
-#define QMCSPL_EVAL_MINBLOCKS 2
+#define QMCSPL_EVAL_MINBLOCKS 1
 #endif
+#ifndef QMCSPL_EVAL_THREADS
+#define QMCSPL_EVAL_THREADS 512
+#endif
+// Threads per block of the B-spline evaluation kernels.  With cell-ordered positions the
+// 16 warps of one 512-thread block evaluate 16 consecutive (neighbouring) positions on one
+// SM, so their shared stencil rows hit in that SM's L1; two 256-thread blocks on an SM
+// work on positions far apart in the order.  128 registers x 512 threads fill the SM.
+constexpr int kBspThreads = QMCSPL_EVAL_THREADS;
 
 template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(kEvalThreads, QMCSPL_EVAL_MINBLOCKS) bspline_vgl_kernel(const EvalArgs p)
+__global__ void __launch_bounds__(kBspThreads, QMCSPL_EVAL_MINBLOCKS) bspline_vgl_kernel(const EvalArgs p)
 {
     const int lane = threadIdx.x & 31;
     const int gpw = 32 >> p.lanes_log2;
     const long long total = p.n_pos * p.tiles;
-    const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
-    const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
+    const long long warp = (long long)blockIdx.x * (kBspThreads / 32) + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * (kBspThreads / 32);
     for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw)
         warp_task<T, LAPTAB>(p, w0, lane);
 }
@@ -491,11 +499,11 @@ struct BatchArgs {
 static_assert(sizeof(BatchArgs) <= 32000, "batched kernel parameters exceed the 32 KB limit");
 
 template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(kEvalThreads, QMCSPL_EVAL_MINBLOCKS) bspline_vgl_batched_kernel(const __grid_constant__ BatchArgs b)
+__global__ void __launch_bounds__(kBspThreads, QMCSPL_EVAL_MINBLOCKS) bspline_vgl_batched_kernel(const __grid_constant__ BatchArgs b)
 {
     const int lane = threadIdx.x & 31;
-    const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
-    const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
+    const long long warp = (long long)blockIdx.x * (kBspThreads / 32) + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * (kBspThreads / 32);
     const long long total = b.start[b.n_cells];
     int c = 0;
     for (long long w = warp; w < total; w += wstride) {
@@ -509,9 +517,9 @@ __global__ void __launch_bounds__(kEvalThreads, QMCSPL_EVAL_MINBLOCKS) bspline_v
 template <typename K>
 long long grid_for(K kernel, long long warps)
 {
-    long long blocks = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+    long long blocks = (warps + kBspThreads / 32 - 1) / (kBspThreads / 32);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kEvalThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBspThreads, 0) != cudaSuccess)
         per_sm = 1;
     if (per_sm < 1) per_sm = 1;
     const long long cap = (long long)sm_count() * per_sm;
@@ -525,7 +533,7 @@ int launch_typed(const EvalArgs& a, cudaStream_t st)
     const int gpw = 32 >> a.lanes_log2;
     const long long warps = (a.n_pos * a.tiles + gpw - 1) / gpw;
     const long long blocks = grid_for(bspline_vgl_kernel<T, LAPTAB>, warps);
-    bspline_vgl_kernel<T, LAPTAB><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
+    bspline_vgl_kernel<T, LAPTAB><<<(unsigned)blocks, kBspThreads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "bspline_vgl_kernel launch");
 }
 
@@ -533,7 +541,7 @@ template <typename T, bool LAPTAB>
 int launch_batched_typed(const BatchArgs& b, cudaStream_t st)
 {
     const long long blocks = grid_for(bspline_vgl_batched_kernel<T, LAPTAB>, b.start[b.n_cells]);
-    bspline_vgl_batched_kernel<T, LAPTAB><<<(unsigned)blocks, kEvalThreads, 0, st>>>(b);
+    bspline_vgl_batched_kernel<T, LAPTAB><<<(unsigned)blocks, kBspThreads, 0, st>>>(b);
     return cuda_error(cudaGetLastError(), "bspline_vgl_batched_kernel launch");
 }
 
