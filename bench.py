@@ -100,7 +100,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
@@ -142,12 +142,11 @@ class ClockSampler:
 
 
 def dist_setup():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    from paper_1309_6250_gb300.replicas import env_rank_world
+    rank, ws, local = env_rank_world()
     if ws <= 1:
         return 0, 1, None
     import torch.distributed as dist
-    rank = int(os.environ["RANK"])
-    local = int(os.environ.get("LOCAL_RANK", rank))
     import torch
     torch.cuda.set_device(local)
     dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -324,9 +323,10 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     from paper_1309_6250_gb300.api import OrbitalSplines
 
+    from paper_1309_6250_gb300 import replicas
     w = inputs.make_workload(args.workload, n_pos=args.n_pos)
     if rank > 0:   # weak scaling: every rank its own walkers
-        w.pos[:] = inputs.positions(w.lattice, w.pos.shape[0], w.cell.pos_seed + 7919 * rank)
+        w.pos[:] = replicas.rank_positions(w.lattice, w.pos.shape[0], w.cell.pos_seed, rank)
     n_pos, n_orb = w.pos.shape[0], w.coef.shape[0]
     stream = torch.cuda.current_stream()
 
@@ -359,13 +359,9 @@ def run_ours(args):
     prof = spl.profile_read()
     spl.profile(False)
     spl.sync()
-    total_ms = sum(ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.max_over_ranks(sum(ms), dist, dev)
     evals_per_step = n_pos * n_orb
-    value = evals_per_step * ws * args.steps / (total_ms * 1e-3)
+    value = replicas.job_throughput(evals_per_step * args.steps, ws, total_ms * 1e-3)
 
     # end to end through the host-buffer entry point: pinned positions in, outputs back
     pos_h = torch.from_numpy(w.pos).pin_memory()
@@ -381,12 +377,8 @@ def run_ours(args):
     for _ in range(e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = evals_per_step * ws * e2e_steps / e2e_s
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e_value = replicas.job_throughput(evals_per_step * e2e_steps, ws, e2e_s)
     d2h = sum(o.numel() * o.element_size() for o in host_out)
 
     # roofline of the dominant kernel, from its own CUDA-event launch times
@@ -478,7 +470,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3")
