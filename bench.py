@@ -341,7 +341,21 @@ def run_ours(args):
     info = spl.info()
     pos_d = torch.from_numpy(w.pos).to(dev)
     outs = spl.alloc_outputs(n_pos)
-    step = lambda: spl.eval_vgl(pos_d, out=outs)
+    eager = lambda: spl.eval_vgl(pos_d, out=outs)
+    step = eager
+    graph = None
+    if not args.no_graph:
+        # one step (records + sort + evaluation) captured once and replayed: no launch gaps
+        cap = torch.cuda.Stream()
+        cap.wait_stream(stream)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(cap):
+            spl.eval_vgl(pos_d, out=outs, stream=cap)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(graph, stream=cap):
+                spl.eval_vgl(pos_d, out=outs, stream=cap)
+        torch.cuda.synchronize()
+        step = graph.replay    # replays on the current (timed) stream
     cell_order = args.order == "cell" or (args.order == "auto" and n_pos >= 8192)
     kernels_per_step = 4 if cell_order else 1     # bin, scan, place + evaluation
 
@@ -352,10 +366,13 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    spl.profile(True)
     sampler.start()
     ms = time_steps(step, args.steps, 0, torch, stream)
     clocks = sampler.stop()
+    spl.sync()
+    # the evaluation kernel's own launch time, from the library's CUDA events (eager calls)
+    spl.profile(True)
+    time_steps(eager, max(10, args.steps // 4), 0, torch, stream)
     prof = spl.profile_read()
     spl.profile(False)
     spl.sync()
@@ -441,6 +458,7 @@ def run_ours(args):
                    "accumulate": {"f64": "f64", "df64": "double-float (f32 pairs)"}.get(args.storage, "f32"),
                    "order": "cell" if cell_order else "input",
                    "table_bytes": info["table_bytes"], "lanes": info["lanes"], "tiles": info["tiles"],
+                   "cuda_graph": graph is not None,
                    "l2": "table and outputs larger than L2 (no flush needed)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -479,6 +497,7 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of CUDA-graph replays")
     ap.add_argument("--n-pos", type=int, default=None, help="use only the first N positions (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -119,3 +119,28 @@ def test_batched_graph_capture_and_validation():
     with pytest.raises(_lib.QmcsplError) as ei:
         eval_batched([spls[0], other], [pos[0], pos[0]])
     assert ei.value.code == _lib.ERR_ARG
+
+
+def test_eval_vgl_cell_order_captured_in_cuda_graph():
+    """After one call at a size (scratch allocated) qmcspl_eval_vgl -- records, sort and
+    evaluation -- can be captured in a CUDA graph; replays give the eager results."""
+    w = inputs.make_workload("c2", n_pos=20000)
+    spl = splines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32", separate_lap=True)
+    pos = torch.from_numpy(w.pos).to(dev())
+    ref = [t.clone() for t in spl.eval_vgl(pos)]
+    spl.sync()
+    out = spl.alloc_outputs(pos.shape[0])
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        spl.eval_vgl(pos, out=out, stream=s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            spl.eval_vgl(pos, out=out, stream=s)
+    for t in out:
+        t.zero_()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(out, ref):
+        assert torch.equal(a, b)
