@@ -276,6 +276,21 @@ int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void
 int qmcspl_profile(qmcspl_t h, int enable);
 int qmcspl_profile_read(qmcspl_t h, double* eval_ms, double* order_ms, long long* launches);
 
+/*
+ * qmcspl_save / qmcspl_load -- keep built tables on disk (checkpoint and resume).
+ *
+ * Not in the paper.  qmcspl_save writes the handle's geometry (lattice, grid, orbital
+ * count, method, storage, layout) and its tables, byte for byte, with a 64-bit FNV-1a
+ * checksum of the table bytes; it synchronises the device and blocks.  qmcspl_load
+ * reads such a file and builds a handle on the current device without the planewave
+ * construction (the tables are uploaded as stored, on `stream`; the call blocks).
+ * A file that is truncated, carries another magic, format or layout version, has
+ * inconsistent sizes or fails the checksum is rejected with QMCSPL_ERR_ARG before any
+ * device memory is allocated; I/O failures give QMCSPL_ERR_ARG with the OS message.
+ */
+int qmcspl_save(qmcspl_t h, const char* path);
+int qmcspl_load(qmcspl_t* out, const char* path, void* stream);
+
 /* qmcspl_sync -- synchronise `stream` and report (then clear) any device-side error the
  * handle's kernels recorded: QMCSPL_ERR_DEVICE for non-finite positions. */
 int qmcspl_sync(qmcspl_t h, void* stream);

@@ -83,6 +83,8 @@ PROTOTYPES = [
     ("qmcspl_profile", I, [VP, I]),
     ("qmcspl_profile_read", I, [VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_longlong)]),
+    ("qmcspl_save", I, [VP, ctypes.c_char_p]),
+    ("qmcspl_load", I, [ctypes.POINTER(VP), ctypes.c_char_p, VP]),
     ("qmcspl_sync", I, [VP, VP]),
     ("qmcspl_last_error", ctypes.c_char_p, []),
     ("qmcspl_version", I, []),

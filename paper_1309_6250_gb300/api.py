@@ -63,6 +63,31 @@ class OrbitalSplines:
         self.lattice = lat
         self.out_dtype = torch.float64 if storage in ("f64", "df64") else torch.float32
 
+    @classmethod
+    def load(cls, path: str, device: Optional[torch.device] = None,
+             stream: Optional[torch.cuda.Stream] = None) -> "OrbitalSplines":
+        """Handle from a file written by save() (no planewave construction)."""
+        self = cls.__new__(cls)
+        self.lib = _lib.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.qmcspl_load(ctypes.byref(h), str(path).encode(), _stream_handle(stream)))
+        self.handle = h
+        inf = self.info()
+        self.method = {v: k for k, v in _lib.METHODS.items()}[inf["method"]]
+        self.storage = {v: k for k, v in _lib.STORAGE.items()}[inf["storage"]]
+        self.n_orb = inf["n_orb"]
+        self.dims = tuple(inf["dims"])
+        self.lattice = None
+        self.out_dtype = torch.float64 if self.storage in ("f64", "df64") else torch.float32
+        return self
+
+    def save(self, path: str) -> None:
+        """Write the built tables (and geometry) to `path`."""
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.qmcspl_save(self.handle, str(path).encode()))
+
     # -- lifecycle ---------------------------------------------------------
     def close(self) -> None:
         if getattr(self, "handle", None) is not None and self.handle.value:

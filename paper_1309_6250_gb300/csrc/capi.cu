@@ -70,7 +70,34 @@ void fill_eval_args(const Handle* h, EvalArgs* a)
     a->err = h->d_err;
 }
 
-namespace {
+bool inv3(const double m[9], double out[9]);
+
+// Lattice, inverse and the chain-rule matrices of Sec. II (Coordinates):
+//   grad_cart[a] = sum_i N_i ainv[i][a] grad_t[i]
+//   lap = sum_ij N_i N_j (a^-1 a^-T)_ij H_ij, off-diagonal terms counted twice.
+bool handle_geometry(Handle* h, const double lattice[9])
+{
+    double ainv[9];
+    if (!inv3(lattice, ainv)) return false;
+    std::memcpy(h->lattice, lattice, sizeof(h->lattice));
+    std::memcpy(h->ainv, ainv, sizeof(h->ainv));
+    for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < 3; ++i) h->mg[3 * a + i] = h->dims[i] * ainv[3 * i + a];
+    double M[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int a = 0; a < 3; ++a) s += ainv[3 * i + a] * ainv[3 * j + a];
+            M[3 * i + j] = (double)h->dims[i] * h->dims[j] * s;
+        }
+    h->ml[0] = M[0];
+    h->ml[1] = M[4];
+    h->ml[2] = M[8];
+    h->ml[3] = 2.0 * M[1];
+    h->ml[4] = 2.0 * M[2];
+    h->ml[5] = 2.0 * M[5];
+    return true;
+}
 
 bool inv3(const double m[9], double out[9])
 {
@@ -94,6 +121,8 @@ bool inv3(const double m[9], double out[9])
     out[8] = (m[0] * m[4] - m[1] * m[3]) * id;
     return true;
 }
+
+namespace {
 
 inline long long miller_key(int a, int b, int c)
 {
@@ -242,25 +271,7 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
     for (int a = 0; a < 3; ++a) h->dims[a] = dims[a];
     h->n_orb = n_orb;
     h->n_pw = n_pw;
-    std::memcpy(h->lattice, lattice, sizeof(h->lattice));
-    std::memcpy(h->ainv, ainv, sizeof(h->ainv));
-    // chain rule: grad_cart[a] = sum_i N_i ainv[i][a] grad_t[i];
-    // lap = sum_ij N_i N_j (a^-1 a^-T)_ij H_ij, off-diagonal terms counted twice
-    for (int a = 0; a < 3; ++a)
-        for (int i = 0; i < 3; ++i) h->mg[3 * a + i] = dims[i] * ainv[3 * i + a];
-    double M[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double s = 0.0;
-            for (int a = 0; a < 3; ++a) s += ainv[3 * i + a] * ainv[3 * j + a];
-            M[3 * i + j] = (double)dims[i] * dims[j] * s;
-        }
-    h->ml[0] = M[0];
-    h->ml[1] = M[4];
-    h->ml[2] = M[8];
-    h->ml[3] = 2.0 * M[1];
-    h->ml[4] = 2.0 * M[2];
-    h->ml[5] = 2.0 * M[5];
+    handle_geometry(h, lattice);
 
     h->elem_bytes = (h->storage == QMCSPL_F64 || h->storage == QMCSPL_DF64) ? 8 : (h->storage == QMCSPL_F32 ? 4 : 2);
     const int E = (int)(16 / h->elem_bytes);

@@ -78,3 +78,19 @@ def test_validation_without_gpu(lib):
     assert lib.qmcspl_eval_vgl(None, None, 0, None, None, None, None) == _lib.ERR_ARG
     assert lib.qmcspl_sync(None, None) == _lib.ERR_ARG
     assert lib.qmcspl_destroy(None) == _lib.OK
+
+
+def test_load_rejects_bad_files_without_gpu(lib, tmp_path):
+    """qmcspl_load validates the file before touching the device."""
+    h = ctypes.c_void_p()
+    missing = str(tmp_path / "none.qmcspl").encode()
+    assert lib.qmcspl_load(ctypes.byref(h), missing, None) == _lib.ERR_ARG
+    bad = tmp_path / "bad.qmcspl"
+    bad.write_bytes(b"NOTQMCSP" + b"\0" * 200)
+    assert lib.qmcspl_load(ctypes.byref(h), str(bad).encode(), None) == _lib.ERR_ARG
+    assert b"not a qmcspl table file" in lib.qmcspl_last_error()
+    short = tmp_path / "short.qmcspl"
+    short.write_bytes(b"QMCSPLTB")
+    assert lib.qmcspl_load(ctypes.byref(h), str(short).encode(), None) == _lib.ERR_ARG
+    assert h.value is None
+    assert lib.qmcspl_save(None, b"/tmp/x") == _lib.ERR_ARG

@@ -76,3 +76,28 @@ def test_batched_with_cell_order_matches_single_launches():
         s.sync()
         for a, b in zip(o, single):
             assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("method,storage,sep", [("smooth", "f32", True), ("interp", "df64", False),
+                                                ("pp", "bf16", False), ("lagrange", "f64", True)])
+def test_save_load_round_trip(tmp_path, method, storage, sep):
+    """qmcspl_save / qmcspl_load: the loaded handle evaluates to the same bits; a flipped
+    byte in the tables fails the checksum."""
+    from paper_1309_6250_gb300 import _lib
+    from paper_1309_6250_gb300.api import OrbitalSplines
+    dims = (10, 11, 12)
+    lat, mil, coef = inputs.random_cell(950, dims, 9, 6.0, 5.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method=method, storage=storage, separate_lap=sep, lanes=4)
+    path = tmp_path / "t.qmcspl"
+    spl.save(path)
+    loaded = OrbitalSplines.load(path, device=dev())
+    assert loaded.info() == spl.info()
+    pos = inputs.positions(lat, 20000, 4, -1, 2)
+    for a, b in zip(gpu_eval(spl, pos), gpu_eval(loaded, pos)):
+        assert np.array_equal(a, b)
+    raw = bytearray(path.read_bytes())
+    raw[-100] ^= 0x01
+    path.write_bytes(bytes(raw))
+    with pytest.raises(_lib.QmcsplError) as ei:
+        OrbitalSplines.load(path, device=dev())
+    assert ei.value.code == _lib.ERR_ARG
