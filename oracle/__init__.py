@@ -23,6 +23,9 @@ What the oracle computes, in the paper's order:
    [4 1 ... 1] solves with right-hand side 6 x second differences, applied along each
    axis of the coefficient's label, Eq. (pp-splinecoefficients3).
 5. Evaluation and adjoint: plain C loops in qmcspl_oracle.c.
+6. Bloch orbitals at k != 0 (Sec. II): tables of the complex periodic part u_nk as
+   interleaved real and imaginary functions, evaluated by the same C loops, then
+   multiplied by exp(i k.r) with the product rule (bloch_combine).
 
 Readings of the paper that the code depends on:
 * gamma_G (Eq. b-splinecoefficients) is a product over axes of
@@ -348,6 +351,140 @@ def pp_tables(values: np.ndarray) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Bloch orbitals at k != 0 (Sec. II): phi_nk(r) = u_nk(r) exp(i k.r)
+# ---------------------------------------------------------------------------
+# u_nk = sum_G c_G exp(i G.r) is lattice-periodic but complex, so its real and imaginary
+# parts are two real functions on the grid (twice the data of a Gamma-point orbital).
+# Tables are built for both and stored as adjacent functions (Re u_0, Im u_0, Re u_1, ...);
+# the factor exp(i k.r) is applied after the polynomial evaluation, with the
+# UNWRAPPED position r.  Separate derivative tables approximate the periodic parts of
+# the derivatives of phi itself: grad phi = exp(i k.r) sum_G i(k+G) c_G exp(i G.r) and
+# lap phi = -exp(i k.r) sum_G |k+G|^2 c_G exp(i G.r).
+
+def kvector(lattice, kpoint) -> np.ndarray:
+    """Cartesian k = 2 pi a^-T kpoint (kpoint in units of the reciprocal vectors)."""
+    return reciprocal(lattice) @ np.asarray(kpoint, dtype=np.float64)
+
+
+def bloch_pw_eval(lattice, miller, coef, kpoint, pos):
+    """Direct planewave sums of Bloch orbitals (complex):
+    phi = sum_G c_G e^{i(k+G).r}, grad phi = sum_G i(k+G) c_G e^{...}, lap phi = -sum_G |k+G|^2 c_G e^{...}."""
+    K = g_vectors(lattice, miller) + kvector(lattice, kpoint)[None, :]      # [n_pw, 3]
+    pos = _f64(pos).reshape(-1, 3)
+    E = np.exp(1j * (pos @ K.T))                                            # [P, n_pw]
+    c = np.asarray(coef, dtype=np.complex128)
+    val = E @ c.T
+    grad = np.stack([(E * (1j * K[:, a])[None, :]) @ c.T for a in range(3)], axis=1)
+    lap = (E * (-np.einsum("ij,ij->i", K, K))[None, :]) @ c.T
+    return val, grad, lap
+
+
+def interleave(z: np.ndarray) -> np.ndarray:
+    """Complex [..., O] -> real [..., 2O] with Re and Im of each orbital adjacent."""
+    z = np.asarray(z, dtype=np.complex128)
+    out = np.empty(z.shape[:-1] + (2 * z.shape[-1],))
+    out[..., 0::2] = z.real
+    out[..., 1::2] = z.imag
+    return out
+
+
+def deinterleave(x: np.ndarray) -> np.ndarray:
+    """Inverse of interleave: real [..., 2O] -> complex [..., O]."""
+    x = np.asarray(x, dtype=np.float64)
+    return x[..., 0::2] + 1j * x[..., 1::2]
+
+
+def _complex_grid(miller, weighted, dims) -> np.ndarray:
+    """sum_G weighted[o,G] exp(i G.x_l) on the grid, complex [Nx,Ny,Nz,O] (inverse FFT x N)."""
+    X = fold(miller, weighted, dims)
+    n = X.shape[1] * X.shape[2] * X.shape[3]
+    return np.moveaxis(np.fft.ifftn(X, axes=(1, 2, 3)) * n, 0, -1)
+
+
+def bloch_derivative_weights(lattice, miller, kpoint, what: str) -> np.ndarray:
+    """Per-planewave multiplier of the periodic part of phi or a derivative of phi:
+    'value' 1, 'dx'/'dy'/'dz' i(k+G)_a, 'lap' -|k+G|^2."""
+    K = g_vectors(lattice, miller) + kvector(lattice, kpoint)[None, :]
+    if what == "value":
+        return np.ones(K.shape[0], dtype=np.complex128)
+    if what in ("dx", "dy", "dz"):
+        return 1j * K[:, "xyz".index(what[1])]
+    if what == "lap":
+        return -np.einsum("ij,ij->i", K, K).astype(np.complex128)
+    raise ValueError(what)
+
+
+def bloch_grid_values(lattice, miller, coef, kpoint, dims, what: str = "value") -> np.ndarray:
+    """Grid values of the periodic part of phi (u) or of one of its derivatives,
+    interleaved real [Nx,Ny,Nz,2O]."""
+    w = np.asarray(coef) * bloch_derivative_weights(lattice, miller, kpoint, what)[None, :]
+    return interleave(_complex_grid(miller, w, dims))
+
+
+def bloch_tables(method: str, lattice, miller, coef, kpoint, dims, laplacian: bool = False):
+    """Tables of u_nk (and of the periodic part of lap phi) for every method, interleaved.
+
+    smooth: (beta, beta_lap or None), Eq. (b-splinecoefficients) applied to u's coefficients;
+    interp: (beta, beta_lap or None), the cyclic systems solved for Re and Im separately;
+    lagrange: [5, Nx, Ny, Nz, 2O] grid values of u and of the periodic parts of grad phi, lap phi;
+    pp: [8, Nx, Ny, Nz, 2O] pp coefficients of Re u and Im u.
+    """
+    if method == "smooth":
+        w = np.asarray(coef) / gamma(miller, dims)[None, :]
+        beta = interleave(_complex_grid(miller, w, dims))
+        lap = None
+        if laplacian:
+            wl = w * bloch_derivative_weights(lattice, miller, kpoint, "lap")[None, :]
+            lap = interleave(_complex_grid(miller, wl, dims))
+        return beta, lap
+    if method == "interp":
+        beta = interpolating_coefficients(bloch_grid_values(lattice, miller, coef, kpoint, dims))
+        lap = None
+        if laplacian:
+            lap = interpolating_coefficients(bloch_grid_values(lattice, miller, coef, kpoint, dims, "lap"))
+        return beta, lap
+    if method == "lagrange":
+        return np.ascontiguousarray(np.stack(
+            [bloch_grid_values(lattice, miller, coef, kpoint, dims, w)
+             for w in ("value", "dx", "dy", "dz", "lap")]))
+    if method == "pp":
+        return pp_tables(bloch_grid_values(lattice, miller, coef, kpoint, dims))
+    raise ValueError(method)
+
+
+def bloch_combine(val, grad, lap, lattice, kpoint, pos, grad_of_u: bool = True, lap_of_u: bool = True):
+    """Outputs of phi = u e^{ik.r} from those of the interleaved u tables (real [P,2O], [P,3,2O],
+    [P,2O]) -> complex [P,O], [P,3,O], [P,O]:
+      phi = e^{ik.r} u
+      grad phi = e^{ik.r} (grad u + i k u)               (grad_of_u; else grad is already
+                                                          the periodic part of grad phi)
+      lap phi = e^{ik.r} (lap u + 2 i k.grad u - |k|^2 u)  (lap_of_u; else lap is already
+                                                          the periodic part of lap phi)."""
+    k = kvector(lattice, kpoint)
+    pos = _f64(pos).reshape(-1, 3)
+    ph = np.exp(1j * (pos @ k))[:, None]
+    u, gu, lu = deinterleave(val), deinterleave(grad), deinterleave(lap)
+    gphi = gu + 1j * k[None, :, None] * u[:, None, :] if grad_of_u else gu
+    lphi = lu + 2j * np.einsum("a,pao->po", k, gu) - float(k @ k) * u if lap_of_u else lu
+    return ph * u, ph[:, :, None] * gphi, ph * lphi
+
+
+def bloch_eval(method: str, tables, lattice, kpoint, pos, tables_lap=None):
+    """Bloch-orbital value, gradient and Laplacian (complex) through the oracle evaluators
+    of each method on interleaved u tables, then bloch_combine."""
+    if method in ("smooth", "interp"):
+        v, g, l = bspline_eval(tables, lattice, pos, beta_lap=tables_lap)
+        return bloch_combine(v, g, l, lattice, kpoint, pos, True, tables_lap is None)
+    if method == "lagrange":
+        v, g, l = lagrange_eval(tables, lattice, pos)
+        return bloch_combine(v, g, l, lattice, kpoint, pos, False, False)
+    if method == "pp":
+        v, g, l = pp_eval(tables, lattice, pos)
+        return bloch_combine(v, g, l, lattice, kpoint, pos, True, True)
+    raise ValueError(method)
+
+
+# ---------------------------------------------------------------------------
 # evaluation (C loops)
 # ---------------------------------------------------------------------------
 
@@ -456,7 +593,10 @@ def relative_error(test: np.ndarray, ref: np.ndarray) -> float:
     scale = float(np.max(np.abs(ref))) if ref.size else 0.0
     if scale == 0.0:
         return float(np.max(np.abs(test))) if test.size else 0.0
-    return float(np.max(np.abs(np.asarray(test, dtype=np.float64) - ref))) / scale
+    t = np.asarray(test)
+    if not np.iscomplexobj(t):
+        t = t.astype(np.float64)
+    return float(np.max(np.abs(t - ref))) / scale
 
 
 def relative_mean_absolute_error(test: np.ndarray, ref: np.ndarray) -> float:

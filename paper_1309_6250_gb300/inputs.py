@@ -69,20 +69,22 @@ CELLS: Dict[str, Cell] = {
 }
 
 
-def miller_set(lattice: np.ndarray, ecut: float) -> np.ndarray:
-    """All integer Miller triples n with |G|^2/2 <= ecut, G = 2*pi*a^{-T} n.
+def miller_set(lattice: np.ndarray, ecut: float, kpoint=None) -> np.ndarray:
+    """All integer Miller triples n with |k + G|^2/2 <= ecut, G = 2*pi*a^{-T} n.
 
+    k = 2*pi*a^{-T} kpoint (kpoint in units of the reciprocal vectors; None = Gamma).
     Returned as an int32 array [n_pw, 3] in lexicographic (n1, n2, n3) order.
     """
     lat = np.asarray(lattice, dtype=np.float64)
     bmat = 2.0 * np.pi * np.linalg.inv(lat).T          # columns: reciprocal vectors
+    kf = np.zeros(3) if kpoint is None else np.asarray(kpoint, dtype=np.float64)
     gmax = math.sqrt(2.0 * ecut)
-    # |n_i| <= gmax * |a_i| / (2 pi) bounds every component.
-    nmax = [int(math.floor(gmax * np.linalg.norm(lat[:, i]) / (2.0 * np.pi))) + 1
+    # |n_i + kf_i| <= gmax * |a_i| / (2 pi) bounds every component.
+    nmax = [int(math.floor(gmax * np.linalg.norm(lat[:, i]) / (2.0 * np.pi) + abs(kf[i]))) + 1
             for i in range(3)]
     r = [np.arange(-m, m + 1) for m in nmax]
     n = np.stack(np.meshgrid(*r, indexing="ij"), axis=-1).reshape(-1, 3)
-    g = n @ bmat.T
+    g = (n + kf[None, :]) @ bmat.T
     keep = 0.5 * np.einsum("ij,ij->i", g, g) <= ecut * (1.0 + 1e-14)
     return np.ascontiguousarray(n[keep].astype(np.int32))
 
@@ -117,6 +119,23 @@ def pw_coefficients(lattice: np.ndarray, miller: np.ndarray, n_orb: int,
     if zero.size:
         c[:, zero[0]] = c0 * env[zero[0]]
     return c
+
+
+def bloch_coefficients(lattice: np.ndarray, miller: np.ndarray, n_band: int, kpoint,
+                       decay: float, seed: int) -> np.ndarray:
+    """Coefficients c[n_band, n_pw] (complex128) of Bloch orbitals at k != 0.
+
+    phi_nk(r) = sum_G c_G exp(i (k + G).r) has no Hermitian symmetry: every c_G is drawn
+    independently, c_G = (x + i y)/sqrt(2) * exp(-|k + G|^2/d) with x, y ~ N(0,1).
+    """
+    lat = np.asarray(lattice, dtype=np.float64)
+    bmat = 2.0 * np.pi * np.linalg.inv(lat).T
+    kf = np.asarray(kpoint, dtype=np.float64)
+    g = (miller.astype(np.float64) + kf[None, :]) @ bmat.T
+    env = np.exp(-np.einsum("ij,ij->i", g, g) / decay)
+    rng = np.random.default_rng(seed)
+    draws = rng.standard_normal((n_band, miller.shape[0], 2))
+    return (draws[..., 0] + 1j * draws[..., 1]) / math.sqrt(2.0) * env[None, :]
 
 
 def positions(lattice: np.ndarray, n_pos: int, seed: int,
@@ -166,6 +185,41 @@ def random_cell(seed: int, dims: Tuple[int, int, int], n_orb: int, ecut: float,
     mil = miller_set(lattice, ecut)
     coef = pw_coefficients(lattice, mil, n_orb, decay, seed)
     return np.asarray(lattice, dtype=np.float64), mil, coef
+
+
+# k points in units of the reciprocal vectors of the (simple cubic) synthetic cells: the
+# zone-boundary points X and R of the cubic Brillouin zone and a point of no symmetry.
+# Sec. III reports the same conclusions at several k points, so any of them will do.
+KPOINTS: Dict[str, Tuple[float, float, float]] = {
+    "gamma": (0.0, 0.0, 0.0),
+    "X": (0.5, 0.0, 0.0),
+    "R": (0.5, 0.5, 0.5),
+    "generic": (0.137, -0.291, 0.412),
+}
+
+
+def random_bloch_cell(seed: int, n_band: int, ecut: float, decay: float, kpoint,
+                      lattice: Optional[np.ndarray] = None) -> Tuple[np.ndarray, ...]:
+    """Small random k != 0 workload for tests: (lattice, miller, coef)."""
+    if lattice is None:
+        lattice = np.eye(3) * 6.0
+    mil = miller_set(lattice, ecut, kpoint)
+    coef = bloch_coefficients(lattice, mil, n_band, kpoint, decay, seed)
+    return np.asarray(lattice, dtype=np.float64), mil, coef
+
+
+def make_bloch_workload(key: str, kpoint, n_pos: Optional[int] = None,
+                        n_band: Optional[int] = None) -> Workload:
+    """Cell `key` with complex orbitals at `kpoint`: half as many bands as the cell has
+    real orbitals (the same table bytes), the same grid, cutoff and positions."""
+    cell = CELLS[key]
+    lat = cell.lattice
+    mil = miller_set(lat, cell.ecut, kpoint)
+    nb = cell.n_orb // 2 if n_band is None else n_band
+    coef = bloch_coefficients(lat, mil, nb, kpoint, cell.decay, cell.coef_seed + 500)
+    npos = cell.n_pos if n_pos is None else n_pos
+    pos = positions(lat, npos, cell.pos_seed)
+    return Workload(cell, lat, mil, coef, pos)
 
 
 def all_cells() -> List[str]:
