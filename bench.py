@@ -284,6 +284,43 @@ def bench_backward(args, dev, stream):
             "value": n * o / (t * 1e-3), "ms_per_step": t}
 
 
+def bench_bloch(args, dev, stream):
+    """Complex Bloch orbitals at k != 0 (Sec. II) on the MgO-like 64-atom cell: 64 bands at
+    the zone corner R = (1/2, 1/2, 1/2) on 96^3 (the same table bytes as the 128 real
+    orbitals), 2048 walkers x 256 electrons, FP32 smoothing + Laplacian tables, cell order.
+    value = complex orbital evaluations (value, gradient, Laplacian) per second."""
+    import torch
+    from paper_1309_6250_gb300.api import OrbitalSplines
+    kp = inputs.KPOINTS["R"]
+    w = inputs.make_bloch_workload("c3", kp)
+    spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32",
+                         separate_lap=True, device=dev, kpoint=kp)
+    pos = torch.from_numpy(w.pos).to(dev)
+    out = spl.alloc_outputs(pos.shape[0])
+    step = lambda: spl.eval_vgl(pos, out=out)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    spl.profile(True)
+    ms = time_steps(step, max(10, args.steps // 4), 0, torch, stream)
+    prof = spl.profile_read()
+    spl.profile(False)
+    spl.sync()
+    t = sum(ms) / len(ms) * 1e-3
+    k_s = prof["eval_ms"] * 1e-3 / max(1, prof["launches"])
+    n_pos, n_band = w.pos.shape[0], w.coef.shape[0]
+    n_fun = 2 * n_band
+    bpe = algorithmic_bytes_per_eval("f32", spl.info()["n_tables"], n_fun)
+    res = {"workload": "MgO-like 64-atom cell, 64 complex bands at k = R (1/2,1/2,1/2), 96^3, "
+                       "2048 x 256 positions, f32 smoothing + Laplacian tables",
+           "unit": "complex orbital evaluations/s", "value": n_pos * n_band / t, "ms_per_step": t * 1e3,
+           "eval_kernel_ms": k_s * 1e3, "order_kernels_ms": prof["order_ms"] / max(1, prof["launches"]),
+           "real_function_evals_per_s": n_pos * n_fun / t,
+           "algorithmic_gbs": bpe * n_pos * n_fun / k_s / 1e9}
+    spl.close()
+    return res
+
+
 def bench_batched(args, dev, stream):
     """The uneven three-cell workload (Al-like 32-atom: 48 orbitals, 64^3, 512 x 96 e;
     Si-like 64-atom: 128 orbitals, 80^3, 1024 x 256 e; MgO-like 16-atom: 32 orbitals,
@@ -435,7 +472,7 @@ def run_ours(args):
                 "algorithmic_gbs": vb * evals_per_step / vk / 1e9,
                 "frac_of_hbm": vb * evals_per_step / vk / 1e9 / hbm}
 
-    batched = methods = backward = None
+    batched = methods = backward = bloch = None
     if not args.no_variants and rank == 0:
         del outs
         spl.close()
@@ -443,6 +480,7 @@ def run_ours(args):
         batched = bench_batched(args, dev, stream)
         methods = bench_methods(args, dev, stream)
         backward = bench_backward(args, dev, stream)
+        bloch = bench_bloch(args, dev, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -477,6 +515,7 @@ def run_ours(args):
         "batched": batched,
         "methods_si8_48": methods,
         "backward_si64_72": backward,
+        "bloch_mgo64_96": bloch,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -31,6 +31,9 @@
  *     QMCSPL_BF16.
  *     Output layouts (P positions, O orbitals, row-major):
  *         val [P][O],   grad [P][3][O] (Cartesian x, y, z),   lap [P][O].
+ *     For a Bloch handle (opts.bloch = 1) every element is a complex number stored as
+ *     (re, im), i.e. the same layouts with a trailing [2]: val [P][O][2],
+ *     grad [P][3][O][2], lap [P][O][2] (the layout of complex64 / complex128 arrays).
  */
 #ifndef QMCSPL_H
 #define QMCSPL_H
@@ -81,6 +84,22 @@ typedef struct {
                           each owning one 16-byte chunk of every stored row: 0 = choose
                           automatically, else 1, 2, 4, 8, 16 or 32.  Rows are padded to
                           a multiple of lanes x 16 bytes. */
+    int separate_grad; /* B-splines: 1 = also build tables of d_x phi, d_y phi, d_z phi (the
+                          separate gradient approximations of Sec. III C; requires
+                          separate_lap = 1, five tables in all, memory x5) and return
+                          their values as the gradient.  Not for double-float tables.
+                          Ignored by Lagrange (always five tables) and pp. */
+    int bloch;         /* 0 = real Gamma-point orbitals (Hermitian coefficients, real
+                          outputs).  1 = complex Bloch orbitals at crystal momentum k
+                          (Sec. II): phi_n(r) = u_n(r) exp(i k.r) with the periodic part
+                          u_n(r) = sum_G c_{G n} exp(i G.r), so the planewave sum is
+                          sum_G c_{G n} exp(i (k+G).r).  No symmetry is required of the
+                          coefficients; Re u_n and Im u_n are tabulated as two adjacent
+                          real functions (twice the table memory of n_orb real orbitals)
+                          and every output is complex (see qmcspl_eval_vgl). */
+    double kpoint[3];  /* bloch = 1: k in units of the reciprocal lattice vectors,
+                          k = 2 pi a^{-T} kpoint (Cartesian, 1/bohr).  Ignored when
+                          bloch = 0. */
 } qmcspl_opts;
 
 typedef struct {
@@ -88,13 +107,18 @@ typedef struct {
     int n_orb;               /* orbitals */
     int n_orb_padded;        /* orbitals per stored row (zero padded) */
     int method, storage, separate_lap;
-    int n_tables;            /* value tables stored: 1, 2 (B-spline + Laplacian), 5, or 1 pp table of 8 entries */
+    int n_tables;            /* value tables stored: 1, 2 (B-spline + Laplacian), 5 (Lagrange, or
+                                B-spline with separate gradient tables), or 1 pp table of 8 entries */
     int entries_per_point;   /* stored values per grid point per orbital row: 1, or 8 (pp) */
     int rows_z;              /* stored z planes per (x, y) column (periodic ghost planes included) */
     int lanes;               /* threads sharing one position in the eval kernel */
     int tiles;               /* orbital tiles per position */
     long long table_bytes;   /* device bytes of all coefficient tables */
     long long n_pw;          /* planewaves the tables were built from */
+    int bloch;               /* 1: complex Bloch orbitals (n_orb complex orbitals, stored as
+                                2 n_orb real functions per row: Re u_0, Im u_0, Re u_1, ...) */
+    double kpoint[3];        /* k in units of the reciprocal lattice vectors (bloch = 1) */
+    int separate_grad;       /* 1: B-spline with separate gradient tables */
 } qmcspl_info_t;
 
 /*
@@ -111,11 +135,16 @@ typedef struct {
  *   dims     host int[3], grid points per lattice vector, each in [4, 4096]
  *   n_pw     number of planewaves, >= 1
  *   miller   host int[n_pw][3], integer Miller indices n of G = 2 pi a^{-T} n; each
- *            G must appear once and -G must be present (real orbitals)
- *   n_orb    number of orbitals, >= 1
- *   coef     host double[n_orb][n_pw][2], (re, im) of c_{G n}; must satisfy
- *            c_{-G} = conj(c_G) to 1e-12 relative, else QMCSPL_ERR_NOT_HERMITIAN
- *   opts     host pointer to the options (method, storage, separate_lap)
+ *            G must appear once and (real orbitals) -G must be present
+ *   n_orb    number of orbitals, >= 1 (complex orbitals for a Bloch handle)
+ *   coef     host double[n_orb][n_pw][2], (re, im) of c_{G n}; real orbitals must
+ *            satisfy c_{-G} = conj(c_G) to 1e-12 relative, else
+ *            QMCSPL_ERR_NOT_HERMITIAN; Bloch orbitals have no such condition
+ *   opts     host pointer to the options (method, storage, separate_lap, lanes, bloch,
+ *            kpoint).  For a Bloch handle the separate derivative tables approximate
+ *            the periodic parts of the derivatives of phi itself: the Laplacian table
+ *            (B-splines with separate_lap, Lagrange) is built from -|k+G|^2 c_G and
+ *            the Lagrange gradient tables from i (k+G) c_G.
  *   stream   cudaStream_t the construction runs on; the call blocks until the tables
  *            are complete, then frees its temporaries
  *
@@ -142,7 +171,13 @@ int qmcspl_info(qmcspl_t h, qmcspl_info_t* out);
  * (pp-splineinterpolation3) gives the value and reduced derivatives; the chain rule
  * of Sec. II (Coordinates) gives grad = N_i (a^-1)^T grad_t and
  * lap = sum_ij N_i N_j (a^-1 a^-T)_ij d2/dt_i dt_j.  With a separate Laplacian table
- * (B-splines) or for Lagrange, lap (and for Lagrange grad) is the interpolated table.
+ * (B-splines) or for Lagrange, lap is the interpolated table; with separate gradient
+ * tables (Lagrange, B-splines with separate_grad) so is grad.
+ * Bloch handles (Sec. II): with c + i s = exp(i k.r) at the unwrapped position r,
+ *   phi = (c + i s) u,   grad phi = (c + i s)(grad u + i k u),
+ *   lap phi = (c + i s)(lap u + 2 i k.grad u - |k|^2 u),
+ * where a separate table replaces the bracket by its own interpolated value.  The
+ * factor is computed once per position in FP64.
  *
  *   pos    device double[n_pos][3], Cartesian (bohr); non-finite entries give NaN
  *          outputs for that position and QMCSPL_ERR_DEVICE at qmcspl_sync
@@ -180,7 +215,8 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
  *   dpos      device double[n_pos][3], WRITTEN with dL/dr.  NULL skips it.
  * The coefficient adjoint scatters into 64 stencil rows per position with atomic
  * adds, so its summation order (and last bits) vary from run to run.
- * QMCSPL_ERR_UNSUPPORTED for Lagrange and pp handles.
+ * QMCSPL_ERR_UNSUPPORTED for Lagrange, pp, double-float, Bloch and separate-gradient
+ * handles.
  */
 int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, const void* gv,
                              const void* gg, const void* gl, void* dcoef, void* dcoef_lap,
@@ -192,8 +228,9 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
  * Walkers of cells with different orbital counts and grids go through one launch
  * whose work list spreads every cell's positions evenly over the whole GPU (each warp
  * task moves the same number of bytes whatever the cell).  All handles must be
- * B-spline handles on one device with the same storage type and the same
- * separate_lap setting.
+ * B-spline handles without separate gradient tables on one device with the same
+ * storage type, the same separate_lap setting and the same bloch setting (k points may
+ * differ per cell).
  *   n_cells   1..QMCSPL_MAX_BATCH
  *   h         host array of n_cells handles
  *   pos, val, grad, lap   host arrays of n_cells DEVICE pointers (layouts as above;
@@ -213,9 +250,11 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* h, const double* const* pos
 
 /*
  * qmcspl_get_table -- copy one stored table back to the host in canonical layout
- * double[Nx][Ny][Nz][O] (padding and ghost planes removed, converted to double).
+ * double[Nx][Ny][Nz][O] (padding and ghost planes removed, converted to double); a
+ * Bloch handle gives double[Nx][Ny][Nz][O][2], (Re, Im) of the tabulated periodic part.
  *   table  B-splines: 0 = coefficients, 1 = Laplacian coefficients (separate_lap);
- *          Lagrange: 0..4 = phi, d_x phi, d_y phi, d_z phi, lap phi;
+ *          Lagrange, and B-splines with separate_grad: 0..4 = tables of phi, d_x phi,
+ *          d_y phi, d_z phi, lap phi;
  *          pp: 0..7 = sigma^{kappa mu nu} with index 4(kappa-1) + 2(mu-1) + (nu-1).
  * Blocking.
  */
@@ -250,6 +289,8 @@ int qmcspl_set_order(qmcspl_t h, int mode);
  * positions and the outputs, laid out as for qmcspl_eval_vgl.
  *   n_pos  0 .. QMCSPL_NOALLOC_MAX_POS; larger counts fail with QMCSPL_ERR_ARG
  *          before anything is launched
+ * Bloch handles are not accepted (QMCSPL_ERR_UNSUPPORTED): their phase factors need
+ * per-position scratch that the fixed array does not hold.
  *   stream cudaStream_t; asynchronous like qmcspl_eval_vgl
  * The first call on a device looks up the array's device address (a one-time set-up
  * per device, under a lock); make that first call before capturing any stream.

@@ -318,6 +318,40 @@ def smoothing_tables(lattice, miller, coef, dims, laplacian: bool = False):
     return beta, lap
 
 
+def derivative_tables(method: str, lattice, miller, coef, dims) -> np.ndarray:
+    """[5, Nx, Ny, Nz, O]: B-spline coefficients of separate approximations (Sec. III C)
+    of phi, d_x phi, d_y phi, d_z phi and lap phi, each built from its own planewave sum
+    (multipliers 1, i G_a, -|G|^2): smoothing by Eq. (b-splinecoefficients), interpolating
+    by the cyclic solves of the grid values."""
+    out = []
+    G = g_vectors(lattice, miller)
+    for what in ("value", "dx", "dy", "dz", "lap"):
+        if method == "smooth":
+            if what == "value":
+                m = np.ones(G.shape[0], dtype=np.complex128)
+            elif what == "lap":
+                m = -np.einsum("ij,ij->i", G, G).astype(np.complex128)
+            else:
+                m = 1j * G[:, "xyz".index(what[1])]
+            w = np.asarray(coef) * (m / gamma(miller, dims))[None, :]
+            f, _ = grid_sum(fold(miller, w, dims))
+            out.append(f)
+        elif method == "interp":
+            out.append(interpolating_coefficients(grid_values(lattice, miller, coef, dims, what)))
+        else:
+            raise ValueError(method)
+    return np.ascontiguousarray(np.stack(out))
+
+
+def bspline_eval_separate(tabs, lattice, pos):
+    """Value, gradient and Laplacian from five separate B-spline approximations: each is the
+    value of its own spline (no derivatives of the value spline, no chain rule)."""
+    val = bspline_eval(tabs[0], lattice, pos)[0]
+    grad = np.stack([bspline_eval(tabs[1 + a], lattice, pos)[0] for a in range(3)], axis=1)
+    lap = bspline_eval(tabs[4], lattice, pos)[0]
+    return val, grad, lap
+
+
 # ---------------------------------------------------------------------------
 # Lagrange and pp-spline tables
 # ---------------------------------------------------------------------------
@@ -421,14 +455,27 @@ def bloch_grid_values(lattice, miller, coef, kpoint, dims, what: str = "value") 
     return interleave(_complex_grid(miller, w, dims))
 
 
-def bloch_tables(method: str, lattice, miller, coef, kpoint, dims, laplacian: bool = False):
+def bloch_tables(method: str, lattice, miller, coef, kpoint, dims, laplacian: bool = False,
+                 gradient: bool = False):
     """Tables of u_nk (and of the periodic part of lap phi) for every method, interleaved.
 
     smooth: (beta, beta_lap or None), Eq. (b-splinecoefficients) applied to u's coefficients;
     interp: (beta, beta_lap or None), the cyclic systems solved for Re and Im separately;
     lagrange: [5, Nx, Ny, Nz, 2O] grid values of u and of the periodic parts of grad phi, lap phi;
     pp: [8, Nx, Ny, Nz, 2O] pp coefficients of Re u and Im u.
+    gradient=True (smooth, interp): [5, Nx, Ny, Nz, 2O] B-spline coefficients of u and of the
+    periodic parts of d_x phi, d_y phi, d_z phi and lap phi (separate approximations).
     """
+    if gradient and method in ("smooth", "interp"):
+        out = []
+        for what in ("value", "dx", "dy", "dz", "lap"):
+            if method == "smooth":
+                w = np.asarray(coef) * (bloch_derivative_weights(lattice, miller, kpoint, what) /
+                                        gamma(miller, dims))[None, :]
+                out.append(interleave(_complex_grid(miller, w, dims)))
+            else:
+                out.append(interpolating_coefficients(bloch_grid_values(lattice, miller, coef, kpoint, dims, what)))
+        return np.ascontiguousarray(np.stack(out))
     if method == "smooth":
         w = np.asarray(coef) / gamma(miller, dims)[None, :]
         beta = interleave(_complex_grid(miller, w, dims))
@@ -472,6 +519,9 @@ def bloch_combine(val, grad, lap, lattice, kpoint, pos, grad_of_u: bool = True, 
 def bloch_eval(method: str, tables, lattice, kpoint, pos, tables_lap=None):
     """Bloch-orbital value, gradient and Laplacian (complex) through the oracle evaluators
     of each method on interleaved u tables, then bloch_combine."""
+    if method in ("smooth", "interp") and np.ndim(tables) == 5:   # separate gradient tables
+        v, g, l = bspline_eval_separate(tables, lattice, pos)
+        return bloch_combine(v, g, l, lattice, kpoint, pos, False, False)
     if method in ("smooth", "interp"):
         v, g, l = bspline_eval(tables, lattice, pos, beta_lap=tables_lap)
         return bloch_combine(v, g, l, lattice, kpoint, pos, True, tables_lap is None)

@@ -50,7 +50,8 @@ class QmcsplError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int), ("storage", ctypes.c_int), ("separate_lap", ctypes.c_int),
-                ("lanes", ctypes.c_int)]
+                ("lanes", ctypes.c_int), ("separate_grad", ctypes.c_int), ("bloch", ctypes.c_int),
+                ("kpoint", ctypes.c_double * 3)]
 
 
 class Info(ctypes.Structure):
@@ -58,7 +59,8 @@ class Info(ctypes.Structure):
                 ("method", ctypes.c_int), ("storage", ctypes.c_int), ("separate_lap", ctypes.c_int),
                 ("n_tables", ctypes.c_int), ("entries_per_point", ctypes.c_int),
                 ("rows_z", ctypes.c_int), ("lanes", ctypes.c_int), ("tiles", ctypes.c_int),
-                ("table_bytes", ctypes.c_longlong), ("n_pw", ctypes.c_longlong)]
+                ("table_bytes", ctypes.c_longlong), ("n_pw", ctypes.c_longlong),
+                ("bloch", ctypes.c_int), ("kpoint", ctypes.c_double * 3), ("separate_grad", ctypes.c_int)]
 
 
 _lock = threading.Lock()

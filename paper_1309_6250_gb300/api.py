@@ -6,7 +6,11 @@ arithmetic in the CUDA library.
     val, grad, lap = spl.eval_vgl(pos)          # pos: float64 CUDA tensor [P, 3]
 
 Output layouts: val [P, O], grad [P, 3, O] (Cartesian), lap [P, O]; float64 for "f64"
-tables, float32 otherwise.
+and "df64" tables, float32 otherwise.  Complex Bloch orbitals at k != 0 (Sec. II,
+phi = u exp(i k.r)):
+
+    spl = OrbitalSplines(lattice, dims, miller, coef, kpoint=(0.5, 0.0, 0.0))
+    val, grad, lap = spl.eval_vgl(pos)          # complex64 / complex128 tensors
 """
 from __future__ import annotations
 
@@ -28,13 +32,18 @@ def _ptr(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
     return ctypes.c_void_p(0 if t is None else t.data_ptr())
 
 
+_COMPLEX = {torch.float32: torch.complex64, torch.float64: torch.complex128}
+
+
 class OrbitalSplines:
-    """Coefficient tables of n_orb real planewave orbitals on one CUDA device."""
+    """Coefficient tables of n_orb planewave orbitals on one CUDA device: real Gamma-point
+    orbitals, or (kpoint given, in units of the reciprocal vectors) complex Bloch orbitals."""
 
     def __init__(self, lattice, dims: Sequence[int], miller, coef, method: str = "smooth",
                  storage: str = "f32", separate_lap: bool = True,
                  device: Optional[torch.device] = None,
-                 stream: Optional[torch.cuda.Stream] = None, lanes: int = 0):
+                 stream: Optional[torch.cuda.Stream] = None, lanes: int = 0, kpoint=None,
+                 separate_grad: bool = False):
         self.lib = _lib.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(3, 3))
@@ -48,7 +57,10 @@ class OrbitalSplines:
         if mil.shape[0] != n_pw:
             raise ValueError("miller and coef disagree on the number of planewaves")
         craw = np.ascontiguousarray(c.view(np.float64).reshape(n_orb, n_pw, 2))
-        opts = _lib.Opts(_lib.METHODS[method], _lib.STORAGE[storage], int(bool(separate_lap)), int(lanes))
+        bloch = kpoint is not None
+        kp = (ctypes.c_double * 3)(*([float(x) for x in kpoint] if bloch else [0.0, 0.0, 0.0]))
+        opts = _lib.Opts(_lib.METHODS[method], _lib.STORAGE[storage], int(bool(separate_lap)), int(lanes),
+                         int(bool(separate_grad)), int(bloch), kp)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = _stream_handle(stream)
@@ -61,7 +73,15 @@ class OrbitalSplines:
         self.n_orb = n_orb
         self.dims = tuple(int(x) for x in dm)
         self.lattice = lat
+        self.separate_grad = bool(self.info()["separate_grad"])
+        self._set_kinds(storage, bloch, kpoint)
+
+    def _set_kinds(self, storage, bloch, kpoint):
+        self.bloch = bool(bloch)
+        self.kpoint = tuple(float(x) for x in kpoint) if self.bloch else None
+        self.n_fun = self.n_orb * (2 if self.bloch else 1)     # stored real functions per row
         self.out_dtype = torch.float64 if storage in ("f64", "df64") else torch.float32
+        self.result_dtype = _COMPLEX[self.out_dtype] if self.bloch else self.out_dtype
 
     @classmethod
     def load(cls, path: str, device: Optional[torch.device] = None,
@@ -80,7 +100,8 @@ class OrbitalSplines:
         self.n_orb = inf["n_orb"]
         self.dims = tuple(inf["dims"])
         self.lattice = None
-        self.out_dtype = torch.float64 if self.storage in ("f64", "df64") else torch.float32
+        self.separate_grad = bool(inf["separate_grad"])
+        self._set_kinds(self.storage, inf["bloch"], inf["kpoint"])
         return self
 
     def save(self, path: str) -> None:
@@ -104,11 +125,13 @@ class OrbitalSplines:
     def info(self) -> dict:
         inf = _lib.Info()
         _lib.check(self.lib.qmcspl_info(self.handle, ctypes.byref(inf)))
-        return {k: (list(getattr(inf, k)) if k == "dims" else getattr(inf, k)) for k, _ in inf._fields_}
+        return {k: (list(getattr(inf, k)) if k in ("dims", "kpoint") else getattr(inf, k))
+                for k, _ in inf._fields_}
 
     def get_table(self, index: int = 0, stream=None) -> np.ndarray:
-        """Stored table `index` in canonical layout [Nx, Ny, Nz, O] as float64."""
-        out = np.zeros(self.dims + (self.n_orb,), dtype=np.float64)
+        """Stored table `index` in canonical layout [Nx, Ny, Nz, O] as float64 ([..., 2 O]
+        with Re and Im of each orbital adjacent for Bloch orbitals)."""
+        out = np.zeros(self.dims + (self.n_fun,), dtype=np.float64)
         with torch.cuda.device(self.device):
             _lib.check(self.lib.qmcspl_get_table(self.handle, int(index), out.ctypes.data,
                                                  _stream_handle(stream)))
@@ -141,7 +164,7 @@ class OrbitalSplines:
 
     # -- evaluation --------------------------------------------------------
     def alloc_outputs(self, n_pos: int):
-        kw = dict(dtype=self.out_dtype, device=self.device)
+        kw = dict(dtype=self.result_dtype, device=self.device)
         return (torch.empty((n_pos, self.n_orb), **kw), torch.empty((n_pos, 3, self.n_orb), **kw),
                 torch.empty((n_pos, self.n_orb), **kw))
 
@@ -169,9 +192,9 @@ class OrbitalSplines:
         pos = pos.reshape(-1, 3).contiguous()
         n = pos.shape[0]
         if out is None:
-            out = (torch.empty((n, self.n_orb), dtype=self.out_dtype),
-                   torch.empty((n, 3, self.n_orb), dtype=self.out_dtype),
-                   torch.empty((n, self.n_orb), dtype=self.out_dtype))
+            out = (torch.empty((n, self.n_orb), dtype=self.result_dtype),
+                   torch.empty((n, 3, self.n_orb), dtype=self.result_dtype),
+                   torch.empty((n, self.n_orb), dtype=self.result_dtype))
         val, grad, lap = out
         with torch.cuda.device(self.device):
             _lib.check(self.lib.qmcspl_eval_vgl_host(self.handle, _ptr(pos), n, _ptr(val), _ptr(grad),

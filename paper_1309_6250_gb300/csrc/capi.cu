@@ -2,7 +2,8 @@
 //
 // Host-side work only: argument validation, the Hermitian check of the planewave
 // coefficients (real Gamma-point orbitals, Sec. III), the chain-rule matrices of
-// Sec. II (Coordinates), table sizing, and dispatch to the kernels.
+// Sec. II (Coordinates), the Cartesian k of Bloch orbitals, table sizing, and dispatch
+// to the kernels.
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -68,6 +69,10 @@ void fill_eval_args(const Handle* h, EvalArgs* a)
         a->mll[i] = (float)(h->ml[i] - (double)a->mlh[i]);
     }
     a->err = h->d_err;
+    for (int i = 0; i < 3; ++i) {
+        a->kc[i] = h->kcart[i];
+        a->kcf[i] = (float)h->kcart[i];
+    }
 }
 
 bool inv3(const double m[9], double out[9]);
@@ -96,6 +101,13 @@ bool handle_geometry(Handle* h, const double lattice[9])
     h->ml[3] = 2.0 * M[1];
     h->ml[4] = 2.0 * M[2];
     h->ml[5] = 2.0 * M[5];
+    // Bloch k (Sec. II): k = 2 pi a^-T kpoint; kred = a^-T kpoint so that k.r = 2 pi kred.r
+    for (int a = 0; a < 3; ++a) {
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i) s += ainv[3 * i + a] * h->kpoint[i];
+        h->kred[a] = h->bloch ? s : 0.0;
+        h->kcart[a] = h->bloch ? 2.0 * M_PI * s : 0.0;
+    }
     return true;
 }
 
@@ -130,8 +142,9 @@ inline long long miller_key(int a, int b, int c)
     return ((a + off) << 42) | ((b + off) << 21) | (c + off);
 }
 
-// Real (Gamma-point) orbitals need every -G and c_{-G} = conj(c_G).
-int check_hermitian(int n_pw, const int* miller, int n_orb, const double* coef)
+// Distinct, in-range Miller indices and finite coefficients; real (Gamma-point)
+// orbitals also need every -G and c_{-G} = conj(c_G).
+int check_planewaves(int n_pw, const int* miller, int n_orb, const double* coef, bool hermitian)
 {
     std::unordered_map<long long, int> index;
     index.reserve((size_t)n_pw * 2);
@@ -147,6 +160,7 @@ int check_hermitian(int n_pw, const int* miller, int n_orb, const double* coef)
         if (!std::isfinite(coef[i])) return set_error(QMCSPL_ERR_ARG, "non-finite coefficient");
         cmax = std::fmax(cmax, std::fabs(coef[i]));
     }
+    if (!hermitian) return QMCSPL_OK;
     const double tol = 1e-12 * (cmax > 0 ? cmax : 1.0);
     for (int g = 0; g < n_pw; ++g) {
         auto it = index.find(miller_key(-miller[3 * g], -miller[3 * g + 1], -miller[3 * g + 2]));
@@ -201,6 +215,7 @@ void free_handle(Handle* h)
     if (h->ord_perm) cudaFree(h->ord_perm);
     if (h->ord_count) cudaFree(h->ord_count);
     if (h->ord_rec) cudaFree(h->ord_rec);
+    if (h->ord_phase) cudaFree(h->ord_phase);
     if (h->prof_ev) {
         for (int i = 0; i < 3 * kProfCalls; ++i) cudaEventDestroy(h->prof_ev[i]);
         delete[] h->prof_ev;
@@ -258,7 +273,19 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
         if (!std::isfinite(lattice[i])) return set_error(QMCSPL_ERR_ARG, "non-finite lattice");
     double ainv[9];
     if (!inv3(lattice, ainv)) return set_error(QMCSPL_ERR_ARG, "singular lattice");
-    int rc = check_hermitian(n_pw, miller, n_orb, coef);
+    if (opts->bloch != 0 && opts->bloch != 1) return set_error(QMCSPL_ERR_ARG, "bloch must be 0 or 1");
+    const bool is_bspline = opts->method == QMCSPL_BSPLINE_SMOOTH || opts->method == QMCSPL_BSPLINE_INTERP;
+    if (is_bspline && opts->separate_grad) {
+        if (!opts->separate_lap)
+            return set_error(QMCSPL_ERR_ARG, "separate_grad needs separate_lap (the five-table layout)");
+        if (opts->storage == QMCSPL_DF64)
+            return set_error(QMCSPL_ERR_UNSUPPORTED, "separate gradient tables are not available in double-float");
+    }
+    if (opts->bloch)
+        for (int i = 0; i < 3; ++i)
+            if (!std::isfinite(opts->kpoint[i])) return set_error(QMCSPL_ERR_ARG, "non-finite kpoint");
+    if (opts->bloch && n_orb > (1 << 29)) return set_error(QMCSPL_ERR_ARG, "n_orb too large");
+    int rc = check_planewaves(n_pw, miller, n_orb, coef, opts->bloch == 0);
     if (rc != QMCSPL_OK) return rc;
 
     Handle* h = new (std::nothrow) Handle();
@@ -268,14 +295,17 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
     h->storage = opts->storage;
     const bool bspline = h->method == QMCSPL_BSPLINE_SMOOTH || h->method == QMCSPL_BSPLINE_INTERP;
     h->separate_lap = bspline ? (opts->separate_lap != 0) : (h->method == QMCSPL_LAGRANGE);
+    h->separate_grad = bspline ? (opts->separate_grad != 0) : (h->method == QMCSPL_LAGRANGE);
     for (int a = 0; a < 3; ++a) h->dims[a] = dims[a];
-    h->n_orb = n_orb;
+    h->bloch = opts->bloch;
+    for (int i = 0; i < 3; ++i) h->kpoint[i] = h->bloch ? opts->kpoint[i] : 0.0;
+    h->n_orb = n_orb << h->bloch;   // stored real functions: Re u, Im u per Bloch orbital
     h->n_pw = n_pw;
     handle_geometry(h, lattice);
 
     h->elem_bytes = (h->storage == QMCSPL_F64 || h->storage == QMCSPL_DF64) ? 8 : (h->storage == QMCSPL_F32 ? 4 : 2);
     const int E = (int)(16 / h->elem_bytes);
-    const int n_chunks = (n_orb + E - 1) / E;
+    const int n_chunks = (h->n_orb + E - 1) / E;
     if (opts->lanes == 0) {
         choose_lanes(n_chunks, h->lanes_log2, h->tiles);
     } else {
@@ -293,7 +323,7 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
     switch (h->method) {
     case QMCSPL_LAGRANGE: h->n_tables = 5; h->entries = 1; h->rows_z = dims[2] + 3; break;
     case QMCSPL_PPSPLINE: h->n_tables = 1; h->entries = 8; h->rows_z = dims[2] + 1; break;
-    default: h->n_tables = h->separate_lap ? 2 : 1; h->entries = 1; h->rows_z = dims[2] + 3; break;
+    default: h->n_tables = h->separate_grad ? 5 : (h->separate_lap ? 2 : 1); h->entries = 1; h->rows_z = dims[2] + 3; break;
     }
     h->table_elems = (size_t)dims[0] * dims[1] * h->rows_z * h->entries * h->n_orb_p;
 
@@ -335,7 +365,7 @@ int qmcspl_info(qmcspl_t h, qmcspl_info_t* out)
     if (!h || !out) return set_error(QMCSPL_ERR_ARG, "NULL argument");
     std::memset(out, 0, sizeof(*out));
     for (int a = 0; a < 3; ++a) out->dims[a] = h->dims[a];
-    out->n_orb = h->n_orb;
+    out->n_orb = h->n_orb >> h->bloch;
     out->n_orb_padded = h->n_orb_p;
     out->method = h->method;
     out->storage = h->storage;
@@ -347,6 +377,9 @@ int qmcspl_info(qmcspl_t h, qmcspl_info_t* out)
     out->tiles = h->tiles;
     out->table_bytes = (long long)(h->table_elems * h->elem_bytes * h->n_tables);
     out->n_pw = h->n_pw;
+    out->bloch = h->bloch;
+    out->separate_grad = h->separate_grad;
+    for (int i = 0; i < 3; ++i) out->kpoint[i] = h->kpoint[i];
     return QMCSPL_OK;
 }
 
@@ -356,19 +389,22 @@ static int eval_dispatch(Handle* h, const double* pos, long long n_pos, void* va
     cudaEvent_t* ev = nullptr;
     if (h->prof_on && h->prof_n < kProfCalls) ev = h->prof_ev + 3 * h->prof_n++;
     if (ev) cudaEventRecord(ev[0], st);
-    const int* perm = nullptr;
-    const void* rec = nullptr;
+    Prepared pr;
     const bool sort = use_cell_order(h, n_pos);
-    if (sort || n_pos >= kRecordMinPositions) {
-        const int rc = prepare_positions(h, pos, n_pos, sort, &rec, &perm, st);
+    // Bloch handles always take the per-position pass: it computes the phase factors
+    if (sort || n_pos >= kRecordMinPositions || h->bloch) {
+        const int rc = prepare_positions(h, pos, n_pos, sort, &pr, st);
         if (rc != QMCSPL_OK) return rc;
     }
     if (ev) cudaEventRecord(ev[1], st);
     int rc;
     switch (h->method) {
-    case QMCSPL_LAGRANGE: rc = launch_lagrange_vgl(h, pos, rec, perm, n_pos, val, grad, lap, st); break;
-    case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, rec, perm, n_pos, val, grad, lap, st); break;
-    default: rc = launch_bspline_vgl(h, pos, rec, perm, n_pos, val, grad, lap, st); break;
+    case QMCSPL_LAGRANGE: rc = launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st); break;
+    case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, pr, n_pos, val, grad, lap, st); break;
+    default:
+        rc = h->separate_grad ? launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st)
+                              : launch_bspline_vgl(h, pos, pr, n_pos, val, grad, lap, st);
+        break;
     }
     if (ev) cudaEventRecord(ev[2], st);
     return rc;
@@ -473,6 +509,9 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is implemented for B-spline handles");
     if (h->storage == QMCSPL_DF64)
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for double-float tables");
+    if (h->bloch) return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for Bloch orbitals");
+    if (h->separate_grad)
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for separate gradient tables");
     if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
     if (dcoef_lap && !(h->separate_lap && dcoef))
         return set_error(QMCSPL_ERR_ARG, "dcoef_lap needs a separate-Laplacian handle and dcoef");
@@ -496,28 +535,28 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* po
     for (int c = 0; c < n_cells; ++c) {
         if (!hs[c]) return set_error(QMCSPL_ERR_ARG, "NULL handle in batch");
         if (hs[c]->device != hs[0]->device) return set_error(QMCSPL_ERR_ARG, "handles on different devices");
-        if (hs[c]->storage != hs[0]->storage || hs[c]->separate_lap != hs[0]->separate_lap)
-            return set_error(QMCSPL_ERR_ARG, "handles of a batch must share storage type and separate_lap");
-        if (hs[c]->method != QMCSPL_BSPLINE_SMOOTH && hs[c]->method != QMCSPL_BSPLINE_INTERP)
-            return set_error(QMCSPL_ERR_UNSUPPORTED, "batched evaluation is for B-spline handles");
+        if (hs[c]->storage != hs[0]->storage || hs[c]->separate_lap != hs[0]->separate_lap ||
+            hs[c]->bloch != hs[0]->bloch)
+            return set_error(QMCSPL_ERR_ARG, "handles of a batch must share storage type, separate_lap and bloch");
+        if ((hs[c]->method != QMCSPL_BSPLINE_SMOOTH && hs[c]->method != QMCSPL_BSPLINE_INTERP) ||
+            hs[c]->separate_grad)
+            return set_error(QMCSPL_ERR_UNSUPPORTED,
+                             "batched evaluation is for B-spline handles without separate gradient tables");
         if (n_pos[c] < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
         if (n_pos[c] > 0 && !pos[c]) return set_error(QMCSPL_ERR_ARG, "pos is NULL");
     }
     DeviceGuard dg(hs[0]->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int* perms[QMCSPL_MAX_BATCH];
-    const void* recs[QMCSPL_MAX_BATCH];
+    Prepared prs[QMCSPL_MAX_BATCH];
     for (int c = 0; c < n_cells; ++c) {
-        perms[c] = nullptr;
-        recs[c] = nullptr;
         const bool sort = n_pos[c] > 0 && use_cell_order(hs[c], n_pos[c]);
-        if (sort || n_pos[c] >= kRecordMinPositions) {
-            const int rc = prepare_positions(hs[c], pos[c], n_pos[c], sort, &recs[c], &perms[c], st);
+        if (n_pos[c] > 0 && (sort || n_pos[c] >= kRecordMinPositions || hs[c]->bloch)) {
+            const int rc = prepare_positions(hs[c], pos[c], n_pos[c], sort, &prs[c], st);
             if (rc != QMCSPL_OK) return rc;
         }
     }
-    return launch_batched(n_cells, reinterpret_cast<const Handle* const*>(hs), pos, recs, perms, n_pos, val,
-                          grad, lap, st);
+    return launch_batched(n_cells, reinterpret_cast<const Handle* const*>(hs), pos, prs, n_pos, val, grad, lap,
+                          st);
 }
 
 int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream)

@@ -17,7 +17,7 @@ namespace qmcspl {
 namespace {
 
 constexpr char kMagic[8] = {'Q', 'M', 'C', 'S', 'P', 'L', 'T', 'B'};
-constexpr int kFormatVersion = 1;
+constexpr int kFormatVersion = 2;   // 2: Bloch flag and k point
 constexpr int kLayoutVersion = 1;   // ghost planes, padding and chunk order of the tables
 
 struct FileHeader {
@@ -25,14 +25,15 @@ struct FileHeader {
     int format_version, layout_version;
     int dims[3];
     int n_orb, n_orb_p;
-    int method, storage, separate_lap;
+    int method, storage, separate_lap, separate_grad;
     int lanes_log2, tiles;
     int n_tables, entries, rows_z;
-    int pad;
+    int bloch;
     long long n_pw;
     long long table_elems;
     long long elem_bytes;
     double lattice[9];
+    double kpoint[3];
     unsigned long long checksum;   // FNV-1a 64 of the table bytes
 };
 
@@ -88,6 +89,7 @@ extern "C" int qmcspl_save(qmcspl_t h, const char* path)
     hd.method = h->method;
     hd.storage = h->storage;
     hd.separate_lap = h->separate_lap;
+    hd.separate_grad = h->separate_grad;
     hd.lanes_log2 = h->lanes_log2;
     hd.tiles = h->tiles;
     hd.n_tables = h->n_tables;
@@ -97,6 +99,8 @@ extern "C" int qmcspl_save(qmcspl_t h, const char* path)
     hd.table_elems = (long long)h->table_elems;
     hd.elem_bytes = (long long)h->elem_bytes;
     std::memcpy(hd.lattice, h->lattice, sizeof(hd.lattice));
+    hd.bloch = h->bloch;
+    std::memcpy(hd.kpoint, h->kpoint, sizeof(hd.kpoint));
     hd.checksum = fnv1a(buf.data(), buf.size());
     FILE* f = std::fopen(path, "wb");
     if (!f) return io_error("cannot open", path);
@@ -137,6 +141,15 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
            hd.rows_z == hd.dims[2] + (hd.method == QMCSPL_PPSPLINE ? 1 : 3) &&
            hd.table_elems == (long long)hd.dims[0] * hd.dims[1] * hd.rows_z * hd.entries * hd.n_orb_p;
     for (int i = 0; i < 9; ++i) sane = sane && std::isfinite(hd.lattice[i]);
+    sane = sane && (hd.bloch == 0 || (hd.bloch == 1 && hd.n_orb % 2 == 0));
+    sane = sane && (hd.separate_grad == 0 || hd.separate_grad == 1) && (hd.separate_lap == 0 || hd.separate_lap == 1);
+    {
+        const int want = hd.method == QMCSPL_PPSPLINE ? 1
+                         : (hd.method == QMCSPL_LAGRANGE || hd.separate_grad) ? 5
+                         : (hd.separate_lap ? 2 : 1);
+        sane = sane && hd.n_tables == want && hd.entries == (hd.method == QMCSPL_PPSPLINE ? 8 : 1);
+    }
+    for (int i = 0; i < 3; ++i) sane = sane && std::isfinite(hd.kpoint[i]) && (hd.bloch || hd.kpoint[i] == 0.0);
     if (!sane) {
         std::fclose(f);
         return set_error(QMCSPL_ERR_ARG, "inconsistent table file header");
@@ -164,12 +177,15 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
     h->method = hd.method;
     h->storage = hd.storage;
     h->separate_lap = hd.separate_lap;
+    h->separate_grad = hd.separate_grad;
     h->lanes_log2 = hd.lanes_log2;
     h->tiles = hd.tiles;
     h->n_tables = hd.n_tables;
     h->entries = hd.entries;
     h->rows_z = hd.rows_z;
     h->n_pw = hd.n_pw;
+    h->bloch = hd.bloch;
+    for (int i = 0; i < 3; ++i) h->kpoint[i] = hd.kpoint[i];
     h->table_elems = (size_t)hd.table_elems;
     h->elem_bytes = (size_t)hd.elem_bytes;
     if (!handle_geometry(h, hd.lattice)) {

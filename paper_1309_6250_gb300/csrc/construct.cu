@@ -2,18 +2,25 @@
 //
 // Every table of the paper is a real-space sum over the planewave set,
 //     T(x_l) = sum_G w(G) c_G exp(i G.x_l),       x_l = grid point l (s = l / N),
-// with a per-planewave multiplier w(G):
-//   smoothing B-spline   1/gamma_G                        Eq. (b-splinecoefficients)
-//   interpolating        1/prod_m (1 + cos(th_m)/2)       the periodic [1/4 1 1/4] system
-//                                                         of "Interpolating B-spline
-//                                                         coefficients", diagonalised
-//   separate Laplacian   -|G|^2 times the above           Sec. III A / III C
-//   Lagrange tables      1, i G_x, i G_y, i G_z, -|G|^2   Sec. III C, Appendix A
-//   pp-spline sigma      prod over the axes labelled 2 of the periodic [4 1 .. 1]
-//                        second-derivative system, diagonalised:
-//                        6 (cos th - 1) / (2 + cos th)   Eq. (pp-splinecoefficients3)
+// with a per-planewave multiplier w(G) = (basis factor) x (derivative factor):
+//   basis   smoothing B-spline   1/gamma_G                     Eq. (b-splinecoefficients)
+//           interpolating        1/prod_m (1 + cos(th_m)/2)    the periodic [1/4 1 1/4]
+//                                                              system of "Interpolating
+//                                                              B-spline coefficients",
+//                                                              diagonalised
+//           grid values          1                             Lagrange tables (App. A)
+//           pp-spline sigma      prod over the axes labelled 2 of the periodic
+//                                [4 1 .. 1] second-derivative system, diagonalised:
+//                                6 (cos th - 1) / (2 + cos th) Eq. (pp-splinecoefficients3)
+//   deriv   value 1; d_a phi i G_a; lap phi -|G|^2 (the separate gradient and Laplacian
+//           approximations of Sec. III C: B-splines optionally, Lagrange always)
 // with th_m = 2 pi n_m / N_m.  The cyclic systems are circulant, so dividing the folded
 // spectrum by their eigenvalues is their exact solution.
+//
+// Bloch orbitals (Sec. II, phi = u exp(i k.r)): the same sums give the complex periodic
+// part u (and, for the derivative tables, the periodic parts of grad phi and lap phi,
+// whose multipliers use k + G: i (k+G)_a, -|k+G|^2); the layout step then stores Re and
+// Im of each orbital as two adjacent real functions.
 //
 // Steps (all FP64, all in this file's kernels):
 //   1. scatter_kernel: fold c_G w(G) onto the N1 x N2 x N3 frequency grid
@@ -42,7 +49,8 @@ struct ScatterArgs {
     int o0, oc;               // orbital chunk
     int dims[3];
     double bmat[9];           // G_a = sum_i bmat[3a+i] n_i
-    int kind;
+    double kc[3];             // Cartesian k added to G in the derivative multipliers (0: Gamma)
+    int basis, deriv;         // BuildBasis, BuildDeriv
     int pp_axes;              // bit 2: x, bit 1: y, bit 0: z carry label 2
     double2* F;               // [N1][N2][N3][oc]
 };
@@ -87,34 +95,31 @@ __global__ void scatter_kernel(const ScatterArgs a)
     const int n0 = a.miller[3 * g], n1 = a.miller[3 * g + 1], n2 = a.miller[3 * g + 2];
     const int k0 = fold(n0, a.dims[0]), k1 = fold(n1, a.dims[1]), k2 = fold(n2, a.dims[2]);
     const double2 c = a.coef[(long long)(a.o0 + oc) * a.n_pw + g];
-    const double G0 = a.bmat[0] * n0 + a.bmat[1] * n1 + a.bmat[2] * n2;
-    const double G1 = a.bmat[3] * n0 + a.bmat[4] * n1 + a.bmat[5] * n2;
-    const double G2 = a.bmat[6] * n0 + a.bmat[7] * n1 + a.bmat[8] * n2;
+    const double G0 = a.bmat[0] * n0 + a.bmat[1] * n1 + a.bmat[2] * n2 + a.kc[0];
+    const double G1 = a.bmat[3] * n0 + a.bmat[4] * n1 + a.bmat[5] * n2 + a.kc[1];
+    const double G2 = a.bmat[6] * n0 + a.bmat[7] * n1 + a.bmat[8] * n2 + a.kc[2];
     const double g2 = G0 * G0 + G1 * G1 + G2 * G2;
-    double wr = 1.0, wi = 0.0;   // complex multiplier w(G)
-    switch (a.kind) {
-    case kBuildSmoothValue:
-        wr = 1.0 / (gamma_axis(n0, a.dims[0]) * gamma_axis(n1, a.dims[1]) * gamma_axis(n2, a.dims[2]));
+    double b = 1.0;              // basis factor (real)
+    switch (a.basis) {
+    case kBasisSmooth:
+        b = 1.0 / (gamma_axis(n0, a.dims[0]) * gamma_axis(n1, a.dims[1]) * gamma_axis(n2, a.dims[2]));
         break;
-    case kBuildSmoothLap:
-        wr = -g2 / (gamma_axis(n0, a.dims[0]) * gamma_axis(n1, a.dims[1]) * gamma_axis(n2, a.dims[2]));
+    case kBasisInterp:
+        b = 1.0 / (interp_axis(k0, a.dims[0]) * interp_axis(k1, a.dims[1]) * interp_axis(k2, a.dims[2]));
         break;
-    case kBuildInterpValue:
-        wr = 1.0 / (interp_axis(k0, a.dims[0]) * interp_axis(k1, a.dims[1]) * interp_axis(k2, a.dims[2]));
+    case kBasisPP:
+        if (a.pp_axes & 4) b *= pp_axis(k0, a.dims[0]);
+        if (a.pp_axes & 2) b *= pp_axis(k1, a.dims[1]);
+        if (a.pp_axes & 1) b *= pp_axis(k2, a.dims[2]);
         break;
-    case kBuildInterpLap:
-        wr = -g2 / (interp_axis(k0, a.dims[0]) * interp_axis(k1, a.dims[1]) * interp_axis(k2, a.dims[2]));
-        break;
-    case kBuildGridValue: break;
-    case kBuildGridDx: wr = 0.0; wi = G0; break;
-    case kBuildGridDy: wr = 0.0; wi = G1; break;
-    case kBuildGridDz: wr = 0.0; wi = G2; break;
-    case kBuildGridLap: wr = -g2; break;
-    case kBuildPP:
-        if (a.pp_axes & 4) wr *= pp_axis(k0, a.dims[0]);
-        if (a.pp_axes & 2) wr *= pp_axis(k1, a.dims[1]);
-        if (a.pp_axes & 1) wr *= pp_axis(k2, a.dims[2]);
-        break;
+    default: break;
+    }
+    double wr = b, wi = 0.0;     // complex multiplier w(G) = basis x derivative factor
+    switch (a.deriv) {
+    case kDerivX: wr = 0.0; wi = b * G0; break;
+    case kDerivY: wr = 0.0; wi = b * G1; break;
+    case kDerivZ: wr = 0.0; wi = b * G2; break;
+    case kDerivLap: wr = -g2 * b; break;
     default: break;
     }
     const double vr = c.x * wr - c.y * wi;
@@ -226,26 +231,32 @@ struct LayoutArgs {
     int rows_z;
     int entries, entry;
     int zshift;               // 1: zz = z + 1 (B-spline / Lagrange); 0: zz = z (pp)
+    int cplx;                 // 1: Bloch, functions 2o and 2o + 1 are Re and Im of orbital o
 };
 
-// table[x][y][zz][entry][o0 + o] = Re F[x][y][(zz - zshift) mod N3][o]
+// Real orbitals:  table[x][y][zz][entry][o0 + o] = Re F[x][y][(zz - zshift) mod N3][o]
+// Bloch orbitals: table[...][2 (o0 + o) + part] = (Re, Im) F[...][o], part = 0, 1.
+// Thread f covers function f of the chunk (oc << cplx functions).
 template <typename T>
 __global__ void layout_kernel(const LayoutArgs a)
 {
+    const int nf = a.oc << a.cplx;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)a.N1 * a.N2 * a.rows_z * a.oc;
+    const long long total = (long long)a.N1 * a.N2 * a.rows_z * nf;
     if (idx >= total) return;
-    const int o = (int)(idx % a.oc);
-    long long r = idx / a.oc;
+    const int f = (int)(idx % nf);
+    const int o = f >> a.cplx;
+    long long r = idx / nf;
     const int zz = (int)(r % a.rows_z);
     r /= a.rows_z;
     const int y = (int)(r % a.N2);
     const int x = (int)(r / a.N2);
     int z = zz - a.zshift;
     z = z < 0 ? z + a.N3 : (z >= a.N3 ? z - a.N3 : z);
-    const double v = a.F[(((long long)x * a.N2 + y) * a.N3 + z) * a.oc + o].x;
+    const double2 F = a.F[(((long long)x * a.N2 + y) * a.N3 + z) * a.oc + o];
+    const double v = (f & a.cplx) ? F.y : F.x;
     T* t = static_cast<T*>(a.tab);
-    t[((((long long)x * a.N2 + y) * a.rows_z + zz) * a.entries + a.entry) * a.o_p + a.o0 + o] =
+    t[((((long long)x * a.N2 + y) * a.rows_z + zz) * a.entries + a.entry) * a.o_p + (a.o0 << a.cplx) + f] =
         from_double<T>(v);
 }
 
@@ -253,25 +264,28 @@ __global__ void layout_kernel(const LayoutArgs a)
 // (hi0, hi1, lo0, lo1), hi = v rounded to float, lo = (v - hi) rounded to float.
 __global__ void layout_df_kernel(const LayoutArgs a)
 {
+    const int nf = a.oc << a.cplx;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)a.N1 * a.N2 * a.rows_z * a.oc;
+    const long long total = (long long)a.N1 * a.N2 * a.rows_z * nf;
     if (idx >= total) return;
-    const int o = (int)(idx % a.oc);
-    long long r = idx / a.oc;
+    const int f = (int)(idx % nf);
+    const int o = f >> a.cplx;
+    long long r = idx / nf;
     const int zz = (int)(r % a.rows_z);
     r /= a.rows_z;
     const int y = (int)(r % a.N2);
     const int x = (int)(r / a.N2);
     int z = zz - a.zshift;
     z = z < 0 ? z + a.N3 : (z >= a.N3 ? z - a.N3 : z);
-    const double v = a.F[(((long long)x * a.N2 + y) * a.N3 + z) * a.oc + o].x;
+    const double2 F = a.F[(((long long)x * a.N2 + y) * a.N3 + z) * a.oc + o];
+    const double v = (f & a.cplx) ? F.y : F.x;
     const float hi = __double2float_rn(v);
     const float lo = __double2float_rn(v - (double)hi);
     const long long row = (((long long)x * a.N2 + y) * a.rows_z + zz) * a.o_p;   // in 8-byte elements
-    const int oo = a.o0 + o;
-    float* f = static_cast<float*>(a.tab) + 2 * (row + (oo & ~1)) + (oo & 1);
-    f[0] = hi;
-    f[2] = lo;
+    const int oo = (a.o0 << a.cplx) + f;
+    float* dst = static_cast<float*>(a.tab) + 2 * (row + (oo & ~1)) + (oo & 1);
+    dst[0] = hi;
+    dst[2] = lo;
 }
 
 int launch_layout(const Handle* h, const double2* F, int tab, int entry, int o0, int oc,
@@ -290,7 +304,8 @@ int launch_layout(const Handle* h, const double2* F, int tab, int entry, int o0,
     a.entries = h->entries;
     a.entry = entry;
     a.zshift = (h->method == QMCSPL_PPSPLINE) ? 0 : 1;
-    const long long total = (long long)a.N1 * a.N2 * a.rows_z * a.oc;
+    a.cplx = h->bloch ? 1 : 0;
+    const long long total = (long long)a.N1 * a.N2 * a.rows_z * (a.oc << a.cplx);
     const unsigned blocks = (unsigned)((total + 255) / 256);
     switch (h->storage) {
     case QMCSPL_DF64: layout_df_kernel<<<blocks, 256, 0, st>>>(a); break;
@@ -318,7 +333,7 @@ int launch_dft(const DftArgs& a, cudaStream_t st)
 }
 
 struct TableJob {
-    int tab, entry, kind, pp_axes;
+    int tab, entry, basis, deriv, pp_axes;
 };
 
 }  // namespace
@@ -338,31 +353,25 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
         if (2 * kmax[a] + 1 >= h->dims[a]) kmax[a] = -1;   // band covers the whole axis
 
     std::vector<TableJob> jobs;
-    switch (h->method) {
-    case QMCSPL_BSPLINE_SMOOTH:
-        jobs.push_back({0, 0, kBuildSmoothValue, 0});
-        if (h->separate_lap) jobs.push_back({1, 0, kBuildSmoothLap, 0});
-        break;
-    case QMCSPL_BSPLINE_INTERP:
-        jobs.push_back({0, 0, kBuildInterpValue, 0});
-        if (h->separate_lap) jobs.push_back({1, 0, kBuildInterpLap, 0});
-        break;
-    case QMCSPL_LAGRANGE:
-        jobs.push_back({0, 0, kBuildGridValue, 0});
-        jobs.push_back({1, 0, kBuildGridDx, 0});
-        jobs.push_back({2, 0, kBuildGridDy, 0});
-        jobs.push_back({3, 0, kBuildGridDz, 0});
-        jobs.push_back({4, 0, kBuildGridLap, 0});
-        break;
-    default:   // pp: entry e = 4(kappa-1) + 2(mu-1) + (nu-1); label 2 <=> bit set
-        for (int e = 0; e < 8; ++e) jobs.push_back({0, e, kBuildPP, e});
-        break;
+    const int basis = h->method == QMCSPL_BSPLINE_SMOOTH   ? kBasisSmooth
+                      : h->method == QMCSPL_BSPLINE_INTERP ? kBasisInterp
+                      : h->method == QMCSPL_LAGRANGE       ? kBasisGrid
+                                                           : kBasisPP;
+    if (h->method == QMCSPL_PPSPLINE) {
+        // entry e = 4(kappa-1) + 2(mu-1) + (nu-1); label 2 <=> bit set
+        for (int e = 0; e < 8; ++e) jobs.push_back({0, e, kBasisPP, kDerivValue, e});
+    } else if (h->n_tables == 5) {   // phi, d_x phi, d_y phi, d_z phi, lap phi
+        for (int d = 0; d < 5; ++d) jobs.push_back({d, 0, basis, d, 0});
+    } else {
+        jobs.push_back({0, 0, basis, kDerivValue, 0});
+        if (h->separate_lap) jobs.push_back({1, 0, basis, kDerivLap, 0});
     }
 
     const size_t per_orb = (size_t)N1 * N2 * N3 * sizeof(double2);
     int oc_max = (int)(kGridBudget / per_orb);
     if (oc_max < 1) oc_max = 1;
-    if (oc_max > h->n_orb) oc_max = h->n_orb;
+    const int n_band = h->n_orb >> h->bloch;   // coefficient rows (complex orbitals when Bloch)
+    if (oc_max > n_band) oc_max = n_band;
 
     int* d_miller = nullptr;
     double2* d_coef = nullptr;
@@ -372,7 +381,7 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
     do {
         e = cudaMallocAsync((void**)&d_miller, sizeof(int) * 3 * (size_t)n_pw, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(miller)"); break; }
-        e = cudaMallocAsync((void**)&d_coef, sizeof(double2) * (size_t)n_pw * h->n_orb, st);
+        e = cudaMallocAsync((void**)&d_coef, sizeof(double2) * (size_t)n_pw * n_band, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(coef)"); break; }
         e = cudaMallocAsync((void**)&F[0], per_orb * oc_max, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(grid)"); break; }
@@ -381,7 +390,7 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
         e = cudaMemcpyAsync(d_miller, miller_host, sizeof(int) * 3 * (size_t)n_pw,
                             cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "upload miller"); break; }
-        e = cudaMemcpyAsync(d_coef, coef_host, sizeof(double2) * (size_t)n_pw * h->n_orb,
+        e = cudaMemcpyAsync(d_coef, coef_host, sizeof(double2) * (size_t)n_pw * n_band,
                             cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "upload coefficients"); break; }
 
@@ -389,8 +398,8 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
         for (int a = 0; a < 3; ++a)
             for (int i = 0; i < 3; ++i) bmat[3 * a + i] = 2.0 * M_PI * h->ainv[3 * i + a];
 
-        for (int o0 = 0; o0 < h->n_orb && rc == QMCSPL_OK; o0 += oc_max) {
-            const int oc = (h->n_orb - o0 < oc_max) ? h->n_orb - o0 : oc_max;
+        for (int o0 = 0; o0 < n_band && rc == QMCSPL_OK; o0 += oc_max) {
+            const int oc = (n_band - o0 < oc_max) ? n_band - o0 : oc_max;
             for (const TableJob& job : jobs) {
                 e = cudaMemsetAsync(F[0], 0, per_orb * oc, st);
                 if (e != cudaSuccess) { rc = cuda_error(e, "cudaMemsetAsync(grid)"); break; }
@@ -402,7 +411,9 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
                 s.oc = oc;
                 for (int a = 0; a < 3; ++a) s.dims[a] = h->dims[a];
                 std::memcpy(s.bmat, bmat, sizeof(bmat));
-                s.kind = job.kind;
+                for (int a = 0; a < 3; ++a) s.kc[a] = h->kcart[a];
+                s.basis = job.basis;
+                s.deriv = job.deriv;
                 s.pp_axes = job.pp_axes;
                 s.F = F[0];
                 const long long tot = (long long)oc * n_pw;

@@ -5,6 +5,8 @@
 //   grad phi = N_i (a^-1)^T grad_t phi               (chain rule, Sec. II Coordinates)
 //   lap phi  = sum_ij N_i N_j (a^-1 a^-T)_ij d2phi/dt_i dt_j, or, with the separate
 //              Laplacian table of Sec. III C, the same tricubic sum over beta_lap.
+// For Bloch orbitals (Sec. II) the stored functions are Re u and Im u of each orbital and
+// the epilogue multiplies by exp(i k.r) with the product rule (bloch_apply).
 //
 // Work mapping.  A group of L = 2^k lanes shares one position; each lane owns one
 // 16-byte chunk of every stored row (2, 4 or 8 orbitals for f64, f32, bf16), the
@@ -140,17 +142,19 @@ __device__ __forceinline__ void bspline_warp_task(const EvalArgs& p, long long w
     const int o0 = chunk * E;
     if (o0 >= p.n_orb) return;
     const bool vec = p.vec_out != 0;
+    A cg[3][E];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const A m0 = (A)p.mg[3 * a], m1 = (A)p.mg[3 * a + 1], m2 = (A)p.mg[3 * a + 2];
+#pragma unroll
+        for (int e = 0; e < E; ++e) cg[a][e] = fma(m0, gx[e], fma(m1, gy[e], m2 * gz[e]));
+    }
+    if (p.phase) bloch_apply<A, E>(p, ip, v, cg, lp, true, !LAPTAB);
     if (p.val) store_run<A, E>(static_cast<A*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
     if (p.grad) {
         A* g = static_cast<A*>(p.grad) + ip * 3 * p.n_orb + o0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const A m0 = (A)p.mg[3 * a], m1 = (A)p.mg[3 * a + 1], m2 = (A)p.mg[3 * a + 2];
-            A c[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) c[e] = fma(m0, gx[e], fma(m1, gy[e], m2 * gz[e]));
-            store_run<A, E>(g + (size_t)a * p.n_orb, c, o0, p.n_orb, vec);
-        }
+        for (int a = 0; a < 3; ++a) store_run<A, E>(g + (size_t)a * p.n_orb, cg[a], o0, p.n_orb, vec);
     }
     if (p.lap) store_run<A, E>(static_cast<A*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
 }
@@ -294,17 +298,19 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
         unpack2(GZ[j], gz[2 * j], gz[2 * j + 1]);
         unpack2(LP[j], lp[2 * j], lp[2 * j + 1]);
     }
+    float cg[3][E];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float m0 = p.mgf[3 * a], m1 = p.mgf[3 * a + 1], m2 = p.mgf[3 * a + 2];
+#pragma unroll
+        for (int e = 0; e < E; ++e) cg[a][e] = fmaf(m0, gx[e], fmaf(m1, gy[e], m2 * gz[e]));
+    }
+    if (p.phase) bloch_apply<float, E>(p, ip, v, cg, lp, true, !LAPTAB);
     if (p.val) store_run<float, E>(static_cast<float*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
     if (p.grad) {
         float* g = static_cast<float*>(p.grad) + ip * 3 * p.n_orb + o0;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float m0 = p.mgf[3 * a], m1 = p.mgf[3 * a + 1], m2 = p.mgf[3 * a + 2];
-            float cg[E];
-#pragma unroll
-            for (int e = 0; e < E; ++e) cg[e] = fmaf(m0, gx[e], fmaf(m1, gy[e], m2 * gz[e]));
-            store_run<float, E>(g + (size_t)a * p.n_orb, cg, o0, p.n_orb, vec);
-        }
+        for (int a = 0; a < 3; ++a) store_run<float, E>(g + (size_t)a * p.n_orb, cg[a], o0, p.n_orb, vec);
     }
     if (p.lap) store_run<float, E>(static_cast<float*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
 }
@@ -429,15 +435,13 @@ __device__ __forceinline__ void bspline_warp_task_df(const EvalArgs& p, long lon
     if (o0 >= p.n_orb) return;
     const bool vec = p.vec_out != 0;
     float a0, a1, b0, b1;
-    double v[E], lp[E];
+    dfloat dv[E], dl[E], dg[3][E];
     unpack2(Vh, a0, a1); unpack2(Vl, b0, b1);
-    v[0] = df_to_double(a0, b0); v[1] = df_to_double(a1, b1);
+    dv[0] = {a0, b0}; dv[1] = {a1, b1};
     unpack2(Lh, a0, a1); unpack2(Ll, b0, b1);
-    lp[0] = df_to_double(a0, b0); lp[1] = df_to_double(a1, b1);
-    if (p.val) store_run<double, E>(static_cast<double*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
-    if (p.grad) {
+    dl[0] = {a0, b0}; dl[1] = {a1, b1};
+    if (p.grad || p.phase) {
         // chain rule in double-float: grad_a = sum_i mg[a][i] grad_t[i]
-        double* g = static_cast<double*>(p.grad) + ip * 3 * p.n_orb + o0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             f32x2 Gh = 0, Gl = 0;
@@ -446,10 +450,38 @@ __device__ __forceinline__ void bspline_warp_task_df(const EvalArgs& p, long lon
             df_fma2(Gh, Gl, pack2(m0h, m0h), pack2(m0l, m0l), pack2(-m0h, -m0h), Xh, Xl);
             df_fma2(Gh, Gl, pack2(m1h, m1h), pack2(m1l, m1l), pack2(-m1h, -m1h), Yh, Yl);
             df_fma2(Gh, Gl, pack2(m2h, m2h), pack2(m2l, m2l), pack2(-m2h, -m2h), Zh, Zl);
-            double cg[E];
             unpack2(Gh, a0, a1); unpack2(Gl, b0, b1);
-            cg[0] = df_to_double(a0, b0);
-            cg[1] = df_to_double(a1, b1);
+            dg[a][0] = {a0, b0};
+            dg[a][1] = {a1, b1};
+        }
+    }
+    if (p.phase) {   // one complex orbital per lane, in double-float
+        const double2 ph = __ldg(p.phase + ip);
+        const dfloat c = df_from_double(ph.x), sn = df_from_double(ph.y);
+        const dfloat k[3] = {df_from_double(p.kc[0]), df_from_double(p.kc[1]), df_from_double(p.kc[2])};
+        const dfloat kk = df_add(df_add(df_mul(k[0], k[0]), df_mul(k[1], k[1])), df_mul(k[2], k[2]));
+        dfloat gr[3] = {dg[0][0], dg[1][0], dg[2][0]}, gi[3] = {dg[0][1], dg[1][1], dg[2][1]};
+        bloch_one<dfloat>(dv[0], dv[1], gr, gi, dl[0], dl[1], k, kk, c, sn, true, !LAPTAB);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            dg[a][0] = gr[a];
+            dg[a][1] = gi[a];
+        }
+    }
+    double v[E], lp[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        v[e] = df_to_double(dv[e].h, dv[e].l);
+        lp[e] = df_to_double(dl[e].h, dl[e].l);
+    }
+    if (p.val) store_run<double, E>(static_cast<double*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
+    if (p.grad) {
+        double* g = static_cast<double*>(p.grad) + ip * 3 * p.n_orb + o0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double cg[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) cg[e] = df_to_double(dg[a][e].h, dg[a][e].l);
             store_run<double, E>(g + (size_t)a * p.n_orb, cg, o0, p.n_orb, vec);
         }
     }
@@ -557,14 +589,15 @@ void set_outputs(const Handle* h, EvalArgs& a, void* val, void* grad, void* lap)
 
 }  // namespace
 
-int launch_bspline_vgl(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
-                       void* val, void* grad, void* lap, cudaStream_t st)
+int launch_bspline_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
+                       void* grad, void* lap, cudaStream_t st)
 {
     EvalArgs a;
     fill_eval_args(h, &a);
     a.pos = pos;
-    a.rec = rec;
-    a.perm = perm;
+    a.rec = pr.rec;
+    a.perm = pr.perm;
+    a.phase = pr.phase;
     a.n_pos = n_pos;
     set_outputs(h, a, val, grad, lap);
     const bool lt = h->separate_lap != 0;
@@ -577,9 +610,9 @@ int launch_bspline_vgl(const Handle* h, const double* pos, const void* rec, cons
     }
 }
 
-int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const void* const* rec,
-                   const int* const* perm, const long long* n_pos, void* const* val, void* const* grad,
-                   void* const* lap, cudaStream_t st)
+int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const Prepared* pr,
+                   const long long* n_pos, void* const* val, void* const* grad, void* const* lap,
+                   cudaStream_t st)
 {
     thread_local BatchArgs B;   // about 16 KB: kept off the stack, one per calling thread
     B.n_cells = n_cells;
@@ -588,8 +621,9 @@ int launch_batched(int n_cells, const Handle* const* hs, const double* const* po
         EvalArgs& a = B.cell[c];
         fill_eval_args(hs[c], &a);
         a.pos = pos[c];
-        a.rec = rec[c];
-        a.perm = perm[c];
+        a.rec = pr[c].rec;
+        a.perm = pr[c].perm;
+        a.phase = pr[c].phase;
         a.n_pos = n_pos[c];
         set_outputs(hs[c], a, val[c], grad[c], lap[c]);
         const int gpw = 32 >> a.lanes_log2;

@@ -333,6 +333,91 @@ __device__ __forceinline__ void df_fma2(f32x2& Ah, f32x2& Al, f32x2 wh, f32x2 wl
     Ah = S;
 }
 
+// ---- Bloch orbitals (Sec. II): phi = u exp(i k.r) ----
+// The same arithmetic in float, double and double-float through one set of names.
+__device__ __forceinline__ float nadd(float a, float b) { return a + b; }
+__device__ __forceinline__ double nadd(double a, double b) { return a + b; }
+__device__ __forceinline__ dfloat nadd(dfloat a, dfloat b) { return df_add(a, b); }
+__device__ __forceinline__ float nsub(float a, float b) { return a - b; }
+__device__ __forceinline__ double nsub(double a, double b) { return a - b; }
+__device__ __forceinline__ dfloat nsub(dfloat a, dfloat b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ float nmul(float a, float b) { return a * b; }
+__device__ __forceinline__ double nmul(double a, double b) { return a * b; }
+__device__ __forceinline__ dfloat nmul(dfloat a, dfloat b) { return df_mul(a, b); }
+
+// (x + i y) <- (x + i y)(c + i s)
+template <typename N>
+__device__ __forceinline__ void crot(N& x, N& y, N c, N s)
+{
+    const N r = nsub(nmul(x, c), nmul(y, s));
+    y = nadd(nmul(x, s), nmul(y, c));
+    x = r;
+}
+
+// One complex orbital.  In: value (vr, vi), Cartesian gradient (gr, gi) and Laplacian
+// (lr, li) of the periodic part u; where grad_u / lap_u is false the gradient / Laplacian
+// given is already the periodic part of grad phi / lap phi (a separate table).  Out: the
+// same of phi, with c + i s = exp(i k.r), kk = |k|^2:
+//   phi = (c + i s) u
+//   grad phi = (c + i s)(grad u + i k u)
+//   lap phi = (c + i s)(lap u + 2 i k.grad u - |k|^2 u)
+template <typename N>
+__device__ __forceinline__ void bloch_one(N& vr, N& vi, N* gr, N* gi, N& lr, N& li, const N* k, N kk, N c,
+                                          N s, bool grad_u, bool lap_u)
+{
+    if (lap_u) {   // uses grad u, so before the gradient is completed
+        const N kgr = nadd(nadd(nmul(k[0], gr[0]), nmul(k[1], gr[1])), nmul(k[2], gr[2]));
+        const N kgi = nadd(nadd(nmul(k[0], gi[0]), nmul(k[1], gi[1])), nmul(k[2], gi[2]));
+        lr = nsub(nsub(lr, nadd(kgi, kgi)), nmul(kk, vr));
+        li = nsub(nadd(li, nadd(kgr, kgr)), nmul(kk, vi));
+    }
+    if (grad_u) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const N r = nsub(gr[a], nmul(k[a], vi));
+            gi[a] = nadd(gi[a], nmul(k[a], vr));
+            gr[a] = r;
+        }
+    }
+    crot(vr, vi, c, s);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) crot(gr[a], gi[a], c, s);
+    crot(lr, li, c, s);
+}
+
+// A lane's E outputs of type A (float or double): E/2 complex orbitals with Re and Im
+// adjacent; g[a] holds Cartesian gradient component a.  Position ip's factor is read
+// from p.phase (computed in FP64 by the per-position pass).
+template <typename A, int E>
+__device__ __forceinline__ void bloch_apply(const EvalArgs& p, long long ip, A* v, A (*g)[E], A* lp, bool grad_u,
+                                            bool lap_u)
+{
+    const double2 ph = __ldg(p.phase + ip);
+    A k[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if constexpr (sizeof(A) == 8) k[a] = p.kc[a];
+        else k[a] = p.kcf[a];
+    }
+    const A kk = k[0] * k[0] + k[1] * k[1] + k[2] * k[2];
+    const A c = (A)ph.x, s = (A)ph.y;
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) {
+        A gr[3], gi[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gr[a] = g[a][2 * j];
+            gi[a] = g[a][2 * j + 1];
+        }
+        bloch_one<A>(v[2 * j], v[2 * j + 1], gr, gi, lp[2 * j], lp[2 * j + 1], k, kk, c, s, grad_u, lap_u);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            g[a][2 * j] = gr[a];
+            g[a][2 * j + 1] = gi[a];
+        }
+    }
+}
+
 // Streaming stores of E consecutive outputs (vector when allowed).
 template <typename A, int E>
 __device__ __forceinline__ void store_run(A* dst, const A* v, int o0, int n_orb, bool vec)

@@ -1,10 +1,13 @@
-// eval_variants.cu -- Lagrange and pp-spline evaluation (the paper's other bases).
+// eval_variants.cu -- five-table and pp-spline evaluation.
 //
-// Lagrange (Appendix A, Eq. lagrangeinterpolation3 with the basis of Eq. lagrangebasis):
-// five tables hold the grid values of phi, d_x phi, d_y phi, d_z phi and lap phi
-// (Sec. III C: Lagrange always uses separate gradient and Laplacian approximations),
-// so one set of weights l_i(tx) l_j(ty) l_k(tz) interpolates all five and the gradient
-// and Laplacian come out Cartesian with no chain rule.
+// Five tables (Sec. III C, separate approximations of the gradient and the Laplacian):
+// tables of phi, d_x phi, d_y phi, d_z phi and lap phi, interpolated with one set of
+// weights w_i(tx) w_j(ty) w_k(tz), so the gradient and Laplacian come out Cartesian with
+// no chain rule.  Two bases use it:
+//   Lagrange (Appendix A, Eq. lagrangeinterpolation3, basis Eq. lagrangebasis): the
+//   tables are grid values; Lagrange always uses the separate approximations;
+//   B-splines with separate gradient tables (opts.separate_grad): the tables are
+//   smoothing or interpolating B-spline coefficients, weights Eq. (b-splinebasis).
 //
 // pp-spline (Appendix B, Eq. pp-splineinterpolation3 with the basis of
 // Eq. pp-splinebasis): eight coefficients sigma^{kappa mu nu} per grid point stored
@@ -12,7 +15,8 @@
 // basis polynomials followed by the chain rule of Sec. II.
 //
 // Work mapping, loads and stores as in eval_bspline.cu: a group of L lanes per
-// position, one 16-byte chunk of each row per lane.
+// position, one 16-byte chunk of each row per lane.  Bloch orbitals (Sec. II) take the
+// same epilogue as the B-splines (bloch_apply).
 #include "eval_common.cuh"
 
 namespace qmcspl {
@@ -29,8 +33,26 @@ __device__ __forceinline__ void lagrange_weights(A t, A* w)
     w[3] = A(1.0 / 6.0) * tp1 * t * tm1;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kEvalThreads, 2) lagrange_vgl_kernel(const EvalArgs p)
+// Value weights of the five-table bases at offsets -1..2.
+enum FiveTableBasis : int { kFiveLagrange = 0, kFiveBSpline = 1 };
+
+template <int BASIS, typename A>
+__device__ __forceinline__ void value_weights(A t, A* w)
+{
+    if constexpr (BASIS == kFiveLagrange) {
+        lagrange_weights<A>(t, w);
+    } else {   // Eq. (b-splinebasis)
+        const A s = A(1) - t;
+        const A t2 = t * t;
+        w[0] = A(0.25) * s * s * s;
+        w[1] = (A(0.75) * t - A(1.5)) * t2 + A(1);
+        w[2] = ((A(-0.75) * t + A(0.75)) * t + A(0.75)) * t + A(0.25);
+        w[3] = A(0.25) * t2 * t;
+    }
+}
+
+template <typename T, int BASIS>
+__global__ void __launch_bounds__(kEvalThreads, 2) five_table_vgl_kernel(const EvalArgs p)
 {
     using A = typename Traits<T>::A;
     constexpr int E = Traits<T>::E;
@@ -59,9 +81,9 @@ __global__ void __launch_bounds__(kEvalThreads, 2) lagrange_vgl_kernel(const Eva
         if (!active) continue;
         if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
         A lx[4], ly[4], lz[4];
-        lagrange_weights<A>((A)tx, lx);
-        lagrange_weights<A>((A)ty, ly);
-        lagrange_weights<A>((A)tz, lz);
+        value_weights<BASIS, A>((A)tx, lx);
+        value_weights<BASIS, A>((A)ty, ly);
+        value_weights<BASIS, A>((A)tz, lz);
         const int chunk = tile * L + sub;
         const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
         A acc[5][E];
@@ -101,6 +123,8 @@ __global__ void __launch_bounds__(kEvalThreads, 2) lagrange_vgl_kernel(const Eva
         const int o0 = chunk * E;
         if (o0 >= p.n_orb) continue;
         const bool vec = p.vec_out != 0;
+        // Bloch: the gradient and Laplacian tables hold the periodic parts of grad phi, lap phi
+        if (p.phase) bloch_apply<A, E>(p, ip, acc[0], acc + 1, acc[4], false, false);
         if (p.val) store_run<A, E>(static_cast<A*>(p.val) + ip * p.n_orb + o0, acc[0], o0, p.n_orb, vec);
         if (p.grad)
 #pragma unroll
@@ -219,19 +243,21 @@ __global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs 
         const int o0 = chunk * E;
         if (o0 >= p.n_orb) continue;
         const bool vec = p.vec_out != 0;
+        A cg[3][E];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const A* mgv = nullptr;
+            if constexpr (sizeof(A) == 8) mgv = p.mg; else mgv = p.mgf;
+            const A m0 = mgv[3 * a], m1 = mgv[3 * a + 1], m2 = mgv[3 * a + 2];
+#pragma unroll
+            for (int e = 0; e < E; ++e) cg[a][e] = fma(m0, gx[e], fma(m1, gy[e], m2 * gz[e]));
+        }
+        if (p.phase) bloch_apply<A, E>(p, ip, v, cg, lp, true, true);
         if (p.val) store_run<A, E>(static_cast<A*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
         if (p.grad) {
             A* g = static_cast<A*>(p.grad) + ip * 3 * p.n_orb + o0;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const A* mgv = nullptr;
-                if constexpr (sizeof(A) == 8) mgv = p.mg; else mgv = p.mgf;
-                const A m0 = mgv[3 * a], m1 = mgv[3 * a + 1], m2 = mgv[3 * a + 2];
-                A c[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) c[e] = fma(m0, gx[e], fma(m1, gy[e], m2 * gz[e]));
-                store_run<A, E>(g + (size_t)a * p.n_orb, c, o0, p.n_orb, vec);
-            }
+            for (int a = 0; a < 3; ++a) store_run<A, E>(g + (size_t)a * p.n_orb, cg[a], o0, p.n_orb, vec);
         }
         if (p.lap) store_run<A, E>(static_cast<A*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
     }
@@ -255,17 +281,18 @@ int launch_variant(void (*kernel)(EvalArgs), const EvalArgs& a, cudaStream_t st,
     return cuda_error(cudaGetLastError(), name);
 }
 
-template <typename T> struct LagrangeK {};
+template <typename T> struct FiveK {};
 template <typename T> struct PPK {};
 
-EvalArgs make_args(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
-                   void* val, void* grad, void* lap)
+EvalArgs make_args(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
+                   void* grad, void* lap)
 {
     EvalArgs a;
     fill_eval_args(h, &a);
     a.pos = pos;
-    a.rec = rec;
-    a.perm = perm;
+    a.rec = pr.rec;
+    a.perm = pr.perm;
+    a.phase = pr.phase;
     a.n_pos = n_pos;
     a.val = val;
     a.grad = grad;
@@ -278,23 +305,32 @@ EvalArgs make_args(const Handle* h, const double* pos, const void* rec, const in
 
 }  // namespace
 
-int launch_lagrange_vgl(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
-                        void* val, void* grad, void* lap, cudaStream_t st)
+int launch_five_table_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
+                          void* grad, void* lap, cudaStream_t st)
 {
-    const EvalArgs a = make_args(h, pos, rec, perm, n_pos, val, grad, lap);
+    const EvalArgs a = make_args(h, pos, pr, n_pos, val, grad, lap);
+    const char* name = "five_table_vgl_kernel";
+    if (h->method == QMCSPL_LAGRANGE) {
+        switch (h->storage) {
+        case QMCSPL_F64: return launch_variant<FiveK, double>(five_table_vgl_kernel<double, kFiveLagrange>, a, st, name);
+        case QMCSPL_F32: return launch_variant<FiveK, float>(five_table_vgl_kernel<float, kFiveLagrange>, a, st, name);
+        default:
+            return launch_variant<FiveK, __nv_bfloat16>(five_table_vgl_kernel<__nv_bfloat16, kFiveLagrange>, a, st,
+                                                        name);
+        }
+    }
     switch (h->storage) {
-    case QMCSPL_F64: return launch_variant<LagrangeK, double>(lagrange_vgl_kernel<double>, a, st, "lagrange_vgl_kernel");
-    case QMCSPL_F32: return launch_variant<LagrangeK, float>(lagrange_vgl_kernel<float>, a, st, "lagrange_vgl_kernel");
+    case QMCSPL_F64: return launch_variant<FiveK, double>(five_table_vgl_kernel<double, kFiveBSpline>, a, st, name);
+    case QMCSPL_F32: return launch_variant<FiveK, float>(five_table_vgl_kernel<float, kFiveBSpline>, a, st, name);
     default:
-        return launch_variant<LagrangeK, __nv_bfloat16>(lagrange_vgl_kernel<__nv_bfloat16>, a, st,
-                                                        "lagrange_vgl_kernel");
+        return launch_variant<FiveK, __nv_bfloat16>(five_table_vgl_kernel<__nv_bfloat16, kFiveBSpline>, a, st, name);
     }
 }
 
-int launch_pp_vgl(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
-                  void* val, void* grad, void* lap, cudaStream_t st)
+int launch_pp_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
+                  void* grad, void* lap, cudaStream_t st)
 {
-    const EvalArgs a = make_args(h, pos, rec, perm, n_pos, val, grad, lap);
+    const EvalArgs a = make_args(h, pos, pr, n_pos, val, grad, lap);
     switch (h->storage) {
     case QMCSPL_F64: return launch_variant<PPK, double>(pp_vgl_kernel<double>, a, st, "pp_vgl_kernel");
     case QMCSPL_F32: return launch_variant<PPK, float>(pp_vgl_kernel<float>, a, st, "pp_vgl_kernel");

@@ -55,6 +55,8 @@ extern "C" int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long 
         return set_error(QMCSPL_ERR_ARG, "qmcspl_eval_vgl_noalloc: n_pos " + std::to_string(n_pos) +
                                              " exceeds QMCSPL_NOALLOC_MAX_POS (" +
                                              std::to_string(kNoAllocMaxPos) + ")");
+    if (h->bloch)
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "qmcspl_eval_vgl_noalloc: Bloch handles need per-position phase scratch");
     if (n_pos == 0) return QMCSPL_OK;
     if (!pos) return set_error(QMCSPL_ERR_ARG, "pos is NULL");
     int prev = -1;
@@ -70,10 +72,15 @@ extern "C" int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long 
         int* count = scratch + 2 * kNoAllocMaxPos;
         rc = build_cell_order(h, pos, n_pos, bin, count, perm, g, st);
         if (rc == QMCSPL_OK) {
+            Prepared pr;
+            pr.perm = perm;
             switch (h->method) {
-            case QMCSPL_LAGRANGE: rc = launch_lagrange_vgl(h, pos, nullptr, perm, n_pos, val, grad, lap, st); break;
-            case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, nullptr, perm, n_pos, val, grad, lap, st); break;
-            default: rc = launch_bspline_vgl(h, pos, nullptr, perm, n_pos, val, grad, lap, st); break;
+            case QMCSPL_LAGRANGE: rc = launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st); break;
+            case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, pr, n_pos, val, grad, lap, st); break;
+            default:
+                rc = h->separate_grad ? launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st)
+                                      : launch_bspline_vgl(h, pos, pr, n_pos, val, grad, lap, st);
+                break;
             }
         }
     }

@@ -14,6 +14,8 @@
 //    the cell.  Within a bin the order is whatever the atomics give; it does not change
 //    any result, since each position is computed the same way and written to its own
 //    output rows.
+// 3. Bloch phase factors (Sec. II, phi = u exp(i k.r)).  exp(i k.r) at the unwrapped
+//    position, in FP64, once per position, for the evaluation epilogues.
 #include "eval_common.cuh"
 
 namespace qmcspl {
@@ -33,6 +35,8 @@ struct PrepArgs {
     int edge;
     int nb[3];
     void* rec;                // records (kind 1, 2 or 3), may be null
+    double2* phase;           // Bloch phase factors, may be null
+    double kred[3];           // a^-T kpoint: k.r = 2 pi (kred . r)
     int* bin;                 // per-position bin (with count)
     int* count;               // bin counters, null: no binning
 };
@@ -70,6 +74,15 @@ __global__ void prepare_kernel(const PrepArgs a)
         float4* q = static_cast<float4*>(a.rec) + 2 * i;
         q[0] = make_float4(__int_as_float(cell), x.h, x.l, y.h);
         q[1] = make_float4(y.l, z.h, z.l, 0.0f);
+    }
+    if (a.phase) {
+        // k.r / (2 pi) = kred . r; only its fractional part matters
+        const double* r = a.pos + 3 * i;
+        const double u = __fma_rn(a.kred[0], r[0], __fma_rn(a.kred[1], r[1], __dmul_rn(a.kred[2], r[2])));
+        const double f = u - rint(u);
+        double sn, cs;
+        sincospi(2.0 * f, &sn, &cs);
+        a.phase[i] = make_double2(cs, sn);
     }
     if (a.count) {
         const int b = ((ix / a.edge) * a.nb[1] + iy / a.edge) * a.nb[2] + iz / a.edge;
@@ -122,12 +135,14 @@ __global__ void place_kernel(const int* bin, long long n, int* offset, int* perm
     perm[slot] = (int)i;
 }
 
-PrepArgs prep_args(const Handle* h, const double* pos, long long n, void* rec, int* bin, int* count,
-                   const BinGeometry* g)
+PrepArgs prep_args(const Handle* h, const double* pos, long long n, void* rec, double2* phase, int* bin,
+                   int* count, const BinGeometry* g)
 {
     PrepArgs a;
     a.pos = pos;
     a.n = n;
+    a.phase = phase;
+    for (int i = 0; i < 3; ++i) a.kred[i] = h->kred[i];
     for (int i = 0; i < 9; ++i) a.ainv[i] = h->ainv[i];
     for (int i = 0; i < 3; ++i) {
         a.dims[i] = h->dims[i];
@@ -189,21 +204,21 @@ int record_kind(const Handle* h)
     return 1;
 }
 
-int build_records(const Handle* h, const double* pos, long long n_pos, void* rec, int* bin, int* count,
-                  const BinGeometry* g, cudaStream_t st)
+int build_records(const Handle* h, const double* pos, long long n_pos, void* rec, double2* phase, int* bin,
+                  int* count, const BinGeometry* g, cudaStream_t st)
 {
     if (count) {
         cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int) * (size_t)(g->n_bins + 1), st);
         if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(bin counts)");
     }
-    return launch_prepare(prep_args(h, pos, n_pos, rec, bin, count, g), rec ? record_kind(h) : 0, st);
+    return launch_prepare(prep_args(h, pos, n_pos, rec, phase, bin, count, g), rec ? record_kind(h) : 0, st);
 }
 
 // Cell order without records (the positions are reduced again by the evaluation kernel).
 int build_cell_order(const Handle* h, const double* pos, long long n_pos, int* bin, int* count,
                      int* perm, const BinGeometry& g, cudaStream_t st)
 {
-    int rc = build_records(h, pos, n_pos, nullptr, bin, count, &g, st);
+    int rc = build_records(h, pos, n_pos, nullptr, nullptr, bin, count, &g, st);
     if (rc != QMCSPL_OK) return rc;
     const unsigned blocks = (unsigned)((n_pos + 255) / 256);
     scan_kernel<<<1, kScanThreads, 0, st>>>(count, g.n_bins);
@@ -221,14 +236,17 @@ static int grow_scratch(Handle* h, long long n_pos, int n_bins)
     if (h->ord_perm) cudaFree(h->ord_perm);
     if (h->ord_count) cudaFree(h->ord_count);
     if (h->ord_rec) cudaFree(h->ord_rec);
+    if (h->ord_phase) cudaFree(h->ord_phase);
     h->ord_bin = h->ord_perm = h->ord_count = nullptr;
     h->ord_rec = nullptr;
+    h->ord_phase = nullptr;
     h->ord_cap = 0;
     h->ord_nbins = 0;
     cudaError_t e = cudaMalloc((void**)&h->ord_bin, sizeof(int) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->ord_perm, sizeof(int) * (size_t)cap);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->ord_count, sizeof(int) * (size_t)nb);
     if (e == cudaSuccess) e = cudaMalloc(&h->ord_rec, 32 * (size_t)cap);
+    if (e == cudaSuccess && h->bloch) e = cudaMalloc((void**)&h->ord_phase, sizeof(double2) * (size_t)cap);
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(position scratch)");
     h->ord_cap = cap;
     h->ord_nbins = nb;
@@ -245,21 +263,23 @@ int cell_order(Handle* h, const double* pos, long long n_pos, const int** perm, 
     return rc;
 }
 
-int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, const void** rec,
-                      const int** perm, cudaStream_t st)
+int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, Prepared* out,
+                      cudaStream_t st)
 {
     const BinGeometry g = bin_geometry(h);
     int rc = grow_scratch(h, n_pos, g.n_bins);
     if (rc != QMCSPL_OK) return rc;
-    *rec = h->ord_rec;
-    *perm = nullptr;
-    if (!sort) return build_records(h, pos, n_pos, h->ord_rec, nullptr, nullptr, nullptr, st);
-    rc = build_records(h, pos, n_pos, h->ord_rec, h->ord_bin, h->ord_count, &g, st);
+    out->rec = h->ord_rec;
+    out->perm = nullptr;
+    out->phase = h->bloch ? h->ord_phase : nullptr;
+    double2* phase = h->bloch ? h->ord_phase : nullptr;
+    if (!sort) return build_records(h, pos, n_pos, h->ord_rec, phase, nullptr, nullptr, nullptr, st);
+    rc = build_records(h, pos, n_pos, h->ord_rec, phase, h->ord_bin, h->ord_count, &g, st);
     if (rc != QMCSPL_OK) return rc;
     const unsigned blocks = (unsigned)((n_pos + 255) / 256);
     scan_kernel<<<1, kScanThreads, 0, st>>>(h->ord_count, g.n_bins);
     place_kernel<<<blocks, 256, 0, st>>>(h->ord_bin, n_pos, h->ord_count, h->ord_perm);
-    *perm = h->ord_perm;
+    out->perm = h->ord_perm;
     return cuda_error(cudaGetLastError(), "cell-order kernels");
 }
 

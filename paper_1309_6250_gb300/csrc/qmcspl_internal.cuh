@@ -31,22 +31,26 @@ constexpr int kEvalThreads = 256;     // eval kernels: 8 warps per block
 constexpr int kProfCalls = 4096;      // calls qmcspl_profile can record
 constexpr long long kRecordMinPositions = 8192;   // from here on positions are reduced in a pass of their own
 
-enum BuildKind : int {
-    kBuildSmoothValue = 0,   // c_G / gamma_G
-    kBuildSmoothLap = 1,     // -|G|^2 c_G / gamma_G
-    kBuildInterpValue = 2,   // c_G / prod(1 + cos(th)/2)
-    kBuildInterpLap = 3,     // -|G|^2 c_G / prod(1 + cos(th)/2)
-    kBuildGridValue = 4,     // c_G                (Lagrange phi)
-    kBuildGridDx = 5,        // i G_x c_G          (Lagrange d_x phi)
-    kBuildGridDy = 6,
-    kBuildGridDz = 7,
-    kBuildGridLap = 8,       // -|G|^2 c_G         (Lagrange lap phi)
-    kBuildPP = 9,            // c_G prod_{axes with label 2} 6(cos th - 1)/(2 + cos th)
+// Per-planewave multiplier of a table sum (construct.cu) = basis factor x derivative
+// factor.  For Bloch orbitals every G in a derivative factor stands for k + G.
+enum BuildBasis : int {
+    kBasisSmooth = 0,        // 1 / gamma_G                       (smoothing B-spline)
+    kBasisInterp = 1,        // 1 / prod(1 + cos(th)/2)           (interpolating B-spline)
+    kBasisGrid = 2,          // 1                                 (grid values: Lagrange)
+    kBasisPP = 3,            // prod over label-2 axes of 6(cos th - 1)/(2 + cos th)
+};
+enum BuildDeriv : int {
+    kDerivValue = 0,         // 1          (phi)
+    kDerivX = 1,             // i G_x      (d_x phi)
+    kDerivY = 2,             // i G_y
+    kDerivZ = 3,             // i G_z
+    kDerivLap = 4,           // -|G|^2     (lap phi)
 };
 
 // Eval parameters shared by the B-spline, Lagrange and pp kernels (passed by value).
 struct EvalArgs {
-    const void* tab[5];       // tables (B-spline: value, Laplacian; Lagrange: 5; pp: 1)
+    const void* tab[5];       // tables (B-spline: value[, Laplacian]; five-table: phi, d_x, d_y,
+                              // d_z, lap phi; pp: 1)
     long long col_stride;     // elements between successive (x, y) columns
     int row_stride;           // elements between successive z rows (O_p, or 8 O_p for pp)
     int nx, ny, nz;
@@ -68,6 +72,11 @@ struct EvalArgs {
     void* lap;
     int vec_out;              // outputs may use 16-byte vector stores
     int* err;                 // device error word (bit 0: non-finite position)
+    // Bloch orbitals (Sec. II): the n_orb stored functions are Re u, Im u of n_orb / 2
+    // complex orbitals; phase[ip] = (cos k.r, sin k.r) at the unwrapped position
+    const double2* phase;     // null: real orbitals
+    double kc[3];             // Cartesian k (1/bohr)
+    float kcf[3];
 };
 
 }  // namespace qmcspl
@@ -76,13 +85,18 @@ struct EvalArgs {
 struct qmcspl_s {
     int device = 0;
     int method = 0, storage = 0, separate_lap = 0;
+    int separate_grad = 0;    // B-splines: tables of d_x, d_y, d_z phi too (five tables)
     int dims[3] = {0, 0, 0};
-    int n_orb = 0, n_orb_p = 0;
+    int n_orb = 0, n_orb_p = 0;   // stored real functions per row (2 per orbital when bloch)
     int n_tables = 0;
     int entries = 1;          // 8 for pp
     int rows_z = 0;
     int lanes_log2 = 0, tiles = 1;
     long long n_pw = 0;
+    int bloch = 0;            // complex Bloch orbitals: phi = u exp(i k.r)
+    double kpoint[3] = {0.0, 0.0, 0.0};   // k in units of the reciprocal vectors
+    double kcart[3] = {0.0, 0.0, 0.0};    // Cartesian k = 2 pi a^-T kpoint
+    double kred[3] = {0.0, 0.0, 0.0};     // a^-T kpoint: k.r = 2 pi (kred . r)
     double lattice[9];
     double ainv[9];
     double mg[9];
@@ -103,6 +117,7 @@ struct qmcspl_s {
     int* ord_count = nullptr;
     int* ord_perm = nullptr;
     void* ord_rec = nullptr;  // per-position coordinate records (32 bytes each)
+    double2* ord_phase = nullptr;   // Bloch handles: exp(i k.r) per position
     long long ord_cap = 0;    // positions the scratch can hold
     int ord_nbins = 0;        // bins the count array can hold
     int order_mode = 0;       // QMCSPL_ORDER_AUTO / INPUT / CELL
@@ -133,18 +148,27 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
                  cudaStream_t stream);
 
 // ---- evaluation launchers ----
-int launch_bspline_vgl(const Handle* h, const double* pos, const void* rec, const int* perm,
-                       long long n_pos, void* val, void* grad, void* lap, cudaStream_t stream);
-int launch_lagrange_vgl(const Handle* h, const double* pos, const void* rec, const int* perm,
-                        long long n_pos, void* val, void* grad, void* lap, cudaStream_t stream);
-int launch_pp_vgl(const Handle* h, const double* pos, const void* rec, const int* perm, long long n_pos,
-                  void* val, void* grad, void* lap, cudaStream_t stream);
+// Prepared per-position data of one evaluation: coordinate records, the evaluation
+// order and (Bloch handles) the phase factors; any may be null.
+struct Prepared {
+    const void* rec = nullptr;
+    const int* perm = nullptr;
+    const double2* phase = nullptr;
+};
+int launch_bspline_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
+                       void* grad, void* lap, cudaStream_t stream);
+// Five tables (phi, d_x phi, d_y phi, d_z phi, lap phi) interpolated with one set of
+// weights: Lagrange, and B-splines with separate gradient tables.
+int launch_five_table_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
+                          void* grad, void* lap, cudaStream_t stream);
+int launch_pp_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
+                  void* grad, void* lap, cudaStream_t stream);
 int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
                             const void* gv, const void* gg, const void* gl, void* dcoef,
                             void* dcoef_lap, double* dpos, cudaStream_t stream);
-int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos,
-                   const void* const* rec, const int* const* perm, const long long* n_pos,
-                   void* const* val, void* const* grad, void* const* lap, cudaStream_t stream);
+int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const Prepared* pr,
+                   const long long* n_pos, void* const* val, void* const* grad, void* const* lap,
+                   cudaStream_t stream);
 
 // ---- cell ordering (order.cu) ----
 // Bin geometry of a handle: bins of `edge` grid cells per axis, nb[3] bins per axis.
@@ -171,11 +195,13 @@ int cell_order(Handle* h, const double* pos, long long n_pos, const int** perm, 
 // cell = ix | iy << 10 | iz << 20, or -1 for a non-finite position.
 // With `count` non-null the kernel also bins the positions for the cell order.
 int record_kind(const Handle* h);
-int build_records(const Handle* h, const double* pos, long long n_pos, void* rec, int* bin, int* count,
-                  const BinGeometry* g, cudaStream_t stream);
-// Records (and, when sorting, the cell order) in the handle's scratch.
-int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, const void** rec,
-                      const int** perm, cudaStream_t stream);
+// With `phase` non-null (Bloch handles) the same pass writes exp(i k.r) per position.
+int build_records(const Handle* h, const double* pos, long long n_pos, void* rec, double2* phase, int* bin,
+                  int* count, const BinGeometry* g, cudaStream_t stream);
+// Records, phase factors (Bloch handles) and, when sorting, the cell order in the
+// handle's scratch.
+int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, Prepared* out,
+                      cudaStream_t stream);
 
 // fill the common part of EvalArgs from a handle
 void fill_eval_args(const Handle* h, EvalArgs* a);

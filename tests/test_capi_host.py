@@ -37,13 +37,14 @@ def test_version_and_empty_error(lib):
     assert lib.qmcspl_last_error() == b""
 
 
-def _create(lib, lattice, dims, miller, coef, method=0, storage=0, sep=0):
+def _create(lib, lattice, dims, miller, coef, method=0, storage=0, sep=0, bloch=0, kpoint=(0.0, 0.0, 0.0),
+            sep_grad=0):
     h = ctypes.c_void_p()
     lat = np.ascontiguousarray(lattice, dtype=np.float64)
     dm = np.ascontiguousarray(dims, dtype=np.int32)
     mil = np.ascontiguousarray(miller, dtype=np.int32)
     c = np.ascontiguousarray(np.asarray(coef, dtype=np.complex128)).view(np.float64)
-    opts = _lib.Opts(method, storage, sep, 0)
+    opts = _lib.Opts(method, storage, sep, 0, sep_grad, bloch, (ctypes.c_double * 3)(*kpoint))
     rc = lib.qmcspl_create(ctypes.byref(h), lat.ctypes.data, dm.ctypes.data, mil.shape[0],
                            mil.ctypes.data, c.shape[0], c.ctypes.data, ctypes.byref(opts), None)
     return rc, h
@@ -74,6 +75,21 @@ def test_validation_without_gpu(lib):
     # duplicated G
     rc, _ = _create(lib, lat, (8, 8, 8), np.vstack([mil, mil[:1]]), np.hstack([coef, coef[:, :1]]))
     assert rc == _lib.ERR_ARG and b"duplicate" in lib.qmcspl_last_error()
+    # Bloch options: flag must be 0/1, k finite; duplicates are still rejected
+    assert _create(lib, lat, (8, 8, 8), mil, coef, bloch=2)[0] == _lib.ERR_ARG
+    rc, _ = _create(lib, lat, (8, 8, 8), mil, coef, bloch=1, kpoint=(0.5, float("nan"), 0.0))
+    assert rc == _lib.ERR_ARG and b"kpoint" in lib.qmcspl_last_error()
+    rc, _ = _create(lib, lat, (8, 8, 8), np.vstack([mil, mil[:1]]), np.hstack([coef, coef[:, :1]]),
+                    bloch=1, kpoint=(0.5, 0.0, 0.0))
+    assert rc == _lib.ERR_ARG and b"duplicate" in lib.qmcspl_last_error()
+    nonfinite = coef.copy()
+    nonfinite[0, 0] = np.nan
+    rc, _ = _create(lib, lat, (8, 8, 8), mil, nonfinite, bloch=1, kpoint=(0.5, 0.0, 0.0))
+    assert rc == _lib.ERR_ARG and b"non-finite" in lib.qmcspl_last_error()
+    # separate gradient tables need the Laplacian table and are not available in double-float
+    rc, _ = _create(lib, lat, (8, 8, 8), mil, coef, sep=0, sep_grad=1)
+    assert rc == _lib.ERR_ARG and b"separate_lap" in lib.qmcspl_last_error()
+    assert _create(lib, lat, (8, 8, 8), mil, coef, storage=3, sep=1, sep_grad=1)[0] == _lib.ERR_UNSUPPORTED
     # NULL handle calls
     assert lib.qmcspl_eval_vgl(None, None, 0, None, None, None, None) == _lib.ERR_ARG
     assert lib.qmcspl_sync(None, None) == _lib.ERR_ARG

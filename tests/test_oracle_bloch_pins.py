@@ -230,3 +230,26 @@ def test_bloch_coefficients_are_not_hermitian_and_cutoff_is_centred_on_minus_k()
     coef = inputs.bloch_coefficients(lat, mil, 2, KGEN, 4.0, 5)
     v, _, _ = oracle.bloch_pw_eval(lat, mil, coef, KGEN, inputs.positions(lat, 10, 1))
     assert np.abs(v.imag).max() > 1e-3
+
+
+@pytest.mark.parametrize("method", ["smooth", "interp"])
+def test_bloch_separate_gradient_tables(method):
+    """Separate gradient tables of a Bloch orbital approximate the periodic part of grad phi,
+    sum_G i(k+G) c_G e^{iG.r}: the interpolating ones reproduce the planewave gradient at
+    grid points; both obey Bloch's theorem."""
+    dims = np.array([8, 9, 10])
+    lat, mil, coef = inputs.random_bloch_cell(15, 2, 4.0, 4.0, KGEN, NONORTHO)
+    tabs = oracle.bloch_tables(method, lat, mil, coef, KGEN, tuple(dims), gradient=True)
+    assert tabs.shape == (5,) + tuple(dims) + (4,)
+    rng = np.random.default_rng(4)
+    pos = (rng.integers(0, dims, size=(20, 3)) / dims) @ lat.T + lat @ np.array([1.0, 2.0, -1.0])
+    v, g, l = oracle.bloch_eval(method, tabs, lat, KGEN, pos)
+    if method == "interp":
+        pv, pg, pl = oracle.bloch_pw_eval(lat, mil, coef, KGEN, pos)
+        for a, b in ((v, pv), (g, pg), (l, pl)):
+            assert oracle.relative_error(a, b) < 1e-12
+    R = lat @ np.array([2.0, -1.0, 1.0])
+    v2, g2, l2 = oracle.bloch_eval(method, tabs, lat, KGEN, pos + R)
+    f = np.exp(1j * oracle.kvector(lat, KGEN) @ R)
+    for a, b in ((v2, v), (g2, g), (l2, l)):
+        assert oracle.relative_error(a, f * b) < 1e-12

@@ -596,3 +596,66 @@ def test_adjoint_positions_fd(sep_lap):
             fd[p, a] = (_loss(beta, lat, pos + e, gv, gg, gl, blap) -
                         _loss(beta, lat, pos - e, gv, gg, gl, blap)) / (2 * h)
     assert oracle.relative_error(dpos, fd) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# separate gradient tables for B-splines (Sec. III C)
+# ---------------------------------------------------------------------------
+
+def test_separate_gradient_tables_single_planewave_closed_form():
+    """Smoothing spline of d_a phi for one planewave c e^{iG.r}, at grid points (weights
+    [1/4, 1, 1/4, 0]): i G_a c e^{iG.r} prod_m (1 + cos th_m / 2)/gamma(th_m); the Laplacian
+    table gives -|G|^2 times the same factor."""
+    dims = np.array([8, 10, 12])
+    n = np.array([2, -1, 3])
+    mil = np.array([n, -n], dtype=np.int32)
+    c = 0.7 - 0.2j
+    coef = np.array([[c, np.conj(c)]])
+    tabs = oracle.derivative_tables("smooth", NONORTHO, mil, coef, tuple(dims))
+    rng = np.random.default_rng(31)
+    j = rng.integers(0, dims, size=(20, 3))
+    pos = (j / dims) @ NONORTHO.T
+    v, g, l = oracle.bspline_eval_separate(tabs, NONORTHO, pos)
+    th = 2 * np.pi * n / dims
+    S = np.prod((1 + 0.5 * np.cos(th)) / oracle.gamma_axis(th))
+    G = 2 * np.pi * np.linalg.inv(NONORTHO).T @ n
+    e = c * np.exp(1j * pos @ G)
+    np.testing.assert_allclose(v[:, 0], 2 * np.real(e) * S, atol=1e-12)
+    np.testing.assert_allclose(g[:, :, 0], 2 * np.real(1j * e[:, None] * G[None, :]) * S, atol=1e-11)
+    np.testing.assert_allclose(l[:, 0], -2 * (G @ G) * np.real(e) * S, atol=1e-10)
+
+
+def test_interpolating_gradient_tables_reproduce_planewave_gradient_at_grid_points():
+    """Interpolating B-splines pass through the grid values of the function they
+    approximate, so separate gradient and Laplacian tables give the planewave gradient and
+    Laplacian exactly at grid points."""
+    dims = np.array([8, 9, 10])
+    lat, mil, coef = inputs.random_cell(32, tuple(dims), 3, 5.0, 4.0, NONORTHO)
+    tabs = oracle.derivative_tables("interp", lat, mil, coef, tuple(dims))
+    rng = np.random.default_rng(33)
+    pos = (rng.integers(0, dims, size=(20, 3)) / dims) @ lat.T
+    v, g, l = oracle.bspline_eval_separate(tabs, lat, pos)
+    pv, pg, pl, _ = oracle.pw_eval(lat, mil, coef, pos)
+    assert oracle.relative_error(v, pv) < 1e-12
+    assert oracle.relative_error(g, pg) < 1e-12
+    assert oracle.relative_error(l, pl) < 1e-12
+
+
+@pytest.mark.parametrize("method", ["smooth", "interp"])
+def test_separate_gradient_converges_faster_than_derivative(method):
+    """Sec. III C / Fig. 1: a separate approximation of the gradient converges like a
+    value (h^4) where the derivative of the value spline converges as h^3."""
+    lat = np.eye(3) * 5.0
+    mil = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 1], [0, -1, -1], [1, -1, 0], [-1, 1, 0]],
+                   dtype=np.int32)
+    coef = np.array([[0.4 + 0.2j, 0.4 - 0.2j, 0.3, 0.3, -0.25j, 0.25j]])
+    pos = inputs.positions(lat, 200, 34)
+    _, pg, _, _ = oracle.pw_eval(lat, mil, coef, pos)
+    sep, der = [], []
+    for n in (8, 16, 32):
+        tabs = oracle.derivative_tables(method, lat, mil, coef, (n, n, n))
+        sep.append(np.abs(oracle.bspline_eval_separate(tabs, lat, pos)[1] - pg).max())
+        der.append(np.abs(oracle.bspline_eval(tabs[0], lat, pos)[1] - pg).max())
+    assert sep[1] / sep[2] > 12
+    assert 6 < der[1] / der[2] < 12
+    assert sep[2] < der[2]
