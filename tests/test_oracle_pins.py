@@ -659,3 +659,30 @@ def test_separate_gradient_converges_faster_than_derivative(method):
     assert sep[1] / sep[2] > 12
     assert 6 < der[1] / der[2] < 12
     assert sep[2] < der[2]
+
+
+# ---------------------------------------------------------------------------
+# the paper's accuracy conclusions (Sec. III A, Fig. 1; Sec. IV) on the synthetic analogue
+# ---------------------------------------------------------------------------
+
+def test_fig1_conclusions_hold_for_the_oracle():
+    """At natural spacing for every cutoff: smoothing B-splines are more accurate than
+    interpolating splines, which are more accurate than Lagrange interpolation (values);
+    pp-splines and interpolating B-splines give the same values; separate approximations of
+    the gradient and Laplacian of the splines are more accurate than derivatives of the
+    spline."""
+    import fig1_analogue as f1
+    rows = f1.run((10.0, 20.0, 40.0), use_oracle=True, n_orb=8, n_pos=500)
+    for ecut in (10.0, 20.0, 40.0):
+        r = {x["row"]: x for x in rows if x["ecut"] == ecut}
+        assert r["smooth"]["value"] < r["interp"]["value"] < r["lagrange"]["value"]
+        assert r["pp"]["value"] == pytest.approx(r["interp"]["value"], rel=1e-10)
+        for m in ("smooth", "interp"):
+            assert r[m + "_sep"]["lap"] < r[m]["lap"]
+            assert r[m + "_sep"]["grad"] < r[m]["grad"]
+        assert r["smooth_sep"]["lap"] < r["interp_sep"]["lap"] < r["lagrange"]["lap"]
+        assert r["smooth_sep"]["grad"] < r["interp_sep"]["grad"] < r["lagrange"]["grad"]
+    # the errors fall as the cutoff (and the natural grid) grows
+    for lab in ("smooth", "interp", "lagrange"):
+        v = [x["value"] for x in rows if x["row"] == lab]
+        assert v[0] > v[1] > v[2]
