@@ -26,6 +26,8 @@ What the oracle computes, in the paper's order:
 6. Bloch orbitals at k != 0 (Sec. II): tables of the complex periodic part u_nk as
    interleaved real and imaginary functions, evaluated by the same C loops, then
    multiplied by exp(i k.r) with the product rule (bloch_combine).
+7. A consumer of the outputs (Sec. I): Slater matrices per walker and spin block, the
+   log-determinant, the local kinetic energy and the drift (slater_kinetic).
 
 Readings of the paper that the code depends on:
 * gamma_G (Eq. b-splinecoefficients) is a product over axes of
@@ -632,6 +634,45 @@ def bspline_adjoint(beta, lattice, pos, gv, gg, gl, beta_lap=None):
     if rc:
         raise RuntimeError("orc_bspline_adjoint failed")
     return dbeta, dbl, dpos
+
+
+# ---------------------------------------------------------------------------
+# Slater-determinant consumer of the orbital outputs (Sec. I)
+# ---------------------------------------------------------------------------
+# The trial wave function of Sec. I is Psi = J D with D a Slater determinant of the
+# single-particle orbitals; without the Jastrow factor and with the electrons split into
+# spin blocks, Psi = det A_up det A_dn, A_s[i][j] = phi_j(r_i) over the block's electrons i
+# and its first n_s orbitals j.  The kinetic part of the local energy E_L = H Psi / Psi is
+# T_L = -1/2 sum_i lap_i Psi / Psi, and by Jacobi's formula (row i of A replaced by its
+# Laplacian) lap_i det A / det A = sum_j (A^-1)_ji lap phi_j(r_i), so
+# T_L = -1/2 sum_s tr(A_s^-1 L_s) with L_s[i][j] = lap phi_j(r_i); likewise the drift
+# grad_i ln|Psi| = sum_j (A^-1)_ji grad phi_j(r_i).
+
+def slater_kinetic(val, grad, lap, n_walkers: int, n_elec: int, n_up: int):
+    """Per walker: (logdet [W] = ln|det A_up| + ln|det A_dn|, sign [W], kinetic [W] = T_L,
+    drift [W, n_elec, 3]) from orbital outputs val [W*n_elec, O], grad [W*n_elec, 3, O],
+    lap [W*n_elec, O] (walker-major positions; electrons 0..n_up-1 spin up).  numpy's
+    slogdet and inv serve as library steps."""
+    val = np.asarray(val, dtype=np.float64)
+    grad = np.asarray(grad, dtype=np.float64)
+    lap = np.asarray(lap, dtype=np.float64)
+    logdet = np.zeros(n_walkers)
+    sign = np.ones(n_walkers)
+    kin = np.zeros(n_walkers)
+    drift = np.zeros((n_walkers, n_elec, 3))
+    for w in range(n_walkers):
+        for e0, n in ((0, n_up), (n_up, n_elec - n_up)):
+            if n == 0:
+                continue
+            rows = slice(w * n_elec + e0, w * n_elec + e0 + n)
+            A = val[rows, :n]
+            sg, ld = np.linalg.slogdet(A)
+            logdet[w] += ld
+            sign[w] *= sg
+            Ainv = np.linalg.inv(A)
+            kin[w] += -0.5 * np.trace(Ainv @ lap[rows, :n])
+            drift[w, e0:e0 + n] = np.einsum("ji,iaj->ia", Ainv, grad[rows, :, :n])
+    return logdet, sign, kin, drift
 
 
 # ---------------------------------------------------------------------------
