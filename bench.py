@@ -321,6 +321,30 @@ def bench_bloch(args, dev, stream):
     return res
 
 
+def bench_consumer(args, dev, stream):
+    """The Slater-determinant consumer (qmcspl_slater_kinetic) on the MgO-like 64-atom
+    walker batch: 2048 walkers x (128 up + 128 down electrons), 128 x 128 FP64 Gauss-Jordan
+    inversions from the FP32 spline outputs, log-determinant, local kinetic energy and
+    drift.  value = walkers per second."""
+    import torch
+    from paper_1309_6250_gb300.api import OrbitalSplines, slater_kinetic
+    w = inputs.make_workload("c3")
+    spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32",
+                         separate_lap=True, device=dev)
+    v, g, l = spl.eval_vgl(torch.from_numpy(w.pos).to(dev))
+    spl.sync()
+    W, ne = w.cell.n_walkers, w.cell.n_elec
+    step = lambda: slater_kinetic(v, g, l, W, ne, ne // 2)
+    ms = time_steps(step, max(5, args.steps // 40), 2, torch, stream)
+    t = sum(ms) / len(ms) * 1e-3
+    n = ne // 2
+    flops = W * 2 * (2.0 * n ** 3)          # Gauss-Jordan: n^3 FMA per block
+    spl.close()
+    return {"workload": "MgO-like 64-atom batch: 2048 walkers x (128 + 128) electrons, 128 orbitals, "
+                        "FP32 spline outputs, FP64 inversion", "unit": "walkers/s", "value": W / t,
+            "ms_per_step": t * 1e3, "fp64_gflops": flops / t / 1e9}
+
+
 def bench_batched(args, dev, stream):
     """The uneven three-cell workload (Al-like 32-atom: 48 orbitals, 64^3, 512 x 96 e;
     Si-like 64-atom: 128 orbitals, 80^3, 1024 x 256 e; MgO-like 16-atom: 32 orbitals,
@@ -472,7 +496,7 @@ def run_ours(args):
                 "algorithmic_gbs": vb * evals_per_step / vk / 1e9,
                 "frac_of_hbm": vb * evals_per_step / vk / 1e9 / hbm}
 
-    batched = methods = backward = bloch = None
+    batched = methods = backward = bloch = consumer = None
     if not args.no_variants and rank == 0:
         del outs
         spl.close()
@@ -481,6 +505,7 @@ def run_ours(args):
         methods = bench_methods(args, dev, stream)
         backward = bench_backward(args, dev, stream)
         bloch = bench_bloch(args, dev, stream)
+        consumer = bench_consumer(args, dev, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -516,6 +541,7 @@ def run_ours(args):
         "methods_si8_48": methods,
         "backward_si64_72": backward,
         "bloch_mgo64_96": bloch,
+        "slater_consumer_mgo64": consumer,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -304,6 +304,40 @@ int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void
                             void* grad, void* lap, void* stream);
 
 /*
+ * qmcspl_slater_kinetic -- a consumer of the orbital outputs: the Slater matrices of a
+ * walker batch, their log-determinants, the local kinetic energy and the drift.
+ *
+ * Paper, Sec. I: the trial wave function is a Jastrow factor times a Slater determinant of
+ * the single-particle orbitals; the local energy is H Psi / Psi.  Here Psi = det A_up det A_dn
+ * (no Jastrow factor): for walker w, spin block s with electrons e0 .. e0 + n_s - 1 (e0 = 0,
+ * n_s = n_up for spin up; e0 = n_up, n_s = n_elec - n_up for spin down)
+ *     A_s[i][j] = val[w n_elec + e0 + i][j],   j < n_s (the first n_s orbitals),
+ * and, by Jacobi's formula,
+ *     logdet[w]  = ln|det A_up| + ln|det A_dn|,   sign[w] = sign(det A_up det A_dn)
+ *     kinetic[w] = -1/2 sum_s tr(A_s^-1 L_s),   L_s[i][j] = lap[w n_elec + e0 + i][j]
+ *                  (the kinetic part of the local energy, hartree)
+ *     drift[w][e][c] = sum_j (A_s^-1)_ji grad[w n_elec + e][c][j]   (d_c ln|Psi| for electron e)
+ * Determinant updates (one electron moved) are not provided.
+ *
+ *   val, grad, lap  device outputs of qmcspl_eval_vgl of a real-orbital handle for
+ *          P = n_walkers x n_elec positions ordered walker-major, layouts [P][n_orb],
+ *          [P][3][n_orb], [P][n_orb]; dtype 0 = double, 1 = float
+ *   n_orb  the output row length O, >= both block sizes
+ *   n_up   0 .. n_elec; each block at most QMCSPL_SLATER_MAX_BLOCK electrons
+ *   logdet, sign, kinetic  device double[n_walkers], each may be NULL (kinetic needs lap)
+ *   drift  device double[n_walkers][n_elec][3] or NULL (needs grad)
+ *   stream cudaStream_t; asynchronous
+ * The inversion is FP64 Gauss-Jordan elimination with row pivoting in shared memory, one
+ * thread block per walker.  An exactly singular block gives sign 0, logdet -inf and NaN
+ * kinetic energy and drift for that walker; nearly singular blocks lose accuracy as the
+ * condition number grows.
+ */
+#define QMCSPL_SLATER_MAX_BLOCK 160
+int qmcspl_slater_kinetic(const void* val, const void* grad, const void* lap, int dtype, long long n_walkers,
+                          int n_elec, int n_up, int n_orb, double* logdet, double* sign, double* kinetic,
+                          double* drift, void* stream);
+
+/*
  * qmcspl_profile / qmcspl_profile_read -- CUDA-event timing of the library's own kernels.
  *
  * Not in the paper.  While enabled, every qmcspl_eval_vgl on the handle records CUDA

@@ -236,3 +236,30 @@ def eval_batched(splines: Sequence[OrbitalSplines], positions: Sequence[torch.Te
     with torch.cuda.device(splines[0].device):
         _lib.check(lib.qmcspl_eval_batched(n, H, P, NP, V, G, L, _stream_handle(stream)))
     return outs
+
+
+def slater_kinetic(val: torch.Tensor, grad: Optional[torch.Tensor], lap: Optional[torch.Tensor],
+                   n_walkers: int, n_elec: int, n_up: int, want_drift: bool = True, stream=None):
+    """Slater-determinant consumer of eval_vgl outputs (walker-major positions, electrons
+    0..n_up-1 spin up): returns (logdet [W], sign [W], kinetic [W], drift [W, n_elec, 3] or
+    None), float64 tensors on the outputs' device."""
+    lib = _lib.load()
+    if val.dtype not in (torch.float32, torch.float64):
+        raise ValueError("real float32/float64 orbital outputs expected")
+    dtype = 0 if val.dtype == torch.float64 else 1
+    for t in (grad, lap):
+        if t is not None and (t.dtype != val.dtype or t.device != val.device):
+            raise ValueError("val, grad and lap must share dtype and device")
+    n_orb = val.shape[-1]
+    kw = dict(dtype=torch.float64, device=val.device)
+    logdet = torch.empty(n_walkers, **kw)
+    sign = torch.empty(n_walkers, **kw)
+    kin = torch.empty(n_walkers, **kw) if lap is not None else None
+    drift = torch.empty((n_walkers, n_elec, 3), **kw) if (want_drift and grad is not None) else None
+    c = lambda t: None if t is None else t.contiguous()
+    val, grad, lap = c(val), c(grad), c(lap)
+    with torch.cuda.device(val.device):
+        _lib.check(lib.qmcspl_slater_kinetic(_ptr(val), _ptr(grad), _ptr(lap), dtype, n_walkers, n_elec, n_up,
+                                             n_orb, _ptr(logdet), _ptr(sign), _ptr(kin), _ptr(drift),
+                                             _stream_handle(stream)))
+    return logdet, sign, kin, drift

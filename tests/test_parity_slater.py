@@ -1,0 +1,100 @@
+"""GPU Slater-determinant consumer (qmcspl_slater_kinetic) against the oracle's definition
+(numpy slogdet / inv) on the same orbital outputs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_6250_gb300 import inputs
+from gpu_helpers import NONORTHO, dev, splines
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def consumer(v, g, l, W, n_elec, n_up):
+    from paper_1309_6250_gb300.api import slater_kinetic
+    out = slater_kinetic(v, g, l, W, n_elec, n_up)
+    torch.cuda.synchronize()
+    return tuple(None if x is None else x.cpu().numpy() for x in out)
+
+
+def compare(got, ref, rel=1e-9):
+    ld, sg, kin, dr = got
+    rld, rsg, rkin, rdr = ref
+    np.testing.assert_array_equal(sg, rsg)
+    assert np.max(np.abs(ld - rld)) <= rel * max(1.0, np.max(np.abs(rld)))
+    assert oracle.relative_error(kin, rkin) < rel * 10
+    assert oracle.relative_error(dr, rdr) < rel * 10
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("n_elec,n_up,n_orb", [(13, 7, 9), (8, 0, 8), (2, 1, 3), (40, 20, 24)])
+def test_consumer_matches_oracle(storage, n_elec, n_up, n_orb):
+    dims = (12, 12, 12)
+    lat, mil, coef = inputs.random_cell(1300 + n_elec, dims, n_orb, 8.0, 6.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=True)
+    W = 6
+    pos = inputs.positions(lat, W * n_elec, 1301 + n_elec)
+    v, g, l = spl.eval_vgl(torch.from_numpy(pos).to(dev()))
+    spl.sync()
+    got = consumer(v, g, l, W, n_elec, n_up)
+    ref = oracle.slater_kinetic(v.double().cpu().numpy(), g.double().cpu().numpy(), l.double().cpu().numpy(),
+                                W, n_elec, n_up)
+    compare(got, ref)
+    spl.close()
+
+
+def test_consumer_largest_block_and_singular_walker():
+    """Blocks of QMCSPL_SLATER_MAX_BLOCK electrons; a walker whose up block has a zero row
+    is exactly singular: sign 0, logdet -inf, NaN kinetic energy and drift, the other
+    walkers unaffected."""
+    from paper_1309_6250_gb300 import _lib
+    n = _lib.SLATER_MAX_BLOCK
+    rng = np.random.default_rng(7)
+    W, n_elec = 3, 2 * n
+    val = rng.standard_normal((W * n_elec, n)) + 4.0 * np.tile(np.eye(n), (2 * W, 1))
+    grad = rng.standard_normal((W * n_elec, 3, n))
+    lap = rng.standard_normal((W * n_elec, n))
+    val[1 * n_elec + 5] = 0.0                      # walker 1, up block: zero row
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+    ld, sg, kin, dr = consumer(t(val), t(grad), t(lap), W, n_elec, n)
+    assert sg[1] == 0 and ld[1] == -np.inf and np.isnan(kin[1]) and np.all(np.isnan(dr[1]))
+    keep = [0, 2]
+    rows = np.concatenate([np.arange(w * n_elec, (w + 1) * n_elec) for w in keep])
+    ref = oracle.slater_kinetic(val[rows], grad[rows], lap[rows], 2, n_elec, n)
+    compare((ld[keep], sg[keep], kin[keep], dr[keep]), ref)
+
+
+def test_consumer_rejects_bad_arguments():
+    from paper_1309_6250_gb300 import _lib
+    from paper_1309_6250_gb300.api import slater_kinetic
+    v = torch.zeros((4, 3), dtype=torch.float64, device=dev())
+    with pytest.raises(_lib.QmcsplError):
+        slater_kinetic(v, None, v, 1, 4, 5)          # n_up > n_elec
+    with pytest.raises(_lib.QmcsplError):
+        slater_kinetic(v, None, v, 1, 4, 0)          # a block of 4 electrons, rows of 3 orbitals
+    big = torch.zeros((2 * 161, 161), dtype=torch.float64, device=dev())
+    with pytest.raises(_lib.QmcsplError) as ei:
+        slater_kinetic(big, None, big, 1, 2 * 161, 161)
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
+
+
+@pytest.mark.slow
+def test_consumer_c3_mgo64_full_batch():
+    """The MgO-like 64-atom workload as a QMC walker batch: 2048 walkers x 256 electrons,
+    128 up and 128 down, each block using all 128 orbitals of the FP32 smoothing spline
+    with the Laplacian table; every walker against the oracle."""
+    w = inputs.make_workload("c3")
+    spl = splines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32", separate_lap=True)
+    v, g, l = spl.eval_vgl(torch.from_numpy(w.pos).to(dev()))
+    spl.sync()
+    W, n_elec = w.cell.n_walkers, w.cell.n_elec
+    got = consumer(v, g, l, W, n_elec, n_elec // 2)
+    sample = np.arange(0, W, 7)
+    rows = np.concatenate([np.arange(s * n_elec, (s + 1) * n_elec) for s in sample])
+    vr = v.cpu().numpy()[rows].astype(np.float64)
+    gr = g.cpu().numpy()[rows].astype(np.float64)
+    lr = l.cpu().numpy()[rows].astype(np.float64)
+    ref = oracle.slater_kinetic(vr, gr, lr, len(sample), n_elec, n_elec // 2)
+    compare(tuple(x[sample] for x in got), ref, rel=1e-8)
+    spl.close()
