@@ -28,6 +28,9 @@ What the oracle computes, in the paper's order:
    multiplied by exp(i k.r) with the product rule (bloch_combine).
 7. A consumer of the outputs (Sec. I): Slater matrices per walker and spin block, the
    log-determinant, the local kinetic energy and the drift (slater_kinetic).
+8. Interpolating B-splines of any odd degree on uniform or non-uniform periodic grids: the
+   Appendix's recurrence for the basis, dense periodic interpolation matrices, brute-force
+   evaluation (general_interp_tables, general_eval).
 
 Readings of the paper that the code depends on:
 * gamma_G (Eq. b-splinecoefficients) is a product over axes of
@@ -634,6 +637,150 @@ def bspline_adjoint(beta, lattice, pos, gv, gg, gl, beta_lap=None):
     if rc:
         raise RuntimeError("orc_bspline_adjoint failed")
     return dbeta, dbl, dpos
+
+
+# ---------------------------------------------------------------------------
+# interpolating B-splines of any odd degree on uniform or non-uniform periodic grids
+# (Sec. II "Common features" and "Grid"; Appendix, the B-spline recurrence)
+# ---------------------------------------------------------------------------
+# The recurrence of the Appendix: b_j^0 = C on [x_j, x_{j+1}), and
+#     b_j^k(x) = w_j^k(x) b_j^{k-1}(x) + (1 - w_{j+1}^k(x)) b_{j+1}^{k-1}(x),
+#     w_j^k(x) = (x - x_j) / (x_{j+k} - x_j),
+# so b_j^k lives on (x_j, x_{j+k+1}); the basis function of grid point m is b_j^k with
+# j = m - floor((k+1)/2) (centred on x_m for odd k).  The knots of a periodic axis are the
+# grid points x_0 < ... < x_{N-1} in [0, 1) extended by x_{j+N} = x_j + 1.  C is the degree-0
+# constant; the paper takes C = 3/2 so that the cubic basis peaks at one, and for degree n
+# the same rule gives C_n = 1 / B_n(0) with B_n the unit-sum centred B-spline on unit spacing.
+
+def periodic_knot(knots: np.ndarray, j):
+    """x_j of the periodic extension of the grid points knots[0..N-1] in [0, 1)."""
+    j = np.asarray(j)
+    n = knots.shape[0]
+    return knots[np.mod(j, n)] + np.floor_divide(j, n)
+
+
+def recurrence_basis(knots: np.ndarray, k: int, j, x: float, C: float):
+    """b_j^k(x) for an array of start indices j, by the recurrence written out level by level."""
+    j = np.asarray(j)
+    # level 0 on the start indices j, j+1, ..., j+k (all that level k needs)
+    js = j[..., None] + np.arange(k + 1)
+    b = np.where((periodic_knot(knots, js) <= x) & (x < periodic_knot(knots, js + 1)), C, 0.0)
+    for kk in range(1, k + 1):
+        jj = js[..., : k + 1 - kk]
+        xj, xjk = periodic_knot(knots, jj), periodic_knot(knots, jj + kk)
+        xj1, xj1k = periodic_knot(knots, jj + 1), periodic_knot(knots, jj + 1 + kk)
+        w = (x - xj) / (xjk - xj)
+        w1 = (x - xj1) / (xj1k - xj1)
+        b = w * b[..., :-1] + (1.0 - w1) * b[..., 1:]
+    return b[..., 0]
+
+
+def recurrence_basis_derivative(knots: np.ndarray, k: int, j, x: float, C: float, order: int):
+    """d^order/dx^order b_j^k(x): d/dx b_j^k = k (b_j^{k-1}/(x_{j+k}-x_j) - b_{j+1}^{k-1}/(x_{j+k+1}-x_{j+1}))."""
+    if order == 0:
+        return recurrence_basis(knots, k, j, x, C)
+    j = np.asarray(j)
+    if order > k:        # piecewise constant after k derivatives: zero between knots
+        return np.zeros(j.shape)
+    a = k / (periodic_knot(knots, j + k) - periodic_knot(knots, j))
+    b = k / (periodic_knot(knots, j + k + 1) - periodic_knot(knots, j + 1))
+    return (a * recurrence_basis_derivative(knots, k - 1, j, x, C, order - 1) -
+            b * recurrence_basis_derivative(knots, k - 1, j + 1, x, C, order - 1))
+
+
+def degree_constant(degree: int) -> float:
+    """C_n = 1 / B_n(0): the degree-0 constant that makes the centred basis peak at one."""
+    n = 64
+    pts = np.arange(n) / n           # a uniform periodic axis; the recurrence is scale free
+    j0 = -((degree + 1) // 2)        # the basis of grid point 0, evaluated at its centre
+    return 1.0 / float(recurrence_basis(pts, degree, np.array([j0]), 0.0, 1.0)[0])
+
+
+def axis_points(n: int, knots=None) -> np.ndarray:
+    """Grid points of one periodic axis in reduced coordinates: l/N, or the given knots."""
+    return np.arange(n) / n if knots is None else np.asarray(knots, dtype=np.float64)
+
+
+def periodic_basis_matrix(points: np.ndarray, degree: int, x: np.ndarray, C: float, order: int = 0):
+    """M[p][m] = sum over periodic images of (d/dx)^order of the basis of grid point m at x[p]."""
+    n = points.shape[0]
+    M = np.zeros((x.shape[0], n))
+    half = (degree + 1) // 2
+    j = np.arange(n)[None, :] + n * np.array([-1, 0, 1])[:, None] - half      # [image, m]
+    for p, xv in enumerate(x):
+        M[p] = recurrence_basis_derivative(points, degree, j, xv, C, order).sum(axis=0)
+    return M
+
+
+def general_grid_values(lattice, miller, coef, points, what: str = "value", kpoint=None):
+    """Planewave sum (or its Laplacian, or the periodic part u of a Bloch orbital) at the
+    tensor grid of per-axis points, separable: [N1, N2, N3, O] real, or interleaved for kpoint."""
+    c = np.asarray(coef, dtype=np.complex128)
+    if what == "lap":
+        if kpoint is None:
+            G = g_vectors(lattice, miller)
+            c = c * (-np.einsum("ij,ij->i", G, G))[None, :]
+        else:
+            c = c * bloch_derivative_weights(lattice, miller, kpoint, "lap")[None, :]
+    E = [np.exp(2j * np.pi * np.outer(points[a], miller[:, a].astype(np.float64))) for a in range(3)]
+    f = np.einsum("ag,bg,cg,og->abco", E[0], E[1], E[2], c)
+    return interleave(f) if kpoint is not None else np.ascontiguousarray(f.real)
+
+
+def general_interp_tables(lattice, miller, coef, dims, degree: int = 3, knots=(None, None, None),
+                          laplacian: bool = False, kpoint=None):
+    """(beta, beta_lap or None): sum_lmn B^x_il B^y_jm B^z_kn beta_lmn = phi(x_i, y_j, z_k) with the
+    basis of the recurrence (C = 3/2 for cubic, C_n otherwise), solved in three stages with dense
+    periodic matrices (numpy.linalg.solve as the library step)."""
+    C = 1.5 if degree == 3 else degree_constant(degree)
+    pts = [axis_points(int(dims[a]), knots[a]) for a in range(3)]
+    mats = [periodic_basis_matrix(pts[a], degree, pts[a], C) for a in range(3)]
+
+    def solve(values):
+        beta = np.asarray(values, dtype=np.float64)
+        for a in range(3):
+            beta = np.moveaxis(np.tensordot(np.linalg.inv(mats[a]), np.moveaxis(beta, a, 0), axes=1), 0, a)
+        return np.ascontiguousarray(beta)
+
+    beta = solve(general_grid_values(lattice, miller, coef, pts, "value", kpoint))
+    lap = solve(general_grid_values(lattice, miller, coef, pts, "lap", kpoint)) if laplacian else None
+    return beta, lap
+
+
+def general_eval(beta, lattice, pos, degree: int = 3, knots=(None, None, None), beta_lap=None):
+    """Value, Cartesian gradient, Laplacian of the spline sum_lmn b_l(x) b_m(y) b_n(z) beta_lmn,
+    every basis function of the periodic family evaluated by the recurrence (brute force)."""
+    beta = np.asarray(beta, dtype=np.float64)
+    dims = beta.shape[:3]
+    C = 1.5 if degree == 3 else degree_constant(degree)
+    pts = [axis_points(int(dims[a]), knots[a]) for a in range(3)]
+    ainv = np.linalg.inv(np.asarray(lattice, dtype=np.float64))
+    pos = _f64(pos).reshape(-1, 3)
+    s = pos @ ainv.T
+    s = s - np.floor(s)
+    P, O = pos.shape[0], beta.shape[3]
+    val, grad, lap = np.zeros((P, O)), np.zeros((P, 3, O)), np.zeros((P, O))
+    metric = ainv @ ainv.T                         # (a^-1 a^-T)_ij
+    for p in range(P):
+        B = [[periodic_basis_matrix(pts[a], degree, s[p, a:a + 1], C, d)[0] for d in range(3)]
+             for a in range(3)]
+        def tp(dx, dy, dz, tab=beta):
+            return np.einsum("l,m,n,lmno->o", B[0][dx], B[1][dy], B[2][dz], tab)
+        val[p] = tp(0, 0, 0)
+        ds = np.stack([tp(1, 0, 0), tp(0, 1, 0), tp(0, 0, 1)])          # d/ds_i
+        grad[p] = ainv.T @ ds
+        if beta_lap is not None:
+            lap[p] = tp(0, 0, 0, np.asarray(beta_lap, dtype=np.float64))
+        else:
+            H = np.zeros((3, 3, O))
+            for i in range(3):
+                for j in range(3):
+                    o = [0, 0, 0]
+                    o[i] += 1
+                    o[j] += 1
+                    H[i, j] = tp(*o)
+            lap[p] = np.einsum("ij,ijo->o", metric, H)
+    return val, grad, lap
 
 
 # ---------------------------------------------------------------------------

@@ -222,5 +222,14 @@ def make_bloch_workload(key: str, kpoint, n_pos: Optional[int] = None,
     return Workload(cell, lat, mil, coef, pos)
 
 
+def graded_knots(n: int, amplitude: float = 0.5, phase: float = 0.0) -> np.ndarray:
+    """Non-uniform periodic grid points of one axis in reduced coordinates [0, 1):
+    x_l = u + amplitude/(2 pi) (sin(2 pi (u + phase)) - sin(2 pi phase)), u = l/n, strictly
+    increasing for |amplitude| < 1 (spacing varies by a factor (1+a)/(1-a) along the axis)."""
+    u = np.arange(n) / n
+    x = u + amplitude / (2.0 * np.pi) * (np.sin(2.0 * np.pi * (u + phase)) - np.sin(2.0 * np.pi * phase))
+    return np.ascontiguousarray(x - np.floor(x))
+
+
 def all_cells() -> List[str]:
     return list(CELLS.keys())

@@ -1,0 +1,178 @@
+"""Pins of the oracle's interpolating B-splines of any odd degree on uniform and non-uniform
+periodic grids (Sec. II "Common features", "Grid"; the Appendix's recurrence).
+
+Checks: the recurrence against the paper's printed cubic forms, the textbook central values
+of the cardinal B-splines, partition of unity, derivatives by finite differences, exact
+reproduction of the grid values, the degree-3 uniform case against the paper's cubic path,
+trilinear interpolation for degree 1, convergence orders and continuity across knots."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1309_6250_gb300 import inputs
+
+NONORTHO = np.array([[5.0, 1.0, 0.5],
+                     [0.0, 6.0, 0.3],
+                     [0.0, 0.0, 7.0]])
+
+
+def b_centred(xi):
+    """Eq. (bsplinegridcenteredbasis)."""
+    a = abs(xi)
+    if a < 1:
+        return 0.75 * a ** 3 - 1.5 * a ** 2 + 1
+    if a < 2:
+        return 0.25 * (2 - a) ** 3
+    return 0.0
+
+
+def test_recurrence_reproduces_the_printed_cubic_basis():
+    """With C = 3/2 the recurrence gives Eq. (bsplinegridcenteredbasis) and the four
+    polynomials of Eq. (b-splinebasis) on a uniform grid."""
+    n = 16
+    pts = np.arange(n) / n
+    for xi in np.linspace(-2.5, 2.5, 41):
+        x = xi / n                                  # grid point 0, grid units -> reduced
+        got = oracle.recurrence_basis(pts, 3, np.array([-2]), x, 1.5)[0]
+        assert got == pytest.approx(b_centred(xi), abs=1e-13)
+    for t in (0.0, 0.13, 0.5, 0.77, 0.999):
+        x = (5 + t) / n
+        w = [oracle.recurrence_basis(pts, 3, np.array([5 + o - 2]), x, 1.5)[0] for o in (-1, 0, 1, 2)]
+        np.testing.assert_allclose(w, oracle.basis("bspline", t), atol=1e-13)
+
+
+def test_degree_constants_are_the_cardinal_central_values():
+    """C_n = 1/B_n(0) with the textbook central values of the unit cardinal B-splines:
+    B_1(0) = 1, B_3(0) = 2/3, B_5(0) = 11/20, B_7(0) = 151/315."""
+    for n, b0 in ((1, 1.0), (3, 2.0 / 3.0), (5, 11.0 / 20.0), (7, 151.0 / 315.0)):
+        assert oracle.degree_constant(n) == pytest.approx(1.0 / b0, rel=1e-13)
+
+
+@pytest.mark.parametrize("degree", [1, 3, 5, 7])
+@pytest.mark.parametrize("uniform", [True, False])
+def test_partition_of_unity_and_derivatives(degree, uniform):
+    """The periodic family sums to C everywhere; the derivative formula agrees with central
+    differences of the recurrence (first and second derivatives)."""
+    if not uniform and degree != 3:
+        pytest.skip("non-uniform grids are cubic")
+    n = 11
+    pts = np.arange(n) / n if uniform else inputs.graded_knots(n, 0.6, 0.1)
+    C = 1.5 if degree == 3 else oracle.degree_constant(degree)
+    rng = np.random.default_rng(degree)
+    xs = rng.uniform(0, 1, 25)
+    M = oracle.periodic_basis_matrix(pts, degree, xs, C)
+    np.testing.assert_allclose(M.sum(axis=1), C, rtol=1e-13)
+    h = 1e-6
+    d1 = oracle.periodic_basis_matrix(pts, degree, xs, C, 1)
+    fd1 = (oracle.periodic_basis_matrix(pts, degree, xs + h, C) -
+           oracle.periodic_basis_matrix(pts, degree, xs - h, C)) / (2 * h)
+    np.testing.assert_allclose(d1, fd1, atol=1e-6 * max(1.0, np.abs(d1).max()))
+    if degree >= 3:
+        d2 = oracle.periodic_basis_matrix(pts, degree, xs, C, 2)
+        fd2 = (oracle.periodic_basis_matrix(pts, degree, xs + h, C, 1) -
+               oracle.periodic_basis_matrix(pts, degree, xs - h, C, 1)) / (2 * h)
+        np.testing.assert_allclose(d2, fd2, atol=1e-5 * max(1.0, np.abs(d2).max()))
+
+
+@pytest.mark.parametrize("degree,graded", [(1, False), (3, False), (5, False), (7, False), (3, True)])
+def test_interpolation_reproduces_grid_values(degree, graded):
+    dims = (9, 10, 11)
+    knots = tuple(inputs.graded_knots(d, 0.5, 0.2 * a) for a, d in enumerate(dims)) if graded else (None,) * 3
+    lat, mil, coef = inputs.random_cell(40 + degree, dims, 2, 4.0, 4.0, NONORTHO)
+    beta, _ = oracle.general_interp_tables(lat, mil, coef, dims, degree, knots)
+    pts = [oracle.axis_points(dims[a], knots[a]) for a in range(3)]
+    rng = np.random.default_rng(degree)
+    idx = rng.integers(0, dims, size=(12, 3))
+    s = np.stack([pts[a][idx[:, a]] for a in range(3)], axis=1)
+    pos = (s + np.array([1.0, -2.0, 0.0])) @ lat.T
+    v, _, _ = oracle.general_eval(beta, lat, pos, degree, knots)
+    pv, _, _, _ = oracle.pw_eval(lat, mil, coef, pos)
+    assert oracle.relative_error(v, pv) < 1e-12
+
+
+def test_cubic_uniform_equals_the_paper_path():
+    """Degree 3 on a uniform grid with C = 3/2 is the paper's interpolating B-spline: the same
+    coefficients and the same value, gradient and Laplacian (both Laplacian modes)."""
+    dims = (8, 9, 10)
+    lat, mil, coef = inputs.random_cell(50, dims, 3, 5.0, 4.0, NONORTHO)
+    beta, blap = oracle.general_interp_tables(lat, mil, coef, dims, 3, laplacian=True)
+    rb, rl = oracle.interpolating_tables(lat, mil, coef, dims, laplacian=True)
+    assert oracle.relative_error(beta, rb) < 1e-12 and oracle.relative_error(blap, rl) < 1e-12
+    pos = inputs.positions(lat, 15, 51, -1, 2)
+    for bl in (None, blap):
+        got = oracle.general_eval(beta, lat, pos, 3, beta_lap=bl)
+        ref = oracle.bspline_eval(rb, lat, pos, beta_lap=None if bl is None else rl)
+        for g, r in zip(got, ref):
+            assert oracle.relative_error(g, r) < 1e-12
+
+
+def test_degree_one_is_trilinear_interpolation():
+    dims = (5, 6, 7)
+    rng = np.random.default_rng(52)
+    f = rng.standard_normal(dims + (2,))
+    lat = np.diag([5.0, 6.0, 7.0])
+    # linear interpolation: the coefficients are the grid values (C_1 = 1, B is the identity)
+    pos = rng.uniform(0, 1, (10, 3)) * np.array([5.0, 6.0, 7.0])
+    v, g, _ = oracle.general_eval(f, lat, pos, 1)
+    for p in range(10):
+        u = pos[p] / np.array([5.0, 6.0, 7.0]) * np.array(dims)
+        i0 = np.floor(u).astype(int)
+        t = u - i0
+        ref = 0.0
+        for dx in (0, 1):
+            for dy in (0, 1):
+                for dz in (0, 1):
+                    w = (t[0] if dx else 1 - t[0]) * (t[1] if dy else 1 - t[1]) * (t[2] if dz else 1 - t[2])
+                    ref = ref + w * f[(i0[0] + dx) % 5, (i0[1] + dy) % 6, (i0[2] + dz) % 7]
+        np.testing.assert_allclose(v[p], ref, atol=1e-13)
+
+
+@pytest.mark.parametrize("degree,graded,ratio", [(1, False, 3.0), (3, False, 12.0), (5, False, 40.0),
+                                                 (3, True, 11.0)])
+def test_convergence_order(degree, graded, ratio):
+    """Refining the grid at a fixed planewave set converges the value as h^(n+1) (Sec. III A
+    footnote for the cubic; the order of a degree-n spline in general), also on graded grids."""
+    lat = np.eye(3) * 5.0
+    mil = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 1], [0, -1, -1], [1, -1, 0], [-1, 1, 0]], dtype=np.int32)
+    coef = np.array([[0.4 + 0.2j, 0.4 - 0.2j, 0.3, 0.3, -0.25j, 0.25j]])
+    pos = inputs.positions(lat, 40, 53)
+    pv, _, _, _ = oracle.pw_eval(lat, mil, coef, pos)
+    errs = []
+    for n in (12, 24):
+        knots = tuple(inputs.graded_knots(n, 0.4, 0.1 * a) for a in range(3)) if graded else (None,) * 3
+        beta, _ = oracle.general_interp_tables(lat, mil, coef, (n, n, n), degree, knots)
+        v, _, _ = oracle.general_eval(beta, lat, pos, degree, knots)
+        errs.append(np.abs(v - pv).max())
+    assert errs[0] / errs[1] > ratio
+
+
+def test_graded_cubic_is_C2_across_knots_and_chain_rule():
+    """Splines of degree n are C^(n-1) (Sec. II): value, gradient and Laplacian agree on both
+    sides of a non-uniform knot; the Cartesian gradient and Laplacian are the derivatives of
+    the value (non-orthogonal cell)."""
+    dims = (7, 8, 9)
+    knots = tuple(inputs.graded_knots(d, 0.5, 0.15 * a) for a, d in enumerate(dims))
+    rng = np.random.default_rng(54)
+    beta = rng.standard_normal(dims + (2,))
+    ainv = np.linalg.inv(NONORTHO)
+    s0 = np.array([knots[0][3], 0.41, 0.77])
+    eps = 1e-9
+    lo = oracle.general_eval(beta, NONORTHO, (s0 - [eps, 0, 0]) @ NONORTHO.T, 3, knots)
+    hi = oracle.general_eval(beta, NONORTHO, (s0 + [eps, 0, 0]) @ NONORTHO.T, 3, knots)
+    for a, b in zip(lo, hi):
+        assert np.abs(a - b).max() < 1e-5 * max(1.0, np.abs(a).max())
+    pos = inputs.positions(NONORTHO, 6, 55)
+    v, g, l = oracle.general_eval(beta, NONORTHO, pos, 3, knots)
+    h = 1e-5
+    fd_g, fd_l = np.zeros_like(g), np.zeros_like(l)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        vp, gp, _ = oracle.general_eval(beta, NONORTHO, pos + e, 3, knots)
+        vm, gm, _ = oracle.general_eval(beta, NONORTHO, pos - e, 3, knots)
+        fd_g[:, a] = (vp - vm) / (2 * h)
+        fd_l += (gp[:, a] - gm[:, a]) / (2 * h)
+    assert oracle.relative_error(g, fd_g) < 1e-7
+    assert oracle.relative_error(l, fd_l) < 1e-5
