@@ -119,6 +119,8 @@ typedef struct {
                                 2 n_orb real functions per row: Re u_0, Im u_0, Re u_1, ...) */
     double kpoint[3];        /* k in units of the reciprocal lattice vectors (bloch = 1) */
     int separate_grad;       /* 1: B-spline with separate gradient tables */
+    int degree;              /* B-spline degree (3 unless created by qmcspl_create_grid) */
+    int nonuniform;          /* 1: per-axis grid points (qmcspl_create_grid) */
 } qmcspl_info_t;
 
 /*
@@ -154,6 +156,39 @@ typedef struct {
 int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int n_pw,
                   const int* miller, int n_orb, const double* coef, const qmcspl_opts* opts,
                   void* stream);
+
+/*
+ * qmcspl_create_grid -- qmcspl_create for interpolating B-splines of another odd degree or
+ * on a non-uniform grid.
+ *
+ * Paper: Sec. II, "Common features" (each method may use polynomials of any order n; the
+ * paper uses cubics) and "Grid" (uniform or non-uniform grids); Appendix, the B-spline
+ * recurrence and "Interpolating B-spline coefficients" (interpolation needs no evenly
+ * spaced grid).  The basis of grid point m is the recurrence's b_j^n centred on x_m, with
+ * the degree-0 constant C_n = 1 / B_n(0) so that it peaks at one (C_3 = 3/2 as in the paper;
+ * C_1 = 1, C_5 = 20/11, C_7 = 315/151).  The coefficients interpolate phi (and, with
+ * separate_lap, lap phi) at every grid point.
+ *
+ *   grid->degree    1, 3, 5 or 7 (0 = 3).  Uniform grids: the periodic system is solved
+ *                   exactly in Fourier space (its symbol sum_j C_n B_n(j) e^{i j th}).
+ *   grid->knots[a]  NULL for a uniform axis, else host double[dims[a]]: the grid points of
+ *                   axis a in reduced coordinates, strictly increasing in [0, 1); either
+ *                   all three axes or none.  Non-uniform grids are cubic; the planewave band
+ *                   must fit the grid (dims[a] >= 2 max|n_a| + 1, else QMCSPL_ERR_ARG) and
+ *                   the cyclic tridiagonal system is solved along each axis in FP64.
+ * Other arguments as qmcspl_create; opts->method must be QMCSPL_BSPLINE_INTERP, storage
+ * F64, F32 or BF16, separate_grad 0 (else QMCSPL_ERR_UNSUPPORTED); Bloch orbitals are
+ * accepted.  dims[a] >= degree + 1.  Evaluation (qmcspl_eval_vgl, _host, _noalloc) has the
+ * same outputs; the stencil is (n + 1)^3 points.  Backward and batched evaluation are not
+ * available for these handles (QMCSPL_ERR_UNSUPPORTED).  grid = NULL is qmcspl_create.
+ */
+typedef struct {
+    int degree;
+    const double* knots[3];
+} qmcspl_grid_opts;
+int qmcspl_create_grid(qmcspl_t* out, const double lattice[9], const int dims[3], int n_pw,
+                       const int* miller, int n_orb, const double* coef, const qmcspl_opts* opts,
+                       const qmcspl_grid_opts* grid, void* stream);
 
 /* qmcspl_destroy -- synchronise the device and free the handle and its tables.
  * NULL is accepted. */

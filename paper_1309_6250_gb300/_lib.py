@@ -61,7 +61,12 @@ class Info(ctypes.Structure):
                 ("n_tables", ctypes.c_int), ("entries_per_point", ctypes.c_int),
                 ("rows_z", ctypes.c_int), ("lanes", ctypes.c_int), ("tiles", ctypes.c_int),
                 ("table_bytes", ctypes.c_longlong), ("n_pw", ctypes.c_longlong),
-                ("bloch", ctypes.c_int), ("kpoint", ctypes.c_double * 3), ("separate_grad", ctypes.c_int)]
+                ("bloch", ctypes.c_int), ("kpoint", ctypes.c_double * 3), ("separate_grad", ctypes.c_int),
+                ("degree", ctypes.c_int), ("nonuniform", ctypes.c_int)]
+
+
+class GridOpts(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int), ("knots", ctypes.c_void_p * 3)]
 
 
 _lock = threading.Lock()
@@ -74,6 +79,8 @@ I = ctypes.c_int
 # (name, restype, argtypes) of every entry point of include/qmcspl.h
 PROTOTYPES = [
     ("qmcspl_create", I, [ctypes.POINTER(VP), VP, VP, I, VP, I, VP, ctypes.POINTER(Opts), VP]),
+    ("qmcspl_create_grid", I, [ctypes.POINTER(VP), VP, VP, I, VP, I, VP, ctypes.POINTER(Opts),
+                               ctypes.POINTER(GridOpts), VP]),
     ("qmcspl_destroy", I, [VP]),
     ("qmcspl_info", I, [VP, ctypes.POINTER(Info)]),
     ("qmcspl_eval_vgl", I, [VP, VP, LL, VP, VP, VP, VP]),

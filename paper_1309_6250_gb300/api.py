@@ -43,7 +43,7 @@ class OrbitalSplines:
                  storage: str = "f32", separate_lap: bool = True,
                  device: Optional[torch.device] = None,
                  stream: Optional[torch.cuda.Stream] = None, lanes: int = 0, kpoint=None,
-                 separate_grad: bool = False):
+                 separate_grad: bool = False, degree: int = 3, knots=None):
         self.lib = _lib.load()
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         lat = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(3, 3))
@@ -62,11 +62,19 @@ class OrbitalSplines:
         opts = _lib.Opts(_lib.METHODS[method], _lib.STORAGE[storage], int(bool(separate_lap)), int(lanes),
                          int(bool(separate_grad)), int(bloch), kp)
         h = ctypes.c_void_p()
+        grid = None
+        kn = None
+        if degree != 3 or knots is not None:
+            kn = [None if knots is None else np.ascontiguousarray(np.asarray(knots[a], dtype=np.float64))
+                  for a in range(3)]
+            grid = _lib.GridOpts(int(degree), (ctypes.c_void_p * 3)(
+                *[None if k is None else k.ctypes.data for k in kn]))
         with torch.cuda.device(self.device):
             st = _stream_handle(stream)
-            _lib.check(self.lib.qmcspl_create(ctypes.byref(h), lat.ctypes.data, dm.ctypes.data, n_pw,
-                                              mil.ctypes.data, n_orb, craw.ctypes.data,
-                                              ctypes.byref(opts), st))
+            _lib.check(self.lib.qmcspl_create_grid(ctypes.byref(h), lat.ctypes.data, dm.ctypes.data, n_pw,
+                                                   mil.ctypes.data, n_orb, craw.ctypes.data,
+                                                   ctypes.byref(opts), None if grid is None else ctypes.byref(grid),
+                                                   st))
         self.handle = h
         self.method = method
         self.storage = storage

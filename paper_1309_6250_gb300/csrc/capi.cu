@@ -10,6 +10,7 @@
 #include <string>
 #include <unordered_map>
 
+#include "general_basis.cuh"
 #include "qmcspl_internal.cuh"
 
 namespace qmcspl {
@@ -72,7 +73,9 @@ void fill_eval_args(const Handle* h, EvalArgs* a)
     for (int i = 0; i < 3; ++i) {
         a->kc[i] = h->kcart[i];
         a->kcf[i] = (float)h->kcart[i];
+        a->knots[i] = h->nonuniform ? h->d_knots + (size_t)i * kMaxDim : nullptr;
     }
+    a->cdeg = degree_constant(h->degree);
 }
 
 bool inv3(const double m[9], double out[9]);
@@ -86,14 +89,18 @@ bool handle_geometry(Handle* h, const double lattice[9])
     if (!inv3(lattice, ainv)) return false;
     std::memcpy(h->lattice, lattice, sizeof(h->lattice));
     std::memcpy(h->ainv, ainv, sizeof(h->ainv));
+    // uniform grids differentiate with respect to u = N s (factor N_i), non-uniform ones
+    // with respect to s itself
+    double nf[3];
+    for (int i = 0; i < 3; ++i) nf[i] = h->nonuniform ? 1.0 : (double)h->dims[i];
     for (int a = 0; a < 3; ++a)
-        for (int i = 0; i < 3; ++i) h->mg[3 * a + i] = h->dims[i] * ainv[3 * i + a];
+        for (int i = 0; i < 3; ++i) h->mg[3 * a + i] = nf[i] * ainv[3 * i + a];
     double M[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
             double s = 0.0;
             for (int a = 0; a < 3; ++a) s += ainv[3 * i + a] * ainv[3 * j + a];
-            M[3 * i + j] = (double)h->dims[i] * h->dims[j] * s;
+            M[3 * i + j] = nf[i] * nf[j] * s;
         }
     h->ml[0] = M[0];
     h->ml[1] = M[4];
@@ -216,6 +223,7 @@ void free_handle(Handle* h)
     if (h->ord_count) cudaFree(h->ord_count);
     if (h->ord_rec) cudaFree(h->ord_rec);
     if (h->ord_phase) cudaFree(h->ord_phase);
+    if (h->d_knots) cudaFree(h->d_knots);
     if (h->prof_ev) {
         for (int i = 0; i < 3 * kProfCalls; ++i) cudaEventDestroy(h->prof_ev[i]);
         delete[] h->prof_ev;
@@ -252,6 +260,13 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
                   const int* miller, int n_orb, const double* coef, const qmcspl_opts* opts,
                   void* stream)
 {
+    return qmcspl_create_grid(out, lattice, dims, n_pw, miller, n_orb, coef, opts, nullptr, stream);
+}
+
+int qmcspl_create_grid(qmcspl_t* out, const double lattice[9], const int dims[3], int n_pw,
+                       const int* miller, int n_orb, const double* coef, const qmcspl_opts* opts,
+                       const qmcspl_grid_opts* grid, void* stream)
+{
     g_err.clear();
     if (!out) return set_error(QMCSPL_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -285,6 +300,32 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
         for (int i = 0; i < 3; ++i)
             if (!std::isfinite(opts->kpoint[i])) return set_error(QMCSPL_ERR_ARG, "non-finite kpoint");
     if (opts->bloch && n_orb > (1 << 29)) return set_error(QMCSPL_ERR_ARG, "n_orb too large");
+    int degree = 3;
+    bool nonuni = false;
+    if (grid) {
+        degree = grid->degree == 0 ? 3 : grid->degree;
+        if (degree != 1 && degree != 3 && degree != 5 && degree != 7)
+            return set_error(QMCSPL_ERR_ARG, "degree must be 1, 3, 5 or 7");
+        for (int a = 0; a < 3; ++a) nonuni = nonuni || grid->knots[a] != nullptr;
+        if (nonuni && degree != 3) return set_error(QMCSPL_ERR_UNSUPPORTED, "non-uniform grids are cubic");
+        if ((degree != 3 || nonuni) &&
+            (opts->method != QMCSPL_BSPLINE_INTERP || opts->storage == QMCSPL_DF64 || opts->separate_grad))
+            return set_error(QMCSPL_ERR_UNSUPPORTED,
+                             "other degrees and non-uniform grids are for interpolating B-splines "
+                             "(f64, f32 or bf16 tables, no separate gradient tables)");
+        for (int a = 0; a < 3; ++a) {
+            if (dims[a] < degree + 1) return set_error(QMCSPL_ERR_ARG, "grid too small for the degree");
+            const double* k = grid->knots[a];
+            if (!nonuni) continue;
+            if (!k) return set_error(QMCSPL_ERR_ARG, "non-uniform grids need the points of all three axes");
+            for (int i = 0; i < dims[a]; ++i) {
+                if (!std::isfinite(k[i]) || k[i] < 0.0 || k[i] >= 1.0)
+                    return set_error(QMCSPL_ERR_ARG, "grid points must lie in [0, 1)");
+                if (i > 0 && !(k[i] > k[i - 1]))
+                    return set_error(QMCSPL_ERR_ARG, "grid points must be strictly increasing");
+            }
+        }
+    }
     int rc = check_planewaves(n_pw, miller, n_orb, coef, opts->bloch == 0);
     if (rc != QMCSPL_OK) return rc;
 
@@ -296,6 +337,12 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
     const bool bspline = h->method == QMCSPL_BSPLINE_SMOOTH || h->method == QMCSPL_BSPLINE_INTERP;
     h->separate_lap = bspline ? (opts->separate_lap != 0) : (h->method == QMCSPL_LAGRANGE);
     h->separate_grad = bspline ? (opts->separate_grad != 0) : (h->method == QMCSPL_LAGRANGE);
+    h->degree = degree;
+    h->nonuniform = nonuni ? 1 : 0;
+    h->zshift = (h->method == QMCSPL_PPSPLINE) ? 0 : (degree - 1) / 2;
+    if (nonuni)
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < dims[a]; ++i) h->knots[a][i] = grid->knots[a][i];
     for (int a = 0; a < 3; ++a) h->dims[a] = dims[a];
     h->bloch = opts->bloch;
     for (int i = 0; i < 3; ++i) h->kpoint[i] = h->bloch ? opts->kpoint[i] : 0.0;
@@ -323,7 +370,11 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
     switch (h->method) {
     case QMCSPL_LAGRANGE: h->n_tables = 5; h->entries = 1; h->rows_z = dims[2] + 3; break;
     case QMCSPL_PPSPLINE: h->n_tables = 1; h->entries = 8; h->rows_z = dims[2] + 1; break;
-    default: h->n_tables = h->separate_grad ? 5 : (h->separate_lap ? 2 : 1); h->entries = 1; h->rows_z = dims[2] + 3; break;
+    default:
+        h->n_tables = h->separate_grad ? 5 : (h->separate_lap ? 2 : 1);
+        h->entries = 1;
+        h->rows_z = dims[2] + degree;   // (degree - 1)/2 ghost planes below, (degree + 1)/2 above
+        break;
     }
     h->table_elems = (size_t)dims[0] * dims[1] * h->rows_z * h->entries * h->n_orb_p;
 
@@ -336,6 +387,9 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
         return rc;
     }
     e = cudaMalloc((void**)&h->d_err, sizeof(int));
+    if (e == cudaSuccess && nonuni) e = cudaMalloc((void**)&h->d_knots, sizeof(double) * 3 * kMaxDim);
+    if (e == cudaSuccess && nonuni)
+        e = cudaMemcpyAsync(h->d_knots, h->knots, sizeof(double) * 3 * kMaxDim, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->tables, 0, bytes, st);
     if (e != cudaSuccess) {
@@ -379,6 +433,8 @@ int qmcspl_info(qmcspl_t h, qmcspl_info_t* out)
     out->n_pw = h->n_pw;
     out->bloch = h->bloch;
     out->separate_grad = h->separate_grad;
+    out->degree = h->degree;
+    out->nonuniform = h->nonuniform;
     for (int i = 0; i < 3; ++i) out->kpoint[i] = h->kpoint[i];
     return QMCSPL_OK;
 }
@@ -402,8 +458,9 @@ static int eval_dispatch(Handle* h, const double* pos, long long n_pos, void* va
     case QMCSPL_LAGRANGE: rc = launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st); break;
     case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, pr, n_pos, val, grad, lap, st); break;
     default:
-        rc = h->separate_grad ? launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st)
-                              : launch_bspline_vgl(h, pos, pr, n_pos, val, grad, lap, st);
+        rc = h->separate_grad  ? launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st)
+             : is_general(h) ? launch_general_vgl(h, pos, pr, n_pos, val, grad, lap, st)
+                               : launch_bspline_vgl(h, pos, pr, n_pos, val, grad, lap, st);
         break;
     }
     if (ev) cudaEventRecord(ev[2], st);
@@ -512,6 +569,8 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
     if (h->bloch) return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for Bloch orbitals");
     if (h->separate_grad)
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for separate gradient tables");
+    if (is_general(h))
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is implemented for cubic B-splines on uniform grids");
     if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
     if (dcoef_lap && !(h->separate_lap && dcoef))
         return set_error(QMCSPL_ERR_ARG, "dcoef_lap needs a separate-Laplacian handle and dcoef");
@@ -539,7 +598,7 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* po
             hs[c]->bloch != hs[0]->bloch)
             return set_error(QMCSPL_ERR_ARG, "handles of a batch must share storage type, separate_lap and bloch");
         if ((hs[c]->method != QMCSPL_BSPLINE_SMOOTH && hs[c]->method != QMCSPL_BSPLINE_INTERP) ||
-            hs[c]->separate_grad)
+            hs[c]->separate_grad || is_general(hs[c]))
             return set_error(QMCSPL_ERR_UNSUPPORTED,
                              "batched evaluation is for B-spline handles without separate gradient tables");
         if (n_pos[c] < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
@@ -579,7 +638,7 @@ int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream)
         return cuda_error(e, "table copy");
     }
     const int N1 = h->dims[0], N2 = h->dims[1], N3 = h->dims[2];
-    const int zshift = (h->method == QMCSPL_PPSPLINE) ? 0 : 1;
+    const int zshift = h->zshift;
     for (int x = 0; x < N1; ++x)
         for (int y = 0; y < N2; ++y)
             for (int z = 0; z < N3; ++z) {

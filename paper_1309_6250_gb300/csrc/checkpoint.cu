@@ -1,8 +1,9 @@
 // checkpoint.cu -- qmcspl_save / qmcspl_load: built tables to and from a file.
 //
 // File layout (little-endian, as the host writes it):
-//   FileHeader (fixed size, below), then n_tables * table_elems * elem_bytes bytes of
-//   tables exactly as they sit on the device.
+//   FileHeader (fixed size, below); for a non-uniform grid the grid points of the three
+//   axes (dims[0] + dims[1] + dims[2] doubles); then n_tables * table_elems * elem_bytes
+//   bytes of tables exactly as they sit on the device.  The checksum covers both.
 #include <cerrno>
 #include <cmath>
 #include <cstdio>
@@ -17,7 +18,7 @@ namespace qmcspl {
 namespace {
 
 constexpr char kMagic[8] = {'Q', 'M', 'C', 'S', 'P', 'L', 'T', 'B'};
-constexpr int kFormatVersion = 2;   // 2: Bloch flag and k point
+constexpr int kFormatVersion = 3;   // 2: Bloch flag and k point; 3: degree and grid points
 constexpr int kLayoutVersion = 1;   // ghost planes, padding and chunk order of the tables
 
 struct FileHeader {
@@ -29,6 +30,7 @@ struct FileHeader {
     int lanes_log2, tiles;
     int n_tables, entries, rows_z;
     int bloch;
+    int degree, nonuniform;
     long long n_pw;
     long long table_elems;
     long long elem_bytes;
@@ -100,11 +102,20 @@ extern "C" int qmcspl_save(qmcspl_t h, const char* path)
     hd.elem_bytes = (long long)h->elem_bytes;
     std::memcpy(hd.lattice, h->lattice, sizeof(hd.lattice));
     hd.bloch = h->bloch;
+    hd.degree = h->degree;
+    hd.nonuniform = h->nonuniform;
     std::memcpy(hd.kpoint, h->kpoint, sizeof(hd.kpoint));
-    hd.checksum = fnv1a(buf.data(), buf.size());
+    std::vector<double> pts;
+    if (h->nonuniform)
+        for (int a = 0; a < 3; ++a) pts.insert(pts.end(), h->knots[a], h->knots[a] + h->dims[a]);
+    const size_t pbytes = pts.size() * sizeof(double);
+    hd.checksum = fnv1a(buf.data(), buf.size(),
+                        fnv1a(reinterpret_cast<const unsigned char*>(pts.data()), pbytes));
     FILE* f = std::fopen(path, "wb");
     if (!f) return io_error("cannot open", path);
-    const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 && std::fwrite(buf.data(), 1, bytes, f) == bytes;
+    const bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+                    (pbytes == 0 || std::fwrite(pts.data(), 1, pbytes, f) == pbytes) &&
+                    std::fwrite(buf.data(), 1, bytes, f) == bytes;
     const bool closed = std::fclose(f) == 0;
     if (!ok || !closed) return io_error("cannot write", path);
     return QMCSPL_OK;
@@ -138,7 +149,9 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
     const long long eb = hd.storage == QMCSPL_BF16 ? 2 : (hd.storage == QMCSPL_F32 ? 4 : 8);
     sane = sane && hd.elem_bytes == eb && (long long)hd.n_orb_p * hd.elem_bytes % 16 == 0 &&
            hd.n_orb_p == hd.tiles * (1 << hd.lanes_log2) * (int)(16 / eb) &&
-           hd.rows_z == hd.dims[2] + (hd.method == QMCSPL_PPSPLINE ? 1 : 3) &&
+           (hd.degree == 1 || hd.degree == 3 || hd.degree == 5 || hd.degree == 7) &&
+           (hd.nonuniform == 0 || (hd.nonuniform == 1 && hd.degree == 3)) &&
+           hd.rows_z == hd.dims[2] + (hd.method == QMCSPL_PPSPLINE ? 1 : hd.degree) &&
            hd.table_elems == (long long)hd.dims[0] * hd.dims[1] * hd.rows_z * hd.entries * hd.n_orb_p;
     for (int i = 0; i < 9; ++i) sane = sane && std::isfinite(hd.lattice[i]);
     sane = sane && (hd.bloch == 0 || (hd.bloch == 1 && hd.n_orb % 2 == 0));
@@ -155,6 +168,12 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
         return set_error(QMCSPL_ERR_ARG, "inconsistent table file header");
     }
     const size_t bytes = (size_t)hd.table_elems * (size_t)hd.elem_bytes * (size_t)hd.n_tables;
+    std::vector<double> pts(hd.nonuniform ? (size_t)hd.dims[0] + hd.dims[1] + hd.dims[2] : 0);
+    const size_t pbytes = pts.size() * sizeof(double);
+    if (pbytes && std::fread(pts.data(), 1, pbytes, f) != pbytes) {
+        std::fclose(f);
+        return set_error(QMCSPL_ERR_ARG, "truncated table file (grid points)");
+    }
     std::vector<unsigned char> buf;
     try {
         buf.resize(bytes);
@@ -166,7 +185,18 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
     const bool extra = std::fgetc(f) != EOF;
     std::fclose(f);
     if (got != bytes || extra) return set_error(QMCSPL_ERR_ARG, "table file has the wrong size");
-    if (fnv1a(buf.data(), buf.size()) != hd.checksum) return set_error(QMCSPL_ERR_ARG, "table file checksum mismatch");
+    if (fnv1a(buf.data(), buf.size(), fnv1a(reinterpret_cast<const unsigned char*>(pts.data()), pbytes)) !=
+        hd.checksum)
+        return set_error(QMCSPL_ERR_ARG, "table file checksum mismatch");
+    {
+        size_t o = 0;
+        for (int a = 0; a < 3 && hd.nonuniform; ++a)
+            for (int i = 0; i < hd.dims[a]; ++i, ++o) {
+                const double v = pts[o];
+                if (!std::isfinite(v) || v < 0.0 || v >= 1.0 || (i > 0 && !(v > pts[o - 1])))
+                    return set_error(QMCSPL_ERR_ARG, "table file has invalid grid points");
+            }
+    }
 
     Handle* h = new (std::nothrow) Handle();
     if (!h) return set_error(QMCSPL_ERR_OOM, "host allocation failed");
@@ -186,6 +216,14 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
     h->n_pw = hd.n_pw;
     h->bloch = hd.bloch;
     for (int i = 0; i < 3; ++i) h->kpoint[i] = hd.kpoint[i];
+    h->degree = hd.degree;
+    h->nonuniform = hd.nonuniform;
+    h->zshift = hd.method == QMCSPL_PPSPLINE ? 0 : (hd.degree - 1) / 2;
+    {
+        size_t o = 0;
+        for (int a = 0; a < 3 && hd.nonuniform; ++a)
+            for (int i = 0; i < hd.dims[a]; ++i) h->knots[a][i] = pts[o++];
+    }
     h->table_elems = (size_t)hd.table_elems;
     h->elem_bytes = (size_t)hd.elem_bytes;
     if (!handle_geometry(h, hd.lattice)) {
@@ -195,6 +233,9 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMalloc(&h->tables, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, sizeof(int));
+    if (e == cudaSuccess && h->nonuniform) e = cudaMalloc((void**)&h->d_knots, sizeof(double) * 3 * kMaxDim);
+    if (e == cudaSuccess && h->nonuniform)
+        e = cudaMemcpyAsync(h->d_knots, h->knots, sizeof(double) * 3 * kMaxDim, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->tables, buf.data(), bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -14,6 +14,14 @@
 //                                6 (cos th - 1) / (2 + cos th) Eq. (pp-splinecoefficients3)
 //   deriv   value 1; d_a phi i G_a; lap phi -|G|^2 (the separate gradient and Laplacian
 //           approximations of Sec. III C: B-splines optionally, Lagrange always)
+//   odd degree n (uniform grid): 1 / prod_m S_n(th_m), S_n(th) = sum_j C_n B_n(j) e^{i j th},
+//           the symbol of the periodic interpolation system of the degree-n basis
+//
+// Non-uniform grids (Sec. II "Grid": interpolating splines need no even spacing): the
+// planewave sum is evaluated at the per-axis grid points by the same separable passes with
+// the true frequencies (the band must fit the grid, 2 n_max + 1 <= N, so folded indices
+// map back to frequencies), then the cyclic tridiagonal interpolation system of the
+// non-uniform cubic basis is solved along each axis (Thomas + Sherman-Morrison).
 // with th_m = 2 pi n_m / N_m.  The cyclic systems are circulant, so dividing the folded
 // spectrum by their eigenvalues is their exact solution.
 //
@@ -33,6 +41,7 @@
 #include <cstring>
 #include <vector>
 
+#include "general_basis.cuh"
 #include "qmcspl_internal.cuh"
 
 namespace qmcspl {
@@ -50,6 +59,7 @@ struct ScatterArgs {
     int dims[3];
     double bmat[9];           // G_a = sum_i bmat[3a+i] n_i
     double kc[3];             // Cartesian k added to G in the derivative multipliers (0: Gamma)
+    double sym[4];            // kBasisInterpN: C_n B_n(j), j = 0..3
     int basis, deriv;         // BuildBasis, BuildDeriv
     int pp_axes;              // bit 2: x, bit 1: y, bit 0: z carry label 2
     double2* F;               // [N1][N2][N3][oc]
@@ -107,6 +117,15 @@ __global__ void scatter_kernel(const ScatterArgs a)
     case kBasisInterp:
         b = 1.0 / (interp_axis(k0, a.dims[0]) * interp_axis(k1, a.dims[1]) * interp_axis(k2, a.dims[2]));
         break;
+    case kBasisInterpN: {
+        const int kk[3] = {k0, k1, k2};
+        for (int ax = 0; ax < 3; ++ax) {
+            double sv = a.sym[0];
+            for (int j = 1; j < 4; ++j) sv += 2.0 * a.sym[j] * cospi(2.0 * (double)(j * kk[ax]) / (double)a.dims[ax]);
+            b /= sv;
+        }
+        break;
+    }
     case kBasisPP:
         if (a.pp_axes & 4) b *= pp_axis(k0, a.dims[0]);
         if (a.pp_axes & 2) b *= pp_axis(k1, a.dims[1]);
@@ -138,6 +157,7 @@ struct DftArgs {
     int kmax;                 // nonzero input rows: k <= kmax or k >= N - kmax; -1 = all
     int skip_mode;            // 0: every line; 1: outer = k1; 2: outer = k1 * D2 + k2
     int D1, kmax1, D2, kmax2; // band of the outer index (skip_mode 1, 2)
+    const double* pts;        // non-uniform output points s_l in [0, 1) (null: s_l = l / N)
 };
 
 __device__ __forceinline__ bool in_band(int k, int kmax, int N)
@@ -155,6 +175,7 @@ __global__ void __launch_bounds__(kDftInner * kDftRows) dft_pass_kernel(const Df
     const long long i = (b - outer * tiles_inner) * kDftInner + (threadIdx.x % kDftInner);
     const int ty = threadIdx.x / kDftInner;
     const int N = a.N;
+    const bool nonuni = a.pts != nullptr;
 
     bool zero = false;
     if (a.skip_mode == 1) {
@@ -169,7 +190,8 @@ __global__ void __launch_bounds__(kDftInner * kDftRows) dft_pass_kernel(const Df
                 a.out[((long long)outer * N + l) * a.inner + i] = make_double2(0.0, 0.0);
         return;
     }
-    const int full = (a.kmax < 0 || 2 * a.kmax + 1 >= N);
+    // non-uniform points need the true frequency of every row: never the folded "full" view
+    const int full = (a.kmax < 0 || (!nonuni && 2 * a.kmax + 1 >= N));
     const int nlo = full ? N : a.kmax + 1;           // rows k = 0 .. nlo-1
     const int nhi = full ? 0 : a.kmax;               // rows k = N-kmax .. N-1
     const int nb = nlo + nhi;
@@ -188,6 +210,38 @@ __global__ void __launch_bounds__(kDftInner * kDftRows) dft_pass_kernel(const Df
     __syncthreads();
     if (i >= a.inner) return;
     const int tx = threadIdx.x % kDftInner;
+    if (nonuni) {
+        // out[l] = sum_k in[k] exp(2 pi i f(k) s_l), f(k) = k (low rows) or k - N (high rows);
+        // the factors follow by repeated multiplication with exp(2 pi i s_l)
+        for (int l = ty; l < N; l += kDftRows) {
+            const double sl = a.pts[l];
+            double sb, cb;
+            sincospi(2.0 * sl, &sb, &cb);
+            double re = 0.0, im = 0.0;
+            double wr = 1.0, wi = 0.0;
+            for (int j = 0; j < nlo; ++j) {
+                const double2 v = rows[j * kDftInner + tx];
+                re = fma(v.x, wr, fma(-v.y, wi, re));
+                im = fma(v.x, wi, fma(v.y, wr, im));
+                const double t = wr * cb - wi * sb;
+                wi = wr * sb + wi * cb;
+                wr = t;
+            }
+            if (nhi) {
+                sincospi(-2.0 * (double)nhi * sl, &wi, &wr);
+                for (int j = nlo; j < nb; ++j) {
+                    const double2 v = rows[j * kDftInner + tx];
+                    re = fma(v.x, wr, fma(-v.y, wi, re));
+                    im = fma(v.x, wi, fma(v.y, wr, im));
+                    const double t = wr * cb - wi * sb;
+                    wi = wr * sb + wi * cb;
+                    wr = t;
+                }
+            }
+            a.out[((long long)outer * N + l) * a.inner + i] = make_double2(re, im);
+        }
+        return;
+    }
     for (int l = ty; l < N; l += kDftRows) {
         double re = 0.0, im = 0.0;
         int idx = 0;                                  // (k l) mod N for k = 0, 1, ...
@@ -303,7 +357,7 @@ int launch_layout(const Handle* h, const double2* F, int tab, int entry, int o0,
     a.rows_z = h->rows_z;
     a.entries = h->entries;
     a.entry = entry;
-    a.zshift = (h->method == QMCSPL_PPSPLINE) ? 0 : 1;
+    a.zshift = h->zshift;
     a.cplx = h->bloch ? 1 : 0;
     const long long total = (long long)a.N1 * a.N2 * a.rows_z * (a.oc << a.cplx);
     const unsigned blocks = (unsigned)((total + 255) / 256);
@@ -318,7 +372,7 @@ int launch_layout(const Handle* h, const double2* F, int tab, int entry, int o0,
 
 int launch_dft(const DftArgs& a, cudaStream_t st)
 {
-    const int full = (a.kmax < 0 || 2 * a.kmax + 1 >= a.N);
+    const int full = (a.kmax < 0 || (!a.pts && 2 * a.kmax + 1 >= a.N));
     const int nb = full ? a.N : 2 * a.kmax + 1;
     const size_t smem = ((size_t)nb * kDftInner + a.N) * sizeof(double2);
     const long long tiles_inner = (a.inner + kDftInner - 1) / kDftInner;
@@ -336,6 +390,135 @@ struct TableJob {
     int tab, entry, basis, deriv, pp_axes;
 };
 
+// Cyclic tridiagonal interpolation system of one non-uniform axis, row i:
+//   a_i beta_{i-1} + b_i beta_i + c_i beta_{i+1} = f_i   (indices mod N),
+// a, b, c the cubic basis of grid points i-1, i, i+1 at grid point i.  Sherman-Morrison:
+// A = T + u v^T with gamma = -b_0, T's corners removed and diagonal b_0 - gamma,
+// b_{N-1} - a_0 c_{N-1} / gamma; u = (gamma, 0.., c_{N-1}), v = (1, 0.., a_0 / gamma);
+// x = y - (v.y) / (1 + v.q) q with T y = f, T q = u.  The Thomas factors of T and q do not
+// depend on the right-hand side, so they are computed once here:
+//   coef[0][i] = a_i, coef[1][i] = c'_i, coef[2][i] = 1 / m_i, coef[3][i] = q_i.
+struct AxisSystem {
+    std::vector<double> coef;   // 4 N
+    double v_last = 0.0;        // a_0 / gamma
+    double inv_denom = 0.0;     // 1 / (1 + v.q)
+};
+
+AxisSystem axis_system(const double* knots, int n, double C)
+{
+    std::vector<double> a(n), b(n), c(n);
+    for (int i = 0; i < n; ++i) {
+        double w[4], dw[4];
+        nonuniform_cubic_weights<double>(knots, n, i, periodic_knot(knots, n, i), C, w, dw, nullptr);
+        a[i] = w[0];
+        b[i] = w[1];
+        c[i] = w[2];
+    }
+    const double gamma = -b[0];
+    std::vector<double> bd(b);
+    bd[0] = b[0] - gamma;
+    bd[n - 1] = b[n - 1] - a[0] * c[n - 1] / gamma;
+    AxisSystem s;
+    s.coef.assign(4 * (size_t)n, 0.0);
+    double* A = s.coef.data();
+    double* CP = A + n;
+    double* IM = A + 2 * n;
+    double* Q = A + 3 * n;
+    for (int i = 0; i < n; ++i) A[i] = a[i];
+    IM[0] = 1.0 / bd[0];
+    CP[0] = c[0] * IM[0];
+    for (int i = 1; i < n; ++i) {
+        IM[i] = 1.0 / (bd[i] - a[i] * CP[i - 1]);
+        CP[i] = (i < n - 1) ? c[i] * IM[i] : 0.0;
+    }
+    std::vector<double> u(n, 0.0);
+    u[0] = gamma;
+    u[n - 1] = c[n - 1];
+    Q[0] = u[0] * IM[0];
+    for (int i = 1; i < n; ++i) Q[i] = (u[i] - a[i] * Q[i - 1]) * IM[i];
+    for (int i = n - 2; i >= 0; --i) Q[i] -= CP[i] * Q[i + 1];
+    s.v_last = a[0] / gamma;
+    s.inv_denom = 1.0 / (1.0 + Q[0] + s.v_last * Q[n - 1]);
+    return s;
+}
+
+struct SolveArgs {
+    double2* F;               // array viewed as [outer][N][inner], solved in place along N
+    long long outer, inner;
+    int N;
+    const double* coef;       // AxisSystem::coef on the device
+    double v_last, inv_denom;
+};
+
+__global__ void cyclic_solve_kernel(const SolveArgs s)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= s.outer * s.inner) return;
+    const long long o = idx / s.inner, in = idx - o * s.inner;
+    double2* x = s.F + o * s.N * s.inner + in;
+    const long long st = s.inner;
+    const int N = s.N;
+    const double* A = s.coef;
+    const double* CP = A + N;
+    const double* IM = A + 2 * N;
+    const double* Q = A + 3 * N;
+    double2 prev = x[0];
+    prev.x *= IM[0];
+    prev.y *= IM[0];
+    x[0] = prev;
+    for (int l = 1; l < N; ++l) {   // forward sweep
+        double2 cur = x[l * st];
+        cur.x = (cur.x - A[l] * prev.x) * IM[l];
+        cur.y = (cur.y - A[l] * prev.y) * IM[l];
+        x[l * st] = cur;
+        prev = cur;
+    }
+    double2 next = prev;             // back substitution
+    for (int l = N - 2; l >= 0; --l) {
+        double2 y = x[l * st];
+        y.x -= CP[l] * next.x;
+        y.y -= CP[l] * next.y;
+        x[l * st] = y;
+        next = y;
+    }
+    const double2 y0 = x[0], yn = x[(N - 1) * st];
+    const double cr = (y0.x + s.v_last * yn.x) * s.inv_denom;
+    const double ci = (y0.y + s.v_last * yn.y) * s.inv_denom;
+    for (int l = 0; l < N; ++l) {
+        double2 v = x[l * st];
+        v.x -= cr * Q[l];
+        v.y -= ci * Q[l];
+        x[l * st] = v;
+    }
+}
+
+int launch_solve(double2* F, long long outer, int N, long long inner, const double* coef, const AxisSystem& sys,
+                 cudaStream_t st)
+{
+    SolveArgs s;
+    s.F = F;
+    s.outer = outer;
+    s.inner = inner;
+    s.N = N;
+    s.coef = coef;
+    s.v_last = sys.v_last;
+    s.inv_denom = sys.inv_denom;
+    const long long n = outer * inner;
+    cyclic_solve_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s);
+    return cuda_error(cudaGetLastError(), "cyclic_solve_kernel launch");
+}
+
+// C_n B_n(j), j = 0..3: the symbol coefficients of the degree-n interpolation system
+void degree_symbol(int n, double sym[4])
+{
+    static const double B[4][4] = {{1.0, 0.0, 0.0, 0.0},
+                                   {2.0 / 3.0, 1.0 / 6.0, 0.0, 0.0},
+                                   {11.0 / 20.0, 13.0 / 60.0, 1.0 / 120.0, 0.0},
+                                   {151.0 / 315.0, 397.0 / 1680.0, 1.0 / 42.0, 1.0 / 5040.0}};
+    const int r = (n - 1) / 2;
+    for (int j = 0; j < 4; ++j) sym[j] = degree_constant(n) * B[r][j];
+}
+
 }  // namespace
 
 int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef_host,
@@ -349,14 +532,27 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
             v = v < 0 ? -v : v;
             if (v > kmax[a]) kmax[a] = v;
         }
+    if (h->nonuniform)
+        for (int a = 0; a < 3; ++a)
+            if (2 * kmax[a] + 1 > h->dims[a])
+                return set_error(QMCSPL_ERR_ARG, "a non-uniform grid needs N >= 2 n_max + 1 points per axis "
+                                                 "(the planewave band must fit the grid)");
     for (int a = 0; a < 3; ++a)
-        if (2 * kmax[a] + 1 >= h->dims[a]) kmax[a] = -1;   // band covers the whole axis
+        if (2 * kmax[a] + 1 >= h->dims[a] && !(h->nonuniform && 2 * kmax[a] + 1 == h->dims[a]))
+            kmax[a] = -1;   // band covers the whole axis
 
     std::vector<TableJob> jobs;
-    const int basis = h->method == QMCSPL_BSPLINE_SMOOTH   ? kBasisSmooth
-                      : h->method == QMCSPL_BSPLINE_INTERP ? kBasisInterp
-                      : h->method == QMCSPL_LAGRANGE       ? kBasisGrid
-                                                           : kBasisPP;
+    int basis = h->method == QMCSPL_BSPLINE_SMOOTH   ? kBasisSmooth
+                : h->method == QMCSPL_BSPLINE_INTERP ? kBasisInterp
+                : h->method == QMCSPL_LAGRANGE       ? kBasisGrid
+                                                     : kBasisPP;
+    if (h->nonuniform) basis = kBasisGrid;                 // grid values, then the axis solves
+    else if (h->degree != 3) basis = kBasisInterpN;
+    double sym[4] = {0.0, 0.0, 0.0, 0.0};
+    if (basis == kBasisInterpN) degree_symbol(h->degree, sym);
+    AxisSystem sys[3];
+    if (h->nonuniform)
+        for (int a = 0; a < 3; ++a) sys[a] = axis_system(h->knots[a], h->dims[a], degree_constant(3));
     if (h->method == QMCSPL_PPSPLINE) {
         // entry e = 4(kappa-1) + 2(mu-1) + (nu-1); label 2 <=> bit set
         for (int e = 0; e < 8; ++e) jobs.push_back({0, e, kBasisPP, kDerivValue, e});
@@ -376,9 +572,23 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
     int* d_miller = nullptr;
     double2* d_coef = nullptr;
     double2* F[2] = {nullptr, nullptr};
+    double* d_sys = nullptr;   // non-uniform: 3 axis systems of 4 N doubles
     int rc = QMCSPL_OK;
     cudaError_t e;
     do {
+        if (h->nonuniform) {
+            const size_t nd = 4 * (size_t)(N1 + N2 + N3);
+            e = cudaMallocAsync((void**)&d_sys, sizeof(double) * nd, st);
+            if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(axis systems)"); break; }
+            size_t off = 0;
+            for (int a = 0; a < 3; ++a) {
+                e = cudaMemcpyAsync(d_sys + off, sys[a].coef.data(), sizeof(double) * sys[a].coef.size(),
+                                    cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) break;
+                off += sys[a].coef.size();
+            }
+            if (e != cudaSuccess) { rc = cuda_error(e, "upload axis systems"); break; }
+        }
         e = cudaMallocAsync((void**)&d_miller, sizeof(int) * 3 * (size_t)n_pw, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(miller)"); break; }
         e = cudaMallocAsync((void**)&d_coef, sizeof(double2) * (size_t)n_pw * n_band, st);
@@ -412,6 +622,7 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
                 for (int a = 0; a < 3; ++a) s.dims[a] = h->dims[a];
                 std::memcpy(s.bmat, bmat, sizeof(bmat));
                 for (int a = 0; a < 3; ++a) s.kc[a] = h->kcart[a];
+                for (int j = 0; j < 4; ++j) s.sym[j] = sym[j];
                 s.basis = job.basis;
                 s.deriv = job.deriv;
                 s.pp_axes = job.pp_axes;
@@ -425,21 +636,33 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
                 d.in = F[0]; d.out = F[1];
                 d.outer = (long long)N1 * N2; d.N = N3; d.inner = oc; d.kmax = kmax[2];
                 d.skip_mode = 2; d.D1 = N1; d.kmax1 = kmax[0]; d.D2 = N2; d.kmax2 = kmax[1];
+                d.pts = h->nonuniform ? h->d_knots + 2 * kMaxDim : nullptr;
                 if ((rc = launch_dft(d, st)) != QMCSPL_OK) break;
                 // y: [N1][N2][N3*oc], lines outside the k1 band are zero
                 d.in = F[1]; d.out = F[0];
                 d.outer = N1; d.N = N2; d.inner = (long long)N3 * oc; d.kmax = kmax[1];
                 d.skip_mode = 1; d.D1 = N1; d.kmax1 = kmax[0]; d.D2 = 1; d.kmax2 = -1;
+                d.pts = h->nonuniform ? h->d_knots + kMaxDim : nullptr;
                 if ((rc = launch_dft(d, st)) != QMCSPL_OK) break;
                 // x: [1][N1][N2*N3*oc]
                 d.in = F[0]; d.out = F[1];
                 d.outer = 1; d.N = N1; d.inner = (long long)N2 * N3 * oc; d.kmax = kmax[0];
                 d.skip_mode = 0;
+                d.pts = h->nonuniform ? h->d_knots : nullptr;
                 if ((rc = launch_dft(d, st)) != QMCSPL_OK) break;
+                if (h->nonuniform) {   // interpolation systems along x, y, z (any order)
+                    const double* c0 = d_sys;
+                    const double* c1 = c0 + 4 * (size_t)N1;
+                    const double* c2 = c1 + 4 * (size_t)N2;
+                    if ((rc = launch_solve(F[1], 1, N1, (long long)N2 * N3 * oc, c0, sys[0], st)) != QMCSPL_OK) break;
+                    if ((rc = launch_solve(F[1], N1, N2, (long long)N3 * oc, c1, sys[1], st)) != QMCSPL_OK) break;
+                    if ((rc = launch_solve(F[1], (long long)N1 * N2, N3, oc, c2, sys[2], st)) != QMCSPL_OK) break;
+                }
                 if ((rc = launch_layout(h, F[1], job.tab, job.entry, o0, oc, st)) != QMCSPL_OK) break;
             }
         }
     } while (0);
+    if (d_sys) cudaFreeAsync(d_sys, st);
     if (F[0]) cudaFreeAsync(F[0], st);
     if (F[1]) cudaFreeAsync(F[1], st);
     if (d_coef) cudaFreeAsync(d_coef, st);

@@ -1,0 +1,151 @@
+// general_basis.cuh -- B-spline basis weights of any odd degree on uniform grids, and of
+// degree 3 on non-uniform periodic grids (Appendix, the B-spline recurrence), for the
+// general evaluation kernel and the host-side construction of non-uniform systems.
+//
+// The recurrence b_j^k = w_j^k b_j^{k-1} + (1 - w_{j+1}^k) b_{j+1}^{k-1},
+// w_j^k(x) = (x - x_j)/(x_{j+k} - x_j), b_j^0 = C on [x_j, x_{j+1}), gives on the knot
+// interval [x_i, x_{i+1}) the k + 1 nonzero functions b_{i-k}^k .. b_i^k.  The basis of grid
+// point m is b_j^k with j = m - (k+1)/2 (odd k), so on interval i the stencil is the grid
+// points i - (k-1)/2 .. i + (k+1)/2, weight index r = m - i + (k-1)/2.
+#pragma once
+
+#include <cmath>
+
+namespace qmcspl {
+
+constexpr int kMaxDegree = 7;
+
+// C_n = 1 / B_n(0) (the centred basis peaks at one; 3/2 for the cubic as in the paper)
+__host__ __device__ inline double degree_constant(int n)
+{
+    switch (n) {
+    case 1: return 1.0;
+    case 3: return 1.5;
+    case 5: return 20.0 / 11.0;
+    default: return 315.0 / 151.0;   // n = 7
+    }
+}
+
+// Uniform knots (unit spacing), local coordinate t in [0, 1) of the interval.  With the
+// partition-of-unity levels P_d[r] = b_{i-d+r}^d (C = 1):
+//   P_d[r] = ((t + d - r) P_{d-1}[r-1] + (r + 1 - t) P_{d-1}[r]) / d,
+//   d/du P_n[r] = P_{n-1}[r-1] - P_{n-1}[r],   d2/du2 P_n[r] = D_{n-1}[r-1] - D_{n-1}[r]
+// with D_{n-1}[r] = P_{n-2}[r-1] - P_{n-2}[r] (entries outside 0..d are zero).  The
+// weights are C_n P_n; derivatives are with respect to u = N s (grid units).
+template <typename A, int DEG>
+__host__ __device__ inline void uniform_weights(A t, A C, A* w, A* dw, A* d2w)
+{
+    A lev[3][DEG + 1];   // P_{DEG-2}, P_{DEG-1}, P_DEG (zero padded)
+    A P[DEG + 1];
+#pragma unroll
+    for (int r = 0; r <= DEG; ++r) P[r] = A(0);
+    P[0] = A(1);
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+        for (int r = 0; r <= DEG; ++r) lev[l][r] = A(0);
+    if (DEG - 2 == 0) lev[0][0] = A(1);
+#pragma unroll
+    for (int d = 1; d <= DEG; ++d) {
+        A Q[DEG + 1];
+#pragma unroll
+        for (int r = 0; r <= DEG; ++r) {
+            if (r > d) {
+                Q[r] = A(0);
+                continue;
+            }
+            const A left = r > 0 ? P[r - 1] : A(0);
+            const A right = r < d ? P[r] : A(0);
+            Q[r] = ((t + A(d - r)) * left + (A(r + 1) - t) * right) / A(d);
+        }
+#pragma unroll
+        for (int r = 0; r <= DEG; ++r) P[r] = Q[r];
+        if (d == DEG - 2)
+#pragma unroll
+            for (int r = 0; r <= DEG; ++r) lev[0][r] = P[r];
+        if (d == DEG - 1)
+#pragma unroll
+            for (int r = 0; r <= DEG; ++r) lev[1][r] = P[r];
+    }
+    if (DEG == 1) {   // P_0 = [1] is the degree-0 level
+        lev[1][0] = A(1);
+    }
+#pragma unroll
+    for (int r = 0; r <= DEG; ++r) {
+        w[r] = C * P[r];
+        const A a = r > 0 ? lev[1][r - 1] : A(0);
+        const A b = r < DEG ? lev[1][r] : A(0);
+        dw[r] = C * (a - b);
+        if (d2w) {
+            // D_{n-1}[q] = P_{n-2}[q-1] - P_{n-2}[q], q = 0..n-1
+            auto D = [&](int q) -> A {
+                if (q < 0 || q > DEG - 1 || DEG < 2) return A(0);
+                const A x = q > 0 ? lev[0][q - 1] : A(0);
+                const A y = q < DEG - 1 ? lev[0][q] : A(0);
+                return x - y;
+            };
+            d2w[r] = C * (D(r - 1) - D(r));
+        }
+    }
+}
+
+// x_j of the periodic extension of knots[0..n-1] in [0, 1)
+__host__ __device__ inline double periodic_knot(const double* knots, int n, int j)
+{
+    int q = j / n, r = j - q * n;
+    if (r < 0) {
+        r += n;
+        q -= 1;
+    }
+    return knots[r] + (double)q;
+}
+
+// Cubic weights on the non-uniform interval [x_i, x_{i+1}) at x (same period as the knots),
+// for the grid points i-1 .. i+2, and their first and second derivatives with respect to
+// the reduced coordinate.  De Boor's triangular evaluation of the recurrence.
+template <typename A>
+__host__ __device__ inline void nonuniform_cubic_weights(const double* knots, int n, int i, double x, A C,
+                                                         A* w, A* dw, A* d2w)
+{
+    double left[4], right[4];
+    for (int j = 1; j <= 3; ++j) {
+        left[j] = x - periodic_knot(knots, n, i + 1 - j);
+        right[j] = periodic_knot(knots, n, i + j) - x;
+    }
+    double N1[2], N2[3], N3[4];
+    double Nl[4] = {1.0, 0.0, 0.0, 0.0};
+    for (int j = 1; j <= 3; ++j) {
+        double saved = 0.0;
+        for (int r = 0; r < j; ++r) {
+            const double temp = Nl[r] / (right[r + 1] + left[j - r]);
+            Nl[r] = saved + right[r + 1] * temp;
+            saved = left[j - r] * temp;
+        }
+        Nl[j] = saved;
+        if (j == 1) { N1[0] = Nl[0]; N1[1] = Nl[1]; }
+        if (j == 2) { N2[0] = Nl[0]; N2[1] = Nl[1]; N2[2] = Nl[2]; }
+    }
+    for (int r = 0; r < 4; ++r) N3[r] = Nl[r];
+    // N_d[q] is the degree-d function starting at knot i - d + q
+    auto kn = [&](int j) { return periodic_knot(knots, n, j); };
+    auto b1 = [&](int k) -> double {   // degree-1 function starting at knot k
+        const int q = k - (i - 1);
+        return (q >= 0 && q <= 1) ? N1[q] : 0.0;
+    };
+    auto b2 = [&](int k) -> double {
+        const int q = k - (i - 2);
+        return (q >= 0 && q <= 2) ? N2[q] : 0.0;
+    };
+    auto db2 = [&](int k) -> double {
+        return 2.0 * (b1(k) / (kn(k + 2) - kn(k)) - b1(k + 1) / (kn(k + 3) - kn(k + 1)));
+    };
+    for (int r = 0; r < 4; ++r) {
+        const int k = i - 3 + r;          // start knot of the function of grid point i-1+r
+        w[r] = C * (A)N3[r];
+        const double ak = 3.0 / (kn(k + 3) - kn(k)), bk = 3.0 / (kn(k + 4) - kn(k + 1));
+        dw[r] = C * (A)(ak * b2(k) - bk * b2(k + 1));
+        if (d2w) d2w[r] = C * (A)(ak * db2(k) - bk * db2(k + 1));
+    }
+}
+
+}  // namespace qmcspl

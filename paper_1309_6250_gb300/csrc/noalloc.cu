@@ -78,8 +78,9 @@ extern "C" int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long 
             case QMCSPL_LAGRANGE: rc = launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st); break;
             case QMCSPL_PPSPLINE: rc = launch_pp_vgl(h, pos, pr, n_pos, val, grad, lap, st); break;
             default:
-                rc = h->separate_grad ? launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st)
-                                      : launch_bspline_vgl(h, pos, pr, n_pos, val, grad, lap, st);
+                rc = h->separate_grad  ? launch_five_table_vgl(h, pos, pr, n_pos, val, grad, lap, st)
+                     : is_general(h) ? launch_general_vgl(h, pos, pr, n_pos, val, grad, lap, st)
+                                       : launch_bspline_vgl(h, pos, pr, n_pos, val, grad, lap, st);
                 break;
             }
         }

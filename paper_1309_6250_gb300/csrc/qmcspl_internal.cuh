@@ -38,6 +38,8 @@ enum BuildBasis : int {
     kBasisInterp = 1,        // 1 / prod(1 + cos(th)/2)           (interpolating B-spline)
     kBasisGrid = 2,          // 1                                 (grid values: Lagrange)
     kBasisPP = 3,            // prod over label-2 axes of 6(cos th - 1)/(2 + cos th)
+    kBasisInterpN = 4,       // 1 / prod S_n(th), S_n = sum_m C_n B_n(m) e^{i m th}: interpolating
+                             // B-spline of odd degree n on a uniform grid
 };
 enum BuildDeriv : int {
     kDerivValue = 0,         // 1          (phi)
@@ -77,6 +79,9 @@ struct EvalArgs {
     const double2* phase;     // null: real orbitals
     double kc[3];             // Cartesian k (1/bohr)
     float kcf[3];
+    // general B-splines (degree other than 3, or non-uniform grids)
+    const double* knots[3];   // per-axis grid points in [0, 1) (non-uniform grids), else null
+    double cdeg;              // degree-0 constant C of the recurrence
 };
 
 }  // namespace qmcspl
@@ -86,6 +91,11 @@ struct qmcspl_s {
     int device = 0;
     int method = 0, storage = 0, separate_lap = 0;
     int separate_grad = 0;    // B-splines: tables of d_x, d_y, d_z phi too (five tables)
+    int degree = 3;           // odd B-spline degree (interpolating B-splines may use 1, 3, 5, 7)
+    int nonuniform = 0;       // 1: per-axis grid points (cubic interpolating B-splines)
+    int zshift = 1;           // ghost planes below z = 0: (degree - 1) / 2 (pp: 0)
+    double* d_knots = nullptr;            // device copy of the grid points, 3 x kMaxDim
+    double knots[3][qmcspl::kMaxDim];     // host copy (non-uniform grids)
     int dims[3] = {0, 0, 0};
     int n_orb = 0, n_orb_p = 0;   // stored real functions per row (2 per orbital when bloch)
     int n_tables = 0;
@@ -163,6 +173,10 @@ int launch_five_table_vgl(const Handle* h, const double* pos, const Prepared& pr
                           void* grad, void* lap, cudaStream_t stream);
 int launch_pp_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
                   void* grad, void* lap, cudaStream_t stream);
+// B-splines of degree other than 3, or on non-uniform grids (eval_general.cu)
+int launch_general_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
+                       void* grad, void* lap, cudaStream_t stream);
+inline bool is_general(const Handle* h) { return h->degree != 3 || h->nonuniform; }
 int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
                             const void* gv, const void* gg, const void* gl, void* dcoef,
                             void* dcoef_lap, double* dpos, cudaStream_t stream);

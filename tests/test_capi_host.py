@@ -96,13 +96,43 @@ def test_validation_without_gpu(lib):
     assert lib.qmcspl_destroy(None) == _lib.OK
 
 
+def test_grid_options_validated_without_gpu(lib):
+    """qmcspl_create_grid checks degree, method and grid points before touching the device."""
+    lat, mil, coef = inputs.random_cell(2, (8, 8, 8), 2, 4.0, 4.0, np.eye(3) * 6.0)
+
+    def create(degree, knots, method=1, storage=0):
+        h = ctypes.c_void_p()
+        latc = np.ascontiguousarray(lat)
+        dm = np.array([8, 8, 8], dtype=np.int32)
+        c = np.ascontiguousarray(coef.astype(np.complex128)).view(np.float64)
+        opts = _lib.Opts(method, storage, 0, 0)
+        ks = [None if k is None else np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+        g = _lib.GridOpts(degree, (ctypes.c_void_p * 3)(*[None if k is None else k.ctypes.data for k in ks]))
+        return lib.qmcspl_create_grid(ctypes.byref(h), latc.ctypes.data, dm.ctypes.data, mil.shape[0],
+                                      mil.ctypes.data, coef.shape[0], c.ctypes.data, ctypes.byref(opts),
+                                      ctypes.byref(g), None)
+
+    u = np.arange(8) / 8.0
+    assert create(4, (None,) * 3) == _lib.ERR_ARG                       # even degree
+    assert create(5, (None,) * 3, method=0) == _lib.ERR_UNSUPPORTED     # smoothing, degree 5
+    assert create(5, (None,) * 3, storage=3) == _lib.ERR_UNSUPPORTED    # double-float
+    assert create(5, (u, u, u)) == _lib.ERR_UNSUPPORTED                 # non-uniform quintic
+    assert create(3, (u, None, u)) == _lib.ERR_ARG                      # one axis missing
+    bad = u.copy()
+    bad[3] = bad[2]
+    assert create(3, (u, bad, u)) == _lib.ERR_ARG and b"increasing" in lib.qmcspl_last_error()
+    out = u.copy()
+    out[7] = 1.0
+    assert create(3, (u, u, out)) == _lib.ERR_ARG
+
+
 def test_load_rejects_bad_files_without_gpu(lib, tmp_path):
     """qmcspl_load validates the file before touching the device."""
     h = ctypes.c_void_p()
     missing = str(tmp_path / "none.qmcspl").encode()
     assert lib.qmcspl_load(ctypes.byref(h), missing, None) == _lib.ERR_ARG
     bad = tmp_path / "bad.qmcspl"
-    bad.write_bytes(b"NOTQMCSP" + b"\0" * 200)
+    bad.write_bytes(b"NOTQMCSP" + b"\0" * 4096)
     assert lib.qmcspl_load(ctypes.byref(h), str(bad).encode(), None) == _lib.ERR_ARG
     assert b"not a qmcspl table file" in lib.qmcspl_last_error()
     short = tmp_path / "short.qmcspl"
