@@ -345,6 +345,29 @@ def bench_consumer(args, dev, stream):
             "ms_per_step": t * 1e3, "fp64_gflops": flops / t / 1e9}
 
 
+def bench_general(args, dev, stream):
+    """Interpolating B-splines of degree 1, 3, 5, 7 and a graded (non-uniform) cubic grid on
+    the Si-like 8-atom cell (16 orbitals, 48^3, 1024 walkers x 32 electrons, FP32 tables
+    with the Laplacian table): orbital evaluations per second.  Degree 3 on the uniform grid
+    is the tuned cubic kernel, the others the general kernel ((n+1)^3-point stencils)."""
+    import torch
+    from paper_1309_6250_gb300.api import OrbitalSplines
+    w = inputs.make_workload("c2")
+    pos = torch.from_numpy(w.pos).to(dev)
+    evals = w.pos.shape[0] * w.coef.shape[0]
+    out = {}
+    graded = tuple(inputs.graded_knots(d, 0.5, 0.17 * a) for a, d in enumerate(w.cell.grid))
+    for name, kw in (("degree1", dict(degree=1)), ("degree3", dict(degree=3)), ("degree5", dict(degree=5)),
+                     ("degree7", dict(degree=7)), ("graded_cubic", dict(knots=graded))):
+        spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="interp", storage="f32",
+                             separate_lap=True, device=dev, **kw)
+        t = _time_handle(spl, pos, torch, stream, max(10, args.steps // 4))
+        out[name] = {"value": evals / (t * 1e-3), "ms_per_step": t}
+        spl.close()
+    return {"workload": "c2 Si-like 8-atom, 16 orbitals, 48^3, 32768 positions, f32 interpolating + Lap",
+            "unit": UNIT, "results": out}
+
+
 def bench_batched(args, dev, stream):
     """The uneven three-cell workload (Al-like 32-atom: 48 orbitals, 64^3, 512 x 96 e;
     Si-like 64-atom: 128 orbitals, 80^3, 1024 x 256 e; MgO-like 16-atom: 32 orbitals,
@@ -496,7 +519,7 @@ def run_ours(args):
                 "algorithmic_gbs": vb * evals_per_step / vk / 1e9,
                 "frac_of_hbm": vb * evals_per_step / vk / 1e9 / hbm}
 
-    batched = methods = backward = bloch = consumer = None
+    batched = methods = backward = bloch = consumer = general = None
     if not args.no_variants and rank == 0:
         del outs
         spl.close()
@@ -506,6 +529,7 @@ def run_ours(args):
         backward = bench_backward(args, dev, stream)
         bloch = bench_bloch(args, dev, stream)
         consumer = bench_consumer(args, dev, stream)
+        general = bench_general(args, dev, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -542,6 +566,7 @@ def run_ours(args):
         "backward_si64_72": backward,
         "bloch_mgo64_96": bloch,
         "slater_consumer_mgo64": consumer,
+        "general_degree_si8_48": general,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -564,9 +589,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of CUDA-graph replays")
     ap.add_argument("--n-pos", type=int, default=None, help="use only the first N positions (profiling)")
+    ap.add_argument("--only", default="all",
+                    choices=["all", "bloch", "consumer", "general", "methods", "batched", "backward"],
+                    help="run one secondary leg alone and print its JSON (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only != "all":
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        leg = {"bloch": bench_bloch, "consumer": bench_consumer, "general": bench_general,
+               "methods": bench_methods, "batched": bench_batched, "backward": bench_backward}[args.only]
+        print(json.dumps({"leg": args.only, **leg(args, dev, torch.cuda.current_stream())}), flush=True)
     else:
         run_ours(args)
 

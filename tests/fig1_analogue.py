@@ -95,6 +95,43 @@ def run(ecuts: Sequence[float] = ECUTS, storage: str = "f64", use_oracle: bool =
     return rows
 
 
+def run_degrees(ecuts: Sequence[float] = ECUTS, degrees: Sequence[int] = (1, 3, 5, 7), storage: str = "f64",
+                n_orb: int = 16, n_pos: int = 2000, device=None) -> List[Dict]:
+    """Relative MAE of interpolating B-splines of each odd degree at the natural spacing
+    (derivatives of the spline; the Laplacian from a separate table and from the Hessian)."""
+    import torch
+    from paper_1309_6250_gb300.api import OrbitalSplines
+    rows = []
+    for ecut in ecuts:
+        lat, mil, coef, pos = workload(ecut, n_orb, n_pos)
+        dims = natural_dims(lat, ecut)
+        pv, pg, pl, _ = oracle.pw_eval(lat, mil, coef, pos)
+        m = oracle.relative_mean_absolute_error
+        for deg in degrees:
+            res = {"ecut": ecut, "dims": dims, "n_pw": int(mil.shape[0]), "row": "degree%d" % deg}
+            for sep in (False, True):
+                spl = OrbitalSplines(lat, dims, mil, coef, method="interp", storage=storage, separate_lap=sep,
+                                     degree=deg, device=device)
+                v, g, l = (x.double().cpu().numpy() for x in spl.eval_vgl(torch.from_numpy(pos).to(device)))
+                spl.sync()
+                spl.close()
+                if not sep:
+                    res.update(value=m(v, pv), grad=m(g, pg), lap=m(l, pl))
+                else:
+                    res["lap_sep"] = m(l, pl)
+            rows.append(res)
+    return rows
+
+
+def degree_table(rows: List[Dict]) -> str:
+    out = ["| Ecut (Ha) | N | degree | value | grad | lap (Hessian) | lap (separate table) |",
+           "|---|---|---|---|---|---|---|"]
+    for r in rows:
+        out.append("| %g | %d | %s | %.2e | %.2e | %.2e | %.2e |" % (r["ecut"], r["dims"][0], r["row"][6:],
+                                                                  r["value"], r["grad"], r["lap"], r["lap_sep"]))
+    return "\n".join(out)
+
+
 def table(rows: List[Dict]) -> str:
     """Markdown: one table per quantity, cutoffs down, rows of ROWS across."""
     out = []
@@ -115,6 +152,8 @@ def main():
     ap.add_argument("--storage", default="f64", choices=["f64", "f32", "bf16"])
     ap.add_argument("--ecut", type=float, nargs="*", default=list(ECUTS))
     ap.add_argument("--oracle", action="store_true", help="approximations from the oracle (no GPU)")
+    ap.add_argument("--degrees", action="store_true",
+                    help="also tabulate interpolating B-splines of degree 1, 3, 5, 7 (GPU)")
     args = ap.parse_args()
     device = None
     if not args.oracle:
@@ -123,6 +162,9 @@ def main():
     rows = run(args.ecut, args.storage, args.oracle, device=device)
     print("approximations: %s%s" % ("oracle" if args.oracle else "GPU", "" if args.oracle else " " + args.storage))
     print(table(rows))
+    if args.degrees and not args.oracle:
+        print("\ninterpolating B-splines by degree (GPU %s):\n" % args.storage)
+        print(degree_table(run_degrees(args.ecut, storage=args.storage, device=device)))
 
 
 if __name__ == "__main__":
