@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "general_basis.cuh"
 #include "qmcspl_internal.cuh"
@@ -79,6 +80,28 @@ void fill_eval_args(const Handle* h, EvalArgs* a)
 }
 
 bool inv3(const double m[9], double out[9]);
+
+int upload_grid_points(Handle* h, cudaStream_t st)
+{
+    const size_t nd = 3 * (size_t)kMaxDim;
+    std::vector<double> buf(nd * 2 + nd / 2 + 1, 0.0);
+    float* fs = reinterpret_cast<float*>(buf.data() + 2 * nd);
+    for (int a = 0; a < 3; ++a) {
+        const int n = h->dims[a];
+        for (int i = 0; i < n; ++i) {
+            buf[a * kMaxDim + i] = h->knots[a][i];
+            const double sp = periodic_knot(h->knots[a], n, i + 1) - h->knots[a][i];
+            buf[nd + a * kMaxDim + i] = sp;
+            fs[a * kMaxDim + i] = (float)sp;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (!h->d_knots) e = cudaMalloc((void**)&h->d_knots, sizeof(double) * buf.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_knots, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return cuda_error(e, "grid point upload");
+}
 
 // Lattice, inverse and the chain-rule matrices of Sec. II (Coordinates):
 //   grad_cart[a] = sum_i N_i ainv[i][a] grad_t[i]
@@ -387,13 +410,14 @@ int qmcspl_create_grid(qmcspl_t* out, const double lattice[9], const int dims[3]
         return rc;
     }
     e = cudaMalloc((void**)&h->d_err, sizeof(int));
-    if (e == cudaSuccess && nonuni) e = cudaMalloc((void**)&h->d_knots, sizeof(double) * 3 * kMaxDim);
-    if (e == cudaSuccess && nonuni)
-        e = cudaMemcpyAsync(h->d_knots, h->knots, sizeof(double) * 3 * kMaxDim, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->tables, 0, bytes, st);
     if (e != cudaSuccess) {
         rc = cuda_error(e, "table initialisation");
+        free_handle(h);
+        return rc;
+    }
+    if (nonuni && (rc = upload_grid_points(h, st)) != QMCSPL_OK) {
         free_handle(h);
         return rc;
     }

@@ -233,9 +233,7 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMalloc(&h->tables, bytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, sizeof(int));
-    if (e == cudaSuccess && h->nonuniform) e = cudaMalloc((void**)&h->d_knots, sizeof(double) * 3 * kMaxDim);
-    if (e == cudaSuccess && h->nonuniform)
-        e = cudaMemcpyAsync(h->d_knots, h->knots, sizeof(double) * 3 * kMaxDim, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && h->nonuniform && upload_grid_points(h, st) != QMCSPL_OK) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->tables, buf.data(), bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

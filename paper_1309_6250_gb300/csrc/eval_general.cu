@@ -12,7 +12,9 @@
 // so a stencil column is n + 1 contiguous rows.
 //
 // One group of L lanes per position and one 16-byte chunk per lane, as in eval_bspline.cu;
-// scalar arithmetic (this path is not the tuned cubic one).
+// scalar arithmetic (this path is not the tuned cubic one).  With per-position records
+// (order.cu) the cell and local coordinate come precomputed and the weights are built in
+// the table's arithmetic type; without them every lane reduces its position in FP64.
 #include "eval_common.cuh"
 #include "general_basis.cuh"
 
@@ -25,39 +27,46 @@ __device__ __forceinline__ int wrapn(int x, int n)
     return x < 0 ? x + n : x;
 }
 
-// Largest i with knots[i] <= f (f in [0, 1)); points below knots[0] belong to the last
-// interval of the previous period: i = N - 1 and f + 1.
-__device__ __forceinline__ int knot_interval(const double* knots, int n, double& f)
+// Knot spacings of the three axes in the arithmetic type A: the device grid-point buffer
+// holds [3][kMaxDim] points, then [3][kMaxDim] double spacings, then [3][kMaxDim] float ones.
+template <typename A>
+__device__ __forceinline__ const A* spacings(const EvalArgs& p)
 {
-    if (!(f >= knots[0])) {
-        f += 1.0;
-        return n - 1;
-    }
-    int lo = 0, hi = n - 1;   // knots[lo] <= f
-    while (lo < hi) {         // at most log2(512) + 1 steps
-        const int mid = (lo + hi + 1) >> 1;
-        if (knots[mid] <= f) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
+    const double* base = p.knots[0] + 3 * kMaxDim;
+    if constexpr (sizeof(A) == 8) return base;
+    else return reinterpret_cast<const float*>(base + 3 * kMaxDim);
 }
 
-template <typename A, int DEG, bool NONUNI>
-__device__ __forceinline__ void axis_weights(const EvalArgs& p, int axis, double f, int n, int& i0, A* w,
-                                             A* dw, A* d2w)
+// Cell index and local coordinate of the fractional coordinate f in [0, 1) on one axis:
+// uniform grids u = N f, cell floor(u), t = u - floor(u); graded grids the interval of the
+// grid points and the offset from its left point (both in FP64, then rounded to A).
+template <typename A, bool NONUNI>
+__device__ __forceinline__ void locate(const EvalArgs& p, int axis, double f, int n, int& i0, A& loc)
 {
     if constexpr (NONUNI) {
         const double* kn = p.knots[axis];
         double x = f;
         i0 = knot_interval(kn, n, x);
-        nonuniform_cubic_weights<A>(kn, n, i0, x, (A)p.cdeg, w, dw, d2w);
+        loc = (A)(x - kn[i0]);
     } else {
         const double u = (double)n * f;
         const double fl = floor(u);
         int k = (int)fl;
         if (k >= n) k -= n;
         i0 = k;
-        uniform_weights<A, DEG>((A)(u - fl), (A)p.cdeg, w, dw, d2w);
+        loc = (A)(u - fl);
+    }
+}
+
+// Weights of one axis from its cell and local coordinate.
+template <typename A, int DEG, bool NONUNI>
+__device__ __forceinline__ void axis_weights(const EvalArgs& p, int axis, int i0, A loc, A* w, A* dw, A* d2w)
+{
+    if constexpr (NONUNI) {
+        const int n = axis == 0 ? p.nx : (axis == 1 ? p.ny : p.nz);
+        nonuniform_cubic_weights_local<A, A>(spacings<A>(p) + axis * kMaxDim, n, i0, loc, (A)p.cdeg, w, dw, d2w);
+    } else {
+        uniform_weights<A, DEG>(loc, (A)p.cdeg, w, dw, d2w);
     }
 }
 
@@ -87,25 +96,49 @@ __global__ void __launch_bounds__(kEvalThreads, 1) general_vgl_kernel(const Eval
         const long long q = gid / p.tiles;
         const int tile = (int)(gid - q * p.tiles);
         const long long ip = p.perm ? (long long)p.perm[q] : q;
-        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
-        double f[3];
+        // cell and local coordinate per axis (t on uniform grids, the offset from the
+        // interval's left grid point on graded ones): from the per-position record, or
+        // reduced here in FP64; the weights are then built once, from these alone
+        int ci[3];
+        A loc[3];
         bool ok = true;
+        if (p.rec) {
+            int cell;
+            if constexpr (sizeof(A) == 8) {
+                const double2* qr = static_cast<const double2*>(p.rec) + 2 * ip;
+                const double2 a0 = __ldg(qr), a1 = __ldg(qr + 1);
+                loc[0] = a0.x;
+                loc[1] = a0.y;
+                loc[2] = a1.x;
+                cell = __double2loint(a1.y);
+            } else {
+                const float4 qr = __ldg(static_cast<const float4*>(p.rec) + ip);
+                cell = __float_as_int(qr.x);
+                loc[0] = qr.y;
+                loc[1] = qr.z;
+                loc[2] = qr.w;
+            }
+            unpack_cell(cell, ci[0], ci[1], ci[2], ok);
+        } else {
+            const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+            const int dims[3] = {p.nx, p.ny, p.nz};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const double s = crystal(p.ainv[3 * a], p.ainv[3 * a + 1], p.ainv[3 * a + 2], r);
-            f[a] = s - floor(s);
-            ok = ok && isfinite(f[a]);
+            for (int a = 0; a < 3; ++a) {
+                const double s = crystal(p.ainv[3 * a], p.ainv[3 * a + 1], p.ainv[3 * a + 2], r);
+                double f = s - floor(s);
+                const bool o = isfinite(f);
+                ok = ok && o;
+                if (!o) f = 0.0;
+                locate<A, NONUNI>(p, a, f, dims[a], ci[a], loc[a]);
+                if (!o) loc[a] = A(__longlong_as_double(0x7ff8000000000000LL));
+            }
         }
-        if (!ok) {
-            if (sub == 0 && tile == 0) atomicOr(p.err, 1);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) f[a] = 0.0;
-        }
-        int ix, iy, iz;
+        if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+        const int ix = ci[0], iy = ci[1], iz = ci[2];
         A wx[W], dwx[W], d2wx[W], wy[W], dwy[W], d2wy[W], wz[W], dwz[W], d2wz[W];
-        axis_weights<A, DEG, NONUNI>(p, 0, f[0], p.nx, ix, wx, dwx, LAPTAB ? nullptr : d2wx);
-        axis_weights<A, DEG, NONUNI>(p, 1, f[1], p.ny, iy, wy, dwy, LAPTAB ? nullptr : d2wy);
-        axis_weights<A, DEG, NONUNI>(p, 2, f[2], p.nz, iz, wz, dwz, LAPTAB ? nullptr : d2wz);
+        axis_weights<A, DEG, NONUNI>(p, 0, ix, loc[0], wx, dwx, LAPTAB ? nullptr : d2wx);
+        axis_weights<A, DEG, NONUNI>(p, 1, iy, loc[1], wy, dwy, LAPTAB ? nullptr : d2wy);
+        axis_weights<A, DEG, NONUNI>(p, 2, iz, loc[2], wz, dwz, LAPTAB ? nullptr : d2wz);
         if (!ok) {   // NaN outputs for a non-finite position
             const A nan = A(__longlong_as_double(0x7ff8000000000000LL));
 #pragma unroll
@@ -224,7 +257,7 @@ int launch_general_vgl(const Handle* h, const double* pos, const Prepared& pr, l
     EvalArgs a;
     fill_eval_args(h, &a);
     a.pos = pos;
-    a.rec = nullptr;          // this kernel reduces its own coordinates
+    a.rec = pr.rec;           // records of kind 1/2 (uniform) or 4/5 (non-uniform), or none
     a.perm = pr.perm;
     a.phase = pr.phase;
     a.n_pos = n_pos;

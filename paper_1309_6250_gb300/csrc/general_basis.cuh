@@ -100,6 +100,24 @@ __host__ __device__ inline double periodic_knot(const double* knots, int n, int 
     return knots[r] + (double)q;
 }
 
+// Largest i with knots[i] <= f (f in [0, 1)); points below knots[0] belong to the last
+// interval of the previous period: i = n - 1 and f becomes f + 1.  Bisection, at most
+// log2(n) + 1 steps.
+__host__ __device__ inline int knot_interval(const double* knots, int n, double& f)
+{
+    if (!(f >= knots[0])) {
+        f += 1.0;
+        return n - 1;
+    }
+    int lo = 0, hi = n - 1;   // knots[lo] <= f
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (knots[mid] <= f) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 // Cubic weights on the non-uniform interval [x_i, x_{i+1}) at x (same period as the knots),
 // for the grid points i-1 .. i+2, and their first and second derivatives with respect to
 // the reduced coordinate.  De Boor's triangular evaluation of the recurrence.
@@ -143,6 +161,62 @@ __host__ __device__ inline void nonuniform_cubic_weights(const double* knots, in
         const int k = i - 3 + r;          // start knot of the function of grid point i-1+r
         w[r] = C * (A)N3[r];
         const double ak = 3.0 / (kn(k + 3) - kn(k)), bk = 3.0 / (kn(k + 4) - kn(k + 1));
+        dw[r] = C * (A)(ak * b2(k) - bk * b2(k + 1));
+        if (d2w) d2w[r] = C * (A)(ak * db2(k) - bk * db2(k + 1));
+    }
+}
+
+// The same cubic weights from the offset dx = x - x_i inside interval i and the periodic
+// knot spacings hs[j] = x_{j+1} - x_j (j mod n), in the arithmetic type S of the spacings:
+// every knot difference the recurrence needs is a sum of consecutive spacings, so no
+// absolute coordinate (and no FP64 for FP32 tables) is involved.
+template <typename S, typename A>
+__host__ __device__ inline void nonuniform_cubic_weights_local(const S* hs, int n, int i, S dx, A C, A* w,
+                                                               A* dw, A* d2w)
+{
+    auto h = [&](int j) -> S {
+        j %= n;
+        return hs[j < 0 ? j + n : j];
+    };
+    // kd(a, b) = x_a - x_b for b <= a <= b + 4
+    auto kd = [&](int a, int b) -> S {
+        S s = S(0);
+        for (int j = b; j < a; ++j) s += h(j);
+        return s;
+    };
+    S left[4], right[4];
+    left[1] = dx;
+    left[2] = dx + h(i - 1);
+    left[3] = left[2] + h(i - 2);
+    right[1] = h(i) - dx;
+    right[2] = right[1] + h(i + 1);
+    right[3] = right[2] + h(i + 2);
+    S N1[2], N2[3];
+    S Nl[4] = {S(1), S(0), S(0), S(0)};
+    for (int j = 1; j <= 3; ++j) {
+        S saved = S(0);
+        for (int r = 0; r < j; ++r) {
+            const S temp = Nl[r] / (right[r + 1] + left[j - r]);
+            Nl[r] = saved + right[r + 1] * temp;
+            saved = left[j - r] * temp;
+        }
+        Nl[j] = saved;
+        if (j == 1) { N1[0] = Nl[0]; N1[1] = Nl[1]; }
+        if (j == 2) { N2[0] = Nl[0]; N2[1] = Nl[1]; N2[2] = Nl[2]; }
+    }
+    auto b1 = [&](int k) -> S {
+        const int q = k - (i - 1);
+        return (q >= 0 && q <= 1) ? N1[q] : S(0);
+    };
+    auto b2 = [&](int k) -> S {
+        const int q = k - (i - 2);
+        return (q >= 0 && q <= 2) ? N2[q] : S(0);
+    };
+    auto db2 = [&](int k) -> S { return S(2) * (b1(k) / kd(k + 2, k) - b1(k + 1) / kd(k + 3, k + 1)); };
+    for (int r = 0; r < 4; ++r) {
+        const int k = i - 3 + r;
+        w[r] = C * (A)Nl[r];
+        const S ak = S(3) / kd(k + 3, k), bk = S(3) / kd(k + 4, k + 1);
         dw[r] = C * (A)(ak * b2(k) - bk * b2(k + 1));
         if (d2w) d2w[r] = C * (A)(ak * db2(k) - bk * db2(k + 1));
     }

@@ -17,6 +17,7 @@
 // 3. Bloch phase factors (Sec. II, phi = u exp(i k.r)).  exp(i k.r) at the unwrapped
 //    position, in FP64, once per position, for the evaluation epilogues.
 #include "eval_common.cuh"
+#include "general_basis.cuh"
 
 namespace qmcspl {
 namespace {
@@ -36,6 +37,7 @@ struct PrepArgs {
     int nb[3];
     void* rec;                // records (kind 1, 2 or 3), may be null
     double2* phase;           // Bloch phase factors, may be null
+    const double* knots;      // non-uniform grids: [3][kMaxDim] grid points (record kinds 4, 5)
     double kred[3];           // a^-T kpoint: k.r = 2 pi (kred . r)
     int* bin;                 // per-position bin (with count)
     int* count;               // bin counters, null: no binning
@@ -53,6 +55,37 @@ __device__ __forceinline__ void reduce_position(const PrepArgs& a, long long i, 
     ok = o0 && o1 && o2;
 }
 
+// Non-uniform grids: per axis the interval of the grid points that holds the position and
+// the offset from its left point (reduced units).
+__device__ __forceinline__ void locate_position(const PrepArgs& a, long long i, int& ix, int& iy, int& iz,
+                                                double& tx, double& ty, double& tz, bool& ok)
+{
+    const double r[3] = {a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2]};
+    int c[3];
+    double d[3];
+    ok = true;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double s = crystal(a.ainv[3 * ax], a.ainv[3 * ax + 1], a.ainv[3 * ax + 2], r);
+        double f = s - floor(s);
+        const bool o = isfinite(f);
+        ok = ok && o;
+        if (o) {
+            const double* kn = a.knots + ax * kMaxDim;
+            c[ax] = knot_interval(kn, a.dims[ax], f);
+            d[ax] = f - kn[c[ax]];
+        } else {
+            c[ax] = 0;
+            d[ax] = __longlong_as_double(0x7ff8000000000000LL);
+        }
+    }
+    ix = c[0];
+    iy = c[1];
+    iz = c[2];
+    tx = d[0];
+    ty = d[1];
+    tz = d[2];
+}
+
 template <int KIND>
 __global__ void prepare_kernel(const PrepArgs a)
 {
@@ -61,11 +94,12 @@ __global__ void prepare_kernel(const PrepArgs a)
     int ix, iy, iz;
     double tx, ty, tz;
     bool ok;
-    reduce_position(a, i, ix, iy, iz, tx, ty, tz, ok);
+    if (KIND >= 4) locate_position(a, i, ix, iy, iz, tx, ty, tz, ok);
+    else reduce_position(a, i, ix, iy, iz, tx, ty, tz, ok);
     const int cell = ok ? (ix | (iy << 10) | (iz << 20)) : -1;
-    if (KIND == 1) {
+    if (KIND == 1 || KIND == 4) {
         static_cast<float4*>(a.rec)[i] = make_float4(__int_as_float(cell), (float)tx, (float)ty, (float)tz);
-    } else if (KIND == 2) {
+    } else if (KIND == 2 || KIND == 5) {
         double2* q = static_cast<double2*>(a.rec) + 2 * i;
         q[0] = make_double2(tx, ty);
         q[1] = make_double2(tz, __hiloint2double(0, cell));
@@ -142,6 +176,7 @@ PrepArgs prep_args(const Handle* h, const double* pos, long long n, void* rec, d
     a.pos = pos;
     a.n = n;
     a.phase = phase;
+    a.knots = h->nonuniform ? h->d_knots : nullptr;
     for (int i = 0; i < 3; ++i) a.kred[i] = h->kred[i];
     for (int i = 0; i < 9; ++i) a.ainv[i] = h->ainv[i];
     for (int i = 0; i < 3; ++i) {
@@ -162,6 +197,8 @@ int launch_prepare(const PrepArgs& a, int kind, cudaStream_t st)
     case 1: prepare_kernel<1><<<blocks, 256, 0, st>>>(a); break;
     case 2: prepare_kernel<2><<<blocks, 256, 0, st>>>(a); break;
     case 3: prepare_kernel<3><<<blocks, 256, 0, st>>>(a); break;
+    case 4: prepare_kernel<4><<<blocks, 256, 0, st>>>(a); break;
+    case 5: prepare_kernel<5><<<blocks, 256, 0, st>>>(a); break;
     default: prepare_kernel<0><<<blocks, 256, 0, st>>>(a); break;
     }
     return cuda_error(cudaGetLastError(), "prepare_kernel launch");
@@ -199,6 +236,7 @@ bool use_cell_order(const Handle* h, long long n_pos)
 
 int record_kind(const Handle* h)
 {
+    if (h->nonuniform) return h->storage == QMCSPL_F64 ? 5 : 4;
     if (h->storage == QMCSPL_DF64) return 3;
     if (h->storage == QMCSPL_F64) return 2;
     return 1;

@@ -94,7 +94,8 @@ struct qmcspl_s {
     int degree = 3;           // odd B-spline degree (interpolating B-splines may use 1, 3, 5, 7)
     int nonuniform = 0;       // 1: per-axis grid points (cubic interpolating B-splines)
     int zshift = 1;           // ghost planes below z = 0: (degree - 1) / 2 (pp: 0)
-    double* d_knots = nullptr;            // device copy of the grid points, 3 x kMaxDim
+    double* d_knots = nullptr;            // device: grid points [3][kMaxDim], their periodic
+                                          // spacings [3][kMaxDim] (double), then as float
     double knots[3][qmcspl::kMaxDim];     // host copy (non-uniform grids)
     int dims[3] = {0, 0, 0};
     int n_orb = 0, n_orb_p = 0;   // stored real functions per row (2 per orbital when bloch)
@@ -206,6 +207,8 @@ int cell_order(Handle* h, const double* pos, long long n_pos, const int** perm, 
 //   kind 1 (float / bfloat16 tables): 16 bytes {int cell, float tx, ty, tz}
 //   kind 2 (double tables):           32 bytes {double tx, ty, tz; int cell, pad}
 //   kind 3 (double-float tables):     32 bytes {int cell, float txh, txl, tyh, tyl, tzh, tzl, pad}
+//   kind 4, 5: as kinds 1, 2 for non-uniform grids, with the offset of the position from the
+//              left grid point of its interval (reduced units) in place of t
 // cell = ix | iy << 10 | iz << 20, or -1 for a non-finite position.
 // With `count` non-null the kernel also bins the positions for the cell order.
 int record_kind(const Handle* h);
@@ -216,6 +219,9 @@ int build_records(const Handle* h, const double* pos, long long n_pos, void* rec
 // handle's scratch.
 int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, Prepared* out,
                       cudaStream_t stream);
+
+// Allocate (once) and fill the device grid-point buffer of a non-uniform handle.
+int upload_grid_points(Handle* h, cudaStream_t stream);
 
 // fill the common part of EvalArgs from a handle
 void fill_eval_args(const Handle* h, EvalArgs* a);
