@@ -357,20 +357,28 @@ int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void
  *   val, grad, lap  device outputs of qmcspl_eval_vgl of a real-orbital handle for
  *          P = n_walkers x n_elec positions ordered walker-major, layouts [P][n_orb],
  *          [P][3][n_orb], [P][n_orb]; dtype 0 = double, 1 = float
+ *   arith  enum qmcspl_slater_arith
  *   n_orb  the output row length O, >= both block sizes
  *   n_up   0 .. n_elec; each block at most QMCSPL_SLATER_MAX_BLOCK electrons
  *   logdet, sign, kinetic  device double[n_walkers], each may be NULL (kinetic needs lap)
  *   drift  device double[n_walkers][n_elec][3] or NULL (needs grad)
  *   stream cudaStream_t; asynchronous
- * The inversion is FP64 Gauss-Jordan elimination with row pivoting in shared memory, one
- * thread block per walker.  An exactly singular block gives sign 0, logdet -inf and NaN
+ * The inversion is Gauss-Jordan elimination with row pivoting in shared memory, one thread
+ * block per walker, in FP64 or in double-float (arith).  An exactly singular block gives sign 0, logdet -inf and NaN
  * kinetic energy and drift for that walker; nearly singular blocks lose accuracy as the
  * condition number grows.
  */
 #define QMCSPL_SLATER_MAX_BLOCK 160
-int qmcspl_slater_kinetic(const void* val, const void* grad, const void* lap, int dtype, long long n_walkers,
-                          int n_elec, int n_up, int n_orb, double* logdet, double* sign, double* kinetic,
-                          double* drift, void* stream);
+enum qmcspl_slater_arith {
+    QMCSPL_SLATER_FP64 = 0,   /* FP64 elimination (GB300's FP64 pipe) */
+    QMCSPL_SLATER_DF64 = 1    /* double-float elimination on the FP32 pipe: each entry a pair
+                                 of floats (~48 significant bits), error-free FP32 updates;
+                                 results agree with FP64 to about 1e-13 times the condition
+                                 number */
+};
+int qmcspl_slater_kinetic(const void* val, const void* grad, const void* lap, int dtype, int arith,
+                          long long n_walkers, int n_elec, int n_up, int n_orb, double* logdet, double* sign,
+                          double* kinetic, double* drift, void* stream);
 
 /*
  * qmcspl_profile / qmcspl_profile_read -- CUDA-event timing of the library's own kernels.

@@ -34,6 +34,7 @@ DF64 = 3
 MAX_BATCH = 48
 NOALLOC_MAX_POS = 1 << 20
 SLATER_MAX_BLOCK = 160
+SLATER_ARITH = {"f64": 0, "df64": 1}
 
 ORDER_AUTO = 0
 ORDER_INPUT = 1
@@ -95,7 +96,7 @@ PROTOTYPES = [
                                 ctypes.POINTER(ctypes.c_longlong)]),
     ("qmcspl_save", I, [VP, ctypes.c_char_p]),
     ("qmcspl_load", I, [ctypes.POINTER(VP), ctypes.c_char_p, VP]),
-    ("qmcspl_slater_kinetic", I, [VP, VP, VP, I, LL, I, I, I, VP, VP, VP, VP, VP]),
+    ("qmcspl_slater_kinetic", I, [VP, VP, VP, I, I, LL, I, I, I, VP, VP, VP, VP, VP]),
     ("qmcspl_sync", I, [VP, VP]),
     ("qmcspl_last_error", ctypes.c_char_p, []),
     ("qmcspl_version", I, []),

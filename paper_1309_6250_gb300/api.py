@@ -247,10 +247,12 @@ def eval_batched(splines: Sequence[OrbitalSplines], positions: Sequence[torch.Te
 
 
 def slater_kinetic(val: torch.Tensor, grad: Optional[torch.Tensor], lap: Optional[torch.Tensor],
-                   n_walkers: int, n_elec: int, n_up: int, want_drift: bool = True, stream=None):
+                   n_walkers: int, n_elec: int, n_up: int, want_drift: bool = True, stream=None,
+                   arith: str = "df64"):
     """Slater-determinant consumer of eval_vgl outputs (walker-major positions, electrons
     0..n_up-1 spin up): returns (logdet [W], sign [W], kinetic [W], drift [W, n_elec, 3] or
-    None), float64 tensors on the outputs' device."""
+    None), float64 tensors on the outputs' device.  arith: 'df64' (double-float elimination
+    on the FP32 pipe) or 'f64'."""
     lib = _lib.load()
     if val.dtype not in (torch.float32, torch.float64):
         raise ValueError("real float32/float64 orbital outputs expected")
@@ -267,7 +269,8 @@ def slater_kinetic(val: torch.Tensor, grad: Optional[torch.Tensor], lap: Optiona
     c = lambda t: None if t is None else t.contiguous()
     val, grad, lap = c(val), c(grad), c(lap)
     with torch.cuda.device(val.device):
-        _lib.check(lib.qmcspl_slater_kinetic(_ptr(val), _ptr(grad), _ptr(lap), dtype, n_walkers, n_elec, n_up,
+        _lib.check(lib.qmcspl_slater_kinetic(_ptr(val), _ptr(grad), _ptr(lap), dtype, _lib.SLATER_ARITH[arith],
+                                             n_walkers, n_elec, n_up,
                                              n_orb, _ptr(logdet), _ptr(sign), _ptr(kin), _ptr(drift),
                                              _stream_handle(stream)))
     return logdet, sign, kin, drift

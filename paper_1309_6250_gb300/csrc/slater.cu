@@ -17,16 +17,25 @@
 // row swaps become a column permutation of the inverse, applied by index.  The kinetic
 // term and the drift then read lap and grad rows once, coalesced.
 //
-// The elimination is n^3 FP64 FMAs per block (2.1 M for n = 128), so this consumer runs on
-// GB300's FP64 pipe; every loop is bounded by n.
+// The elimination is n^3 multiply-adds per block (2.1 M for n = 128).  Two arithmetic
+// modes: FP64 (GB300's FP64 pipe bounds it), and double-float, where every matrix entry is
+// a pair of floats (hi + lo, ~48 significant bits) and each elimination update is an
+// error-free FP32 multiply-add done two columns at a time with fma.rn.f32x2 (see df_fma2):
+// the FP32 pipe carries it, several times faster on this part.  Every loop is bounded by n.
 #include <cmath>
 
-#include "qmcspl_internal.cuh"
+#include "eval_common.cuh"
 
 namespace qmcspl {
 namespace {
 
 constexpr int kSlaterThreads = 256;
+#ifndef QMCSPL_SLATER_DF_THREADS
+#define QMCSPL_SLATER_DF_THREADS 512
+#endif
+// double-float kernel: one CTA per SM (its matrix fills shared memory), so the CTA itself
+// must bring the warps that hide the latency of the dependent FP32 chains
+constexpr int kSlaterDfThreads = QMCSPL_SLATER_DF_THREADS;
 constexpr int kSlaterMaxBlock = QMCSPL_SLATER_MAX_BLOCK;
 
 struct SlaterArgs {
@@ -39,6 +48,7 @@ struct SlaterArgs {
     double* sign;
     double* kinetic;
     double* drift;
+    int arith;                // 0: FP64, 1: double-float
 };
 
 template <typename T>
@@ -47,7 +57,8 @@ __device__ __forceinline__ double ld(const void* p, long long i)
     return (double)__ldg(static_cast<const T*>(p) + i);
 }
 
-// Block-wide sum of one double per thread; every thread gets the total.
+// Block-wide sum of one double per thread (NT threads); every thread gets the total.
+template <int NT = kSlaterThreads>
 __device__ double block_sum(double v, double* red)
 {
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -56,8 +67,26 @@ __device__ double block_sum(double v, double* red)
     if (lane == 0) red[wid] = v;
     __syncthreads();
     double t = 0.0;
-    for (int w = 0; w < kSlaterThreads / 32; ++w) t += red[w];
+    for (int w = 0; w < NT / 32; ++w) t += red[w];
     return t;
+}
+
+// ln|det| = sum_k ln|pivot_k| over the block's pivots (one logarithm per pivot, spread over
+// the threads); sgn is multiplied by the sign of the determinant (pivot signs and row swaps).
+// Called by all threads.
+template <int NT = kSlaterThreads>
+__device__ double pivot_logdet(const double* pivd, const int* piv, int n, double& sgn, double* red)
+{
+    double part = 0.0;
+    int neg = 0;
+    for (int k = threadIdx.x; k < n; k += NT) {
+        part += log(fabs(pivd[k]));
+        neg += (pivd[k] < 0.0) + (piv[k] != k);
+    }
+    const double ld = block_sum<NT>(part, red);
+    const double nn = block_sum<NT>((double)neg, red);
+    if (((long long)nn) & 1) sgn = -sgn;
+    return ld;
 }
 
 template <typename T>
@@ -71,6 +100,7 @@ __global__ void __launch_bounds__(kSlaterThreads) slater_kernel(const SlaterArgs
     __shared__ double rowk[kSlaterMaxBlock];
     __shared__ int s_p;
     __shared__ double s_d;
+    __shared__ double pivd[kSlaterMaxBlock];   // pivot values: ln|det| and sign at the end
 
     const long long w = blockIdx.x;
     if (w >= a.n_walkers) return;
@@ -118,6 +148,7 @@ __global__ void __launch_bounds__(kSlaterThreads) slater_kernel(const SlaterArgs
                     s_p = bi;
                     s_d = A[bi * ns + k];   // the pivot value (the swap below moves, not changes, it)
                     piv[k] = bi;
+                    pivd[k] = s_d;
                 }
             }
             __syncthreads();
@@ -134,9 +165,6 @@ __global__ void __launch_bounds__(kSlaterThreads) slater_kernel(const SlaterArgs
                 sing = true;
                 break;
             }
-            logdet += log(fabs(d));
-            if (d < 0.0) sgn = -sgn;
-            if (p != k) sgn = -sgn;
             // scaled pivot row (its pivot entry becomes 1/d) and the pivot column
             for (int j = tid; j < n; j += kSlaterThreads) {
                 const double r = (j == k ? 1.0 : A[k * ns + j]) / d;
@@ -161,6 +189,7 @@ __global__ void __launch_bounds__(kSlaterThreads) slater_kernel(const SlaterArgs
             singular = true;
             break;
         }
+        logdet += pivot_logdet(pivd, piv, n, sgn, red);
         // The row swaps of the elimination permute the columns of the inverse: undoing
         // them in reverse order maps column c of A^-1 to column colmap[c] of A.
         if (tid == 0) {
@@ -207,16 +236,273 @@ __global__ void __launch_bounds__(kSlaterThreads) slater_kernel(const SlaterArgs
     }
 }
 
+// 1 / d in double-float: one Newton step on the float reciprocal, e = 1 - d y to ~2^-48.
+__device__ __forceinline__ dfloat df_recip(dfloat d)
+{
+    const float y = 1.0f / d.h;
+    const float p = __fmul_rn(d.h, y);
+    const float pe = fmaf(d.h, y, -p);                  // d.h y = p + pe exactly
+    const float e = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, p), pe), __fmul_rn(d.l, y));
+    return df_norm(y, __fmul_rn(y, e));
+}
+
+// The same computation in double-float.  Shared memory holds the matrix as two float arrays
+// Ah, Al of [n][ns] with ns = n rounded up to even, plus 2 (zero padding columns stay zero
+// through the elimination), so that column pairs (j, j+1) are one 8-byte word of each.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 1) slater_df_kernel(const SlaterArgs a)
+{
+    extern __shared__ float fsm[];
+    __shared__ double red[NT / 32];
+    __shared__ int piv[kSlaterMaxBlock];
+    __shared__ int colmap[kSlaterMaxBlock];
+    __shared__ f32x2 fw[3][kSlaterMaxBlock];   // per row: (-f_h, -f_h), (-f_l, -f_l), (f_h, f_h)
+    __shared__ __align__(8) float rkh[kSlaterMaxBlock + 2], rkl[kSlaterMaxBlock + 2];
+    __shared__ int s_p;
+    __shared__ float s_dh, s_dl;
+    __shared__ double pivd[kSlaterMaxBlock];
+
+    const long long w = blockIdx.x;
+    if (w >= a.n_walkers) return;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    const long long O = a.n_orb;
+    double logdet = 0.0, sgn = 1.0, kin = 0.0;
+    bool singular = false;
+
+    for (int blk = 0; blk < 2; ++blk) {
+        const int e0 = blk == 0 ? 0 : a.n_up;
+        const int n = blk == 0 ? a.n_up : a.n_elec - a.n_up;
+        if (n == 0) continue;
+        const int nw = (n + 1) & ~1;                        // columns processed, in pairs
+        const int ns = nw + 2;                              // row stride (floats)
+        const long long base = w * a.n_elec + e0;
+        float* Ah = fsm;
+        float* Al = fsm + (size_t)n * ns;
+
+        __syncthreads();
+        for (int i = wid; i < n; i += NT / 32)
+            for (int j = lane; j < ns; j += 32) {
+                const double v = j < n ? ld<T>(a.val, (base + i) * O + j) : 0.0;
+                const dfloat x = df_from_double(v);
+                Ah[i * ns + j] = x.h;
+                Al[i * ns + j] = x.l;
+            }
+        __syncthreads();
+
+        bool sing = false;
+        for (int k = 0; k < n; ++k) {
+            if (wid == 0) {
+                float best = -1.0f;
+                int bi = k;
+                for (int i = k + lane; i < n; i += 32) {
+                    const float v = fabsf(Ah[i * ns + k]);
+                    if (v > best) {
+                        best = v;
+                        bi = i;
+                    }
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                    }
+                }
+                if (lane == 0) {
+                    s_p = bi;
+                    s_dh = Ah[bi * ns + k];
+                    s_dl = Al[bi * ns + k];
+                    piv[k] = bi;
+                    pivd[k] = (double)s_dh + (double)s_dl;
+                }
+            }
+            __syncthreads();
+            const int p = s_p;
+            const dfloat d = {s_dh, s_dl};
+            if (p != k)
+                for (int j = tid; j < nw; j += NT) {
+                    float t = Ah[k * ns + j];
+                    Ah[k * ns + j] = Ah[p * ns + j];
+                    Ah[p * ns + j] = t;
+                    t = Al[k * ns + j];
+                    Al[k * ns + j] = Al[p * ns + j];
+                    Al[p * ns + j] = t;
+                }
+            __syncthreads();
+            if (d.h == 0.0f) {   // exactly singular (uniform)
+                sing = true;
+                break;
+            }
+            const dfloat inv = df_recip(d);
+            for (int j = tid; j < nw; j += NT) {
+                const dfloat x = (j == k) ? dfloat{1.0f, 0.0f} : dfloat{Ah[k * ns + j], Al[k * ns + j]};
+                const dfloat r = df_mul(x, inv);
+                rkh[j] = r.h;
+                rkl[j] = r.l;
+                Ah[k * ns + j] = r.h;
+                Al[k * ns + j] = r.l;
+            }
+            // pivot column of the other rows: the multipliers, packed for the update, and the
+            // entries set to 0 so that the update leaves -f_i / d there (Gauss-Jordan)
+            for (int i = tid; i < n; i += NT)
+                if (i != k) {
+                    const float fh = Ah[i * ns + k], fl = Al[i * ns + k];
+                    Ah[i * ns + k] = 0.0f;
+                    Al[i * ns + k] = 0.0f;
+                    fw[0][i] = pack2(-fh, -fh);
+                    fw[1][i] = pack2(-fl, -fl);
+                    fw[2][i] = pack2(fh, fh);
+                }
+            __syncthreads();
+            // A[i][j] += (-f_i) rowk[j], two columns per packed operation.  A lane holds two
+            // column pairs of rowk in registers and updates four rows for each (eight
+            // independent error-free chains), loads first, then arithmetic, then stores.
+            {
+                constexpr int R = 4, NW = NT / 32;
+                const f32x2* rh2 = reinterpret_cast<const f32x2*>(rkh);
+                const f32x2* rl2 = reinterpret_cast<const f32x2*>(rkl);
+                const int np = nw / 2;
+                for (int m0 = lane; m0 < np; m0 += 64) {
+                    const int m1 = m0 + 32;
+                    const bool v1 = m1 < np;
+                    const f32x2 Bh0 = rh2[m0], Bl0 = rl2[m0];
+                    const f32x2 Bh1 = v1 ? rh2[m1] : 0ull, Bl1 = v1 ? rl2[m1] : 0ull;
+                    for (int ib = wid; ib < n; ib += R * NW) {
+                        f32x2 Xh[2 * R], Xl[2 * R];
+                        bool act[R];
+#pragma unroll
+                        for (int u = 0; u < R; ++u) {
+                            const int i = ib + u * NW;
+                            act[u] = i < n && i != k;
+                            const f32x2* ph = reinterpret_cast<const f32x2*>(Ah + i * ns);
+                            const f32x2* pl = reinterpret_cast<const f32x2*>(Al + i * ns);
+                            Xh[2 * u] = act[u] ? ph[m0] : 0ull;
+                            Xl[2 * u] = act[u] ? pl[m0] : 0ull;
+                            Xh[2 * u + 1] = (act[u] && v1) ? ph[m1] : 0ull;
+                            Xl[2 * u + 1] = (act[u] && v1) ? pl[m1] : 0ull;
+                        }
+#pragma unroll
+                        for (int u = 0; u < R; ++u) {
+                            const int i = ib + u * NW;
+                            const int ii = act[u] ? i : 0;
+                            const f32x2 wh = fw[0][ii], wl = fw[1][ii], nwh = fw[2][ii];
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                f32x2& H = Xh[2 * u + q];
+                                f32x2& Lo = Xl[2 * u + q];
+                                df_fma2(H, Lo, wh, wl, nwh, q ? Bh1 : Bh0, q ? Bl1 : Bl0);
+                                // renormalise (two-sum): entries are updated n times and reused
+                                // as pivots, multipliers and reciprocals (|lo| << |hi| assumed)
+                                const f32x2 S = add2(H, Lo);
+                                const f32x2 BB = sub2(S, H);
+                                Lo = add2(sub2(H, sub2(S, BB)), sub2(Lo, BB));
+                                H = S;
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < R; ++u) {
+                            const int i = ib + u * NW;
+                            if (!act[u]) continue;
+                            f32x2* ph = reinterpret_cast<f32x2*>(Ah + i * ns);
+                            f32x2* pl = reinterpret_cast<f32x2*>(Al + i * ns);
+                            ph[m0] = Xh[2 * u];
+                            pl[m0] = Xl[2 * u];
+                            if (v1) {
+                                ph[m1] = Xh[2 * u + 1];
+                                pl[m1] = Xl[2 * u + 1];
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (sing) {
+            singular = true;
+            break;
+        }
+        logdet += pivot_logdet<NT>(pivd, piv, n, sgn, red);
+        if (tid == 0) {
+            for (int c = 0; c < n; ++c) colmap[c] = c;
+            for (int k = n - 1; k >= 0; --k) {
+                const int t = colmap[k];
+                colmap[k] = colmap[piv[k]];
+                colmap[piv[k]] = t;
+            }
+        }
+        __syncthreads();
+        // the inverse entries as doubles (h + l) for the final dot products
+        if (a.kinetic) {
+            double part = 0.0;
+            for (int i = wid; i < n; i += NT / 32) {
+                const int ci = colmap[i];
+                for (int j = lane; j < n; j += 32) {
+                    const double x = (double)Ah[j * ns + ci] + (double)Al[j * ns + ci];
+                    part = fma(x, ld<T>(a.lap, (base + i) * O + j), part);
+                }
+            }
+            kin += -0.5 * block_sum<NT>(part, red);
+        }
+        if (a.drift) {
+            for (int ic = wid; ic < 3 * n; ic += NT / 32) {
+                const int i = ic / 3, c = ic - (ic / 3) * 3;
+                const int ci = colmap[i];
+                double s = 0.0;
+                for (int j = lane; j < n; j += 32) {
+                    const double x = (double)Ah[j * ns + ci] + (double)Al[j * ns + ci];
+                    s = fma(x, ld<T>(a.grad, ((base + i) * 3 + c) * O + j), s);
+                }
+                for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                if (lane == 0) a.drift[((w * a.n_elec) + e0 + i) * 3 + c] = s;
+            }
+        }
+    }
+    if (tid == 0) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        const double inf = __longlong_as_double(0x7ff0000000000000LL);
+        if (a.logdet) a.logdet[w] = singular ? -inf : logdet;
+        if (a.sign) a.sign[w] = singular ? 0.0 : sgn;
+        if (a.kinetic) a.kinetic[w] = singular ? nan : kin;
+    }
+    if (singular && a.drift) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        for (int e = tid; e < 3 * a.n_elec; e += NT) a.drift[w * a.n_elec * 3 + e] = nan;
+    }
+}
+
+template <typename T>
+int launch_slater(const SlaterArgs& a, int nmax, cudaStream_t st)
+{
+    if (a.arith == 1) {
+        const int ns = ((nmax + 1) & ~1) + 2;
+        const size_t smem = 2 * (size_t)nmax * ns * sizeof(float);
+        cudaError_t e = cudaFuncSetAttribute(slater_df_kernel<T, kSlaterDfThreads>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(slater_df_kernel)");
+        slater_df_kernel<T, kSlaterDfThreads><<<(unsigned)a.n_walkers, kSlaterDfThreads, smem, st>>>(a);
+        return cuda_error(cudaGetLastError(), "slater_df_kernel launch");
+    }
+    const size_t smem = (size_t)nmax * (nmax + 1) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(slater_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(slater_kernel)");
+    slater_kernel<T><<<(unsigned)a.n_walkers, kSlaterThreads, smem, st>>>(a);
+    return cuda_error(cudaGetLastError(), "slater_kernel launch");
+}
+
 }  // namespace
 }  // namespace qmcspl
 
 using namespace qmcspl;
 
-extern "C" int qmcspl_slater_kinetic(const void* val, const void* grad, const void* lap, int dtype,
+extern "C" int qmcspl_slater_kinetic(const void* val, const void* grad, const void* lap, int dtype, int arith,
                                      long long n_walkers, int n_elec, int n_up, int n_orb, double* logdet,
                                      double* sign, double* kinetic, double* drift, void* stream)
 {
     if (dtype != 0 && dtype != 1) return set_error(QMCSPL_ERR_ARG, "dtype must be 0 (double) or 1 (float)");
+    if (arith != QMCSPL_SLATER_FP64 && arith != QMCSPL_SLATER_DF64)
+        return set_error(QMCSPL_ERR_ARG, "arith must be QMCSPL_SLATER_FP64 or QMCSPL_SLATER_DF64");
     if (n_walkers < 0) return set_error(QMCSPL_ERR_ARG, "n_walkers < 0");
     if (n_elec < 1 || n_up < 0 || n_up > n_elec) return set_error(QMCSPL_ERR_ARG, "need n_elec >= 1, 0 <= n_up <= n_elec");
     const int n_dn = n_elec - n_up;
@@ -241,17 +527,7 @@ extern "C" int qmcspl_slater_kinetic(const void* val, const void* grad, const vo
     a.sign = sign;
     a.kinetic = kinetic;
     a.drift = drift;
-    const size_t smem = (size_t)nmax * (nmax + 1) * sizeof(double);
+    a.arith = arith;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e;
-    if (dtype == 0) {
-        e = cudaFuncSetAttribute(slater_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(slater_kernel)");
-        slater_kernel<double><<<(unsigned)n_walkers, kSlaterThreads, smem, st>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(slater_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(slater_kernel)");
-        slater_kernel<float><<<(unsigned)n_walkers, kSlaterThreads, smem, st>>>(a);
-    }
-    return cuda_error(cudaGetLastError(), "slater_kernel launch");
+    return dtype == 0 ? launch_slater<double>(a, nmax, st) : launch_slater<float>(a, nmax, st);
 }

@@ -11,9 +11,9 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
-def consumer(v, g, l, W, n_elec, n_up):
+def consumer(v, g, l, W, n_elec, n_up, arith="df64"):
     from paper_1309_6250_gb300.api import slater_kinetic
-    out = slater_kinetic(v, g, l, W, n_elec, n_up)
+    out = slater_kinetic(v, g, l, W, n_elec, n_up, arith=arith)
     torch.cuda.synchronize()
     return tuple(None if x is None else x.cpu().numpy() for x in out)
 
@@ -27,9 +27,10 @@ def compare(got, ref, rel=1e-9):
     assert oracle.relative_error(dr, rdr) < rel * 10
 
 
+@pytest.mark.parametrize("arith", ["f64", "df64"])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("n_elec,n_up,n_orb", [(13, 7, 9), (8, 0, 8), (2, 1, 3), (40, 20, 24)])
-def test_consumer_matches_oracle(storage, n_elec, n_up, n_orb):
+def test_consumer_matches_oracle(storage, n_elec, n_up, n_orb, arith):
     dims = (12, 12, 12)
     lat, mil, coef = inputs.random_cell(1300 + n_elec, dims, n_orb, 8.0, 6.0, NONORTHO)
     spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=True)
@@ -37,14 +38,15 @@ def test_consumer_matches_oracle(storage, n_elec, n_up, n_orb):
     pos = inputs.positions(lat, W * n_elec, 1301 + n_elec)
     v, g, l = spl.eval_vgl(torch.from_numpy(pos).to(dev()))
     spl.sync()
-    got = consumer(v, g, l, W, n_elec, n_up)
+    got = consumer(v, g, l, W, n_elec, n_up, arith)
     ref = oracle.slater_kinetic(v.double().cpu().numpy(), g.double().cpu().numpy(), l.double().cpu().numpy(),
                                 W, n_elec, n_up)
     compare(got, ref)
     spl.close()
 
 
-def test_consumer_largest_block_and_singular_walker():
+@pytest.mark.parametrize("arith", ["f64", "df64"])
+def test_consumer_largest_block_and_singular_walker(arith):
     """Blocks of QMCSPL_SLATER_MAX_BLOCK electrons; a walker whose up block has a zero row
     is exactly singular: sign 0, logdet -inf, NaN kinetic energy and drift, the other
     walkers unaffected."""
@@ -57,7 +59,7 @@ def test_consumer_largest_block_and_singular_walker():
     lap = rng.standard_normal((W * n_elec, n))
     val[1 * n_elec + 5] = 0.0                      # walker 1, up block: zero row
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev())
-    ld, sg, kin, dr = consumer(t(val), t(grad), t(lap), W, n_elec, n)
+    ld, sg, kin, dr = consumer(t(val), t(grad), t(lap), W, n_elec, n, arith)
     assert sg[1] == 0 and ld[1] == -np.inf and np.isnan(kin[1]) and np.all(np.isnan(dr[1]))
     keep = [0, 2]
     rows = np.concatenate([np.arange(w * n_elec, (w + 1) * n_elec) for w in keep])
@@ -80,7 +82,8 @@ def test_consumer_rejects_bad_arguments():
 
 
 @pytest.mark.slow
-def test_consumer_c3_mgo64_full_batch():
+@pytest.mark.parametrize("arith", ["f64", "df64"])
+def test_consumer_c3_mgo64_full_batch(arith):
     """The MgO-like 64-atom workload as a QMC walker batch: 2048 walkers x 256 electrons,
     128 up and 128 down, each block using all 128 orbitals of the FP32 smoothing spline
     with the Laplacian table; every walker against the oracle."""
@@ -89,7 +92,7 @@ def test_consumer_c3_mgo64_full_batch():
     v, g, l = spl.eval_vgl(torch.from_numpy(w.pos).to(dev()))
     spl.sync()
     W, n_elec = w.cell.n_walkers, w.cell.n_elec
-    got = consumer(v, g, l, W, n_elec, n_elec // 2)
+    got = consumer(v, g, l, W, n_elec, n_elec // 2, arith)
     sample = np.arange(0, W, 7)
     rows = np.concatenate([np.arange(s * n_elec, (s + 1) * n_elec) for s in sample])
     vr = v.cpu().numpy()[rows].astype(np.float64)
