@@ -85,11 +85,23 @@ def _load():
             lib.orc_pp_eval.argtypes = [dp, ip, I, dp, L, dp, dp, dp, dp]
             lib.orc_pw_eval.argtypes = [I, ip, I, dp, dp, L, dp, dp, dp, dp, dp]
             lib.orc_bspline_adjoint.argtypes = [dp, dp, ip, I, dp, L, dp, dp, dp, dp, dp, dp, dp]
+            lib.orc_set_threads.argtypes = [I]
+            lib.orc_set_threads.restype = None
+            lib.orc_get_threads.argtypes = []
+            lib.orc_get_threads.restype = I
             for name in ("orc_bspline_basis", "orc_lagrange_basis", "orc_pp_basis"):
                 getattr(lib, name).argtypes = [ctypes.c_double, I, dp]
                 getattr(lib, name).restype = None
             _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the C loops (timing only); returns the previous count."""
+    lib = _load()
+    prev = lib.orc_get_threads()
+    lib.orc_set_threads(int(n))
+    return prev
 
 
 def _d(a: Optional[np.ndarray]):
