@@ -158,8 +158,8 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
                   void* stream);
 
 /*
- * qmcspl_create_grid -- qmcspl_create for interpolating B-splines of another odd degree or
- * on a non-uniform grid.
+ * qmcspl_create_grid -- qmcspl_create for B-splines of another odd degree, or interpolating
+ * B-splines on a non-uniform grid.
  *
  * Paper: Sec. II, "Common features" (each method may use polynomials of any order n; the
  * paper uses cubics) and "Grid" (uniform or non-uniform grids); Appendix, the B-spline
@@ -176,9 +176,10 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
  *                   all three axes or none.  Non-uniform grids are cubic; the planewave band
  *                   must fit the grid (dims[a] >= 2 max|n_a| + 1, else QMCSPL_ERR_ARG) and
  *                   the cyclic tridiagonal system is solved along each axis in FP64.
- * Other arguments as qmcspl_create; opts->method must be QMCSPL_BSPLINE_INTERP, storage
- * F64, F32 or BF16, separate_grad 0 (else QMCSPL_ERR_UNSUPPORTED); Bloch orbitals are
- * accepted.  dims[a] >= degree + 1.  Evaluation (qmcspl_eval_vgl, _host, _noalloc) has the
+ * Other arguments as qmcspl_create; opts->method QMCSPL_BSPLINE_INTERP, or on uniform
+ * grids also QMCSPL_BSPLINE_SMOOTH (Eq. b-splinecoefficients with gamma the Fourier
+ * transform of the degree-n basis, C_n sinc^{n+1}(th/2) per axis); storage F64, F32 or BF16;
+ * separate_grad 0 (else QMCSPL_ERR_UNSUPPORTED); Bloch orbitals are accepted.  dims[a] >= degree + 1.  Evaluation (qmcspl_eval_vgl, _host, _noalloc) has the
  * same outputs; the stencil is (n + 1)^3 points.  Backward and batched evaluation are not
  * available for these handles (QMCSPL_ERR_UNSUPPORTED).  grid = NULL is qmcspl_create.
  */

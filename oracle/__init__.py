@@ -708,6 +708,34 @@ def degree_constant(degree: int) -> float:
     return 1.0 / float(recurrence_basis(pts, degree, np.array([j0]), 0.0, 1.0)[0])
 
 
+def gamma_degree_axis(theta, degree: int) -> np.ndarray:
+    """Fourier transform of the centred degree-n basis (degree-0 constant C_n): the unit
+    B-spline is the (n+1)-fold convolution of the unit box, so its transform is
+    sinc^{n+1}(th/2); times C_n, and C_n at th = 0.  For n = 3 this is the paper's gamma."""
+    theta = np.asarray(theta, dtype=np.float64)
+    C = 1.5 if degree == 3 else degree_constant(degree)
+    out = np.full(theta.shape, C)
+    nz = theta != 0.0
+    h = 0.5 * theta[nz]
+    out[nz] = C * (np.sin(h) / h) ** (degree + 1)
+    return out
+
+
+def smoothing_tables_degree(lattice, miller, coef, dims, degree: int, laplacian: bool = False):
+    """Eq. (b-splinecoefficients) for the degree-n basis: beta = sum_G c_G / gamma_G exp(iG.x)
+    with gamma_G the product over axes of gamma_degree_axis(2 pi n_m / N_m)."""
+    th = 2.0 * np.pi * miller.astype(np.float64) / np.asarray(dims, dtype=np.float64)
+    g = gamma_degree_axis(th[:, 0], degree) * gamma_degree_axis(th[:, 1], degree) * \
+        gamma_degree_axis(th[:, 2], degree)
+    w = np.asarray(coef) / g[None, :]
+    beta, _ = grid_sum(fold(miller, w, dims))
+    lap = None
+    if laplacian:
+        G = g_vectors(lattice, miller)
+        lap, _ = grid_sum(fold(miller, w * (-np.einsum("ij,ij->i", G, G))[None, :], dims))
+    return beta, lap
+
+
 def axis_points(n: int, knots=None) -> np.ndarray:
     """Grid points of one periodic axis in reduced coordinates: l/N, or the given knots."""
     return np.arange(n) / n if knots is None else np.asarray(knots, dtype=np.float64)

@@ -331,10 +331,12 @@ int qmcspl_create_grid(qmcspl_t* out, const double lattice[9], const int dims[3]
             return set_error(QMCSPL_ERR_ARG, "degree must be 1, 3, 5 or 7");
         for (int a = 0; a < 3; ++a) nonuni = nonuni || grid->knots[a] != nullptr;
         if (nonuni && degree != 3) return set_error(QMCSPL_ERR_UNSUPPORTED, "non-uniform grids are cubic");
-        if ((degree != 3 || nonuni) &&
-            (opts->method != QMCSPL_BSPLINE_INTERP || opts->storage == QMCSPL_DF64 || opts->separate_grad))
+        // other degrees: interpolating or smoothing B-splines; non-uniform grids: interpolating
+        const bool ok_method = nonuni ? opts->method == QMCSPL_BSPLINE_INTERP
+                                      : (opts->method == QMCSPL_BSPLINE_INTERP || opts->method == QMCSPL_BSPLINE_SMOOTH);
+        if ((degree != 3 || nonuni) && (!ok_method || opts->storage == QMCSPL_DF64 || opts->separate_grad))
             return set_error(QMCSPL_ERR_UNSUPPORTED,
-                             "other degrees and non-uniform grids are for interpolating B-splines "
+                             "other degrees are for B-splines, non-uniform grids for interpolating ones "
                              "(f64, f32 or bf16 tables, no separate gradient tables)");
         for (int a = 0; a < 3; ++a) {
             if (dims[a] < degree + 1) return set_error(QMCSPL_ERR_ARG, "grid too small for the degree");

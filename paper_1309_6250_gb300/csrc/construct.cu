@@ -14,8 +14,10 @@
 //                                6 (cos th - 1) / (2 + cos th) Eq. (pp-splinecoefficients3)
 //   deriv   value 1; d_a phi i G_a; lap phi -|G|^2 (the separate gradient and Laplacian
 //           approximations of Sec. III C: B-splines optionally, Lagrange always)
-//   odd degree n (uniform grid): 1 / prod_m S_n(th_m), S_n(th) = sum_j C_n B_n(j) e^{i j th},
-//           the symbol of the periodic interpolation system of the degree-n basis
+//   odd degree n (uniform grid): interpolating 1 / prod_m S_n(th_m), S_n(th) = sum_j C_n B_n(j)
+//           e^{i j th}, the symbol of the periodic interpolation system of the degree-n basis;
+//           smoothing 1 / prod_m C_n sinc^{n+1}(th_m / 2), the Fourier transform of the
+//           degree-n basis (the paper's gamma_G for n = 3)
 //
 // Non-uniform grids (Sec. II "Grid": interpolating splines need no even spacing): the
 // planewave sum is evaluated at the per-axis grid points by the same separable passes with
@@ -60,6 +62,8 @@ struct ScatterArgs {
     double bmat[9];           // G_a = sum_i bmat[3a+i] n_i
     double kc[3];             // Cartesian k added to G in the derivative multipliers (0: Gamma)
     double sym[4];            // kBasisInterpN: C_n B_n(j), j = 0..3
+    int degree;               // kBasisSmoothN: the odd degree n
+    double cdeg;              // kBasisSmoothN: C_n
     int basis, deriv;         // BuildBasis, BuildDeriv
     int pp_axes;              // bit 2: x, bit 1: y, bit 0: z carry label 2
     double2* F;               // [N1][N2][N3][oc]
@@ -123,6 +127,22 @@ __global__ void scatter_kernel(const ScatterArgs a)
             double sv = a.sym[0];
             for (int j = 1; j < 4; ++j) sv += 2.0 * a.sym[j] * cospi(2.0 * (double)(j * kk[ax]) / (double)a.dims[ax]);
             b /= sv;
+        }
+        break;
+    }
+    case kBasisSmoothN: {
+        // gamma per axis: C_n (sin(th/2) / (th/2))^{n+1}, C_n at th = 0
+        const int nn[3] = {n0, n1, n2};
+        for (int ax = 0; ax < 3; ++ax) {
+            double g = a.cdeg;
+            if (nn[ax] != 0) {
+                const double h = 3.141592653589793238462643383279502884 * (double)nn[ax] / (double)a.dims[ax];
+                const double sc = sinpi((double)nn[ax] / (double)a.dims[ax]) / h;
+                double pw = 1.0;
+                for (int e = 0; e <= a.degree; ++e) pw *= sc;
+                g *= pw;
+            }
+            b /= g;
         }
         break;
     }
@@ -547,7 +567,7 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
                 : h->method == QMCSPL_LAGRANGE       ? kBasisGrid
                                                      : kBasisPP;
     if (h->nonuniform) basis = kBasisGrid;                 // grid values, then the axis solves
-    else if (h->degree != 3) basis = kBasisInterpN;
+    else if (h->degree != 3) basis = h->method == QMCSPL_BSPLINE_SMOOTH ? kBasisSmoothN : kBasisInterpN;
     double sym[4] = {0.0, 0.0, 0.0, 0.0};
     if (basis == kBasisInterpN) degree_symbol(h->degree, sym);
     AxisSystem sys[3];
@@ -623,6 +643,8 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
                 std::memcpy(s.bmat, bmat, sizeof(bmat));
                 for (int a = 0; a < 3; ++a) s.kc[a] = h->kcart[a];
                 for (int j = 0; j < 4; ++j) s.sym[j] = sym[j];
+                s.degree = h->degree;
+                s.cdeg = degree_constant(h->degree);
                 s.basis = job.basis;
                 s.deriv = job.deriv;
                 s.pp_axes = job.pp_axes;

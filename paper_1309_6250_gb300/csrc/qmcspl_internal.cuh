@@ -40,6 +40,7 @@ enum BuildBasis : int {
     kBasisPP = 3,            // prod over label-2 axes of 6(cos th - 1)/(2 + cos th)
     kBasisInterpN = 4,       // 1 / prod S_n(th), S_n = sum_m C_n B_n(m) e^{i m th}: interpolating
                              // B-spline of odd degree n on a uniform grid
+    kBasisSmoothN = 5,       // 1 / prod C_n sinc^{n+1}(th/2): smoothing B-spline of odd degree n
 };
 enum BuildDeriv : int {
     kDerivValue = 0,         // 1          (phi)

@@ -114,7 +114,8 @@ def test_grid_options_validated_without_gpu(lib):
 
     u = np.arange(8) / 8.0
     assert create(4, (None,) * 3) == _lib.ERR_ARG                       # even degree
-    assert create(5, (None,) * 3, method=0) == _lib.ERR_UNSUPPORTED     # smoothing, degree 5
+    assert create(5, (None,) * 3, method=2) == _lib.ERR_UNSUPPORTED     # Lagrange, degree 5
+    assert create(3, (u, u, u), method=0) == _lib.ERR_UNSUPPORTED       # smoothing, non-uniform
     assert create(5, (None,) * 3, storage=3) == _lib.ERR_UNSUPPORTED    # double-float
     assert create(5, (u, u, u)) == _lib.ERR_UNSUPPORTED                 # non-uniform quintic
     assert create(3, (u, None, u)) == _lib.ERR_ARG                      # one axis missing

@@ -176,3 +176,79 @@ def test_graded_cubic_is_C2_across_knots_and_chain_rule():
         fd_l += (gp[:, a] - gm[:, a]) / (2 * h)
     assert oracle.relative_error(g, fd_g) < 1e-7
     assert oracle.relative_error(l, fd_l) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# smoothing B-splines of other odd degrees (Eq. b-splinecoefficients with the degree-n basis)
+# ---------------------------------------------------------------------------
+
+def fourier_of_recurrence_basis(theta, degree, nodes=32):
+    """Integral over R of the recurrence's centred degree-n basis (with C_n) times
+    cos(theta xi), by Gauss-Legendre on every unit piece of its support."""
+    C = 1.5 if degree == 3 else oracle.degree_constant(degree)
+    nb = 64
+    pts = np.arange(nb) / nb
+    x, w = np.polynomial.legendre.leggauss(nodes)
+    half = (degree + 1) // 2
+    total = 0.0
+    for lo in range(-half, half):
+        xi = lo + 0.5 * (x + 1)
+        vals = np.array([oracle.recurrence_basis(pts, degree, np.array([-half]), v / nb, C)[0] for v in xi])
+        total += 0.5 * np.sum(w * vals * np.cos(theta * xi))
+    return total
+
+
+@pytest.mark.parametrize("degree", [1, 3, 5, 7])
+def test_degree_gamma_is_the_fourier_transform_of_the_basis(degree):
+    """gamma for the degree-n basis is the Fourier transform of the recurrence's centred basis
+    (the paper defines gamma this way for the cubic); degree 3 is the paper's gamma."""
+    for th in (0.0, 0.3, 1.0, 2.0, np.pi, 4.5):
+        assert oracle.gamma_degree_axis(np.array([th]), degree)[0] == pytest.approx(
+            fourier_of_recurrence_basis(th, degree), rel=1e-10, abs=1e-13)
+    th = np.linspace(0, 6, 25)
+    if degree == 3:
+        np.testing.assert_allclose(oracle.gamma_degree_axis(th, 3), oracle.gamma_axis(th), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("degree", [1, 5])
+def test_degree_smoothing_fourier_components_are_exact(degree):
+    """The smoothing spline of degree n reproduces every planewave coefficient c_G when no G
+    aliases: its Fourier component (grid sum of beta times the basis transform) is c_G."""
+    lat, mil, coef = inputs.random_cell(60 + degree, (9, 10, 11), 2, 4.0, 4.0, NONORTHO)
+    dims = np.array((9, 10, 11))
+    assert np.all(np.abs(mil).max(0) < dims / 2)
+    beta, _ = oracle.smoothing_tables_degree(lat, mil, coef, tuple(dims), degree)
+    bhat = np.fft.fftn(np.moveaxis(beta, -1, 0), axes=(1, 2, 3))
+    cache = {}
+    for idx, n in enumerate(mil[::7]):
+        th = 2 * np.pi * n / dims
+        Q = 1.0
+        for a in range(3):
+            key = round(float(th[a]), 14)
+            if key not in cache:
+                cache[key] = fourier_of_recurrence_basis(th[a], degree)
+            Q *= cache[key]
+        k = np.mod(n, dims)
+        comp = bhat[:, k[0], k[1], k[2]] * Q / dims.prod()
+        j = np.nonzero(np.all(mil == n, axis=1))[0][0]
+        np.testing.assert_allclose(comp, coef[:, j], atol=1e-11 * np.abs(coef).max())
+
+
+def test_degree_smoothing_cubic_is_the_paper_path_and_higher_degree_converges_faster():
+    dims = (8, 9, 10)
+    lat, mil, coef = inputs.random_cell(70, dims, 2, 5.0, 4.0, NONORTHO)
+    b3, l3 = oracle.smoothing_tables_degree(lat, mil, coef, dims, 3, laplacian=True)
+    rb, rl = oracle.smoothing_tables(lat, mil, coef, dims, laplacian=True)
+    assert oracle.relative_error(b3, rb) < 1e-13 and oracle.relative_error(l3, rl) < 1e-13
+    lat = np.eye(3) * 5.0
+    mil = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 1], [0, -1, -1], [1, -1, 0], [-1, 1, 0]], dtype=np.int32)
+    coef = np.array([[0.4 + 0.2j, 0.4 - 0.2j, 0.3, 0.3, -0.25j, 0.25j]])
+    pos = inputs.positions(lat, 40, 71)
+    pv, _, _, _ = oracle.pw_eval(lat, mil, coef, pos)
+    for degree, grids, ratio in ((1, (24, 48), 3.0), (5, (12, 24), 40.0)):   # degree 1: past its pre-asymptotic range
+        errs = []
+        for n in grids:
+            beta, _ = oracle.smoothing_tables_degree(lat, mil, coef, (n, n, n), degree)
+            v, _, _ = oracle.general_eval(beta, lat, pos, degree)
+            errs.append(np.abs(v - pv).max())
+        assert errs[0] / errs[1] > ratio

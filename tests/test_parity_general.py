@@ -135,3 +135,23 @@ def test_general_with_position_records_matches_oracle(degree, nonuni, storage):
     ref = oracle.general_eval(spl.get_table(0), lat, pos[sample], degree, kk)
     assert_parity((v[sample], g[sample], l[sample]), ref, TOL[storage], "records deg %d %s" % (degree, storage))
     spl.close()
+
+
+@pytest.mark.parametrize("degree", [1, 5, 7])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_smoothing_of_other_degrees_matches_oracle(degree, storage):
+    """Smoothing B-splines of degree n (Eq. b-splinecoefficients with the degree-n gamma):
+    tables and outputs against the oracle, with and without the Laplacian table."""
+    dims = (11, 12, 13)
+    lat, mil, coef = inputs.random_cell(1450 + degree, dims, 5, 5.0, 4.0, NONORTHO)
+    rb, rl = oracle.smoothing_tables_degree(lat, mil, coef, dims, degree, laplacian=True)
+    for sep in (False, True):
+        spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=sep, degree=degree)
+        assert oracle.relative_error(spl.get_table(0), rb) < TTOL[storage]
+        if sep:
+            assert oracle.relative_error(spl.get_table(1), rl) < TTOL[storage]
+        pos = inputs.positions(lat, 50, 1451, -1, 2)
+        got = gpu_eval(spl, pos)
+        ref = oracle.general_eval(spl.get_table(0), lat, pos, degree, beta_lap=spl.get_table(1) if sep else None)
+        assert_parity(got, ref, TOL[storage], "smoothing degree %d %s sep=%d" % (degree, storage, sep))
+        spl.close()
