@@ -24,6 +24,8 @@
  *     asynchronous on that stream unless a call says otherwise.  Errors a kernel
  *     detects on the device (a non-finite position) are recorded in the handle and
  *     reported by qmcspl_sync().
+ *   - Threads: calls on different handles may run concurrently; calls on one handle must
+ *     not (a handle owns scratch memory that its evaluations reuse).
  *   - Lattice: row-major 3x3 with the lattice vectors a_1, a_2, a_3 as COLUMNS (bohr),
  *     so r = a s for crystal coordinates s.  Positions may lie anywhere; they are
  *     wrapped into the cell (Eq. reducedcoordinate).

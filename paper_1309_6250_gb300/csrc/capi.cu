@@ -521,20 +521,38 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
     const long long cap = 1LL << 16;                   // positions per chunk
     cudaError_t e;
     if (!h->st_ready) {
+        // all or nothing: on a failure everything created so far is released again
+        cudaStream_t ss[2] = {nullptr, nullptr};
+        cudaEvent_t ee[6] = {};
+        double* sp[2] = {nullptr, nullptr};
+        void* so[2] = {nullptr, nullptr};
+        int n_ev = 0;
+        e = cudaSuccess;
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaStreamCreateWithFlags(&ss[b], cudaStreamNonBlocking);
+        for (; n_ev < 6 && e == cudaSuccess; ++n_ev) {
+            e = cudaEventCreateWithFlags(&ee[n_ev], cudaEventDisableTiming);
+            if (e != cudaSuccess) break;
+        }
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            e = cudaMalloc((void**)&sp[b], sizeof(double) * 3 * cap);
+            if (e == cudaSuccess) e = cudaMalloc(&so[b], row * 5 * cap);
+        }
+        if (e != cudaSuccess) {
+            const int rc = cuda_error(e, "host staging set-up");
+            for (int b = 0; b < 2; ++b) {
+                if (ss[b]) cudaStreamDestroy(ss[b]);
+                if (sp[b]) cudaFree(sp[b]);
+                if (so[b]) cudaFree(so[b]);
+            }
+            for (int i = 0; i < n_ev; ++i) cudaEventDestroy(ee[i]);
+            return rc;
+        }
         for (int b = 0; b < 2; ++b) {
-            e = cudaStreamCreateWithFlags(&h->st_stream[b], cudaStreamNonBlocking);
-            if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreate");
+            h->st_stream[b] = ss[b];
+            h->st_pos[b] = sp[b];
+            h->st_out[b] = so[b];
         }
-        for (int i = 0; i < 6; ++i) {
-            e = cudaEventCreateWithFlags(&h->st_ev[i], cudaEventDisableTiming);
-            if (e != cudaSuccess) return cuda_error(e, "cudaEventCreate");
-        }
-        for (int b = 0; b < 2; ++b) {
-            e = cudaMalloc((void**)&h->st_pos[b], sizeof(double) * 3 * cap);
-            if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(staging)");
-            e = cudaMalloc(&h->st_out[b], row * 5 * cap);
-            if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(staging)");
-        }
+        for (int i = 0; i < 6; ++i) h->st_ev[i] = ee[i];
         h->st_cap = cap;
         h->st_ready = true;
     }
