@@ -384,6 +384,17 @@ int qmcspl_slater_kinetic(const void* val, const void* grad, const void* lap, in
                           double* kinetic, double* drift, void* stream);
 
 /*
+ * qmcspl_debug_fail_alloc -- test hook: make one device allocation of the library fail.
+ *
+ * Not in the paper.  After n further successful device allocations (any call, any thread)
+ * the next one reports cudaErrorMemoryAllocation, as if the device were full; the hook then
+ * switches itself off.  n < 0 switches it off.  Every entry point must then return
+ * QMCSPL_ERR_OOM (or QMCSPL_ERR_CUDA) and release what it had allocated, leaving the handle
+ * (if any) usable.  Returns QMCSPL_OK.
+ */
+int qmcspl_debug_fail_alloc(long long n);
+
+/*
  * qmcspl_profile / qmcspl_profile_read -- CUDA-event timing of the library's own kernels.
  *
  * Not in the paper.  While enabled, every qmcspl_eval_vgl on the handle records CUDA

@@ -97,15 +97,19 @@ PROTOTYPES = [
     ("qmcspl_save", I, [VP, ctypes.c_char_p]),
     ("qmcspl_load", I, [ctypes.POINTER(VP), ctypes.c_char_p, VP]),
     ("qmcspl_slater_kinetic", I, [VP, VP, VP, I, I, LL, I, I, I, VP, VP, VP, VP, VP]),
+    ("qmcspl_debug_fail_alloc", I, [LL]),
     ("qmcspl_sync", I, [VP, VP]),
     ("qmcspl_last_error", ctypes.c_char_p, []),
     ("qmcspl_version", I, []),
 ]
 
 
-def load(path: str = LIB_PATH):
-    """Load the library (once) and attach the prototypes.  Raises if it is missing."""
+def load(path: str = None):
+    """Load the library (once) and attach the prototypes.  Raises if it is missing.
+    QMCSPL_LIBRARY in the environment names another build of it (e.g. the bounds-checked
+    libqmcspl_debug.so) to load instead."""
     global _lib
+    path = path or os.environ.get("QMCSPL_LIBRARY") or LIB_PATH
     with _lock:
         if _lib is None:
             if not os.path.exists(path):

@@ -2,6 +2,9 @@
 
 Each translation unit under csrc/ is compiled in parallel, then linked into one
 shared library next to this file.  No PyTorch headers or libraries are involved.
+build(debug_bounds=True) makes libqmcspl_debug.so instead: the same library compiled with
+QMCSPL_DEBUG_BOUNDS, where every table load and position index of the kernels is range
+checked (a bad one is flagged in the error word and skipped, never trapped).
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqmcspl.so")
+DEBUG_LIB = os.path.join(HERE, "libqmcspl_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(os.path.dirname(HERE), "include")]
@@ -38,9 +42,10 @@ def _newest_input() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
-def _compile(src: str, verbose_ptxas: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+def _compile(src: str, verbose_ptxas: bool, debug_bounds: bool = False) -> str:
+    bdir = BUILD + ("_debug" if debug_bounds else "")
+    obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *(["-DQMCSPL_DEBUG_BOUNDS"] if debug_bounds else []), "-c", src, "-o", obj]
     if verbose_ptxas:
         cmd[1:1] = ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -51,23 +56,26 @@ def _compile(src: str, verbose_ptxas: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libqmcspl.so; returns its path."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, debug_bounds: bool = False) -> str:
+    """Compile every csrc/*.cu for sm_103a and link libqmcspl.so (libqmcspl_debug.so with
+    debug_bounds); returns its path."""
+    lib = DEBUG_LIB if debug_bounds else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(BUILD + ("_debug" if debug_bounds else ""), exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas, debug_bounds), srcs))
+    tmp = lib + ".%d.tmp" % os.getpid()
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared",
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv,
+                debug_bounds="--debug-bounds" in sys.argv))

@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
 #pragma unroll
                     for (int n = 0; n < 4; ++n) {
                         A c[E];
-                        unpack<T>(ldg16(t0 + col + n * rowb), c);
+                        unpack<T>(ldg_table(p, t0 + col + n * rowb), c);
 #pragma unroll
                         for (int e = 0; e < E; ++e) {
                             a[0][e] = fma(w[2][n], c[e], a[0][e]);
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
                             a[3][e] = fma(d3w[n], c[e], a[3][e]);
                         }
                         if (LAPTAB) {
-                            unpack<T>(ldg16(t1 + col + n * rowb), c);
+                            unpack<T>(ldg_table(p, t1 + col + n * rowb), c);
 #pragma unroll
                             for (int e = 0; e < E; ++e) {
                                 al[0][e] = fma(w[2][n], c[e], al[0][e]);

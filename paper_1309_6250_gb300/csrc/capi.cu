@@ -4,6 +4,7 @@
 // coefficients (real Gamma-point orbitals, Sec. III), the chain-rule matrices of
 // Sec. II (Coordinates), the Cartesian k of Bloch orbitals, table sizing, and dispatch
 // to the kernels.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -30,6 +31,38 @@ int cuda_error(cudaError_t e, const char* what)
     cudaGetLastError();   // clear a sticky launch error so later calls can proceed
     g_err = std::string(what) + ": " + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? QMCSPL_ERR_OOM : QMCSPL_ERR_CUDA;
+}
+
+// Allocation failure injection (tests): -1 = off; n >= 0 = the allocation after n more
+// successful ones fails once, then injection switches itself off.
+static std::atomic<long long> g_fail_countdown{-1};
+
+static bool inject_failure()
+{
+    long long v = g_fail_countdown.load();
+    while (v >= 0) {
+        const long long next = v == 0 ? -1 : v - 1;
+        if (g_fail_countdown.compare_exchange_weak(v, next)) return v == 0;
+    }
+    return false;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes)
+{
+    if (inject_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t st)
+{
+    if (inject_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
 }
 
 int sm_count()
@@ -71,6 +104,8 @@ void fill_eval_args(const Handle* h, EvalArgs* a)
         a->mll[i] = (float)(h->ml[i] - (double)a->mlh[i]);
     }
     a->err = h->d_err;
+    a->tab_lo = static_cast<const char*>(h->tables);
+    a->tab_hi = a->tab_lo + h->table_elems * h->elem_bytes * h->n_tables;
     for (int i = 0; i < 3; ++i) {
         a->kc[i] = h->kcart[i];
         a->kcf[i] = (float)h->kcart[i];
@@ -96,7 +131,7 @@ int upload_grid_points(Handle* h, cudaStream_t st)
         }
     }
     cudaError_t e = cudaSuccess;
-    if (!h->d_knots) e = cudaMalloc((void**)&h->d_knots, sizeof(double) * buf.size());
+    if (!h->d_knots) e = dev_malloc((void**)&h->d_knots, sizeof(double) * buf.size());
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->d_knots, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -277,6 +312,12 @@ extern "C" {
 
 int qmcspl_version(void) { return 10000 * 1 + 100 * 0 + 0; }
 
+int qmcspl_debug_fail_alloc(long long n)
+{
+    g_fail_countdown.store(n < 0 ? -1 : n);
+    return QMCSPL_OK;
+}
+
 const char* qmcspl_last_error(void) { return g_err.c_str(); }
 
 int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int n_pw,
@@ -405,13 +446,13 @@ int qmcspl_create_grid(qmcspl_t* out, const double lattice[9], const int dims[3]
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t bytes = h->table_elems * h->elem_bytes * h->n_tables;
-    cudaError_t e = cudaMalloc(&h->tables, bytes);
+    cudaError_t e = dev_malloc(&h->tables, bytes);
     if (e != cudaSuccess) {
         rc = cuda_error(e, "cudaMalloc(tables)");
         free_handle(h);
         return rc;
     }
-    e = cudaMalloc((void**)&h->d_err, sizeof(int));
+    e = dev_malloc((void**)&h->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->tables, 0, bytes, st);
     if (e != cudaSuccess) {
@@ -534,8 +575,8 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
             if (e != cudaSuccess) break;
         }
         for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
-            e = cudaMalloc((void**)&sp[b], sizeof(double) * 3 * cap);
-            if (e == cudaSuccess) e = cudaMalloc(&so[b], row * 5 * cap);
+            e = dev_malloc((void**)&sp[b], sizeof(double) * 3 * cap);
+            if (e == cudaSuccess) e = dev_malloc(&so[b], row * 5 * cap);
         }
         if (e != cudaSuccess) {
             const int rc = cuda_error(e, "host staging set-up");
@@ -786,6 +827,9 @@ int qmcspl_sync(qmcspl_t h, void* stream)
     if (e != cudaSuccess) return cuda_error(e, "error word read");
     if (flag) {
         cudaMemset(h->d_err, 0, sizeof(int));
+        if (flag & 2)
+            return set_error(QMCSPL_ERR_DEVICE, "a kernel caught an out-of-range table or position index "
+                                                "(bounds-checked build)");
         return set_error(QMCSPL_ERR_DEVICE, "a kernel saw a non-finite position");
     }
     return QMCSPL_OK;

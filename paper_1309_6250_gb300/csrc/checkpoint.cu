@@ -231,8 +231,8 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
         return set_error(QMCSPL_ERR_ARG, "singular lattice in table file");
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMalloc(&h->tables, bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_err, sizeof(int));
+    cudaError_t e = dev_malloc(&h->tables, bytes);
+    if (e == cudaSuccess) e = dev_malloc((void**)&h->d_err, sizeof(int));
     if (e == cudaSuccess && h->nonuniform && upload_grid_points(h, st) != QMCSPL_OK) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->tables, buf.data(), bytes, cudaMemcpyHostToDevice, st);

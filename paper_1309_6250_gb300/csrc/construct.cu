@@ -598,7 +598,7 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
     do {
         if (h->nonuniform) {
             const size_t nd = 4 * (size_t)(N1 + N2 + N3);
-            e = cudaMallocAsync((void**)&d_sys, sizeof(double) * nd, st);
+            e = dev_malloc_async((void**)&d_sys, sizeof(double) * nd, st);
             if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(axis systems)"); break; }
             size_t off = 0;
             for (int a = 0; a < 3; ++a) {
@@ -609,13 +609,13 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
             }
             if (e != cudaSuccess) { rc = cuda_error(e, "upload axis systems"); break; }
         }
-        e = cudaMallocAsync((void**)&d_miller, sizeof(int) * 3 * (size_t)n_pw, st);
+        e = dev_malloc_async((void**)&d_miller, sizeof(int) * 3 * (size_t)n_pw, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(miller)"); break; }
-        e = cudaMallocAsync((void**)&d_coef, sizeof(double2) * (size_t)n_pw * n_band, st);
+        e = dev_malloc_async((void**)&d_coef, sizeof(double2) * (size_t)n_pw * n_band, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(coef)"); break; }
-        e = cudaMallocAsync((void**)&F[0], per_orb * oc_max, st);
+        e = dev_malloc_async((void**)&F[0], per_orb * oc_max, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(grid)"); break; }
-        e = cudaMallocAsync((void**)&F[1], per_orb * oc_max, st);
+        e = dev_malloc_async((void**)&F[1], per_orb * oc_max, st);
         if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(grid)"); break; }
         e = cudaMemcpyAsync(d_miller, miller_host, sizeof(int) * 3 * (size_t)n_pw,
                             cudaMemcpyHostToDevice, st);

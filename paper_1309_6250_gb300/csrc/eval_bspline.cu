@@ -49,7 +49,7 @@ __device__ __forceinline__ void bspline_warp_task(const EvalArgs& p, long long w
     const bool active = gid < total;
     const long long q = active ? gid / p.tiles : 0;
     const int tile = active ? (int)(gid - q * p.tiles) : 0;
-    const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
+    const long long ip = active ? order_index(p, q) : q;
     int ix, iy, iz;
     double tx, ty, tz;
     bool ok;
@@ -90,10 +90,10 @@ __device__ __forceinline__ void bspline_warp_task(const EvalArgs& p, long long w
             const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb;
             uint4 raw[4], rawl[4];
 #pragma unroll
-            for (int n = 0; n < 4; ++n) raw[n] = ldg16(t0 + col + n * rowb);
+            for (int n = 0; n < 4; ++n) raw[n] = ldg_table(p, t0 + col + n * rowb);
             if (LAPTAB) {
 #pragma unroll
-                for (int n = 0; n < 4; ++n) rawl[n] = ldg16(t1 + col + n * rowb);
+                for (int n = 0; n < 4; ++n) rawl[n] = ldg_table(p, t1 + col + n * rowb);
             }
             A a0[E], a1[E], a2[E], al[E];
 #pragma unroll
@@ -179,7 +179,7 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
     const bool active = gid < total;
     const long long q = active ? gid / p.tiles : 0;
     const int tile = active ? (int)(gid - q * p.tiles) : 0;
-    const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
+    const long long ip = active ? order_index(p, q) : q;
     int ix, iy, iz;
     float tx, ty, tz;
     bool ok;
@@ -222,10 +222,10 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
     {
         const size_t col = (size_t)(xs[0] * p.ny + ys[0]) * colb;
 #pragma unroll
-        for (int n = 0; n < 4; ++n) cur[n] = ldg16(t0 + col + n * rowb);
+        for (int n = 0; n < 4; ++n) cur[n] = ldg_table(p, t0 + col + n * rowb);
         if (LAPTAB) {
 #pragma unroll
-            for (int n = 0; n < 4; ++n) cur[4 + n] = ldg16(t1 + col + n * rowb);
+            for (int n = 0; n < 4; ++n) cur[4 + n] = ldg_table(p, t1 + col + n * rowb);
         }
     }
 #pragma unroll
@@ -235,10 +235,10 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
             const int ln = (c + 1) >> 2, mn = (c + 1) & 3;
             const size_t col = (size_t)(xs[ln] * p.ny + ys[mn]) * colb;
 #pragma unroll
-            for (int n = 0; n < 4; ++n) nxt[n] = ldg16(t0 + col + n * rowb);
+            for (int n = 0; n < 4; ++n) nxt[n] = ldg_table(p, t0 + col + n * rowb);
             if (LAPTAB) {
 #pragma unroll
-                for (int n = 0; n < 4; ++n) nxt[4 + n] = ldg16(t1 + col + n * rowb);
+                for (int n = 0; n < 4; ++n) nxt[4 + n] = ldg_table(p, t1 + col + n * rowb);
             }
         }
         f32x2 A0[NP], A1[NP], A2[NP], AL[NP];
@@ -336,7 +336,7 @@ __device__ __forceinline__ void bspline_warp_task_df(const EvalArgs& p, long lon
     const bool active = gid < total;
     const long long q = active ? gid / p.tiles : 0;
     const int tile = active ? (int)(gid - q * p.tiles) : 0;
-    const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
+    const long long ip = active ? order_index(p, q) : q;
     int ix, iy, iz;
     dfloat tx, ty, tz;
     bool ok;
@@ -384,10 +384,10 @@ __device__ __forceinline__ void bspline_warp_task_df(const EvalArgs& p, long lon
         const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb;
         uint4 raw[4], rawl[4];
 #pragma unroll
-        for (int n = 0; n < 4; ++n) raw[n] = ldg16(t0 + col + n * rowb);
+        for (int n = 0; n < 4; ++n) raw[n] = ldg_table(p, t0 + col + n * rowb);
         if (LAPTAB) {
 #pragma unroll
-            for (int n = 0; n < 4; ++n) rawl[n] = ldg16(t1 + col + n * rowb);
+            for (int n = 0; n < 4; ++n) rawl[n] = ldg_table(p, t1 + col + n * rowb);
         }
         f32x2 A0h = 0, A0l = 0, A1h = 0, A1l = 0, A2h = 0, A2l = 0, ALh = 0, ALl = 0;
 #pragma unroll

@@ -19,6 +19,34 @@ __device__ __forceinline__ uint4 ldg16(const void* p)
     return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
+// A table load.  In a QMCSPL_DEBUG_BOUNDS build every address is checked against the
+// handle's table allocation (and 16-byte alignment); a bad one sets bit 1 of the error word
+// and reads zeros instead of memory (never a trap).  Other builds load directly.
+__device__ __forceinline__ uint4 ldg_table(const EvalArgs& p, const char* a)
+{
+#ifdef QMCSPL_DEBUG_BOUNDS
+    if (a < p.tab_lo || a + 16 > p.tab_hi || (reinterpret_cast<uintptr_t>(a) & 15)) {
+        atomicOr(p.err, 2);
+        return make_uint4(0u, 0u, 0u, 0u);
+    }
+#endif
+    return ldg16(a);
+}
+
+// The position evaluated q-th (through the evaluation order when there is one); range
+// checked in QMCSPL_DEBUG_BOUNDS builds (bit 1 of the error word, position 0 used instead).
+__device__ __forceinline__ long long order_index(const EvalArgs& p, long long q)
+{
+    long long ip = p.perm ? (long long)p.perm[q] : q;
+#ifdef QMCSPL_DEBUG_BOUNDS
+    if (ip < 0 || ip >= p.n_pos) {
+        atomicOr(p.err, 2);
+        ip = 0;
+    }
+#endif
+    return ip;
+}
+
 template <typename T>
 __device__ __forceinline__ void unpack(const uint4& r, typename Traits<T>::A* v);
 

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) general_vgl_kernel(const Eval
         if (gid >= total) continue;
         const long long q = gid / p.tiles;
         const int tile = (int)(gid - q * p.tiles);
-        const long long ip = p.perm ? (long long)p.perm[q] : q;
+        const long long ip = order_index(p, q);
         // cell and local coordinate per axis (t on uniform grids, the offset from the
         // interval's left grid point on graded ones): from the per-position record, or
         // reduced here in FP64; the weights are then built once, from these alone
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) general_vgl_kernel(const Eval
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
                     A c[E];
-                    unpack<T>(ldg16(c0 + k * rowb), c);
+                    unpack<T>(ldg_table(p, c0 + k * rowb), c);
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         a0[e] = fma(wz[k], c[e], a0[e]);
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kEvalThreads, 1) general_vgl_kernel(const Eval
                     }
                     if (LAPTAB) {
                         A cl[E];
-                        unpack<T>(ldg16(static_cast<const char*>(p.tab[1]) + col + k * rowb), cl);
+                        unpack<T>(ldg_table(p, static_cast<const char*>(p.tab[1]) + col + k * rowb), cl);
 #pragma unroll
                         for (int e = 0; e < E; ++e) al[e] = fma(wz[k], cl[e], al[e]);
                     }

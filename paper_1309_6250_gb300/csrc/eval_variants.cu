@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) five_table_vgl_kernel(const E
         const bool active = gid < total;
         const long long q = active ? gid / p.tiles : 0;
         const int tile = active ? (int)(gid - q * p.tiles) : 0;
-        const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
+        const long long ip = active ? order_index(p, q) : q;
         int ix, iy, iz;
         A tx, ty, tz;
         bool ok;
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) five_table_vgl_kernel(const E
                     const char* base = static_cast<const char*>(p.tab[k]) + col;
                     uint4 raw[4];
 #pragma unroll
-                    for (int n = 0; n < 4; ++n) raw[n] = ldg16(base + n * rowb);
+                    for (int n = 0; n < 4; ++n) raw[n] = ldg_table(p, base + n * rowb);
                     A a[E];
 #pragma unroll
                     for (int e = 0; e < E; ++e) a[e] = A(0);
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs 
         const bool active = gid < total;
         const long long q = active ? gid / p.tiles : 0;
         const int tile = active ? (int)(gid - q * p.tiles) : 0;
-        const long long ip = (active && p.perm) ? (long long)p.perm[q] : q;
+        const long long ip = active ? order_index(p, q) : q;
         int ix, iy, iz;
         A tx, ty, tz;
         bool ok;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs 
 #pragma unroll
                         for (int nu = 0; nu < 2; ++nu) {
                             A c[E];
-                            unpack<T>(ldg16(col + k * rowb + (size_t)(4 * kap + 2 * mu + nu) * entb), c);
+                            unpack<T>(ldg_table(p, col + k * rowb + (size_t)(4 * kap + 2 * mu + nu) * entb), c);
 #pragma unroll
                             for (int e = 0; e < E; ++e) {
                                 a0[e] = fma(wz[nu][k], c[e], a0[e]);

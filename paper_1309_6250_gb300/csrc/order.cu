@@ -280,11 +280,11 @@ static int grow_scratch(Handle* h, long long n_pos, int n_bins)
     h->ord_phase = nullptr;
     h->ord_cap = 0;
     h->ord_nbins = 0;
-    cudaError_t e = cudaMalloc((void**)&h->ord_bin, sizeof(int) * (size_t)cap);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->ord_perm, sizeof(int) * (size_t)cap);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&h->ord_count, sizeof(int) * (size_t)nb);
-    if (e == cudaSuccess) e = cudaMalloc(&h->ord_rec, 32 * (size_t)cap);
-    if (e == cudaSuccess && h->bloch) e = cudaMalloc((void**)&h->ord_phase, sizeof(double2) * (size_t)cap);
+    cudaError_t e = dev_malloc((void**)&h->ord_bin, sizeof(int) * (size_t)cap);
+    if (e == cudaSuccess) e = dev_malloc((void**)&h->ord_perm, sizeof(int) * (size_t)cap);
+    if (e == cudaSuccess) e = dev_malloc((void**)&h->ord_count, sizeof(int) * (size_t)nb);
+    if (e == cudaSuccess) e = dev_malloc(&h->ord_rec, 32 * (size_t)cap);
+    if (e == cudaSuccess && h->bloch) e = dev_malloc((void**)&h->ord_phase, sizeof(double2) * (size_t)cap);
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(position scratch)");
     h->ord_cap = cap;
     h->ord_nbins = nb;

@@ -83,6 +83,8 @@ struct EvalArgs {
     // general B-splines (degree other than 3, or non-uniform grids)
     const double* knots[3];   // per-axis grid points in [0, 1) (non-uniform grids), else null
     double cdeg;              // degree-0 constant C of the recurrence
+    const char* tab_lo;       // the handle's table allocation [tab_lo, tab_hi): every table
+    const char* tab_hi;       // load is checked against it in QMCSPL_DEBUG_BOUNDS builds
 };
 
 }  // namespace qmcspl
@@ -154,6 +156,11 @@ namespace qmcspl {
 // ---- error reporting (thread-local message) ----
 int set_error(int code, const std::string& msg);
 int cuda_error(cudaError_t e, const char* what);
+
+// ---- device allocations: every one goes through these, so that the test hook
+// qmcspl_debug_fail_alloc can make a chosen one fail ----
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t stream);
 
 // ---- construction (construct.cu) ----
 int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef_host,

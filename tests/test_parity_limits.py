@@ -81,3 +81,30 @@ def test_constant_orbital(method):
     v, g, l = gpu_eval(spl, pos)
     assert np.abs(v - 2.5).max() < 1e-13
     assert np.abs(g).max() < 1e-12 and np.abs(l).max() < 1e-11
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4), (5, 6, 7)])
+@pytest.mark.parametrize("method,storage,sep", [("smooth", "f64", True), ("smooth", "f32", False),
+                                                ("interp", "bf16", True), ("interp", "df64", False),
+                                                ("lagrange", "f32", True), ("pp", "f64", False)])
+def test_tiny_grids_every_method(dims, method, storage, sep):
+    """The smallest grids accepted (4 points per axis), where every stencil wraps and the
+    ghost planes repeat the same planes; positions inside and far outside the cell, with
+    and without records and cell order."""
+    lat, mil, coef = inputs.random_cell(1510, dims, 5, 2.0, 3.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method=method, storage=storage, separate_lap=sep)
+    n_tab = {"lagrange": 5, "pp": 8}.get(method, 2 if sep else 1)
+    tabs = [spl.get_table(i) for i in range(n_tab)]
+    pos = inputs.positions(lat, 60, 1511, -3, 4)
+    if method in ("smooth", "interp"):
+        ref = oracle.bspline_eval(tabs[0], lat, pos, beta_lap=tabs[1] if sep else None)
+    elif method == "lagrange":
+        ref = oracle.lagrange_eval(np.stack(tabs), lat, pos)
+    else:
+        ref = oracle.pp_eval(np.stack(tabs), lat, pos)
+    assert_parity(gpu_eval(spl, pos), ref, TOL[storage], "tiny %s %s/%s" % (dims, method, storage))
+    many = np.concatenate([pos] * 150)
+    spl.set_order("cell")
+    v, g, l = gpu_eval(spl, many)
+    assert_parity((v[:60], g[:60], l[:60]), ref, TOL[storage], "tiny cell order")
+    spl.close()
