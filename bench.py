@@ -451,8 +451,12 @@ def run_ours(args):
                 spl.eval_vgl(pos_d, out=outs, stream=cap)
         torch.cuda.synchronize()
         step = graph.replay    # replays on the current (timed) stream
-    cell_order = args.order == "cell" or (args.order == "auto" and n_pos >= 8192)
-    kernels_per_step = 4 if cell_order else 1     # bin, scan, place + evaluation
+    # the path qmcspl_eval_vgl takes (the rule of qmcspl_set_order)
+    staged = bool(info["staged"]) and args.order == "pencil"
+    cell_order = staged or args.order in ("cell", "pencil") or (args.order == "auto" and n_pos >= 8192)
+    order_name = "pencil" if staged else ("cell" if cell_order else "input")
+    kernel_name = "bspline_vgl_staged_kernel" if staged else "bspline_vgl_kernel"
+    kernels_per_step = 4 if cell_order else 1     # records/bins, scan, place + evaluation
 
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     for _ in range(args.warmup):
@@ -498,13 +502,13 @@ def run_ours(args):
     bpe = algorithmic_bytes_per_eval(args.storage, info["n_tables"], n_orb)
     launch_s = prof["eval_ms"] * 1e-3 / max(1, prof["launches"])
     achieved = bpe * evals_per_step / launch_s / 1e9
-    key = "bspline_vgl/%s/%s/%s" % (w.cell.name, args.storage, "cell" if cell_order else "input")
+    key = "%s/%s/%s/%s" % (kernel_name.replace("_kernel", ""), w.cell.name, args.storage, order_name)
     traffic = load_traffic(key)
 
     variants = {}
     if not args.no_variants and rank == 0:
-        for st, order in (("f32", "input"), ("bf16", "auto"), ("f64", "auto"), ("df64", "auto"),
-                          ("bf16", "input")):
+        for st, order in (("f32", "input"), ("f32", "pencil"), ("bf16", "auto"), ("bf16", "pencil"),
+                          ("f64", "auto"), ("df64", "auto"), ("bf16", "input")):
             if st == args.storage and order == args.order:
                 continue
             del outs
@@ -554,7 +558,7 @@ def run_ours(args):
                    "n_orb": n_orb, "grid": list(w.cell.grid), "walkers": w.cell.n_walkers,
                    "electrons": w.cell.n_elec, "positions": n_pos, "storage": args.storage,
                    "accumulate": {"f64": "f64", "df64": "double-float (f32 pairs)"}.get(args.storage, "f32"),
-                   "order": "cell" if cell_order else "input",
+                   "order": order_name,
                    "table_bytes": info["table_bytes"], "lanes": info["lanes"], "tiles": info["tiles"],
                    "cuda_graph": graph is not None,
                    "l2": "table and outputs larger than L2 (no flush needed)",
@@ -562,7 +566,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
                      "frac_of_nominal": achieved / 7900.0,
-                     "kernel": "bspline_vgl_kernel", "bytes_per_eval": bpe,
+                     "kernel": kernel_name, "bytes_per_eval": bpe,
                      "kernel_ms": launch_s * 1e3,
                      "order_kernels_ms": prof["order_ms"] / max(1, prof["launches"])},
         "roofline_l1": l1_roofline(bpe * evals_per_step, launch_s, clocks),
@@ -595,7 +599,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3")
     ap.add_argument("--storage", default="f32", choices=["f64", "df64", "f32", "bf16"])
-    ap.add_argument("--order", default="auto", choices=["auto", "input", "cell"])
+    ap.add_argument("--order", default="auto", choices=["auto", "input", "cell", "pencil"])
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

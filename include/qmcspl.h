@@ -123,6 +123,8 @@ typedef struct {
     int separate_grad;       /* 1: B-spline with separate gradient tables */
     int degree;              /* B-spline degree (3 unless created by qmcspl_create_grid) */
     int nonuniform;          /* 1: per-axis grid points (qmcspl_create_grid) */
+    int staged;              /* 1: pencil order evaluates with the shared-memory-staged kernel
+                                (see qmcspl_set_order); 0: it falls back to cell order */
 } qmcspl_info_t;
 
 /*
@@ -307,10 +309,26 @@ int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream);
  * caches instead of re-reading them from HBM.  Cell order sorts the positions into
  * spatial bins first (a counting sort on the device, in scratch memory the handle
  * allocates on first use and grows when a call has more positions).
+ * Pencil order sorts them into columns of 2 x 2 grid cells in (x, y), each by z cell, and
+ * evaluates them with the staged kernel: each z plane of the 5 x 5 stencil columns of a
+ * pencil is copied into shared memory once (tiled tensor copies) and read there by every
+ * position of the pencil that needs it.  It applies to cubic B-splines on uniform grids
+ * with FP32 or BF16 tables, without separate gradient tables, whose rows are 128, 256 or
+ * 512 bytes with one 16-byte chunk per lane (32, 64 or 128 FP32 orbitals; 64, 128 or 256
+ * BF16 orbitals); other handles, the batched call and qmcspl_eval_vgl_noalloc take cell
+ * order instead.  On GB300 cell order is the faster of the two for every workload measured,
+ * so pencil order is never chosen automatically.
  *   mode  QMCSPL_ORDER_AUTO (default: cell order for 8192 positions or more),
- *         QMCSPL_ORDER_INPUT or QMCSPL_ORDER_CELL
+ *         QMCSPL_ORDER_INPUT, QMCSPL_ORDER_CELL or QMCSPL_ORDER_PENCIL
+ * A staged evaluation whose pipeline stalls for about a second (a fault of this library,
+ * not of the input) gives up; qmcspl_sync then returns QMCSPL_ERR_TIMEOUT.
  */
-enum qmcspl_order { QMCSPL_ORDER_AUTO = 0, QMCSPL_ORDER_INPUT = 1, QMCSPL_ORDER_CELL = 2 };
+enum qmcspl_order {
+    QMCSPL_ORDER_AUTO = 0,
+    QMCSPL_ORDER_INPUT = 1,
+    QMCSPL_ORDER_CELL = 2,
+    QMCSPL_ORDER_PENCIL = 3
+};
 int qmcspl_set_order(qmcspl_t h, int mode);
 
 /*
@@ -393,6 +411,16 @@ int qmcspl_slater_kinetic(const void* val, const void* grad, const void* lap, in
  * (if any) usable.  Returns QMCSPL_OK.
  */
 int qmcspl_debug_fail_alloc(long long n);
+
+/*
+ * qmcspl_debug_stall_pipeline -- test hook: the next n staged evaluations (pencil order)
+ * run with a producer warp that copies nothing, so that every consumer wait of the
+ * pipeline runs out (about a second) exactly as it would if the pipeline had stalled.  The
+ * launch then ends on its own; qmcspl_sync returns QMCSPL_ERR_TIMEOUT, the outputs of that
+ * call are undefined, and the handle stays usable.  n <= 0 switches the hook off.  Returns
+ * QMCSPL_OK.
+ */
+int qmcspl_debug_stall_pipeline(int n);
 
 /*
  * qmcspl_profile / qmcspl_profile_read -- CUDA-event timing of the library's own kernels.

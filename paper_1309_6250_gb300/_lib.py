@@ -39,6 +39,7 @@ SLATER_ARITH = {"f64": 0, "df64": 1}
 ORDER_AUTO = 0
 ORDER_INPUT = 1
 ORDER_CELL = 2
+ORDER_PENCIL = 3
 
 METHODS = {"smooth": BSPLINE_SMOOTH, "interp": BSPLINE_INTERP, "lagrange": LAGRANGE, "pp": PPSPLINE}
 STORAGE = {"f64": F64, "f32": F32, "bf16": BF16, "df64": DF64}
@@ -63,7 +64,7 @@ class Info(ctypes.Structure):
                 ("rows_z", ctypes.c_int), ("lanes", ctypes.c_int), ("tiles", ctypes.c_int),
                 ("table_bytes", ctypes.c_longlong), ("n_pw", ctypes.c_longlong),
                 ("bloch", ctypes.c_int), ("kpoint", ctypes.c_double * 3), ("separate_grad", ctypes.c_int),
-                ("degree", ctypes.c_int), ("nonuniform", ctypes.c_int)]
+                ("degree", ctypes.c_int), ("nonuniform", ctypes.c_int), ("staged", ctypes.c_int)]
 
 
 class GridOpts(ctypes.Structure):
@@ -98,6 +99,7 @@ PROTOTYPES = [
     ("qmcspl_load", I, [ctypes.POINTER(VP), ctypes.c_char_p, VP]),
     ("qmcspl_slater_kinetic", I, [VP, VP, VP, I, I, LL, I, I, I, VP, VP, VP, VP, VP]),
     ("qmcspl_debug_fail_alloc", I, [LL]),
+    ("qmcspl_debug_stall_pipeline", I, [I]),
     ("qmcspl_sync", I, [VP, VP]),
     ("qmcspl_last_error", ctypes.c_char_p, []),
     ("qmcspl_version", I, []),

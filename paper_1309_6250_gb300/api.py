@@ -146,8 +146,10 @@ class OrbitalSplines:
         return out
 
     def set_order(self, mode: str) -> None:
-        """Order in which eval_vgl visits positions: 'auto', 'input' or 'cell'."""
-        code = {"auto": _lib.ORDER_AUTO, "input": _lib.ORDER_INPUT, "cell": _lib.ORDER_CELL}[mode]
+        """Order in which eval_vgl visits positions: 'auto', 'input', 'cell' or 'pencil'
+        (2 x 2-cell pencils evaluated by the shared-memory-staged kernel where it applies)."""
+        code = {"auto": _lib.ORDER_AUTO, "input": _lib.ORDER_INPUT, "cell": _lib.ORDER_CELL,
+                "pencil": _lib.ORDER_PENCIL}[mode]
         _lib.check(self.lib.qmcspl_set_order(self.handle, code))
 
     def profile(self, enable: bool = True) -> None:

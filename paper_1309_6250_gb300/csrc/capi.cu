@@ -14,6 +14,7 @@
 
 #include "general_basis.cuh"
 #include "qmcspl_internal.cuh"
+#include "staged.cuh"
 
 namespace qmcspl {
 
@@ -502,6 +503,7 @@ int qmcspl_info(qmcspl_t h, qmcspl_info_t* out)
     out->separate_grad = h->separate_grad;
     out->degree = h->degree;
     out->nonuniform = h->nonuniform;
+    out->staged = staged_eligible(h) ? 1 : 0;
     for (int i = 0; i < 3; ++i) out->kpoint[i] = h->kpoint[i];
     return QMCSPL_OK;
 }
@@ -513,6 +515,16 @@ static int eval_dispatch(Handle* h, const double* pos, long long n_pos, void* va
     if (h->prof_on && h->prof_n < kProfCalls) ev = h->prof_ev + 3 * h->prof_n++;
     if (ev) cudaEventRecord(ev[0], st);
     Prepared pr;
+    BinGeometry pg;
+    StagedArgs sa;
+    if (use_staged(h, n_pos) && staged_plan(h, n_pos, &pg, &sa)) {
+        int rc = prepare_positions(h, pos, n_pos, true, &pr, st, &pg);
+        if (rc != QMCSPL_OK) return rc;
+        if (ev) cudaEventRecord(ev[1], st);
+        rc = launch_bspline_vgl_staged(h, pr, n_pos, val, grad, lap, sa, st);
+        if (ev) cudaEventRecord(ev[2], st);
+        return rc;
+    }
     const bool sort = use_cell_order(h, n_pos);
     // Bloch handles always take the per-position pass: it computes the phase factors
     if (sort || n_pos >= kRecordMinPositions || h->bloch) {
@@ -809,7 +821,7 @@ int qmcspl_set_order(qmcspl_t h, int mode)
 {
     g_err.clear();
     if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
-    if (mode < QMCSPL_ORDER_AUTO || mode > QMCSPL_ORDER_CELL) return set_error(QMCSPL_ERR_ARG, "unknown order mode");
+    if (mode < QMCSPL_ORDER_AUTO || mode > QMCSPL_ORDER_PENCIL) return set_error(QMCSPL_ERR_ARG, "unknown order mode");
     h->order_mode = mode;
     return QMCSPL_OK;
 }
@@ -827,9 +839,11 @@ int qmcspl_sync(qmcspl_t h, void* stream)
     if (e != cudaSuccess) return cuda_error(e, "error word read");
     if (flag) {
         cudaMemset(h->d_err, 0, sizeof(int));
+        if (flag & 4)
+            return set_error(QMCSPL_ERR_TIMEOUT, "a wait of the staged evaluation pipeline gave up");
         if (flag & 2)
-            return set_error(QMCSPL_ERR_DEVICE, "a kernel caught an out-of-range table or position index "
-                                                "(bounds-checked build)");
+            return set_error(QMCSPL_ERR_DEVICE, "a kernel caught an out-of-range table, plane or position "
+                                                "index");
         return set_error(QMCSPL_ERR_DEVICE, "a kernel saw a non-finite position");
     }
     return QMCSPL_OK;

@@ -33,7 +33,7 @@ struct PrepArgs {
     long long n;
     double ainv[9];
     int dims[3];
-    int edge;
+    int edge[3];              // grid cells per bin edge, per axis
     int nb[3];
     void* rec;                // records (kind 1, 2 or 3), may be null
     double2* phase;           // Bloch phase factors, may be null
@@ -119,46 +119,52 @@ __global__ void prepare_kernel(const PrepArgs a)
         a.phase[i] = make_double2(cs, sn);
     }
     if (a.count) {
-        const int b = ((ix / a.edge) * a.nb[1] + iy / a.edge) * a.nb[2] + iz / a.edge;
+        const int b = ((ix / a.edge[0]) * a.nb[1] + iy / a.edge[1]) * a.nb[2] + iz / a.edge[2];
         a.bin[i] = b;
         atomicAdd(a.count + b, 1);
     }
 }
 
 // In-place exclusive scan of count[0 .. n) by one block; count[n] receives the total.
+// Each warp owns one contiguous segment and walks it 32 entries at a time (coalesced):
+// first the segment sums, then, from the block-wide prefix of those, the scan itself.
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(int* count, int n)
 {
-    __shared__ int warp_sum[kScanThreads / 32];
-    const int per = (n + kScanThreads - 1) / kScanThreads;
-    const int lo = threadIdx.x * per;
-    const int hi = min(lo + per, n);
-    int s = 0;
-    for (int i = lo; i < hi; ++i) s += count[i];
-    // block-wide exclusive scan of the per-thread sums
+    constexpr int kWarps = kScanThreads / 32;
+    __shared__ int seg_sum[kWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = s;
-    for (int off = 1; off < 32; off <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, off);
-        if (lane >= off) incl += v;
-    }
-    if (lane == 31) warp_sum[wid] = incl;
+    const int per = ((n + kScanThreads - 1) / kScanThreads) * 32;   // a multiple of 32
+    const int lo = min(wid * per, n), hi = min(lo + per, n);
+    int s = 0;
+#pragma unroll 4
+    for (int i = lo + lane; i < hi; i += 32) s += count[i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) seg_sum[wid] = s;
     __syncthreads();
     if (wid == 0) {
-        int w = warp_sum[lane];
+        const int v = seg_sum[lane];
+        int incl = v;
         for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, w, off);
-            if (lane >= off) w += v;
+            const int u = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += u;
         }
-        warp_sum[lane] = w;   // inclusive over warps
+        seg_sum[lane] = incl - v;   // exclusive over segments
+        if (lane == 31) count[n] = incl;
     }
     __syncthreads();
-    int run = incl - s + (wid > 0 ? warp_sum[wid - 1] : 0);
-    for (int i = lo; i < hi; ++i) {
-        const int c = count[i];
-        count[i] = run;
-        run += c;
+    int carry = seg_sum[wid];
+    for (int base = lo; base < hi; base += 32) {
+        const int i = base + lane;
+        const int c = i < hi ? count[i] : 0;
+        int incl = c;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += u;
+        }
+        if (i < hi) count[i] = carry + incl - c;
+        carry += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (threadIdx.x == kScanThreads - 1) count[n] = run;
 }
 
 __global__ void place_kernel(const int* bin, long long n, int* offset, int* perm)
@@ -182,8 +188,8 @@ PrepArgs prep_args(const Handle* h, const double* pos, long long n, void* rec, d
     for (int i = 0; i < 3; ++i) {
         a.dims[i] = h->dims[i];
         a.nb[i] = g ? g->nb[i] : 1;
+        a.edge[i] = g ? g->edge[i] : 1;
     }
-    a.edge = g ? g->edge : 1;
     a.rec = rec;
     a.bin = bin;
     a.count = count;
@@ -209,18 +215,19 @@ int launch_prepare(const PrepArgs& a, int kind, cudaStream_t st)
 BinGeometry bin_geometry(const Handle* h)
 {
     BinGeometry g;
-    g.edge = QMCSPL_BIN_EDGE;
+    int edge = QMCSPL_BIN_EDGE;
     for (;;) {
         long long nb = 1;
         for (int a = 0; a < 3; ++a) {
-            g.nb[a] = (h->dims[a] + g.edge - 1) / g.edge;
+            g.edge[a] = edge;
+            g.nb[a] = (h->dims[a] + edge - 1) / edge;
             nb *= g.nb[a];
         }
         if (nb <= kMaxBins) {
             g.n_bins = (int)nb;
             return g;
         }
-        g.edge *= 2;
+        edge *= 2;
     }
 }
 
@@ -229,7 +236,8 @@ bool use_cell_order(const Handle* h, long long n_pos)
     if (n_pos >= (1LL << 31) - 1) return false;
     switch (h->order_mode) {
     case QMCSPL_ORDER_INPUT: return false;
-    case QMCSPL_ORDER_CELL: return true;
+    case QMCSPL_ORDER_CELL:
+    case QMCSPL_ORDER_PENCIL: return true;   // pencil order where staged evaluation does not apply
     default: return n_pos >= 8192;
     }
 }
@@ -302,9 +310,9 @@ int cell_order(Handle* h, const double* pos, long long n_pos, const int** perm, 
 }
 
 int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, Prepared* out,
-                      cudaStream_t st)
+                      cudaStream_t st, const BinGeometry* geom)
 {
-    const BinGeometry g = bin_geometry(h);
+    const BinGeometry g = geom ? *geom : bin_geometry(h);
     int rc = grow_scratch(h, n_pos, g.n_bins);
     if (rc != QMCSPL_OK) return rc;
     out->rec = h->ord_rec;
@@ -318,6 +326,7 @@ int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, 
     scan_kernel<<<1, kScanThreads, 0, st>>>(h->ord_count, g.n_bins);
     place_kernel<<<blocks, 256, 0, st>>>(h->ord_bin, n_pos, h->ord_count, h->ord_perm);
     out->perm = h->ord_perm;
+    out->bin_end = h->ord_count;
     return cuda_error(cudaGetLastError(), "cell-order kernels");
 }
 

@@ -173,6 +173,7 @@ struct Prepared {
     const void* rec = nullptr;
     const int* perm = nullptr;
     const double2* phase = nullptr;
+    const int* bin_end = nullptr;   // sorted: one past the last position of every bin
 };
 int launch_bspline_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
                        void* grad, void* lap, cudaStream_t stream);
@@ -194,9 +195,10 @@ int launch_batched(int n_cells, const Handle* const* hs, const double* const* po
                    cudaStream_t stream);
 
 // ---- cell ordering (order.cu) ----
-// Bin geometry of a handle: bins of `edge` grid cells per axis, nb[3] bins per axis.
+// Bin geometry of a handle: bins of edge[a] grid cells along axis a, nb[a] bins along it;
+// bins are numbered x-major, z fastest.
 struct BinGeometry {
-    int edge;
+    int edge[3];
     int nb[3];
     int n_bins;
 };
@@ -224,9 +226,9 @@ int record_kind(const Handle* h);
 int build_records(const Handle* h, const double* pos, long long n_pos, void* rec, double2* phase, int* bin,
                   int* count, const BinGeometry* g, cudaStream_t stream);
 // Records, phase factors (Bloch handles) and, when sorting, the cell order in the
-// handle's scratch.
+// handle's scratch: bins of the handle's bin_geometry, or of `geom` when given.
 int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, Prepared* out,
-                      cudaStream_t stream);
+                      cudaStream_t stream, const BinGeometry* geom = nullptr);
 
 // Allocate (once) and fill the device grid-point buffer of a non-uniform handle.
 int upload_grid_points(Handle* h, cudaStream_t stream);

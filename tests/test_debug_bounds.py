@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SUITES = ["tests/test_parity_bspline.py", "tests/test_parity_variants.py", "tests/test_parity_limits.py",
           "tests/test_parity_bloch.py", "tests/test_parity_general.py", "tests/test_parity_separate_grad.py",
-          "tests/test_parity_order_batched.py", "tests/test_parity_backward.py"]
+          "tests/test_parity_order_batched.py", "tests/test_parity_backward.py", "tests/test_parity_staged.py"]
 
 
 def test_parity_suites_under_the_bounds_checked_build():
