@@ -357,8 +357,8 @@ def bench_consumer(args, dev, stream):
 
 
 def bench_general(args, dev, stream):
-    """Interpolating B-splines of degree 1, 3, 5, 7 and a graded (non-uniform) cubic grid on
-    the Si-like 8-atom cell (16 orbitals, 48^3, 1024 walkers x 32 electrons, FP32 tables
+    """Interpolating B-splines of degree 1, 3, 5, 7 on the uniform grid and of degree 3, 5, 7 on a
+    graded (non-uniform) grid of the same size, on the Si-like 8-atom cell (16 orbitals, 48^3, 1024 walkers x 32 electrons, FP32 tables
     with the Laplacian table): orbital evaluations per second.  Degree 3 on the uniform grid
     is the tuned cubic kernel, the others the general kernel ((n+1)^3-point stencils)."""
     import torch
@@ -369,7 +369,8 @@ def bench_general(args, dev, stream):
     out = {}
     graded = tuple(inputs.graded_knots(d, 0.5, 0.17 * a) for a, d in enumerate(w.cell.grid))
     for name, kw in (("degree1", dict(degree=1)), ("degree3", dict(degree=3)), ("degree5", dict(degree=5)),
-                     ("degree7", dict(degree=7)), ("graded_cubic", dict(knots=graded))):
+                     ("degree7", dict(degree=7)), ("graded_cubic", dict(knots=graded)),
+                     ("graded_degree5", dict(degree=5, knots=graded)), ("graded_degree7", dict(degree=7, knots=graded))):
         spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="interp", storage="f32",
                              separate_lap=True, device=dev, **kw)
         t = _time_handle(spl, pos, torch, stream, max(10, args.steps // 4))

@@ -162,8 +162,8 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
                   void* stream);
 
 /*
- * qmcspl_create_grid -- qmcspl_create for B-splines of another odd degree, or interpolating
- * B-splines on a non-uniform grid.
+ * qmcspl_create_grid -- qmcspl_create for B-splines of another odd degree, and interpolating
+ * B-splines of any of these degrees on a non-uniform grid.
  *
  * Paper: Sec. II, "Common features" (each method may use polynomials of any order n; the
  * paper uses cubics) and "Grid" (uniform or non-uniform grids); Appendix, the B-spline
@@ -177,9 +177,12 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
  *                   exactly in Fourier space (its symbol sum_j C_n B_n(j) e^{i j th}).
  *   grid->knots[a]  NULL for a uniform axis, else host double[dims[a]]: the grid points of
  *                   axis a in reduced coordinates, strictly increasing in [0, 1); either
- *                   all three axes or none.  Non-uniform grids are cubic; the planewave band
- *                   must fit the grid (dims[a] >= 2 max|n_a| + 1, else QMCSPL_ERR_ARG) and
- *                   the cyclic tridiagonal system is solved along each axis in FP64.
+ *                   all three axes or none.  Any of the four degrees; the planewave band
+ *                   must fit the grid (dims[a] >= 2 max|n_a| + 1, else QMCSPL_ERR_ARG).  The
+ *                   periodic interpolation system is solved along each axis in FP64: cyclic
+ *                   tridiagonal for the cubic, the identity for degree 1, and for degrees 5
+ *                   and 7 through the inverse of the cyclic banded matrix (computed on the
+ *                   host, O(N^3) per axis; QMCSPL_ERR_ARG if it is singular).
  * Other arguments as qmcspl_create; opts->method QMCSPL_BSPLINE_INTERP, or on uniform
  * grids also QMCSPL_BSPLINE_SMOOTH (Eq. b-splinecoefficients with gamma the Fourier
  * transform of the degree-n basis, C_n sinc^{n+1}(th/2) per axis); storage F64, F32 or BF16;

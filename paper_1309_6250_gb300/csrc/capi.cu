@@ -372,7 +372,6 @@ int qmcspl_create_grid(qmcspl_t* out, const double lattice[9], const int dims[3]
         if (degree != 1 && degree != 3 && degree != 5 && degree != 7)
             return set_error(QMCSPL_ERR_ARG, "degree must be 1, 3, 5 or 7");
         for (int a = 0; a < 3; ++a) nonuni = nonuni || grid->knots[a] != nullptr;
-        if (nonuni && degree != 3) return set_error(QMCSPL_ERR_UNSUPPORTED, "non-uniform grids are cubic");
         // other degrees: interpolating or smoothing B-splines; non-uniform grids: interpolating
         const bool ok_method = nonuni ? opts->method == QMCSPL_BSPLINE_INTERP
                                       : (opts->method == QMCSPL_BSPLINE_INTERP || opts->method == QMCSPL_BSPLINE_SMOOTH);

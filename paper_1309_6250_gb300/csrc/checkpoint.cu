@@ -150,7 +150,7 @@ extern "C" int qmcspl_load(qmcspl_t* out, const char* path, void* stream)
     sane = sane && hd.elem_bytes == eb && (long long)hd.n_orb_p * hd.elem_bytes % 16 == 0 &&
            hd.n_orb_p == hd.tiles * (1 << hd.lanes_log2) * (int)(16 / eb) &&
            (hd.degree == 1 || hd.degree == 3 || hd.degree == 5 || hd.degree == 7) &&
-           (hd.nonuniform == 0 || (hd.nonuniform == 1 && hd.degree == 3)) &&
+           (hd.nonuniform == 0 || hd.nonuniform == 1) &&
            hd.rows_z == hd.dims[2] + (hd.method == QMCSPL_PPSPLINE ? 1 : hd.degree) &&
            hd.table_elems == (long long)hd.dims[0] * hd.dims[1] * hd.rows_z * hd.entries * hd.n_orb_p;
     for (int i = 0; i < 9; ++i) sane = sane && std::isfinite(hd.lattice[i]);

@@ -18,14 +18,16 @@
 //           e^{i j th}, the symbol of the periodic interpolation system of the degree-n basis;
 //           smoothing 1 / prod_m C_n sinc^{n+1}(th_m / 2), the Fourier transform of the
 //           degree-n basis (the paper's gamma_G for n = 3)
+// with th_m = 2 pi n_m / N_m.  The cyclic systems of uniform grids are circulant, so dividing
+// the folded spectrum by their eigenvalues is their exact solution.
 //
 // Non-uniform grids (Sec. II "Grid": interpolating splines need no even spacing): the
 // planewave sum is evaluated at the per-axis grid points by the same separable passes with
 // the true frequencies (the band must fit the grid, 2 n_max + 1 <= N, so folded indices
-// map back to frequencies), then the cyclic tridiagonal interpolation system of the
-// non-uniform cubic basis is solved along each axis (Thomas + Sherman-Morrison).
-// with th_m = 2 pi n_m / N_m.  The cyclic systems are circulant, so dividing the folded
-// spectrum by their eigenvalues is their exact solution.
+// map back to frequencies), then the periodic interpolation system of the non-uniform basis
+// is solved along each axis: cyclic tridiagonal for the cubic (Thomas + Sherman-Morrison),
+// the identity for degree 1, and for degrees 5 and 7 the FP64 inverse of the banded cyclic
+// collocation matrix applied to every grid line.
 //
 // Bloch orbitals (Sec. II, phi = u exp(i k.r)): the same sums give the complex periodic
 // part u (and, for the derivative tables, the periodic parts of grad phi and lap phi,
@@ -41,6 +43,7 @@
 // Orbitals are processed in chunks so the complex grids stay below a fixed budget.
 #include <cmath>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include "general_basis.cuh"
@@ -528,6 +531,108 @@ int launch_solve(double2* F, long long outer, int N, long long inner, const doub
     return cuda_error(cudaGetLastError(), "cyclic_solve_kernel launch");
 }
 
+// Degree-n interpolation on a non-uniform periodic axis (n = 5, 7): the collocation matrix
+// M[i][m] = sum over periodic images of the basis of grid point m at grid point x_i is cyclic
+// with bandwidth n; it is inverted once on the host (Gauss-Jordan elimination with partial
+// pivoting, FP64; N <= 512) and the inverse applied to every grid line on the device.
+template <int DEG>
+void collocation_row(const std::vector<double>& hs, int n, int i, double C, double* w)
+{
+    double dw[DEG + 1];
+    nonuniform_weights_local<double, double, DEG>(hs.data(), n, i, 0.0, C, w, dw, nullptr);
+}
+
+bool collocation_inverse(const double* knots, int n, int degree, std::vector<double>& inv)
+{
+    std::vector<double> hs(n);
+    for (int i = 0; i < n; ++i) hs[i] = (i + 1 < n ? knots[i + 1] : knots[0] + 1.0) - knots[i];
+    const double C = degree_constant(degree);
+    const int H = (degree - 1) / 2;
+    std::vector<double> M((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (degree == 5) collocation_row<5>(hs, n, i, C, w);
+        else collocation_row<7>(hs, n, i, C, w);
+        for (int r = 0; r <= degree; ++r) {
+            int m = (i - H + r) % n;
+            if (m < 0) m += n;
+            M[(size_t)i * n + m] += w[r];
+        }
+    }
+    inv.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(M[(size_t)r * n + c]) > std::fabs(M[(size_t)piv * n + c])) piv = r;
+        if (!(std::fabs(M[(size_t)piv * n + c]) > 0.0)) return false;
+        if (piv != c)
+            for (int k = 0; k < n; ++k) {
+                std::swap(M[(size_t)c * n + k], M[(size_t)piv * n + k]);
+                std::swap(inv[(size_t)c * n + k], inv[(size_t)piv * n + k]);
+            }
+        const double d = 1.0 / M[(size_t)c * n + c];
+        for (int k = 0; k < n; ++k) {
+            M[(size_t)c * n + k] *= d;
+            inv[(size_t)c * n + k] *= d;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = M[(size_t)r * n + c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < n; ++k) {
+                M[(size_t)r * n + k] -= f * M[(size_t)c * n + k];
+                inv[(size_t)r * n + k] -= f * inv[(size_t)c * n + k];
+            }
+        }
+    }
+    return true;
+}
+
+struct DenseArgs {
+    const double2* in;        // [outer][N][inner]
+    double2* out;             // the same shape
+    long long outer, inner;
+    int N;
+    const double* minv;       // N x N, row-major
+};
+
+// out[o][i][k] = sum_m minv[i][m] in[o][m][k], one thread per output element
+__global__ void dense_axis_kernel(const DenseArgs a)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long line = (long long)a.N * a.inner;
+    if (idx >= a.outer * line) return;
+    const long long o = idx / line, rem = idx - o * line;
+    const int i = (int)(rem / a.inner);
+    const long long k = rem - (long long)i * a.inner;
+    const double* row = a.minv + (size_t)i * a.N;
+    const double2* x = a.in + o * line + k;
+    double re = 0.0, im = 0.0;
+    for (int m = 0; m < a.N; ++m) {
+        const double c = __ldg(row + m);
+        const double2 v = x[(long long)m * a.inner];
+        re = fma(c, v.x, re);
+        im = fma(c, v.y, im);
+    }
+    a.out[idx] = make_double2(re, im);
+}
+
+int launch_dense(const double2* in, double2* out, long long outer, int N, long long inner, const double* minv,
+                 cudaStream_t st)
+{
+    DenseArgs a;
+    a.in = in;
+    a.out = out;
+    a.outer = outer;
+    a.inner = inner;
+    a.N = N;
+    a.minv = minv;
+    const long long n = outer * N * inner;
+    dense_axis_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+    return cuda_error(cudaGetLastError(), "dense_axis_kernel launch");
+}
+
 // C_n B_n(j), j = 0..3: the symbol coefficients of the degree-n interpolation system
 void degree_symbol(int n, double sym[4])
 {
@@ -570,9 +675,18 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
     else if (h->degree != 3) basis = h->method == QMCSPL_BSPLINE_SMOOTH ? kBasisSmoothN : kBasisInterpN;
     double sym[4] = {0.0, 0.0, 0.0, 0.0};
     if (basis == kBasisInterpN) degree_symbol(h->degree, sym);
+    // non-uniform grids: cubic, the cyclic tridiagonal systems; degree 5 and 7, dense inverses;
+    // degree 1 interpolates with the identity (the coefficients are the grid values)
+    const bool tridiag = h->nonuniform && h->degree == 3;
+    const bool dense = h->nonuniform && h->degree >= 5;
     AxisSystem sys[3];
-    if (h->nonuniform)
+    std::vector<double> minv[3];
+    if (tridiag)
         for (int a = 0; a < 3; ++a) sys[a] = axis_system(h->knots[a], h->dims[a], degree_constant(3));
+    if (dense)
+        for (int a = 0; a < 3; ++a)
+            if (!collocation_inverse(h->knots[a], h->dims[a], h->degree, minv[a]))
+                return set_error(QMCSPL_ERR_ARG, "the interpolation system of a non-uniform axis is singular");
     if (h->method == QMCSPL_PPSPLINE) {
         // entry e = 4(kappa-1) + 2(mu-1) + (nu-1); label 2 <=> bit set
         for (int e = 0; e < 8; ++e) jobs.push_back({0, e, kBasisPP, kDerivValue, e});
@@ -592,11 +706,24 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
     int* d_miller = nullptr;
     double2* d_coef = nullptr;
     double2* F[2] = {nullptr, nullptr};
-    double* d_sys = nullptr;   // non-uniform: 3 axis systems of 4 N doubles
+    double* d_sys = nullptr;   // non-uniform: 3 axis systems of 4 N doubles, or 3 inverses of N^2
     int rc = QMCSPL_OK;
     cudaError_t e;
     do {
-        if (h->nonuniform) {
+        if (dense) {
+            const size_t nd = (size_t)N1 * N1 + (size_t)N2 * N2 + (size_t)N3 * N3;
+            e = dev_malloc_async((void**)&d_sys, sizeof(double) * nd, st);
+            if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(axis inverses)"); break; }
+            size_t off = 0;
+            for (int a = 0; a < 3; ++a) {
+                e = cudaMemcpyAsync(d_sys + off, minv[a].data(), sizeof(double) * minv[a].size(),
+                                    cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) break;
+                off += minv[a].size();
+            }
+            if (e != cudaSuccess) { rc = cuda_error(e, "upload axis inverses"); break; }
+        }
+        if (tridiag) {
             const size_t nd = 4 * (size_t)(N1 + N2 + N3);
             e = dev_malloc_async((void**)&d_sys, sizeof(double) * nd, st);
             if (e != cudaSuccess) { rc = cuda_error(e, "cudaMallocAsync(axis systems)"); break; }
@@ -672,15 +799,24 @@ int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef
                 d.skip_mode = 0;
                 d.pts = h->nonuniform ? h->d_knots : nullptr;
                 if ((rc = launch_dft(d, st)) != QMCSPL_OK) break;
-                if (h->nonuniform) {   // interpolation systems along x, y, z (any order)
+                double2* res = F[1];
+                if (tridiag) {   // interpolation systems along x, y, z (any order)
                     const double* c0 = d_sys;
                     const double* c1 = c0 + 4 * (size_t)N1;
                     const double* c2 = c1 + 4 * (size_t)N2;
                     if ((rc = launch_solve(F[1], 1, N1, (long long)N2 * N3 * oc, c0, sys[0], st)) != QMCSPL_OK) break;
                     if ((rc = launch_solve(F[1], N1, N2, (long long)N3 * oc, c1, sys[1], st)) != QMCSPL_OK) break;
                     if ((rc = launch_solve(F[1], (long long)N1 * N2, N3, oc, c2, sys[2], st)) != QMCSPL_OK) break;
+                } else if (dense) {   // x: F1 -> F0, y: F0 -> F1, z: F1 -> F0
+                    const double* m0 = d_sys;
+                    const double* m1 = m0 + (size_t)N1 * N1;
+                    const double* m2 = m1 + (size_t)N2 * N2;
+                    if ((rc = launch_dense(F[1], F[0], 1, N1, (long long)N2 * N3 * oc, m0, st)) != QMCSPL_OK) break;
+                    if ((rc = launch_dense(F[0], F[1], N1, N2, (long long)N3 * oc, m1, st)) != QMCSPL_OK) break;
+                    if ((rc = launch_dense(F[1], F[0], (long long)N1 * N2, N3, oc, m2, st)) != QMCSPL_OK) break;
+                    res = F[0];
                 }
-                if ((rc = launch_layout(h, F[1], job.tab, job.entry, o0, oc, st)) != QMCSPL_OK) break;
+                if ((rc = launch_layout(h, res, job.tab, job.entry, o0, oc, st)) != QMCSPL_OK) break;
             }
         }
     } while (0);

@@ -1,6 +1,6 @@
-// general_basis.cuh -- B-spline basis weights of any odd degree on uniform grids, and of
-// degree 3 on non-uniform periodic grids (Appendix, the B-spline recurrence), for the
-// general evaluation kernel and the host-side construction of non-uniform systems.
+// general_basis.cuh -- B-spline basis weights of any odd degree on uniform and on
+// non-uniform periodic grids (Appendix, the B-spline recurrence), for the general
+// evaluation kernel and the host-side construction of the non-uniform interpolation systems.
 //
 // The recurrence b_j^k = w_j^k b_j^{k-1} + (1 - w_{j+1}^k) b_{j+1}^{k-1},
 // w_j^k(x) = (x - x_j)/(x_{j+k} - x_j), b_j^0 = C on [x_j, x_{j+1}), gives on the knot
@@ -166,34 +166,42 @@ __host__ __device__ inline void nonuniform_cubic_weights(const double* knots, in
     }
 }
 
-// The same cubic weights from the offset dx = x - x_i inside interval i and the periodic
-// knot spacings hs[j] = x_{j+1} - x_j (j mod n), in the arithmetic type S of the spacings:
-// every knot difference the recurrence needs is a sum of consecutive spacings, so no
-// absolute coordinate (and no FP64 for FP32 tables) is involved.
-template <typename S, typename A>
-__host__ __device__ inline void nonuniform_cubic_weights_local(const S* hs, int n, int i, S dx, A C, A* w,
-                                                               A* dw, A* d2w)
+// Weights of odd degree DEG on the non-uniform interval [x_i, x_{i+1}): the DEG + 1 nonzero
+// functions b_{i-DEG}^DEG .. b_i^DEG (grid points i - (DEG-1)/2 .. i + (DEG+1)/2) at
+// x = x_i + dx, with their first and second derivatives with respect to the reduced
+// coordinate; de Boor's triangular evaluation of the recurrence, and
+//   d/dx b_j^k = k (b_j^{k-1} / (x_{j+k} - x_j) - b_{j+1}^{k-1} / (x_{j+k+1} - x_{j+1})).
+// Everything comes from dx and the periodic knot spacings hs[j] = x_{j+1} - x_j (j mod n), in
+// the arithmetic type S of the spacings: every knot difference the recurrence needs is a sum
+// of consecutive spacings, so no absolute coordinate (and no FP64 for FP32 tables) is involved.
+template <typename S, typename A, int DEG>
+__host__ __device__ inline void nonuniform_weights_local(const S* hs, int n, int i, S dx, A C, A* w, A* dw,
+                                                         A* d2w)
 {
     auto h = [&](int j) -> S {
         j %= n;
         return hs[j < 0 ? j + n : j];
     };
-    // kd(a, b) = x_a - x_b for b <= a <= b + 4
+    // kd(a, b) = x_a - x_b for b <= a <= b + DEG + 1
     auto kd = [&](int a, int b) -> S {
         S s = S(0);
         for (int j = b; j < a; ++j) s += h(j);
         return s;
     };
-    S left[4], right[4];
+    S left[DEG + 1], right[DEG + 1];
     left[1] = dx;
-    left[2] = dx + h(i - 1);
-    left[3] = left[2] + h(i - 2);
     right[1] = h(i) - dx;
-    right[2] = right[1] + h(i + 1);
-    right[3] = right[2] + h(i + 2);
-    S N1[2], N2[3];
-    S Nl[4] = {S(1), S(0), S(0), S(0)};
-    for (int j = 1; j <= 3; ++j) {
+    for (int j = 2; j <= DEG; ++j) {
+        left[j] = left[j - 1] + h(i - j + 1);
+        right[j] = right[j - 1] + h(i + j - 1);
+    }
+    // Nl[q]: the level-j function starting at knot i - j + q; levels DEG - 1 and DEG - 2 kept
+    S Nl[DEG + 1], N1[DEG + 1], N2[DEG + 1];
+    for (int q = 0; q <= DEG; ++q) Nl[q] = N1[q] = N2[q] = S(0);
+    Nl[0] = S(1);
+    if (DEG == 1) N1[0] = S(1);
+    if (DEG == 2) N2[0] = S(1);
+    for (int j = 1; j <= DEG; ++j) {
         S saved = S(0);
         for (int r = 0; r < j; ++r) {
             const S temp = Nl[r] / (right[r + 1] + left[j - r]);
@@ -201,24 +209,28 @@ __host__ __device__ inline void nonuniform_cubic_weights_local(const S* hs, int 
             saved = left[j - r] * temp;
         }
         Nl[j] = saved;
-        if (j == 1) { N1[0] = Nl[0]; N1[1] = Nl[1]; }
-        if (j == 2) { N2[0] = Nl[0]; N2[1] = Nl[1]; N2[2] = Nl[2]; }
+        if (j == DEG - 1)
+            for (int q = 0; q <= j; ++q) N1[q] = Nl[q];
+        if (j == DEG - 2)
+            for (int q = 0; q <= j; ++q) N2[q] = Nl[q];
     }
-    auto b1 = [&](int k) -> S {
-        const int q = k - (i - 1);
-        return (q >= 0 && q <= 1) ? N1[q] : S(0);
+    auto b1 = [&](int k) -> S {   // level DEG - 1, starting at knot k
+        const int q = k - (i - (DEG - 1));
+        return (q >= 0 && q <= DEG - 1) ? N1[q] : S(0);
     };
-    auto b2 = [&](int k) -> S {
-        const int q = k - (i - 2);
-        return (q >= 0 && q <= 2) ? N2[q] : S(0);
+    auto b2 = [&](int k) -> S {   // level DEG - 2
+        const int q = k - (i - (DEG - 2));
+        return (DEG >= 2 && q >= 0 && q <= DEG - 2) ? N2[q] : S(0);
     };
-    auto db2 = [&](int k) -> S { return S(2) * (b1(k) / kd(k + 2, k) - b1(k + 1) / kd(k + 3, k + 1)); };
-    for (int r = 0; r < 4; ++r) {
-        const int k = i - 3 + r;
+    auto db1 = [&](int k) -> S {
+        return S(DEG - 1) * (b2(k) / kd(k + DEG - 1, k) - b2(k + 1) / kd(k + DEG, k + 1));
+    };
+    for (int r = 0; r <= DEG; ++r) {
+        const int k = i - DEG + r;   // start knot of the function of grid point i - (DEG-1)/2 + r
         w[r] = C * (A)Nl[r];
-        const S ak = S(3) / kd(k + 3, k), bk = S(3) / kd(k + 4, k + 1);
-        dw[r] = C * (A)(ak * b2(k) - bk * b2(k + 1));
-        if (d2w) d2w[r] = C * (A)(ak * db2(k) - bk * db2(k + 1));
+        const S ak = S(DEG) / kd(k + DEG, k), bk = S(DEG) / kd(k + DEG + 1, k + 1);
+        dw[r] = C * (A)(ak * b1(k) - bk * b1(k + 1));
+        if (d2w) d2w[r] = DEG >= 2 ? C * (A)(ak * db1(k) - bk * db1(k + 1)) : A(0);
     }
 }
 

@@ -117,8 +117,8 @@ def test_grid_options_validated_without_gpu(lib):
     assert create(5, (None,) * 3, method=2) == _lib.ERR_UNSUPPORTED     # Lagrange, degree 5
     assert create(3, (u, u, u), method=0) == _lib.ERR_UNSUPPORTED       # smoothing, non-uniform
     assert create(5, (None,) * 3, storage=3) == _lib.ERR_UNSUPPORTED    # double-float
-    assert create(5, (u, u, u)) == _lib.ERR_UNSUPPORTED                 # non-uniform quintic
     assert create(3, (u, None, u)) == _lib.ERR_ARG                      # one axis missing
+    assert create(7, (None, u, u)) == _lib.ERR_ARG                      # the same, degree 7
     bad = u.copy()
     bad[3] = bad[2]
     assert create(3, (u, bad, u)) == _lib.ERR_ARG and b"increasing" in lib.qmcspl_last_error()

@@ -55,8 +55,6 @@ def test_degree_constants_are_the_cardinal_central_values():
 def test_partition_of_unity_and_derivatives(degree, uniform):
     """The periodic family sums to C everywhere; the derivative formula agrees with central
     differences of the recurrence (first and second derivatives)."""
-    if not uniform and degree != 3:
-        pytest.skip("non-uniform grids are cubic")
     n = 11
     pts = np.arange(n) / n if uniform else inputs.graded_knots(n, 0.6, 0.1)
     C = 1.5 if degree == 3 else oracle.degree_constant(degree)
@@ -76,7 +74,8 @@ def test_partition_of_unity_and_derivatives(degree, uniform):
         np.testing.assert_allclose(d2, fd2, atol=1e-5 * max(1.0, np.abs(d2).max()))
 
 
-@pytest.mark.parametrize("degree,graded", [(1, False), (3, False), (5, False), (7, False), (3, True)])
+@pytest.mark.parametrize("degree,graded", [(1, False), (3, False), (5, False), (7, False), (1, True), (3, True),
+                                           (5, True), (7, True)])
 def test_interpolation_reproduces_grid_values(degree, graded):
     dims = (9, 10, 11)
     knots = tuple(inputs.graded_knots(d, 0.5, 0.2 * a) for a, d in enumerate(dims)) if graded else (None,) * 3
@@ -130,7 +129,8 @@ def test_degree_one_is_trilinear_interpolation():
 
 
 @pytest.mark.parametrize("degree,graded,ratio", [(1, False, 3.0), (3, False, 12.0), (5, False, 40.0),
-                                                 (3, True, 11.0)])
+                                                 (1, True, 3.0), (3, True, 11.0), (5, True, 35.0),
+                                                 (7, True, 150.0)])
 def test_convergence_order(degree, graded, ratio):
     """Refining the grid at a fixed planewave set converges the value as h^(n+1) (Sec. III A
     footnote for the cubic; the order of a degree-n spline in general), also on graded grids."""
@@ -148,7 +148,8 @@ def test_convergence_order(degree, graded, ratio):
     assert errs[0] / errs[1] > ratio
 
 
-def test_graded_cubic_is_C2_across_knots_and_chain_rule():
+@pytest.mark.parametrize("degree", [3, 5])
+def test_graded_spline_is_smooth_across_knots_and_chain_rule(degree):
     """Splines of degree n are C^(n-1) (Sec. II): value, gradient and Laplacian agree on both
     sides of a non-uniform knot; the Cartesian gradient and Laplacian are the derivatives of
     the value (non-orthogonal cell)."""
@@ -159,23 +160,56 @@ def test_graded_cubic_is_C2_across_knots_and_chain_rule():
     ainv = np.linalg.inv(NONORTHO)
     s0 = np.array([knots[0][3], 0.41, 0.77])
     eps = 1e-9
-    lo = oracle.general_eval(beta, NONORTHO, (s0 - [eps, 0, 0]) @ NONORTHO.T, 3, knots)
-    hi = oracle.general_eval(beta, NONORTHO, (s0 + [eps, 0, 0]) @ NONORTHO.T, 3, knots)
+    lo = oracle.general_eval(beta, NONORTHO, (s0 - [eps, 0, 0]) @ NONORTHO.T, degree, knots)
+    hi = oracle.general_eval(beta, NONORTHO, (s0 + [eps, 0, 0]) @ NONORTHO.T, degree, knots)
     for a, b in zip(lo, hi):
         assert np.abs(a - b).max() < 1e-5 * max(1.0, np.abs(a).max())
     pos = inputs.positions(NONORTHO, 6, 55)
-    v, g, l = oracle.general_eval(beta, NONORTHO, pos, 3, knots)
+    v, g, l = oracle.general_eval(beta, NONORTHO, pos, degree, knots)
     h = 1e-5
     fd_g, fd_l = np.zeros_like(g), np.zeros_like(l)
     for a in range(3):
         e = np.zeros(3)
         e[a] = h
-        vp, gp, _ = oracle.general_eval(beta, NONORTHO, pos + e, 3, knots)
-        vm, gm, _ = oracle.general_eval(beta, NONORTHO, pos - e, 3, knots)
+        vp, gp, _ = oracle.general_eval(beta, NONORTHO, pos + e, degree, knots)
+        vm, gm, _ = oracle.general_eval(beta, NONORTHO, pos - e, degree, knots)
         fd_g[:, a] = (vp - vm) / (2 * h)
         fd_l += (gp[:, a] - gm[:, a]) / (2 * h)
     assert oracle.relative_error(g, fd_g) < 1e-7
     assert oracle.relative_error(l, fd_l) < 1e-5
+
+
+def test_degree_one_graded_is_piecewise_linear_interpolation():
+    """Degree 1 on a graded grid: the coefficients are the grid values (the collocation matrix
+    is the identity) and the spline is trilinear interpolation between neighbouring grid
+    points with weights (x - x_i) / (x_{i+1} - x_i) per axis."""
+    dims = (5, 6, 7)
+    knots = tuple(inputs.graded_knots(d, 0.5, 0.2 * a) for a, d in enumerate(dims))
+    lat, mil, coef = inputs.random_cell(56, dims, 2, 3.0, 4.0, np.diag([5.0, 6.0, 7.0]))
+    beta, _ = oracle.general_interp_tables(lat, mil, coef, dims, 1, knots)
+    grid = oracle.general_grid_values(lat, mil, coef, [np.asarray(k) for k in knots])
+    np.testing.assert_allclose(beta, grid, atol=1e-12 * np.abs(grid).max())
+    rng = np.random.default_rng(57)
+    s = rng.uniform(0, 1, (10, 3))
+    v, _, _ = oracle.general_eval(beta, lat, s @ lat.T, 1, knots)
+    for p in range(10):
+        i0, t = [], []
+        for a in range(3):
+            k = np.asarray(knots[a])
+            x = s[p, a]
+            i = int(np.searchsorted(k, x, side="right")) - 1
+            if i < 0:                               # below the first point: last interval
+                i, x = dims[a] - 1, x + 1.0
+            right = k[i + 1] if i + 1 < dims[a] else k[0] + 1.0
+            i0.append(i)
+            t.append((x - k[i]) / (right - k[i]))
+        ref = 0.0
+        for dx in (0, 1):
+            for dy in (0, 1):
+                for dz in (0, 1):
+                    w = (t[0] if dx else 1 - t[0]) * (t[1] if dy else 1 - t[1]) * (t[2] if dz else 1 - t[2])
+                    ref = ref + w * beta[(i0[0] + dx) % dims[0], (i0[1] + dy) % dims[1], (i0[2] + dz) % dims[2]]
+        np.testing.assert_allclose(v[p], ref, atol=1e-13 * max(1.0, np.abs(ref).max()))
 
 
 # ---------------------------------------------------------------------------

@@ -1,5 +1,6 @@
-"""GPU interpolating B-splines of degree 1, 5, 7 on uniform grids and cubic ones on graded
-(non-uniform) grids (qmcspl_create_grid) against the oracle's recurrence-based definition."""
+"""GPU interpolating B-splines of degree 1, 5, 7 on uniform grids and of degree 1, 3, 5, 7 on
+graded (non-uniform) grids (qmcspl_create_grid) against the oracle's recurrence-based
+definition."""
 import numpy as np
 import pytest
 
@@ -18,7 +19,7 @@ def graded(dims):
 
 
 CASES = ([(deg, False, st, sep) for deg in (1, 5, 7) for st in ("f64", "f32", "bf16") for sep in (False, True)] +
-         [(3, True, st, sep) for st in ("f64", "f32", "bf16") for sep in (False, True)])
+         [(deg, True, st, sep) for deg in (1, 3, 5, 7) for st in ("f64", "f32", "bf16") for sep in (False, True)])
 
 
 @pytest.mark.parametrize("degree,nonuni,storage,sep", CASES)
@@ -80,7 +81,7 @@ def test_general_orders_noalloc_checkpoint_and_rejections(tmp_path):
     from paper_1309_6250_gb300.api import OrbitalSplines, eval_batched
     dims = (14, 14, 14)
     lat, mil, coef = inputs.random_cell(1430, dims, 12, 6.0, 5.0, NONORTHO)
-    for kw in (dict(degree=5), dict(knots=graded(dims))):
+    for kw in (dict(degree=5), dict(knots=graded(dims)), dict(degree=7, knots=graded(dims))):
         spl = splines(lat, dims, mil, coef, method="interp", storage="f32", separate_lap=False, **kw)
         pos = torch.from_numpy(inputs.positions(lat, 10000, 1431, -1, 2)).to(dev())
         spl.set_order("input")
@@ -117,7 +118,8 @@ def test_general_orders_noalloc_checkpoint_and_rejections(tmp_path):
     assert ei.value.code == _lib.ERR_ARG
 
 
-@pytest.mark.parametrize("degree,nonuni", [(1, False), (5, False), (7, False), (3, True)])
+@pytest.mark.parametrize("degree,nonuni", [(1, False), (5, False), (7, False), (1, True), (3, True), (5, True),
+                                           (7, True)])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_general_with_position_records_matches_oracle(degree, nonuni, storage):
     """From 8192 positions on, a per-position pass precomputes the cell and local coordinate
