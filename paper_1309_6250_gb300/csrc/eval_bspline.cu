@@ -497,26 +497,35 @@ __device__ __forceinline__ void warp_task(const EvalArgs& p, long long w0, int l
     else bspline_warp_task_x2<T, LAPTAB>(p, w0, lane);
 }
 
-#ifndef QMCSPL_EVAL_MINBLOCKS
-#define QMCSPL_EVAL_MINBLOCKS 1
-#endif
 #ifndef QMCSPL_EVAL_THREADS
 #define QMCSPL_EVAL_THREADS 512
 #endif
-// Threads per block of the B-spline evaluation kernels.  With cell-ordered positions the
-// 16 warps of one 512-thread block evaluate 16 consecutive (neighbouring) positions on one
-// SM, so their shared stencil rows hit in that SM's L1; two 256-thread blocks on an SM
-// work on positions far apart in the order.  128 registers x 512 threads fill the SM.
-constexpr int kBspThreads = QMCSPL_EVAL_THREADS;
+#ifndef QMCSPL_EVAL_THREADS_F32_LAP
+#define QMCSPL_EVAL_THREADS_F32_LAP 640
+#endif
+// Threads per block of the B-spline evaluation kernels (one block per SM).  With cell-ordered
+// positions the warps of one block evaluate consecutive (neighbouring) positions on one SM, so
+// their shared stencil rows hit in that SM's L1; two smaller blocks on an SM would work on
+// positions far apart in the order.  512 threads x 128 registers fill the register file; the
+// single-cell FP32 kernel with the Laplacian table fits in 96 registers (16 bytes spilled) and
+// runs 20 warps (640 threads), which hides more of the L1/L2 latency (1.205 vs 1.262 ms on the
+// 128-orbital step; 576, 672 and 768 threads were slower).  The batched kernel keeps 512.
+template <typename T, bool LAPTAB> struct BspBlock {
+    static constexpr int threads = QMCSPL_EVAL_THREADS;
+};
+template <> struct BspBlock<float, true> {
+    static constexpr int threads = QMCSPL_EVAL_THREADS_F32_LAP;
+};
 
 template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(kBspThreads, QMCSPL_EVAL_MINBLOCKS) bspline_vgl_kernel(const EvalArgs p)
+__global__ void __launch_bounds__(BspBlock<T, LAPTAB>::threads, 1) bspline_vgl_kernel(const EvalArgs p)
 {
+    constexpr int WPB = BspBlock<T, LAPTAB>::threads / 32;
     const int lane = threadIdx.x & 31;
     const int gpw = 32 >> p.lanes_log2;
     const long long total = p.n_pos * p.tiles;
-    const long long warp = (long long)blockIdx.x * (kBspThreads / 32) + (threadIdx.x >> 5);
-    const long long wstride = (long long)gridDim.x * (kBspThreads / 32);
+    const long long warp = (long long)blockIdx.x * WPB + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * WPB;
     for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw)
         warp_task<T, LAPTAB>(p, w0, lane);
 }
@@ -531,11 +540,12 @@ struct BatchArgs {
 static_assert(sizeof(BatchArgs) <= 32000, "batched kernel parameters exceed the 32 KB limit");
 
 template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(kBspThreads, QMCSPL_EVAL_MINBLOCKS) bspline_vgl_batched_kernel(const __grid_constant__ BatchArgs b)
+__global__ void __launch_bounds__(QMCSPL_EVAL_THREADS, 1) bspline_vgl_batched_kernel(const __grid_constant__ BatchArgs b)
 {
+    constexpr int WPB = QMCSPL_EVAL_THREADS / 32;
     const int lane = threadIdx.x & 31;
-    const long long warp = (long long)blockIdx.x * (kBspThreads / 32) + (threadIdx.x >> 5);
-    const long long wstride = (long long)gridDim.x * (kBspThreads / 32);
+    const long long warp = (long long)blockIdx.x * WPB + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * WPB;
     const long long total = b.start[b.n_cells];
     int c = 0;
     for (long long w = warp; w < total; w += wstride) {
@@ -547,11 +557,11 @@ __global__ void __launch_bounds__(kBspThreads, QMCSPL_EVAL_MINBLOCKS) bspline_vg
 }
 
 template <typename K>
-long long grid_for(K kernel, long long warps)
+long long grid_for(K kernel, int threads, long long warps)
 {
-    long long blocks = (warps + kBspThreads / 32 - 1) / (kBspThreads / 32);
+    long long blocks = (warps + threads / 32 - 1) / (threads / 32);
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBspThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess)
         per_sm = 1;
     if (per_sm < 1) per_sm = 1;
     const long long cap = (long long)sm_count() * per_sm;
@@ -564,16 +574,18 @@ int launch_typed(const EvalArgs& a, cudaStream_t st)
 {
     const int gpw = 32 >> a.lanes_log2;
     const long long warps = (a.n_pos * a.tiles + gpw - 1) / gpw;
-    const long long blocks = grid_for(bspline_vgl_kernel<T, LAPTAB>, warps);
-    bspline_vgl_kernel<T, LAPTAB><<<(unsigned)blocks, kBspThreads, 0, st>>>(a);
+    constexpr int threads = BspBlock<T, LAPTAB>::threads;
+    const long long blocks = grid_for(bspline_vgl_kernel<T, LAPTAB>, threads, warps);
+    bspline_vgl_kernel<T, LAPTAB><<<(unsigned)blocks, threads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "bspline_vgl_kernel launch");
 }
 
 template <typename T, bool LAPTAB>
 int launch_batched_typed(const BatchArgs& b, cudaStream_t st)
 {
-    const long long blocks = grid_for(bspline_vgl_batched_kernel<T, LAPTAB>, b.start[b.n_cells]);
-    bspline_vgl_batched_kernel<T, LAPTAB><<<(unsigned)blocks, kBspThreads, 0, st>>>(b);
+    constexpr int threads = QMCSPL_EVAL_THREADS;
+    const long long blocks = grid_for(bspline_vgl_batched_kernel<T, LAPTAB>, threads, b.start[b.n_cells]);
+    bspline_vgl_batched_kernel<T, LAPTAB><<<(unsigned)blocks, threads, 0, st>>>(b);
     return cuda_error(cudaGetLastError(), "bspline_vgl_batched_kernel launch");
 }
 
