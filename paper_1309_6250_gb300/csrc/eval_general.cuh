@@ -73,8 +73,12 @@ __device__ __forceinline__ void axis_weights(const EvalArgs& p, int axis, int i0
     }
 }
 
+// Two blocks per SM (at most 128 registers) for the stencils of degree 3 and up: their weight
+// arrays would otherwise take up to 255 registers and leave 8 warps per SM (degree 7: 0.184 ->
+// 0.160 ms, graded cubic 0.062 -> 0.056 ms on the Si-like 16-orbital step; three blocks spill
+// too much).
 template <typename T, int DEG, bool NONUNI, bool LAPTAB>
-__global__ void __launch_bounds__(kEvalThreads, 1) general_vgl_kernel(const EvalArgs p)
+__global__ void __launch_bounds__(kEvalThreads, DEG == 1 ? 1 : 2) general_vgl_kernel(const EvalArgs p)
 {
     using A = typename Traits<T>::A;
     constexpr int E = Traits<T>::E;
