@@ -507,20 +507,23 @@ __device__ __forceinline__ void warp_task(const EvalArgs& p, long long w0, int l
 // positions the warps of one block evaluate consecutive (neighbouring) positions on one SM, so
 // their shared stencil rows hit in that SM's L1; two smaller blocks on an SM would work on
 // positions far apart in the order.  512 threads x 128 registers fill the register file; the
-// single-cell FP32 kernel with the Laplacian table fits in 96 registers (16 bytes spilled) and
-// runs 20 warps (640 threads), which hides more of the L1/L2 latency (1.205 vs 1.262 ms on the
-// 128-orbital step; 576, 672 and 768 threads were slower).  The batched kernel keeps 512.
+// single-cell FP32 kernel with the Laplacian table also comes in a 640-thread shape that fits in
+// 96 registers (16 bytes spilled) and runs 20 warps, which hides more of the L1/L2 latency on
+// large launches (1.205 vs 1.262 ms on the 128-orbital step; 576, 672 and 768 threads were
+// slower).  Launches of only a few rounds of warp tasks keep 512 threads: their last, partly
+// filled round costs more with the bigger block.  The batched kernel keeps 512.
 template <typename T, bool LAPTAB> struct BspBlock {
-    static constexpr int threads = QMCSPL_EVAL_THREADS;
+    static constexpr int large = QMCSPL_EVAL_THREADS;   // threads of the shape for large launches
 };
 template <> struct BspBlock<float, true> {
-    static constexpr int threads = QMCSPL_EVAL_THREADS_F32_LAP;
+    static constexpr int large = QMCSPL_EVAL_THREADS_F32_LAP;
 };
+constexpr int kLargeLaunchRounds = 4;   // warp-task rounds from which the large shape is used
 
-template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(BspBlock<T, LAPTAB>::threads, 1) bspline_vgl_kernel(const EvalArgs p)
+template <typename T, bool LAPTAB, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) bspline_vgl_kernel(const EvalArgs p)
 {
-    constexpr int WPB = BspBlock<T, LAPTAB>::threads / 32;
+    constexpr int WPB = THREADS / 32;
     const int lane = threadIdx.x & 31;
     const int gpw = 32 >> p.lanes_log2;
     const long long total = p.n_pos * p.tiles;
@@ -569,15 +572,25 @@ long long grid_for(K kernel, int threads, long long warps)
     return blocks < 1 ? 1 : blocks;
 }
 
+template <typename T, bool LAPTAB, int THREADS>
+int launch_shape(const EvalArgs& a, long long warps, cudaStream_t st)
+{
+    const long long blocks = grid_for(bspline_vgl_kernel<T, LAPTAB, THREADS>, THREADS, warps);
+    bspline_vgl_kernel<T, LAPTAB, THREADS><<<(unsigned)blocks, THREADS, 0, st>>>(a);
+    return cuda_error(cudaGetLastError(), "bspline_vgl_kernel launch");
+}
+
 template <typename T, bool LAPTAB>
 int launch_typed(const EvalArgs& a, cudaStream_t st)
 {
     const int gpw = 32 >> a.lanes_log2;
     const long long warps = (a.n_pos * a.tiles + gpw - 1) / gpw;
-    constexpr int threads = BspBlock<T, LAPTAB>::threads;
-    const long long blocks = grid_for(bspline_vgl_kernel<T, LAPTAB>, threads, warps);
-    bspline_vgl_kernel<T, LAPTAB><<<(unsigned)blocks, threads, 0, st>>>(a);
-    return cuda_error(cudaGetLastError(), "bspline_vgl_kernel launch");
+    constexpr int large = BspBlock<T, LAPTAB>::large;
+    if constexpr (large != QMCSPL_EVAL_THREADS) {
+        if (warps >= (long long)kLargeLaunchRounds * sm_count() * (large / 32))
+            return launch_shape<T, LAPTAB, large>(a, warps, st);
+    }
+    return launch_shape<T, LAPTAB, QMCSPL_EVAL_THREADS>(a, warps, st);
 }
 
 template <typename T, bool LAPTAB>
