@@ -161,49 +161,120 @@ __global__ void __launch_bounds__(kEvalThreads, DEG == 1 ? 1 : 2) general_vgl_ke
         // rows zz = z + H: the W rows of the stencil start at zz = iz
         const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
         A v[E], gx[E], gy[E], gz[E], lp[E];
+        if constexpr (sizeof(A) == 4) {
+            // float and bfloat16 tables: the same sums on packed FP32 pairs (fma.rn.f32x2, two
+            // orbitals per instruction, the same rounding per element as the scalar path)
+            constexpr int NP = Pairs<T>::N;
+            f32x2 V[NP], GX[NP], GY[NP], GZ[NP], LP[NP];
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = gx[e] = gy[e] = gz[e] = lp[e] = A(0);
+            for (int j = 0; j < NP; ++j) V[j] = GX[j] = GY[j] = GZ[j] = LP[j] = 0ull;
+            f32x2 wz2[W], dwz2[W], d2wz2[W];
 #pragma unroll
-        for (int l = 0; l < W; ++l) {
+            for (int k = 0; k < W; ++k) {
+                wz2[k] = pack2(wz[k], wz[k]);
+                dwz2[k] = pack2(dwz[k], dwz[k]);
+                if (!LAPTAB) d2wz2[k] = pack2(d2wz[k], d2wz[k]);
+            }
 #pragma unroll
-            for (int m = 0; m < W; ++m) {
-                const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb + off;
-                const char* c0 = static_cast<const char*>(p.tab[0]) + col;
-                A a0[E], a1[E], a2[E], al[E];
+            for (int l = 0; l < W; ++l) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) a0[e] = a1[e] = a2[e] = al[e] = A(0);
+                for (int m = 0; m < W; ++m) {
+                    const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb + off;
+                    const char* c0 = static_cast<const char*>(p.tab[0]) + col;
+                    f32x2 A0[NP], A1[NP], A2[NP], AL[NP];
 #pragma unroll
-                for (int k = 0; k < W; ++k) {
-                    A c[E];
-                    unpack<T>(ldg_table(p, c0 + k * rowb), c);
+                    for (int j = 0; j < NP; ++j) A0[j] = A1[j] = A2[j] = AL[j] = 0ull;
 #pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        a0[e] = fma(wz[k], c[e], a0[e]);
-                        a1[e] = fma(dwz[k], c[e], a1[e]);
-                        if (!LAPTAB) a2[e] = fma(d2wz[k], c[e], a2[e]);
+                    for (int k = 0; k < W; ++k) {
+                        f32x2 cv[NP];
+                        Pairs<T>::get(ldg_table(p, c0 + k * rowb), cv);
+#pragma unroll
+                        for (int j = 0; j < NP; ++j) {
+                            A0[j] = ffma2(wz2[k], cv[j], A0[j]);
+                            A1[j] = ffma2(dwz2[k], cv[j], A1[j]);
+                            if (!LAPTAB) A2[j] = ffma2(d2wz2[k], cv[j], A2[j]);
+                        }
+                        if (LAPTAB) {
+                            Pairs<T>::get(ldg_table(p, static_cast<const char*>(p.tab[1]) + col + k * rowb), cv);
+#pragma unroll
+                            for (int j = 0; j < NP; ++j) AL[j] = ffma2(wz2[k], cv[j], AL[j]);
+                        }
+                    }
+                    const A w00 = wx[l] * wy[m], w10 = dwx[l] * wy[m], w01 = wx[l] * dwy[m];
+                    const f32x2 W00 = pack2(w00, w00), W10 = pack2(w10, w10), W01 = pack2(w01, w01);
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        V[j] = ffma2(W00, A0[j], V[j]);
+                        GX[j] = ffma2(W10, A0[j], GX[j]);
+                        GY[j] = ffma2(W01, A0[j], GY[j]);
+                        GZ[j] = ffma2(W00, A1[j], GZ[j]);
                     }
                     if (LAPTAB) {
-                        A cl[E];
-                        unpack<T>(ldg_table(p, static_cast<const char*>(p.tab[1]) + col + k * rowb), cl);
 #pragma unroll
-                        for (int e = 0; e < E; ++e) al[e] = fma(wz[k], cl[e], al[e]);
+                        for (int j = 0; j < NP; ++j) LP[j] = ffma2(W00, AL[j], LP[j]);
+                    } else {
+                        const A c0w = mlv[0] * (d2wx[l] * wy[m]) + mlv[1] * (wx[l] * d2wy[m]) + mlv[3] * (dwx[l] * dwy[m]);
+                        const A c1w = mlv[4] * w10 + mlv[5] * w01;
+                        const A c2w = mlv[2] * w00;
+                        const f32x2 C0 = pack2(c0w, c0w), C1 = pack2(c1w, c1w), C2 = pack2(c2w, c2w);
+#pragma unroll
+                        for (int j = 0; j < NP; ++j) LP[j] = ffma2(C0, A0[j], ffma2(C1, A1[j], ffma2(C2, A2[j], LP[j])));
                     }
                 }
-                const A w00 = wx[l] * wy[m], w10 = dwx[l] * wy[m], w01 = wx[l] * dwy[m];
-                A c0w = 0, c1w = 0, c2w = 0;
-                if (!LAPTAB) {
-                    c0w = mlv[0] * (d2wx[l] * wy[m]) + mlv[1] * (wx[l] * d2wy[m]) + mlv[3] * (dwx[l] * dwy[m]);
-                    c1w = mlv[4] * w10 + mlv[5] * w01;
-                    c2w = mlv[2] * w00;
-                }
+            }
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    v[e] = fma(w00, a0[e], v[e]);
-                    gx[e] = fma(w10, a0[e], gx[e]);
-                    gy[e] = fma(w01, a0[e], gy[e]);
-                    gz[e] = fma(w00, a1[e], gz[e]);
-                    if (LAPTAB) lp[e] = fma(w00, al[e], lp[e]);
-                    else lp[e] = fma(c0w, a0[e], fma(c1w, a1[e], fma(c2w, a2[e], lp[e])));
+            for (int j = 0; j < NP; ++j) {
+                unpack2(V[j], v[2 * j], v[2 * j + 1]);
+                unpack2(GX[j], gx[2 * j], gx[2 * j + 1]);
+                unpack2(GY[j], gy[2 * j], gy[2 * j + 1]);
+                unpack2(GZ[j], gz[2 * j], gz[2 * j + 1]);
+                unpack2(LP[j], lp[2 * j], lp[2 * j + 1]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) v[e] = gx[e] = gy[e] = gz[e] = lp[e] = A(0);
+#pragma unroll
+            for (int l = 0; l < W; ++l) {
+#pragma unroll
+                for (int m = 0; m < W; ++m) {
+                    const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb + off;
+                    const char* c0 = static_cast<const char*>(p.tab[0]) + col;
+                    A a0[E], a1[E], a2[E], al[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) a0[e] = a1[e] = a2[e] = al[e] = A(0);
+#pragma unroll
+                    for (int k = 0; k < W; ++k) {
+                        A c[E];
+                        unpack<T>(ldg_table(p, c0 + k * rowb), c);
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            a0[e] = fma(wz[k], c[e], a0[e]);
+                            a1[e] = fma(dwz[k], c[e], a1[e]);
+                            if (!LAPTAB) a2[e] = fma(d2wz[k], c[e], a2[e]);
+                        }
+                        if (LAPTAB) {
+                            A cl[E];
+                            unpack<T>(ldg_table(p, static_cast<const char*>(p.tab[1]) + col + k * rowb), cl);
+#pragma unroll
+                            for (int e = 0; e < E; ++e) al[e] = fma(wz[k], cl[e], al[e]);
+                        }
+                    }
+                    const A w00 = wx[l] * wy[m], w10 = dwx[l] * wy[m], w01 = wx[l] * dwy[m];
+                    A c0w = 0, c1w = 0, c2w = 0;
+                    if (!LAPTAB) {
+                        c0w = mlv[0] * (d2wx[l] * wy[m]) + mlv[1] * (wx[l] * d2wy[m]) + mlv[3] * (dwx[l] * dwy[m]);
+                        c1w = mlv[4] * w10 + mlv[5] * w01;
+                        c2w = mlv[2] * w00;
+                    }
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        v[e] = fma(w00, a0[e], v[e]);
+                        gx[e] = fma(w10, a0[e], gx[e]);
+                        gy[e] = fma(w01, a0[e], gy[e]);
+                        gz[e] = fma(w00, a1[e], gz[e]);
+                        if (LAPTAB) lp[e] = fma(w00, al[e], lp[e]);
+                        else lp[e] = fma(c0w, a0[e], fma(c1w, a1[e], fma(c2w, a2[e], lp[e])));
+                    }
                 }
             }
         }
