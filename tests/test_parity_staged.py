@@ -186,3 +186,15 @@ def test_stalled_pipeline_times_out_and_recovers():
     for a, b in zip(again, ref):
         assert torch.equal(a, b)
     spl.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_staged_full_size_bit_identical(storage):
+    """The MgO-like 128-orbital workload at full size (96^3, 2,048 x 256 positions): 221,184
+    pencil bins, two z segments per pencil; pencil order gives exactly the cell-order outputs."""
+    w = inputs.make_workload("c3")
+    spl = splines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage=storage,
+                  separate_lap=True)
+    assert spl.info()["staged"] == 1
+    assert_identical(both_orders(spl, torch.from_numpy(w.pos).to(dev())))
+    spl.close()
