@@ -258,8 +258,12 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
  *   dpos      device double[n_pos][3], WRITTEN with dL/dr.  NULL skips it.
  * The coefficient adjoint scatters into 64 stencil rows per position with atomic
  * adds, so its summation order (and last bits) vary from run to run.
- * QMCSPL_ERR_UNSUPPORTED for Lagrange, pp, double-float, Bloch and separate-gradient
- * handles.
+ * Bloch handles (complex outputs z): gv, gg, gl hold g = dL/dRe z + i dL/dIm z in the
+ * complex output layouts ([P][O][2], [P][3][O][2], [P][O][2]); dcoef and dcoef_lap are the
+ * gradients of the stored tables of Re u and Im u, canonical layout [Nx][Ny][Nz][O][2]; dpos
+ * includes the derivative of the phase exp(i k.r).
+ * QMCSPL_ERR_UNSUPPORTED for Lagrange, pp, double-float, separate-gradient handles and
+ * B-splines of another degree or on a non-uniform grid.
  */
 int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, const void* gv,
                              const void* gg, const void* gl, void* dcoef, void* dcoef_lap,

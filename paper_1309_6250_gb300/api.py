@@ -214,11 +214,14 @@ class OrbitalSplines:
     def backward(self, pos: torch.Tensor, gv=None, gg=None, gl=None, dcoef=None, dcoef_lap=None,
                  want_dpos: bool = True, stream=None):
         """Adjoint of eval_vgl: accumulates dL/dbeta into dcoef (and dcoef_lap) and
-        returns dL/dr [P, 3] (float64) when want_dpos."""
+        returns dL/dr [P, 3] (float64) when want_dpos.  For Bloch handles the upstream
+        gradients are complex (dL/dRe z + i dL/dIm z, the convention of torch.autograd) and
+        dcoef has coef_shape()."""
         pos = self._check_pos(pos)
         n = pos.shape[0]
         dpos = torch.empty((n, 3), dtype=torch.float64, device=self.device) if want_dpos else None
-        c = lambda t: None if t is None else t.contiguous()
+        # complex upstream gradients (Bloch handles) may carry a lazy conjugation bit
+        c = lambda t: None if t is None else (t.resolve_conj() if t.is_complex() else t).contiguous()
         gv, gg, gl = c(gv), c(gg), c(gl)
         with torch.cuda.device(self.device):
             _lib.check(self.lib.qmcspl_eval_vgl_backward(
@@ -227,7 +230,9 @@ class OrbitalSplines:
         return dpos
 
     def coef_shape(self) -> Tuple[int, int, int, int]:
-        return self.dims + (self.n_orb,)
+        """Shape of a coefficient gradient: [Nx, Ny, Nz, stored functions] (for Bloch handles
+        the stored functions are Re u and Im u of each orbital, adjacent)."""
+        return self.dims + (self.n_fun,)
 
 
 def eval_batched(splines: Sequence[OrbitalSplines], positions: Sequence[torch.Tensor],

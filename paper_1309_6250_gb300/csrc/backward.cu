@@ -15,6 +15,17 @@
 // where d(lap)/dt_i needs the third derivatives of the spline (Hessian-derived
 // Laplacian) or the gradient of the Laplacian table.  The stencil weights are
 // recomputed here, not stored by the forward pass.
+//
+// Bloch orbitals (Sec. II): the outputs are complex, z = e w with e = exp(i k.r) and w the
+// bracket of bloch_apply (u; grad u + i k u; lap u + 2 i k.grad u - |k|^2 u, or the
+// Laplacian table's value).  With upstream g = dL/dRe z + i dL/dIm z (complex, the layout of
+// the outputs), the upstream of the bracket is h = conj(e) g, and transposing the bracket gives
+// the upstream of the tabulated u (its real part for the Re u table, its imaginary part for Im u):
+//   u:       h_val - i k.h_grad - |k|^2 h_lap      (the last term with the Hessian Laplacian)
+//   grad u:  h_grad - 2 i k h_lap                  (the last term with the Hessian Laplacian)
+//   lap u:   h_lap
+// after which the real adjoint above applies unchanged.  The position adjoint gains the
+// derivative of the phase, d e / d r = i k e:  dL/dr += -k sum_z Im(conj(h_z) w_z).
 #include "eval_common.cuh"
 
 namespace qmcspl {
@@ -29,6 +40,7 @@ struct BwdArgs {
     void* dcoef_lap;
     double* dpos;             // [P][3], zeroed before the launch, accumulated
     int vec_atomic;           // dcoef rows allow 16-byte vector atomics
+    int bloch;                // complex Bloch outputs: pairs (Re u, Im u) of stored functions (selects the kernel)
 };
 
 template <typename A>
@@ -53,7 +65,7 @@ __device__ __forceinline__ void atomic_run(A* dst, const A* v, int o0, int n_orb
         if (o0 + j < n_orb) atomicAdd(dst + j, v[j]);
 }
 
-template <typename T, bool LAPTAB>
+template <typename T, bool LAPTAB, bool BLOCH>
 __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs b)
 {
     using A = typename Traits<T>::A;
@@ -93,6 +105,7 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
         const int o0 = chunk * E;
         // upstream weights of my orbitals (zero for inactive lanes and padding)
         A wv[E], wl[E], gt[3][E];
+        A hv[E], hl[E], hg[3][E];   // Bloch: upstream of the bracket (phase term of dL/dr)
         {
             A wg[3][E];
             const A* gvp = static_cast<const A*>(b.gv);
@@ -103,6 +116,54 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
             load_run<A>(use && glp ? glp + ip * n_orb + o0 : nullptr, wl, o0, n_orb, E);
             for (int a = 0; a < 3; ++a)
                 load_run<A>(use && ggp ? ggp + (ip * 3 + a) * n_orb + o0 : nullptr, wg[a], o0, n_orb, E);
+            if constexpr (BLOCH) {
+                // upstream of the bracket, h = conj(e) g, kept for the phase term of dL/dr;
+                // then the upstream of the tabulated u (see the header)
+                const double* rr = p.pos + 3 * ip;
+                const double uk = __fma_rn(p.kred[0], rr[0], __fma_rn(p.kred[1], rr[1], __dmul_rn(p.kred[2], rr[2])));
+                double sn, cs;
+                sincospi(2.0 * (uk - rint(uk)), &sn, &cs);
+                const A c = (A)cs, sph = (A)sn;
+                const A ka[3] = {(A)p.kc[0], (A)p.kc[1], (A)p.kc[2]};
+                const A kk = ka[0] * ka[0] + ka[1] * ka[1] + ka[2] * ka[2];
+                auto rot = [&](A& x, A& y) {   // (x + i y) <- conj(e) (x + i y)
+                    const A xr = c * x + sph * y, yi = c * y - sph * x;
+                    x = xr;
+                    y = yi;
+                };
+#pragma unroll
+                for (int j = 0; j < E / 2; ++j) {
+                    const int r = 2 * j, q = 2 * j + 1;
+                    rot(wv[r], wv[q]);
+                    rot(wl[r], wl[q]);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) rot(wg[a][r], wg[a][q]);
+                    hv[r] = wv[r];
+                    hv[q] = wv[q];
+                    hl[r] = wl[r];
+                    hl[q] = wl[q];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        hg[a][r] = wg[a][r];
+                        hg[a][q] = wg[a][q];
+                    }
+                    // -i k.h_grad = (k.Im h_grad, -k.Re h_grad)
+                    const A khr = ka[0] * wg[0][r] + ka[1] * wg[1][r] + ka[2] * wg[2][r];
+                    const A khi = ka[0] * wg[0][q] + ka[1] * wg[1][q] + ka[2] * wg[2][q];
+                    wv[r] += khi;
+                    wv[q] -= khr;
+                    if (!LAPTAB) {
+                        wv[r] -= kk * hl[r];
+                        wv[q] -= kk * hl[q];
+                        // -2 i k_a h_lap = (2 k_a Im h_lap, -2 k_a Re h_lap)
+#pragma unroll
+                        for (int a = 0; a < 3; ++a) {
+                            wg[a][r] += A(2) * ka[a] * hl[q];
+                            wg[a][q] -= A(2) * ka[a] * hl[r];
+                        }
+                    }
+                }
+            }
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -153,10 +214,12 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
         if (b.dpos) {
             // reduced derivatives of my orbitals: gradient, Hessian, gradient of the Laplacian
             A g1[3][E], h2[6][E], d3[3][E];
+            A u0[E], lam[E];   // Bloch: value of u and of the Laplacian table, for the phase term
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 for (int i = 0; i < 3; ++i) g1[i][e] = d3[i][e] = A(0);
                 for (int i = 0; i < 6; ++i) h2[i][e] = A(0);
+                u0[e] = lam[e] = A(0);
             }
             const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
             const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb
@@ -199,6 +262,13 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
                     const A z1 = ml0 * d2bx * by + ml1 * bx * d2by + ml3 * dbx * dby;
                     const A z2 = ml4 * dbx * by + ml5 * bx * dby;
                     const A z3 = ml2 * bx * by;
+                    if constexpr (BLOCH) {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            u0[e] += bx * by * a[0][e];
+                            if (LAPTAB) lam[e] += bx * by * al[0][e];
+                        }
+                    }
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
                         g1[0][e] += dbx * by * a[0][e];
@@ -231,14 +301,55 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
                 u[1] += (double)(wv[e] * g1[1][e] + hxy * gt[0][e] + hyy * gt[1][e] + hyz * gt[2][e] + wl[e] * d3[1][e]);
                 u[2] += (double)(wv[e] * g1[2][e] + hxz * gt[0][e] + hyz * gt[1][e] + hzz * gt[2][e] + wl[e] * d3[2][e]);
             }
+            // Bloch: the phase term, sum over outputs z of Im(conj(h_z) w_z) with the bracket w
+            double sph = 0.0;
+            if constexpr (BLOCH) {
+                const A ka[3] = {(A)p.kc[0], (A)p.kc[1], (A)p.kc[2]};
+                const A kk = ka[0] * ka[0] + ka[1] * ka[1] + ka[2] * ka[2];
+                auto imc = [](A hr, A hi, A wr, A wi) { return hr * wi - hi * wr; };   // Im(conj(h) w)
+#pragma unroll
+                for (int j = 0; j < E / 2; ++j) {
+                    const int r = 2 * j, q = 2 * j + 1;
+                    A gc[3][2];   // Cartesian gradient of Re u, Im u
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        gc[a][0] = (A)p.mg[3 * a] * g1[0][r] + (A)p.mg[3 * a + 1] * g1[1][r] + (A)p.mg[3 * a + 2] * g1[2][r];
+                        gc[a][1] = (A)p.mg[3 * a] * g1[0][q] + (A)p.mg[3 * a + 1] * g1[1][q] + (A)p.mg[3 * a + 2] * g1[2][q];
+                    }
+                    const A ur = u0[r], ui = u0[q];
+                    A acc = imc(hv[r], hv[q], ur, ui);
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        acc += imc(hg[a][r], hg[a][q], gc[a][0] - ka[a] * ui, gc[a][1] + ka[a] * ur);
+                    A lr, li;
+                    if (LAPTAB) {
+                        lr = lam[r];
+                        li = lam[q];
+                    } else {
+                        const A hl_r = ml0 * h2[0][r] + ml1 * h2[1][r] + ml2 * h2[2][r] + ml3 * h2[3][r] +
+                                       ml4 * h2[4][r] + ml5 * h2[5][r];
+                        const A hl_i = ml0 * h2[0][q] + ml1 * h2[1][q] + ml2 * h2[2][q] + ml3 * h2[3][q] +
+                                       ml4 * h2[4][q] + ml5 * h2[5][q];
+                        const A kgr = ka[0] * gc[0][0] + ka[1] * gc[1][0] + ka[2] * gc[2][0];
+                        const A kgi = ka[0] * gc[0][1] + ka[1] * gc[1][1] + ka[2] * gc[2][1];
+                        lr = hl_r - A(2) * kgi - kk * ur;
+                        li = hl_i + A(2) * kgr - kk * ui;
+                    }
+                    acc += imc(hl[r], hl[q], lr, li);
+                    sph += (double)acc;
+                }
+            }
             // sum over the lanes of the group (all lanes of the warp take part)
-            for (int off = L >> 1; off > 0; off >>= 1)
+            for (int off = L >> 1; off > 0; off >>= 1) {
 #pragma unroll
                 for (int i = 0; i < 3; ++i) u[i] += __shfl_xor_sync(kFullMask, u[i], off);
+                sph += __shfl_xor_sync(kFullMask, sph, off);
+            }
             if (active && sub == 0) {
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    const double d = p.mg[3 * a] * u[0] + p.mg[3 * a + 1] * u[1] + p.mg[3 * a + 2] * u[2];
+                    const double d = p.mg[3 * a] * u[0] + p.mg[3 * a + 1] * u[1] + p.mg[3 * a + 2] * u[2] -
+                                     p.kc[a] * sph;
                     atomicAdd(b.dpos + 3 * ip + a, d);
                 }
             }
@@ -246,23 +357,29 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
     }
 }
 
-template <typename T, bool LAPTAB>
-int launch_typed(const BwdArgs& a, cudaStream_t st)
+template <typename T, bool LAPTAB, bool BLOCH>
+int launch_one(const BwdArgs& a, cudaStream_t st)
 {
     const int gpw = 32 >> a.e.lanes_log2;
     const long long groups = a.e.n_pos * a.e.tiles;
     const long long warps = (groups + gpw - 1) / gpw;
     long long blocks = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bspline_bwd_kernel<T, LAPTAB>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bspline_bwd_kernel<T, LAPTAB, BLOCH>,
                                                                   kEvalThreads, 0);
     if (e != cudaSuccess) return cuda_error(e, "occupancy query");
     if (per_sm < 1) per_sm = 1;
     const long long cap = (long long)sm_count() * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    bspline_bwd_kernel<T, LAPTAB><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
+    bspline_bwd_kernel<T, LAPTAB, BLOCH><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "bspline_bwd_kernel launch");
+}
+
+template <typename T, bool LAPTAB>
+int launch_typed(const BwdArgs& a, cudaStream_t st)
+{
+    return a.bloch ? launch_one<T, LAPTAB, true>(a, st) : launch_one<T, LAPTAB, false>(a, st);
 }
 
 }  // namespace
@@ -281,6 +398,7 @@ int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
     a.dcoef = dcoef;
     a.dcoef_lap = dcoef_lap;
     a.dpos = dpos;
+    a.bloch = h->bloch;
     const size_t ob = (h->storage == QMCSPL_F64) ? 8 : 4;
     const uintptr_t al = (uintptr_t)dcoef | (uintptr_t)dcoef_lap;
     a.vec_atomic = ((h->n_orb * ob) % 16 == 0) && (al % 16 == 0);

@@ -110,6 +110,7 @@ void fill_eval_args(const Handle* h, EvalArgs* a)
     for (int i = 0; i < 3; ++i) {
         a->kc[i] = h->kcart[i];
         a->kcf[i] = (float)h->kcart[i];
+        a->kred[i] = h->kred[i];
         a->knots[i] = h->nonuniform ? h->d_knots + (size_t)i * kMaxDim : nullptr;
     }
     a->cdeg = degree_constant(h->degree);
@@ -662,7 +663,6 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is implemented for B-spline handles");
     if (h->storage == QMCSPL_DF64)
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for double-float tables");
-    if (h->bloch) return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for Bloch orbitals");
     if (h->separate_grad)
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for separate gradient tables");
     if (is_general(h))

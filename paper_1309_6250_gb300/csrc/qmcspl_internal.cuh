@@ -80,6 +80,7 @@ struct EvalArgs {
     const double2* phase;     // null: real orbitals
     double kc[3];             // Cartesian k (1/bohr)
     float kcf[3];
+    double kred[3];           // a^-T kpoint: k.r = 2 pi (kred . r)
     // general B-splines (degree other than 3, or non-uniform grids)
     const double* knots[3];   // per-axis grid points in [0, 1) (non-uniform grids), else null
     double cdeg;              // degree-0 constant C of the recurrence

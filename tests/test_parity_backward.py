@@ -156,3 +156,94 @@ def test_backward_rejects_variants():
         with pytest.raises(_lib.QmcsplError) as ei:
             splines(lat, dims, mil, coef, method=method, storage="df64")
         assert ei.value.code == _lib.ERR_UNSUPPORTED
+
+
+# ---------------------------------------------------------------------------
+# Bloch orbitals (complex outputs z = exp(i k.r) w): the adjoint of the bracket and of the phase
+# ---------------------------------------------------------------------------
+
+def complex_upstream(n, n_orb, seed):
+    gv, gg, gl = inputs.upstream_weights(n, 2 * n_orb, seed)
+    c = lambda a: a[..., 0::2] + 1j * a[..., 1::2]
+    return c(gv), c(gg), c(gl)
+
+
+def bloch_loss(z, g):
+    """L = sum Re(conj(g) z) = sum (Re g Re z + Im g Im z): g is dL/dRe z + i dL/dIm z."""
+    return float(sum(np.sum((np.conj(gi) * zi).real) for gi, zi in zip(g, z)))
+
+
+def gpu_backward_complex(spl, pos, g):
+    sep = bool(spl.info()["separate_lap"])
+    cd = torch.complex128 if spl.out_dtype == torch.float64 else torch.complex64
+    dc = torch.zeros(spl.coef_shape(), dtype=spl.out_dtype, device=dev())
+    dcl = torch.zeros_like(dc) if sep else None
+    dpos = spl.backward(t(pos, torch.float64), *(t(x, cd) for x in g), dcoef=dc, dcoef_lap=dcl)
+    spl.sync()
+    return dc.double().cpu().numpy(), None if dcl is None else dcl.double().cpu().numpy(), \
+        dpos.cpu().numpy()
+
+
+@pytest.mark.parametrize("storage,tol_lin,tol_fd", [("f64", 1e-11, 1e-6), ("f32", 2e-5, 3e-3)])
+@pytest.mark.parametrize("sep", [False, True])
+def test_bloch_backward_linearity_and_position_fd(storage, tol_lin, tol_fd, sep):
+    """L is linear in the stored tables: sum(dL/dbeta * beta') = L(beta') for random tables
+    beta' evaluated by the oracle (Bloch forward: spline of u, then the phase and the product
+    rule); dL/dr against central differences of the oracle forward on the handle's own tables
+    (h = 1e-4 bohr, positions away from grid planes)."""
+    k = inputs.KPOINTS["generic"]
+    dims = (10, 11, 12)
+    n_orb = 3
+    lat, mil, coef = inputs.random_bloch_cell(1700, n_orb, 5.0, 4.0, k, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=sep, kpoint=k)
+    pos = inputs.positions(lat, 120, 1701, -1, 2)
+    pos = pos[away_from_planes(lat, dims, pos, 0.02)]
+    n = pos.shape[0]
+    g = complex_upstream(n, n_orb, 1702)
+    if storage == "f32":
+        g = tuple((x.real.astype(np.float32) + 1j * x.imag.astype(np.float32)).astype(np.complex128) for x in g)
+    dc, dcl, dpos = gpu_backward_complex(spl, pos, g)
+    rng = np.random.default_rng(1703)
+    for _ in range(2):
+        b1 = rng.standard_normal(dims + (2 * n_orb,))
+        b2 = rng.standard_normal(dims + (2 * n_orb,)) if sep else None
+        z = oracle.bloch_eval("smooth", b1, lat, k, pos, tables_lap=b2)
+        lin = np.sum(dc * b1) + (np.sum(dcl * b2) if sep else 0.0)
+        ref = bloch_loss(z, g)
+        assert abs(lin - ref) <= tol_lin * max(1.0, abs(ref)), (lin, ref)
+    beta = spl.get_table(0)
+    blap = spl.get_table(1) if sep else None
+    h = 1e-4
+    fd = np.zeros_like(dpos)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        lp = []
+        for sgn in (1, -1):
+            z = oracle.bloch_eval("smooth", beta, lat, k, pos + sgn * e, tables_lap=blap)
+            lp.append(sum(np.sum((np.conj(gi) * zi).real.reshape(n, -1), axis=1) for gi, zi in zip(g, z)))
+        fd[:, a] = (lp[0] - lp[1]) / (2 * h)
+    assert oracle.relative_error(dpos, fd) < tol_fd
+
+
+def test_bloch_autograd_matches_the_direct_adjoint():
+    """Complex outputs through torch.autograd: the gradient torch passes back for a real loss is
+    dL/dRe z + i dL/dIm z, so positions and coefficients get exactly the direct adjoint."""
+    from paper_1309_6250_gb300.autograd import evaluate
+    k = inputs.KPOINTS["X"]
+    dims = (10, 10, 12)
+    lat, mil, coef = inputs.random_bloch_cell(1710, 4, 5.0, 4.0, k, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="smooth", storage="f64", separate_lap=True, kpoint=k)
+    beta, beta_lap = spl.coefficient_parameters()
+    assert tuple(beta.shape) == spl.coef_shape() == dims + (8,)
+    pos_np = inputs.positions(lat, 64, 1711)
+    pos = t(pos_np, torch.float64).requires_grad_(True)
+    g = complex_upstream(64, 4, 1712)
+    v, gr, l = evaluate(spl, pos, beta, beta_lap)
+    assert v.dtype == torch.complex128
+    loss = sum((torch.conj(t(gi, torch.complex128)) * zi).real.sum() for gi, zi in zip(g, (v, gr, l)))
+    loss.backward()
+    dc, dcl, dpos = gpu_backward_complex(spl, pos_np, g)
+    assert oracle.relative_error(pos.grad.cpu().numpy(), dpos) < 1e-13
+    assert oracle.relative_error(beta.grad.cpu().numpy(), dc) < 1e-13
+    assert oracle.relative_error(beta_lap.grad.cpu().numpy(), dcl) < 1e-13

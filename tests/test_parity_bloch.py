@@ -153,9 +153,6 @@ def test_bloch_rejections_and_checkpoint(tmp_path):
     lat, mil, coef = inputs.random_bloch_cell(950, 3, 5.0, 4.0, KGEN, np.eye(3) * 6.0)
     spl = splines(lat, dims, mil, coef, method="smooth", storage="f64", separate_lap=False, kpoint=KGEN)
     pos = t(inputs.positions(lat, 64, 951, -1, 2))
-    with pytest.raises(_lib.QmcsplError) as ei:
-        spl.backward(pos)
-    assert ei.value.code == _lib.ERR_UNSUPPORTED
     lib = _lib.load()
     out = spl.alloc_outputs(64)
     rc = lib.qmcspl_eval_vgl_noalloc(spl.handle, pos.data_ptr(), 64, out[0].data_ptr(),
