@@ -245,7 +245,7 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
                          void* grad_host, void* lap_host, void* stream);
 
 /*
- * qmcspl_eval_vgl_backward -- adjoint of qmcspl_eval_vgl for the B-spline methods.
+ * qmcspl_eval_vgl_backward -- adjoint of qmcspl_eval_vgl for the B-spline and Lagrange methods.
  *
  * Not in the paper: for a scalar loss L with upstream gradients gv = dL/dval,
  * gg = dL/dgrad, gl = dL/dlap (same layouts and dtype as the outputs; any may be NULL
@@ -262,8 +262,11 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
  * complex output layouts ([P][O][2], [P][3][O][2], [P][O][2]); dcoef and dcoef_lap are the
  * gradients of the stored tables of Re u and Im u, canonical layout [Nx][Ny][Nz][O][2]; dpos
  * includes the derivative of the phase exp(i k.r).
- * QMCSPL_ERR_UNSUPPORTED for Lagrange, pp, double-float, separate-gradient handles and
- * B-splines of another degree or on a non-uniform grid.
+ * Five-table handles (Lagrange, and B-splines with separate_grad): the outputs are the values
+ * of the tables phi, d_x phi, d_y phi, d_z phi, lap phi with one set of weights, so dcoef is
+ * [5][Nx][Ny][Nz][O] (those tables in that order, canonical layout) and dcoef_lap must be NULL.
+ * QMCSPL_ERR_UNSUPPORTED for pp, double-float tables and B-splines of another degree or on a
+ * non-uniform grid.
  */
 int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, const void* gv,
                              const void* gg, const void* gl, void* dcoef, void* dcoef_lap,

@@ -15,6 +15,7 @@ from __future__ import annotations
 
 from typing import Optional
 
+import numpy as np
 import torch
 
 from .api import OrbitalSplines
@@ -34,10 +35,13 @@ class SplineOrbitalFunction(torch.autograd.Function):
         (pos,) = ctx.saved_tensors
         need_pos = ctx.needs_input_grad[0]
         need_coef = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
-        sep = bool(spl.info()["separate_lap"])
+        inf = spl.info()
+        five = inf["n_tables"] == 5   # Lagrange, B-splines with separate gradient tables
+        sep = bool(inf["separate_lap"]) and not five
         dcoef = dcoef_lap = None
         if need_coef:
-            dcoef = torch.zeros(spl.coef_shape(), dtype=spl.out_dtype, device=spl.device)
+            shape = ((5,) if five else ()) + spl.coef_shape()
+            dcoef = torch.zeros(shape, dtype=spl.out_dtype, device=spl.device)
             if sep:
                 dcoef_lap = torch.zeros_like(dcoef)
         dpos = None
@@ -49,8 +53,13 @@ class SplineOrbitalFunction(torch.autograd.Function):
 
 def coefficient_parameters(spl: OrbitalSplines):
     """Leaf tensors (requires_grad) holding the handle's coefficient tables in canonical
-    layout [Nx, Ny, Nz, O], in the output dtype: (beta, beta_lap or None)."""
+    layout [Nx, Ny, Nz, O], in the output dtype: (beta, beta_lap or None).  Five-table
+    handles (Lagrange, B-splines with separate gradient tables) give all five tables as one
+    [5, Nx, Ny, Nz, O] tensor and None."""
     inf = spl.info()
+    if inf["n_tables"] == 5:
+        t = torch.from_numpy(np.stack([spl.get_table(i) for i in range(5)]))
+        return t.to(device=spl.device, dtype=spl.out_dtype).requires_grad_(True), None
     out = []
     for idx in range(2):
         if idx == 1 and not inf["separate_lap"]:

@@ -382,6 +382,210 @@ int launch_typed(const BwdArgs& a, cudaStream_t st)
     return a.bloch ? launch_one<T, LAPTAB, true>(a, st) : launch_one<T, LAPTAB, false>(a, st);
 }
 
+// ---- five tables (Lagrange; B-splines with separate gradient tables) ----
+// The outputs are the values of five interpolants with one set of weights W = w_l w_m w_n
+// (tables phi, d_x phi, d_y phi, d_z phi, lap phi, Sec. III C), so the adjoint of table t is
+// dbeta_t += g_t W with g_t its output's upstream (value, the Cartesian gradient components,
+// Laplacian), and dL/dr = N (a^-1)^T sum_t g_t grad_t(value of table t).  Bloch handles take
+// the upstream through the phase first (h_t = conj(e) g_t; the tables hold the periodic parts
+// of phi and of its derivatives) and add -k sum_t Im(conj(h_t) w_t) to dL/dr.
+enum BwdFiveBasis : int { kBwdLagrange = 0, kBwdBSpline = 1 };
+
+template <int BASIS, typename A>
+__device__ __forceinline__ void five_weights(A t, A* w, A* dw)
+{
+    if constexpr (BASIS == kBwdLagrange) {   // Eq. (lagrangebasis) and its derivative
+        const A tm1 = t - A(1), tm2 = t - A(2), tp1 = t + A(1);
+        w[0] = A(-1.0 / 6.0) * t * tm1 * tm2;
+        w[1] = A(0.5) * tp1 * tm1 * tm2;
+        w[2] = A(-0.5) * tp1 * t * tm2;
+        w[3] = A(1.0 / 6.0) * tp1 * t * tm1;
+        const A t2 = t * t;
+        dw[0] = A(-1.0 / 6.0) * (A(3) * t2 - A(6) * t + A(2));
+        dw[1] = A(0.5) * (A(3) * t2 - A(4) * t - A(1));
+        dw[2] = A(-0.5) * (A(3) * t2 - A(2) * t - A(2));
+        dw[3] = A(1.0 / 6.0) * (A(3) * t2 - A(1));
+    } else {
+        bspline_weights<A>(t, w, dw, nullptr);
+    }
+}
+
+template <typename T, int BASIS, bool BLOCH>
+__global__ void __launch_bounds__(kEvalThreads) five_table_bwd_kernel(const BwdArgs b)
+{
+    using A = typename Traits<T>::A;
+    constexpr int E = Traits<T>::E;
+    const EvalArgs& p = b.e;
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << p.lanes_log2;
+    const int sub = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const int gpw = 32 >> p.lanes_log2;
+    const long long total = p.n_pos * p.tiles;
+    const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
+    const size_t rowb = (size_t)p.row_stride * sizeof(T);
+    const size_t colb = (size_t)p.col_stride * sizeof(T);
+    const int n_orb = p.n_orb;
+    const size_t canon = (size_t)p.nx * p.ny * p.nz * n_orb;   // one canonical table
+
+    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
+        const long long gid = w0 + (lane >> p.lanes_log2);
+        const bool active = gid < total;
+        const long long ip = active ? gid / p.tiles : 0;
+        const int tile = active ? (int)(gid - ip * p.tiles) : 0;
+        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+        int ix, iy, iz;
+        double tx, ty, tz;
+        bool ok;
+        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+        if (active && !ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+        A w[3][4], dw[3][4];
+        five_weights<BASIS, A>((A)tx, w[0], dw[0]);
+        five_weights<BASIS, A>((A)ty, w[1], dw[1]);
+        five_weights<BASIS, A>((A)tz, w[2], dw[2]);
+        const int chunk = tile * L + sub;
+        const int o0 = chunk * E;
+        const bool use = active && o0 < n_orb;
+        // upstream of the five tables: value, Cartesian gradient components, Laplacian
+        A up[5][E];
+        {
+            const A* gvp = static_cast<const A*>(b.gv);
+            const A* ggp = static_cast<const A*>(b.gg);
+            const A* glp = static_cast<const A*>(b.gl);
+            load_run<A>(use && gvp ? gvp + ip * n_orb + o0 : nullptr, up[0], o0, n_orb, E);
+            for (int a = 0; a < 3; ++a)
+                load_run<A>(use && ggp ? ggp + (ip * 3 + a) * n_orb + o0 : nullptr, up[1 + a], o0, n_orb, E);
+            load_run<A>(use && glp ? glp + ip * n_orb + o0 : nullptr, up[4], o0, n_orb, E);
+        }
+        if constexpr (BLOCH) {
+            const double uk = __fma_rn(p.kred[0], r[0], __fma_rn(p.kred[1], r[1], __dmul_rn(p.kred[2], r[2])));
+            double sn, cs;
+            sincospi(2.0 * (uk - rint(uk)), &sn, &cs);
+            const A c = (A)cs, sp = (A)sn;
+#pragma unroll
+            for (int t = 0; t < 5; ++t)
+#pragma unroll
+                for (int j = 0; j < E / 2; ++j) {
+                    const A x = up[t][2 * j], y = up[t][2 * j + 1];
+                    up[t][2 * j] = c * x + sp * y;
+                    up[t][2 * j + 1] = c * y - sp * x;
+                }
+        }
+        int xs[4], ys[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            xs[j] = wrap1(ix + j - 1, p.nx);
+            ys[j] = wrap1(iy + j - 1, p.ny);
+        }
+
+        // ---- coefficient adjoint: scatter into 64 stencil rows of each table ----
+        if (b.dcoef && use) {
+            A* dc = static_cast<A*>(b.dcoef);
+            const bool vec = b.vec_atomic != 0;
+            for (int l = 0; l < 4; ++l)
+                for (int m = 0; m < 4; ++m)
+                    for (int n = 0; n < 4; ++n) {
+                        const int z = wrap1(iz + n - 1, p.nz);
+                        const A B = w[0][l] * w[1][m] * w[2][n];
+                        const size_t row = (((size_t)xs[l] * p.ny + ys[m]) * p.nz + z) * n_orb + o0;
+#pragma unroll
+                        for (int t = 0; t < 5; ++t) {
+                            A v[E];
+#pragma unroll
+                            for (int e = 0; e < E; ++e) v[e] = up[t][e] * B;
+                            atomic_run<A, E>(dc + t * canon + row, v, o0, n_orb, vec);
+                        }
+                    }
+        }
+
+        // ---- position adjoint ----
+        if (b.dpos) {
+            double u[3] = {0.0, 0.0, 0.0};
+            double sph = 0.0;
+            const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
+            for (int l = 0; l < 4; ++l)
+                for (int m = 0; m < 4; ++m) {
+                    const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb + off;
+                    const A wdx = dw[0][l] * w[1][m], wdy = w[0][l] * dw[1][m], wxy = w[0][l] * w[1][m];
+                    // sa = sum over tables and orbitals of upstream x (z-contracted value), sd the
+                    // same with the z-derivative weights; sv the Bloch phase sum
+                    A sa = 0, sd = 0, sv = 0;
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) {
+                        const char* base = static_cast<const char*>(p.tab[t]) + col;
+                        A a[E], ad[E];
+#pragma unroll
+                        for (int e = 0; e < E; ++e) a[e] = ad[e] = A(0);
+#pragma unroll
+                        for (int n = 0; n < 4; ++n) {
+                            A cvals[E];
+                            unpack<T>(ldg_table(p, base + n * rowb), cvals);
+#pragma unroll
+                            for (int e = 0; e < E; ++e) {
+                                a[e] = fma(w[2][n], cvals[e], a[e]);
+                                ad[e] = fma(dw[2][n], cvals[e], ad[e]);
+                            }
+                        }
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            sa += up[t][e] * a[e];
+                            sd += up[t][e] * ad[e];
+                        }
+                        if constexpr (BLOCH) {
+#pragma unroll
+                            for (int j = 0; j < E / 2; ++j)   // Im(conj(h) a)
+                                sv += up[t][2 * j] * a[2 * j + 1] - up[t][2 * j + 1] * a[2 * j];
+                        }
+                    }
+                    u[0] += (double)(wdx * sa);
+                    u[1] += (double)(wdy * sa);
+                    u[2] += (double)(wxy * sd);
+                    if constexpr (BLOCH) sph += (double)(wxy * sv);
+                }
+            for (int o = L >> 1; o > 0; o >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) u[i] += __shfl_xor_sync(kFullMask, u[i], o);
+                sph += __shfl_xor_sync(kFullMask, sph, o);
+            }
+            if (active && sub == 0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const double d = p.mg[3 * a] * u[0] + p.mg[3 * a + 1] * u[1] + p.mg[3 * a + 2] * u[2] -
+                                     (BLOCH ? p.kc[a] * sph : 0.0);
+                    atomicAdd(b.dpos + 3 * ip + a, d);
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int BASIS, bool BLOCH>
+int launch_five(const BwdArgs& a, cudaStream_t st)
+{
+    const int gpw = 32 >> a.e.lanes_log2;
+    const long long warps = (a.e.n_pos * a.e.tiles + gpw - 1) / gpw;
+    long long blocks = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, five_table_bwd_kernel<T, BASIS, BLOCH>,
+                                                                  kEvalThreads, 0);
+    if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+    if (per_sm < 1) per_sm = 1;
+    const long long cap = (long long)sm_count() * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    five_table_bwd_kernel<T, BASIS, BLOCH><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
+    return cuda_error(cudaGetLastError(), "five_table_bwd_kernel launch");
+}
+
+template <typename T>
+int launch_five_typed(const BwdArgs& a, bool lagrange, cudaStream_t st)
+{
+    if (lagrange)
+        return a.bloch ? launch_five<T, kBwdLagrange, true>(a, st) : launch_five<T, kBwdLagrange, false>(a, st);
+    return a.bloch ? launch_five<T, kBwdBSpline, true>(a, st) : launch_five<T, kBwdBSpline, false>(a, st);
+}
+
 }  // namespace
 
 int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos, const void* gv,
@@ -407,6 +611,14 @@ int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
         if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(dpos)");
     }
     if (!dcoef && !dpos) return QMCSPL_OK;
+    if (h->n_tables == 5) {   // Lagrange, or B-splines with separate gradient tables
+        const bool lag = h->method == QMCSPL_LAGRANGE;
+        switch (h->storage) {
+        case QMCSPL_F64: return launch_five_typed<double>(a, lag, st);
+        case QMCSPL_F32: return launch_five_typed<float>(a, lag, st);
+        default: return launch_five_typed<__nv_bfloat16>(a, lag, st);
+        }
+    }
     const bool lt = h->separate_lap != 0;
     switch (h->storage) {
     case QMCSPL_F64: return lt ? launch_typed<double, true>(a, st) : launch_typed<double, false>(a, st);

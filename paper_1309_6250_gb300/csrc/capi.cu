@@ -659,18 +659,18 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
 {
     g_err.clear();
     if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
-    if (h->method != QMCSPL_BSPLINE_SMOOTH && h->method != QMCSPL_BSPLINE_INTERP)
-        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is implemented for B-spline handles");
+    if (h->method == QMCSPL_PPSPLINE)
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for pp-splines");
     if (h->storage == QMCSPL_DF64)
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for double-float tables");
-    if (h->separate_grad)
-        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for separate gradient tables");
     if (is_general(h))
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is implemented for cubic B-splines on uniform grids");
     if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
-    if (dcoef_lap && !(h->separate_lap && dcoef))
-        return set_error(QMCSPL_ERR_ARG, "dcoef_lap needs a separate-Laplacian handle and dcoef");
-    if (dcoef && h->separate_lap && !dcoef_lap)
+    const bool five = h->n_tables == 5;   // dcoef holds all five tables
+    if (dcoef_lap && (five || !(h->separate_lap && dcoef)))
+        return set_error(QMCSPL_ERR_ARG, five ? "five-table handle: dcoef holds all tables, dcoef_lap must be NULL"
+                                              : "dcoef_lap needs a separate-Laplacian handle and dcoef");
+    if (dcoef && !five && h->separate_lap && !dcoef_lap)
         return set_error(QMCSPL_ERR_ARG, "separate-Laplacian handle: dcoef_lap is required with dcoef");
     if (n_pos == 0) return QMCSPL_OK;
     if (!pos) return set_error(QMCSPL_ERR_ARG, "pos is NULL");

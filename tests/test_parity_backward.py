@@ -143,7 +143,7 @@ def test_backward_rejects_variants():
     from paper_1309_6250_gb300 import _lib
     dims = (8, 8, 8)
     lat, mil, coef = inputs.random_cell(5, dims, 2, 5.0, 4.0, np.eye(3) * 6.0)
-    spl = splines(lat, dims, mil, coef, method="lagrange", storage="f64")
+    spl = splines(lat, dims, mil, coef, method="pp", storage="f64")
     pos = torch.zeros((4, 3), dtype=torch.float64, device=dev())
     with pytest.raises(_lib.QmcsplError) as ei:
         spl.backward(pos)
@@ -247,3 +247,109 @@ def test_bloch_autograd_matches_the_direct_adjoint():
     assert oracle.relative_error(pos.grad.cpu().numpy(), dpos) < 1e-13
     assert oracle.relative_error(beta.grad.cpu().numpy(), dc) < 1e-13
     assert oracle.relative_error(beta_lap.grad.cpu().numpy(), dcl) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# five tables (Lagrange; B-splines with separate gradient tables): dcoef holds all five
+# ---------------------------------------------------------------------------
+
+FIVE = [dict(method="lagrange", separate_lap=True),
+        dict(method="smooth", separate_lap=True, separate_grad=True),
+        dict(method="interp", separate_lap=True, separate_grad=True)]
+
+
+def five_forward(method, tabs, lat, pos, k=None):
+    if k is not None:
+        return oracle.bloch_eval(method, tabs, lat, k, pos)
+    if method == "lagrange":
+        return oracle.lagrange_eval(tabs, lat, pos)
+    return oracle.bspline_eval_separate(tabs, lat, pos)
+
+
+@pytest.mark.parametrize("kw", FIVE, ids=["lagrange", "smooth_sepgrad", "interp_sepgrad"])
+@pytest.mark.parametrize("storage,tol_lin,tol_fd", [("f64", 1e-11, 1e-6), ("f32", 2e-5, 3e-3)])
+@pytest.mark.parametrize("bloch", [False, True])
+def test_five_table_backward_linearity_and_position_fd(kw, storage, tol_lin, tol_fd, bloch):
+    """The outputs are the values of five interpolants, linear in the five tables: the
+    coefficient adjoint by sum(dL/dbeta * beta') = L(beta') with the oracle on random tables,
+    the position adjoint against central differences of the oracle forward (positions away
+    from grid planes, where the Lagrange interpolant's derivatives jump)."""
+    dims = (10, 11, 12)
+    n_orb = 3
+    k = inputs.KPOINTS["generic"] if bloch else None
+    if bloch:
+        lat, mil, coef = inputs.random_bloch_cell(1800, n_orb, 5.0, 4.0, k, NONORTHO)
+        spl = splines(lat, dims, mil, coef, storage=storage, kpoint=k, **kw)
+    else:
+        lat, mil, coef = inputs.random_cell(1800, dims, n_orb, 5.0, 4.0, NONORTHO)
+        spl = splines(lat, dims, mil, coef, storage=storage, **kw)
+    assert spl.info()["n_tables"] == 5
+    nf = spl.coef_shape()[-1]
+    pos = inputs.positions(lat, 120, 1801, -1, 2)
+    pos = pos[away_from_planes(lat, dims, pos, 0.02)]
+    n = pos.shape[0]
+    if bloch:
+        g = complex_upstream(n, n_orb, 1802)
+        cd = torch.complex128 if storage == "f64" else torch.complex64
+    else:
+        g = inputs.upstream_weights(n, n_orb, 1802)
+        cd = spl.out_dtype
+    if storage == "f32":
+        r32 = lambda x: (x.real.astype(np.float32) + 1j * x.imag.astype(np.float32)) if bloch else \
+            x.astype(np.float32).astype(np.float64)
+        g = tuple(r32(x) for x in g)
+    dc = torch.zeros((5,) + spl.coef_shape(), dtype=spl.out_dtype, device=dev())
+    dpos = spl.backward(t(pos, torch.float64), *(t(x, cd) for x in g), dcoef=dc)
+    spl.sync()
+    dc, dpos = dc.double().cpu().numpy(), dpos.cpu().numpy()
+    loss = (lambda z: bloch_loss(z, g)) if bloch else \
+        (lambda z: float(sum(np.sum(gi * zi) for gi, zi in zip(g, z))))
+    rng = np.random.default_rng(1803)
+    for _ in range(2):
+        b5 = rng.standard_normal((5,) + dims + (nf,))
+        ref = loss(five_forward(kw["method"], b5, lat, pos, k))
+        lin = np.sum(dc * b5)
+        assert abs(lin - ref) <= tol_lin * max(1.0, abs(ref)), (lin, ref)
+    tabs = np.stack([spl.get_table(i) for i in range(5)])
+    h = 1e-4
+    fd = np.zeros_like(dpos)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        lp = []
+        for sgn in (1, -1):
+            z = five_forward(kw["method"], tabs, lat, pos + sgn * e, k)
+            if bloch:
+                lp.append(sum(np.sum((np.conj(gi) * zi).real.reshape(n, -1), axis=1) for gi, zi in zip(g, z)))
+            else:
+                lp.append(sum(np.sum((gi * zi).reshape(n, -1), axis=1) for gi, zi in zip(g, z)))
+        fd[:, a] = (lp[0] - lp[1]) / (2 * h)
+    assert oracle.relative_error(dpos, fd) < tol_fd
+    spl.close()
+
+
+def test_five_table_autograd_and_argument_checks():
+    from paper_1309_6250_gb300 import _lib
+    from paper_1309_6250_gb300.autograd import evaluate
+    dims = (10, 10, 12)
+    lat, mil, coef = inputs.random_cell(1810, dims, 4, 5.0, 4.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="lagrange", storage="f64", separate_lap=True)
+    beta, none = spl.coefficient_parameters()
+    assert none is None and tuple(beta.shape) == (5,) + spl.coef_shape()
+    pos_np = inputs.positions(lat, 64, 1811)
+    pos = t(pos_np, torch.float64).requires_grad_(True)
+    gv, gg, gl = inputs.upstream_weights(64, 4, 1812)
+    v, g, l = evaluate(spl, pos, beta)
+    loss = (v * t(gv, torch.float64)).sum() + (g * t(gg, torch.float64)).sum() + \
+        (l * t(gl, torch.float64)).sum()
+    loss.backward()
+    dc = torch.zeros((5,) + spl.coef_shape(), dtype=torch.float64, device=dev())
+    dpos = spl.backward(t(pos_np, torch.float64), t(gv, torch.float64), t(gg, torch.float64),
+                        t(gl, torch.float64), dcoef=dc)
+    spl.sync()
+    assert oracle.relative_error(pos.grad.cpu().numpy(), dpos.cpu().numpy()) < 1e-13
+    assert oracle.relative_error(beta.grad.cpu().numpy(), dc.cpu().numpy()) < 1e-13
+    # all five tables go to dcoef: a separate dcoef_lap is refused
+    with pytest.raises(_lib.QmcsplError) as ei:
+        spl.backward(t(pos_np, torch.float64), t(gv, torch.float64), dcoef=dc, dcoef_lap=torch.zeros_like(dc))
+    assert ei.value.code == _lib.ERR_ARG

@@ -86,9 +86,6 @@ def test_separate_gradient_orders_noalloc_checkpoint_and_rejections(tmp_path):
     torch.cuda.synchronize()
     assert all(torch.equal(a, b) for a, b in zip(out, ref))
     with pytest.raises(_lib.QmcsplError) as ei:
-        spl.backward(pos)
-    assert ei.value.code == _lib.ERR_UNSUPPORTED
-    with pytest.raises(_lib.QmcsplError) as ei:
         eval_batched([spl], [pos])
     assert ei.value.code == _lib.ERR_UNSUPPORTED
     back.close()
