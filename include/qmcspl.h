@@ -245,7 +245,7 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
                          void* grad_host, void* lap_host, void* stream);
 
 /*
- * qmcspl_eval_vgl_backward -- adjoint of qmcspl_eval_vgl for the B-spline and Lagrange methods.
+ * qmcspl_eval_vgl_backward -- adjoint of qmcspl_eval_vgl (every method; cubic, uniform grids).
  *
  * Not in the paper: for a scalar loss L with upstream gradients gv = dL/dval,
  * gg = dL/dgrad, gl = dL/dlap (same layouts and dtype as the outputs; any may be NULL
@@ -265,7 +265,9 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
  * Five-table handles (Lagrange, and B-splines with separate_grad): the outputs are the values
  * of the tables phi, d_x phi, d_y phi, d_z phi, lap phi with one set of weights, so dcoef is
  * [5][Nx][Ny][Nz][O] (those tables in that order, canonical layout) and dcoef_lap must be NULL.
- * QMCSPL_ERR_UNSUPPORTED for pp, double-float tables and B-splines of another degree or on a
+ * pp handles: dcoef is [8][Nx][Ny][Nz][O], sigma^{kappa mu nu} at index 4(kappa-1) + 2(mu-1) +
+ * (nu-1) as in qmcspl_get_table; dcoef_lap must be NULL.
+ * QMCSPL_ERR_UNSUPPORTED for double-float tables and B-splines of another degree or on a
  * non-uniform grid.
  */
 int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, const void* gv,

@@ -36,11 +36,12 @@ class SplineOrbitalFunction(torch.autograd.Function):
         need_pos = ctx.needs_input_grad[0]
         need_coef = ctx.needs_input_grad[1] or ctx.needs_input_grad[2]
         inf = spl.info()
-        five = inf["n_tables"] == 5   # Lagrange, B-splines with separate gradient tables
-        sep = bool(inf["separate_lap"]) and not five
+        # Lagrange and B-splines with separate gradient tables: five tables; pp: eight entries
+        n_multi = 5 if inf["n_tables"] == 5 else (8 if inf["entries_per_point"] == 8 else 0)
+        sep = bool(inf["separate_lap"]) and not n_multi
         dcoef = dcoef_lap = None
         if need_coef:
-            shape = ((5,) if five else ()) + spl.coef_shape()
+            shape = ((n_multi,) if n_multi else ()) + spl.coef_shape()
             dcoef = torch.zeros(shape, dtype=spl.out_dtype, device=spl.device)
             if sep:
                 dcoef_lap = torch.zeros_like(dcoef)
@@ -55,10 +56,11 @@ def coefficient_parameters(spl: OrbitalSplines):
     """Leaf tensors (requires_grad) holding the handle's coefficient tables in canonical
     layout [Nx, Ny, Nz, O], in the output dtype: (beta, beta_lap or None).  Five-table
     handles (Lagrange, B-splines with separate gradient tables) give all five tables as one
-    [5, Nx, Ny, Nz, O] tensor and None."""
+    [5, Nx, Ny, Nz, O] tensor and None, pp handles their eight entries as [8, Nx, Ny, Nz, O]."""
     inf = spl.info()
-    if inf["n_tables"] == 5:
-        t = torch.from_numpy(np.stack([spl.get_table(i) for i in range(5)]))
+    n_multi = 5 if inf["n_tables"] == 5 else (8 if inf["entries_per_point"] == 8 else 0)
+    if n_multi:
+        t = torch.from_numpy(np.stack([spl.get_table(i) for i in range(n_multi)]))
         return t.to(device=spl.device, dtype=spl.out_dtype).requires_grad_(True), None
     out = []
     for idx in range(2):

@@ -65,6 +65,107 @@ __device__ __forceinline__ void atomic_run(A* dst, const A* v, int o0, int n_orb
         if (o0 + j < n_orb) atomicAdd(dst + j, v[j]);
 }
 
+// ---- Bloch handles: the upstream through the phase and the bracket, and the phase term ----
+// (see the header).  Per lane: E stored functions = E/2 complex orbitals (Re, Im adjacent).
+
+// In: g (complex upstream of the outputs) in wv, wg (Cartesian), wl.  Out: h = conj(e) g in
+// hv, hg, hl; the upstream of the tabulated u in wv, wg, wl.
+template <typename A, int E, bool LAPTAB>
+__device__ __forceinline__ void bloch_upstream(const EvalArgs& p, const double* rr, A* wv, A (*wg)[E], A* wl,
+                                               A* hv, A (*hg)[E], A* hl)
+{
+    const double uk = __fma_rn(p.kred[0], rr[0], __fma_rn(p.kred[1], rr[1], __dmul_rn(p.kred[2], rr[2])));
+    double sn, cs;
+    sincospi(2.0 * (uk - rint(uk)), &sn, &cs);
+    const A c = (A)cs, sph = (A)sn;
+    const A ka[3] = {(A)p.kc[0], (A)p.kc[1], (A)p.kc[2]};
+    const A kk = ka[0] * ka[0] + ka[1] * ka[1] + ka[2] * ka[2];
+    auto rot = [&](A& x, A& y) {   // (x + i y) <- conj(e) (x + i y)
+        const A xr = c * x + sph * y, yi = c * y - sph * x;
+        x = xr;
+        y = yi;
+    };
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) {
+        const int r = 2 * j, q = 2 * j + 1;
+        rot(wv[r], wv[q]);
+        rot(wl[r], wl[q]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) rot(wg[a][r], wg[a][q]);
+        hv[r] = wv[r];
+        hv[q] = wv[q];
+        hl[r] = wl[r];
+        hl[q] = wl[q];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            hg[a][r] = wg[a][r];
+            hg[a][q] = wg[a][q];
+        }
+        // -i k.h_grad = (k.Im h_grad, -k.Re h_grad)
+        const A khr = ka[0] * wg[0][r] + ka[1] * wg[1][r] + ka[2] * wg[2][r];
+        const A khi = ka[0] * wg[0][q] + ka[1] * wg[1][q] + ka[2] * wg[2][q];
+        wv[r] += khi;
+        wv[q] -= khr;
+        if (!LAPTAB) {
+            wv[r] -= kk * hl[r];
+            wv[q] -= kk * hl[q];
+            // -2 i k_a h_lap = (2 k_a Im h_lap, -2 k_a Re h_lap)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                wg[a][r] += A(2) * ka[a] * hl[q];
+                wg[a][q] -= A(2) * ka[a] * hl[r];
+            }
+        }
+    }
+}
+
+// sum over the lane's complex orbitals and the outputs z of Im(conj(h_z) w_z), the bracket w
+// rebuilt from the value u0, the reduced gradient g1 and Hessian h2 (xx, yy, zz, xy, xz, yz) of u,
+// or the Laplacian table's value lam
+template <typename A, int E, bool LAPTAB>
+__device__ __forceinline__ double bloch_phase_sum(const EvalArgs& p, const A* u0, const A (*g1)[E],
+                                                  const A (*h2)[E], const A* lam, const A* hv,
+                                                  const A (*hg)[E], const A* hl)
+{
+    const A ka[3] = {(A)p.kc[0], (A)p.kc[1], (A)p.kc[2]};
+    const A kk = ka[0] * ka[0] + ka[1] * ka[1] + ka[2] * ka[2];
+    const A ml0 = (A)p.ml[0], ml1 = (A)p.ml[1], ml2 = (A)p.ml[2];
+    const A ml3 = (A)p.ml[3], ml4 = (A)p.ml[4], ml5 = (A)p.ml[5];
+    auto imc = [](A hr, A hi, A wr, A wi) { return hr * wi - hi * wr; };   // Im(conj(h) w)
+    double sph = 0.0;
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) {
+        const int r = 2 * j, q = 2 * j + 1;
+        A gc[3][2];   // Cartesian gradient of Re u, Im u
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            gc[a][0] = (A)p.mg[3 * a] * g1[0][r] + (A)p.mg[3 * a + 1] * g1[1][r] + (A)p.mg[3 * a + 2] * g1[2][r];
+            gc[a][1] = (A)p.mg[3 * a] * g1[0][q] + (A)p.mg[3 * a + 1] * g1[1][q] + (A)p.mg[3 * a + 2] * g1[2][q];
+        }
+        const A ur = u0[r], ui = u0[q];
+        A acc = imc(hv[r], hv[q], ur, ui);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) acc += imc(hg[a][r], hg[a][q], gc[a][0] - ka[a] * ui, gc[a][1] + ka[a] * ur);
+        A lr, li;
+        if (LAPTAB) {
+            lr = lam[r];
+            li = lam[q];
+        } else {
+            const A hl_r = ml0 * h2[0][r] + ml1 * h2[1][r] + ml2 * h2[2][r] + ml3 * h2[3][r] + ml4 * h2[4][r] +
+                           ml5 * h2[5][r];
+            const A hl_i = ml0 * h2[0][q] + ml1 * h2[1][q] + ml2 * h2[2][q] + ml3 * h2[3][q] + ml4 * h2[4][q] +
+                           ml5 * h2[5][q];
+            const A kgr = ka[0] * gc[0][0] + ka[1] * gc[1][0] + ka[2] * gc[2][0];
+            const A kgi = ka[0] * gc[0][1] + ka[1] * gc[1][1] + ka[2] * gc[2][1];
+            lr = hl_r - A(2) * kgi - kk * ur;
+            li = hl_i + A(2) * kgr - kk * ui;
+        }
+        acc += imc(hl[r], hl[q], lr, li);
+        sph += (double)acc;
+    }
+    return sph;
+}
+
 template <typename T, bool LAPTAB, bool BLOCH>
 __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs b)
 {
@@ -116,54 +217,7 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
             load_run<A>(use && glp ? glp + ip * n_orb + o0 : nullptr, wl, o0, n_orb, E);
             for (int a = 0; a < 3; ++a)
                 load_run<A>(use && ggp ? ggp + (ip * 3 + a) * n_orb + o0 : nullptr, wg[a], o0, n_orb, E);
-            if constexpr (BLOCH) {
-                // upstream of the bracket, h = conj(e) g, kept for the phase term of dL/dr;
-                // then the upstream of the tabulated u (see the header)
-                const double* rr = p.pos + 3 * ip;
-                const double uk = __fma_rn(p.kred[0], rr[0], __fma_rn(p.kred[1], rr[1], __dmul_rn(p.kred[2], rr[2])));
-                double sn, cs;
-                sincospi(2.0 * (uk - rint(uk)), &sn, &cs);
-                const A c = (A)cs, sph = (A)sn;
-                const A ka[3] = {(A)p.kc[0], (A)p.kc[1], (A)p.kc[2]};
-                const A kk = ka[0] * ka[0] + ka[1] * ka[1] + ka[2] * ka[2];
-                auto rot = [&](A& x, A& y) {   // (x + i y) <- conj(e) (x + i y)
-                    const A xr = c * x + sph * y, yi = c * y - sph * x;
-                    x = xr;
-                    y = yi;
-                };
-#pragma unroll
-                for (int j = 0; j < E / 2; ++j) {
-                    const int r = 2 * j, q = 2 * j + 1;
-                    rot(wv[r], wv[q]);
-                    rot(wl[r], wl[q]);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) rot(wg[a][r], wg[a][q]);
-                    hv[r] = wv[r];
-                    hv[q] = wv[q];
-                    hl[r] = wl[r];
-                    hl[q] = wl[q];
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        hg[a][r] = wg[a][r];
-                        hg[a][q] = wg[a][q];
-                    }
-                    // -i k.h_grad = (k.Im h_grad, -k.Re h_grad)
-                    const A khr = ka[0] * wg[0][r] + ka[1] * wg[1][r] + ka[2] * wg[2][r];
-                    const A khi = ka[0] * wg[0][q] + ka[1] * wg[1][q] + ka[2] * wg[2][q];
-                    wv[r] += khi;
-                    wv[q] -= khr;
-                    if (!LAPTAB) {
-                        wv[r] -= kk * hl[r];
-                        wv[q] -= kk * hl[q];
-                        // -2 i k_a h_lap = (2 k_a Im h_lap, -2 k_a Re h_lap)
-#pragma unroll
-                        for (int a = 0; a < 3; ++a) {
-                            wg[a][r] += A(2) * ka[a] * hl[q];
-                            wg[a][q] -= A(2) * ka[a] * hl[r];
-                        }
-                    }
-                }
-            }
+            if constexpr (BLOCH) bloch_upstream<A, E, LAPTAB>(p, p.pos + 3 * ip, wv, wg, wl, hv, hg, hl);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -303,42 +357,7 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
             }
             // Bloch: the phase term, sum over outputs z of Im(conj(h_z) w_z) with the bracket w
             double sph = 0.0;
-            if constexpr (BLOCH) {
-                const A ka[3] = {(A)p.kc[0], (A)p.kc[1], (A)p.kc[2]};
-                const A kk = ka[0] * ka[0] + ka[1] * ka[1] + ka[2] * ka[2];
-                auto imc = [](A hr, A hi, A wr, A wi) { return hr * wi - hi * wr; };   // Im(conj(h) w)
-#pragma unroll
-                for (int j = 0; j < E / 2; ++j) {
-                    const int r = 2 * j, q = 2 * j + 1;
-                    A gc[3][2];   // Cartesian gradient of Re u, Im u
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        gc[a][0] = (A)p.mg[3 * a] * g1[0][r] + (A)p.mg[3 * a + 1] * g1[1][r] + (A)p.mg[3 * a + 2] * g1[2][r];
-                        gc[a][1] = (A)p.mg[3 * a] * g1[0][q] + (A)p.mg[3 * a + 1] * g1[1][q] + (A)p.mg[3 * a + 2] * g1[2][q];
-                    }
-                    const A ur = u0[r], ui = u0[q];
-                    A acc = imc(hv[r], hv[q], ur, ui);
-#pragma unroll
-                    for (int a = 0; a < 3; ++a)
-                        acc += imc(hg[a][r], hg[a][q], gc[a][0] - ka[a] * ui, gc[a][1] + ka[a] * ur);
-                    A lr, li;
-                    if (LAPTAB) {
-                        lr = lam[r];
-                        li = lam[q];
-                    } else {
-                        const A hl_r = ml0 * h2[0][r] + ml1 * h2[1][r] + ml2 * h2[2][r] + ml3 * h2[3][r] +
-                                       ml4 * h2[4][r] + ml5 * h2[5][r];
-                        const A hl_i = ml0 * h2[0][q] + ml1 * h2[1][q] + ml2 * h2[2][q] + ml3 * h2[3][q] +
-                                       ml4 * h2[4][q] + ml5 * h2[5][q];
-                        const A kgr = ka[0] * gc[0][0] + ka[1] * gc[1][0] + ka[2] * gc[2][0];
-                        const A kgi = ka[0] * gc[0][1] + ka[1] * gc[1][1] + ka[2] * gc[2][1];
-                        lr = hl_r - A(2) * kgi - kk * ur;
-                        li = hl_i + A(2) * kgr - kk * ui;
-                    }
-                    acc += imc(hl[r], hl[q], lr, li);
-                    sph += (double)acc;
-                }
-            }
+            if constexpr (BLOCH) sph = bloch_phase_sum<A, E, LAPTAB>(p, u0, g1, h2, lam, hv, hg, hl);
             // sum over the lanes of the group (all lanes of the warp take part)
             for (int off = L >> 1; off > 0; off >>= 1) {
 #pragma unroll
@@ -586,6 +605,238 @@ int launch_five_typed(const BwdArgs& a, bool lagrange, cudaStream_t st)
     return a.bloch ? launch_five<T, kBwdBSpline, true>(a, st) : launch_five<T, kBwdBSpline, false>(a, st);
 }
 
+// ---- pp-splines (Eq. pp-splineinterpolation3): eight coefficients sigma^{kappa mu nu} per grid
+// point, a 2 x 2 x 2 corner stencil, weights s_i^kappa(t) (Eq. pp-splinebasis).  The outputs
+// are derivatives of one spline with the chain rule, as for the B-splines with the Hessian
+// Laplacian, so the adjoint has the same form with the pp weights and their derivatives up to
+// the third (s^1 is linear, s^2 cubic: d3 s^2_0 = -1, d3 s^2_1 = 1); dcoef holds the eight
+// tables [8][Nx][Ny][Nz][O], entry 4 kappa + 2 mu + nu.
+template <typename A>
+__device__ __forceinline__ void pp_bwd_weights(A t, A w[2][2], A dw[2][2], A d2w[2][2], A d3w[2][2])
+{
+    const A t2 = t * t;
+    w[0][0] = A(1) - t;
+    w[0][1] = t;
+    w[1][0] = ((A(-1.0 / 6.0) * t + A(0.5)) * t - A(1.0 / 3.0)) * t;
+    w[1][1] = (A(1.0 / 6.0) * t2 - A(1.0 / 6.0)) * t;
+    dw[0][0] = A(-1);
+    dw[0][1] = A(1);
+    dw[1][0] = A(-0.5) * t2 + t - A(1.0 / 3.0);
+    dw[1][1] = A(0.5) * t2 - A(1.0 / 6.0);
+    d2w[0][0] = A(0);
+    d2w[0][1] = A(0);
+    d2w[1][0] = A(1) - t;
+    d2w[1][1] = t;
+    d3w[0][0] = A(0);
+    d3w[0][1] = A(0);
+    d3w[1][0] = A(-1);
+    d3w[1][1] = A(1);
+}
+
+template <typename T, bool BLOCH>
+__global__ void __launch_bounds__(kEvalThreads) pp_bwd_kernel(const BwdArgs b)
+{
+    using A = typename Traits<T>::A;
+    constexpr int E = Traits<T>::E;
+    const EvalArgs& p = b.e;
+    const int lane = threadIdx.x & 31;
+    const int L = 1 << p.lanes_log2;
+    const int sub = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const int gpw = 32 >> p.lanes_log2;
+    const long long total = p.n_pos * p.tiles;
+    const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
+    const size_t rowb = (size_t)p.row_stride * sizeof(T);   // one z row: 8 entries x O_p
+    const size_t entb = rowb / 8;
+    const size_t colb = (size_t)p.col_stride * sizeof(T);
+    const int n_orb = p.n_orb;
+    const size_t canon = (size_t)p.nx * p.ny * p.nz * n_orb;
+    const A ml0 = (A)p.ml[0], ml1 = (A)p.ml[1], ml2 = (A)p.ml[2];
+    const A ml3 = (A)p.ml[3], ml4 = (A)p.ml[4], ml5 = (A)p.ml[5];
+
+    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
+        const long long gid = w0 + (lane >> p.lanes_log2);
+        const bool active = gid < total;
+        const long long ip = active ? gid / p.tiles : 0;
+        const int tile = active ? (int)(gid - ip * p.tiles) : 0;
+        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+        int ix, iy, iz;
+        double tx, ty, tz;
+        bool ok;
+        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+        if (active && !ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+        A w[3][2][2], dw[3][2][2], d2w[3][2][2], d3w[3][2][2];
+        pp_bwd_weights<A>((A)tx, w[0], dw[0], d2w[0], d3w[0]);
+        pp_bwd_weights<A>((A)ty, w[1], dw[1], d2w[1], d3w[1]);
+        pp_bwd_weights<A>((A)tz, w[2], dw[2], d2w[2], d3w[2]);
+        const int chunk = tile * L + sub;
+        const int o0 = chunk * E;
+        const bool use = active && o0 < n_orb;
+        A wv[E], wl[E], gt[3][E];
+        A hv[E], hl[E], hg[3][E];
+        {
+            A wg[3][E];
+            const A* gvp = static_cast<const A*>(b.gv);
+            const A* ggp = static_cast<const A*>(b.gg);
+            const A* glp = static_cast<const A*>(b.gl);
+            load_run<A>(use && gvp ? gvp + ip * n_orb + o0 : nullptr, wv, o0, n_orb, E);
+            load_run<A>(use && glp ? glp + ip * n_orb + o0 : nullptr, wl, o0, n_orb, E);
+            for (int a = 0; a < 3; ++a)
+                load_run<A>(use && ggp ? ggp + (ip * 3 + a) * n_orb + o0 : nullptr, wg[a], o0, n_orb, E);
+            if constexpr (BLOCH) bloch_upstream<A, E, false>(p, r, wv, wg, wl, hv, hg, hl);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    gt[i][e] = (A)p.mg[i] * wg[0][e] + (A)p.mg[3 + i] * wg[1][e] + (A)p.mg[6 + i] * wg[2][e];
+        }
+        int xs[2], ys[2], zs[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            xs[j] = ix + j < p.nx ? ix + j : 0;
+            ys[j] = iy + j < p.ny ? iy + j : 0;
+            zs[j] = iz + j < p.nz ? iz + j : 0;
+        }
+
+        // ---- coefficient adjoint: 8 corners x 8 entries ----
+        if (b.dcoef && use) {
+            A* dc = static_cast<A*>(b.dcoef);
+            const bool vec = b.vec_atomic != 0;
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j)
+                    for (int k = 0; k < 2; ++k) {
+                        const size_t row = (((size_t)xs[i] * p.ny + ys[j]) * p.nz + zs[k]) * n_orb + o0;
+                        for (int ent = 0; ent < 8; ++ent) {
+                            const int kap = ent >> 2, mu = (ent >> 1) & 1, nu = ent & 1;
+                            const A x0 = w[0][kap][i], x1 = dw[0][kap][i], x2 = d2w[0][kap][i];
+                            const A y0 = w[1][mu][j], y1 = dw[1][mu][j], y2 = d2w[1][mu][j];
+                            const A z0 = w[2][nu][k], z1 = dw[2][nu][k], z2 = d2w[2][nu][k];
+                            const A B = x0 * y0 * z0, Bx = x1 * y0 * z0, By = x0 * y1 * z0, Bz = x0 * y0 * z1;
+                            const A lapB = ml0 * x2 * y0 * z0 + ml1 * x0 * y2 * z0 + ml2 * x0 * y0 * z2 +
+                                           ml3 * x1 * y1 * z0 + ml4 * x1 * y0 * z1 + ml5 * x0 * y1 * z1;
+                            A v[E];
+#pragma unroll
+                            for (int e = 0; e < E; ++e)
+                                v[e] = wv[e] * B + gt[0][e] * Bx + gt[1][e] * By + gt[2][e] * Bz + wl[e] * lapB;
+                            atomic_run<A, E>(dc + ent * canon + row, v, o0, n_orb, vec);
+                        }
+                    }
+        }
+
+        // ---- position adjoint: gradient, Hessian and gradient of the Laplacian of the spline ----
+        if (b.dpos) {
+            A g1[3][E], h2[6][E], d3[3][E], u0[E];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                for (int i = 0; i < 3; ++i) g1[i][e] = d3[i][e] = A(0);
+                for (int i = 0; i < 6; ++i) h2[i][e] = A(0);
+                u0[e] = A(0);
+            }
+            const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j) {
+                    const char* col = static_cast<const char*>(p.tab[0]) + (size_t)(xs[i] * p.ny + ys[j]) * colb + off;
+                    for (int km = 0; km < 4; ++km) {
+                        const int kap = km >> 1, mu = km & 1;
+                        A a[4][E];
+#pragma unroll
+                        for (int e = 0; e < E; ++e) a[0][e] = a[1][e] = a[2][e] = a[3][e] = A(0);
+#pragma unroll
+                        for (int k = 0; k < 2; ++k)
+#pragma unroll
+                            for (int nu = 0; nu < 2; ++nu) {
+                                A c[E];
+                                unpack<T>(ldg_table(p, col + k * rowb + (size_t)(4 * kap + 2 * mu + nu) * entb), c);
+#pragma unroll
+                                for (int e = 0; e < E; ++e) {
+                                    a[0][e] = fma(w[2][nu][k], c[e], a[0][e]);
+                                    a[1][e] = fma(dw[2][nu][k], c[e], a[1][e]);
+                                    a[2][e] = fma(d2w[2][nu][k], c[e], a[2][e]);
+                                    a[3][e] = fma(d3w[2][nu][k], c[e], a[3][e]);
+                                }
+                            }
+                        const A bx = w[0][kap][i], dbx = dw[0][kap][i], d2bx = d2w[0][kap][i], d3bx = d3w[0][kap][i];
+                        const A by = w[1][mu][j], dby = dw[1][mu][j], d2by = d2w[1][mu][j], d3by = d3w[1][mu][j];
+                        // third-derivative weights contracted with the Laplacian metric
+                        const A x0 = ml0 * d3bx * by + ml1 * dbx * d2by + ml3 * d2bx * dby;
+                        const A x1 = ml4 * d2bx * by + ml5 * dbx * dby;
+                        const A x2 = ml2 * dbx * by;
+                        const A y0 = ml0 * d2bx * dby + ml1 * bx * d3by + ml3 * dbx * d2by;
+                        const A y1 = ml4 * dbx * dby + ml5 * bx * d2by;
+                        const A y2 = ml2 * bx * dby;
+                        const A z1 = ml0 * d2bx * by + ml1 * bx * d2by + ml3 * dbx * dby;
+                        const A z2 = ml4 * dbx * by + ml5 * bx * dby;
+                        const A z3 = ml2 * bx * by;
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            if constexpr (BLOCH) u0[e] += bx * by * a[0][e];
+                            g1[0][e] += dbx * by * a[0][e];
+                            g1[1][e] += bx * dby * a[0][e];
+                            g1[2][e] += bx * by * a[1][e];
+                            h2[0][e] += d2bx * by * a[0][e];
+                            h2[1][e] += bx * d2by * a[0][e];
+                            h2[2][e] += bx * by * a[2][e];
+                            h2[3][e] += dbx * dby * a[0][e];
+                            h2[4][e] += dbx * by * a[1][e];
+                            h2[5][e] += bx * dby * a[1][e];
+                            d3[0][e] += x0 * a[0][e] + x1 * a[1][e] + x2 * a[2][e];
+                            d3[1][e] += y0 * a[0][e] + y1 * a[1][e] + y2 * a[2][e];
+                            d3[2][e] += z1 * a[1][e] + z2 * a[2][e] + z3 * a[3][e];
+                        }
+                    }
+                }
+            double u[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const A hxx = h2[0][e], hyy = h2[1][e], hzz = h2[2][e];
+                const A hxy = h2[3][e], hxz = h2[4][e], hyz = h2[5][e];
+                u[0] += (double)(wv[e] * g1[0][e] + hxx * gt[0][e] + hxy * gt[1][e] + hxz * gt[2][e] + wl[e] * d3[0][e]);
+                u[1] += (double)(wv[e] * g1[1][e] + hxy * gt[0][e] + hyy * gt[1][e] + hyz * gt[2][e] + wl[e] * d3[1][e]);
+                u[2] += (double)(wv[e] * g1[2][e] + hxz * gt[0][e] + hyz * gt[1][e] + hzz * gt[2][e] + wl[e] * d3[2][e]);
+            }
+            double sph = 0.0;
+            if constexpr (BLOCH) sph = bloch_phase_sum<A, E, false>(p, u0, g1, h2, u0, hv, hg, hl);
+            for (int o = L >> 1; o > 0; o >>= 1) {
+#pragma unroll
+                for (int i = 0; i < 3; ++i) u[i] += __shfl_xor_sync(kFullMask, u[i], o);
+                sph += __shfl_xor_sync(kFullMask, sph, o);
+            }
+            if (active && sub == 0) {
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const double d = p.mg[3 * a] * u[0] + p.mg[3 * a + 1] * u[1] + p.mg[3 * a + 2] * u[2] -
+                                     (BLOCH ? p.kc[a] * sph : 0.0);
+                    atomicAdd(b.dpos + 3 * ip + a, d);
+                }
+            }
+        }
+    }
+}
+
+template <typename T, bool BLOCH>
+int launch_pp_bwd(const BwdArgs& a, cudaStream_t st)
+{
+    const int gpw = 32 >> a.e.lanes_log2;
+    const long long warps = (a.e.n_pos * a.e.tiles + gpw - 1) / gpw;
+    long long blocks = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pp_bwd_kernel<T, BLOCH>, kEvalThreads, 0);
+    if (e != cudaSuccess) return cuda_error(e, "occupancy query");
+    if (per_sm < 1) per_sm = 1;
+    const long long cap = (long long)sm_count() * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    pp_bwd_kernel<T, BLOCH><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
+    return cuda_error(cudaGetLastError(), "pp_bwd_kernel launch");
+}
+
+template <typename T>
+int launch_pp_typed(const BwdArgs& a, cudaStream_t st)
+{
+    return a.bloch ? launch_pp_bwd<T, true>(a, st) : launch_pp_bwd<T, false>(a, st);
+}
+
 }  // namespace
 
 int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos, const void* gv,
@@ -611,6 +862,13 @@ int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
         if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync(dpos)");
     }
     if (!dcoef && !dpos) return QMCSPL_OK;
+    if (h->method == QMCSPL_PPSPLINE) {
+        switch (h->storage) {
+        case QMCSPL_F64: return launch_pp_typed<double>(a, st);
+        case QMCSPL_F32: return launch_pp_typed<float>(a, st);
+        default: return launch_pp_typed<__nv_bfloat16>(a, st);
+        }
+    }
     if (h->n_tables == 5) {   // Lagrange, or B-splines with separate gradient tables
         const bool lag = h->method == QMCSPL_LAGRANGE;
         switch (h->storage) {

@@ -659,18 +659,17 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
 {
     g_err.clear();
     if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
-    if (h->method == QMCSPL_PPSPLINE)
-        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for pp-splines");
     if (h->storage == QMCSPL_DF64)
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for double-float tables");
     if (is_general(h))
         return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is implemented for cubic B-splines on uniform grids");
     if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
-    const bool five = h->n_tables == 5;   // dcoef holds all five tables
-    if (dcoef_lap && (five || !(h->separate_lap && dcoef)))
-        return set_error(QMCSPL_ERR_ARG, five ? "five-table handle: dcoef holds all tables, dcoef_lap must be NULL"
-                                              : "dcoef_lap needs a separate-Laplacian handle and dcoef");
-    if (dcoef && !five && h->separate_lap && !dcoef_lap)
+    // five-table and pp handles: dcoef holds all their tables (5, or the 8 pp entries)
+    const bool multi = h->n_tables == 5 || h->method == QMCSPL_PPSPLINE;
+    if (dcoef_lap && (multi || !(h->separate_lap && dcoef)))
+        return set_error(QMCSPL_ERR_ARG, multi ? "five-table or pp handle: dcoef holds all tables, dcoef_lap must be NULL"
+                                               : "dcoef_lap needs a separate-Laplacian handle and dcoef");
+    if (dcoef && !multi && h->separate_lap && !dcoef_lap)
         return set_error(QMCSPL_ERR_ARG, "separate-Laplacian handle: dcoef_lap is required with dcoef");
     if (n_pos == 0) return QMCSPL_OK;
     if (!pos) return set_error(QMCSPL_ERR_ARG, "pos is NULL");

@@ -143,8 +143,8 @@ def test_backward_rejects_variants():
     from paper_1309_6250_gb300 import _lib
     dims = (8, 8, 8)
     lat, mil, coef = inputs.random_cell(5, dims, 2, 5.0, 4.0, np.eye(3) * 6.0)
-    spl = splines(lat, dims, mil, coef, method="pp", storage="f64")
     pos = torch.zeros((4, 3), dtype=torch.float64, device=dev())
+    spl = splines(lat, dims, mil, coef, method="interp", storage="f64", degree=5)
     with pytest.raises(_lib.QmcsplError) as ei:
         spl.backward(pos)
     assert ei.value.code == _lib.ERR_UNSUPPORTED
@@ -255,7 +255,8 @@ def test_bloch_autograd_matches_the_direct_adjoint():
 
 FIVE = [dict(method="lagrange", separate_lap=True),
         dict(method="smooth", separate_lap=True, separate_grad=True),
-        dict(method="interp", separate_lap=True, separate_grad=True)]
+        dict(method="interp", separate_lap=True, separate_grad=True),
+        dict(method="pp", separate_lap=False)]
 
 
 def five_forward(method, tabs, lat, pos, k=None):
@@ -263,17 +264,20 @@ def five_forward(method, tabs, lat, pos, k=None):
         return oracle.bloch_eval(method, tabs, lat, k, pos)
     if method == "lagrange":
         return oracle.lagrange_eval(tabs, lat, pos)
+    if method == "pp":
+        return oracle.pp_eval(tabs, lat, pos)
     return oracle.bspline_eval_separate(tabs, lat, pos)
 
 
-@pytest.mark.parametrize("kw", FIVE, ids=["lagrange", "smooth_sepgrad", "interp_sepgrad"])
+@pytest.mark.parametrize("kw", FIVE, ids=["lagrange", "smooth_sepgrad", "interp_sepgrad", "pp"])
 @pytest.mark.parametrize("storage,tol_lin,tol_fd", [("f64", 1e-11, 1e-6), ("f32", 2e-5, 3e-3)])
 @pytest.mark.parametrize("bloch", [False, True])
 def test_five_table_backward_linearity_and_position_fd(kw, storage, tol_lin, tol_fd, bloch):
-    """The outputs are the values of five interpolants, linear in the five tables: the
-    coefficient adjoint by sum(dL/dbeta * beta') = L(beta') with the oracle on random tables,
-    the position adjoint against central differences of the oracle forward (positions away
-    from grid planes, where the Lagrange interpolant's derivatives jump)."""
+    """Five-table handles (the outputs are the values of five interpolants) and pp-splines
+    (eight coefficient entries per grid point): the outputs are linear in the tables, so the
+    coefficient adjoint is checked by sum(dL/dbeta * beta') = L(beta') with the oracle on random
+    tables, and the position adjoint against central differences of the oracle forward
+    (positions away from grid planes, where the Lagrange interpolant's derivatives jump)."""
     dims = (10, 11, 12)
     n_orb = 3
     k = inputs.KPOINTS["generic"] if bloch else None
@@ -283,7 +287,8 @@ def test_five_table_backward_linearity_and_position_fd(kw, storage, tol_lin, tol
     else:
         lat, mil, coef = inputs.random_cell(1800, dims, n_orb, 5.0, 4.0, NONORTHO)
         spl = splines(lat, dims, mil, coef, storage=storage, **kw)
-    assert spl.info()["n_tables"] == 5
+    n_tab = 8 if kw["method"] == "pp" else 5
+    assert spl.info()["n_tables"] == 5 or kw["method"] == "pp"
     nf = spl.coef_shape()[-1]
     pos = inputs.positions(lat, 120, 1801, -1, 2)
     pos = pos[away_from_planes(lat, dims, pos, 0.02)]
@@ -298,7 +303,7 @@ def test_five_table_backward_linearity_and_position_fd(kw, storage, tol_lin, tol
         r32 = lambda x: (x.real.astype(np.float32) + 1j * x.imag.astype(np.float32)) if bloch else \
             x.astype(np.float32).astype(np.float64)
         g = tuple(r32(x) for x in g)
-    dc = torch.zeros((5,) + spl.coef_shape(), dtype=spl.out_dtype, device=dev())
+    dc = torch.zeros((n_tab,) + spl.coef_shape(), dtype=spl.out_dtype, device=dev())
     dpos = spl.backward(t(pos, torch.float64), *(t(x, cd) for x in g), dcoef=dc)
     spl.sync()
     dc, dpos = dc.double().cpu().numpy(), dpos.cpu().numpy()
@@ -306,11 +311,11 @@ def test_five_table_backward_linearity_and_position_fd(kw, storage, tol_lin, tol
         (lambda z: float(sum(np.sum(gi * zi) for gi, zi in zip(g, z))))
     rng = np.random.default_rng(1803)
     for _ in range(2):
-        b5 = rng.standard_normal((5,) + dims + (nf,))
+        b5 = rng.standard_normal((n_tab,) + dims + (nf,))
         ref = loss(five_forward(kw["method"], b5, lat, pos, k))
         lin = np.sum(dc * b5)
         assert abs(lin - ref) <= tol_lin * max(1.0, abs(ref)), (lin, ref)
-    tabs = np.stack([spl.get_table(i) for i in range(5)])
+    tabs = np.stack([spl.get_table(i) for i in range(n_tab)])
     h = 1e-4
     fd = np.zeros_like(dpos)
     for a in range(3):
