@@ -1,5 +1,7 @@
-// backward.cu -- adjoint of the tricubic B-spline evaluation (not part of the paper:
-// gradients of a downstream scalar L for orbital optimisation and forces).
+// backward.cu -- adjoint of the evaluation (not part of the paper: gradients of a downstream
+// scalar L for orbital optimisation and forces), for the tricubic B-splines below, and further
+// down for the five-table handles (Lagrange, B-splines with separate gradient tables) and the
+// pp-splines.
 //
 // Given upstream weights wv = dL/dval, wg = dL/dgrad (Cartesian), wl = dL/dlap for one
 // position and orbital, the chain rule of Sec. II (Coordinates) is transposed first:
@@ -36,7 +38,7 @@ struct BwdArgs {
     const void* gv;           // [P][O] output dtype, may be null
     const void* gg;           // [P][3][O]
     const void* gl;           // [P][O]
-    void* dcoef;              // [Nx][Ny][Nz][O] output dtype, accumulated
+    void* dcoef;              // [Nx][Ny][Nz][O] output dtype, accumulated ([5][..] five tables, [8][..] pp)
     void* dcoef_lap;
     double* dpos;             // [P][3], zeroed before the launch, accumulated
     int vec_atomic;           // dcoef rows allow 16-byte vector atomics
