@@ -839,14 +839,18 @@ def slater_kinetic(val, grad, lap, n_walkers: int, n_elec: int, n_up: int):
     """Per walker: (logdet [W] = ln|det A_up| + ln|det A_dn|, sign [W], kinetic [W] = T_L,
     drift [W, n_elec, 3]) from orbital outputs val [W*n_elec, O], grad [W*n_elec, 3, O],
     lap [W*n_elec, O] (walker-major positions; electrons 0..n_up-1 spin up).  numpy's
-    slogdet and inv serve as library steps."""
-    val = np.asarray(val, dtype=np.float64)
-    grad = np.asarray(grad, dtype=np.float64)
-    lap = np.asarray(lap, dtype=np.float64)
+    slogdet and inv serve as library steps.  Complex orbitals (Bloch functions, Sec. II)
+    give complex determinants: then sign is the unit complex number det / |det| of the
+    product, and the kinetic term and the drift are complex (Jacobi's formula holds as is)."""
+    cplx = any(np.iscomplexobj(x) for x in (val, grad, lap))
+    dt = np.complex128 if cplx else np.float64
+    val = np.asarray(val, dtype=dt)
+    grad = np.asarray(grad, dtype=dt)
+    lap = np.asarray(lap, dtype=dt)
     logdet = np.zeros(n_walkers)
-    sign = np.ones(n_walkers)
-    kin = np.zeros(n_walkers)
-    drift = np.zeros((n_walkers, n_elec, 3))
+    sign = np.ones(n_walkers, dtype=dt)
+    kin = np.zeros(n_walkers, dtype=dt)
+    drift = np.zeros((n_walkers, n_elec, 3), dtype=dt)
     for w in range(n_walkers):
         for e0, n in ((0, n_up), (n_up, n_elec - n_up)):
             if n == 0:

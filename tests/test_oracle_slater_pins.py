@@ -120,3 +120,76 @@ def test_exchange_antisymmetry_and_two_by_two():
     ld1, s1, k1, _ = oracle.slater_kinetic(v, g, l, 1, 2, 2)
     assert ld1[0] == pytest.approx(math.log(abs(D)), abs=1e-12) and s1[0] == np.sign(D)
     assert k1[0] == pytest.approx(-0.5 * lapD / D, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# complex orbitals (Bloch functions, Sec. II): complex determinants
+# ---------------------------------------------------------------------------
+
+def test_complex_planewave_determinant_kinetic_energy_and_phase():
+    """Orbitals exp(i (k+G_j).r) are eigenfunctions of -1/2 lap with eigenvalues |k+G_j|^2/2, so
+    T_L = 1/2 sum_j |k+G_j|^2 (real) at every configuration; the determinant's modulus and phase
+    agree with a direct product formula for one electron per block."""
+    n_up, n_dn = 5, 3
+    rng = np.random.default_rng(20)
+    B = 2 * np.pi * np.linalg.inv(LAT).T
+    kvec = B @ np.array([0.137, -0.291, 0.412])
+    gs = []
+    while len(gs) < 5:
+        g = tuple(int(x) for x in rng.integers(-2, 3, 3))
+        if g not in gs:
+            gs.append(g)
+    kg = np.array([kvec + B @ np.array(g) for g in gs])          # [5, 3]
+    W = 4
+    pos = rng.uniform(0, 6, (W * (n_up + n_dn), 3))
+    ph = np.exp(1j * pos @ kg.T)                                    # [P, 5]
+    val = ph
+    grad = 1j * kg.T[None, :, :] * ph[:, None, :]
+    lap = -np.sum(kg ** 2, axis=1)[None, :] * ph
+    logdet, sign, kin, drift = oracle.slater_kinetic(val, grad, lap, W, n_up + n_dn, n_up)
+    k2 = np.sum(kg ** 2, axis=1)
+    np.testing.assert_allclose(kin, 0.5 * (k2[:n_up].sum() + k2[:n_dn].sum()), rtol=1e-10, atol=1e-10)
+    assert np.iscomplexobj(sign) and np.allclose(np.abs(sign), 1.0)
+    # one electron per block: det = phi_0(r), so ln|det| = 0 and sign = exp(i (k+G_0).r)
+    ld1, sg1, _, d1 = oracle.slater_kinetic(val, grad, lap, W * 4, 2, 1)
+    np.testing.assert_allclose(ld1, 0.0, atol=1e-12)
+    np.testing.assert_allclose(sg1, ph[0::2, 0] * ph[1::2, 0], rtol=1e-12)
+    np.testing.assert_allclose(d1[:, 0], 1j * np.broadcast_to(kg[0], d1[:, 0].shape), rtol=1e-12)
+
+
+def test_complex_drift_and_kinetic_by_finite_differences():
+    """Random complex orbitals (random complex planewave sums): the drift is grad_i ln det and the
+    kinetic term -1/2 lap_i det / det summed over i, both by central differences of det."""
+    rng = np.random.default_rng(21)
+    B = 2 * np.pi * np.linalg.inv(LAT).T
+    mil = rng.integers(-2, 3, (9, 3))
+    coef = rng.standard_normal((4, 9)) + 1j * rng.standard_normal((4, 9))
+    kvec = B @ np.array([0.25, 0.1, -0.3])
+    kg = np.array([kvec + B @ m for m in mil])
+
+    def orbitals(r):
+        e = np.exp(1j * r @ kg.T)                                   # [P, 9]
+        v = e @ coef.T
+        g = np.einsum("pg,ga,og->pao", 1j * e, kg, coef)
+        l = (e * -np.sum(kg ** 2, axis=1)) @ coef.T
+        return v, g, l
+
+    n = 4
+    r0 = rng.uniform(0, 6, (n, 3))
+    v, g, l = orbitals(r0)
+    _, _, kin, drift = oracle.slater_kinetic(v, g, l, 1, n, n)
+    det = lambda r: np.linalg.det(orbitals(r)[0][:, :n])
+    d0 = det(r0)
+    h = 1e-4
+    fd_drift = np.zeros((n, 3), dtype=complex)
+    lap_sum = 0.0
+    for i in range(n):
+        for a in range(3):
+            rp, rm = r0.copy(), r0.copy()
+            rp[i, a] += h
+            rm[i, a] -= h
+            dp, dm = det(rp), det(rm)
+            fd_drift[i, a] = (dp - dm) / (2 * h) / d0
+            lap_sum += (dp - 2 * d0 + dm) / h ** 2 / d0
+    np.testing.assert_allclose(drift[0], fd_drift, rtol=1e-6, atol=1e-6)
+    assert abs(kin[0] - (-0.5 * lap_sum)) < 1e-4 * max(1.0, abs(kin[0]))
