@@ -322,7 +322,8 @@ def bench_bloch(args, dev, stream):
     """Complex Bloch orbitals at k != 0 (Sec. II) on the MgO-like 64-atom cell: 64 bands at
     the zone corner R = (1/2, 1/2, 1/2) on 96^3 (the same table bytes as the 128 real
     orbitals), 2048 walkers x 256 electrons, FP32 smoothing + Laplacian tables, cell order.
-    value = complex orbital evaluations (value, gradient, Laplacian) per second."""
+    value = complex orbital evaluations (value, gradient, Laplacian) per second.  The outputs
+    then feed the complex Slater consumer (4096 walkers x (64 + 64) electrons)."""
     import torch
     from paper_1309_6250_gb300.api import OrbitalSplines
     kp = inputs.KPOINTS["R"]
@@ -351,6 +352,18 @@ def bench_bloch(args, dev, stream):
            "eval_kernel_ms": k_s * 1e3, "order_kernels_ms": prof["order_ms"] / max(1, prof["launches"]),
            "real_function_evals_per_s": n_pos * n_fun / t,
            "algorithmic_gbs": bpe * n_pos * n_fun / k_s / 1e9}
+    # the same outputs as complex Slater matrices: 4096 walkers x (64 + 64) electrons, 64 bands
+    from paper_1309_6250_gb300.api import slater_kinetic
+    v, g, l = out
+    ne = 2 * n_band
+    W = n_pos // ne
+    cstep = lambda: slater_kinetic(v, g, l, W, ne, n_band, arith="f64")
+    cms = time_steps(cstep, max(5, args.steps // 40), 2, torch, stream)
+    ct = sum(cms) / len(cms) * 1e-3
+    res["consumer"] = {"workload": f"{W} walkers x ({n_band} + {n_band}) electrons, {n_band} complex bands, "
+                                   "FP64 complex Gauss-Jordan", "unit": "walkers/s", "value": W / ct,
+                       "ms_per_step": ct * 1e3,
+                       "gflops_equiv": W * 2 * 8.0 * n_band ** 3 / ct / 1e9}
     spl.close()
     return res
 

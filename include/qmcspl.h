@@ -387,21 +387,30 @@ int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void
  *     drift[w][e][c] = sum_j (A_s^-1)_ji grad[w n_elec + e][c][j]   (d_c ln|Psi| for electron e)
  * Determinant updates (one electron moved) are not provided.
  *
- *   val, grad, lap  device outputs of qmcspl_eval_vgl of a real-orbital handle for
- *          P = n_walkers x n_elec positions ordered walker-major, layouts [P][n_orb],
- *          [P][3][n_orb], [P][n_orb]; dtype 0 = double, 1 = float
- *   arith  enum qmcspl_slater_arith
- *   n_orb  the output row length O, >= both block sizes
+ *   val, grad, lap  device outputs of qmcspl_eval_vgl for P = n_walkers x n_elec positions
+ *          ordered walker-major, layouts [P][n_orb], [P][3][n_orb], [P][n_orb]; dtype 0 = double,
+ *          1 = float (real orbitals), 2 = complex double, 3 = complex float (Bloch orbitals,
+ *          the (re, im) layouts of a Bloch handle's outputs)
+ *   arith  enum qmcspl_slater_arith (complex dtypes: QMCSPL_SLATER_FP64 only, else
+ *          QMCSPL_ERR_UNSUPPORTED)
+ *   n_orb  the output row length O (orbitals), >= both block sizes
  *   n_up   0 .. n_elec; each block at most QMCSPL_SLATER_MAX_BLOCK electrons
- *   logdet, sign, kinetic  device double[n_walkers], each may be NULL (kinetic needs lap)
- *   drift  device double[n_walkers][n_elec][3] or NULL (needs grad)
+ *          (QMCSPL_SLATER_MAX_COMPLEX_BLOCK for complex dtypes)
+ *   logdet device double[n_walkers] or NULL
+ *   sign, kinetic  device double[n_walkers] or NULL (kinetic needs lap); for complex dtypes
+ *          double[n_walkers][2]: sign = (cos, sin) of the phase of det A_up det A_dn, kinetic
+ *          = the complex kinetic term (re, im)
+ *   drift  device double[n_walkers][n_elec][3] or NULL (needs grad); complex dtypes
+ *          double[n_walkers][n_elec][3][2]
  *   stream cudaStream_t; asynchronous
  * The inversion is Gauss-Jordan elimination with row pivoting in shared memory, one thread
- * block per walker, in FP64 or in double-float (arith).  An exactly singular block gives sign 0, logdet -inf and NaN
+ * block per walker, in FP64 or in double-float (arith); complex entries in FP64 with the
+ * pivot of largest modulus.  An exactly singular block gives sign 0, logdet -inf and NaN
  * kinetic energy and drift for that walker; nearly singular blocks lose accuracy as the
  * condition number grows.
  */
 #define QMCSPL_SLATER_MAX_BLOCK 160
+#define QMCSPL_SLATER_MAX_COMPLEX_BLOCK 112
 enum qmcspl_slater_arith {
     QMCSPL_SLATER_FP64 = 0,   /* FP64 elimination (GB300's FP64 pipe) */
     QMCSPL_SLATER_DF64 = 1    /* double-float elimination on the FP32 pipe: each entry a pair

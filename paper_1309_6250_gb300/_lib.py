@@ -34,6 +34,7 @@ DF64 = 3
 MAX_BATCH = 48
 NOALLOC_MAX_POS = 1 << 20
 SLATER_MAX_BLOCK = 160
+SLATER_MAX_COMPLEX_BLOCK = 112
 SLATER_ARITH = {"f64": 0, "df64": 1}
 
 ORDER_AUTO = 0

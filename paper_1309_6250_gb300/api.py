@@ -255,25 +255,30 @@ def eval_batched(splines: Sequence[OrbitalSplines], positions: Sequence[torch.Te
 
 def slater_kinetic(val: torch.Tensor, grad: Optional[torch.Tensor], lap: Optional[torch.Tensor],
                    n_walkers: int, n_elec: int, n_up: int, want_drift: bool = True, stream=None,
-                   arith: str = "df64"):
+                   arith: Optional[str] = None):
     """Slater-determinant consumer of eval_vgl outputs (walker-major positions, electrons
     0..n_up-1 spin up): returns (logdet [W], sign [W], kinetic [W], drift [W, n_elec, 3] or
-    None), float64 tensors on the outputs' device.  arith: 'df64' (double-float elimination
-    on the FP32 pipe) or 'f64'."""
+    None) on the outputs' device.  Real outputs: float64 tensors; arith 'df64' (double-float
+    elimination on the FP32 pipe, the default) or 'f64'.  Complex outputs of a Bloch handle:
+    complex128 sign (the phase of the determinant), kinetic and drift, FP64 elimination."""
     lib = _lib.load()
-    if val.dtype not in (torch.float32, torch.float64):
-        raise ValueError("real float32/float64 orbital outputs expected")
-    dtype = 0 if val.dtype == torch.float64 else 1
+    cplx = val.dtype in (torch.complex64, torch.complex128)
+    if val.dtype not in (torch.float32, torch.float64, torch.complex64, torch.complex128):
+        raise ValueError("float32/float64 or complex64/complex128 orbital outputs expected")
+    dtype = {torch.float64: 0, torch.float32: 1, torch.complex128: 2, torch.complex64: 3}[val.dtype]
+    if arith is None:
+        arith = "f64" if cplx else "df64"
     for t in (grad, lap):
         if t is not None and (t.dtype != val.dtype or t.device != val.device):
             raise ValueError("val, grad and lap must share dtype and device")
     n_orb = val.shape[-1]
     kw = dict(dtype=torch.float64, device=val.device)
+    ck = dict(dtype=torch.complex128, device=val.device)
     logdet = torch.empty(n_walkers, **kw)
-    sign = torch.empty(n_walkers, **kw)
-    kin = torch.empty(n_walkers, **kw) if lap is not None else None
-    drift = torch.empty((n_walkers, n_elec, 3), **kw) if (want_drift and grad is not None) else None
-    c = lambda t: None if t is None else t.contiguous()
+    sign = torch.empty(n_walkers, **(ck if cplx else kw))
+    kin = torch.empty(n_walkers, **(ck if cplx else kw)) if lap is not None else None
+    drift = torch.empty((n_walkers, n_elec, 3), **(ck if cplx else kw)) if (want_drift and grad is not None) else None
+    c = lambda t: None if t is None else (t.resolve_conj() if t.is_complex() else t).contiguous()
     val, grad, lap = c(val), c(grad), c(lap)
     with torch.cuda.device(val.device):
         _lib.check(lib.qmcspl_slater_kinetic(_ptr(val), _ptr(grad), _ptr(lap), dtype, _lib.SLATER_ARITH[arith],

@@ -22,6 +22,7 @@
 // a pair of floats (hi + lo, ~48 significant bits) and each elimination update is an
 // error-free FP32 multiply-add done two columns at a time with fma.rn.f32x2 (see df_fma2):
 // the FP32 pipe carries it, several times faster on this part.  Every loop is bounded by n.
+// Complex orbitals (Bloch functions) take a complex FP64 elimination (slater_complex_kernel).
 #include <cmath>
 
 #include "eval_common.cuh"
@@ -472,6 +473,216 @@ __global__ void __launch_bounds__(NT, 1) slater_df_kernel(const SlaterArgs a)
     }
 }
 
+// ---- complex orbitals (Bloch functions, Sec. II) ----
+// The same elimination on complex FP64 entries (double2), for outputs of a Bloch handle
+// (complex val, grad, lap: pairs (re, im) of T).  The pivot is the entry of largest modulus;
+// ln|det A| = sum_k ln|d_k| and the phase of det A is sum_k arg d_k + pi (number of row swaps),
+// reported as (cos, sin).  The kinetic term and the drift are complex (Jacobi's formula).
+constexpr int kSlaterCplxMaxBlock = QMCSPL_SLATER_MAX_COMPLEX_BLOCK;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+template <typename T>
+__device__ __forceinline__ double2 ldc(const void* p, long long i)   // complex element i
+{
+    const T* q = static_cast<const T*>(p) + 2 * i;
+    return make_double2((double)__ldg(q), (double)__ldg(q + 1));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSlaterThreads) slater_complex_kernel(const SlaterArgs a)
+{
+    extern __shared__ double2 csm[];
+    __shared__ double red[kSlaterThreads / 32];
+    __shared__ int piv[kSlaterCplxMaxBlock];
+    __shared__ int colmap[kSlaterCplxMaxBlock];
+    __shared__ double2 fcol[kSlaterCplxMaxBlock];
+    __shared__ double2 rowk[kSlaterCplxMaxBlock];
+    __shared__ double2 pivd[kSlaterCplxMaxBlock];
+    __shared__ int s_p;
+    __shared__ double2 s_d;
+
+    const long long w = blockIdx.x;
+    if (w >= a.n_walkers) return;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    const long long O = a.n_orb;
+    double logdet = 0.0, arg = 0.0;
+    double2 kin = make_double2(0.0, 0.0);
+    bool singular = false;
+
+    for (int blk = 0; blk < 2; ++blk) {
+        const int e0 = blk == 0 ? 0 : a.n_up;
+        const int n = blk == 0 ? a.n_up : a.n_elec - a.n_up;
+        if (n == 0) continue;
+        const int ns = n + 1;
+        const long long base = w * a.n_elec + e0;
+        double2* A = csm;   // [n][n + 1]
+
+        __syncthreads();
+        for (int i = wid; i < n; i += kSlaterThreads / 32)
+            for (int j = lane; j < n; j += 32) A[i * ns + j] = ldc<T>(a.val, (base + i) * O + j);
+        __syncthreads();
+
+        bool sing = false;
+        for (int k = 0; k < n; ++k) {
+            if (wid == 0) {   // pivot: largest |A[i][k]|^2 over i >= k (first one on ties)
+                double best = -1.0;
+                int bi = k;
+                for (int i = k + lane; i < n; i += 32) {
+                    const double2 z = A[i * ns + k];
+                    const double v = fma(z.x, z.x, z.y * z.y);
+                    if (v > best) {
+                        best = v;
+                        bi = i;
+                    }
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                    }
+                }
+                if (lane == 0) {
+                    s_p = bi;
+                    s_d = A[bi * ns + k];
+                    piv[k] = bi;
+                    pivd[k] = s_d;
+                }
+            }
+            __syncthreads();
+            const int p = s_p;
+            const double2 d = s_d;
+            if (p != k)
+                for (int j = tid; j < n; j += kSlaterThreads) {
+                    const double2 t = A[k * ns + j];
+                    A[k * ns + j] = A[p * ns + j];
+                    A[p * ns + j] = t;
+                }
+            __syncthreads();
+            if (d.x == 0.0 && d.y == 0.0) {
+                sing = true;
+                break;
+            }
+            // 1/d = conj(d) / |d|^2
+            const double m2 = fma(d.x, d.x, d.y * d.y);
+            const double2 inv = make_double2(d.x / m2, -d.y / m2);
+            for (int j = tid; j < n; j += kSlaterThreads) {
+                const double2 r = cmul(j == k ? make_double2(1.0, 0.0) : A[k * ns + j], inv);
+                rowk[j] = r;
+                A[k * ns + j] = r;
+            }
+            for (int i = tid; i < n; i += kSlaterThreads)
+                if (i != k) fcol[i] = A[i * ns + k];
+            __syncthreads();
+            for (int i = wid; i < n; i += kSlaterThreads / 32) {
+                if (i == k) continue;
+                const double2 f = fcol[i];
+                for (int j = lane; j < n; j += 32) {
+                    const double2 x = (j == k) ? make_double2(0.0, 0.0) : A[i * ns + j];
+                    const double2 r = rowk[j];
+                    A[i * ns + j] = make_double2(x.x - fma(f.x, r.x, -f.y * r.y), x.y - fma(f.x, r.y, f.y * r.x));
+                }
+            }
+            __syncthreads();
+        }
+        if (sing) {
+            singular = true;
+            break;
+        }
+        {   // ln|det| and the phase from the pivots and the row swaps
+            double lp = 0.0, ap = 0.0;
+            int swaps = 0;
+            for (int k = tid; k < n; k += kSlaterThreads) {
+                const double2 z = pivd[k];
+                lp += 0.5 * log(fma(z.x, z.x, z.y * z.y));
+                ap += atan2(z.y, z.x);
+                swaps += piv[k] != k;
+            }
+            logdet += block_sum(lp, red);
+            arg += block_sum(ap, red);
+            if (((long long)block_sum((double)swaps, red)) & 1) arg += M_PI;
+        }
+        if (tid == 0) {
+            for (int c = 0; c < n; ++c) colmap[c] = c;
+            for (int k = n - 1; k >= 0; --k) {
+                const int t = colmap[k];
+                colmap[k] = colmap[piv[k]];
+                colmap[piv[k]] = t;
+            }
+        }
+        __syncthreads();
+        if (a.kinetic) {   // T_s = -1/2 sum_ij (A^-1)_ji L_ij
+            double pr = 0.0, pi = 0.0;
+            for (int i = wid; i < n; i += kSlaterThreads / 32) {
+                const int ci = colmap[i];
+                for (int j = lane; j < n; j += 32) {
+                    const double2 t = cmul(A[j * ns + ci], ldc<T>(a.lap, (base + i) * O + j));
+                    pr += t.x;
+                    pi += t.y;
+                }
+            }
+            kin.x += -0.5 * block_sum(pr, red);
+            kin.y += -0.5 * block_sum(pi, red);
+        }
+        if (a.drift) {
+            for (int ic = wid; ic < 3 * n; ic += kSlaterThreads / 32) {
+                const int i = ic / 3, c = ic - (ic / 3) * 3;
+                const int ci = colmap[i];
+                double sr = 0.0, si = 0.0;
+                for (int j = lane; j < n; j += 32) {
+                    const double2 t = cmul(A[j * ns + ci], ldc<T>(a.grad, ((base + i) * 3 + c) * O + j));
+                    sr += t.x;
+                    si += t.y;
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, off);
+                    si += __shfl_xor_sync(0xffffffffu, si, off);
+                }
+                if (lane == 0) {
+                    double* q = a.drift + 2 * (((w * a.n_elec) + e0 + i) * 3 + c);
+                    q[0] = sr;
+                    q[1] = si;
+                }
+            }
+        }
+    }
+    if (tid == 0) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        const double inf = __longlong_as_double(0x7ff0000000000000LL);
+        if (a.logdet) a.logdet[w] = singular ? -inf : logdet;
+        if (a.sign) {
+            double sn, cs;
+            sincos(arg, &sn, &cs);
+            a.sign[2 * w] = singular ? 0.0 : cs;
+            a.sign[2 * w + 1] = singular ? 0.0 : sn;
+        }
+        if (a.kinetic) {
+            a.kinetic[2 * w] = singular ? nan : kin.x;
+            a.kinetic[2 * w + 1] = singular ? nan : kin.y;
+        }
+    }
+    if (singular && a.drift) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        for (int e = tid; e < 6 * a.n_elec; e += kSlaterThreads) a.drift[w * a.n_elec * 6 + e] = nan;
+    }
+}
+
+template <typename T>
+int launch_slater_complex(const SlaterArgs& a, int nmax, cudaStream_t st)
+{
+    const size_t smem = (size_t)nmax * (nmax + 1) * sizeof(double2);
+    cudaError_t e = cudaFuncSetAttribute(slater_complex_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(slater_complex_kernel)");
+    slater_complex_kernel<T><<<(unsigned)a.n_walkers, kSlaterThreads, smem, st>>>(a);
+    return cuda_error(cudaGetLastError(), "slater_complex_kernel launch");
+}
+
 template <typename T>
 int launch_slater(const SlaterArgs& a, int nmax, cudaStream_t st)
 {
@@ -500,15 +711,20 @@ extern "C" int qmcspl_slater_kinetic(const void* val, const void* grad, const vo
                                      long long n_walkers, int n_elec, int n_up, int n_orb, double* logdet,
                                      double* sign, double* kinetic, double* drift, void* stream)
 {
-    if (dtype != 0 && dtype != 1) return set_error(QMCSPL_ERR_ARG, "dtype must be 0 (double) or 1 (float)");
+    if (dtype < 0 || dtype > 3)
+        return set_error(QMCSPL_ERR_ARG, "dtype must be 0 (double), 1 (float), 2 (complex double) or 3 (complex float)");
     if (arith != QMCSPL_SLATER_FP64 && arith != QMCSPL_SLATER_DF64)
         return set_error(QMCSPL_ERR_ARG, "arith must be QMCSPL_SLATER_FP64 or QMCSPL_SLATER_DF64");
+    const bool cplx = dtype >= 2;
+    if (cplx && arith != QMCSPL_SLATER_FP64)
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "complex orbitals are eliminated in FP64 (QMCSPL_SLATER_FP64)");
     if (n_walkers < 0) return set_error(QMCSPL_ERR_ARG, "n_walkers < 0");
     if (n_elec < 1 || n_up < 0 || n_up > n_elec) return set_error(QMCSPL_ERR_ARG, "need n_elec >= 1, 0 <= n_up <= n_elec");
     const int n_dn = n_elec - n_up;
     const int nmax = n_up > n_dn ? n_up : n_dn;
-    if (nmax > kSlaterMaxBlock)
-        return set_error(QMCSPL_ERR_UNSUPPORTED, "spin block larger than QMCSPL_SLATER_MAX_BLOCK");
+    if (nmax > (cplx ? kSlaterCplxMaxBlock : kSlaterMaxBlock))
+        return set_error(QMCSPL_ERR_UNSUPPORTED, cplx ? "spin block larger than QMCSPL_SLATER_MAX_COMPLEX_BLOCK"
+                                                      : "spin block larger than QMCSPL_SLATER_MAX_BLOCK");
     if (n_orb < nmax) return set_error(QMCSPL_ERR_ARG, "n_orb (the output row length) is smaller than a spin block");
     if (!val) return set_error(QMCSPL_ERR_ARG, "val is NULL");
     if (kinetic && !lap) return set_error(QMCSPL_ERR_ARG, "kinetic needs lap");
@@ -529,5 +745,10 @@ extern "C" int qmcspl_slater_kinetic(const void* val, const void* grad, const vo
     a.drift = drift;
     a.arith = arith;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    return dtype == 0 ? launch_slater<double>(a, nmax, st) : launch_slater<float>(a, nmax, st);
+    switch (dtype) {
+    case 0: return launch_slater<double>(a, nmax, st);
+    case 1: return launch_slater<float>(a, nmax, st);
+    case 2: return launch_slater_complex<double>(a, nmax, st);
+    default: return launch_slater_complex<float>(a, nmax, st);
+    }
 }

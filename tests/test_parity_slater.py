@@ -1,5 +1,5 @@
 """GPU Slater-determinant consumer (qmcspl_slater_kinetic) against the oracle's definition
-(numpy slogdet / inv) on the same orbital outputs."""
+(numpy slogdet / inv) on the same orbital outputs, real and complex (Bloch orbitals)."""
 import numpy as np
 import pytest
 
@@ -101,3 +101,63 @@ def test_consumer_c3_mgo64_full_batch(arith):
     ref = oracle.slater_kinetic(vr, gr, lr, len(sample), n_elec, n_elec // 2)
     compare(tuple(x[sample] for x in got), ref, rel=1e-8)
     spl.close()
+
+
+# ---------------------------------------------------------------------------
+# complex orbitals (outputs of a Bloch handle): complex determinants, FP64 elimination
+# ---------------------------------------------------------------------------
+
+def compare_complex(got, ref, rel=1e-9):
+    ld, sg, kin, dr = got
+    rld, rsg, rkin, rdr = ref
+    assert np.max(np.abs(ld - rld)) <= rel * max(1.0, np.max(np.abs(rld)))
+    assert np.max(np.abs(sg - rsg)) <= rel * 100
+    assert oracle.relative_error(kin, rkin) < rel * 10
+    assert oracle.relative_error(dr, rdr) < rel * 10
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("n_elec,n_up,n_orb", [(13, 7, 9), (8, 0, 8), (2, 1, 3), (40, 20, 24)])
+def test_complex_consumer_matches_oracle(storage, n_elec, n_up, n_orb):
+    k = inputs.KPOINTS["generic"]
+    dims = (12, 12, 12)
+    lat, mil, coef = inputs.random_bloch_cell(1900 + n_elec, n_orb, 8.0, 6.0, k, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=True, kpoint=k)
+    W = 6
+    pos = inputs.positions(lat, W * n_elec, 1901 + n_elec, -1, 2)
+    v, g, l = spl.eval_vgl(torch.from_numpy(pos).to(dev()))
+    spl.sync()
+    assert v.is_complex()
+    got = consumer(v, g, l, W, n_elec, n_up, arith="f64")
+    ref = oracle.slater_kinetic(v.cpu().numpy().astype(np.complex128), g.cpu().numpy().astype(np.complex128),
+                                l.cpu().numpy().astype(np.complex128), W, n_elec, n_up)
+    compare_complex(got, ref)
+    spl.close()
+
+
+def test_complex_consumer_largest_block_singular_walker_and_rejections():
+    from paper_1309_6250_gb300 import _lib
+    from paper_1309_6250_gb300.api import slater_kinetic
+    n = _lib.SLATER_MAX_COMPLEX_BLOCK
+    rng = np.random.default_rng(1910)
+    W, n_elec = 3, 2 * n
+    c = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    val = c(W * n_elec, n) + 4.0 * np.tile(np.eye(n), (2 * W, 1))
+    grad = c(W * n_elec, 3, n)
+    lap = c(W * n_elec, n)
+    val[2 * n_elec + n + 3] = 0.0                  # walker 2, down block: zero row
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+    ld, sg, kin, dr = consumer(tt(val), tt(grad), tt(lap), W, n_elec, n, "f64")
+    assert sg[2] == 0 and ld[2] == -np.inf and np.isnan(kin[2]) and np.all(np.isnan(dr[2]))
+    keep = [0, 1]
+    rows = np.concatenate([np.arange(w * n_elec, (w + 1) * n_elec) for w in keep])
+    ref = oracle.slater_kinetic(val[rows], grad[rows], lap[rows], 2, n_elec, n)
+    compare_complex((ld[keep], sg[keep], kin[keep], dr[keep]), ref)
+    v = tt(val[: 2 * n])
+    big = torch.zeros((2 * (n + 1), n + 1), dtype=torch.complex128, device=dev())
+    with pytest.raises(_lib.QmcsplError) as ei:
+        slater_kinetic(big, None, big, 1, 2 * (n + 1), n + 1)          # a block over the limit
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
+    with pytest.raises(_lib.QmcsplError) as ei:
+        slater_kinetic(v, None, v, 1, 2 * n, n, arith="df64")            # complex in double-float
+    assert ei.value.code == _lib.ERR_UNSUPPORTED
