@@ -294,6 +294,50 @@ def bench_methods(args, dev, stream):
             "results": out}
 
 
+def bench_methods_c3(args, dev, stream, clocks=None):
+    """The paper's bases at the 128-orbital scale: MgO-like 64-atom cell, 96^3, 2048 walkers x
+    256 electrons, FP32 tables, cell order.  Per method the evaluation kernel's own time
+    (library CUDA events) and its gathered bytes against the L1/LSU data-path peak: smoothing
+    without the Laplacian table (Hessian Laplacian, 1 table), interpolating with it (2 tables),
+    Lagrange and B-splines with separate gradient tables (5 tables each), pp (8 points x 8
+    entries = 64 values, as one table)."""
+    import torch
+    from paper_1309_6250_gb300.api import OrbitalSplines
+    w = inputs.make_workload("c3")
+    pos = torch.from_numpy(w.pos).to(dev)
+    n_pos, n_orb = w.pos.shape[0], w.coef.shape[0]
+    evals = n_pos * n_orb
+    out = {}
+    for name, kw in (("smooth", dict(method="smooth", separate_lap=False)),
+                     ("interp_lap", dict(method="interp", separate_lap=True)),
+                     ("lagrange", dict(method="lagrange", separate_lap=True)),
+                     ("smooth_sep_grad", dict(method="smooth", separate_lap=True, separate_grad=True)),
+                     ("pp", dict(method="pp", separate_lap=False))):
+        spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, storage="f32", device=dev, **kw)
+        o = spl.alloc_outputs(n_pos)
+        step = lambda: spl.eval_vgl(pos, out=o)
+        for _ in range(3):
+            step()
+        torch.cuda.synchronize()
+        spl.profile(True)
+        ms = time_steps(step, max(5, args.steps // 40), 0, torch, stream)
+        prof = spl.profile_read()
+        spl.profile(False)
+        spl.sync()
+        k_s = prof["eval_ms"] * 1e-3 / max(1, prof["launches"])
+        n_tab = spl.info()["n_tables"]
+        bpe = algorithmic_bytes_per_eval("f32", n_tab, n_orb)
+        out[name] = {"value": evals / (sum(ms) / len(ms) * 1e-3), "ms_per_step": sum(ms) / len(ms),
+                     "eval_kernel_ms": k_s * 1e3, "tables": n_tab, "bytes_per_eval": bpe,
+                     "table_bytes": spl.info()["table_bytes"],
+                     "roofline_l1": l1_roofline(bpe * evals, k_s, clocks)}
+        del o
+        spl.close()
+        torch.cuda.empty_cache()
+    return {"workload": "c3 MgO-like 64-atom, 128 orbitals, 96^3, 2048 x 256 positions, f32 tables, cell order",
+            "unit": UNIT, "results": out}
+
+
 def bench_backward(args, dev, stream):
     """Adjoint pass on the Si-like 64-atom cell (128 orbitals, 72^3, FP32 tables with the
     Laplacian table, 4096 positions, N(0,1) upstream weights): coefficient scatter and
@@ -578,13 +622,14 @@ def run_ours(args):
                 "algorithmic_gbs": vb * evals_per_step / vk / 1e9,
                 "frac_of_hbm": vb * evals_per_step / vk / 1e9 / hbm}
 
-    batched = methods = backward = bloch = consumer = general = None
+    batched = methods = methods_c3 = backward = bloch = consumer = general = None
     if not args.no_variants and rank == 0:
         del outs
         spl.close()
         torch.cuda.empty_cache()
         batched = bench_batched(args, dev, stream)
         methods = bench_methods(args, dev, stream)
+        methods_c3 = bench_methods_c3(args, dev, stream, clocks)
         backward = bench_backward(args, dev, stream)
         bloch = bench_bloch(args, dev, stream)
         consumer = bench_consumer(args, dev, stream)
@@ -630,6 +675,7 @@ def run_ours(args):
         "variants": variants,
         "batched": batched,
         "methods_si8_48": methods,
+        "methods_mgo64_96": methods_c3,
         "backward_si64_72": backward,
         "bloch_mgo64_96": bloch,
         "slater_consumer_mgo64": consumer,
@@ -657,7 +703,8 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="time eager calls instead of CUDA-graph replays")
     ap.add_argument("--n-pos", type=int, default=None, help="use only the first N positions (profiling)")
     ap.add_argument("--only", default="all",
-                    choices=["all", "bloch", "consumer", "general", "methods", "batched", "backward"],
+                    choices=["all", "bloch", "consumer", "general", "methods", "methods_c3", "batched",
+                             "backward"],
                     help="run one secondary leg alone and print its JSON (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -666,7 +713,7 @@ def main():
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         leg = {"bloch": bench_bloch, "consumer": bench_consumer, "general": bench_general,
-               "methods": bench_methods, "batched": bench_batched, "backward": bench_backward}[args.only]
+               "methods": bench_methods, "methods_c3": bench_methods_c3, "batched": bench_batched, "backward": bench_backward}[args.only]
         print(json.dumps({"leg": args.only, **leg(args, dev, torch.cuda.current_stream())}), flush=True)
     else:
         run_ours(args)

@@ -51,86 +51,195 @@ __device__ __forceinline__ void value_weights(A t, A* w)
     }
 }
 
+// Scalar path (double tables): one warp task = the groups [w0, w0 + groups per warp).
 template <typename T, int BASIS>
-__global__ void __launch_bounds__(kEvalThreads, 2) five_table_vgl_kernel(const EvalArgs p)
+__device__ __forceinline__ void five_table_task(const EvalArgs& p, long long w0, int lane)
 {
     using A = typename Traits<T>::A;
     constexpr int E = Traits<T>::E;
-    const int lane = threadIdx.x & 31;
     const int L = 1 << p.lanes_log2;
     const int sub = lane & (L - 1);
     const int gbase = lane & ~(L - 1);
-    const int gpw = 32 >> p.lanes_log2;
     const long long total = p.n_pos * p.tiles;
-    const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
-    const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
     const size_t rowb = (size_t)p.row_stride * sizeof(T);
     const size_t colb = (size_t)p.col_stride * sizeof(T);
 
-    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
-        const long long gid = w0 + (lane >> p.lanes_log2);
-        const bool active = gid < total;
-        const long long q = active ? gid / p.tiles : 0;
-        const int tile = active ? (int)(gid - q * p.tiles) : 0;
-        const long long ip = active ? order_index(p, q) : q;
-        int ix, iy, iz;
-        A tx, ty, tz;
-        bool ok;
-        if constexpr (sizeof(A) == 8) coords_double(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
-        else coords_float(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
-        if (!active) continue;
-        if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
-        A lx[4], ly[4], lz[4];
-        value_weights<BASIS, A>((A)tx, lx);
-        value_weights<BASIS, A>((A)ty, ly);
-        value_weights<BASIS, A>((A)tz, lz);
-        const int chunk = tile * L + sub;
-        const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
-        A acc[5][E];
+    const long long gid = w0 + (lane >> p.lanes_log2);
+    const bool active = gid < total;
+    const long long q = active ? gid / p.tiles : 0;
+    const int tile = active ? (int)(gid - q * p.tiles) : 0;
+    const long long ip = active ? order_index(p, q) : q;
+    int ix, iy, iz;
+    A tx, ty, tz;
+    bool ok;
+    coords_double(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    if (!active) return;
+    if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+    A lx[4], ly[4], lz[4];
+    value_weights<BASIS, A>(tx, lx);
+    value_weights<BASIS, A>(ty, ly);
+    value_weights<BASIS, A>(tz, lz);
+    const int chunk = tile * L + sub;
+    const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
+    A acc[5][E];
 #pragma unroll
-        for (int k = 0; k < 5; ++k)
+    for (int k = 0; k < 5; ++k)
 #pragma unroll
-            for (int e = 0; e < E; ++e) acc[k][e] = A(0);
+        for (int e = 0; e < E; ++e) acc[k][e] = A(0);
 #pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const int x = wrap1(ix + l - 1, p.nx);
+    for (int l = 0; l < 4; ++l) {
+        const int x = wrap1(ix + l - 1, p.nx);
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int y = wrap1(iy + m - 1, p.ny);
-                const size_t col = (size_t)(x * p.ny + y) * colb + off;
-                const A wxy = lx[l] * ly[m];
+        for (int m = 0; m < 4; ++m) {
+            const int y = wrap1(iy + m - 1, p.ny);
+            const size_t col = (size_t)(x * p.ny + y) * colb + off;
+            const A wxy = lx[l] * ly[m];
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    const char* base = static_cast<const char*>(p.tab[k]) + col;
-                    uint4 raw[4];
+            for (int k = 0; k < 5; ++k) {
+                const char* base = static_cast<const char*>(p.tab[k]) + col;
+                uint4 raw[4];
 #pragma unroll
-                    for (int n = 0; n < 4; ++n) raw[n] = ldg_table(p, base + n * rowb);
-                    A a[E];
+                for (int n = 0; n < 4; ++n) raw[n] = ldg_table(p, base + n * rowb);
+                A a[E];
 #pragma unroll
-                    for (int e = 0; e < E; ++e) a[e] = A(0);
+                for (int e = 0; e < E; ++e) a[e] = A(0);
 #pragma unroll
-                    for (int n = 0; n < 4; ++n) {
-                        A c[E];
-                        unpack<T>(raw[n], c);
+                for (int n = 0; n < 4; ++n) {
+                    A c[E];
+                    unpack<T>(raw[n], c);
 #pragma unroll
-                        for (int e = 0; e < E; ++e) a[e] = fma(lz[n], c[e], a[e]);
-                    }
-#pragma unroll
-                    for (int e = 0; e < E; ++e) acc[k][e] = fma(wxy, a[e], acc[k][e]);
+                    for (int e = 0; e < E; ++e) a[e] = fma(lz[n], c[e], a[e]);
                 }
+#pragma unroll
+                for (int e = 0; e < E; ++e) acc[k][e] = fma(wxy, a[e], acc[k][e]);
             }
         }
-        const int o0 = chunk * E;
-        if (o0 >= p.n_orb) continue;
-        const bool vec = p.vec_out != 0;
-        // Bloch: the gradient and Laplacian tables hold the periodic parts of grad phi, lap phi
-        if (p.phase) bloch_apply<A, E>(p, ip, acc[0], acc + 1, acc[4], false, false);
-        if (p.val) store_run<A, E>(static_cast<A*>(p.val) + ip * p.n_orb + o0, acc[0], o0, p.n_orb, vec);
-        if (p.grad)
+    }
+    const int o0 = chunk * E;
+    if (o0 >= p.n_orb) return;
+    const bool vec = p.vec_out != 0;
+    // Bloch: the gradient and Laplacian tables hold the periodic parts of grad phi, lap phi
+    if (p.phase) bloch_apply<A, E>(p, ip, acc[0], acc + 1, acc[4], false, false);
+    if (p.val) store_run<A, E>(static_cast<A*>(p.val) + ip * p.n_orb + o0, acc[0], o0, p.n_orb, vec);
+    if (p.grad)
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                store_run<A, E>(static_cast<A*>(p.grad) + (ip * 3 + a) * p.n_orb + o0, acc[1 + a], o0, p.n_orb, vec);
-        if (p.lap) store_run<A, E>(static_cast<A*>(p.lap) + ip * p.n_orb + o0, acc[4], o0, p.n_orb, vec);
+        for (int a = 0; a < 3; ++a)
+            store_run<A, E>(static_cast<A*>(p.grad) + (ip * 3 + a) * p.n_orb + o0, acc[1 + a], o0, p.n_orb, vec);
+    if (p.lap) store_run<A, E>(static_cast<A*>(p.lap) + ip * p.n_orb + o0, acc[4], o0, p.n_orb, vec);
+}
+
+// float and bfloat16 tables: packed FP32 pairs (fma.rn.f32x2), and the 80 loads units of a
+// position (16 columns x 5 tables, four z rows each) walked through a ring of three, so two
+// units' rows are in flight while one is contracted.  Same products and sums, in the same
+// order, as the scalar path.
+template <typename T, int BASIS>
+__device__ __forceinline__ void five_table_task_x2(const EvalArgs& p, long long w0, int lane)
+{
+    constexpr int E = Traits<T>::E;
+    constexpr int NP = Pairs<T>::N;
+    constexpr int kUnits = 16 * 5;
+    constexpr int kRing = 3;
+    const int L = 1 << p.lanes_log2;
+    const int sub = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const long long total = p.n_pos * p.tiles;
+    const size_t rowb = (size_t)p.row_stride * sizeof(T);
+    const size_t colb = (size_t)p.col_stride * sizeof(T);
+
+    const long long gid = w0 + (lane >> p.lanes_log2);
+    const bool active = gid < total;
+    const long long q = active ? gid / p.tiles : 0;
+    const int tile = active ? (int)(gid - q * p.tiles) : 0;
+    const long long ip = active ? order_index(p, q) : q;
+    int ix, iy, iz;
+    float tx, ty, tz;
+    bool ok;
+    coords_float(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    if (!active) return;
+    if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+    float lx[4], ly[4], lz[4];
+    value_weights<BASIS, float>(tx, lx);
+    value_weights<BASIS, float>(ty, ly);
+    value_weights<BASIS, float>(tz, lz);
+    f32x2 lz2[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) lz2[n] = pack2(lz[n], lz[n]);
+    int xs[4], ys[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        xs[j] = wrap1(ix + j - 1, p.nx);
+        ys[j] = wrap1(iy + j - 1, p.ny);
+    }
+    const int chunk = tile * L + sub;
+    const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
+    auto load_unit = [&](int u, uint4* dst) {
+        const int c = u / 5, k = u - 5 * (u / 5);
+        const char* base = static_cast<const char*>(p.tab[k]) + (size_t)(xs[c >> 2] * p.ny + ys[c & 3]) * colb + off;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) dst[n] = ldg_table(p, base + n * rowb);
+    };
+    f32x2 ACC[5][NP];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) ACC[k][j] = 0ull;
+    uint4 ring[kRing][4];
+    load_unit(0, ring[0]);
+    load_unit(1, ring[1]);
+#pragma unroll
+    for (int u = 0; u < kUnits; ++u) {
+        if (u + 2 < kUnits) load_unit(u + 2, ring[(u + 2) % kRing]);
+        const int c = u / 5, k = u - 5 * (u / 5);
+        f32x2 a[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) a[j] = 0ull;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            f32x2 cv[NP];
+            Pairs<T>::get(ring[u % kRing][n], cv);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) a[j] = ffma2(lz2[n], cv[j], a[j]);
+        }
+        const float wxy = lx[c >> 2] * ly[c & 3];
+        const f32x2 W = pack2(wxy, wxy);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) ACC[k][j] = ffma2(W, a[j], ACC[k][j]);
+    }
+    const int o0 = chunk * E;
+    if (o0 >= p.n_orb) return;
+    const bool vec = p.vec_out != 0;
+    float acc[5][E];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int j = 0; j < NP; ++j) unpack2(ACC[k][j], acc[k][2 * j], acc[k][2 * j + 1]);
+    if (p.phase) bloch_apply<float, E>(p, ip, acc[0], acc + 1, acc[4], false, false);
+    if (p.val) store_run<float, E>(static_cast<float*>(p.val) + ip * p.n_orb + o0, acc[0], o0, p.n_orb, vec);
+    if (p.grad)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            store_run<float, E>(static_cast<float*>(p.grad) + (ip * 3 + a) * p.n_orb + o0, acc[1 + a], o0,
+                                p.n_orb, vec);
+    if (p.lap) store_run<float, E>(static_cast<float*>(p.lap) + ip * p.n_orb + o0, acc[4], o0, p.n_orb, vec);
+}
+
+#ifndef QMCSPL_FIVE_THREADS
+#define QMCSPL_FIVE_THREADS 512
+#endif
+// Five-table and pp kernels: one block of QMCSPL_FIVE_THREADS per SM, as the B-spline kernel: the warps of an SM evaluate consecutive
+// (cell-ordered, neighbouring) positions, whose stencil rows then hit in that SM's L1.
+template <typename T, int BASIS, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) five_table_vgl_kernel(const EvalArgs p)
+{
+    constexpr int WPB = THREADS / 32;
+    const int lane = threadIdx.x & 31;
+    const int gpw = 32 >> p.lanes_log2;
+    const long long total = p.n_pos * p.tiles;
+    const long long warp = (long long)blockIdx.x * WPB + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * WPB;
+    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
+        if constexpr (sizeof(T) == 8) five_table_task<T, BASIS>(p, w0, lane);
+        else five_table_task_x2<T, BASIS>(p, w0, lane);
     }
 }
 
@@ -153,24 +262,21 @@ __device__ __forceinline__ void pp_weights(A t, A w[2][2], A dw[2][2], A d2w[2][
     d2w[1][1] = t;
 }
 
+// Scalar path (double tables): one warp task = the groups [w0, w0 + groups per warp).
 template <typename T>
-__global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs p)
+__device__ __forceinline__ void pp_task(const EvalArgs& p, long long w0, int lane)
 {
     using A = typename Traits<T>::A;
     constexpr int E = Traits<T>::E;
-    const int lane = threadIdx.x & 31;
     const int L = 1 << p.lanes_log2;
     const int sub = lane & (L - 1);
     const int gbase = lane & ~(L - 1);
-    const int gpw = 32 >> p.lanes_log2;
     const long long total = p.n_pos * p.tiles;
-    const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
-    const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
     const size_t rowb = (size_t)p.row_stride * sizeof(T);     // one z row: 8 entries x O_p
     const size_t entb = rowb / 8;                              // one entry: O_p
     const size_t colb = (size_t)p.col_stride * sizeof(T);
 
-    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
+    {
         const long long gid = w0 + (lane >> p.lanes_log2);
         const bool active = gid < total;
         const long long q = active ? gid / p.tiles : 0;
@@ -181,7 +287,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs 
         bool ok;
         if constexpr (sizeof(A) == 8) coords_double(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
         else coords_float(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
-        if (!active) continue;
+        if (!active) return;
         if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
         A wx[2][2], dwx[2][2], d2wx[2][2], wy[2][2], dwy[2][2], d2wy[2][2], wz[2][2], dwz[2][2], d2wz[2][2];
         pp_weights<A>((A)tx, wx, dwx, d2wx);
@@ -241,7 +347,7 @@ __global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs 
             }
         }
         const int o0 = chunk * E;
-        if (o0 >= p.n_orb) continue;
+        if (o0 >= p.n_orb) return;
         const bool vec = p.vec_out != 0;
         A cg[3][E];
 #pragma unroll
@@ -263,26 +369,181 @@ __global__ void __launch_bounds__(kEvalThreads, 2) pp_vgl_kernel(const EvalArgs 
     }
 }
 
-template <template <typename> class K, typename T>
-int launch_variant(void (*kernel)(EvalArgs), const EvalArgs& a, cudaStream_t st, const char* name)
+// float and bfloat16 tables: packed FP32 pairs, the 16 load units of a position (2 x 2
+// corner columns x 4 (kappa, mu) labels, four rows each: 2 z corners x 2 nu labels) through a
+// ring of three.  Same products and sums, in the same order, as the scalar path.
+template <typename T>
+__device__ __forceinline__ void pp_task_x2(const EvalArgs& p, long long w0, int lane)
+{
+    constexpr int E = Traits<T>::E;
+    constexpr int NP = Pairs<T>::N;
+    constexpr int kUnits = 16;
+    constexpr int kRing = 3;
+    const int L = 1 << p.lanes_log2;
+    const int sub = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const long long total = p.n_pos * p.tiles;
+    const size_t rowb = (size_t)p.row_stride * sizeof(T);     // one z row: 8 entries x O_p
+    const size_t entb = rowb / 8;                              // one entry: O_p
+    const size_t colb = (size_t)p.col_stride * sizeof(T);
+
+    const long long gid = w0 + (lane >> p.lanes_log2);
+    const bool active = gid < total;
+    const long long q = active ? gid / p.tiles : 0;
+    const int tile = active ? (int)(gid - q * p.tiles) : 0;
+    const long long ip = active ? order_index(p, q) : q;
+    int ix, iy, iz;
+    float tx, ty, tz;
+    bool ok;
+    coords_float(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    if (!active) return;
+    if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+    float wx[2][2], dwx[2][2], d2wx[2][2], wy[2][2], dwy[2][2], d2wy[2][2], wz[2][2], dwz[2][2], d2wz[2][2];
+    pp_weights<float>(tx, wx, dwx, d2wx);
+    pp_weights<float>(ty, wy, dwy, d2wy);
+    pp_weights<float>(tz, wz, dwz, d2wz);
+    f32x2 wz2[2][2], dwz2[2][2], d2wz2[2][2];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            wz2[a][b] = pack2(wz[a][b], wz[a][b]);
+            dwz2[a][b] = pack2(dwz[a][b], dwz[a][b]);
+            d2wz2[a][b] = pack2(d2wz[a][b], d2wz[a][b]);
+        }
+    const float ml0 = p.mlf[0], ml1 = p.mlf[1], ml2 = p.mlf[2];
+    const float ml3 = p.mlf[3], ml4 = p.mlf[4], ml5 = p.mlf[5];
+    const int chunk = tile * L + sub;
+    const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
+    const int xs[2] = {ix, ix + 1 < p.nx ? ix + 1 : 0};
+    const int ys[2] = {iy, iy + 1 < p.ny ? iy + 1 : 0};
+    // unit u: column (i, j) = (u >> 3, (u >> 2) & 1), label km = u & 3; its rows
+    // n = 0..3 are (z corner k, label nu) = (n >> 1, n & 1), entry 4 kappa + 2 mu + nu = 2 km + nu
+    auto load_unit = [&](int u, uint4* dst) {
+        const int i = u >> 3, j = (u >> 2) & 1, km = u & 3;
+        const char* col = static_cast<const char*>(p.tab[0]) + (size_t)(xs[i] * p.ny + ys[j]) * colb + off +
+                          (size_t)(2 * km) * entb;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) dst[n] = ldg_table(p, col + (n >> 1) * rowb + (size_t)(n & 1) * entb);
+    };
+    f32x2 V[NP], GX[NP], GY[NP], GZ[NP], LP[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) V[j] = GX[j] = GY[j] = GZ[j] = LP[j] = 0ull;
+    uint4 ring[kRing][4];
+    load_unit(0, ring[0]);
+    load_unit(1, ring[1]);
+#pragma unroll
+    for (int u = 0; u < kUnits; ++u) {
+        if (u + 2 < kUnits) load_unit(u + 2, ring[(u + 2) % kRing]);
+        const int i = u >> 3, j = (u >> 2) & 1, km = u & 3;
+        const int kap = km >> 1, mu = km & 1;
+        f32x2 a0[NP], a1[NP], a2[NP];
+#pragma unroll
+        for (int e = 0; e < NP; ++e) a0[e] = a1[e] = a2[e] = 0ull;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            const int k = n >> 1, nu = n & 1;
+            f32x2 cv[NP];
+            Pairs<T>::get(ring[u % kRing][n], cv);
+#pragma unroll
+            for (int e = 0; e < NP; ++e) {
+                a0[e] = ffma2(wz2[nu][k], cv[e], a0[e]);
+                a1[e] = ffma2(dwz2[nu][k], cv[e], a1[e]);
+                a2[e] = ffma2(d2wz2[nu][k], cv[e], a2[e]);
+            }
+        }
+        const float w00 = wx[kap][i] * wy[mu][j];
+        const float w10 = dwx[kap][i] * wy[mu][j];
+        const float w01 = wx[kap][i] * dwy[mu][j];
+        const float c0 = ml0 * (d2wx[kap][i] * wy[mu][j]) + ml1 * (wx[kap][i] * d2wy[mu][j]) +
+                         ml3 * (dwx[kap][i] * dwy[mu][j]);
+        const float c1 = ml4 * w10 + ml5 * w01;
+        const float c2 = ml2 * w00;
+        const f32x2 W00 = pack2(w00, w00), W10 = pack2(w10, w10), W01 = pack2(w01, w01);
+        const f32x2 C0 = pack2(c0, c0), C1 = pack2(c1, c1), C2 = pack2(c2, c2);
+#pragma unroll
+        for (int e = 0; e < NP; ++e) {
+            V[e] = ffma2(W00, a0[e], V[e]);
+            GX[e] = ffma2(W10, a0[e], GX[e]);
+            GY[e] = ffma2(W01, a0[e], GY[e]);
+            GZ[e] = ffma2(W00, a1[e], GZ[e]);
+            LP[e] = ffma2(C0, a0[e], ffma2(C1, a1[e], ffma2(C2, a2[e], LP[e])));
+        }
+    }
+    const int o0 = chunk * E;
+    if (o0 >= p.n_orb) return;
+    const bool vec = p.vec_out != 0;
+    float v[E], gx[E], gy[E], gz[E], lp[E];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        unpack2(V[j], v[2 * j], v[2 * j + 1]);
+        unpack2(GX[j], gx[2 * j], gx[2 * j + 1]);
+        unpack2(GY[j], gy[2 * j], gy[2 * j + 1]);
+        unpack2(GZ[j], gz[2 * j], gz[2 * j + 1]);
+        unpack2(LP[j], lp[2 * j], lp[2 * j + 1]);
+    }
+    float cg[3][E];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float m0 = p.mgf[3 * a], m1 = p.mgf[3 * a + 1], m2 = p.mgf[3 * a + 2];
+#pragma unroll
+        for (int e = 0; e < E; ++e) cg[a][e] = fmaf(m0, gx[e], fmaf(m1, gy[e], m2 * gz[e]));
+    }
+    if (p.phase) bloch_apply<float, E>(p, ip, v, cg, lp, true, true);
+    if (p.val) store_run<float, E>(static_cast<float*>(p.val) + ip * p.n_orb + o0, v, o0, p.n_orb, vec);
+    if (p.grad) {
+        float* g = static_cast<float*>(p.grad) + ip * 3 * p.n_orb + o0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) store_run<float, E>(g + (size_t)a * p.n_orb, cg[a], o0, p.n_orb, vec);
+    }
+    if (p.lap) store_run<float, E>(static_cast<float*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
+}
+
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) pp_vgl_kernel(const EvalArgs p)
+{
+    constexpr int WPB = THREADS / 32;
+    const int lane = threadIdx.x & 31;
+    const int gpw = 32 >> p.lanes_log2;
+    const long long total = p.n_pos * p.tiles;
+    const long long warp = (long long)blockIdx.x * WPB + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * WPB;
+    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
+        if constexpr (sizeof(T) == 8) pp_task<T>(p, w0, lane);
+        else pp_task_x2<T>(p, w0, lane);
+    }
+}
+
+template <typename K>
+int launch_one_block_per_sm(K kernel, int threads, const EvalArgs& a, cudaStream_t st, const char* name)
 {
     const int gpw = 32 >> a.lanes_log2;
-    const long long groups = a.n_pos * a.tiles;
-    const long long warps = (groups + gpw - 1) / gpw;
-    long long blocks = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
+    const long long warps = (a.n_pos * a.tiles + gpw - 1) / gpw;
+    long long blocks = (warps + threads / 32 - 1) / (threads / 32);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kEvalThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
     if (e != cudaSuccess) return cuda_error(e, "occupancy query");
     if (per_sm < 1) per_sm = 1;
     const long long cap = (long long)sm_count() * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    kernel<<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
+    kernel<<<(unsigned)blocks, threads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), name);
 }
 
-template <typename T> struct FiveK {};
-template <typename T> struct PPK {};
+template <typename T, int BASIS>
+int launch_five(const EvalArgs& a, cudaStream_t st)
+{
+    return launch_one_block_per_sm(five_table_vgl_kernel<T, BASIS, QMCSPL_FIVE_THREADS>, QMCSPL_FIVE_THREADS, a, st,
+                                   "five_table_vgl_kernel launch");
+}
+
+template <typename T>
+int launch_pp(const EvalArgs& a, cudaStream_t st)
+{
+    return launch_one_block_per_sm(pp_vgl_kernel<T, QMCSPL_FIVE_THREADS>, QMCSPL_FIVE_THREADS, a, st,
+                                   "pp_vgl_kernel launch");
+}
 
 EvalArgs make_args(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
                    void* grad, void* lap)
@@ -309,21 +570,12 @@ int launch_five_table_vgl(const Handle* h, const double* pos, const Prepared& pr
                           void* grad, void* lap, cudaStream_t st)
 {
     const EvalArgs a = make_args(h, pos, pr, n_pos, val, grad, lap);
-    const char* name = "five_table_vgl_kernel";
-    if (h->method == QMCSPL_LAGRANGE) {
-        switch (h->storage) {
-        case QMCSPL_F64: return launch_variant<FiveK, double>(five_table_vgl_kernel<double, kFiveLagrange>, a, st, name);
-        case QMCSPL_F32: return launch_variant<FiveK, float>(five_table_vgl_kernel<float, kFiveLagrange>, a, st, name);
-        default:
-            return launch_variant<FiveK, __nv_bfloat16>(five_table_vgl_kernel<__nv_bfloat16, kFiveLagrange>, a, st,
-                                                        name);
-        }
-    }
+    const bool lag = h->method == QMCSPL_LAGRANGE;
     switch (h->storage) {
-    case QMCSPL_F64: return launch_variant<FiveK, double>(five_table_vgl_kernel<double, kFiveBSpline>, a, st, name);
-    case QMCSPL_F32: return launch_variant<FiveK, float>(five_table_vgl_kernel<float, kFiveBSpline>, a, st, name);
+    case QMCSPL_F64: return lag ? launch_five<double, kFiveLagrange>(a, st) : launch_five<double, kFiveBSpline>(a, st);
+    case QMCSPL_F32: return lag ? launch_five<float, kFiveLagrange>(a, st) : launch_five<float, kFiveBSpline>(a, st);
     default:
-        return launch_variant<FiveK, __nv_bfloat16>(five_table_vgl_kernel<__nv_bfloat16, kFiveBSpline>, a, st, name);
+        return lag ? launch_five<__nv_bfloat16, kFiveLagrange>(a, st) : launch_five<__nv_bfloat16, kFiveBSpline>(a, st);
     }
 }
 
@@ -332,9 +584,9 @@ int launch_pp_vgl(const Handle* h, const double* pos, const Prepared& pr, long l
 {
     const EvalArgs a = make_args(h, pos, pr, n_pos, val, grad, lap);
     switch (h->storage) {
-    case QMCSPL_F64: return launch_variant<PPK, double>(pp_vgl_kernel<double>, a, st, "pp_vgl_kernel");
-    case QMCSPL_F32: return launch_variant<PPK, float>(pp_vgl_kernel<float>, a, st, "pp_vgl_kernel");
-    default: return launch_variant<PPK, __nv_bfloat16>(pp_vgl_kernel<__nv_bfloat16>, a, st, "pp_vgl_kernel");
+    case QMCSPL_F64: return launch_pp<double>(a, st);
+    case QMCSPL_F32: return launch_pp<float>(a, st);
+    default: return launch_pp<__nv_bfloat16>(a, st);
     }
 }
 
