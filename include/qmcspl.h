@@ -391,8 +391,7 @@ int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void
  *          ordered walker-major, layouts [P][n_orb], [P][3][n_orb], [P][n_orb]; dtype 0 = double,
  *          1 = float (real orbitals), 2 = complex double, 3 = complex float (Bloch orbitals,
  *          the (re, im) layouts of a Bloch handle's outputs)
- *   arith  enum qmcspl_slater_arith (complex dtypes: QMCSPL_SLATER_FP64 only, else
- *          QMCSPL_ERR_UNSUPPORTED)
+ *   arith  enum qmcspl_slater_arith, for real and complex dtypes
  *   n_orb  the output row length O (orbitals), >= both block sizes
  *   n_up   0 .. n_elec; each block at most QMCSPL_SLATER_MAX_BLOCK electrons
  *          (QMCSPL_SLATER_MAX_COMPLEX_BLOCK for complex dtypes)
@@ -404,8 +403,8 @@ int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void
  *          double[n_walkers][n_elec][3][2]
  *   stream cudaStream_t; asynchronous
  * The inversion is Gauss-Jordan elimination with row pivoting in shared memory, one thread
- * block per walker, in FP64 or in double-float (arith); complex entries in FP64 with the
- * pivot of largest modulus.  An exactly singular block gives sign 0, logdet -inf and NaN
+ * block per walker, in FP64 or in double-float (arith); complex entries are pivoted on the
+ * largest modulus, and in double-float each of their parts is a float pair.  An exactly singular block gives sign 0, logdet -inf and NaN
  * kinetic energy and drift for that walker; nearly singular blocks lose accuracy as the
  * condition number grows.
  */

@@ -258,16 +258,16 @@ def slater_kinetic(val: torch.Tensor, grad: Optional[torch.Tensor], lap: Optiona
                    arith: Optional[str] = None):
     """Slater-determinant consumer of eval_vgl outputs (walker-major positions, electrons
     0..n_up-1 spin up): returns (logdet [W], sign [W], kinetic [W], drift [W, n_elec, 3] or
-    None) on the outputs' device.  Real outputs: float64 tensors; arith 'df64' (double-float
-    elimination on the FP32 pipe, the default) or 'f64'.  Complex outputs of a Bloch handle:
-    complex128 sign (the phase of the determinant), kinetic and drift, FP64 elimination."""
+    None) on the outputs' device.  arith 'df64' (double-float elimination on the FP32 pipe,
+    the default) or 'f64'.  Real outputs: float64 tensors.  Complex outputs of a Bloch handle:
+    complex128 sign (the phase of the determinant), kinetic and drift."""
     lib = _lib.load()
     cplx = val.dtype in (torch.complex64, torch.complex128)
     if val.dtype not in (torch.float32, torch.float64, torch.complex64, torch.complex128):
         raise ValueError("float32/float64 or complex64/complex128 orbital outputs expected")
     dtype = {torch.float64: 0, torch.float32: 1, torch.complex128: 2, torch.complex64: 3}[val.dtype]
     if arith is None:
-        arith = "f64" if cplx else "df64"
+        arith = "df64"
     for t in (grad, lap):
         if t is not None and (t.dtype != val.dtype or t.device != val.device):
             raise ValueError("val, grad and lap must share dtype and device")

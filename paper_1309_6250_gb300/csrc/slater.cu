@@ -22,7 +22,8 @@
 // a pair of floats (hi + lo, ~48 significant bits) and each elimination update is an
 // error-free FP32 multiply-add done two columns at a time with fma.rn.f32x2 (see df_fma2):
 // the FP32 pipe carries it, several times faster on this part.  Every loop is bounded by n.
-// Complex orbitals (Bloch functions) take a complex FP64 elimination (slater_complex_kernel).
+// Complex orbitals (Bloch functions) take a complex elimination, in FP64 (slater_complex_kernel)
+// or in double-float (slater_cdf_kernel).
 #include <cmath>
 
 #include "eval_common.cuh"
@@ -673,9 +674,300 @@ __global__ void __launch_bounds__(kSlaterThreads) slater_complex_kernel(const Sl
     }
 }
 
+// Complex entries in double-float: four float arrays Rh, Rl, Ih, Il of [n][ns] (real and
+// imaginary parts, each a pair h + l), ns = n rounded up to even, plus 2, as in
+// slater_df_kernel.  The update A[i][j] -= f_i r_j of a complex multiplier f and row entry r is
+// four error-free packed multiply-adds (re += (-f.re) r.re + f.im r.im, im += (-f.re) r.im +
+// (-f.im) r.re), renormalised; 1/d = conj(d) / |d|^2 with the double-float reciprocal.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 1) slater_cdf_kernel(const SlaterArgs a)
+{
+    extern __shared__ float csf[];
+    __shared__ double red[NT / 32];
+    __shared__ int piv[kSlaterCplxMaxBlock];
+    __shared__ int colmap[kSlaterCplxMaxBlock];
+    // per row: -f.re as (wh, wl, -wh), +f.im as (wh, wl, -wh), and -f.im's low part
+    __shared__ f32x2 fw[7][kSlaterCplxMaxBlock];
+    __shared__ __align__(8) float rrh[kSlaterCplxMaxBlock + 2], rrl[kSlaterCplxMaxBlock + 2];
+    __shared__ __align__(8) float rih[kSlaterCplxMaxBlock + 2], ril[kSlaterCplxMaxBlock + 2];
+    __shared__ int s_p;
+    __shared__ float s_d[4];
+    __shared__ double2 pivd[kSlaterCplxMaxBlock];
+
+    const long long w = blockIdx.x;
+    if (w >= a.n_walkers) return;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    const long long O = a.n_orb;
+    double logdet = 0.0, arg = 0.0;
+    double2 kin = make_double2(0.0, 0.0);
+    bool singular = false;
+
+    for (int blk = 0; blk < 2; ++blk) {
+        const int e0 = blk == 0 ? 0 : a.n_up;
+        const int n = blk == 0 ? a.n_up : a.n_elec - a.n_up;
+        if (n == 0) continue;
+        const int nw = (n + 1) & ~1;
+        const int ns = nw + 2;
+        const long long base = w * a.n_elec + e0;
+        const size_t plane = (size_t)n * ns;
+        float* Rh = csf;
+        float* Rl = csf + plane;
+        float* Ih = csf + 2 * plane;
+        float* Il = csf + 3 * plane;
+
+        __syncthreads();
+        for (int i = wid; i < n; i += NT / 32)
+            for (int j = lane; j < ns; j += 32) {
+                const double2 z = j < n ? ldc<T>(a.val, (base + i) * O + j) : make_double2(0.0, 0.0);
+                const dfloat xr = df_from_double(z.x), xi = df_from_double(z.y);
+                Rh[i * ns + j] = xr.h;
+                Rl[i * ns + j] = xr.l;
+                Ih[i * ns + j] = xi.h;
+                Il[i * ns + j] = xi.l;
+            }
+        __syncthreads();
+
+        bool sing = false;
+        for (int k = 0; k < n; ++k) {
+            if (wid == 0) {   // pivot: largest |A[i][k]|^2 (high parts) over i >= k, first on ties
+                float best = -1.0f;
+                int bi = k;
+                for (int i = k + lane; i < n; i += 32) {
+                    const float re = Rh[i * ns + k], im = Ih[i * ns + k];
+                    const float v = fmaf(re, re, im * im);
+                    if (v > best) {
+                        best = v;
+                        bi = i;
+                    }
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+                    if (ob > best || (ob == best && oi < bi)) {
+                        best = ob;
+                        bi = oi;
+                    }
+                }
+                if (lane == 0) {
+                    s_p = bi;
+                    s_d[0] = Rh[bi * ns + k];
+                    s_d[1] = Rl[bi * ns + k];
+                    s_d[2] = Ih[bi * ns + k];
+                    s_d[3] = Il[bi * ns + k];
+                    piv[k] = bi;
+                    pivd[k] = make_double2((double)s_d[0] + (double)s_d[1], (double)s_d[2] + (double)s_d[3]);
+                }
+            }
+            __syncthreads();
+            const int p = s_p;
+            const dfloat dr = {s_d[0], s_d[1]}, di = {s_d[2], s_d[3]};
+            if (p != k)
+                for (int j = tid; j < nw; j += NT) {
+                    float* arr[4] = {Rh, Rl, Ih, Il};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float t = arr[q][k * ns + j];
+                        arr[q][k * ns + j] = arr[q][p * ns + j];
+                        arr[q][p * ns + j] = t;
+                    }
+                }
+            __syncthreads();
+            if (dr.h == 0.0f && di.h == 0.0f) {   // exactly singular (uniform)
+                sing = true;
+                break;
+            }
+            // 1/d = (d.re - i d.im) / |d|^2
+            const dfloat m2 = df_add(df_mul(dr, dr), df_mul(di, di));
+            const dfloat rm = df_recip(m2);
+            const dfloat ir = df_mul(dr, rm), ii = df_neg(df_mul(di, rm));
+            for (int j = tid; j < nw; j += NT) {
+                const dfloat xr = (j == k) ? dfloat{1.0f, 0.0f} : dfloat{Rh[k * ns + j], Rl[k * ns + j]};
+                const dfloat xi = (j == k) ? dfloat{0.0f, 0.0f} : dfloat{Ih[k * ns + j], Il[k * ns + j]};
+                const dfloat zr = df_add(df_mul(xr, ir), df_neg(df_mul(xi, ii)));
+                const dfloat zi = df_add(df_mul(xr, ii), df_mul(xi, ir));
+                rrh[j] = zr.h;
+                rrl[j] = zr.l;
+                rih[j] = zi.h;
+                ril[j] = zi.l;
+                Rh[k * ns + j] = zr.h;
+                Rl[k * ns + j] = zr.l;
+                Ih[k * ns + j] = zi.h;
+                Il[k * ns + j] = zi.l;
+            }
+            // the multipliers of the other rows, packed for the update; their pivot-column
+            // entries set to 0 so that the update leaves -f_i / d there (Gauss-Jordan)
+            for (int i = tid; i < n; i += NT)
+                if (i != k) {
+                    const float frh = Rh[i * ns + k], frl = Rl[i * ns + k];
+                    const float fih = Ih[i * ns + k], fil = Il[i * ns + k];
+                    Rh[i * ns + k] = 0.0f;
+                    Rl[i * ns + k] = 0.0f;
+                    Ih[i * ns + k] = 0.0f;
+                    Il[i * ns + k] = 0.0f;
+                    fw[0][i] = pack2(-frh, -frh);
+                    fw[1][i] = pack2(-frl, -frl);
+                    fw[2][i] = pack2(frh, frh);
+                    fw[3][i] = pack2(fih, fih);
+                    fw[4][i] = pack2(fil, fil);
+                    fw[5][i] = pack2(-fih, -fih);
+                    fw[6][i] = pack2(-fil, -fil);
+                }
+            __syncthreads();
+            {   // a lane holds one column pair of the pivot row and updates R rows
+                constexpr int R = 4, NW = NT / 32;
+                const f32x2* brh = reinterpret_cast<const f32x2*>(rrh);
+                const f32x2* brl = reinterpret_cast<const f32x2*>(rrl);
+                const f32x2* bih = reinterpret_cast<const f32x2*>(rih);
+                const f32x2* bil = reinterpret_cast<const f32x2*>(ril);
+                const int np = nw / 2;
+                for (int m = lane; m < np; m += 32) {
+                    const f32x2 Brh = brh[m], Brl = brl[m], Bih = bih[m], Bil = bil[m];
+                    for (int ib = wid; ib < n; ib += R * NW) {
+                        f32x2 Xrh[R], Xrl[R], Xih[R], Xil[R];
+                        bool act[R];
+#pragma unroll
+                        for (int u = 0; u < R; ++u) {
+                            const int i = ib + u * NW;
+                            act[u] = i < n && i != k;
+                            Xrh[u] = act[u] ? reinterpret_cast<const f32x2*>(Rh + i * ns)[m] : 0ull;
+                            Xrl[u] = act[u] ? reinterpret_cast<const f32x2*>(Rl + i * ns)[m] : 0ull;
+                            Xih[u] = act[u] ? reinterpret_cast<const f32x2*>(Ih + i * ns)[m] : 0ull;
+                            Xil[u] = act[u] ? reinterpret_cast<const f32x2*>(Il + i * ns)[m] : 0ull;
+                        }
+#pragma unroll
+                        for (int u = 0; u < R; ++u) {
+                            const int i = ib + u * NW;
+                            const int q = act[u] ? i : 0;
+                            const f32x2 nrh = fw[0][q], nrl = fw[1][q], prh = fw[2][q];
+                            const f32x2 pih = fw[3][q], pil = fw[4][q], nih = fw[5][q], nil = fw[6][q];
+                            df_fma2(Xrh[u], Xrl[u], nrh, nrl, prh, Brh, Brl);   // re += (-f.re) r.re
+                            df_fma2(Xrh[u], Xrl[u], pih, pil, nih, Bih, Bil);   // re += f.im r.im
+                            df_fma2(Xih[u], Xil[u], nrh, nrl, prh, Bih, Bil);   // im += (-f.re) r.im
+                            df_fma2(Xih[u], Xil[u], nih, nil, pih, Brh, Brl);   // im += (-f.im) r.re
+                            // renormalise both parts (two-sum), as in slater_df_kernel
+                            f32x2 S = add2(Xrh[u], Xrl[u]);
+                            f32x2 BB = sub2(S, Xrh[u]);
+                            Xrl[u] = add2(sub2(Xrh[u], sub2(S, BB)), sub2(Xrl[u], BB));
+                            Xrh[u] = S;
+                            S = add2(Xih[u], Xil[u]);
+                            BB = sub2(S, Xih[u]);
+                            Xil[u] = add2(sub2(Xih[u], sub2(S, BB)), sub2(Xil[u], BB));
+                            Xih[u] = S;
+                        }
+#pragma unroll
+                        for (int u = 0; u < R; ++u) {
+                            const int i = ib + u * NW;
+                            if (!act[u]) continue;
+                            reinterpret_cast<f32x2*>(Rh + i * ns)[m] = Xrh[u];
+                            reinterpret_cast<f32x2*>(Rl + i * ns)[m] = Xrl[u];
+                            reinterpret_cast<f32x2*>(Ih + i * ns)[m] = Xih[u];
+                            reinterpret_cast<f32x2*>(Il + i * ns)[m] = Xil[u];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (sing) {
+            singular = true;
+            break;
+        }
+        {   // ln|det| and the phase from the pivots and the row swaps
+            double lp = 0.0, ap = 0.0;
+            int swaps = 0;
+            for (int k = tid; k < n; k += NT) {
+                const double2 z = pivd[k];
+                lp += 0.5 * log(fma(z.x, z.x, z.y * z.y));
+                ap += atan2(z.y, z.x);
+                swaps += piv[k] != k;
+            }
+            logdet += block_sum<NT>(lp, red);
+            arg += block_sum<NT>(ap, red);
+            if (((long long)block_sum<NT>((double)swaps, red)) & 1) arg += M_PI;
+        }
+        if (tid == 0) {
+            for (int c = 0; c < n; ++c) colmap[c] = c;
+            for (int k = n - 1; k >= 0; --k) {
+                const int t = colmap[k];
+                colmap[k] = colmap[piv[k]];
+                colmap[piv[k]] = t;
+            }
+        }
+        __syncthreads();
+        // the inverse entries as complex doubles for the final dot products
+        auto inv_at = [&](int j, int c) {
+            return make_double2((double)Rh[j * ns + c] + (double)Rl[j * ns + c],
+                                (double)Ih[j * ns + c] + (double)Il[j * ns + c]);
+        };
+        if (a.kinetic) {   // T_s = -1/2 sum_ij (A^-1)_ji L_ij
+            double pr = 0.0, pi = 0.0;
+            for (int i = wid; i < n; i += NT / 32) {
+                const int ci = colmap[i];
+                for (int j = lane; j < n; j += 32) {
+                    const double2 t = cmul(inv_at(j, ci), ldc<T>(a.lap, (base + i) * O + j));
+                    pr += t.x;
+                    pi += t.y;
+                }
+            }
+            kin.x += -0.5 * block_sum<NT>(pr, red);
+            kin.y += -0.5 * block_sum<NT>(pi, red);
+        }
+        if (a.drift) {
+            for (int ic = wid; ic < 3 * n; ic += NT / 32) {
+                const int i = ic / 3, c = ic - (ic / 3) * 3;
+                const int ci = colmap[i];
+                double sr = 0.0, si = 0.0;
+                for (int j = lane; j < n; j += 32) {
+                    const double2 t = cmul(inv_at(j, ci), ldc<T>(a.grad, ((base + i) * 3 + c) * O + j));
+                    sr += t.x;
+                    si += t.y;
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    sr += __shfl_xor_sync(0xffffffffu, sr, off);
+                    si += __shfl_xor_sync(0xffffffffu, si, off);
+                }
+                if (lane == 0) {
+                    double* q = a.drift + 2 * (((w * a.n_elec) + e0 + i) * 3 + c);
+                    q[0] = sr;
+                    q[1] = si;
+                }
+            }
+        }
+    }
+    if (tid == 0) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        const double inf = __longlong_as_double(0x7ff0000000000000LL);
+        if (a.logdet) a.logdet[w] = singular ? -inf : logdet;
+        if (a.sign) {
+            double sn, cs;
+            sincos(arg, &sn, &cs);
+            a.sign[2 * w] = singular ? 0.0 : cs;
+            a.sign[2 * w + 1] = singular ? 0.0 : sn;
+        }
+        if (a.kinetic) {
+            a.kinetic[2 * w] = singular ? nan : kin.x;
+            a.kinetic[2 * w + 1] = singular ? nan : kin.y;
+        }
+    }
+    if (singular && a.drift) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);
+        for (int e = tid; e < 6 * a.n_elec; e += NT) a.drift[w * a.n_elec * 6 + e] = nan;
+    }
+}
+
 template <typename T>
 int launch_slater_complex(const SlaterArgs& a, int nmax, cudaStream_t st)
 {
+    if (a.arith == 1) {
+        const int ns = ((nmax + 1) & ~1) + 2;
+        const size_t smem = 4 * (size_t)nmax * ns * sizeof(float);
+        cudaError_t e = cudaFuncSetAttribute(slater_cdf_kernel<T, kSlaterDfThreads>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(slater_cdf_kernel)");
+        slater_cdf_kernel<T, kSlaterDfThreads><<<(unsigned)a.n_walkers, kSlaterDfThreads, smem, st>>>(a);
+        return cuda_error(cudaGetLastError(), "slater_cdf_kernel launch");
+    }
     const size_t smem = (size_t)nmax * (nmax + 1) * sizeof(double2);
     cudaError_t e = cudaFuncSetAttribute(slater_complex_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(slater_complex_kernel)");
@@ -716,8 +1008,6 @@ extern "C" int qmcspl_slater_kinetic(const void* val, const void* grad, const vo
     if (arith != QMCSPL_SLATER_FP64 && arith != QMCSPL_SLATER_DF64)
         return set_error(QMCSPL_ERR_ARG, "arith must be QMCSPL_SLATER_FP64 or QMCSPL_SLATER_DF64");
     const bool cplx = dtype >= 2;
-    if (cplx && arith != QMCSPL_SLATER_FP64)
-        return set_error(QMCSPL_ERR_UNSUPPORTED, "complex orbitals are eliminated in FP64 (QMCSPL_SLATER_FP64)");
     if (n_walkers < 0) return set_error(QMCSPL_ERR_ARG, "n_walkers < 0");
     if (n_elec < 1 || n_up < 0 || n_up > n_elec) return set_error(QMCSPL_ERR_ARG, "need n_elec >= 1, 0 <= n_up <= n_elec");
     const int n_dn = n_elec - n_up;

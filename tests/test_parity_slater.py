@@ -116,9 +116,10 @@ def compare_complex(got, ref, rel=1e-9):
     assert oracle.relative_error(dr, rdr) < rel * 10
 
 
+@pytest.mark.parametrize("arith", ["f64", "df64"])
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("n_elec,n_up,n_orb", [(13, 7, 9), (8, 0, 8), (2, 1, 3), (40, 20, 24)])
-def test_complex_consumer_matches_oracle(storage, n_elec, n_up, n_orb):
+def test_complex_consumer_matches_oracle(storage, n_elec, n_up, n_orb, arith):
     k = inputs.KPOINTS["generic"]
     dims = (12, 12, 12)
     lat, mil, coef = inputs.random_bloch_cell(1900 + n_elec, n_orb, 8.0, 6.0, k, NONORTHO)
@@ -128,14 +129,15 @@ def test_complex_consumer_matches_oracle(storage, n_elec, n_up, n_orb):
     v, g, l = spl.eval_vgl(torch.from_numpy(pos).to(dev()))
     spl.sync()
     assert v.is_complex()
-    got = consumer(v, g, l, W, n_elec, n_up, arith="f64")
+    got = consumer(v, g, l, W, n_elec, n_up, arith=arith)
     ref = oracle.slater_kinetic(v.cpu().numpy().astype(np.complex128), g.cpu().numpy().astype(np.complex128),
                                 l.cpu().numpy().astype(np.complex128), W, n_elec, n_up)
     compare_complex(got, ref)
     spl.close()
 
 
-def test_complex_consumer_largest_block_singular_walker_and_rejections():
+@pytest.mark.parametrize("arith", ["f64", "df64"])
+def test_complex_consumer_largest_block_singular_walker_and_rejections(arith):
     from paper_1309_6250_gb300 import _lib
     from paper_1309_6250_gb300.api import slater_kinetic
     n = _lib.SLATER_MAX_COMPLEX_BLOCK
@@ -147,7 +149,7 @@ def test_complex_consumer_largest_block_singular_walker_and_rejections():
     lap = c(W * n_elec, n)
     val[2 * n_elec + n + 3] = 0.0                  # walker 2, down block: zero row
     tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev())
-    ld, sg, kin, dr = consumer(tt(val), tt(grad), tt(lap), W, n_elec, n, "f64")
+    ld, sg, kin, dr = consumer(tt(val), tt(grad), tt(lap), W, n_elec, n, arith)
     assert sg[2] == 0 and ld[2] == -np.inf and np.isnan(kin[2]) and np.all(np.isnan(dr[2]))
     keep = [0, 1]
     rows = np.concatenate([np.arange(w * n_elec, (w + 1) * n_elec) for w in keep])
@@ -156,8 +158,8 @@ def test_complex_consumer_largest_block_singular_walker_and_rejections():
     v = tt(val[: 2 * n])
     big = torch.zeros((2 * (n + 1), n + 1), dtype=torch.complex128, device=dev())
     with pytest.raises(_lib.QmcsplError) as ei:
-        slater_kinetic(big, None, big, 1, 2 * (n + 1), n + 1)          # a block over the limit
+        slater_kinetic(big, None, big, 1, 2 * (n + 1), n + 1, arith=arith)   # a block over the limit
     assert ei.value.code == _lib.ERR_UNSUPPORTED
     with pytest.raises(_lib.QmcsplError) as ei:
-        slater_kinetic(v, None, v, 1, 2 * n, n, arith="df64")            # complex in double-float
-    assert ei.value.code == _lib.ERR_UNSUPPORTED
+        slater_kinetic(v, None, v, 1, 2 * n, 2 * n + 1, arith=arith)         # n_up > n_elec
+    assert ei.value.code == _lib.ERR_ARG
