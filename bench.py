@@ -468,8 +468,9 @@ def bench_general(args, dev, stream):
 def bench_batched(args, dev, stream):
     """The uneven three-cell workload (Al-like 32-atom: 48 orbitals, 64^3, 512 x 96 e;
     Si-like 64-atom: 128 orbitals, 80^3, 1024 x 256 e; MgO-like 16-atom: 32 orbitals,
-    64^3, 2048 x 64 e; FP32 smoothing + Laplacian tables) through one batched launch
-    per step, each cell with the autotuner's tile shape and order."""
+    64^3, 2048 x 64 e; FP32 smoothing + Laplacian tables) through one qmcspl_eval_batched
+    call per step, each cell with the autotuner's tile shape and order (cells this large
+    each get their own launch; smaller ones share the batched kernel)."""
     import torch
     from paper_1309_6250_gb300 import autotune
     from paper_1309_6250_gb300.api import eval_batched

@@ -275,11 +275,15 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
                              double* dpos, void* stream);
 
 /*
- * qmcspl_eval_batched -- qmcspl_eval_vgl for several handles in ONE kernel launch.
+ * qmcspl_eval_batched -- qmcspl_eval_vgl for several handles in one call.
  *
- * Walkers of cells with different orbital counts and grids go through one launch
- * whose work list spreads every cell's positions evenly over the whole GPU (each warp
- * task moves the same number of bytes whatever the cell).  All handles must be
+ * Walkers of cells with different orbital counts and grids go through one batched
+ * launch whose work list spreads every cell's positions evenly over the whole GPU (each
+ * warp task moves the same number of bytes whatever the cell).  A cell with enough work
+ * to fill the GPU for at least four rounds of warp tasks on its own instead gets its own
+ * launch, with the launch shape qmcspl_eval_vgl would use (large launches lose little to
+ * their last, partly filled round, and the single-cell shape is faster); all launches of
+ * a call go to `stream` in cell order.  All handles must be
  * B-spline handles without separate gradient tables on one device with the same
  * storage type, the same separate_lap setting and the same bloch setting (k points may
  * differ per cell).

@@ -640,10 +640,13 @@ int launch_batched(int n_cells, const Handle* const* hs, const double* const* po
                    cudaStream_t st)
 {
     thread_local BatchArgs B;   // about 16 KB: kept off the stack, one per calling thread
-    B.n_cells = n_cells;
+    // cells of at least kLargeLaunchRounds rounds of warp tasks (512-thread blocks on every
+    // SM) get their own launch; the others share one batched launch
+    const long long large = (long long)kLargeLaunchRounds * sm_count() * (QMCSPL_EVAL_THREADS / 32);
+    int nb = 0;
     B.start[0] = 0;
     for (int c = 0; c < n_cells; ++c) {
-        EvalArgs& a = B.cell[c];
+        EvalArgs& a = B.cell[nb];
         fill_eval_args(hs[c], &a);
         a.pos = pos[c];
         a.rec = pr[c].rec;
@@ -652,9 +655,17 @@ int launch_batched(int n_cells, const Handle* const* hs, const double* const* po
         a.n_pos = n_pos[c];
         set_outputs(hs[c], a, val[c], grad[c], lap[c]);
         const int gpw = 32 >> a.lanes_log2;
-        B.start[c + 1] = B.start[c] + (a.n_pos * a.tiles + gpw - 1) / gpw;
+        const long long warps = (a.n_pos * a.tiles + gpw - 1) / gpw;
+        if (warps >= large) {
+            const int rc = launch_bspline_vgl(hs[c], pos[c], pr[c], n_pos[c], val[c], grad[c], lap[c], st);
+            if (rc != QMCSPL_OK) return rc;
+            continue;
+        }
+        B.start[nb + 1] = B.start[nb] + warps;
+        ++nb;
     }
-    if (B.start[n_cells] == 0) return QMCSPL_OK;
+    B.n_cells = nb;
+    if (nb == 0 || B.start[nb] == 0) return QMCSPL_OK;
     const bool lt = hs[0]->separate_lap != 0;
     switch (hs[0]->storage) {
     case QMCSPL_DF64:

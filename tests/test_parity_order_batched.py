@@ -144,3 +144,40 @@ def test_eval_vgl_cell_order_captured_in_cuda_graph():
     torch.cuda.synchronize()
     for a, b in zip(out, ref):
         assert torch.equal(a, b)
+
+
+def test_batched_mixes_own_and_shared_launches():
+    """A call with one cell large enough for its own launch (over four rounds of warp tasks)
+    and two small cells sharing the batched launch: every cell equals its own eval_vgl, also
+    when the call is captured in a CUDA graph and replayed."""
+    from paper_1309_6250_gb300.api import eval_batched
+    cells = []
+    for i, (dims, n_orb, n_pos) in enumerate((((12, 12, 12), 16, 90_000), ((10, 14, 16), 7, 1000),
+                                              ((8, 8, 12), 20, 3001))):
+        lat, mil, coef = inputs.random_cell(520 + i, dims, n_orb, 6.0, 5.0, NONORTHO)
+        cells.append((splines(lat, dims, mil, coef, method="interp", storage="f32", separate_lap=True),
+                      torch.from_numpy(inputs.positions(lat, n_pos, 30 + i, -1, 2)).to(dev())))
+    spls = [c[0] for c in cells]
+    pos = [c[1] for c in cells]
+    singles = [s.eval_vgl(p) for s, p in zip(spls, pos)]
+    torch.cuda.synchronize()
+    outs = eval_batched(spls, pos)
+    torch.cuda.synchronize()
+    for a, b in zip(outs, singles):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        eval_batched(spls, pos, outs=outs, stream=st)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            eval_batched(spls, pos, outs=outs, stream=st)
+    for o in outs:
+        for t in o:
+            t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(outs, singles):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
