@@ -30,7 +30,7 @@ What the oracle computes, in the paper's order:
    log-determinant, the local kinetic energy and the drift (slater_kinetic).
 8. Interpolating B-splines of any odd degree on uniform or non-uniform periodic grids: the
    Appendix's recurrence for the basis, dense periodic interpolation matrices, brute-force
-   evaluation (general_interp_tables, general_eval).
+   evaluation and its transpose (general_interp_tables, general_eval, general_adjoint).
 
 Readings of the paper that the code depends on:
 * gamma_G (Eq. b-splinecoefficients) is a product over axes of
@@ -821,6 +821,72 @@ def general_eval(beta, lattice, pos, degree: int = 3, knots=(None, None, None), 
                     H[i, j] = tp(*o)
             lap[p] = np.einsum("ij,ijo->o", metric, H)
     return val, grad, lap
+
+
+def general_adjoint(beta, lattice, pos, gv, gg, gl, degree: int = 3, knots=(None, None, None), beta_lap=None):
+    """(dbeta, dbeta_lap or None, dpos [P, 3]) for loss = <gv,val> + <gg,grad> + <gl,lap> with
+    the outputs of general_eval: its exact transpose, brute force over every basis function.
+
+    With D_i = d/ds_i and the Cartesian gradient grad = a^-T (D_1, D_2, D_3) phi, the loss
+    is linear in beta: each coefficient gets
+        gv B + sum_i gt_i D_i B + gl sum_ij M_ij D_i D_j B     (gt = a^-1 gg, M = a^-1 a^-T),
+    the last term moving to dbeta_lap (gl B) with a separate Laplacian table.  The position
+    adjoint is dL/dr = a^-T u with u_i = sum_o [gv D_i phi + sum_j (D_i D_j phi) gt_j + gl D_i lap],
+    D_i lap = sum_jk M_jk D_i D_j D_k phi, or D_i of the Laplacian table."""
+    beta = np.asarray(beta, dtype=np.float64)
+    dims = beta.shape[:3]
+    C = 1.5 if degree == 3 else degree_constant(degree)
+    pts = [axis_points(int(dims[a]), knots[a]) for a in range(3)]
+    ainv = np.linalg.inv(np.asarray(lattice, dtype=np.float64))
+    metric = ainv @ ainv.T
+    pos = _f64(pos).reshape(-1, 3)
+    s = pos @ ainv.T
+    s = s - np.floor(s)
+    P = pos.shape[0]
+    bl = None if beta_lap is None else np.asarray(beta_lap, dtype=np.float64)
+    gv = np.asarray(gv, dtype=np.float64).reshape(P, -1)
+    gg = np.asarray(gg, dtype=np.float64).reshape(P, 3, -1)
+    gl = np.asarray(gl, dtype=np.float64).reshape(P, -1)
+    dbeta = np.zeros_like(beta)
+    dbl = None if bl is None else np.zeros_like(beta)
+    dpos = np.zeros((P, 3))
+    for p in range(P):
+        B = [[periodic_basis_matrix(pts[a], degree, s[p, a:a + 1], C, d)[0] for d in range(4)]
+             for a in range(3)]
+
+        def basis(o):   # the tensor D_x^o0 D_y^o1 D_z^o2 of every basis function [N1, N2, N3]
+            return np.einsum("l,m,n->lmn", B[0][o[0]], B[1][o[1]], B[2][o[2]])
+
+        def unit(*axes):
+            o = [0, 0, 0]
+            for a in axes:
+                o[a] += 1
+            return o
+
+        gt = ainv @ gg[p]                                    # [3, O]
+        # coefficient adjoint
+        dbeta += np.einsum("lmn,o->lmno", basis((0, 0, 0)), gv[p])
+        for i in range(3):
+            dbeta += np.einsum("lmn,o->lmno", basis(unit(i)), gt[i])
+        if bl is None:
+            lapB = sum(metric[i, j] * basis(unit(i, j)) for i in range(3) for j in range(3))
+            dbeta += np.einsum("lmn,o->lmno", lapB, gl[p])
+        else:
+            dbl += np.einsum("lmn,o->lmno", basis((0, 0, 0)), gl[p])
+        # position adjoint
+        val = lambda o, tab=beta: np.einsum("lmn,lmno->o", basis(o), tab)
+        u = np.zeros(3)
+        for i in range(3):
+            ui = gv[p] * val(unit(i))
+            for j in range(3):
+                ui = ui + val(unit(i, j)) * gt[j]
+            if bl is None:
+                dlap = sum(metric[j, k] * val(unit(i, j, k)) for j in range(3) for k in range(3))
+            else:
+                dlap = val(unit(i), bl)
+            u[i] = np.sum(ui + gl[p] * dlap)
+        dpos[p] = ainv.T @ u
+    return dbeta, dbl, dpos
 
 
 # ---------------------------------------------------------------------------

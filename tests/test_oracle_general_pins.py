@@ -286,3 +286,71 @@ def test_degree_smoothing_cubic_is_the_paper_path_and_higher_degree_converges_fa
             v, _, _ = oracle.general_eval(beta, lat, pos, degree)
             errs.append(np.abs(v - pv).max())
         assert errs[0] / errs[1] > ratio
+
+
+# ---------------------------------------------------------------------------
+# the adjoint of the general evaluation (general_adjoint)
+# ---------------------------------------------------------------------------
+
+def _general_loss(beta, pos, g, degree, knots, beta_lap=None):
+    v, gr, l = oracle.general_eval(beta, NONORTHO, pos, degree, knots, beta_lap=beta_lap)
+    return float(np.sum(g[0] * v) + np.sum(g[1] * gr) + np.sum(g[2] * l))
+
+
+@pytest.mark.parametrize("sep", [False, True])
+def test_general_adjoint_cubic_uniform_equals_the_cubic_adjoint(sep):
+    """Degree 3 on a uniform grid is the paper's tricubic spline, whose adjoint the C oracle
+    computes by its own loops: the two transposes agree."""
+    dims = (6, 7, 8)
+    rng = np.random.default_rng(60)
+    beta = rng.standard_normal(dims + (3,))
+    blap = rng.standard_normal(dims + (3,)) if sep else None
+    pos = inputs.positions(NONORTHO, 7, 61, -1, 2)
+    g = inputs.upstream_weights(7, 3, 62)
+    dc, dcl, dp = oracle.general_adjoint(beta, NONORTHO, pos, *g, degree=3, beta_lap=blap)
+    rdc, rdcl, rdp = oracle.bspline_adjoint(beta, NONORTHO, pos, *g, beta_lap=blap)
+    assert oracle.relative_error(dc, rdc) < 1e-12
+    if sep:
+        assert oracle.relative_error(dcl, rdcl) < 1e-12
+    assert oracle.relative_error(dp, rdp) < 1e-11
+
+
+@pytest.mark.parametrize("degree,graded", [(1, False), (5, False), (7, False), (1, True), (3, True), (5, True)])
+@pytest.mark.parametrize("sep", [False, True])
+def test_general_adjoint_linearity_and_position_fd(degree, graded, sep):
+    """The loss is linear in the coefficients: sum(dL/dbeta * beta') = L(beta') for random
+    tables beta' through general_eval; and dL/dr against central differences of the loss
+    (positions away from the grid planes, where the degree-1 spline has kinks)."""
+    dims = (8, 9, 10)
+    knots = tuple(inputs.graded_knots(d, 0.45, 0.2 * a) for a, d in enumerate(dims)) if graded \
+        else (None, None, None)
+    rng = np.random.default_rng(63 + degree + 10 * graded)
+    beta = rng.standard_normal(dims + (2,))
+    blap = rng.standard_normal(dims + (2,)) if sep else None
+    pos = inputs.positions(NONORTHO, 6, 64 + degree, -1, 2)
+    pts = [oracle.axis_points(d, k) for d, k in zip(dims, knots)]
+    s = pos @ np.linalg.inv(NONORTHO).T
+    s = s - np.floor(s)
+    for a in range(3):      # keep every position 1e-3 away from a grid plane
+        d = s[:, a, None] - np.concatenate([pts[a], [1.0]])[None, :]
+        near = np.min(np.abs(d), axis=1) < 1e-3
+        s[near, a] += 2e-3
+    pos = s @ NONORTHO.T
+    g = inputs.upstream_weights(6, 2, 65)
+    dc, dcl, dp = oracle.general_adjoint(beta, NONORTHO, pos, *g, degree=degree, knots=knots, beta_lap=blap)
+    for _ in range(2):
+        b1 = rng.standard_normal(dims + (2,))
+        b2 = rng.standard_normal(dims + (2,)) if sep else None
+        lin = np.sum(dc * b1) + (np.sum(dcl * b2) if sep else 0.0)
+        ref = _general_loss(b1, pos, g, degree, knots, b2)
+        assert abs(lin - ref) <= 1e-11 * max(1.0, abs(ref))
+    h = 1e-6
+    fd = np.zeros_like(dp)
+    for p in range(pos.shape[0]):
+        gp = tuple(x[p:p + 1] for x in g)
+        for a in range(3):
+            e = np.zeros(3)
+            e[a] = h
+            fd[p, a] = (_general_loss(beta, pos[p:p + 1] + e, gp, degree, knots, blap) -
+                        _general_loss(beta, pos[p:p + 1] - e, gp, degree, knots, blap)) / (2 * h)
+    assert oracle.relative_error(dp, fd) < 1e-6
