@@ -245,7 +245,7 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
                          void* grad_host, void* lap_host, void* stream);
 
 /*
- * qmcspl_eval_vgl_backward -- adjoint of qmcspl_eval_vgl (every method; cubic, uniform grids).
+ * qmcspl_eval_vgl_backward -- adjoint of qmcspl_eval_vgl (every method, degree and grid).
  *
  * Not in the paper: for a scalar loss L with upstream gradients gv = dL/dval,
  * gg = dL/dgrad, gl = dL/dlap (same layouts and dtype as the outputs; any may be NULL
@@ -267,8 +267,9 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
  * [5][Nx][Ny][Nz][O] (those tables in that order, canonical layout) and dcoef_lap must be NULL.
  * pp handles: dcoef is [8][Nx][Ny][Nz][O], sigma^{kappa mu nu} at index 4(kappa-1) + 2(mu-1) +
  * (nu-1) as in qmcspl_get_table; dcoef_lap must be NULL.
- * QMCSPL_ERR_UNSUPPORTED for double-float tables and B-splines of another degree or on a
- * non-uniform grid.
+ * Double-float tables: the adjoint runs in FP64 on the stored pairs (hi + lo) read as
+ * doubles; dcoef is double (the output dtype).  B-splines of degree 1, 5, 7 and on graded
+ * grids: the same adjoints over their (n + 1)^3-point stencils (a scalar kernel).
  */
 int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, const void* gv,
                              const void* gg, const void* gl, void* dcoef, void* dcoef_lap,

@@ -659,10 +659,6 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
 {
     g_err.clear();
     if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
-    if (h->storage == QMCSPL_DF64)
-        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is not implemented for double-float tables");
-    if (is_general(h))
-        return set_error(QMCSPL_ERR_UNSUPPORTED, "backward is implemented for cubic B-splines on uniform grids");
     if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
     // five-table and pp handles: dcoef holds all their tables (5, or the 8 pp entries)
     const bool multi = h->n_tables == 5 || h->method == QMCSPL_PPSPLINE;

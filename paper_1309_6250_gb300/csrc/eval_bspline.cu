@@ -315,12 +315,9 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
     if (p.lap) store_run<float, E>(static_cast<float*>(p.lap) + ip * p.n_orb + o0, lp, o0, p.n_orb, vec);
 }
 
-// Double-float tables (16-byte chunk = two orbitals as hi0, hi1, lo0, lo1): the same
-// stencil walk with every product and sum carried as a double-float pair on the FP32
-// pipe (see df_fma2), results converted to double at the store.
-struct DF64Tag {
-    float v[2];   // 8 bytes per stored coefficient
-};
+// Double-float tables (DF64Tag chunks, see eval_common.cuh): the same stencil walk with every
+// product and sum carried as a double-float pair on the FP32 pipe (see df_fma2), results
+// converted to double at the store.
 
 template <bool LAPTAB>
 __device__ __forceinline__ void bspline_warp_task_df(const EvalArgs& p, long long w0, int lane)

@@ -12,6 +12,13 @@ template <typename T> struct Traits;
 template <> struct Traits<double> { using A = double; static constexpr int E = 2; };
 template <> struct Traits<float> { using A = float; static constexpr int E = 4; };
 template <> struct Traits<__nv_bfloat16> { using A = float; static constexpr int E = 8; };
+// Double-float tables: a 16-byte chunk holds two orbitals as hi0, hi1, lo0, lo1 (value =
+// hi + lo).  The evaluation kernel computes in double-float; code that computes in double
+// (the adjoint) reads the pairs as doubles through Traits / unpack.
+struct DF64Tag {
+    float v[2];   // 8 bytes per stored coefficient
+};
+template <> struct Traits<DF64Tag> { using A = double; static constexpr int E = 2; };
 
 // 16-byte read-only load of table data.
 __device__ __forceinline__ uint4 ldg16(const void* p)
@@ -61,6 +68,11 @@ template <> __device__ __forceinline__ void unpack<float>(const uint4& r, float*
     v[1] = __uint_as_float(r.y);
     v[2] = __uint_as_float(r.z);
     v[3] = __uint_as_float(r.w);
+}
+template <> __device__ __forceinline__ void unpack<DF64Tag>(const uint4& r, double* v)
+{
+    v[0] = (double)__uint_as_float(r.x) + (double)__uint_as_float(r.z);
+    v[1] = (double)__uint_as_float(r.y) + (double)__uint_as_float(r.w);
 }
 // bfloat16 is the top half of a float: widen by shifting into the high 16 bits.
 template <> __device__ __forceinline__ void unpack<__nv_bfloat16>(const uint4& r, float* v)

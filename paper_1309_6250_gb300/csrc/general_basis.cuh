@@ -30,12 +30,15 @@ __host__ __device__ inline double degree_constant(int n)
 // partition-of-unity levels P_d[r] = b_{i-d+r}^d (C = 1):
 //   P_d[r] = ((t + d - r) P_{d-1}[r-1] + (r + 1 - t) P_{d-1}[r]) / d,
 //   d/du P_n[r] = P_{n-1}[r-1] - P_{n-1}[r],   d2/du2 P_n[r] = D_{n-1}[r-1] - D_{n-1}[r]
-// with D_{n-1}[r] = P_{n-2}[r-1] - P_{n-2}[r] (entries outside 0..d are zero).  The
-// weights are C_n P_n; derivatives are with respect to u = N s (grid units).
+// with D_{n-1}[r] = P_{n-2}[r-1] - P_{n-2}[r] (entries outside 0..d are zero); in general the
+// m-th derivative is the m-th backward difference of P_{n-m}, so the third is
+//   d3/du3 P_n[r] = P_{n-3}[r-3] - 3 P_{n-3}[r-2] + 3 P_{n-3}[r-1] - P_{n-3}[r].
+// The weights are C_n P_n; derivatives are with respect to u = N s (grid units).  d2w and
+// d3w may be null.
 template <typename A, int DEG>
-__host__ __device__ inline void uniform_weights(A t, A C, A* w, A* dw, A* d2w)
+__host__ __device__ inline void uniform_weights(A t, A C, A* w, A* dw, A* d2w, A* d3w = nullptr)
 {
-    A lev[3][DEG + 1];   // P_{DEG-2}, P_{DEG-1}, P_DEG (zero padded)
+    A lev[3][DEG + 1];   // P_{DEG-2}, P_{DEG-1}, P_{DEG-3} (zero padded)
     A P[DEG + 1];
 #pragma unroll
     for (int r = 0; r <= DEG; ++r) P[r] = A(0);
@@ -45,6 +48,7 @@ __host__ __device__ inline void uniform_weights(A t, A C, A* w, A* dw, A* d2w)
 #pragma unroll
         for (int r = 0; r <= DEG; ++r) lev[l][r] = A(0);
     if (DEG - 2 == 0) lev[0][0] = A(1);
+    if (DEG - 3 == 0) lev[2][0] = A(1);
 #pragma unroll
     for (int d = 1; d <= DEG; ++d) {
         A Q[DEG + 1];
@@ -66,6 +70,9 @@ __host__ __device__ inline void uniform_weights(A t, A C, A* w, A* dw, A* d2w)
         if (d == DEG - 1)
 #pragma unroll
             for (int r = 0; r <= DEG; ++r) lev[1][r] = P[r];
+        if (d == DEG - 3)
+#pragma unroll
+            for (int r = 0; r <= DEG; ++r) lev[2][r] = P[r];
     }
     if (DEG == 1) {   // P_0 = [1] is the degree-0 level
         lev[1][0] = A(1);
@@ -85,6 +92,12 @@ __host__ __device__ inline void uniform_weights(A t, A C, A* w, A* dw, A* d2w)
                 return x - y;
             };
             d2w[r] = C * (D(r - 1) - D(r));
+        }
+        if (d3w) {
+            auto P3 = [&](int q) -> A {   // P_{DEG-3}[q], zero outside 0..DEG-3
+                return (DEG >= 3 && q >= 0 && q <= DEG - 3) ? lev[2][q] : A(0);
+            };
+            d3w[r] = C * (P3(r - 3) - A(3) * P3(r - 2) + A(3) * P3(r - 1) - P3(r));
         }
     }
 }
@@ -176,7 +189,7 @@ __host__ __device__ inline void nonuniform_cubic_weights(const double* knots, in
 // of consecutive spacings, so no absolute coordinate (and no FP64 for FP32 tables) is involved.
 template <typename S, typename A, int DEG>
 __host__ __device__ inline void nonuniform_weights_local(const S* hs, int n, int i, S dx, A C, A* w, A* dw,
-                                                         A* d2w)
+                                                         A* d2w, A* d3w = nullptr)
 {
     auto h = [&](int j) -> S {
         j %= n;
@@ -195,12 +208,14 @@ __host__ __device__ inline void nonuniform_weights_local(const S* hs, int n, int
         left[j] = left[j - 1] + h(i - j + 1);
         right[j] = right[j - 1] + h(i + j - 1);
     }
-    // Nl[q]: the level-j function starting at knot i - j + q; levels DEG - 1 and DEG - 2 kept
-    S Nl[DEG + 1], N1[DEG + 1], N2[DEG + 1];
-    for (int q = 0; q <= DEG; ++q) Nl[q] = N1[q] = N2[q] = S(0);
+    // Nl[q]: the level-j function starting at knot i - j + q; levels DEG - 1, DEG - 2 and
+    // DEG - 3 kept
+    S Nl[DEG + 1], N1[DEG + 1], N2[DEG + 1], N3[DEG + 1];
+    for (int q = 0; q <= DEG; ++q) Nl[q] = N1[q] = N2[q] = N3[q] = S(0);
     Nl[0] = S(1);
     if (DEG == 1) N1[0] = S(1);
     if (DEG == 2) N2[0] = S(1);
+    if (DEG == 3) N3[0] = S(1);
     for (int j = 1; j <= DEG; ++j) {
         S saved = S(0);
         for (int r = 0; r < j; ++r) {
@@ -213,6 +228,8 @@ __host__ __device__ inline void nonuniform_weights_local(const S* hs, int n, int
             for (int q = 0; q <= j; ++q) N1[q] = Nl[q];
         if (j == DEG - 2)
             for (int q = 0; q <= j; ++q) N2[q] = Nl[q];
+        if (j == DEG - 3)
+            for (int q = 0; q <= j; ++q) N3[q] = Nl[q];
     }
     auto b1 = [&](int k) -> S {   // level DEG - 1, starting at knot k
         const int q = k - (i - (DEG - 1));
@@ -225,12 +242,23 @@ __host__ __device__ inline void nonuniform_weights_local(const S* hs, int n, int
     auto db1 = [&](int k) -> S {
         return S(DEG - 1) * (b2(k) / kd(k + DEG - 1, k) - b2(k + 1) / kd(k + DEG, k + 1));
     };
+    auto b3 = [&](int k) -> S {   // level DEG - 3
+        const int q = k - (i - (DEG - 3));
+        return (DEG >= 3 && q >= 0 && q <= DEG - 3) ? N3[q] : S(0);
+    };
+    auto db2 = [&](int k) -> S {   // derivative of the level DEG - 2 function starting at knot k
+        return DEG >= 3 ? S(DEG - 2) * (b3(k) / kd(k + DEG - 2, k) - b3(k + 1) / kd(k + DEG - 1, k + 1)) : S(0);
+    };
+    auto d2b1 = [&](int k) -> S {  // second derivative of the level DEG - 1 function
+        return S(DEG - 1) * (db2(k) / kd(k + DEG - 1, k) - db2(k + 1) / kd(k + DEG, k + 1));
+    };
     for (int r = 0; r <= DEG; ++r) {
         const int k = i - DEG + r;   // start knot of the function of grid point i - (DEG-1)/2 + r
         w[r] = C * (A)Nl[r];
         const S ak = S(DEG) / kd(k + DEG, k), bk = S(DEG) / kd(k + DEG + 1, k + 1);
         dw[r] = C * (A)(ak * b1(k) - bk * b1(k + 1));
         if (d2w) d2w[r] = DEG >= 2 ? C * (A)(ak * db1(k) - bk * db1(k + 1)) : A(0);
+        if (d3w) d3w[r] = DEG >= 3 ? C * (A)(ak * d2b1(k) - bk * d2b1(k + 1)) : A(0);
     }
 }
 

@@ -51,6 +51,28 @@ def test_fp64_backward_matches_oracle(method, sep, n_orb):
     assert oracle.relative_error(dpos, rdpos) < 1e-12
 
 
+@pytest.mark.parametrize("method", ["smooth", "interp"])
+@pytest.mark.parametrize("sep", [False, True])
+def test_df64_backward_matches_oracle(method, sep):
+    """Double-float tables: the adjoint runs in FP64 on the stored pairs, so it equals the
+    oracle adjoint on the tables as stored (get_table returns hi + lo) to FP64 rounding."""
+    dims = (9, 10, 11)
+    n_orb = 6
+    lat, mil, coef = inputs.random_cell(640, dims, n_orb, 6.0, 5.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method=method, storage="df64", separate_lap=sep)
+    assert spl.out_dtype == torch.float64
+    beta = spl.get_table(0)
+    blap = spl.get_table(1) if sep else None
+    pos = inputs.positions(lat, 300, 641, -1, 2)
+    gv, gg, gl = inputs.upstream_weights(300, n_orb, 642)
+    dc, dcl, dpos = gpu_backward(spl, pos, gv, gg, gl)
+    rdc, rdcl, rdpos = oracle.bspline_adjoint(beta, lat, pos, gv, gg, gl, beta_lap=blap)
+    assert oracle.relative_error(dc, rdc) < 1e-12
+    if sep:
+        assert oracle.relative_error(dcl, rdcl) < 1e-12
+    assert oracle.relative_error(dpos, rdpos) < 1e-12
+
+
 def test_fp64_linearity_identity_and_position_fd():
     """L is linear in beta: sum(dL/dbeta * beta) = L(beta) with the GPU forward pass; and
     dL/dr against central differences of the GPU forward (h = 1e-4 bohr, FP64)."""
@@ -139,19 +161,11 @@ def test_autograd_function_positions_and_coefficients():
     assert oracle.relative_error(pos.grad.cpu().numpy(), rdpos_v) < 1e-12
 
 
-def test_backward_rejects_variants():
+def test_double_float_variants_are_rejected_at_creation():
     from paper_1309_6250_gb300 import _lib
     dims = (8, 8, 8)
     lat, mil, coef = inputs.random_cell(5, dims, 2, 5.0, 4.0, np.eye(3) * 6.0)
     pos = torch.zeros((4, 3), dtype=torch.float64, device=dev())
-    spl = splines(lat, dims, mil, coef, method="interp", storage="f64", degree=5)
-    with pytest.raises(_lib.QmcsplError) as ei:
-        spl.backward(pos)
-    assert ei.value.code == _lib.ERR_UNSUPPORTED
-    spl = splines(lat, dims, mil, coef, method="smooth", storage="df64")
-    with pytest.raises(_lib.QmcsplError) as ei:
-        spl.backward(pos)
-    assert ei.value.code == _lib.ERR_UNSUPPORTED
     for method in ("lagrange", "pp"):
         with pytest.raises(_lib.QmcsplError) as ei:
             splines(lat, dims, mil, coef, method=method, storage="df64")
@@ -184,7 +198,8 @@ def gpu_backward_complex(spl, pos, g):
         dpos.cpu().numpy()
 
 
-@pytest.mark.parametrize("storage,tol_lin,tol_fd", [("f64", 1e-11, 1e-6), ("f32", 2e-5, 3e-3)])
+@pytest.mark.parametrize("storage,tol_lin,tol_fd", [("f64", 1e-11, 1e-6), ("df64", 1e-11, 1e-6),
+                                                     ("f32", 2e-5, 3e-3)])
 @pytest.mark.parametrize("sep", [False, True])
 def test_bloch_backward_linearity_and_position_fd(storage, tol_lin, tol_fd, sep):
     """L is linear in the stored tables: sum(dL/dbeta * beta') = L(beta') for random tables
@@ -358,3 +373,88 @@ def test_five_table_autograd_and_argument_checks():
     with pytest.raises(_lib.QmcsplError) as ei:
         spl.backward(t(pos_np, torch.float64), t(gv, torch.float64), dcoef=dc, dcoef_lap=torch.zeros_like(dc))
     assert ei.value.code == _lib.ERR_ARG
+
+
+# ---------------------------------------------------------------------------
+# B-splines of other degrees and on graded grids (the general adjoint)
+# ---------------------------------------------------------------------------
+
+def graded(dims):
+    return tuple(inputs.graded_knots(d, 0.45, 0.2 * a) for a, d in enumerate(dims))
+
+
+# f64 for every degree and grid kind, f32 / bf16 on a few (their sums run in FP32: the
+# tolerance allows for up to 512-term FP32 sums per output)
+GENERAL = [(d, g, "f64", sep) for d, g in ((1, False), (5, False), (7, False), (1, True), (3, True), (5, True),
+                                            (7, True)) for sep in (False, True)] + \
+          [(5, False, "f32", True), (7, True, "f32", False), (1, True, "f32", True), (7, False, "bf16", True),
+           (3, True, "bf16", False)]
+
+
+@pytest.mark.parametrize("degree,grad,storage,sep", GENERAL)
+def test_general_backward_matches_oracle(degree, grad, storage, sep):
+    """Coefficient and position adjoints of degree-n B-splines (interpolating; graded grids)
+    against the oracle's brute-force transpose of its evaluation, on the handle's own stored
+    tables; ragged orbital count, positions outside the cell."""
+    dims = (8, 9, 10)
+    n_orb = 5
+    knots = graded(dims) if grad else None
+    lat, mil, coef = inputs.random_cell(1800 + degree, dims, n_orb, 6.0, 5.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="interp", storage=storage, separate_lap=sep, degree=degree,
+                  knots=knots)
+    beta = spl.get_table(0)
+    blap = spl.get_table(1) if sep else None
+    n = 60
+    pos = inputs.positions(lat, n, 1801 + degree, -1, 2)
+    gv, gg, gl = inputs.upstream_weights(n, n_orb, 1802)
+    if storage != "f64":
+        gv, gg, gl = (x.astype(np.float32).astype(np.float64) for x in (gv, gg, gl))
+    dc, dcl, dpos = gpu_backward(spl, pos, gv, gg, gl)
+    rdc, rdcl, rdpos = oracle.general_adjoint(beta, lat, pos, gv, gg, gl, degree=degree,
+                                              knots=knots if grad else (None, None, None), beta_lap=blap)
+    tol = 1e-11 if storage == "f64" else 1e-5
+    assert oracle.relative_error(dc, rdc) < tol
+    if sep:
+        assert oracle.relative_error(dcl, rdcl) < tol
+    assert oracle.relative_error(dpos, rdpos) < tol
+
+
+def test_general_backward_bloch_on_a_graded_grid():
+    """Bloch orbitals with quintic splines on a graded grid: the coefficient adjoint by
+    linearity against the oracle's forward (general evaluation of u, then the phase and the
+    product rule), the position adjoint against central differences of that forward."""
+    k = inputs.KPOINTS["generic"]
+    dims = (9, 10, 11)
+    n_orb = 2
+    knots = graded(dims)
+    lat, mil, coef = inputs.random_bloch_cell(1810, n_orb, 5.0, 4.0, k, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="interp", storage="f64", separate_lap=True, kpoint=k,
+                  degree=5, knots=knots)
+    pos = inputs.positions(lat, 40, 1811, -1, 2)
+    n = pos.shape[0]
+    g = complex_upstream(n, n_orb, 1812)
+    dc, dcl, dpos = gpu_backward_complex(spl, pos, g)
+
+    def forward(b1, b2, p):
+        u = oracle.general_eval(b1, lat, p, 5, knots, beta_lap=b2)
+        return oracle.bloch_combine(*u, lat, k, p, True, False)
+
+    rng = np.random.default_rng(1813)
+    for _ in range(2):
+        b1 = rng.standard_normal(dims + (2 * n_orb,))
+        b2 = rng.standard_normal(dims + (2 * n_orb,))
+        lin = np.sum(dc * b1) + np.sum(dcl * b2)
+        ref = bloch_loss(forward(b1, b2, pos), g)
+        assert abs(lin - ref) <= 1e-11 * max(1.0, abs(ref)), (lin, ref)
+    beta, blap = spl.get_table(0), spl.get_table(1)
+    h = 1e-5
+    fd = np.zeros_like(dpos)
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = h
+        lp = []
+        for sgn in (1, -1):
+            z = forward(beta, blap, pos + sgn * e)
+            lp.append(sum(np.sum((np.conj(gi) * zi).real.reshape(n, -1), axis=1) for gi, zi in zip(g, z)))
+        fd[:, a] = (lp[0] - lp[1]) / (2 * h)
+    assert oracle.relative_error(dpos, fd) < 1e-6

@@ -104,9 +104,11 @@ def test_general_orders_noalloc_checkpoint_and_rejections(tmp_path):
         out = back.eval_vgl(pos)
         torch.cuda.synchronize()
         assert all(torch.equal(a, b) for a, b in zip(out, ref))
-        with pytest.raises(_lib.QmcsplError) as ei:
-            spl.backward(pos)
-        assert ei.value.code == _lib.ERR_UNSUPPORTED
+        # the adjoint of the loaded handle equals the original's (up to the order of the FP32
+        # partial sums of the orbital tiles, which meet in atomic adds)
+        up = torch.ones_like(ref[0])
+        d1, d0 = back.backward(pos, gv=up), spl.backward(pos, gv=up)
+        assert oracle.relative_error(d1.cpu().numpy(), d0.cpu().numpy()) < 1e-6
         with pytest.raises(_lib.QmcsplError) as ei:
             eval_batched([spl], [pos])
         assert ei.value.code == _lib.ERR_UNSUPPORTED
