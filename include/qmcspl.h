@@ -89,8 +89,8 @@ typedef struct {
     int separate_grad; /* B-splines: 1 = also build tables of d_x phi, d_y phi, d_z phi (the
                           separate gradient approximations of Sec. III C; requires
                           separate_lap = 1, five tables in all, memory x5) and return
-                          their values as the gradient.  Not for double-float tables.
-                          Ignored by Lagrange (always five tables) and pp. */
+                          their values as the gradient.  Ignored by Lagrange (always
+                          five tables) and pp. */
     int bloch;         /* 0 = real Gamma-point orbitals (Hermitian coefficients, real
                           outputs).  1 = complex Bloch orbitals at crystal momentum k
                           (Sec. II): phi_n(r) = u_n(r) exp(i k.r) with the periodic part
@@ -409,9 +409,9 @@ int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void
  *   stream cudaStream_t; asynchronous
  * The inversion is Gauss-Jordan elimination with row pivoting in shared memory, one thread
  * block per walker, in FP64 or in double-float (arith); complex entries are pivoted on the
- * largest modulus, and in double-float each of their parts is a float pair.  An exactly singular block gives sign 0, logdet -inf and NaN
- * kinetic energy and drift for that walker; nearly singular blocks lose accuracy as the
- * condition number grows.
+ * largest modulus, and in double-float each of their parts is a float pair.  An exactly
+ * singular block gives sign 0, logdet -inf and NaN kinetic energy and drift for that walker;
+ * nearly singular blocks lose accuracy as the condition number grows.
  */
 #define QMCSPL_SLATER_MAX_BLOCK 160
 #define QMCSPL_SLATER_MAX_COMPLEX_BLOCK 112

@@ -754,6 +754,7 @@ int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
         switch (h->storage) {
         case QMCSPL_F64: return launch_five_typed<double>(a, lag, st);
         case QMCSPL_F32: return launch_five_typed<float>(a, lag, st);
+        case QMCSPL_DF64: return launch_five_typed<DF64Tag>(a, false, st);   // B-splines only
         default: return launch_five_typed<__nv_bfloat16>(a, lag, st);
         }
     }

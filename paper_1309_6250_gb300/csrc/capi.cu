@@ -359,8 +359,6 @@ int qmcspl_create_grid(qmcspl_t* out, const double lattice[9], const int dims[3]
     if (is_bspline && opts->separate_grad) {
         if (!opts->separate_lap)
             return set_error(QMCSPL_ERR_ARG, "separate_grad needs separate_lap (the five-table layout)");
-        if (opts->storage == QMCSPL_DF64)
-            return set_error(QMCSPL_ERR_UNSUPPORTED, "separate gradient tables are not available in double-float");
     }
     if (opts->bloch)
         for (int i = 0; i < 3; ++i)

@@ -17,6 +17,8 @@
 // Work mapping, loads and stores as in eval_bspline.cu: a group of L lanes per
 // position, one 16-byte chunk of each row per lane.  Bloch orbitals (Sec. II) take the
 // same epilogue as the B-splines (bloch_apply).
+#include <type_traits>
+
 #include "eval_common.cuh"
 
 namespace qmcspl {
@@ -223,6 +225,105 @@ __device__ __forceinline__ void five_table_task_x2(const EvalArgs& p, long long 
     if (p.lap) store_run<float, E>(static_cast<float*>(p.lap) + ip * p.n_orb + o0, acc[4], o0, p.n_orb, vec);
 }
 
+// Double-float tables (B-splines with separate gradient tables): every weight, product and sum
+// a double-float pair on the FP32 pipe (df_fma2, two orbitals per packed operation), as the
+// double-float B-spline kernel; the outputs are converted to double for the epilogue.
+template <int BASIS>
+__device__ __forceinline__ void five_table_task_df(const EvalArgs& p, long long w0, int lane)
+{
+    const int L = 1 << p.lanes_log2;
+    const int sub = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const long long total = p.n_pos * p.tiles;
+    const size_t rowb = (size_t)p.row_stride * 8;
+    const size_t colb = (size_t)p.col_stride * 8;
+
+    const long long gid = w0 + (lane >> p.lanes_log2);
+    const bool active = gid < total;
+    const long long q = active ? gid / p.tiles : 0;
+    const int tile = active ? (int)(gid - q * p.tiles) : 0;
+    const long long ip = active ? order_index(p, q) : q;
+    int ix, iy, iz;
+    dfloat t[3];
+    bool ok;
+    if (p.rec) {   // kind-3 record: cell and double-float t
+        const float4* qr = static_cast<const float4*>(p.rec) + 2 * ip;
+        const float4 a = __ldg(qr), b = __ldg(qr + 1);
+        unpack_cell(__float_as_int(a.x), ix, iy, iz, ok);
+        t[0] = {a.y, a.z};
+        t[1] = {a.w, b.x};
+        t[2] = {b.y, b.z};
+    } else {
+        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+        double dx, dy, dz;
+        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, dx, dy, dz, ok);
+        t[0] = df_from_double(dx);
+        t[1] = df_from_double(dy);
+        t[2] = df_from_double(dz);
+    }
+    if (!active) return;
+    if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+    static_assert(BASIS == kFiveBSpline, "double-float five-table handles are B-splines");
+    dfloat lw[3][4], scratch[4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) bspline_weights_df(t[a], lw[a], scratch, nullptr);
+    int xs[4], ys[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        xs[j] = wrap1(ix + j - 1, p.nx);
+        ys[j] = wrap1(iy + j - 1, p.ny);
+    }
+    const int chunk = tile * L + sub;
+    const size_t off = (size_t)chunk * 16 + (size_t)iz * rowb;
+    f32x2 Ah[5], Al[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) Ah[k] = Al[k] = 0ull;
+#pragma unroll 1
+    for (int c = 0; c < 16; ++c) {
+        const int l = c >> 2, m = c & 3;
+        const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb + off;
+        const dfloat wxy = df_mul(lw[0][l], lw[1][m]);
+        const f32x2 xh = pack2(wxy.h, wxy.h), xl = pack2(wxy.l, wxy.l), nxh = pack2(-wxy.h, -wxy.h);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const char* base = static_cast<const char*>(p.tab[k]) + col;
+            uint4 raw[4];
+#pragma unroll
+            for (int n = 0; n < 4; ++n) raw[n] = ldg_table(p, base + n * rowb);
+            f32x2 Sh = 0ull, Sl = 0ull;
+#pragma unroll
+            for (int n = 0; n < 4; ++n) {
+                const f32x2 Bh = pack2u(raw[n].x, raw[n].y), Bl = pack2u(raw[n].z, raw[n].w);
+                const dfloat z = lw[2][n];
+                df_fma2(Sh, Sl, pack2(z.h, z.h), pack2(z.l, z.l), pack2(-z.h, -z.h), Bh, Bl);
+            }
+            df_fma2(Ah[k], Al[k], xh, xl, nxh, Sh, Sl);
+        }
+    }
+    constexpr int E = 2;
+    const int o0 = chunk * E;
+    if (o0 >= p.n_orb) return;
+    const bool vec = p.vec_out != 0;
+    double acc[5][E];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        float h0, h1, l0, l1;
+        unpack2(Ah[k], h0, h1);
+        unpack2(Al[k], l0, l1);
+        acc[k][0] = df_to_double(h0, l0);
+        acc[k][1] = df_to_double(h1, l1);
+    }
+    // Bloch: the gradient and Laplacian tables hold the periodic parts of grad phi, lap phi
+    if (p.phase) bloch_apply<double, E>(p, ip, acc[0], acc + 1, acc[4], false, false);
+    if (p.val) store_run<double, E>(static_cast<double*>(p.val) + ip * p.n_orb + o0, acc[0], o0, p.n_orb, vec);
+    if (p.grad)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            store_run<double, E>(static_cast<double*>(p.grad) + (ip * 3 + a) * p.n_orb + o0, acc[1 + a], o0,
+                                 p.n_orb, vec);
+    if (p.lap) store_run<double, E>(static_cast<double*>(p.lap) + ip * p.n_orb + o0, acc[4], o0, p.n_orb, vec);
+}
+
 #ifndef QMCSPL_FIVE_THREADS
 #define QMCSPL_FIVE_THREADS 512
 #endif
@@ -238,7 +339,8 @@ __global__ void __launch_bounds__(THREADS, 1) five_table_vgl_kernel(const EvalAr
     const long long warp = (long long)blockIdx.x * WPB + (threadIdx.x >> 5);
     const long long wstride = (long long)gridDim.x * WPB;
     for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
-        if constexpr (sizeof(T) == 8) five_table_task<T, BASIS>(p, w0, lane);
+        if constexpr (std::is_same<T, DF64Tag>::value) five_table_task_df<BASIS>(p, w0, lane);
+        else if constexpr (sizeof(T) == 8) five_table_task<T, BASIS>(p, w0, lane);
         else five_table_task_x2<T, BASIS>(p, w0, lane);
     }
 }
@@ -558,7 +660,7 @@ EvalArgs make_args(const Handle* h, const double* pos, const Prepared& pr, long 
     a.val = val;
     a.grad = grad;
     a.lap = lap;
-    const size_t ob = (h->storage == QMCSPL_F64) ? 8 : 4;
+    const size_t ob = (h->storage == QMCSPL_F64 || h->storage == QMCSPL_DF64) ? 8 : 4;
     const uintptr_t al = (uintptr_t)val | (uintptr_t)grad | (uintptr_t)lap;
     a.vec_out = ((h->n_orb * ob) % 16 == 0) && (al % 16 == 0);
     return a;
@@ -574,6 +676,7 @@ int launch_five_table_vgl(const Handle* h, const double* pos, const Prepared& pr
     switch (h->storage) {
     case QMCSPL_F64: return lag ? launch_five<double, kFiveLagrange>(a, st) : launch_five<double, kFiveBSpline>(a, st);
     case QMCSPL_F32: return lag ? launch_five<float, kFiveLagrange>(a, st) : launch_five<float, kFiveBSpline>(a, st);
+    case QMCSPL_DF64: return launch_five<DF64Tag, kFiveBSpline>(a, st);   // B-splines only (qmcspl_create)
     default:
         return lag ? launch_five<__nv_bfloat16, kFiveLagrange>(a, st) : launch_five<__nv_bfloat16, kFiveBSpline>(a, st);
     }

@@ -86,10 +86,9 @@ def test_validation_without_gpu(lib):
     nonfinite[0, 0] = np.nan
     rc, _ = _create(lib, lat, (8, 8, 8), mil, nonfinite, bloch=1, kpoint=(0.5, 0.0, 0.0))
     assert rc == _lib.ERR_ARG and b"non-finite" in lib.qmcspl_last_error()
-    # separate gradient tables need the Laplacian table and are not available in double-float
+    # separate gradient tables need the Laplacian table
     rc, _ = _create(lib, lat, (8, 8, 8), mil, coef, sep=0, sep_grad=1)
     assert rc == _lib.ERR_ARG and b"separate_lap" in lib.qmcspl_last_error()
-    assert _create(lib, lat, (8, 8, 8), mil, coef, storage=3, sep=1, sep_grad=1)[0] == _lib.ERR_UNSUPPORTED
     # NULL handle calls
     assert lib.qmcspl_eval_vgl(None, None, 0, None, None, None, None) == _lib.ERR_ARG
     assert lib.qmcspl_sync(None, None) == _lib.ERR_ARG

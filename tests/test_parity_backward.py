@@ -285,7 +285,8 @@ def five_forward(method, tabs, lat, pos, k=None):
 
 
 @pytest.mark.parametrize("kw", FIVE, ids=["lagrange", "smooth_sepgrad", "interp_sepgrad", "pp"])
-@pytest.mark.parametrize("storage,tol_lin,tol_fd", [("f64", 1e-11, 1e-6), ("f32", 2e-5, 3e-3)])
+@pytest.mark.parametrize("storage,tol_lin,tol_fd", [("f64", 1e-11, 1e-6), ("df64", 1e-11, 1e-6),
+                                                     ("f32", 2e-5, 3e-3)])
 @pytest.mark.parametrize("bloch", [False, True])
 def test_five_table_backward_linearity_and_position_fd(kw, storage, tol_lin, tol_fd, bloch):
     """Five-table handles (the outputs are the values of five interpolants) and pp-splines
@@ -293,6 +294,8 @@ def test_five_table_backward_linearity_and_position_fd(kw, storage, tol_lin, tol
     coefficient adjoint is checked by sum(dL/dbeta * beta') = L(beta') with the oracle on random
     tables, and the position adjoint against central differences of the oracle forward
     (positions away from grid planes, where the Lagrange interpolant's derivatives jump)."""
+    if storage == "df64" and not kw.get("separate_grad"):
+        pytest.skip("double-float tables are for B-splines")
     dims = (10, 11, 12)
     n_orb = 3
     k = inputs.KPOINTS["generic"] if bloch else None
@@ -310,7 +313,7 @@ def test_five_table_backward_linearity_and_position_fd(kw, storage, tol_lin, tol
     n = pos.shape[0]
     if bloch:
         g = complex_upstream(n, n_orb, 1802)
-        cd = torch.complex128 if storage == "f64" else torch.complex64
+        cd = torch.complex128 if storage in ("f64", "df64") else torch.complex64
     else:
         g = inputs.upstream_weights(n, n_orb, 1802)
         cd = spl.out_dtype

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("method", ["smooth", "interp"])
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "df64", "f32", "bf16"])
 @pytest.mark.parametrize("n_orb", [3, 16])
 def test_separate_gradient_tables_match_oracle(method, storage, n_orb):
     dims = (9, 10, 11)
@@ -22,7 +22,7 @@ def test_separate_gradient_tables_match_oracle(method, storage, n_orb):
     inf = spl.info()
     assert inf["n_tables"] == 5 and inf["separate_grad"] == 1
     ref_t = oracle.derivative_tables(method, lat, mil, coef, dims)
-    ttol = {"f64": 1e-12, "f32": 1e-7, "bf16": 8e-3}[storage]
+    ttol = {"f64": 1e-12, "df64": 1e-12, "f32": 1e-7, "bf16": 8e-3}[storage]
     tabs = np.stack([spl.get_table(i) for i in range(5)])
     for i in range(5):
         assert oracle.relative_error(tabs[i], ref_t[i]) < ttol
@@ -39,7 +39,7 @@ def test_separate_gradient_tables_match_oracle(method, storage, n_orb):
     spl.close()
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "df64", "f32"])
 def test_separate_gradient_tables_for_bloch_orbitals(storage):
     kp = inputs.KPOINTS["generic"]
     dims = (9, 10, 11)
@@ -49,7 +49,7 @@ def test_separate_gradient_tables_for_bloch_orbitals(storage):
     ref_t = oracle.bloch_tables("smooth", lat, mil, coef, kp, dims, gradient=True)
     tabs = np.stack([spl.get_table(i) for i in range(5)])
     for i in range(5):
-        assert oracle.relative_error(tabs[i], ref_t[i]) < (1e-12 if storage == "f64" else 1e-7)
+        assert oracle.relative_error(tabs[i], ref_t[i]) < (1e-7 if storage == "f32" else 1e-12)
     pos = inputs.positions(lat, 300, 1211, -1, 2)
     v, g, l = spl.eval_vgl(torch.from_numpy(pos).to(dev()))
     spl.sync()
