@@ -474,8 +474,8 @@ def bench_batched(args, dev, stream):
     import torch
     from paper_1309_6250_gb300 import autotune
     from paper_1309_6250_gb300.api import eval_batched
-    cache = os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(os.path.join(ROOT, "gpurun_out")) \
-        else None
+    import tempfile
+    cache = os.path.join(tempfile.gettempdir(), "qmcspl_autotune.json")   # tuned shapes, reused within a machine
     cells, shapes, evals = [], {}, 0
     for key in ("c4-al32", "c4-si64", "c4-mgo16"):
         w = inputs.make_workload(key)

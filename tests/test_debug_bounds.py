@@ -1,5 +1,5 @@
-"""The bounds-checked build (QMCSPL_DEBUG_BOUNDS; the survey's stand-in for a memory
-sanitizer, which this GPU pool does not offer): every table load and every position index of
+"""The bounds-checked build (QMCSPL_DEBUG_BOUNDS, a stand-in for a memory sanitizer, which is
+not available for these runs): every table load and every position index of
 the kernels is range checked, a bad one is recorded in the error word and skipped.  The GPU
 parity suites run again against that build in a subprocess; their sync() calls would report
 any flagged access as QMCSPL_ERR_DEVICE."""
