@@ -461,3 +461,35 @@ def test_general_backward_bloch_on_a_graded_grid():
             lp.append(sum(np.sum((np.conj(gi) * zi).real.reshape(n, -1), axis=1) for gi, zi in zip(g, z)))
         fd[:, a] = (lp[0] - lp[1]) / (2 * h)
     assert oracle.relative_error(dpos, fd) < 1e-6
+
+
+def test_general_backward_nonfinite_position_and_empty_call():
+    """A non-finite position gives NaN dL/dr for that position only and adds nothing to dbeta;
+    an empty call is a no-op (degree 5 on a graded grid, FP64)."""
+    dims = (8, 9, 10)
+    lat, mil, coef = inputs.random_cell(1820, dims, 4, 6.0, 5.0, NONORTHO)
+    knots = graded(dims)
+    spl = splines(lat, dims, mil, coef, method="interp", storage="f64", separate_lap=False, degree=5,
+                  knots=knots)
+    pos = inputs.positions(lat, 12, 1821, -1, 2)
+    gv, gg, gl = inputs.upstream_weights(12, 4, 1822)
+    bad = pos.copy()
+    bad[5] = np.nan
+    from paper_1309_6250_gb300 import _lib
+    dcb = torch.zeros(spl.coef_shape(), dtype=torch.float64, device=dev())
+    dpb = spl.backward(t(bad, torch.float64), t(gv, torch.float64), t(gg, torch.float64), t(gl, torch.float64),
+                       dcoef=dcb)
+    with pytest.raises(_lib.QmcsplError) as ei:     # the non-finite position is reported
+        spl.sync()
+    assert ei.value.code == _lib.ERR_DEVICE
+    dc_bad, dpos_bad = dcb.cpu().numpy(), dpb.cpu().numpy()
+    keep = np.arange(12) != 5
+    dc_ok, _, dpos_ok = gpu_backward(spl, pos[keep], gv[keep], gg[keep], gl[keep])
+    assert np.all(np.isnan(dpos_bad[5])) and np.all(np.isfinite(dpos_bad[keep]))
+    assert oracle.relative_error(dpos_bad[keep], dpos_ok) < 1e-13
+    assert oracle.relative_error(dc_bad, dc_ok) < 1e-13
+    empty = torch.zeros((0, 3), dtype=torch.float64, device=dev())
+    dc = torch.zeros(spl.coef_shape(), dtype=torch.float64, device=dev())
+    out = spl.backward(empty, dcoef=dc)
+    spl.sync()
+    assert out.shape == (0, 3) and float(dc.abs().sum()) == 0.0
