@@ -265,9 +265,23 @@ def l1_roofline(gather_bytes, launch_s, clocks):
             "peak_kind": "derived: 128 B/clk/SM x 152 SMs x %.0f MHz" % mhz}
 
 
-def _time_handle(spl, pos, torch, stream, steps):
+def _time_handle(spl, pos, torch, stream, steps, graph=True):
+    """Mean ms per qmcspl_eval_vgl call (records, sort and evaluation), as CUDA-graph replays
+    like the main step (small cells are otherwise dominated by the launch gaps of the call's
+    four kernels), or eager calls."""
     out = spl.alloc_outputs(pos.shape[0])
     step = lambda: spl.eval_vgl(pos, out=out)
+    if graph:
+        cap = torch.cuda.Stream()
+        cap.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(cap):
+            spl.eval_vgl(pos, out=out, stream=cap)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=cap):
+                spl.eval_vgl(pos, out=out, stream=cap)
+        torch.cuda.synchronize()
+        step = g.replay
     ms = time_steps(step, steps, 3, torch, stream)
     spl.sync()
     return sum(ms) / len(ms)
@@ -288,10 +302,12 @@ def bench_methods(args, dev, stream):
         spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method=method, storage="f32",
                              separate_lap=sep, device=dev)
         t = _time_handle(spl, pos, torch, stream, max(10, args.steps // 4))
-        out[name] = {"value": evals / (t * 1e-3), "ms_per_step": t, "table_bytes": spl.info()["table_bytes"]}
+        te = _time_handle(spl, pos, torch, stream, max(10, args.steps // 4), graph=False)
+        out[name] = {"value": evals / (t * 1e-3), "ms_per_step": t, "eager_ms_per_step": te,
+                     "table_bytes": spl.info()["table_bytes"]}
         spl.close()
-    return {"workload": "c2 Si-like 8-atom, 16 orbitals, 48^3, 32768 positions, f32 tables", "unit": UNIT,
-            "results": out}
+    return {"workload": "c2 Si-like 8-atom, 16 orbitals, 48^3, 32768 positions, f32 tables, CUDA-graph replays",
+            "unit": UNIT, "results": out}
 
 
 def bench_methods_c3(args, dev, stream, clocks=None):
@@ -461,8 +477,8 @@ def bench_general(args, dev, stream):
         t = _time_handle(spl, pos, torch, stream, max(10, args.steps // 4))
         out[name] = {"value": evals / (t * 1e-3), "ms_per_step": t}
         spl.close()
-    return {"workload": "c2 Si-like 8-atom, 16 orbitals, 48^3, 32768 positions, f32 interpolating + Lap",
-            "unit": UNIT, "results": out}
+    return {"workload": "c2 Si-like 8-atom, 16 orbitals, 48^3, 32768 positions, f32 interpolating + Lap, "
+                        "CUDA-graph replays", "unit": UNIT, "results": out}
 
 
 def bench_batched(args, dev, stream):
