@@ -15,8 +15,10 @@
 // basis polynomials followed by the chain rule of Sec. II.
 //
 // Work mapping, loads and stores as in eval_bspline.cu: a group of L lanes per
-// position, one 16-byte chunk of each row per lane.  Bloch orbitals (Sec. II) take the
-// same epilogue as the B-splines (bloch_apply).
+// position, one 16-byte chunk of each row per lane, one block per SM.  Float and bfloat16
+// tables sum on packed FP32 pairs with the rows of the next load units in flight; double
+// tables take a scalar path, double-float tables (B-splines) double-float arithmetic.  Bloch
+// orbitals (Sec. II) take the same epilogue as the B-splines (bloch_apply).
 #include <type_traits>
 
 #include "eval_common.cuh"
