@@ -252,7 +252,7 @@ __device__ __forceinline__ dfloat df_recip(dfloat d)
 // Ah, Al of [n][ns] with ns = n rounded up to even, plus 2 (zero padding columns stay zero
 // through the elimination), so that column pairs (j, j+1) are one 8-byte word of each.
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT, 1) slater_df_kernel(const SlaterArgs a)
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) slater_df_kernel(const SlaterArgs a)
 {
     extern __shared__ float fsm[];
     __shared__ double red[NT / 32];
@@ -990,10 +990,14 @@ int launch_slater(const SlaterArgs& a, int nmax, cudaStream_t st)
     if (a.arith == 1) {
         const int ns = ((nmax + 1) & ~1) + 2;
         const size_t smem = 2 * (size_t)nmax * ns * sizeof(float);
-        cudaError_t e = cudaFuncSetAttribute(slater_df_kernel<T, kSlaterDfThreads>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // blocks that fit twice in shared memory: two 256-thread CTAs per SM, as for the
+        // complex double-float kernel (static shared memory under 9 KB; 227 KB per SM)
+        const bool two = 2 * (smem + 9 * 1024) <= 227 * 1024;
+        auto k = two ? slater_df_kernel<T, 256> : slater_df_kernel<T, kSlaterDfThreads>;
+        const int nt = two ? 256 : kSlaterDfThreads;
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(slater_df_kernel)");
-        slater_df_kernel<T, kSlaterDfThreads><<<(unsigned)a.n_walkers, kSlaterDfThreads, smem, st>>>(a);
+        k<<<(unsigned)a.n_walkers, nt, smem, st>>>(a);
         return cuda_error(cudaGetLastError(), "slater_df_kernel launch");
     }
     const size_t smem = (size_t)nmax * (nmax + 1) * sizeof(double);
