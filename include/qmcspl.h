@@ -51,7 +51,7 @@ enum qmcspl_status {
     QMCSPL_ERR_ARG = 1,            /* invalid argument (null pointer, size, enum value) */
     QMCSPL_ERR_CUDA = 2,           /* a CUDA runtime call failed */
     QMCSPL_ERR_OOM = 3,            /* device or host allocation failed */
-    QMCSPL_ERR_UNSUPPORTED = 4,    /* combination not supported (e.g. backward of pp) */
+    QMCSPL_ERR_UNSUPPORTED = 4,    /* combination not supported (e.g. batched degree-n handles) */
     QMCSPL_ERR_TIMEOUT = 5,        /* a bounded device wait gave up */
     QMCSPL_ERR_NOT_HERMITIAN = 6,  /* coefficients do not give a real (Gamma-point) orbital */
     QMCSPL_ERR_DEVICE = 7          /* a kernel flagged bad input (non-finite position) */
@@ -186,9 +186,11 @@ int qmcspl_create(qmcspl_t* out, const double lattice[9], const int dims[3], int
  * Other arguments as qmcspl_create; opts->method QMCSPL_BSPLINE_INTERP, or on uniform
  * grids also QMCSPL_BSPLINE_SMOOTH (Eq. b-splinecoefficients with gamma the Fourier
  * transform of the degree-n basis, C_n sinc^{n+1}(th/2) per axis); storage F64, F32 or BF16;
- * separate_grad 0 (else QMCSPL_ERR_UNSUPPORTED); Bloch orbitals are accepted.  dims[a] >= degree + 1.  Evaluation (qmcspl_eval_vgl, _host, _noalloc) has the
- * same outputs; the stencil is (n + 1)^3 points.  Backward and batched evaluation are not
- * available for these handles (QMCSPL_ERR_UNSUPPORTED).  grid = NULL is qmcspl_create.
+ * separate_grad 0 (else QMCSPL_ERR_UNSUPPORTED); Bloch orbitals are accepted.
+ * dims[a] >= degree + 1.  Evaluation (qmcspl_eval_vgl, _host, _noalloc) and the backward
+ * pass have the same outputs and arguments; the stencil is (n + 1)^3 points.  Batched
+ * evaluation is not available for these handles (QMCSPL_ERR_UNSUPPORTED).  grid = NULL is
+ * qmcspl_create.
  */
 typedef struct {
     int degree;
