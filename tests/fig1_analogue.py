@@ -10,14 +10,11 @@ orbitals per cutoff from the seeded generator (c_G ~ N(0,1) exp(-|G|^2/8) over t
 sphere, the MgO-like decay of the workload recipe); 2000 uniform positions.
 
 The approximations are evaluated by the GPU library through its C ABI; the reference is
-the oracle's direct planewave sum (CPU, FP64).  With --oracle the approximations come from
-the oracle as well (no GPU needed).
-
-    python tests/fig1_analogue.py [--storage f32] [--ecut 10 15 20 30 40] [--oracle]
+the oracle's direct planewave sum (CPU, FP64).  With use_oracle=True the approximations come
+from the oracle as well (no GPU needed).  tests/test_fig1_analogue.py runs both.
 """
 from __future__ import annotations
 
-import argparse
 import math
 import os
 import sys
@@ -121,51 +118,3 @@ def run_degrees(ecuts: Sequence[float] = ECUTS, degrees: Sequence[int] = (1, 3, 
                     res["lap_sep"] = m(l, pl)
             rows.append(res)
     return rows
-
-
-def degree_table(rows: List[Dict]) -> str:
-    out = ["| Ecut (Ha) | N | degree | value | grad | lap (Hessian) | lap (separate table) |",
-           "|---|---|---|---|---|---|---|"]
-    for r in rows:
-        out.append("| %g | %d | %s | %.2e | %.2e | %.2e | %.2e |" % (r["ecut"], r["dims"][0], r["row"][6:],
-                                                                  r["value"], r["grad"], r["lap"], r["lap_sep"]))
-    return "\n".join(out)
-
-
-def table(rows: List[Dict]) -> str:
-    """Markdown: one table per quantity, cutoffs down, rows of ROWS across."""
-    out = []
-    for what in ("value", "grad", "lap"):
-        out += ["", "%s:" % what, "",
-                "| Ecut (Ha) | N | PWs | " + " | ".join(r[0] for r in ROWS) + " |",
-                "|---|---|---|" + "---|" * len(ROWS)]
-        for ecut in sorted({r["ecut"] for r in rows}):
-            rs = {r["row"]: r for r in rows if r["ecut"] == ecut}
-            first = next(iter(rs.values()))
-            out.append("| %g | %d | %d | " % (ecut, first["dims"][0], first["n_pw"]) +
-                       " | ".join("%.2e" % rs[lab][what] for lab, _, _ in ROWS) + " |")
-    return "\n".join(out)
-
-
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--storage", default="f64", choices=["f64", "f32", "bf16"])
-    ap.add_argument("--ecut", type=float, nargs="*", default=list(ECUTS))
-    ap.add_argument("--oracle", action="store_true", help="approximations from the oracle (no GPU)")
-    ap.add_argument("--degrees", action="store_true",
-                    help="also tabulate interpolating B-splines of degree 1, 3, 5, 7 (GPU)")
-    args = ap.parse_args()
-    device = None
-    if not args.oracle:
-        import torch
-        device = torch.device("cuda", 0)
-    rows = run(args.ecut, args.storage, args.oracle, device=device)
-    print("approximations: %s%s" % ("oracle" if args.oracle else "GPU", "" if args.oracle else " " + args.storage))
-    print(table(rows))
-    if args.degrees and not args.oracle:
-        print("\ninterpolating B-splines by degree (GPU %s):\n" % args.storage)
-        print(degree_table(run_degrees(args.ecut, storage=args.storage, device=device)))
-
-
-if __name__ == "__main__":
-    main()

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_1309_6250_gb300 import inputs
-from gpu_helpers import NONORTHO, TOL, dev, rounded, splines
+from gpu_helpers import NONORTHO, TOL, dev, oracle_tables, rounded, splines
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -39,8 +39,7 @@ def test_fp64_backward_matches_oracle(method, sep, n_orb):
     dims = (9, 10, 11)
     lat, mil, coef = inputs.random_cell(600 + n_orb, dims, n_orb, 6.0, 5.0, NONORTHO)
     spl = splines(lat, dims, mil, coef, method=method, storage="f64", separate_lap=sep)
-    beta = spl.get_table(0)
-    blap = spl.get_table(1) if sep else None
+    beta, blap = oracle_tables(lat, mil, coef, dims, method, "f64", sep)
     pos = inputs.positions(lat, 300, 12, -1, 2)
     gv, gg, gl = inputs.upstream_weights(300, n_orb, 13)
     dc, dcl, dpos = gpu_backward(spl, pos, gv, gg, gl)
@@ -54,15 +53,14 @@ def test_fp64_backward_matches_oracle(method, sep, n_orb):
 @pytest.mark.parametrize("method", ["smooth", "interp"])
 @pytest.mark.parametrize("sep", [False, True])
 def test_df64_backward_matches_oracle(method, sep):
-    """Double-float tables: the adjoint runs in FP64 on the stored pairs, so it equals the
-    oracle adjoint on the tables as stored (get_table returns hi + lo) to FP64 rounding."""
+    """Double-float tables: the adjoint runs in FP64 on the stored pairs (hi + lo, the FP64
+    table to about 2^-48), so it equals the oracle adjoint on the oracle's FP64 tables."""
     dims = (9, 10, 11)
     n_orb = 6
     lat, mil, coef = inputs.random_cell(640, dims, n_orb, 6.0, 5.0, NONORTHO)
     spl = splines(lat, dims, mil, coef, method=method, storage="df64", separate_lap=sep)
     assert spl.out_dtype == torch.float64
-    beta = spl.get_table(0)
-    blap = spl.get_table(1) if sep else None
+    beta, blap = oracle_tables(lat, mil, coef, dims, method, "df64", sep)
     pos = inputs.positions(lat, 300, 641, -1, 2)
     gv, gg, gl = inputs.upstream_weights(300, n_orb, 642)
     dc, dcl, dpos = gpu_backward(spl, pos, gv, gg, gl)
@@ -114,12 +112,12 @@ def test_fp64_linearity_identity_and_position_fd():
 def test_c5_si64_backward_fp32():
     """Si-like 64-atom cell, 128 orbitals on 72^3, FP32 tables with the Laplacian table,
     4096 positions, N(0,1) upstream weights on value, gradient and Laplacian: coefficient
-    and position gradients against the oracle adjoint (FP64, same rounded tables)."""
+    and position gradients against the oracle adjoint (FP64) on the oracle's tables rounded to
+    FP32 as the GPU stores them."""
     w = inputs.make_workload("c5")
     dims = w.cell.grid
     spl = splines(w.lattice, dims, w.miller, w.coef, method="smooth", storage="f32", separate_lap=True)
-    beta = spl.get_table(0)       # the stored FP32 values, exactly
-    blap = spl.get_table(1)
+    beta, blap = oracle_tables(w.lattice, w.miller, w.coef, dims, "smooth", "f32", True)
     n = w.pos.shape[0]
     gv, gg, gl = inputs.upstream_weights(n, w.coef.shape[0], 3005)
     gv32, gg32, gl32 = (x.astype(np.float32).astype(np.float64) for x in (gv, gg, gl))
@@ -128,9 +126,9 @@ def test_c5_si64_backward_fp32():
     e = [oracle.relative_error(dc, rdc), oracle.relative_error(dcl, rdcl), oracle.relative_error(dpos, rdpos)]
     print("c5 backward relative errors (dcoef, dcoef_lap, dpos): %s" % ["%.2e" % x for x in e])
     assert e[0] < TOL["f32"] and e[1] < TOL["f32"] and e[2] < TOL["f32"]
-    # the exact tables were built from the same planewaves in FP64: within FP32 rounding
-    rb, _ = oracle.smoothing_tables(w.lattice, w.miller, w.coef[:8], dims)
-    assert oracle.relative_error(beta[..., :8], rb) < 1e-7
+    # the stored tables are the oracle's within FP32 rounding
+    assert oracle.relative_error(spl.get_table(0), beta) < 1e-7
+    assert oracle.relative_error(spl.get_table(1), blap) < 1e-7
 
 
 def test_autograd_function_positions_and_coefficients():
@@ -146,8 +144,8 @@ def test_autograd_function_positions_and_coefficients():
     loss = (v * t(gv, torch.float64)).sum() + (g * t(gg, torch.float64)).sum() + \
         (l * t(gl, torch.float64)).sum()
     loss.backward()
-    rdc, rdcl, rdpos = oracle.bspline_adjoint(spl.get_table(0), lat, pos_np, gv, gg, gl,
-                                              beta_lap=spl.get_table(1))
+    rb, rbl = oracle_tables(lat, mil, coef, dims, "smooth", "f64", True)
+    rdc, rdcl, rdpos = oracle.bspline_adjoint(rb, lat, pos_np, gv, gg, gl, beta_lap=rbl)
     assert oracle.relative_error(pos.grad.cpu().numpy(), rdpos) < 1e-12
     assert oracle.relative_error(beta.grad.cpu().numpy(), rdc) < 1e-12
     assert oracle.relative_error(beta_lap.grad.cpu().numpy(), rdcl) < 1e-12
@@ -156,8 +154,7 @@ def test_autograd_function_positions_and_coefficients():
     v, g, l = evaluate(spl, pos)
     (v * t(gv, torch.float64)).sum().backward()
     z = np.zeros_like(gg), np.zeros_like(gl)
-    _, _, rdpos_v = oracle.bspline_adjoint(spl.get_table(0), lat, pos_np, gv, z[0], z[1],
-                                           beta_lap=spl.get_table(1))
+    _, _, rdpos_v = oracle.bspline_adjoint(rb, lat, pos_np, gv, z[0], z[1], beta_lap=rbl)
     assert oracle.relative_error(pos.grad.cpu().numpy(), rdpos_v) < 1e-12
 
 
@@ -204,8 +201,8 @@ def gpu_backward_complex(spl, pos, g):
 def test_bloch_backward_linearity_and_position_fd(storage, tol_lin, tol_fd, sep):
     """L is linear in the stored tables: sum(dL/dbeta * beta') = L(beta') for random tables
     beta' evaluated by the oracle (Bloch forward: spline of u, then the phase and the product
-    rule); dL/dr against central differences of the oracle forward on the handle's own tables
-    (h = 1e-4 bohr, positions away from grid planes)."""
+    rule); dL/dr against central differences of the oracle forward on the oracle's tables rounded
+    as stored (h = 1e-4 bohr, positions away from grid planes)."""
     k = inputs.KPOINTS["generic"]
     dims = (10, 11, 12)
     n_orb = 3
@@ -226,8 +223,7 @@ def test_bloch_backward_linearity_and_position_fd(storage, tol_lin, tol_fd, sep)
         lin = np.sum(dc * b1) + (np.sum(dcl * b2) if sep else 0.0)
         ref = bloch_loss(z, g)
         assert abs(lin - ref) <= tol_lin * max(1.0, abs(ref)), (lin, ref)
-    beta = spl.get_table(0)
-    blap = spl.get_table(1) if sep else None
+    beta, blap = oracle_tables(lat, mil, coef, dims, "smooth", storage, sep, kpoint=k)
     h = 1e-4
     fd = np.zeros_like(dpos)
     for a in range(3):
@@ -333,7 +329,8 @@ def test_five_table_backward_linearity_and_position_fd(kw, storage, tol_lin, tol
         ref = loss(five_forward(kw["method"], b5, lat, pos, k))
         lin = np.sum(dc * b5)
         assert abs(lin - ref) <= tol_lin * max(1.0, abs(ref)), (lin, ref)
-    tabs = np.stack([spl.get_table(i) for i in range(n_tab)])
+    tabs = oracle_tables(lat, mil, coef, dims, kw["method"], storage, kw["separate_lap"],
+                         kw.get("separate_grad", False), kpoint=k)
     h = 1e-4
     fd = np.zeros_like(dpos)
     for a in range(3):
@@ -397,16 +394,15 @@ GENERAL = [(d, g, "f64", sep) for d, g in ((1, False), (5, False), (7, False), (
 @pytest.mark.parametrize("degree,grad,storage,sep", GENERAL)
 def test_general_backward_matches_oracle(degree, grad, storage, sep):
     """Coefficient and position adjoints of degree-n B-splines (interpolating; graded grids)
-    against the oracle's brute-force transpose of its evaluation, on the handle's own stored
-    tables; ragged orbital count, positions outside the cell."""
+    against the oracle's brute-force transpose of its evaluation, on the oracle's tables rounded
+    as stored; ragged orbital count, positions outside the cell."""
     dims = (8, 9, 10)
     n_orb = 5
     knots = graded(dims) if grad else None
     lat, mil, coef = inputs.random_cell(1800 + degree, dims, n_orb, 6.0, 5.0, NONORTHO)
     spl = splines(lat, dims, mil, coef, method="interp", storage=storage, separate_lap=sep, degree=degree,
                   knots=knots)
-    beta = spl.get_table(0)
-    blap = spl.get_table(1) if sep else None
+    beta, blap = oracle_tables(lat, mil, coef, dims, "interp", storage, sep, degree=degree, knots=knots)
     n = 60
     pos = inputs.positions(lat, n, 1801 + degree, -1, 2)
     gv, gg, gl = inputs.upstream_weights(n, n_orb, 1802)
@@ -449,7 +445,7 @@ def test_general_backward_bloch_on_a_graded_grid():
         lin = np.sum(dc * b1) + np.sum(dcl * b2)
         ref = bloch_loss(forward(b1, b2, pos), g)
         assert abs(lin - ref) <= 1e-11 * max(1.0, abs(ref)), (lin, ref)
-    beta, blap = spl.get_table(0), spl.get_table(1)
+    beta, blap = oracle_tables(lat, mil, coef, dims, "interp", "f64", True, kpoint=k, degree=5, knots=knots)
     h = 1e-5
     fd = np.zeros_like(dpos)
     for a in range(3):

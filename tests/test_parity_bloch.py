@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_1309_6250_gb300 import inputs
-from gpu_helpers import NONORTHO, TOL, assert_parity, dev, splines
+from gpu_helpers import NONORTHO, TOL, assert_parity, dev, oracle_tables, splines
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -27,14 +27,11 @@ def gpu_eval_c(spl, pos):
             l.cpu().numpy().astype(np.complex128))
 
 
-def oracle_from_gpu_tables(spl, method, lat, kp, pos, sep):
-    """Oracle evaluation of the tables the GPU stored (exact values of its rounding)."""
+def oracle_reference(method, storage, lat, mil, coef, kp, dims, pos, sep):
+    """Oracle evaluation of the oracle's own tables, rounded the way the GPU stores them."""
+    tabs = oracle_tables(lat, mil, coef, dims, method, storage, sep, kpoint=kp)
     if method in ("smooth", "interp"):
-        beta = spl.get_table(0)
-        blap = spl.get_table(1) if sep else None
-        return oracle.bloch_eval(method, beta, lat, kp, pos, tables_lap=blap)
-    n = 5 if method == "lagrange" else 8
-    tabs = np.stack([spl.get_table(i) for i in range(n)])
+        return oracle.bloch_eval(method, tabs[0], lat, kp, pos, tables_lap=tabs[1])
     return oracle.bloch_eval(method, tabs, lat, kp, pos)
 
 
@@ -64,7 +61,7 @@ def test_bloch_tables_and_outputs_match_oracle(method, storage, sep):
         assert oracle.relative_error(got, ref) < ttol
     pos = inputs.positions(lat, 300, 901, -1, 2)
     got = gpu_eval_c(spl, pos)
-    ref = oracle_from_gpu_tables(spl, method, lat, KGEN, pos, sep)
+    ref = oracle_reference(method, storage, lat, mil, coef, KGEN, dims, pos, sep)
     assert_parity(got, ref, TOL[storage], "bloch %s/%s/sep=%d" % (method, storage, sep))
     # the planewave sum itself, within the approximation error (grid above natural spacing)
     if storage == "f64" and method != "lagrange":

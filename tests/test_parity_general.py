@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 from paper_1309_6250_gb300 import inputs
-from gpu_helpers import NONORTHO, TOL, assert_parity, dev, gpu_eval, splines
+from gpu_helpers import NONORTHO, TOL, assert_parity, dev, gpu_eval, oracle_tables, splines
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -38,8 +38,8 @@ def test_general_tables_and_outputs_match_oracle(degree, nonuni, storage, sep):
         assert oracle.relative_error(spl.get_table(1), rl) < TTOL[storage]
     pos = inputs.positions(lat, 60, 1401, -1, 2)
     got = gpu_eval(spl, pos)
-    ref = oracle.general_eval(spl.get_table(0), lat, pos, degree, kk,
-                              beta_lap=spl.get_table(1) if sep else None)
+    ob, ol = oracle_tables(lat, mil, coef, dims, "interp", storage, sep, degree=degree, knots=knots)
+    ref = oracle.general_eval(ob, lat, pos, degree, kk, beta_lap=ol)
     assert_parity(got, ref, TOL[storage], "degree %d nonuni=%d %s sep=%d" % (degree, nonuni, storage, sep))
     spl.close()
 
@@ -136,7 +136,8 @@ def test_general_with_position_records_matches_oracle(degree, nonuni, storage):
     v, g, l = gpu_eval(spl, pos)
     sample = np.arange(0, 9000, 211)
     kk = knots if nonuni else (None,) * 3
-    ref = oracle.general_eval(spl.get_table(0), lat, pos[sample], degree, kk)
+    ob, _ = oracle_tables(lat, mil, coef, dims, "interp", storage, False, degree=degree, knots=knots)
+    ref = oracle.general_eval(ob, lat, pos[sample], degree, kk)
     assert_parity((v[sample], g[sample], l[sample]), ref, TOL[storage], "records deg %d %s" % (degree, storage))
     spl.close()
 
@@ -156,6 +157,7 @@ def test_smoothing_of_other_degrees_matches_oracle(degree, storage):
             assert oracle.relative_error(spl.get_table(1), rl) < TTOL[storage]
         pos = inputs.positions(lat, 50, 1451, -1, 2)
         got = gpu_eval(spl, pos)
-        ref = oracle.general_eval(spl.get_table(0), lat, pos, degree, beta_lap=spl.get_table(1) if sep else None)
+        ob, ol = oracle_tables(lat, mil, coef, dims, "smooth", storage, sep, degree=degree)
+        ref = oracle.general_eval(ob, lat, pos, degree, beta_lap=ol)
         assert_parity(got, ref, TOL[storage], "smoothing degree %d %s sep=%d" % (degree, storage, sep))
         spl.close()

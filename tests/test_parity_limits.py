@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 from paper_1309_6250_gb300 import inputs
-from gpu_helpers import NONORTHO, TOL, assert_parity, dev, gpu_eval, splines
+from gpu_helpers import NONORTHO, TOL, assert_parity, dev, gpu_eval, oracle_tables, splines
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -37,7 +37,7 @@ def test_maximum_grid_axis_and_boundary_positions(storage):
     mil = mil[np.all(np.abs(mil[:, 1:]) <= 1, axis=1)]             # keep the short axes resolved
     coef = inputs.pw_coefficients(lat, mil, 3, 6.0, 1501)
     spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=True)
-    beta, blap = spl.get_table(0), spl.get_table(1)
+    beta, blap = oracle_tables(lat, mil, coef, dims, "smooth", storage, True)
     pos = boundary_positions(lat, dims)
     got = gpu_eval(spl, pos)
     ref = oracle.bspline_eval(beta, lat, pos, beta_lap=blap)
@@ -63,7 +63,8 @@ def test_large_ragged_orbital_count(storage):
     assert inf["n_orb_padded"] > 301
     pos = inputs.positions(lat, 200, 1503, -1, 2)
     got = gpu_eval(spl, pos)
-    ref = oracle.bspline_eval(spl.get_table(0), lat, pos)
+    beta, _ = oracle_tables(lat, mil, coef, dims, "smooth", storage, False)
+    ref = oracle.bspline_eval(beta, lat, pos)
     assert_parity(got, ref, TOL[storage], "301 orbitals " + storage)
 
 
@@ -93,15 +94,14 @@ def test_tiny_grids_every_method(dims, method, storage, sep):
     and without records and cell order."""
     lat, mil, coef = inputs.random_cell(1510, dims, 5, 2.0, 3.0, NONORTHO)
     spl = splines(lat, dims, mil, coef, method=method, storage=storage, separate_lap=sep)
-    n_tab = {"lagrange": 5, "pp": 8}.get(method, 2 if sep else 1)
-    tabs = [spl.get_table(i) for i in range(n_tab)]
+    tabs = oracle_tables(lat, mil, coef, dims, method, storage, sep)
     pos = inputs.positions(lat, 60, 1511, -3, 4)
     if method in ("smooth", "interp"):
-        ref = oracle.bspline_eval(tabs[0], lat, pos, beta_lap=tabs[1] if sep else None)
+        ref = oracle.bspline_eval(tabs[0], lat, pos, beta_lap=tabs[1])
     elif method == "lagrange":
-        ref = oracle.lagrange_eval(np.stack(tabs), lat, pos)
+        ref = oracle.lagrange_eval(tabs, lat, pos)
     else:
-        ref = oracle.pp_eval(np.stack(tabs), lat, pos)
+        ref = oracle.pp_eval(tabs, lat, pos)
     assert_parity(gpu_eval(spl, pos), ref, TOL[storage], "tiny %s %s/%s" % (dims, method, storage))
     many = np.concatenate([pos] * 150)
     spl.set_order("cell")

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_1309_6250_gb300 import inputs
-from gpu_helpers import NONORTHO, TOL, assert_parity, dev, gpu_eval, splines
+from gpu_helpers import NONORTHO, TOL, assert_parity, dev, gpu_eval, oracle_tables, splines
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -23,9 +23,9 @@ def test_separate_gradient_tables_match_oracle(method, storage, n_orb):
     assert inf["n_tables"] == 5 and inf["separate_grad"] == 1
     ref_t = oracle.derivative_tables(method, lat, mil, coef, dims)
     ttol = {"f64": 1e-12, "df64": 1e-12, "f32": 1e-7, "bf16": 8e-3}[storage]
-    tabs = np.stack([spl.get_table(i) for i in range(5)])
     for i in range(5):
-        assert oracle.relative_error(tabs[i], ref_t[i]) < ttol
+        assert oracle.relative_error(spl.get_table(i), ref_t[i]) < ttol
+    tabs = oracle_tables(lat, mil, coef, dims, method, storage, True, True)
     pos = inputs.positions(lat, 400, 1201, -1, 2)
     got = gpu_eval(spl, pos)
     ref = oracle.bspline_eval_separate(tabs, lat, pos)
@@ -47,9 +47,9 @@ def test_separate_gradient_tables_for_bloch_orbitals(storage):
     spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=True,
                   separate_grad=True, kpoint=kp)
     ref_t = oracle.bloch_tables("smooth", lat, mil, coef, kp, dims, gradient=True)
-    tabs = np.stack([spl.get_table(i) for i in range(5)])
     for i in range(5):
-        assert oracle.relative_error(tabs[i], ref_t[i]) < (1e-7 if storage == "f32" else 1e-12)
+        assert oracle.relative_error(spl.get_table(i), ref_t[i]) < (1e-7 if storage == "f32" else 1e-12)
+    tabs = oracle_tables(lat, mil, coef, dims, "smooth", storage, True, True, kpoint=kp)
     pos = inputs.positions(lat, 300, 1211, -1, 2)
     v, g, l = spl.eval_vgl(torch.from_numpy(pos).to(dev()))
     spl.sync()

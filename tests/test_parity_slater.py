@@ -1,11 +1,15 @@
 """GPU Slater-determinant consumer (qmcspl_slater_kinetic) against the oracle's definition
-(numpy slogdet / inv) on the same orbital outputs, real and complex (Bloch orbitals)."""
+(numpy slogdet / inv) on the same orbital values, real and complex (Bloch orbitals).
+
+The orbital values both sides consume are the oracle's spline outputs (its own tables and
+evaluation), rounded to the dtype the consumer reads; nothing the oracle sees comes from the
+GPU."""
 import numpy as np
 import pytest
 
 import oracle
 from paper_1309_6250_gb300 import inputs
-from gpu_helpers import NONORTHO, dev, splines
+from gpu_helpers import NONORTHO, dev
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -16,6 +20,25 @@ def consumer(v, g, l, W, n_elec, n_up, arith="df64"):
     out = slater_kinetic(v, g, l, W, n_elec, n_up, arith=arith)
     torch.cuda.synchronize()
     return tuple(None if x is None else x.cpu().numpy() for x in out)
+
+
+def oracle_orbitals(lat, mil, coef, dims, pos, storage, kpoint=None):
+    """Smoothing B-spline outputs (with the Laplacian table) of the oracle at `pos`, as the
+    consumer reads them: float64, or rounded to float32 for storage 'f32' (what an FP32-table
+    handle would hand the consumer).  Returns (numpy arrays as the oracle sees them, device
+    tensors for the GPU)."""
+    if kpoint is None:
+        beta, blap = oracle.smoothing_tables(lat, mil, coef, dims, laplacian=True)
+        out = oracle.bspline_eval(beta, lat, pos, beta_lap=blap)
+    else:
+        beta, blap = oracle.bloch_tables("smooth", lat, mil, coef, kpoint, dims, laplacian=True)
+        out = oracle.bloch_eval("smooth", beta, lat, kpoint, pos, tables_lap=blap)
+    dt = {"f64": np.float64, "f32": np.float32}[storage]
+    if kpoint is not None:
+        dt = {np.float64: np.complex128, np.float32: np.complex64}[dt]
+    dev_out = tuple(torch.from_numpy(np.ascontiguousarray(x.astype(dt))).to(dev()) for x in out)
+    ref_in = tuple(x.astype(dt).astype(np.complex128 if kpoint is not None else np.float64) for x in out)
+    return ref_in, dev_out
 
 
 def compare(got, ref, rel=1e-9):
@@ -33,16 +56,12 @@ def compare(got, ref, rel=1e-9):
 def test_consumer_matches_oracle(storage, n_elec, n_up, n_orb, arith):
     dims = (12, 12, 12)
     lat, mil, coef = inputs.random_cell(1300 + n_elec, dims, n_orb, 8.0, 6.0, NONORTHO)
-    spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=True)
     W = 6
     pos = inputs.positions(lat, W * n_elec, 1301 + n_elec)
-    v, g, l = spl.eval_vgl(torch.from_numpy(pos).to(dev()))
-    spl.sync()
+    ref_in, (v, g, l) = oracle_orbitals(lat, mil, coef, dims, pos, storage)
     got = consumer(v, g, l, W, n_elec, n_up, arith)
-    ref = oracle.slater_kinetic(v.double().cpu().numpy(), g.double().cpu().numpy(), l.double().cpu().numpy(),
-                                W, n_elec, n_up)
+    ref = oracle.slater_kinetic(*ref_in, W, n_elec, n_up)
     compare(got, ref)
-    spl.close()
 
 
 @pytest.mark.parametrize("arith", ["f64", "df64"])
@@ -85,22 +104,17 @@ def test_consumer_rejects_bad_arguments():
 @pytest.mark.parametrize("arith", ["f64", "df64"])
 def test_consumer_c3_mgo64_full_batch(arith):
     """The MgO-like 64-atom workload as a QMC walker batch: 2048 walkers x 256 electrons,
-    128 up and 128 down, each block using all 128 orbitals of the FP32 smoothing spline
-    with the Laplacian table; every walker against the oracle."""
+    128 up and 128 down, each block using all 128 orbitals of the smoothing spline with the
+    Laplacian table (the oracle's outputs rounded to FP32, as an FP32-table handle gives them);
+    every 7th walker against the oracle."""
     w = inputs.make_workload("c3")
-    spl = splines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32", separate_lap=True)
-    v, g, l = spl.eval_vgl(torch.from_numpy(w.pos).to(dev()))
-    spl.sync()
+    ref_in, (v, g, l) = oracle_orbitals(w.lattice, w.miller, w.coef, w.cell.grid, w.pos, "f32")
     W, n_elec = w.cell.n_walkers, w.cell.n_elec
     got = consumer(v, g, l, W, n_elec, n_elec // 2, arith)
     sample = np.arange(0, W, 7)
     rows = np.concatenate([np.arange(s * n_elec, (s + 1) * n_elec) for s in sample])
-    vr = v.cpu().numpy()[rows].astype(np.float64)
-    gr = g.cpu().numpy()[rows].astype(np.float64)
-    lr = l.cpu().numpy()[rows].astype(np.float64)
-    ref = oracle.slater_kinetic(vr, gr, lr, len(sample), n_elec, n_elec // 2)
+    ref = oracle.slater_kinetic(*(x[rows] for x in ref_in), len(sample), n_elec, n_elec // 2)
     compare(tuple(x[sample] for x in got), ref, rel=1e-8)
-    spl.close()
 
 
 # ---------------------------------------------------------------------------
@@ -123,17 +137,13 @@ def test_complex_consumer_matches_oracle(storage, n_elec, n_up, n_orb, arith):
     k = inputs.KPOINTS["generic"]
     dims = (12, 12, 12)
     lat, mil, coef = inputs.random_bloch_cell(1900 + n_elec, n_orb, 8.0, 6.0, k, NONORTHO)
-    spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=True, kpoint=k)
     W = 6
     pos = inputs.positions(lat, W * n_elec, 1901 + n_elec, -1, 2)
-    v, g, l = spl.eval_vgl(torch.from_numpy(pos).to(dev()))
-    spl.sync()
+    ref_in, (v, g, l) = oracle_orbitals(lat, mil, coef, dims, pos, storage, kpoint=k)
     assert v.is_complex()
     got = consumer(v, g, l, W, n_elec, n_up, arith=arith)
-    ref = oracle.slater_kinetic(v.cpu().numpy().astype(np.complex128), g.cpu().numpy().astype(np.complex128),
-                                l.cpu().numpy().astype(np.complex128), W, n_elec, n_up)
+    ref = oracle.slater_kinetic(*ref_in, W, n_elec, n_up)
     compare_complex(got, ref)
-    spl.close()
 
 
 @pytest.mark.parametrize("arith", ["f64", "df64"])
