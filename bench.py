@@ -176,19 +176,48 @@ def rounded_table(t, storage):
     return torch.from_numpy(np.ascontiguousarray(t)).to(torch.bfloat16).double().numpy()
 
 
-def oracle_parity(w, storage, sample, got, tables):
-    """Max |gpu - oracle| / max |oracle| per output on sampled positions, the oracle evaluated on
-    the tables rounded as the GPU stores them (the tests' definition of the tolerance)."""
+TOLERANCE = {"f64": 1e-12, "df64": 1e-12, "f32": 2e-6, "bf16": 1e-2}
+
+
+def precision_report(storage, got, ref_fp64, ref_stored, sample_desc):
+    """Error of sampled GPU outputs per output (value, gradient, Laplacian), as
+    max |gpu - oracle| / max |oracle|:
+      max_rel_err_vs_fp64 -- against the oracle on the unrounded FP64 tables: what the storage
+                             type costs, plus the kernel's arithmetic;
+      max_rel_err_arith   -- against the oracle on the tables rounded the way the GPU stores
+                             them: the kernel's arithmetic alone (the parity tests' tolerance);
+      dT_mHa              -- the largest change of the kinetic-energy estimate
+                             T_n = -1/2 sum_p phi_n lap phi_n / sum_p phi_n^2 (Sec. I local energy,
+                             Sec. III A on the Laplacian) over the sampled positions, in mHa,
+                             against the unrounded FP64 oracle."""
+    import oracle
+    names = ("val", "grad", "lap")
+    vs64 = {k: float(oracle.relative_error(g, r)) for k, g, r in zip(names, got, ref_fp64)}
+    arith = {k: float(oracle.relative_error(g, r)) for k, g, r in zip(names, got, ref_stored)}
+    if np.iscomplexobj(got[0]):
+        # Bloch outputs: T_n from Re(conj(phi) lap phi) / |phi|^2
+        t_gpu = -0.5 * np.sum((np.conj(got[0]) * got[2]).real, 0) / np.sum(np.abs(got[0]) ** 2, 0)
+        t_ref = -0.5 * np.sum((np.conj(ref_fp64[0]) * ref_fp64[2]).real, 0) / np.sum(np.abs(ref_fp64[0]) ** 2, 0)
+    else:
+        t_gpu = oracle.kinetic_energy(got[0], got[2])
+        t_ref = oracle.kinetic_energy(ref_fp64[0], ref_fp64[2])
+    tol = TOLERANCE[storage]
+    return {"max_rel_err_vs_fp64": vs64, "max_rel_err_arith": arith,
+            "dT_mHa": float(1e3 * np.max(np.abs(t_gpu - t_ref))), "T_max_Ha": float(np.max(np.abs(t_ref))),
+            "tolerance": tol, "ok": all(e <= tol for e in arith.values()), "sample": sample_desc,
+            "reference": "FP64 oracle (oracle/), tables built by the oracle from the same planewaves"}
+
+
+def bspline_precision(w, storage, sample, got, tables):
+    """precision_report of B-spline outputs (value table + Laplacian table) at w.pos[sample]."""
     import oracle
     beta, blap = tables
-    ref = oracle.bspline_eval(rounded_table(beta, storage), w.lattice, w.pos[sample],
-                              beta_lap=rounded_table(blap, storage))
-    err = {k: float(oracle.relative_error(g, r)) for k, g, r in zip(("val", "grad", "lap"), got, ref)}
-    tol = {"f64": 1e-12, "df64": 1e-12, "f32": 2e-6, "bf16": 1e-2}[storage]
-    return {"max_rel_err": err, "tolerance": tol, "ok": all(e <= tol for e in err.values()),
-            "sample": "%d positions (every %d-th of the step) x %d orbitals" % (len(sample), int(sample[1] - sample[0])
-                                                                    if len(sample) > 1 else 1, w.coef.shape[0]),
-            "reference": "FP64 oracle on the %s-rounded tables" % storage}
+    ref64 = oracle.bspline_eval(beta, w.lattice, w.pos[sample], beta_lap=blap)
+    refst = oracle.bspline_eval(rounded_table(beta, storage), w.lattice, w.pos[sample],
+                                beta_lap=rounded_table(blap, storage))
+    desc = "%d positions (every %d-th of the step) x %d orbitals" % (
+        len(sample), int(sample[1] - sample[0]) if len(sample) > 1 else 1, got[0].shape[-1])
+    return precision_report(storage, got, ref64, refst, desc)
 
 
 def cpu_baseline(w, storage, sep, budget_s=12.0, tables=None):
@@ -220,6 +249,15 @@ def cpu_baseline(w, storage, sep, budget_s=12.0, tables=None):
             "single_thread": {"value": n1 * n_orb / dt1, "sample": "%d positions" % n1, "seconds": dt1}}
 
 
+def workload_config(w, ws=1):
+    """The benchmark's workload, the same dict for both arms (no launch details)."""
+    return {"workload": w.cell.name, "method": "smoothing B-spline + separate Laplacian table",
+            "n_orb": int(w.coef.shape[0]), "grid": list(w.cell.grid), "walkers": w.cell.n_walkers,
+            "electrons": w.cell.n_elec, "positions": int(w.pos.shape[0]),
+            "l2": "table and outputs larger than L2 (no flush needed)",
+            "parallelism": "replicas" if ws > 1 else "single"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -243,26 +281,37 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": w.cell.name, "n_orb": n_orb,
-                                            "grid": list(w.cell.grid), "positions_per_step": n},
+            "data": "synthetic", "config": workload_config(w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d positions x %d orbitals per step" % (n, n_orb)},
+                             "sample": "%d positions x %d orbitals per step (a bounded sample of the "
+                                       "workload's %d positions), FP64 tables prebuilt"
+                                       % (n, n_orb, w.pos.shape[0])},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def l1_roofline(gather_bytes, launch_s, clocks):
-    """Every gathered stencil byte passes through the SM's L1/LSU data path, which moves
-    at most one 128-byte wavefront per clock per SM: 128 B x 152 SMs x the SM clock
-    (2070 MHz maximum, or the median clock sampled under load).  In cell order this path,
-    not HBM, bounds the gather."""
-    mhz = 2070.0
-    if clocks and clocks.get("sm_mhz"):
-        mhz = float(clocks["sm_mhz"])
-    peak = 128.0 * 152 * mhz * 1e6 / 1e9
+def probe_l1(dev):
+    """The SMs' L1 data-path rate for 16-byte loads, measured on this GPU by the library's
+    probe (qmcspl_probe_l1): GB/s over all SMs, bytes per SM clock, and the SM clock it ran at."""
+    import ctypes
+    import torch
+    from paper_1309_6250_gb300 import _lib
+    lib = _lib.load()
+    g, b, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    with torch.cuda.device(dev):
+        _lib.check(lib.qmcspl_probe_l1(ctypes.byref(g), ctypes.byref(b), ctypes.byref(m),
+                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return {"gbs": g.value, "bytes_per_clk_per_sm": b.value, "sm_mhz": m.value,
+            "how": "qmcspl_probe_l1: 2 x 1024 threads per SM, 16-byte ld.global.nc over a 64 KB "
+                   "L1-resident buffer, 8 loads in flight per thread, best of 5 CUDA-event-timed launches"}
+
+
+def l1_roofline(gather_bytes, launch_s, l1):
+    """Every gathered stencil byte passes through the SM's L1 data path; in cell order most of
+    them hit there, and this path, not HBM, bounds the gather.  Peak: the probe's measured rate."""
     achieved = gather_bytes / launch_s / 1e9
-    return {"bound": "l1", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_kind": "derived: 128 B/clk/SM x 152 SMs x %.0f MHz" % mhz}
+    return {"bound": "l1", "achieved": achieved, "peak": l1["gbs"], "unit": "GB/s",
+            "frac": achieved / l1["gbs"], "peak_kind": "measured in this run (qmcspl_probe_l1)"}
 
 
 def _time_handle(spl, pos, torch, stream, steps, graph=True):
@@ -310,25 +359,55 @@ def bench_methods(args, dev, stream):
             "unit": UNIT, "results": out}
 
 
-def bench_methods_c3(args, dev, stream, clocks=None):
+METHOD_LEGS_C3 = (("smooth", dict(method="smooth", separate_lap=False)),
+                  ("interp_lap", dict(method="interp", separate_lap=True)),
+                  ("lagrange", dict(method="lagrange", separate_lap=True)),
+                  ("smooth_sep_grad", dict(method="smooth", separate_lap=True, separate_grad=True)),
+                  ("pp", dict(method="pp", separate_lap=False)))
+
+
+def method_oracle(name, lat, mil, coef, dims, pos, storage):
+    """Oracle outputs of one basis of METHOD_LEGS_C3 at pos: (on the unrounded FP64 tables,
+    on the tables rounded as `storage` stores them)."""
+    import oracle
+    if name == "smooth":
+        t = oracle.smoothing_tables(lat, mil, coef, dims)
+        ev = lambda tt: oracle.bspline_eval(tt[0], lat, pos)
+    elif name == "interp_lap":
+        t = oracle.interpolating_tables(lat, mil, coef, dims, laplacian=True)
+        ev = lambda tt: oracle.bspline_eval(tt[0], lat, pos, beta_lap=tt[1])
+    elif name == "lagrange":
+        t = (oracle.lagrange_tables(lat, mil, coef, dims),)
+        ev = lambda tt: oracle.lagrange_eval(tt[0], lat, pos)
+    elif name == "smooth_sep_grad":
+        t = (oracle.derivative_tables("smooth", lat, mil, coef, dims),)
+        ev = lambda tt: oracle.bspline_eval_separate(tt[0], lat, pos)
+    else:
+        t = (oracle.pp_tables(oracle.grid_values(lat, mil, coef, dims)),)
+        ev = lambda tt: oracle.pp_eval(tt[0], lat, pos)
+    return ev(t), ev(tuple(rounded_table(x, storage) for x in t))
+
+
+def bench_methods_c3(args, dev, stream, l1):
     """The paper's bases at the 128-orbital scale: MgO-like 64-atom cell, 96^3, 2048 walkers x
     256 electrons, FP32 tables, cell order.  Per method the evaluation kernel's own time
-    (library CUDA events) and its gathered bytes against the L1/LSU data-path peak: smoothing
-    without the Laplacian table (Hessian Laplacian, 1 table), interpolating with it (2 tables),
-    Lagrange and B-splines with separate gradient tables (5 tables each), pp (8 points x 8
-    entries = 64 values, as one table)."""
+    (library CUDA events) and its gathered bytes against the measured L1 data-path peak:
+    smoothing without the Laplacian table (Hessian Laplacian, 1 table), interpolating with it
+    (2 tables), Lagrange and B-splines with separate gradient tables (5 tables each), pp (8
+    points x 8 entries = 64 values, as one table).  Per method also the error of the first 16
+    orbitals at every 512th position against the FP64 oracle (unrounded and FP32-rounded
+    tables) and the kinetic-energy change it causes."""
     import torch
     from paper_1309_6250_gb300.api import OrbitalSplines
     w = inputs.make_workload("c3")
     pos = torch.from_numpy(w.pos).to(dev)
     n_pos, n_orb = w.pos.shape[0], w.coef.shape[0]
     evals = n_pos * n_orb
-    out = {}
-    for name, kw in (("smooth", dict(method="smooth", separate_lap=False)),
-                     ("interp_lap", dict(method="interp", separate_lap=True)),
-                     ("lagrange", dict(method="lagrange", separate_lap=True)),
-                     ("smooth_sep_grad", dict(method="smooth", separate_lap=True, separate_grad=True)),
-                     ("pp", dict(method="pp", separate_lap=False))):
+    sample = np.arange(0, n_pos, 512)
+    n_chk = 16
+    sidx = torch.from_numpy(sample).to(dev)
+    out, samples = {}, {}
+    for name, kw in METHOD_LEGS_C3:
         spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, storage="f32", device=dev, **kw)
         o = spl.alloc_outputs(n_pos)
         step = lambda: spl.eval_vgl(pos, out=o)
@@ -340,16 +419,21 @@ def bench_methods_c3(args, dev, stream, clocks=None):
         prof = spl.profile_read()
         spl.profile(False)
         spl.sync()
+        samples[name] = tuple(t[sidx][..., :n_chk].double().cpu().numpy() for t in o)
         k_s = prof["eval_ms"] * 1e-3 / max(1, prof["launches"])
         n_tab = spl.info()["n_tables"]
         bpe = algorithmic_bytes_per_eval("f32", n_tab, n_orb)
         out[name] = {"value": evals / (sum(ms) / len(ms) * 1e-3), "ms_per_step": sum(ms) / len(ms),
                      "eval_kernel_ms": k_s * 1e3, "tables": n_tab, "bytes_per_eval": bpe,
                      "table_bytes": spl.info()["table_bytes"],
-                     "roofline_l1": l1_roofline(bpe * evals, k_s, clocks)}
+                     "roofline_l1": l1_roofline(bpe * evals, k_s, l1)}
         del o
         spl.close()
         torch.cuda.empty_cache()
+    desc = "%d positions (every 512-th) x the first %d orbitals" % (len(sample), n_chk)
+    for name, _ in METHOD_LEGS_C3:
+        r64, rst = method_oracle(name, w.lattice, w.miller, w.coef[:n_chk], w.cell.grid, w.pos[sample], "f32")
+        out[name]["precision"] = precision_report("f32", samples[name], r64, rst, desc)
     return {"workload": "c3 MgO-like 64-atom, 128 orbitals, 96^3, 2048 x 256 positions, f32 tables, cell order",
             "unit": UNIT, "results": out}
 
@@ -426,6 +510,18 @@ def bench_bloch(args, dev, stream):
     res["consumer"] = {"workload": f"{W} walkers x ({n_band} + {n_band}) electrons, {n_band} complex bands, "
                                    "complex Gauss-Jordan", "unit": "walkers/s", "value": cres["df64"]["value"],
                        "ms_per_step": cres["df64"]["ms_per_step"], "arith": cres}
+    # error of the first 8 bands at every 512th position against the FP64 oracle (Bloch tables of
+    # u, then the phase and the product rule), unrounded and FP32-rounded tables
+    import oracle
+    sample = np.arange(0, n_pos, 512)
+    sidx = torch.from_numpy(sample).to(dev)
+    got = tuple(t[sidx][..., :8].cpu().numpy().astype(np.complex128) for t in out)
+    beta, blap = oracle.bloch_tables("smooth", w.lattice, w.miller, w.coef[:8], kp, w.cell.grid, laplacian=True)
+    r64 = oracle.bloch_eval("smooth", beta, w.lattice, kp, w.pos[sample], tables_lap=blap)
+    rst = oracle.bloch_eval("smooth", rounded_table(beta, "f32"), w.lattice, kp, w.pos[sample],
+                            tables_lap=rounded_table(blap, "f32"))
+    res["precision"] = precision_report("f32", got, r64, rst,
+                                        "%d positions (every 512-th) x the first 8 bands" % len(sample))
     spl.close()
     return res
 
@@ -606,13 +702,14 @@ def run_ours(args):
 
     # roofline of the dominant kernel, from its own CUDA-event launch times
     hbm, peak_kind = load_peaks()
+    l1 = probe_l1(dev)
     bpe = algorithmic_bytes_per_eval(args.storage, info["n_tables"], n_orb)
     launch_s = prof["eval_ms"] * 1e-3 / max(1, prof["launches"])
     achieved = bpe * evals_per_step / launch_s / 1e9
     key = "%s/%s/%s/%s" % (kernel_name.replace("_kernel", ""), w.cell.name, args.storage, order_name)
     traffic = load_traffic(key)
 
-    variants = {}
+    variants, var_got = {}, {}
     if not args.no_variants and rank == 0:
         for st, order in (("f32", "input"), ("f32", "pencil"), ("bf16", "auto"), ("bf16", "pencil"),
                           ("f64", "auto"), ("df64", "auto"), ("bf16", "input")):
@@ -640,6 +737,8 @@ def run_ours(args):
                 "order_kernels_ms": vp["order_ms"] / max(1, vp["launches"]),
                 "algorithmic_gbs": vb * evals_per_step / vk / 1e9,
                 "frac_of_hbm": vb * evals_per_step / vk / 1e9 / hbm}
+            if order == "auto" and st not in var_got:
+                var_got[st] = [t[par_idx].double().cpu().numpy() for t in outs]
 
     batched = methods = methods_c3 = backward = bloch = consumer = general = None
     if not args.no_variants and rank == 0:
@@ -648,7 +747,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         batched = bench_batched(args, dev, stream)
         methods = bench_methods(args, dev, stream)
-        methods_c3 = bench_methods_c3(args, dev, stream, clocks)
+        methods_c3 = bench_methods_c3(args, dev, stream, l1)
         backward = bench_backward(args, dev, stream)
         bloch = bench_bloch(args, dev, stream)
         consumer = bench_consumer(args, dev, stream)
@@ -659,31 +758,44 @@ def run_ours(args):
         import oracle
         tables = oracle.smoothing_tables(w.lattice, w.miller, w.coef, w.cell.grid, laplacian=True)
         cpu = cpu_baseline(w, args.storage, True, tables=tables)
-        parity = oracle_parity(w, args.storage, par_sample, par_got, tables)
+        parity = {args.storage: bspline_precision(w, args.storage, par_sample, par_got, tables)}
+        for st, got in var_got.items():
+            parity[st] = bspline_precision(w, st, par_sample, got, tables)
+        parity["headline"] = args.storage
 
+    # DRAM side of the same launch: the ncu-measured bytes (stored, keyed by the kernel source)
+    dram = None
+    if traffic:
+        dram = {"achieved": traffic / launch_s / 1e9, "peak": hbm, "unit": "GB/s", "frac": traffic / launch_s / 1e9 / hbm,
+                "bytes_per_launch": traffic, "peak_kind": peak_kind}
+    inorder = variants.get("%s_input" % args.storage)
+    roofline = l1_roofline(bpe * evals_per_step, launch_s, l1)
+    roofline.update({
+        "traffic": traffic,
+        "traffic_source": ("stored: ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel source "
+                           "(profiles/traffic.json, source hash matches)") if traffic else None,
+        "kernel": kernel_name, "bytes_per_eval": bpe, "kernel_ms": launch_s * 1e3,
+        "order_kernels_ms": prof["order_ms"] / max(1, prof["launches"]),
+        "l1_probe": l1,
+        "dram": dram,
+        "reuse_factor": (bpe * evals_per_step / traffic) if traffic else None,
+        "reuse_factor_note": "algorithmic (gathered) bytes per DRAM byte: stencil rows shared by neighbouring "
+                             "positions in cell order are read from HBM once",
+        "input_order_hbm": None if inorder is None else {
+            "kernel_ms": inorder["eval_kernel_ms"], "achieved": inorder["algorithmic_gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": inorder["frac_of_hbm"], "peak_kind": peak_kind,
+            "note": "the same kernel without cell order: every gathered row comes from HBM or L2"},
+    })
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": w.cell.name, "method": "smoothing B-spline + separate Laplacian table",
-                   "n_orb": n_orb, "grid": list(w.cell.grid), "walkers": w.cell.n_walkers,
-                   "electrons": w.cell.n_elec, "positions": n_pos, "storage": args.storage,
+        "config": workload_config(w, ws),
+        "launch": {"storage": args.storage,
                    "accumulate": {"f64": "f64", "df64": "double-float (f32 pairs)"}.get(args.storage, "f32"),
-                   "order": order_name,
-                   "table_bytes": info["table_bytes"], "lanes": info["lanes"], "tiles": info["tiles"],
-                   "cuda_graph": graph is not None,
-                   "l2": "table and outputs larger than L2 (no flush needed)",
-                   "parallelism": "replicas" if ws > 1 else "single"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                     "frac_of_nominal": achieved / 7900.0,
-                     "kernel": kernel_name, "bytes_per_eval": bpe,
-                     "kernel_ms": launch_s * 1e3,
-                     "order_kernels_ms": prof["order_ms"] / max(1, prof["launches"]),
-                     "note": "achieved counts every gathered stencil row (64 rows per table per evaluation); in cell "
-                             "order most rows are served by L1/L2 (traffic = DRAM bytes per launch), so "
-                             "frac exceeds 1; roofline_l1 is the binding limit"},
-        "roofline_l1": l1_roofline(bpe * evals_per_step, launch_s, clocks),
+                   "order": order_name, "table_bytes": info["table_bytes"], "lanes": info["lanes"],
+                   "tiles": info["tiles"], "cuda_graph": graph is not None},
+        "roofline": roofline,
         "cpu_baseline": cpu,
         "parity": parity,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pos_h.numel() * 8),

@@ -71,8 +71,12 @@ enum qmcspl_storage {
     QMCSPL_DF64 = 3                /* double-float: each coefficient a pair of floats whose
                                       sum carries ~48 significant bits, arithmetic in
                                       error-free FP32 pair operations, double outputs; the
-                                      accuracy class of FP64 at FP32-pipe speed.  B-spline
-                                      evaluation only (no backward, Lagrange or pp). */
+                                      accuracy class of FP64 at FP32-pipe speed.  Cubic
+                                      B-splines on uniform grids (with or without separate
+                                      Laplacian and gradient tables); their backward pass
+                                      runs in FP64 on the stored pairs.  Lagrange, pp and
+                                      B-splines of other degrees or on graded grids
+                                      reject it (QMCSPL_ERR_UNSUPPORTED). */
 };
 
 typedef struct {
@@ -477,6 +481,25 @@ int qmcspl_profile_read(qmcspl_t h, double* eval_ms, double* order_ms, long long
  */
 int qmcspl_save(qmcspl_t h, const char* path);
 int qmcspl_load(qmcspl_t* out, const char* path, void* stream);
+
+/*
+ * qmcspl_probe_l1 -- measured throughput of the SMs' L1 data path (not in the paper).
+ *
+ * Every evaluation gathers 64 coefficient rows per table (Sec. III B).  With positions in
+ * cell order most of those rows are shared with neighbouring positions and come from the
+ * SMs' L1 caches, so the rate that bounds the evaluation kernels is how fast the SMs return
+ * 16-byte loads from L1, not the HBM rate.  This call measures that rate on the current
+ * device: two 1024-thread blocks per SM sweep a 64 KB buffer (L1-resident after the first
+ * pass) with the 16-byte read-only loads the evaluation kernels use (each warp instruction
+ * 512 contiguous bytes), eight independent loads per thread in flight; each launch is timed
+ * with CUDA events on `stream`, best of five after one warm-up launch.
+ *   gbs            [out] bytes returned per second by all SMs together, GB/s
+ *   bytes_per_clk  [out] the same per SM and per SM clock cycle
+ *   sm_mhz         [out] the SM clock of the best launch (clock64 cycles / event time)
+ * Any output may be NULL.  Blocking.  Allocates about 70 KB of device memory for the call and
+ * frees it before returning; changes no device setting.
+ */
+int qmcspl_probe_l1(double* gbs, double* bytes_per_clk, double* sm_mhz, void* stream);
 
 /* qmcspl_sync -- synchronise `stream` and report (then clear) any device-side error the
  * handle's kernels recorded: QMCSPL_ERR_DEVICE for non-finite positions. */

@@ -101,6 +101,8 @@ PROTOTYPES = [
     ("qmcspl_slater_kinetic", I, [VP, VP, VP, I, I, LL, I, I, I, VP, VP, VP, VP, VP]),
     ("qmcspl_debug_fail_alloc", I, [LL]),
     ("qmcspl_debug_stall_pipeline", I, [I]),
+    ("qmcspl_probe_l1", I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), VP]),
     ("qmcspl_sync", I, [VP, VP]),
     ("qmcspl_last_error", ctypes.c_char_p, []),
     ("qmcspl_version", I, []),

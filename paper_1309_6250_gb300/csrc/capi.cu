@@ -26,6 +26,8 @@ int set_error(int code, const std::string& msg)
     return code;
 }
 
+void clear_error() { g_err.clear(); }
+
 int cuda_error(cudaError_t e, const char* what)
 {
     if (e == cudaSuccess) return QMCSPL_OK;

@@ -17,23 +17,29 @@ namespace qmcspl {
 namespace {
 
 constexpr long long kNoAllocMaxPos = QMCSPL_NOALLOC_MAX_POS;
-constexpr long long kNoAllocMaxBins = 1 << 16;   // bin_geometry never exceeds this
-constexpr size_t kScratchInts = (size_t)(2 * kNoAllocMaxPos + kNoAllocMaxBins + 1);
+// bin_geometry never makes more than kMaxBins bins; the counters take one more entry (the total)
+constexpr size_t kScratchInts = (size_t)(2 * kNoAllocMaxPos + kMaxBins + 1);
 constexpr int kMaxDevices = 64;
+static_assert(kScratchInts * sizeof(int) < (16u << 20), "the fixed scratch array stays modest");
 
 static __device__ __align__(256) int g_noalloc_scratch[kScratchInts];
 
 std::mutex g_scratch_mutex;
 int* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of g_noalloc_scratch on the current device `dev` (looked up once).
+// Device address of g_noalloc_scratch on device `dev`, which must be the current device
+// (looked up once per device and cached).
 int scratch_on_device(int dev, int** out)
 {
     if (dev < 0 || dev >= kMaxDevices) return set_error(QMCSPL_ERR_UNSUPPORTED, "device index out of range");
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     if (!g_scratch_ptr[dev]) {
+        int cur = -1;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+        if (cur != dev) return set_error(QMCSPL_ERR_CUDA, "noalloc scratch looked up on the wrong device");
         int* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(noalloc scratch)");
         g_scratch_ptr[dev] = p;
     }
@@ -49,6 +55,7 @@ using namespace qmcspl;
 extern "C" int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long n_pos, void* val,
                                        void* grad, void* lap, void* stream)
 {
+    clear_error();
     if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
     if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
     if (n_pos > kNoAllocMaxPos)
@@ -59,14 +66,16 @@ extern "C" int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long 
         return set_error(QMCSPL_ERR_UNSUPPORTED, "qmcspl_eval_vgl_noalloc: Bloch handles need per-position phase scratch");
     if (n_pos == 0) return QMCSPL_OK;
     if (!pos) return set_error(QMCSPL_ERR_ARG, "pos is NULL");
+    const BinGeometry g = bin_geometry(h);
+    if (g.n_bins > kMaxBins) return set_error(QMCSPL_ERR_UNSUPPORTED, "cell-order bins exceed the scratch array");
     int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != h->device) cudaSetDevice(h->device);
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (prev != h->device && (e = cudaSetDevice(h->device)) != cudaSuccess) return cuda_error(e, "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int* scratch = nullptr;
     int rc = scratch_on_device(h->device, &scratch);
     if (rc == QMCSPL_OK) {
-        const BinGeometry g = bin_geometry(h);
         int* bin = scratch;
         int* perm = scratch + kNoAllocMaxPos;
         int* count = scratch + 2 * kNoAllocMaxPos;
@@ -85,6 +94,9 @@ extern "C" int qmcspl_eval_vgl_noalloc(qmcspl_t h, const double* pos, long long 
             }
         }
     }
-    if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+    if (prev >= 0 && prev != h->device) {
+        e = cudaSetDevice(prev);
+        if (rc == QMCSPL_OK && e != cudaSuccess) rc = cuda_error(e, "cudaSetDevice (restore)");
+    }
     return rc;
 }

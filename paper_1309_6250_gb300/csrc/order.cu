@@ -25,7 +25,6 @@ namespace {
 #ifndef QMCSPL_BIN_EDGE
 #define QMCSPL_BIN_EDGE 4      // grid cells per bin edge (a bin is edge^3 cells)
 #endif
-constexpr int kMaxBins = 1 << 16;
 constexpr int kScanThreads = 1024;
 
 struct PrepArgs {
@@ -94,7 +93,9 @@ __global__ void prepare_kernel(const PrepArgs a)
     int ix, iy, iz;
     double tx, ty, tz;
     bool ok;
-    if (KIND >= 4) locate_position(a, i, ix, iy, iz, tx, ty, tz, ok);
+    // kinds 4, 5 and binning alone (kind 0) on a non-uniform grid: the grid interval that holds
+    // the position, so that bins group positions by the knot intervals they evaluate in
+    if (KIND >= 4 || (KIND == 0 && a.knots)) locate_position(a, i, ix, iy, iz, tx, ty, tz, ok);
     else reduce_position(a, i, ix, iy, iz, tx, ty, tz, ok);
     const int cell = ok ? (ix | (iy << 10) | (iz << 20)) : -1;
     if (KIND == 1 || KIND == 4) {
@@ -297,16 +298,6 @@ static int grow_scratch(Handle* h, long long n_pos, int n_bins)
     h->ord_cap = cap;
     h->ord_nbins = nb;
     return QMCSPL_OK;
-}
-
-int cell_order(Handle* h, const double* pos, long long n_pos, const int** perm, cudaStream_t st)
-{
-    const BinGeometry g = bin_geometry(h);
-    int rc = grow_scratch(h, n_pos, g.n_bins);
-    if (rc != QMCSPL_OK) return rc;
-    rc = build_cell_order(h, pos, n_pos, h->ord_bin, h->ord_count, h->ord_perm, g, st);
-    *perm = h->ord_perm;
-    return rc;
 }
 
 int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, Prepared* out,

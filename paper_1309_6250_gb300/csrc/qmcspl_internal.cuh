@@ -30,6 +30,7 @@ constexpr int kMaxDim = 512;          // grid points per axis accepted by qmcspl
 constexpr int kEvalThreads = 256;     // eval kernels: 8 warps per block
 constexpr int kProfCalls = 4096;      // calls qmcspl_profile can record
 constexpr long long kRecordMinPositions = 8192;   // from here on positions are reduced in a pass of their own
+constexpr int kMaxBins = 1 << 16;     // cell-order bins: bin_geometry widens the bins to stay within this
 
 // Per-planewave multiplier of a table sum (construct.cu) = basis factor x derivative
 // factor.  For Bloch orbitals every G in a derivative factor stands for k + G.
@@ -156,6 +157,7 @@ namespace qmcspl {
 
 // ---- error reporting (thread-local message) ----
 int set_error(int code, const std::string& msg);
+void clear_error();   // every entry point calls this first: "" until something fails
 int cuda_error(cudaError_t e, const char* what);
 
 // ---- device allocations: every one goes through these, so that the test hook
@@ -210,8 +212,6 @@ bool use_cell_order(const Handle* h, long long n_pos);
 // pointers sized for n_pos positions and g.n_bins + 1 counters) on `stream`.
 int build_cell_order(const Handle* h, const double* pos, long long n_pos, int* bin, int* count,
                      int* perm, const BinGeometry& g, cudaStream_t stream);
-// Same, using the handle's own scratch (grown on demand); returns the permutation.
-int cell_order(Handle* h, const double* pos, long long n_pos, const int** perm, cudaStream_t stream);
 
 // Per-position coordinate records: the grid cell and reduced coordinate t of every
 // position, computed once (FP64) so that the evaluation kernels need no FP64 work.

@@ -6,6 +6,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -56,12 +57,42 @@ def test_algorithmic_bytes_per_evaluation():
     assert bench.algorithmic_bytes_per_eval("df64", 1, 128) == pytest.approx(64 * 8 + 40 + 24 / 128)
 
 
-def test_l1_roofline_uses_the_sampled_clock():
-    r = bench.l1_roofline(40.0e9, 1.0e-3, {"sm_mhz": 2000.0})
-    assert r["peak"] == pytest.approx(128 * 152 * 2000e6 / 1e9)
+def test_l1_roofline_uses_the_measured_probe_rate():
+    l1 = {"gbs": 36000.0, "bytes_per_clk_per_sm": 120.0, "sm_mhz": 1974.0}
+    r = bench.l1_roofline(40.0e9, 1.0e-3, l1)
+    assert r["bound"] == "l1" and r["peak"] == 36000.0
     assert r["achieved"] == pytest.approx(40.0e9 / 1e-3 / 1e9)
-    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert bench.l1_roofline(1.0, 1.0, None)["peak"] == pytest.approx(128 * 152 * 2070e6 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 36000.0)
+
+
+def test_precision_report_on_hand_made_outputs():
+    """Errors per output against the unrounded and the rounded reference, and the kinetic-energy
+    change: a Laplacian error of 0.01 at every sample of an orbital with phi = 1 moves its T_n by
+    -1/2 * 0.01 = -5 mHa."""
+    P, O = 8, 3
+    val = np.ones((P, O))
+    grad = np.zeros((P, 3, O))
+    grad[:, 0, :] = 2.0
+    lap = np.full((P, O), -4.0)
+    ref = (val, grad, lap)
+    got = (val.copy(), grad.copy(), lap.copy())
+    got[2][:, 1] += 0.01
+    got[1][3, 0, 2] += 0.002
+    r = bench.precision_report("f32", got, ref, ref, "hand-made")
+    assert r["max_rel_err_vs_fp64"]["val"] == 0.0
+    assert r["max_rel_err_vs_fp64"]["grad"] == pytest.approx(0.001)
+    assert r["max_rel_err_vs_fp64"]["lap"] == pytest.approx(0.0025)
+    assert r["dT_mHa"] == pytest.approx(5.0)
+    assert r["T_max_Ha"] == pytest.approx(2.0)
+    assert r["ok"] is False and r["tolerance"] == 2e-6
+
+
+def test_both_arms_report_the_same_workload_config():
+    from paper_1309_6250_gb300 import inputs
+    r = run_bench("--impl", "reference", "--steps", "1", "--warmup", "1", "--ref-sample", "16")
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["config"] == bench.workload_config(inputs.make_workload("c3"))
 
 
 def test_traffic_is_dropped_when_the_kernel_source_changes(monkeypatch):
