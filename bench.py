@@ -70,8 +70,8 @@ def load_peaks():
 
 
 def load_traffic(key):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source; else None."""
+    """Bytes per launch from the committed ncu capture, if it was taken on the current kernel
+    source: {'dram': DRAM read + write bytes, 'l2': L2 bytes or None}; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -80,7 +80,7 @@ def load_traffic(key):
     e = d.get(key)
     if not e or e.get("kernel_source_sha") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    return {"dram": e.get("dram_bytes_per_launch"), "l2": e.get("l2_bytes_per_launch")}
 
 
 class ClockSampler:
@@ -290,28 +290,49 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def probe_l1(dev):
-    """The SMs' L1 data-path rate for 16-byte loads, measured on this GPU by the library's
-    probe (qmcspl_probe_l1): GB/s over all SMs, bytes per SM clock, and the SM clock it ran at."""
+def probe_cache(dev, level):
+    """The SMs' L1 (level 1) or L2 (level 2) data-path rate for 16-byte loads, measured on this
+    GPU by the library's probe (qmcspl_probe_cache): GB/s over all SMs, bytes per SM clock, and
+    the SM clock it ran at."""
     import ctypes
     import torch
     from paper_1309_6250_gb300 import _lib
     lib = _lib.load()
     g, b, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
     with torch.cuda.device(dev):
-        _lib.check(lib.qmcspl_probe_l1(ctypes.byref(g), ctypes.byref(b), ctypes.byref(m),
-                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        _lib.check(lib.qmcspl_probe_cache(int(level), ctypes.byref(g), ctypes.byref(b), ctypes.byref(m),
+                                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    how = {1: "16-byte ld.global.nc over a 64 KB buffer resident in every L1",
+           2: "16-byte ld.global.cg (L2 only) over a 32 MB buffer resident in L2"}[level]
     return {"gbs": g.value, "bytes_per_clk_per_sm": b.value, "sm_mhz": m.value,
-            "how": "qmcspl_probe_l1: 2 x 1024 threads per SM, 16-byte ld.global.nc over a 64 KB "
-                   "L1-resident buffer, 8 loads in flight per thread, best of 5 CUDA-event-timed launches"}
+            "how": "qmcspl_probe_cache(%d): 2 x 1024 threads per SM, %s, 8 loads in flight per thread, "
+                   "best of 5 CUDA-event-timed launches" % (level, how)}
 
 
 def l1_roofline(gather_bytes, launch_s, l1):
-    """Every gathered stencil byte passes through the SM's L1 data path; in cell order most of
-    them hit there, and this path, not HBM, bounds the gather.  Peak: the probe's measured rate."""
+    """Every gathered stencil byte is requested from the SM's L1 data path (hits there, misses
+    continue to L2).  Peak: the probe's measured L1 rate."""
     achieved = gather_bytes / launch_s / 1e9
     return {"bound": "l1", "achieved": achieved, "peak": l1["gbs"], "unit": "GB/s",
-            "frac": achieved / l1["gbs"], "peak_kind": "measured in this run (qmcspl_probe_l1)"}
+            "frac": achieved / l1["gbs"], "peak_kind": "measured in this run (qmcspl_probe_cache level 1)"}
+
+
+def cache_rooflines(gather_bytes, l2_bytes, dram_bytes, launch_s, l1, l2, hbm, hbm_kind):
+    """The kernel's bytes at each level of the memory hierarchy against that level's measured
+    rate: gathered (algorithmic) bytes through L1, the L2 bytes ncu counted (L1 misses), the DRAM
+    bytes ncu counted.  Levels without a byte count are left out.  The binding level is the one
+    with the highest fraction."""
+    lv = {"l1": l1_roofline(gather_bytes, launch_s, l1)}
+    if l2_bytes:
+        a = l2_bytes / launch_s / 1e9
+        lv["l2"] = {"bound": "l2", "achieved": a, "peak": l2["gbs"], "unit": "GB/s", "frac": a / l2["gbs"],
+                    "bytes_per_launch": l2_bytes, "peak_kind": "measured in this run (qmcspl_probe_cache level 2)"}
+    if dram_bytes:
+        a = dram_bytes / launch_s / 1e9
+        lv["hbm"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                     "bytes_per_launch": dram_bytes, "peak_kind": hbm_kind}
+    top = max(lv.values(), key=lambda r: r["frac"])
+    return dict(top), lv
 
 
 def _time_handle(spl, pos, torch, stream, steps, graph=True):
@@ -702,7 +723,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel, from its own CUDA-event launch times
     hbm, peak_kind = load_peaks()
-    l1 = probe_l1(dev)
+    l1, l2 = probe_cache(dev, 1), probe_cache(dev, 2)
     bpe = algorithmic_bytes_per_eval(args.storage, info["n_tables"], n_orb)
     launch_s = prof["eval_ms"] * 1e-3 / max(1, prof["launches"])
     achieved = bpe * evals_per_step / launch_s / 1e9
@@ -763,24 +784,22 @@ def run_ours(args):
             parity[st] = bspline_precision(w, st, par_sample, got, tables)
         parity["headline"] = args.storage
 
-    # DRAM side of the same launch: the ncu-measured bytes (stored, keyed by the kernel source)
-    dram = None
-    if traffic:
-        dram = {"achieved": traffic / launch_s / 1e9, "peak": hbm, "unit": "GB/s", "frac": traffic / launch_s / 1e9 / hbm,
-                "bytes_per_launch": traffic, "peak_kind": peak_kind}
+    # the launch against each level's measured rate (DRAM and L2 bytes: the stored ncu counts)
+    dram_b = traffic["dram"] if traffic else None
+    l2_b = traffic["l2"] if traffic else None
     inorder = variants.get("%s_input" % args.storage)
-    roofline = l1_roofline(bpe * evals_per_step, launch_s, l1)
+    roofline, levels = cache_rooflines(bpe * evals_per_step, l2_b, dram_b, launch_s, l1, l2, hbm, peak_kind)
     roofline.update({
-        "traffic": traffic,
-        "traffic_source": ("stored: ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel source "
-                           "(profiles/traffic.json, source hash matches)") if traffic else None,
+        "traffic": dram_b,
+        "traffic_source": ("stored: ncu dram__bytes_read.sum + dram__bytes_write.sum (and lts__t_bytes.sum) "
+                           "of this kernel source, profiles/traffic.json (source hash matches)") if traffic else None,
         "kernel": kernel_name, "bytes_per_eval": bpe, "kernel_ms": launch_s * 1e3,
         "order_kernels_ms": prof["order_ms"] / max(1, prof["launches"]),
-        "l1_probe": l1,
-        "dram": dram,
-        "reuse_factor": (bpe * evals_per_step / traffic) if traffic else None,
+        "levels": levels,
+        "probes": {"l1": l1, "l2": l2},
+        "reuse_factor": (bpe * evals_per_step / dram_b) if dram_b else None,
         "reuse_factor_note": "algorithmic (gathered) bytes per DRAM byte: stencil rows shared by neighbouring "
-                             "positions in cell order are read from HBM once",
+                             "positions in cell order are read from HBM about once",
         "input_order_hbm": None if inorder is None else {
             "kernel_ms": inorder["eval_kernel_ms"], "achieved": inorder["algorithmic_gbs"], "peak": hbm,
             "unit": "GB/s", "frac": inorder["frac_of_hbm"], "peak_kind": peak_kind,
@@ -835,7 +854,7 @@ def main():
     ap.add_argument("--n-pos", type=int, default=None, help="use only the first N positions (profiling)")
     ap.add_argument("--only", default="all",
                     choices=["all", "bloch", "consumer", "general", "methods", "methods_c3", "batched",
-                             "backward"],
+                             "backward", "probes"],
                     help="run one secondary leg alone and print its JSON (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -844,7 +863,9 @@ def main():
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         leg = {"bloch": bench_bloch, "consumer": bench_consumer, "general": bench_general,
-               "methods": bench_methods, "methods_c3": bench_methods_c3, "batched": bench_batched, "backward": bench_backward}[args.only]
+               "methods": bench_methods, "methods_c3": lambda a, d, s: bench_methods_c3(a, d, s, probe_cache(d, 1)),
+               "batched": bench_batched, "backward": bench_backward,
+               "probes": lambda a, d, s: {"l1": probe_cache(d, 1), "l2": probe_cache(d, 2)}}[args.only]
         print(json.dumps({"leg": args.only, **leg(args, dev, torch.cuda.current_stream())}), flush=True)
     else:
         run_ours(args)

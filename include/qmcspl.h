@@ -324,6 +324,29 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* h, const double* const* pos
 int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream);
 
 /*
+ * qmcspl_set_table -- overwrite one stored table from a DEVICE array in canonical layout.
+ *
+ * Not in the paper: it makes the coefficient gradient of qmcspl_eval_vgl_backward usable for
+ * optimising the orbitals, since the coefficients of Eq. (b-splineapproximation) (and of the
+ * other bases) can then be changed between evaluations without rebuilding the handle.  The
+ * inverse of qmcspl_get_table:
+ *   table      the same numbering as qmcspl_get_table (B-splines 0 = coefficients, 1 = Laplacian
+ *              coefficients; five-table handles 0..4; pp 0..7 = the sigma entries)
+ *   src        device array [Nx][Ny][Nz][O] (a Bloch handle: [Nx][Ny][Nz][O][2], Re and Im of the
+ *              tabulated periodic part), unpadded, without ghost planes, of src_dtype
+ *   src_dtype  QMCSPL_F64 (double) or QMCSPL_F32 (float)
+ *   stream     cudaStream_t; asynchronous: src must stay valid and unchanged until the work on
+ *              `stream` is done, and evaluations of the handle on other streams must be ordered
+ *              after it by the caller
+ * Each value is converted to the storage type exactly as the construction converts its FP64
+ * coefficients (round to nearest; double-float: hi = rounded value, lo = rounded remainder),
+ * the periodic ghost planes are rewritten and the row padding stays zero, so that
+ * qmcspl_set_table(h, t, table from qmcspl_get_table) leaves the handle bit for bit as it was.
+ * The handle's planewave description is not updated: the tables are what evaluation uses.
+ */
+int qmcspl_set_table(qmcspl_t h, int table, const void* src, int src_dtype, void* stream);
+
+/*
  * qmcspl_set_order -- choose the order in which qmcspl_eval_vgl visits positions.
  *
  * Not in the paper.  Results do not depend on it (each position is computed the same
@@ -483,23 +506,24 @@ int qmcspl_save(qmcspl_t h, const char* path);
 int qmcspl_load(qmcspl_t* out, const char* path, void* stream);
 
 /*
- * qmcspl_probe_l1 -- measured throughput of the SMs' L1 data path (not in the paper).
+ * qmcspl_probe_cache -- measured throughput of the SMs' L1 or L2 data path (not in the paper).
  *
  * Every evaluation gathers 64 coefficient rows per table (Sec. III B).  With positions in
- * cell order most of those rows are shared with neighbouring positions and come from the
- * SMs' L1 caches, so the rate that bounds the evaluation kernels is how fast the SMs return
- * 16-byte loads from L1, not the HBM rate.  This call measures that rate on the current
- * device: two 1024-thread blocks per SM sweep a 64 KB buffer (L1-resident after the first
- * pass) with the 16-byte read-only loads the evaluation kernels use (each warp instruction
- * 512 contiguous bytes), eight independent loads per thread in flight; each launch is timed
- * with CUDA events on `stream`, best of five after one warm-up launch.
- *   gbs            [out] bytes returned per second by all SMs together, GB/s
+ * cell order most of those rows are shared with neighbouring positions and come from the SMs'
+ * L1 caches or from L2, so the rates that bound the evaluation kernels are how fast L1 and L2
+ * return 16-byte loads, not the HBM rate.  This call measures one of them on the current
+ * device: two 1024-thread blocks per SM issue 16-byte loads shaped like the evaluation
+ * kernels' (each warp instruction 512 contiguous bytes), eight independent loads per thread in
+ * flight; each launch is timed with CUDA events on `stream`, best of five after one warm-up.
+ *   level          1: read-only loads (ld.global.nc) over a 64 KB buffer resident in every L1;
+ *                  2: L2-only loads (ld.global.cg) over a 32 MB buffer resident in L2
+ *   gbs            [out] bytes returned per second to all SMs together, GB/s
  *   bytes_per_clk  [out] the same per SM and per SM clock cycle
  *   sm_mhz         [out] the SM clock of the best launch (clock64 cycles / event time)
- * Any output may be NULL.  Blocking.  Allocates about 70 KB of device memory for the call and
- * frees it before returning; changes no device setting.
+ * Any output may be NULL.  Blocking.  Allocates the buffer (64 KB or 32 MB) for the call and
+ * frees it before returning; changes no device setting.  QMCSPL_ERR_ARG for another level.
  */
-int qmcspl_probe_l1(double* gbs, double* bytes_per_clk, double* sm_mhz, void* stream);
+int qmcspl_probe_cache(int level, double* gbs, double* bytes_per_clk, double* sm_mhz, void* stream);
 
 /* qmcspl_sync -- synchronise `stream` and report (then clear) any device-side error the
  * handle's kernels recorded: QMCSPL_ERR_DEVICE for non-finite positions. */

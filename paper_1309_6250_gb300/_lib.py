@@ -92,6 +92,7 @@ PROTOTYPES = [
     ("qmcspl_eval_vgl_backward", I, [VP, VP, LL, VP, VP, VP, VP, VP, VP, VP]),
     ("qmcspl_eval_batched", I, [I, VP, VP, VP, VP, VP, VP, VP]),
     ("qmcspl_get_table", I, [VP, I, VP, VP]),
+    ("qmcspl_set_table", I, [VP, I, VP, I, VP]),
     ("qmcspl_set_order", I, [VP, I]),
     ("qmcspl_profile", I, [VP, I]),
     ("qmcspl_profile_read", I, [VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -101,8 +102,8 @@ PROTOTYPES = [
     ("qmcspl_slater_kinetic", I, [VP, VP, VP, I, I, LL, I, I, I, VP, VP, VP, VP, VP]),
     ("qmcspl_debug_fail_alloc", I, [LL]),
     ("qmcspl_debug_stall_pipeline", I, [I]),
-    ("qmcspl_probe_l1", I, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
-                            ctypes.POINTER(ctypes.c_double), VP]),
+    ("qmcspl_probe_cache", I, [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double), VP]),
     ("qmcspl_sync", I, [VP, VP]),
     ("qmcspl_last_error", ctypes.c_char_p, []),
     ("qmcspl_version", I, []),

@@ -145,6 +145,20 @@ class OrbitalSplines:
                                                  _stream_handle(stream)))
         return out
 
+    def set_table(self, index: int, table: torch.Tensor, stream=None) -> None:
+        """Overwrite stored table `index` (numbering of get_table) from a float64 or float32
+        device tensor of shape coef_shape() (canonical layout); asynchronous on `stream`."""
+        if table.device != self.device or table.dtype not in (torch.float64, torch.float32):
+            raise ValueError("table must be a float64 or float32 tensor on %s" % self.device)
+        if tuple(table.shape) != self.coef_shape():
+            raise ValueError("table shape %s, expected %s" % (tuple(table.shape), self.coef_shape()))
+        t = table.detach().contiguous()
+        code = _lib.F64 if t.dtype == torch.float64 else _lib.F32
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.qmcspl_set_table(self.handle, int(index), _ptr(t), code, ctypes.c_void_p(s.cuda_stream)))
+        t.record_stream(s)   # a temporary copy stays allocated until the stream has read it
+
     def set_order(self, mode: str) -> None:
         """Order in which eval_vgl visits positions: 'auto', 'input', 'cell' or 'pencil'
         (2 x 2-cell pencils evaluated by the shared-memory-staged kernel where it applies)."""

@@ -6,10 +6,18 @@
     # pos.grad: dL/dr [P, 3] (forces);  beta.grad, beta_lap.grad: dL/dbeta (canonical
     # layout [Nx, Ny, Nz, O]), both from qmcspl_eval_vgl_backward.
 
-The forward pass reads the coefficient tables held by the handle; `beta` / `beta_lap`
-stand for those tables in the autograd graph (they must hold the same values, which
-is what coefficient_parameters() returns).  Stencil weights are recomputed in the
-backward kernel rather than saved.
+The forward pass evaluates the coefficient tables held by the handle.  `beta` / `beta_lap`
+are those tables in the autograd graph: whenever a tensor passed as `beta` or `beta_lap`
+differs from the one last uploaded to the handle (another tensor, or the same tensor changed
+in place since, e.g. by an optimiser step: torch's version counter), forward first writes it
+into the handle's tables (qmcspl_set_table, with the storage type's rounding).  So
+
+    opt = torch.optim.SGD([beta], lr=...)
+    for _ in range(n):
+        opt.zero_grad(); loss(evaluate(spl, pos, beta)).backward(); opt.step()
+
+optimises the orbitals' coefficients.  Stencil weights are recomputed in the backward kernel
+rather than saved.
 """
 from __future__ import annotations
 
@@ -21,9 +29,39 @@ import torch
 from .api import OrbitalSplines
 
 
+def _is_table(t) -> bool:
+    return t is not None and t.dim() >= 4
+
+
+def upload_if_changed(spl: OrbitalSplines, index: int, t: torch.Tensor) -> None:
+    """Write `t` into table `index` of the handle unless it is the tensor, at the version, that
+    was written last."""
+    key = (t.data_ptr(), t._version, tuple(t.shape), t.dtype)
+    seen = spl.__dict__.setdefault("_uploaded", {})
+    if seen.get(index) != key:
+        spl.set_table(index, t)
+        seen[index] = key
+
+
+def sync_tables(spl: OrbitalSplines, beta, beta_lap) -> None:
+    """Upload the coefficient tensors of the autograd graph that changed since the last upload:
+    beta [Nx, Ny, Nz, F] is table 0 (beta_lap table 1); a stacked [5 or 8, Nx, Ny, Nz, F] beta
+    holds every table of a five-table or pp handle."""
+    shape = spl.coef_shape()
+    if _is_table(beta):
+        if tuple(beta.shape) == shape:
+            upload_if_changed(spl, 0, beta)
+        else:
+            for i in range(beta.shape[0]):
+                upload_if_changed(spl, i, beta[i])
+    if _is_table(beta_lap):
+        upload_if_changed(spl, 1, beta_lap)
+
+
 class SplineOrbitalFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, pos, beta, beta_lap, spl: OrbitalSplines):
+        sync_tables(spl, beta, beta_lap)
         val, grad, lap = spl.eval_vgl(pos)
         ctx.spl = spl
         ctx.save_for_backward(pos)
@@ -54,21 +92,29 @@ class SplineOrbitalFunction(torch.autograd.Function):
 
 def coefficient_parameters(spl: OrbitalSplines):
     """Leaf tensors (requires_grad) holding the handle's coefficient tables in canonical
-    layout [Nx, Ny, Nz, O], in the output dtype: (beta, beta_lap or None).  Five-table
+    layout [Nx, Ny, Nz, O], in the output dtype: (beta, beta_lap or None).  They are recorded
+    as the handle's current tables (nothing is uploaded until one of them changes).  Five-table
     handles (Lagrange, B-splines with separate gradient tables) give all five tables as one
     [5, Nx, Ny, Nz, O] tensor and None, pp handles their eight entries as [8, Nx, Ny, Nz, O]."""
     inf = spl.info()
     n_multi = 5 if inf["n_tables"] == 5 else (8 if inf["entries_per_point"] == 8 else 0)
+    seen = spl.__dict__.setdefault("_uploaded", {})
     if n_multi:
         t = torch.from_numpy(np.stack([spl.get_table(i) for i in range(n_multi)]))
-        return t.to(device=spl.device, dtype=spl.out_dtype).requires_grad_(True), None
+        t = t.to(device=spl.device, dtype=spl.out_dtype).requires_grad_(True)
+        for i in range(n_multi):
+            v = t[i]
+            seen[i] = (v.data_ptr(), v._version, tuple(v.shape), v.dtype)
+        return t, None
     out = []
     for idx in range(2):
         if idx == 1 and not inf["separate_lap"]:
             out.append(None)
             continue
         t = torch.from_numpy(spl.get_table(idx)).to(device=spl.device, dtype=spl.out_dtype)
-        out.append(t.requires_grad_(True))
+        t.requires_grad_(True)
+        seen[idx] = (t.data_ptr(), t._version, tuple(t.shape), t.dtype)
+        out.append(t)
     return tuple(out)
 
 

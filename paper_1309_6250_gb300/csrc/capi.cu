@@ -766,6 +766,20 @@ int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream)
     return QMCSPL_OK;
 }
 
+int qmcspl_set_table(qmcspl_t h, int table, const void* src, int src_dtype, void* stream)
+{
+    g_err.clear();
+    if (!h || !src) return set_error(QMCSPL_ERR_ARG, "NULL argument");
+    const int n_avail = (h->method == QMCSPL_PPSPLINE) ? 8 : h->n_tables;
+    if (table < 0 || table >= n_avail) return set_error(QMCSPL_ERR_ARG, "table index out of range");
+    if (src_dtype != QMCSPL_F64 && src_dtype != QMCSPL_F32)
+        return set_error(QMCSPL_ERR_ARG, "src_dtype must be QMCSPL_F64 (double) or QMCSPL_F32 (float)");
+    const size_t esz = src_dtype == QMCSPL_F64 ? 8 : 4;
+    if (reinterpret_cast<uintptr_t>(src) % esz) return set_error(QMCSPL_ERR_ARG, "src is not aligned to its element size");
+    DeviceGuard dg(h->device);
+    return launch_set_table(h, table, src, src_dtype == QMCSPL_F64 ? 1 : 0, static_cast<cudaStream_t>(stream));
+}
+
 int qmcspl_profile(qmcspl_t h, int enable)
 {
     g_err.clear();

@@ -43,6 +43,7 @@
 // Orbitals are processed in chunks so the complex grids stay below a fixed budget.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -365,6 +366,51 @@ __global__ void layout_df_kernel(const LayoutArgs a)
     dst[2] = lo;
 }
 
+// A table given by the caller in canonical layout src[x][y][z][f] (f < nf stored functions per
+// row, as qmcspl_get_table returns it) written in the stored layout with the same conversion and
+// ghost planes as layout_kernel / layout_df_kernel; the padding entries of each row are left as
+// they are (zero since construction).
+struct PairTable {};            // double-float storage: (hi, lo) float pairs, as layout_df_kernel
+
+struct SetTableArgs {
+    const void* src;
+    int src_double;           // 1: src is double, 0: float
+    void* tab;
+    int N1, N2, N3;
+    int nf, o_p;
+    int rows_z;
+    int entries, entry;
+    int zshift;
+};
+
+template <typename T>
+__global__ void set_table_kernel(const SetTableArgs a)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)a.N1 * a.N2 * a.rows_z * a.nf;
+    if (idx >= total) return;
+    const int f = (int)(idx % a.nf);
+    long long r = idx / a.nf;
+    const int zz = (int)(r % a.rows_z);
+    r /= a.rows_z;
+    const int y = (int)(r % a.N2);
+    const int x = (int)(r / a.N2);
+    int z = zz - a.zshift;
+    z = z < 0 ? z + a.N3 : (z >= a.N3 ? z - a.N3 : z);
+    const long long s = (((long long)x * a.N2 + y) * a.N3 + z) * a.nf + f;
+    const double v = a.src_double ? static_cast<const double*>(a.src)[s] : (double)static_cast<const float*>(a.src)[s];
+    const long long row = (((long long)x * a.N2 + y) * a.rows_z + zz) * a.entries + a.entry;
+    if constexpr (std::is_same<T, PairTable>::value) {
+        const float hi = __double2float_rn(v);
+        const float lo = __double2float_rn(v - (double)hi);
+        float* dst = static_cast<float*>(a.tab) + 2 * (row * a.o_p + (f & ~1)) + (f & 1);
+        dst[0] = hi;
+        dst[2] = lo;
+    } else {
+        static_cast<T*>(a.tab)[row * a.o_p + f] = from_double<T>(v);
+    }
+}
+
 int launch_layout(const Handle* h, const double2* F, int tab, int entry, int o0, int oc,
                   cudaStream_t st)
 {
@@ -645,6 +691,33 @@ void degree_symbol(int n, double sym[4])
 }
 
 }  // namespace
+
+int launch_set_table(Handle* h, int table, const void* src, int src_double, cudaStream_t st)
+{
+    SetTableArgs a;
+    const bool pp = h->method == QMCSPL_PPSPLINE;
+    a.src = src;
+    a.src_double = src_double;
+    a.tab = h->table(pp ? 0 : table);
+    a.N1 = h->dims[0];
+    a.N2 = h->dims[1];
+    a.N3 = h->dims[2];
+    a.nf = h->n_orb;
+    a.o_p = h->n_orb_p;
+    a.rows_z = h->rows_z;
+    a.entries = h->entries;
+    a.entry = pp ? table : 0;
+    a.zshift = h->zshift;
+    const long long total = (long long)a.N1 * a.N2 * a.rows_z * a.nf;
+    const unsigned blocks = (unsigned)((total + 255) / 256);
+    switch (h->storage) {
+    case QMCSPL_DF64: set_table_kernel<PairTable><<<blocks, 256, 0, st>>>(a); break;
+    case QMCSPL_F64: set_table_kernel<double><<<blocks, 256, 0, st>>>(a); break;
+    case QMCSPL_F32: set_table_kernel<float><<<blocks, 256, 0, st>>>(a); break;
+    default: set_table_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(a); break;
+    }
+    return cuda_error(cudaGetLastError(), "set_table_kernel launch");
+}
 
 int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef_host,
                  cudaStream_t st)

@@ -168,6 +168,9 @@ cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t stream);
 // ---- construction (construct.cu) ----
 int build_tables(Handle* h, int n_pw, const int* miller_host, const double* coef_host,
                  cudaStream_t stream);
+// Overwrite stored table `table` (pp: entry `table`) from a device array in canonical layout
+// [Nx][Ny][Nz][n_orb stored functions], double (src_double = 1) or float.
+int launch_set_table(Handle* h, int table, const void* src, int src_double, cudaStream_t stream);
 
 // ---- evaluation launchers ----
 // Prepared per-position data of one evaluation: coordinate records, the evaluation

@@ -65,6 +65,18 @@ def test_l1_roofline_uses_the_measured_probe_rate():
     assert r["frac"] == pytest.approx(r["achieved"] / 36000.0)
 
 
+def test_cache_rooflines_pick_the_binding_level():
+    l1 = {"gbs": 80000.0}
+    l2 = {"gbs": 20000.0}
+    top, lv = bench.cache_rooflines(40.0e9, 15.0e9, 3.0e9, 1.0e-3, l1, l2, 6800.0, "measured")
+    assert lv["l1"]["frac"] == pytest.approx(0.5)
+    assert lv["l2"]["frac"] == pytest.approx(0.75)
+    assert lv["hbm"]["frac"] == pytest.approx(3000.0 / 6800.0)
+    assert top["bound"] == "l2" and top["frac"] == lv["l2"]["frac"]
+    top, lv = bench.cache_rooflines(40.0e9, None, None, 1.0e-3, l1, l2, 6800.0, "measured")
+    assert set(lv) == {"l1"} and top["bound"] == "l1"
+
+
 def test_precision_report_on_hand_made_outputs():
     """Errors per output against the unrounded and the rounded reference, and the kinetic-energy
     change: a Laplacian error of 0.01 at every sample of an orbital with phi = 1 moves its T_n by
@@ -102,7 +114,7 @@ def test_traffic_is_dropped_when_the_kernel_source_changes(monkeypatch):
         entries = json.load(f)
     key, entry = next(iter(entries.items()))
     if entry["kernel_source_sha"] == bench.kernel_source_hash():
-        assert bench.load_traffic(key) == entry["dram_bytes_per_launch"]
+        assert bench.load_traffic(key)["dram"] == entry["dram_bytes_per_launch"]
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
     assert bench.load_traffic(key) is None
     assert bench.load_traffic("no/such/key") is None

@@ -92,6 +92,8 @@ def test_validation_without_gpu(lib):
     # NULL handle calls
     assert lib.qmcspl_eval_vgl(None, None, 0, None, None, None, None) == _lib.ERR_ARG
     assert lib.qmcspl_sync(None, None) == _lib.ERR_ARG
+    assert lib.qmcspl_set_table(None, 0, None, _lib.F64, None) == _lib.ERR_ARG
+    assert lib.qmcspl_eval_vgl_noalloc(None, None, 0, None, None, None, None) == _lib.ERR_ARG
     assert lib.qmcspl_destroy(None) == _lib.OK
 
 
