@@ -598,38 +598,62 @@ def bench_general(args, dev, stream):
                         "CUDA-graph replays", "unit": UNIT, "results": out}
 
 
-def bench_batched(args, dev, stream):
+def bench_batched(args, dev, stream, l1=None):
     """The uneven three-cell workload (Al-like 32-atom: 48 orbitals, 64^3, 512 x 96 e;
     Si-like 64-atom: 128 orbitals, 80^3, 1024 x 256 e; MgO-like 16-atom: 32 orbitals,
-    64^3, 2048 x 64 e; FP32 smoothing + Laplacian tables) through one qmcspl_eval_batched
-    call per step, each cell with the autotuner's tile shape and order (cells this large
-    each get their own launch; smaller ones share the batched kernel)."""
+    64^3, 2048 x 64 e; FP32 smoothing + Laplacian tables) through one qmcspl_eval_batched_ex
+    call per step, replayed from a CUDA graph.  Each cell has the autotuner's lanes, block shape
+    and order; the launch plan of the call (one launch per cell, or all cells in the one
+    persistent batched launch of 512 or 640 threads per block) is the autotuner's too, and every
+    plan's time is reported.  Sampled outputs of each cell are checked against the oracle."""
     import torch
+    import oracle
     from paper_1309_6250_gb300 import autotune
-    from paper_1309_6250_gb300.api import eval_batched
     import tempfile
     cache = os.path.join(tempfile.gettempdir(), "qmcspl_autotune.json")   # tuned shapes, reused within a machine
-    cells, shapes, evals = [], {}, 0
+    cells, shapes, evals, gathered, works = [], {}, 0, 0.0, []
     for key in ("c4-al32", "c4-si64", "c4-mgo16"):
         w = inputs.make_workload(key)
         spl, t = autotune.tuned_splines(w.lattice, w.cell.grid, w.miller, w.coef, w.pos, storage="f32",
                                         separate_lap=True, device=dev, cache_path=cache, repeats=5)
-        shapes[w.cell.name] = {"lanes": t["lanes"], "order": t["order"]}
+        shapes[w.cell.name] = {"lanes": t["lanes"], "threads": t.get("threads", 0), "order": t["order"]}
         p = torch.from_numpy(w.pos).to(dev)
         cells.append((spl, p, spl.alloc_outputs(p.shape[0])))
-        evals += w.pos.shape[0] * w.coef.shape[0]
+        n = w.pos.shape[0] * w.coef.shape[0]
+        evals += n
+        gathered += n * algorithmic_bytes_per_eval("f32", 2, w.coef.shape[0])
+        works.append(w)
     spls = [c[0] for c in cells]
     pos = [c[1] for c in cells]
     outs = [c[2] for c in cells]
-    step = lambda: eval_batched(spls, pos, outs=outs)
-    ms = time_steps(step, max(10, args.steps // 2), 3, torch, stream)
-    t = sum(ms) / len(ms)
-    for s in spls:
-        s.sync()
-        s.close()
-    return {"workload": "c4 uneven batch (Al-32 48 orb 64^3, Si-64 128 orb 80^3, MgO-16 32 orb 64^3)",
-            "value": evals / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "evals_per_step": evals,
-            "storage": "f32", "shapes": shapes}
+    plan = autotune.tune_batch(spls, pos, outs, storage="f32", key="c4-al32+si64+mgo16", cache_path=cache,
+                               repeats=max(10, args.steps // 2))
+    chosen = {"launch": plan["launch"], "threads": plan["threads"]}
+    # the chosen plan, measured again as graph replays of the whole call
+    t = autotune.time_batch_graph(spls, pos, outs, chosen, repeats=max(10, args.steps // 2))
+    res = {"workload": "c4 uneven batch (Al-32 48 orb 64^3, Si-64 128 orb 80^3, MgO-16 32 orb 64^3)",
+           "value": evals / (t * 1e-3), "unit": UNIT, "ms_per_step": t, "evals_per_step": evals,
+           "storage": "f32", "cuda_graph": True, "shapes": shapes, "launch_plan": chosen,
+           "plans_tried": plan["trials"]}
+    if l1 is not None:
+        res["roofline_l1"] = l1_roofline(gathered, t * 1e-3, l1)
+        res["roofline_l1"]["note"] = "gathered bytes of all cells over the whole call (sorting kernels included)"
+    # sampled outputs of every cell against the oracle (first 8 orbitals)
+    prec = {}
+    for w, (spl, p, o) in zip(works, cells):
+        sample = np.arange(0, w.pos.shape[0], max(1, w.pos.shape[0] // 512))
+        sidx = torch.from_numpy(sample).to(dev)
+        got = tuple(x[sidx][..., :8].double().cpu().numpy() for x in o)
+        beta, blap = oracle.smoothing_tables(w.lattice, w.miller, w.coef[:8], w.cell.grid, laplacian=True)
+        r64 = oracle.bspline_eval(beta, w.lattice, w.pos[sample], beta_lap=blap)
+        rst = oracle.bspline_eval(rounded_table(beta, "f32"), w.lattice, w.pos[sample],
+                                  beta_lap=rounded_table(blap, "f32"))
+        prec[w.cell.name] = precision_report("f32", got, r64, rst, "%d positions x the first 8 orbitals" % len(sample))
+    res["precision"] = prec
+    for s_ in spls:
+        s_.sync()
+        s_.close()
+    return res
 
 
 def run_ours(args):
@@ -766,7 +790,7 @@ def run_ours(args):
         del outs
         spl.close()
         torch.cuda.empty_cache()
-        batched = bench_batched(args, dev, stream)
+        batched = bench_batched(args, dev, stream, l1)
         methods = bench_methods(args, dev, stream)
         methods_c3 = bench_methods_c3(args, dev, stream, l1)
         backward = bench_backward(args, dev, stream)
@@ -864,7 +888,7 @@ def main():
         dev = torch.device("cuda", torch.cuda.current_device())
         leg = {"bloch": bench_bloch, "consumer": bench_consumer, "general": bench_general,
                "methods": bench_methods, "methods_c3": lambda a, d, s: bench_methods_c3(a, d, s, probe_cache(d, 1)),
-               "batched": bench_batched, "backward": bench_backward,
+               "batched": lambda a, d, s: bench_batched(a, d, s, probe_cache(d, 1)), "backward": bench_backward,
                "probes": lambda a, d, s: {"l1": probe_cache(d, 1), "l2": probe_cache(d, 2)}}[args.only]
         print(json.dumps({"leg": args.only, **leg(args, dev, torch.cuda.current_stream())}), flush=True)
     else:

@@ -129,6 +129,7 @@ typedef struct {
     int nonuniform;          /* 1: per-axis grid points (qmcspl_create_grid) */
     int staged;              /* 1: pencil order evaluates with the shared-memory-staged kernel
                                 (see qmcspl_set_order); 0: it falls back to cell order */
+    int block_threads;       /* block shape set by qmcspl_set_block (0 = automatic) */
 } qmcspl_info_t;
 
 /*
@@ -310,6 +311,47 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
 int qmcspl_eval_batched(int n_cells, const qmcspl_t* h, const double* const* pos,
                         const long long* n_pos, void* const* val, void* const* grad,
                         void* const* lap, void* stream);
+
+/*
+ * qmcspl_eval_batched_ex -- qmcspl_eval_batched with an explicit launch plan.
+ *
+ * Not in the paper (the cost model it serves is Sec. III B's: every evaluation gathers 64
+ * coefficient rows, whatever the cell).  opts = NULL is qmcspl_eval_batched.
+ *   opts->launch   QMCSPL_BATCH_AUTO: the rule of qmcspl_eval_batched;
+ *                  QMCSPL_BATCH_SINGLE: every cell's evaluation in the one persistent batched
+ *                  launch (the cells' warp tasks back to back in one static work list);
+ *                  QMCSPL_BATCH_SPLIT: one launch per cell, each with its handle's block shape
+ *   opts->threads  block shape of the batched launch: 0 (= 512) or 512, or 640 for float and
+ *                  bfloat16 tables (else QMCSPL_ERR_UNSUPPORTED)
+ * The cell-order sorting runs per cell before the evaluation launches, as in
+ * qmcspl_eval_batched; the results do not depend on the plan (each position is computed the
+ * same way).  Other arguments and conditions as qmcspl_eval_batched.
+ */
+enum qmcspl_batch_launch {
+    QMCSPL_BATCH_AUTO = 0,
+    QMCSPL_BATCH_SINGLE = 1,
+    QMCSPL_BATCH_SPLIT = 2
+};
+typedef struct {
+    int launch;      /* enum qmcspl_batch_launch */
+    int threads;     /* 0, 512 or 640 */
+} qmcspl_batch_opts;
+int qmcspl_eval_batched_ex(int n_cells, const qmcspl_t* h, const double* const* pos,
+                           const long long* n_pos, void* const* val, void* const* grad,
+                           void* const* lap, const qmcspl_batch_opts* opts, void* stream);
+
+/*
+ * qmcspl_set_block -- block shape of the tricubic B-spline evaluation kernel for this handle.
+ *
+ * Not in the paper.  The kernel walks a static list of warp tasks (one position and one
+ * orbital tile per group of lanes) with one thread block per SM, so the block shape sets how
+ * many neighbouring positions share an SM's L1 at a time (threads / lanes positions per block)
+ * and how many registers each thread may use.  0 = automatic: 640 threads for float tables with
+ * the Laplacian table on launches of four or more rounds of warp tasks, 512 otherwise; 512 or
+ * 640 (float and bfloat16 tables only) fixes the shape.  Results do not depend on it.  The
+ * autotuner (paper_1309_6250_gb300/autotune.py) picks it per workload.
+ */
+int qmcspl_set_block(qmcspl_t h, int threads);
 
 /*
  * qmcspl_get_table -- copy one stored table back to the host in canonical layout

@@ -65,7 +65,15 @@ class Info(ctypes.Structure):
                 ("rows_z", ctypes.c_int), ("lanes", ctypes.c_int), ("tiles", ctypes.c_int),
                 ("table_bytes", ctypes.c_longlong), ("n_pw", ctypes.c_longlong),
                 ("bloch", ctypes.c_int), ("kpoint", ctypes.c_double * 3), ("separate_grad", ctypes.c_int),
-                ("degree", ctypes.c_int), ("nonuniform", ctypes.c_int), ("staged", ctypes.c_int)]
+                ("degree", ctypes.c_int), ("nonuniform", ctypes.c_int), ("staged", ctypes.c_int),
+                ("block_threads", ctypes.c_int)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("launch", ctypes.c_int), ("threads", ctypes.c_int)]
+
+
+BATCH_LAUNCH = {"auto": 0, "single": 1, "split": 2}
 
 
 class GridOpts(ctypes.Structure):
@@ -91,6 +99,8 @@ PROTOTYPES = [
     ("qmcspl_eval_vgl_noalloc", I, [VP, VP, LL, VP, VP, VP, VP]),
     ("qmcspl_eval_vgl_backward", I, [VP, VP, LL, VP, VP, VP, VP, VP, VP, VP]),
     ("qmcspl_eval_batched", I, [I, VP, VP, VP, VP, VP, VP, VP]),
+    ("qmcspl_eval_batched_ex", I, [I, VP, VP, VP, VP, VP, VP, ctypes.POINTER(BatchOpts), VP]),
+    ("qmcspl_set_block", I, [VP, I]),
     ("qmcspl_get_table", I, [VP, I, VP, VP]),
     ("qmcspl_set_table", I, [VP, I, VP, I, VP]),
     ("qmcspl_set_order", I, [VP, I]),

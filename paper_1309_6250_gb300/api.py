@@ -159,6 +159,11 @@ class OrbitalSplines:
             _lib.check(self.lib.qmcspl_set_table(self.handle, int(index), _ptr(t), code, ctypes.c_void_p(s.cuda_stream)))
         t.record_stream(s)   # a temporary copy stays allocated until the stream has read it
 
+    def set_block(self, threads: int) -> None:
+        """Block shape of the B-spline evaluation kernel: 0 (automatic), 512 or 640 threads
+        (640 for float and bfloat16 tables)."""
+        _lib.check(self.lib.qmcspl_set_block(self.handle, int(threads)))
+
     def set_order(self, mode: str) -> None:
         """Order in which eval_vgl visits positions: 'auto', 'input', 'cell' or 'pencil'
         (2 x 2-cell pencils evaluated by the shared-memory-staged kernel where it applies)."""
@@ -250,8 +255,10 @@ class OrbitalSplines:
 
 
 def eval_batched(splines: Sequence[OrbitalSplines], positions: Sequence[torch.Tensor],
-                 outs=None, stream=None):
-    """One kernel launch evaluating several cells (handles of one storage type)."""
+                 outs=None, stream=None, plan=None):
+    """Several cells (handles of one storage type) in one call.  plan = None: the library's
+    rule; else {'launch': 'auto' | 'single' | 'split', 'threads': 0 | 512 | 640} (see
+    qmcspl_eval_batched_ex)."""
     lib = _lib.load()
     n = len(splines)
     if outs is None:
@@ -262,8 +269,11 @@ def eval_batched(splines: Sequence[OrbitalSplines], positions: Sequence[torch.Te
     V = (ctypes.c_void_p * n)(*[o[0].data_ptr() for o in outs])
     G = (ctypes.c_void_p * n)(*[o[1].data_ptr() for o in outs])
     L = (ctypes.c_void_p * n)(*[o[2].data_ptr() for o in outs])
+    opts = None
+    if plan is not None:
+        opts = ctypes.byref(_lib.BatchOpts(_lib.BATCH_LAUNCH[plan.get("launch", "auto")], int(plan.get("threads", 0))))
     with torch.cuda.device(splines[0].device):
-        _lib.check(lib.qmcspl_eval_batched(n, H, P, NP, V, G, L, _stream_handle(stream)))
+        _lib.check(lib.qmcspl_eval_batched_ex(n, H, P, NP, V, G, L, opts, _stream_handle(stream)))
     return outs
 
 

@@ -504,6 +504,7 @@ int qmcspl_info(qmcspl_t h, qmcspl_info_t* out)
     out->degree = h->degree;
     out->nonuniform = h->nonuniform;
     out->staged = staged_eligible(h) ? 1 : 0;
+    out->block_threads = h->block_threads;
     for (int i = 0; i < 3; ++i) out->kpoint[i] = h->kpoint[i];
     return QMCSPL_OK;
 }
@@ -674,13 +675,17 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
                                    static_cast<cudaStream_t>(stream));
 }
 
-int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* pos,
-                        const long long* n_pos, void* const* val, void* const* grad,
-                        void* const* lap, void* stream)
+int qmcspl_eval_batched_ex(int n_cells, const qmcspl_t* hs, const double* const* pos,
+                           const long long* n_pos, void* const* val, void* const* grad,
+                           void* const* lap, const qmcspl_batch_opts* opts, void* stream)
 {
     g_err.clear();
     if (n_cells < 1 || n_cells > QMCSPL_MAX_BATCH)
         return set_error(QMCSPL_ERR_ARG, "n_cells must be in [1, QMCSPL_MAX_BATCH]");
+    const int launch = opts ? opts->launch : QMCSPL_BATCH_AUTO;
+    const int threads = opts ? opts->threads : 0;
+    if (launch < QMCSPL_BATCH_AUTO || launch > QMCSPL_BATCH_SPLIT) return set_error(QMCSPL_ERR_ARG, "unknown batch launch plan");
+    if (threads != 0 && threads != 512 && threads != 640) return set_error(QMCSPL_ERR_ARG, "batch threads must be 0, 512 or 640");
     if (!hs || !pos || !n_pos || !val || !grad || !lap) return set_error(QMCSPL_ERR_ARG, "NULL argument");
     for (int c = 0; c < n_cells; ++c) {
         if (!hs[c]) return set_error(QMCSPL_ERR_ARG, "NULL handle in batch");
@@ -695,6 +700,8 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* po
         if (n_pos[c] < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
         if (n_pos[c] > 0 && !pos[c]) return set_error(QMCSPL_ERR_ARG, "pos is NULL");
     }
+    if (threads == 640 && hs[0]->storage != QMCSPL_F32 && hs[0]->storage != QMCSPL_BF16)
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "640-thread blocks are for float and bfloat16 tables");
     DeviceGuard dg(hs[0]->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Prepared prs[QMCSPL_MAX_BATCH];
@@ -706,7 +713,25 @@ int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* po
         }
     }
     return launch_batched(n_cells, reinterpret_cast<const Handle* const*>(hs), pos, prs, n_pos, val, grad, lap,
-                          st);
+                          launch, threads, st);
+}
+
+int qmcspl_eval_batched(int n_cells, const qmcspl_t* hs, const double* const* pos,
+                        const long long* n_pos, void* const* val, void* const* grad,
+                        void* const* lap, void* stream)
+{
+    return qmcspl_eval_batched_ex(n_cells, hs, pos, n_pos, val, grad, lap, nullptr, stream);
+}
+
+int qmcspl_set_block(qmcspl_t h, int threads)
+{
+    g_err.clear();
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    if (threads != 0 && threads != 512 && threads != 640) return set_error(QMCSPL_ERR_ARG, "threads must be 0, 512 or 640");
+    if (threads == 640 && h->storage != QMCSPL_F32 && h->storage != QMCSPL_BF16)
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "640-thread blocks are for float and bfloat16 tables");
+    h->block_threads = threads;
+    return QMCSPL_OK;
 }
 
 int qmcspl_get_table(qmcspl_t h, int table, double* out_host, void* stream)

@@ -539,10 +539,10 @@ struct BatchArgs {
 };
 static_assert(sizeof(BatchArgs) <= 32000, "batched kernel parameters exceed the 32 KB limit");
 
-template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(QMCSPL_EVAL_THREADS, 1) bspline_vgl_batched_kernel(const __grid_constant__ BatchArgs b)
+template <typename T, bool LAPTAB, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) bspline_vgl_batched_kernel(const __grid_constant__ BatchArgs b)
 {
-    constexpr int WPB = QMCSPL_EVAL_THREADS / 32;
+    constexpr int WPB = THREADS / 32;
     const int lane = threadIdx.x & 31;
     const long long warp = (long long)blockIdx.x * WPB + (threadIdx.x >> 5);
     const long long wstride = (long long)gridDim.x * WPB;
@@ -577,11 +577,21 @@ int launch_shape(const EvalArgs& a, long long warps, cudaStream_t st)
     return cuda_error(cudaGetLastError(), "bspline_vgl_kernel launch");
 }
 
+// Block shapes a caller may choose (qmcspl_set_block, the batched launch plan): 512 threads for
+// every table type, 640 for float and bfloat16 tables (96 registers).
+template <typename T> constexpr bool kHas640 = std::is_same<T, float>::value || std::is_same<T, __nv_bfloat16>::value;
+
+// `threads` = 0: the automatic rule (the large shape from kLargeLaunchRounds rounds of warp tasks
+// on); 512 or 640: that shape.
 template <typename T, bool LAPTAB>
-int launch_typed(const EvalArgs& a, cudaStream_t st)
+int launch_typed(const EvalArgs& a, int threads, cudaStream_t st)
 {
     const int gpw = 32 >> a.lanes_log2;
     const long long warps = (a.n_pos * a.tiles + gpw - 1) / gpw;
+    if constexpr (kHas640<T>) {
+        if (threads == 640) return launch_shape<T, LAPTAB, 640>(a, warps, st);
+    }
+    if (threads == QMCSPL_EVAL_THREADS) return launch_shape<T, LAPTAB, QMCSPL_EVAL_THREADS>(a, warps, st);
     constexpr int large = BspBlock<T, LAPTAB>::large;
     if constexpr (large != QMCSPL_EVAL_THREADS) {
         if (warps >= (long long)kLargeLaunchRounds * sm_count() * (large / 32))
@@ -590,13 +600,21 @@ int launch_typed(const EvalArgs& a, cudaStream_t st)
     return launch_shape<T, LAPTAB, QMCSPL_EVAL_THREADS>(a, warps, st);
 }
 
-template <typename T, bool LAPTAB>
-int launch_batched_typed(const BatchArgs& b, cudaStream_t st)
+template <typename T, bool LAPTAB, int THREADS>
+int launch_batched_shape(const BatchArgs& b, cudaStream_t st)
 {
-    constexpr int threads = QMCSPL_EVAL_THREADS;
-    const long long blocks = grid_for(bspline_vgl_batched_kernel<T, LAPTAB>, threads, b.start[b.n_cells]);
-    bspline_vgl_batched_kernel<T, LAPTAB><<<(unsigned)blocks, threads, 0, st>>>(b);
+    const long long blocks = grid_for(bspline_vgl_batched_kernel<T, LAPTAB, THREADS>, THREADS, b.start[b.n_cells]);
+    bspline_vgl_batched_kernel<T, LAPTAB, THREADS><<<(unsigned)blocks, THREADS, 0, st>>>(b);
     return cuda_error(cudaGetLastError(), "bspline_vgl_batched_kernel launch");
+}
+
+template <typename T, bool LAPTAB>
+int launch_batched_typed(const BatchArgs& b, int threads, cudaStream_t st)
+{
+    if constexpr (kHas640<T>) {
+        if (threads == 640) return launch_batched_shape<T, LAPTAB, 640>(b, st);
+    }
+    return launch_batched_shape<T, LAPTAB, QMCSPL_EVAL_THREADS>(b, st);
 }
 
 void set_outputs(const Handle* h, EvalArgs& a, void* val, void* grad, void* lap)
@@ -623,22 +641,24 @@ int launch_bspline_vgl(const Handle* h, const double* pos, const Prepared& pr, l
     a.n_pos = n_pos;
     set_outputs(h, a, val, grad, lap);
     const bool lt = h->separate_lap != 0;
+    const int th = h->block_threads;
     switch (h->storage) {
-    case QMCSPL_F64: return lt ? launch_typed<double, true>(a, st) : launch_typed<double, false>(a, st);
-    case QMCSPL_F32: return lt ? launch_typed<float, true>(a, st) : launch_typed<float, false>(a, st);
-    case QMCSPL_DF64: return lt ? launch_typed<DF64Tag, true>(a, st) : launch_typed<DF64Tag, false>(a, st);
+    case QMCSPL_F64: return lt ? launch_typed<double, true>(a, th, st) : launch_typed<double, false>(a, th, st);
+    case QMCSPL_F32: return lt ? launch_typed<float, true>(a, th, st) : launch_typed<float, false>(a, th, st);
+    case QMCSPL_DF64: return lt ? launch_typed<DF64Tag, true>(a, th, st) : launch_typed<DF64Tag, false>(a, th, st);
     default:
-        return lt ? launch_typed<__nv_bfloat16, true>(a, st) : launch_typed<__nv_bfloat16, false>(a, st);
+        return lt ? launch_typed<__nv_bfloat16, true>(a, th, st) : launch_typed<__nv_bfloat16, false>(a, th, st);
     }
 }
 
 int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const Prepared* pr,
                    const long long* n_pos, void* const* val, void* const* grad, void* const* lap,
-                   cudaStream_t st)
+                   int launch, int threads, cudaStream_t st)
 {
     thread_local BatchArgs B;   // about 16 KB: kept off the stack, one per calling thread
-    // cells of at least kLargeLaunchRounds rounds of warp tasks (512-thread blocks on every
-    // SM) get their own launch; the others share one batched launch
+    // QMCSPL_BATCH_AUTO: cells of at least kLargeLaunchRounds rounds of warp tasks (512-thread
+    // blocks on every SM) get their own launch, the others share one batched launch;
+    // QMCSPL_BATCH_SINGLE: every cell in the batched launch; QMCSPL_BATCH_SPLIT: every cell alone
     const long long large = (long long)kLargeLaunchRounds * sm_count() * (QMCSPL_EVAL_THREADS / 32);
     int nb = 0;
     B.start[0] = 0;
@@ -653,7 +673,9 @@ int launch_batched(int n_cells, const Handle* const* hs, const double* const* po
         set_outputs(hs[c], a, val[c], grad[c], lap[c]);
         const int gpw = 32 >> a.lanes_log2;
         const long long warps = (a.n_pos * a.tiles + gpw - 1) / gpw;
-        if (warps >= large) {
+        const bool alone = launch == QMCSPL_BATCH_SPLIT || (launch == QMCSPL_BATCH_AUTO && warps >= large);
+        if (alone) {
+            if (warps == 0) continue;
             const int rc = launch_bspline_vgl(hs[c], pos[c], pr[c], n_pos[c], val[c], grad[c], lap[c], st);
             if (rc != QMCSPL_OK) return rc;
             continue;
@@ -666,12 +688,14 @@ int launch_batched(int n_cells, const Handle* const* hs, const double* const* po
     const bool lt = hs[0]->separate_lap != 0;
     switch (hs[0]->storage) {
     case QMCSPL_DF64:
-        return lt ? launch_batched_typed<DF64Tag, true>(B, st) : launch_batched_typed<DF64Tag, false>(B, st);
-    case QMCSPL_F64: return lt ? launch_batched_typed<double, true>(B, st) : launch_batched_typed<double, false>(B, st);
-    case QMCSPL_F32: return lt ? launch_batched_typed<float, true>(B, st) : launch_batched_typed<float, false>(B, st);
+        return lt ? launch_batched_typed<DF64Tag, true>(B, threads, st) : launch_batched_typed<DF64Tag, false>(B, threads, st);
+    case QMCSPL_F64:
+        return lt ? launch_batched_typed<double, true>(B, threads, st) : launch_batched_typed<double, false>(B, threads, st);
+    case QMCSPL_F32:
+        return lt ? launch_batched_typed<float, true>(B, threads, st) : launch_batched_typed<float, false>(B, threads, st);
     default:
-        return lt ? launch_batched_typed<__nv_bfloat16, true>(B, st)
-                  : launch_batched_typed<__nv_bfloat16, false>(B, st);
+        return lt ? launch_batched_typed<__nv_bfloat16, true>(B, threads, st)
+                  : launch_batched_typed<__nv_bfloat16, false>(B, threads, st);
     }
 }
 

@@ -137,6 +137,7 @@ struct qmcspl_s {
     long long ord_cap = 0;    // positions the scratch can hold
     int ord_nbins = 0;        // bins the count array can hold
     int order_mode = 0;       // QMCSPL_ORDER_AUTO / INPUT / CELL
+    int block_threads = 0;    // cubic B-spline kernels: 0 = automatic, else threads per block (512, 640)
     // kernel timing (qmcspl_profile): per call, events before ordering, before and
     // after the evaluation kernel
     bool prof_on = false;
@@ -196,9 +197,10 @@ inline bool is_general(const Handle* h) { return h->degree != 3 || h->nonuniform
 int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
                             const void* gv, const void* gg, const void* gl, void* dcoef,
                             void* dcoef_lap, double* dpos, cudaStream_t stream);
+// launch: QMCSPL_BATCH_AUTO / SINGLE / SPLIT; threads: block shape of the batched launch (0 = 512)
 int launch_batched(int n_cells, const Handle* const* hs, const double* const* pos, const Prepared* pr,
                    const long long* n_pos, void* const* val, void* const* grad, void* const* lap,
-                   cudaStream_t stream);
+                   int launch, int threads, cudaStream_t stream);
 
 // ---- cell ordering (order.cu) ----
 // Bin geometry of a handle: bins of edge[a] grid cells along axis a, nb[a] bins along it;

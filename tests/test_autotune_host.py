@@ -30,3 +30,15 @@ def test_cache_roundtrip(tmp_path):
         f.write("not json")
     assert autotune.load_cache(path) == {}
     assert os.path.exists(path)
+
+
+def test_block_shapes_and_batch_plans():
+    assert autotune.candidate_threads("f32") == [512, 640]
+    assert autotune.candidate_threads("bf16") == [512, 640]
+    assert autotune.candidate_threads("f64") == [512] and autotune.candidate_threads("df64") == [512]
+    plans = autotune.batch_plans("f32")
+    assert {"launch": "split", "threads": 0} in plans
+    assert {"launch": "single", "threads": 640} in plans and {"launch": "single", "threads": 512} in plans
+    assert all(p["launch"] != "single" or p["threads"] == 512 for p in autotune.batch_plans("f64"))
+    # entries of the tuner without the block shape are not read back
+    assert autotune.cache_key("GB300", "smooth", "f32", True, 128, (96, 96, 96), 1).startswith(autotune.CACHE_VERSION)

@@ -47,13 +47,14 @@ def test_autotune_picks_a_candidate_and_caches(tmp_path):
     t = autotune.tune(w.lattice, w.cell.grid, w.miller, w.coef, w.pos, storage="f32", separate_lap=True,
                       device=dev(), repeats=3, cache_path=cache)
     assert t["lanes"] in autotune.candidate_lanes(48, "f32") and t["order"] in ("input", "cell")
-    assert len(t["trials"]) == 2 * len(autotune.candidate_lanes(48, "f32"))
+    assert t["threads"] in autotune.candidate_threads("f32")
+    assert len(t["trials"]) == 2 * len(autotune.candidate_threads("f32")) * len(autotune.candidate_lanes(48, "f32"))
     again = autotune.tune(w.lattice, w.cell.grid, w.miller, w.coef, w.pos, storage="f32",
                           separate_lap=True, device=dev(), cache_path=cache)
     assert again == t
     spl, t2 = autotune.tuned_splines(w.lattice, w.cell.grid, w.miller, w.coef, w.pos, storage="f32",
                                      separate_lap=True, device=dev(), cache_path=cache)
-    assert t2 == t and spl.info()["lanes"] == t["lanes"]
+    assert t2 == t and spl.info()["lanes"] == t["lanes"] and spl.info()["block_threads"] == t["threads"]
     base = splines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32",
                    separate_lap=True)
     for a, b in zip(gpu_eval(spl, w.pos), gpu_eval(base, w.pos)):

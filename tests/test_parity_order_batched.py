@@ -181,3 +181,66 @@ def test_batched_mixes_own_and_shared_launches():
     for a, b in zip(outs, singles):
         for x, y in zip(a, b):
             assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f64"])
+def test_launch_plans_and_block_shapes_give_the_same_bits(storage):
+    """qmcspl_eval_batched_ex: one launch per cell, every cell in the one persistent batched
+    launch with 512 or (float / bfloat16 tables) 640 threads per block, and the automatic rule
+    all give each cell exactly its own qmcspl_eval_vgl outputs, whatever the block shape set on
+    the handles (qmcspl_set_block); the single launch also as a CUDA-graph replay."""
+    from paper_1309_6250_gb300 import _lib
+    from paper_1309_6250_gb300.api import eval_batched
+    cells = []
+    for i, (dims, n_orb, n_pos) in enumerate((((12, 12, 12), 16, 60_000), ((10, 14, 16), 7, 1000),
+                                              ((8, 8, 12), 20, 9001))):
+        lat, mil, coef = inputs.random_cell(540 + i, dims, n_orb, 6.0, 5.0, NONORTHO)
+        cells.append((splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=i != 1),
+                      torch.from_numpy(inputs.positions(lat, n_pos, 40 + i, -1, 2)).to(dev())))
+    # one separate_lap setting per batch: the middle cell goes to its own calls only
+    spls = [cells[0][0], cells[2][0]]
+    pos = [cells[0][1], cells[2][1]]
+    singles = [[t.clone() for t in s.eval_vgl(p)] for s, p in zip(spls, pos)]
+    torch.cuda.synchronize()
+    shapes = [0, 512] + ([640] if storage in ("f32", "bf16") else [])
+    for th in shapes:
+        for s in spls:
+            s.set_block(th)
+            assert s.info()["block_threads"] == th
+        for s, p, ref in zip(spls, pos, singles):
+            got = s.eval_vgl(p)
+            torch.cuda.synchronize()
+            assert all(torch.equal(x, y) for x, y in zip(got, ref))
+        for plan in [{"launch": "auto"}, {"launch": "split"}] + [{"launch": "single", "threads": t} for t in shapes]:
+            outs = eval_batched(spls, pos, plan=plan)
+            torch.cuda.synchronize()
+            for a, b in zip(outs, singles):
+                assert all(torch.equal(x, y) for x, y in zip(a, b)), (th, plan)
+    # the single persistent launch captured in a CUDA graph
+    plan = {"launch": "single", "threads": shapes[-1]}
+    outs = [s.alloc_outputs(p.shape[0]) for s, p in zip(spls, pos)]
+    g = torch.cuda.CUDAGraph()
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        eval_batched(spls, pos, outs=outs, stream=st, plan=plan)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            eval_batched(spls, pos, outs=outs, stream=st, plan=plan)
+    for o in outs:
+        for t in o:
+            t.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(outs, singles):
+        assert all(torch.equal(x, y) for x, y in zip(a, b))
+    # rejected plans and shapes
+    with pytest.raises(_lib.QmcsplError) as ei:
+        eval_batched(spls, pos, plan={"launch": "single", "threads": 256})
+    assert ei.value.code == _lib.ERR_ARG
+    if storage == "f64":
+        with pytest.raises(_lib.QmcsplError) as ei:
+            spls[0].set_block(640)
+        assert ei.value.code == _lib.ERR_UNSUPPORTED
+        with pytest.raises(_lib.QmcsplError) as ei:
+            eval_batched(spls, pos, plan={"launch": "single", "threads": 640})
+        assert ei.value.code == _lib.ERR_UNSUPPORTED
