@@ -483,6 +483,62 @@ def bench_backward(args, dev, stream):
             "value": n * o / (t * 1e-3), "ms_per_step": t}
 
 
+def bench_backward_c3(args, dev, stream, l1=None):
+    """Both adjoints (coefficient scatter and position gradient) at the many-walker scale: the
+    MgO-like 64-atom cell, 128 orbitals on 96^3, FP32 smoothing + Laplacian tables, 2048 walkers x
+    256 electrons, upstream weights N(0,1) on value, gradient and Laplacian (seeded device
+    generator).  Cell order (the default from 8192 positions) against input order; dL/dr of every
+    512th position against the oracle adjoint."""
+    import torch
+    import oracle
+    from paper_1309_6250_gb300.api import OrbitalSplines
+    w = inputs.make_workload("c3")
+    n, o = w.pos.shape[0], w.coef.shape[0]
+    spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32",
+                         separate_lap=True, device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3006)
+    gv = torch.randn((n, o), generator=gen, device=dev, dtype=torch.float32)
+    gg = torch.randn((n, 3, o), generator=gen, device=dev, dtype=torch.float32)
+    gl = torch.randn((n, o), generator=gen, device=dev, dtype=torch.float32)
+    pos = torch.from_numpy(w.pos).to(dev)
+    dc = torch.zeros(spl.coef_shape(), dtype=torch.float32, device=dev)
+    dcl = torch.zeros_like(dc)
+    res = {"workload": "c3 MgO-like 64-atom, 128 orbitals, 96^3, 2048 x 256 positions, f32 smoothing + Laplacian "
+                       "tables, upstream N(0,1) (seed 3006)", "unit": UNIT, "orders": {}}
+    # table rows read (64 per table) + their 64 dbeta rows updated (atomic adds) per orbital-evaluation,
+    # the five upstream values and the position
+    bpe = 2 * 64 * 4 + 2 * 64 * 4 + 5 * 4 + 48.0 / o
+    for order in ("cell", "input"):
+        spl.set_order(order)
+        step = lambda: spl.backward(pos, gv, gg, gl, dcoef=dc, dcoef_lap=dcl)
+        ms = time_steps(step, max(5, args.steps // 40), 2, torch, stream)
+        spl.sync()
+        t = sum(ms) / len(ms)
+        r = {"value": n * o / (t * 1e-3), "ms_per_step": t, "bytes_per_eval": bpe}
+        if l1 is not None:
+            r["roofline_l1"] = l1_roofline(bpe * n * o, t * 1e-3, l1)
+        res["orders"][order] = r
+    res["value"] = res["orders"]["cell"]["value"]
+    res["ms_per_step"] = res["orders"]["cell"]["ms_per_step"]
+    # dL/dr of sampled positions against the oracle adjoint (FP64, on the oracle's FP32-rounded tables)
+    spl.set_order("cell")
+    dpos = spl.backward(pos, gv, gg, gl)
+    spl.sync()
+    sample = np.arange(0, n, 512)
+    sidx = torch.from_numpy(sample).to(dev)
+    up = [x[sidx].double().cpu().numpy() for x in (gv, gg, gl)]
+    beta, blap = oracle.smoothing_tables(w.lattice, w.miller, w.coef, w.cell.grid, laplacian=True)
+    _, _, rdpos = oracle.bspline_adjoint(rounded_table(beta, "f32"), w.lattice, w.pos[sample], *up,
+                                         beta_lap=rounded_table(blap, "f32"))
+    err = float(oracle.relative_error(dpos[sidx].cpu().numpy(), rdpos))
+    res["dpos_parity"] = {"max_rel_err": err, "tolerance": TOLERANCE["f32"], "ok": err <= TOLERANCE["f32"],
+                          "sample": "%d positions (every 512-th)" % len(sample),
+                          "reference": "FP64 oracle adjoint on the oracle's tables rounded to FP32"}
+    spl.close()
+    return res
+
+
 def bench_bloch(args, dev, stream):
     """Complex Bloch orbitals at k != 0 (Sec. II) on the MgO-like 64-atom cell: 64 bands at
     the zone corner R = (1/2, 1/2, 1/2) on 96^3 (the same table bytes as the 128 real
@@ -785,7 +841,7 @@ def run_ours(args):
             if order == "auto" and st not in var_got:
                 var_got[st] = [t[par_idx].double().cpu().numpy() for t in outs]
 
-    batched = methods = methods_c3 = backward = bloch = consumer = general = None
+    batched = methods = methods_c3 = backward = backward_c3 = bloch = consumer = general = None
     if not args.no_variants and rank == 0:
         del outs
         spl.close()
@@ -794,6 +850,7 @@ def run_ours(args):
         methods = bench_methods(args, dev, stream)
         methods_c3 = bench_methods_c3(args, dev, stream, l1)
         backward = bench_backward(args, dev, stream)
+        backward_c3 = bench_backward_c3(args, dev, stream, l1)
         bloch = bench_bloch(args, dev, stream)
         consumer = bench_consumer(args, dev, stream)
         general = bench_general(args, dev, stream)
@@ -851,6 +908,7 @@ def run_ours(args):
         "methods_si8_48": methods,
         "methods_mgo64_96": methods_c3,
         "backward_si64_72": backward,
+        "backward_mgo64_96": backward_c3,
         "bloch_mgo64_96": bloch,
         "slater_consumer_mgo64": consumer,
         "general_degree_si8_48": general,
@@ -878,7 +936,7 @@ def main():
     ap.add_argument("--n-pos", type=int, default=None, help="use only the first N positions (profiling)")
     ap.add_argument("--only", default="all",
                     choices=["all", "bloch", "consumer", "general", "methods", "methods_c3", "batched",
-                             "backward", "probes"],
+                             "backward", "backward_c3", "probes"],
                     help="run one secondary leg alone and print its JSON (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -889,6 +947,7 @@ def main():
         leg = {"bloch": bench_bloch, "consumer": bench_consumer, "general": bench_general,
                "methods": bench_methods, "methods_c3": lambda a, d, s: bench_methods_c3(a, d, s, probe_cache(d, 1)),
                "batched": lambda a, d, s: bench_batched(a, d, s, probe_cache(d, 1)), "backward": bench_backward,
+               "backward_c3": lambda a, d, s: bench_backward_c3(a, d, s, probe_cache(d, 1)),
                "probes": lambda a, d, s: {"l1": probe_cache(d, 1), "l2": probe_cache(d, 2)}}[args.only]
         print(json.dumps({"leg": args.only, **leg(args, dev, torch.cuda.current_stream())}), flush=True)
     else:

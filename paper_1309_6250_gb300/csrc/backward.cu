@@ -39,6 +39,29 @@ int launch_general_backward_bf16(const Handle* h, const BwdArgs& a, cudaStream_t
 
 namespace {
 
+// Grid cell and local coordinate t of position ip in the adjoint's arithmetic type A: from the
+// per-position records when the launch has them (float records for float and bfloat16 tables,
+// double records for double tables), else reduced here in FP64 and rounded to A -- the same
+// values either way.  All 32 lanes must call it.
+template <typename A>
+__device__ __forceinline__ void bwd_coords(const EvalArgs& p, long long ip, int L, int sub, int gbase, int& ix,
+                                           int& iy, int& iz, A& tx, A& ty, A& tz, bool& ok)
+{
+    if constexpr (sizeof(A) == 4) {
+        float x, y, z;
+        coords_float(p, ip, L, sub, gbase, ix, iy, iz, x, y, z, ok);
+        tx = x;
+        ty = y;
+        tz = z;
+    } else {
+        double x, y, z;
+        coords_double(p, ip, L, sub, gbase, ix, iy, iz, x, y, z, ok);
+        tx = x;
+        ty = y;
+        tz = z;
+    }
+}
+
 template <typename T, bool LAPTAB, bool BLOCH>
 __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs b)
 {
@@ -60,19 +83,19 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
     for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
         const long long gid = w0 + (lane >> p.lanes_log2);
         const bool active = gid < total;
-        const long long ip = active ? gid / p.tiles : 0;
-        const int tile = active ? (int)(gid - ip * p.tiles) : 0;
-        const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
+        const long long q = active ? gid / p.tiles : 0;
+        const int tile = active ? (int)(gid - q * p.tiles) : 0;
+        const long long ip = active ? order_index(p, q) : 0;   // through the cell order, if any
         int ix, iy, iz;
-        double tx, ty, tz;
+        A tx, ty, tz;
         bool ok;
-        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+        bwd_coords<A>(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
         if (active && !ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
 
         A w[3][4], dw[3][4], d2w[3][4];
-        bspline_weights<A>((A)tx, w[0], dw[0], d2w[0]);
-        bspline_weights<A>((A)ty, w[1], dw[1], d2w[1]);
-        bspline_weights<A>((A)tz, w[2], dw[2], d2w[2]);
+        bspline_weights<A>(tx, w[0], dw[0], d2w[0]);
+        bspline_weights<A>(ty, w[1], dw[1], d2w[1]);
+        bspline_weights<A>(tz, w[2], dw[2], d2w[2]);
         const A d3w[4] = {A(-1.5), A(4.5), A(-4.5), A(1.5)};
 
         const int chunk = tile * L + sub;
@@ -712,7 +735,7 @@ int launch_pp_typed(const BwdArgs& a, cudaStream_t st)
 
 }  // namespace
 
-int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos, const void* gv,
+int launch_bspline_backward(Handle* h, const double* pos, long long n_pos, const void* gv,
                             const void* gg, const void* gl, void* dcoef, void* dcoef_lap, double* dpos,
                             cudaStream_t st)
 {
@@ -757,6 +780,17 @@ int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
         case QMCSPL_DF64: return launch_five_typed<DF64Tag>(a, false, st);   // B-splines only
         default: return launch_five_typed<__nv_bfloat16>(a, lag, st);
         }
+    }
+    // cubic B-splines: positions in cell order (neighbouring positions scatter into the same
+    // stencil rows one after the other, so the atomics meet in L2 rather than in HBM) and their
+    // coordinates from per-position records (no FP64 in the kernel); double-float tables keep the
+    // FP64 reduction in the kernel
+    if (use_cell_order(h, n_pos)) {
+        Prepared pr;
+        const int rc = prepare_positions(h, pos, n_pos, true, &pr, st);
+        if (rc != QMCSPL_OK) return rc;
+        a.e.perm = pr.perm;
+        a.e.rec = h->storage == QMCSPL_DF64 ? nullptr : pr.rec;
     }
     const bool lt = h->separate_lap != 0;
     switch (h->storage) {

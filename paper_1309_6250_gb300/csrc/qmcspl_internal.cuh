@@ -194,7 +194,7 @@ int launch_pp_vgl(const Handle* h, const double* pos, const Prepared& pr, long l
 int launch_general_vgl(const Handle* h, const double* pos, const Prepared& pr, long long n_pos, void* val,
                        void* grad, void* lap, cudaStream_t stream);
 inline bool is_general(const Handle* h) { return h->degree != 3 || h->nonuniform; }
-int launch_bspline_backward(const Handle* h, const double* pos, long long n_pos,
+int launch_bspline_backward(Handle* h, const double* pos, long long n_pos,
                             const void* gv, const void* gg, const void* gl, void* dcoef,
                             void* dcoef_lap, double* dpos, cudaStream_t stream);
 // launch: QMCSPL_BATCH_AUTO / SINGLE / SPLIT; threads: block shape of the batched launch (0 = 512)

@@ -489,3 +489,73 @@ def test_general_backward_nonfinite_position_and_empty_call():
     out = spl.backward(empty, dcoef=dc)
     spl.sync()
     assert out.shape == (0, 3) and float(dc.abs().sum()) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# cell order (many walkers): the adjoint visits positions sorted by cell, coordinates from records
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+def test_cell_ordered_backward_matches_input_order_and_oracle(storage):
+    """32,768 positions on the Si-like 8-atom cell (16 orbitals, 48^3, smoothing + Laplacian
+    table): the cell-ordered adjoint (the default from 8192 positions) against input order and
+    against the oracle adjoint on the oracle's tables rounded as stored."""
+    w = inputs.make_workload("c2")
+    dims = w.cell.grid
+    spl = splines(w.lattice, dims, w.miller, w.coef, method="smooth", storage=storage, separate_lap=True)
+    n, o = w.pos.shape[0], w.coef.shape[0]
+    gv, gg, gl = inputs.upstream_weights(n, o, 3100)
+    if storage != "f64":
+        gv, gg, gl = (x.astype(np.float32).astype(np.float64) for x in (gv, gg, gl))
+    out = {}
+    for order in ("input", "cell"):
+        spl.set_order(order)
+        out[order] = gpu_backward(spl, w.pos, gv, gg, gl)
+    tol = TOL[storage] if storage != "bf16" else TOL["f32"]    # FP32 arithmetic on the stored tables
+    for a, b in zip(out["cell"], out["input"]):
+        assert oracle.relative_error(a, b) < (1e-13 if storage == "f64" else 1e-6)
+    beta, blap = oracle_tables(w.lattice, w.miller, w.coef, dims, "smooth", storage, True)
+    rdc, rdcl, rdpos = oracle.bspline_adjoint(beta, w.lattice, w.pos, gv, gg, gl, beta_lap=blap)
+    dc, dcl, dpos = out["cell"]
+    for got, ref in ((dc, rdc), (dcl, rdcl), (dpos, rdpos)):
+        assert oracle.relative_error(got, ref) < tol
+    spl.close()
+
+
+@pytest.mark.slow
+def test_c3_mgo64_backward_full_size():
+    """The many-walker adjoint at full size: 2048 x 256 positions, 128 orbitals on 96^3, FP32 tables
+    with the Laplacian table, cell order.  dL/dr of every 1024th position against the oracle
+    adjoint; the coefficient adjoint of the first 8 orbitals by the exact linearity identity
+    sum(dL/dbeta * beta') = L(beta') with random tables beta' evaluated by the oracle at every
+    position (beta' zero for the other orbitals)."""
+    w = inputs.make_workload("c3")
+    dims = w.cell.grid
+    n, o = w.pos.shape[0], w.coef.shape[0]
+    spl = splines(w.lattice, dims, w.miller, w.coef, method="smooth", storage="f32", separate_lap=True)
+    rng = np.random.default_rng(3200)
+    gv = rng.standard_normal((n, o), dtype=np.float32)
+    gg = rng.standard_normal((n, 3, o), dtype=np.float32)
+    gl = rng.standard_normal((n, o), dtype=np.float32)
+    dc = torch.zeros(spl.coef_shape(), dtype=torch.float32, device=dev())
+    dcl = torch.zeros_like(dc)
+    dpos = spl.backward(t(w.pos, torch.float64), t(gv, torch.float32), t(gg, torch.float32), t(gl, torch.float32),
+                        dcoef=dc, dcoef_lap=dcl)
+    spl.sync()
+    sample = np.arange(0, n, 1024)
+    # dL/dr of a position involves every orbital: the oracle adjoint of the sample on all 128
+    bfull, blfull = oracle_tables(w.lattice, w.miller, w.coef, dims, "smooth", "f32", True)
+    up = [x[sample].astype(np.float64) for x in (gv, gg, gl)]
+    _, _, rdpos = oracle.bspline_adjoint(bfull, w.lattice, w.pos[sample], *up, beta_lap=blfull)
+    e_pos = oracle.relative_error(dpos.cpu().numpy()[sample], rdpos)
+    b1 = rng.standard_normal(dims + (8,))
+    b2 = rng.standard_normal(dims + (8,))
+    v, g, l = oracle.bspline_eval(b1, w.lattice, w.pos, beta_lap=b2)
+    ref = float(np.sum(gv[:, :8] * v) + np.sum(gg[:, :, :8] * g) + np.sum(gl[:, :8] * l))
+    dcn, dcln = dc.double().cpu().numpy()[..., :8], dcl.double().cpu().numpy()[..., :8]
+    lin = float(np.sum(dcn * b1) + np.sum(dcln * b2))
+    scale = float(np.sum(np.abs(dcn) * np.abs(b1)) + np.sum(np.abs(dcln) * np.abs(b2)))
+    print("c3 backward: dpos relative error %.2e, linearity %.3e vs %.3e (scale %.3e)" % (e_pos, lin, ref, scale))
+    assert e_pos < TOL["f32"]
+    assert abs(lin - ref) <= 2e-6 * scale
+    spl.close()
