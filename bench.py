@@ -168,12 +168,8 @@ def time_steps(fn, steps, warmup, torch, stream):
 
 def rounded_table(t, storage):
     """A table as the GPU stores it (FP32 or BF16 rounding), back in float64."""
-    if t is None or storage in ("f64", "df64"):
-        return t
-    if storage == "f32":
-        return t.astype(np.float32).astype(np.float64)
-    import torch
-    return torch.from_numpy(np.ascontiguousarray(t)).to(torch.bfloat16).double().numpy()
+    import oracle
+    return oracle.round_to_storage(t, storage)
 
 
 TOLERANCE = {"f64": 1e-12, "df64": 1e-12, "f32": 2e-6, "bf16": 1e-2}

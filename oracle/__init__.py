@@ -933,6 +933,27 @@ def slater_kinetic(val, grad, lap, n_walkers: int, n_elec: int, n_up: int):
 
 
 # ---------------------------------------------------------------------------
+# reduced-precision storage of a table (the benchmark spec's precision pattern: FP64 construction,
+# FP32 / BF16 storage)
+# ---------------------------------------------------------------------------
+
+def round_to_storage(table: Optional[np.ndarray], storage: str) -> Optional[np.ndarray]:
+    """A table of FP64 coefficients as stored in `storage`, back in float64: each value rounded
+    once to the nearest representable number, ties to even -- FP32 (24 significant bits) or
+    BF16 (8 significant bits, FP32's exponent range); FP64 and double-float ('df64': a float pair
+    that carries the FP64 value to about 2^-48) as they are.  Written from the definition of the
+    two formats: frexp gives x = m 2^e with 1/2 <= |m| < 1, and m 2^b is rounded to an integer
+    (numpy.round is round-half-to-even) for b significant bits.  Values here are far from the
+    formats' overflow and subnormal ranges."""
+    if table is None or storage in ("f64", "df64"):
+        return table
+    bits = {"f32": 24, "bf16": 8}[storage]
+    x = np.asarray(table, dtype=np.float64)
+    m, e = np.frexp(x)
+    return np.ldexp(np.round(np.ldexp(m, bits)), e - bits)
+
+
+# ---------------------------------------------------------------------------
 # error metrics
 # ---------------------------------------------------------------------------
 

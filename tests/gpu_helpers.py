@@ -20,12 +20,8 @@ def splines(*a, **k):
 
 
 def rounded(a, storage):
-    import torch
-    if a is None or storage in ("f64", "df64"):
-        return a
-    if storage == "f32":
-        return a.astype(np.float32).astype(np.float64)
-    return torch.from_numpy(np.ascontiguousarray(a)).to(torch.bfloat16).double().numpy()
+    """A table as the GPU stores it, back in float64 (the oracle's single round-to-nearest-even)."""
+    return oracle.round_to_storage(a, storage)
 
 
 def gpu_eval(spl, pos):

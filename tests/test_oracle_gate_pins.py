@@ -12,6 +12,9 @@ E_cut 15 Ha, decay 4): interpolating coefficients from a dense 4096 x 4096 solve
 periodic interpolation system (Appendix, "Interpolating B-spline coefficients") on grid values
 from direct planewave sums, then value, gradient and Laplacian of Eq. (b-splineapproximation)
 as sums over every grid point and its periodic images, with no stencil bookkeeping.
+
+The rounding of a table to its storage type (FP32, BF16), which every reduced-precision parity
+test applies to the oracle's tables, is pinned on hand-computed values and ties.
 """
 import numpy as np
 import pytest
@@ -192,3 +195,41 @@ def test_c1_brute_force_16_cubed_dense_solve_and_full_grid_sum():
     # the interpolating spline passes through the planewave grid values
     gv, _, _ = oracle.bspline_eval(beta, lat, gpts[::97])
     assert oracle.relative_error(gv, phi[::97]) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# storage rounding: one round-to-nearest-even from FP64 to FP32 or BF16
+# ---------------------------------------------------------------------------
+
+def test_round_to_storage_hand_computed_and_ties_to_even():
+    r = oracle.round_to_storage
+    # BF16 keeps 8 significant bits: the spacing above 1 is 2^-7
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -8 + 2.0 ** -30, -(1.0 + 2.0 ** -8),
+                  0.0, 3.0, 255.5, 2.0 ** -100, -6.5])
+    want = np.array([1.0, 1.0, 1.0 + 2 * 2.0 ** -7, 1.0 + 2.0 ** -7, -1.0, 0.0, 3.0, 256.0, 2.0 ** -100, -6.5])
+    np.testing.assert_array_equal(r(x, "bf16"), want)
+    # FP32: 24 significant bits, ties to even, against numpy's own IEEE conversion
+    rng = np.random.default_rng(72)
+    y = rng.standard_normal(100_000) * np.exp(rng.uniform(-20, 20, 100_000))
+    y[:4] = [1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 1.0 + 2.0 ** -24 + 2.0 ** -60, 0.1]
+    np.testing.assert_array_equal(r(y, "f32"), y.astype(np.float32).astype(np.float64))
+    assert r(y, "f64") is y and r(None, "bf16") is None
+
+
+def test_round_to_storage_bf16_is_a_single_rounding():
+    """BF16 of a float64 value is rounded once: values just above a BF16 midpoint round up even
+    when their nearest float32 is the midpoint itself (rounding through float32 first would round
+    those to even, i.e. down, one BF16 step off)."""
+    r = oracle.round_to_storage
+    mid = 1.0 + 2.0 ** -8                      # halfway between 1 and 1 + 2^-7
+    x = np.array([mid + 2.0 ** -30, mid - 2.0 ** -30])
+    assert float(x[0].astype(np.float32)) == mid   # float32 cannot tell them from the midpoint
+    np.testing.assert_array_equal(r(x, "bf16"), [1.0 + 2.0 ** -7, 1.0])
+    # the result is representable in BF16: its FP32 bits have 16 zero low bits
+    rng = np.random.default_rng(73)
+    z = r(rng.standard_normal(10_000), "bf16").astype(np.float32)
+    assert np.all(z.view(np.uint32) & 0xFFFF == 0)
+    # and it is the nearest such value: within half a BF16 step of the input
+    w = rng.standard_normal(10_000)
+    q = r(w, "bf16")
+    assert np.all(np.abs(q - w) <= 0.5 * np.ldexp(1.0, np.frexp(q)[1] - 8) + 1e-300)

@@ -36,11 +36,7 @@ def oracle_tables(method, lattice, miller, coef, dims, sep):
 
 
 def rounded(a, storage):
-    if storage in ("f64", "df64"):
-        return a
-    if storage == "f32":
-        return a.astype(np.float32).astype(np.float64)
-    return torch.from_numpy(a).to(torch.bfloat16).double().numpy()
+    return oracle.round_to_storage(a, storage)
 
 
 def gpu_eval(spl, pos):
