@@ -62,6 +62,204 @@ __device__ __forceinline__ void bwd_coords(const EvalArgs& p, long long ip, int 
     }
 }
 
+// One position's share of both adjoints for the lanes of one group (L lanes, lane `sub` owning the
+// 16-byte chunk `chunk` of every stored row, E orbitals from o0 = chunk E): the coefficient adjoint's
+// 64 stencil-point rows go to scatter(ix, iy, iz, l, m, n, o0, v, vl) (v for the value table, vl for
+// the Laplacian table), the position adjoint is summed over the group and added to dpos[ip] by lane
+// sub = 0 (POS = false leaves the position adjoint out).  first_part: this group's part is the one
+// that reports a non-finite position.  All 32 lanes of the warp must call it (the group reductions
+// shuffle).
+template <typename T, bool LAPTAB, bool BLOCH, typename Scatter, bool POS = true>
+__device__ __forceinline__ void bwd_position(const BwdArgs& b, long long ip, bool active, bool first_part, int chunk,
+                                             int L, int sub, int gbase, Scatter&& scatter)
+{
+    using A = typename Traits<T>::A;
+    constexpr int E = Traits<T>::E;
+    const EvalArgs& p = b.e;
+    const size_t rowb = (size_t)p.row_stride * sizeof(T);
+    const size_t colb = (size_t)p.col_stride * sizeof(T);
+    const int n_orb = p.n_orb;
+    int ix, iy, iz;
+    A tx, ty, tz;
+    bool ok;
+    bwd_coords<A>(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    if (active && !ok && sub == 0 && first_part) atomicOr(p.err, 1);
+
+    A w[3][4], dw[3][4], d2w[3][4];
+    bspline_weights<A>(tx, w[0], dw[0], d2w[0]);
+    bspline_weights<A>(ty, w[1], dw[1], d2w[1]);
+    bspline_weights<A>(tz, w[2], dw[2], d2w[2]);
+    const A d3w[4] = {A(-1.5), A(4.5), A(-4.5), A(1.5)};
+
+    const int o0 = chunk * E;
+    // upstream weights of my orbitals (zero for inactive lanes and padding)
+    A wv[E], wl[E], gt[3][E];
+    A hv[E], hl[E], hg[3][E];   // Bloch: upstream of the bracket (phase term of dL/dr)
+    {
+        A wg[3][E];
+        const A* gvp = static_cast<const A*>(b.gv);
+        const A* ggp = static_cast<const A*>(b.gg);
+        const A* glp = static_cast<const A*>(b.gl);
+        const bool use = active && o0 < n_orb;
+        load_run<A>(use && gvp ? gvp + ip * n_orb + o0 : nullptr, wv, o0, n_orb, E);
+        load_run<A>(use && glp ? glp + ip * n_orb + o0 : nullptr, wl, o0, n_orb, E);
+        for (int a = 0; a < 3; ++a)
+            load_run<A>(use && ggp ? ggp + (ip * 3 + a) * n_orb + o0 : nullptr, wg[a], o0, n_orb, E);
+        if constexpr (BLOCH) bloch_upstream<A, E, LAPTAB>(p, p.pos + 3 * ip, wv, wg, wl, hv, hg, hl);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                gt[i][e] = (A)p.mg[i] * wg[0][e] + (A)p.mg[3 + i] * wg[1][e] + (A)p.mg[6 + i] * wg[2][e];
+    }
+    const A ml0 = (A)p.ml[0], ml1 = (A)p.ml[1], ml2 = (A)p.ml[2];
+    const A ml3 = (A)p.ml[3], ml4 = (A)p.ml[4], ml5 = (A)p.ml[5];
+    int xs[4], ys[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        xs[j] = wrap1(ix + j - 1, p.nx);
+        ys[j] = wrap1(iy + j - 1, p.ny);
+    }
+
+    // ---- coefficient adjoint: the weights of the 64 stencil points, handed to `scatter` ----
+    // (a non-finite position adds nothing; its dL/dr comes out NaN)
+    if (b.dcoef && active && ok && o0 < n_orb) {
+        for (int l = 0; l < 4; ++l)
+            for (int m = 0; m < 4; ++m)
+                for (int n = 0; n < 4; ++n) {
+                    const A B = w[0][l] * w[1][m] * w[2][n];
+                    const A Bx = dw[0][l] * w[1][m] * w[2][n];
+                    const A By = w[0][l] * dw[1][m] * w[2][n];
+                    const A Bz = w[0][l] * w[1][m] * dw[2][n];
+                    A lapB = 0;
+                    if (!LAPTAB)
+                        lapB = ml0 * d2w[0][l] * w[1][m] * w[2][n] + ml1 * w[0][l] * d2w[1][m] * w[2][n] +
+                               ml2 * w[0][l] * w[1][m] * d2w[2][n] + ml3 * dw[0][l] * dw[1][m] * w[2][n] +
+                               ml4 * dw[0][l] * w[1][m] * dw[2][n] + ml5 * w[0][l] * dw[1][m] * dw[2][n];
+                    A v[E], vl[E];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        v[e] = wv[e] * B + gt[0][e] * Bx + gt[1][e] * By + gt[2][e] * Bz;
+                        if (LAPTAB) vl[e] = wl[e] * B;
+                        else v[e] += wl[e] * lapB;
+                    }
+                    scatter(ix, iy, iz, l, m, n, o0, v, vl);
+                }
+    }
+
+    // ---- position adjoint (POS = false: the caller computes it elsewhere) ----
+    if (POS && b.dpos) {
+        // reduced derivatives of my orbitals: gradient, Hessian, gradient of the Laplacian
+        A g1[3][E], h2[6][E], d3[3][E];
+        A u0[E], lam[E];   // Bloch: value of u and of the Laplacian table, for the phase term
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            for (int i = 0; i < 3; ++i) g1[i][e] = d3[i][e] = A(0);
+            for (int i = 0; i < 6; ++i) h2[i][e] = A(0);
+            u0[e] = lam[e] = A(0);
+        }
+        const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
+        const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb
+                                : nullptr;
+        // a lane whose chunk lies past the stored row (a wide group on a short row) reads nothing
+        const bool live = (size_t)chunk * 16 < rowb;
+        for (int l = 0; l < 4; ++l)
+            for (int m = 0; m < 4; ++m) {
+                const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb;
+                A a[4][E], al[2][E];
+#pragma unroll
+                for (int e = 0; e < E; ++e) a[0][e] = a[1][e] = a[2][e] = a[3][e] = al[0][e] = al[1][e] = A(0);
+#pragma unroll
+                for (int n = 0; n < 4 && live; ++n) {
+                    A c[E];
+                    unpack<T>(ldg_table(p, t0 + col + n * rowb), c);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        a[0][e] = fma(w[2][n], c[e], a[0][e]);
+                        a[1][e] = fma(dw[2][n], c[e], a[1][e]);
+                        a[2][e] = fma(d2w[2][n], c[e], a[2][e]);
+                        a[3][e] = fma(d3w[n], c[e], a[3][e]);
+                    }
+                    if (LAPTAB) {
+                        unpack<T>(ldg_table(p, t1 + col + n * rowb), c);
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            al[0][e] = fma(w[2][n], c[e], al[0][e]);
+                            al[1][e] = fma(dw[2][n], c[e], al[1][e]);
+                        }
+                    }
+                }
+                const A bx = w[0][l], dbx = dw[0][l], d2bx = d2w[0][l], d3bx = d3w[l];
+                const A by = w[1][m], dby = dw[1][m], d2by = d2w[1][m], d3by = d3w[m];
+                // third-derivative weights contracted with the Laplacian metric
+                const A x0 = ml0 * d3bx * by + ml1 * dbx * d2by + ml3 * d2bx * dby;
+                const A x1 = ml4 * d2bx * by + ml5 * dbx * dby;
+                const A x2 = ml2 * dbx * by;
+                const A y0 = ml0 * d2bx * dby + ml1 * bx * d3by + ml3 * dbx * d2by;
+                const A y1 = ml4 * dbx * dby + ml5 * bx * d2by;
+                const A y2 = ml2 * bx * dby;
+                const A z1 = ml0 * d2bx * by + ml1 * bx * d2by + ml3 * dbx * dby;
+                const A z2 = ml4 * dbx * by + ml5 * bx * dby;
+                const A z3 = ml2 * bx * by;
+                if constexpr (BLOCH) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        u0[e] += bx * by * a[0][e];
+                        if (LAPTAB) lam[e] += bx * by * al[0][e];
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    g1[0][e] += dbx * by * a[0][e];
+                    g1[1][e] += bx * dby * a[0][e];
+                    g1[2][e] += bx * by * a[1][e];
+                    h2[0][e] += d2bx * by * a[0][e];
+                    h2[1][e] += bx * d2by * a[0][e];
+                    h2[2][e] += bx * by * a[2][e];
+                    h2[3][e] += dbx * dby * a[0][e];
+                    h2[4][e] += dbx * by * a[1][e];
+                    h2[5][e] += bx * dby * a[1][e];
+                    if (LAPTAB) {
+                        d3[0][e] += dbx * by * al[0][e];
+                        d3[1][e] += bx * dby * al[0][e];
+                        d3[2][e] += bx * by * al[1][e];
+                    } else {
+                        d3[0][e] += x0 * a[0][e] + x1 * a[1][e] + x2 * a[2][e];
+                        d3[1][e] += y0 * a[0][e] + y1 * a[1][e] + y2 * a[2][e];
+                        d3[2][e] += z1 * a[1][e] + z2 * a[2][e] + z3 * a[3][e];
+                    }
+                }
+            }
+        // u_i = wv g_i + sum_j H_ij g~_j + wl d3_i, summed over my orbitals (in FP64)
+        double u[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const A hxx = h2[0][e], hyy = h2[1][e], hzz = h2[2][e];
+            const A hxy = h2[3][e], hxz = h2[4][e], hyz = h2[5][e];
+            u[0] += (double)(wv[e] * g1[0][e] + hxx * gt[0][e] + hxy * gt[1][e] + hxz * gt[2][e] + wl[e] * d3[0][e]);
+            u[1] += (double)(wv[e] * g1[1][e] + hxy * gt[0][e] + hyy * gt[1][e] + hyz * gt[2][e] + wl[e] * d3[1][e]);
+            u[2] += (double)(wv[e] * g1[2][e] + hxz * gt[0][e] + hyz * gt[1][e] + hzz * gt[2][e] + wl[e] * d3[2][e]);
+        }
+        // Bloch: the phase term, sum over outputs z of Im(conj(h_z) w_z) with the bracket w
+        double sph = 0.0;
+        if constexpr (BLOCH) sph = bloch_phase_sum<A, E, LAPTAB>(p, u0, g1, h2, lam, hv, hg, hl);
+        // sum over the lanes of the group (all lanes of the warp take part)
+        for (int off = L >> 1; off > 0; off >>= 1) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) u[i] += __shfl_xor_sync(kFullMask, u[i], off);
+            sph += __shfl_xor_sync(kFullMask, sph, off);
+        }
+        if (active && sub == 0) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double d = p.mg[3 * a] * u[0] + p.mg[3 * a + 1] * u[1] + p.mg[3 * a + 2] * u[2] -
+                                 p.kc[a] * sph;
+                atomicAdd(b.dpos + 3 * ip + a, d);
+            }
+        }
+    }
+}
+
 template <typename T, bool LAPTAB, bool BLOCH>
 __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs b)
 {
@@ -76,198 +274,119 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
     const long long total = p.n_pos * p.tiles;
     const long long warp = (long long)blockIdx.x * (kEvalThreads / 32) + (threadIdx.x >> 5);
     const long long wstride = (long long)gridDim.x * (kEvalThreads / 32);
-    const size_t rowb = (size_t)p.row_stride * sizeof(T);
-    const size_t colb = (size_t)p.col_stride * sizeof(T);
     const int n_orb = p.n_orb;
-
+    A* dc = static_cast<A*>(b.dcoef);
+    A* dl = static_cast<A*>(b.dcoef_lap);
+    const bool vec = b.vec_atomic != 0;
+    // global vector atomics into the canonical table layout [Nx][Ny][Nz][O]
+    auto scatter = [&](int ix, int iy, int iz, int l, int m, int n, int o0, const A* v, const A* vl) {
+        const size_t row = (((size_t)wrap1(ix + l - 1, p.nx) * p.ny + wrap1(iy + m - 1, p.ny)) * p.nz +
+                            wrap1(iz + n - 1, p.nz)) * n_orb + o0;
+        atomic_run<A, E>(dc + row, v, o0, n_orb, vec);
+        if (LAPTAB) atomic_run<A, E>(dl + row, vl, o0, n_orb, vec);
+    };
     for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) {
         const long long gid = w0 + (lane >> p.lanes_log2);
         const bool active = gid < total;
         const long long q = active ? gid / p.tiles : 0;
         const int tile = active ? (int)(gid - q * p.tiles) : 0;
         const long long ip = active ? order_index(p, q) : 0;   // through the cell order, if any
-        int ix, iy, iz;
-        A tx, ty, tz;
-        bool ok;
-        bwd_coords<A>(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
-        if (active && !ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+        bwd_position<T, LAPTAB, BLOCH>(b, ip, active, tile == 0, tile * L + sub, L, sub, gbase, scatter);
+    }
+}
 
-        A w[3][4], dw[3][4], d2w[3][4];
-        bspline_weights<A>(tx, w[0], dw[0], d2w[0]);
-        bspline_weights<A>(ty, w[1], dw[1], d2w[1]);
-        bspline_weights<A>(tz, w[2], dw[2], d2w[2]);
-        const A d3w[4] = {A(-1.5), A(4.5), A(-4.5), A(1.5)};
+// ---- coefficient adjoint aggregated per bin of cells (many positions, cell order) ----
+// With positions sorted into bins of 4 x 4 x 4 grid cells, the positions of one bin scatter into a
+// block of only 7 x 7 x 7 stencil points, each touched by many of them.  One thread block takes one
+// (bin, orbital slice): it sums the bin's contributions to those 343 rows of the slice in shared
+// memory (shared-memory atomics), then adds each row to the coefficient gradient with one vector
+// atomic per 16-byte chunk -- instead of one global atomic per position and stencil point.  The
+// position adjoint, which needs the table rows and far more registers, is left to the plain kernel
+// in a second launch over the same cell order.
+constexpr int kBinnedThreads = 512;
+constexpr int kBinSide = 7;                           // stencil points per axis of a 4-cell bin edge
+constexpr int kBinPoints = kBinSide * kBinSide * kBinSide;
 
-        const int chunk = tile * L + sub;
-        const int o0 = chunk * E;
-        // upstream weights of my orbitals (zero for inactive lanes and padding)
-        A wv[E], wl[E], gt[3][E];
-        A hv[E], hl[E], hg[3][E];   // Bloch: upstream of the bracket (phase term of dL/dr)
-        {
-            A wg[3][E];
-            const A* gvp = static_cast<const A*>(b.gv);
-            const A* ggp = static_cast<const A*>(b.gg);
-            const A* glp = static_cast<const A*>(b.gl);
-            const bool use = active && o0 < n_orb;
-            load_run<A>(use && gvp ? gvp + ip * n_orb + o0 : nullptr, wv, o0, n_orb, E);
-            load_run<A>(use && glp ? glp + ip * n_orb + o0 : nullptr, wl, o0, n_orb, E);
-            for (int a = 0; a < 3; ++a)
-                load_run<A>(use && ggp ? ggp + (ip * 3 + a) * n_orb + o0 : nullptr, wg[a], o0, n_orb, E);
-            if constexpr (BLOCH) bloch_upstream<A, E, LAPTAB>(p, p.pos + 3 * ip, wv, wg, wl, hv, hg, hl);
+template <bool LAPTAB> struct BinnedSlice {
+    static constexpr int S = LAPTAB ? 64 : 128;      // orbitals per slice: 343 x S x tables x 4 B of shared memory
+};
+
+template <typename T, bool LAPTAB>
+constexpr size_t binned_smem_bytes()
+{
+    return (size_t)kBinPoints * (LAPTAB ? 2 : 1) * BinnedSlice<LAPTAB>::S * sizeof(float);
+}
+
+struct BinnedArgs {
+    const int* bin_end;       // one past the last sorted position of every bin
+    int nb[3];                // bins per axis (bins of 4 cells per edge)
+    int n_bins, n_slices;
+};
+
+template <typename T, bool LAPTAB>
+__global__ void __launch_bounds__(kBinnedThreads, 1) bspline_bwd_binned_kernel(const BwdArgs b, const BinnedArgs g)
+{
+    using A = typename Traits<T>::A;                  // float (float and bfloat16 tables)
+    constexpr int E = Traits<T>::E;                   // orbitals per 16-byte chunk
+    constexpr int S = BinnedSlice<LAPTAB>::S;
+    constexpr int CH = S / E;                         // chunks of a slice = lanes per position
+    constexpr int GPW = 32 / CH;                      // positions per warp
+    constexpr int NT = LAPTAB ? 2 : 1;
+    constexpr int WARPS = kBinnedThreads / 32;
+    // acc[((point * NT + table) * E + e) * CH + chunk]: the CH lanes of a position hit consecutive words
+    extern __shared__ float acc[];
+    const EvalArgs& p = b.e;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sub = lane & (CH - 1), gbase = lane & ~(CH - 1), grp = lane / CH;
+    const int n_orb = p.n_orb;
+    const bool vec = b.vec_atomic != 0;
+    const int items = g.n_bins * g.n_slices;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int bin = item / g.n_slices, slice = item - bin * g.n_slices;
+        const int start = bin ? g.bin_end[bin - 1] : 0, end = g.bin_end[bin];
+        if (start >= end) continue;                   // the same for the whole block
+        const int bz = bin % g.nb[2], by = (bin / g.nb[2]) % g.nb[1], bx = bin / (g.nb[2] * g.nb[1]);
+        __syncthreads();                              // the previous item's flush has read acc
+        for (int i = threadIdx.x; i < kBinPoints * NT * E * CH; i += kBinnedThreads) acc[i] = 0.f;
+        __syncthreads();
+        auto scatter = [&](int ix, int iy, int iz, int l, int m, int n, int, const A* v, const A* vl) {
+            const int pt = ((ix - 4 * bx + l) * kBinSide + (iy - 4 * by + m)) * kBinSide + (iz - 4 * bz + n);
+            float* a0 = acc + (size_t)pt * NT * E * CH + sub;
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+            for (int e = 0; e < E; ++e) atomicAdd(a0 + e * CH, v[e]);
+            if (LAPTAB) {
 #pragma unroll
-                for (int e = 0; e < E; ++e)
-                    gt[i][e] = (A)p.mg[i] * wg[0][e] + (A)p.mg[3 + i] * wg[1][e] + (A)p.mg[6 + i] * wg[2][e];
+                for (int e = 0; e < E; ++e) atomicAdd(a0 + (E + e) * CH, vl[e]);
+            }
+        };
+        for (int q0 = start + warp * GPW; q0 < end; q0 += WARPS * GPW) {   // warp-uniform bound
+            const int q = q0 + grp;
+            const bool active = q < end;
+            const long long ip = active ? order_index(p, q) : order_index(p, start);
+            bwd_position<T, LAPTAB, false, decltype(scatter)&, false>(b, ip, active, slice == 0, slice * CH + sub, CH,
+                                                                     sub, gbase, scatter);
         }
-        const A ml0 = (A)p.ml[0], ml1 = (A)p.ml[1], ml2 = (A)p.ml[2];
-        const A ml3 = (A)p.ml[3], ml4 = (A)p.ml[4], ml5 = (A)p.ml[5];
-        int xs[4], ys[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            xs[j] = wrap1(ix + j - 1, p.nx);
-            ys[j] = wrap1(iy + j - 1, p.ny);
-        }
-
-        // ---- coefficient adjoint: scatter into 64 stencil rows ----
-        if (b.dcoef && active && o0 < n_orb) {
-            A* dc = static_cast<A*>(b.dcoef);
-            A* dl = static_cast<A*>(b.dcoef_lap);
-            const bool vec = b.vec_atomic != 0;
-            for (int l = 0; l < 4; ++l)
-                for (int m = 0; m < 4; ++m)
-                    for (int n = 0; n < 4; ++n) {
-                        const int z = wrap1(iz + n - 1, p.nz);
-                        const A B = w[0][l] * w[1][m] * w[2][n];
-                        const A Bx = dw[0][l] * w[1][m] * w[2][n];
-                        const A By = w[0][l] * dw[1][m] * w[2][n];
-                        const A Bz = w[0][l] * w[1][m] * dw[2][n];
-                        A lapB = 0;
-                        if (!LAPTAB)
-                            lapB = ml0 * d2w[0][l] * w[1][m] * w[2][n] + ml1 * w[0][l] * d2w[1][m] * w[2][n] +
-                                   ml2 * w[0][l] * w[1][m] * d2w[2][n] + ml3 * dw[0][l] * dw[1][m] * w[2][n] +
-                                   ml4 * dw[0][l] * w[1][m] * dw[2][n] + ml5 * w[0][l] * dw[1][m] * dw[2][n];
-                        A v[E], vl[E];
-#pragma unroll
-                        for (int e = 0; e < E; ++e) {
-                            v[e] = wv[e] * B + gt[0][e] * Bx + gt[1][e] * By + gt[2][e] * Bz;
-                            if (LAPTAB) vl[e] = wl[e] * B;
-                            else v[e] += wl[e] * lapB;
-                        }
-                        const size_t row = (((size_t)xs[l] * p.ny + ys[m]) * p.nz + z) * n_orb + o0;
-                        atomic_run<A, E>(dc + row, v, o0, n_orb, vec);
-                        if (LAPTAB) atomic_run<A, E>(dl + row, vl, o0, n_orb, vec);
-                    }
-        }
-
-        // ---- position adjoint ----
-        if (b.dpos) {
-            // reduced derivatives of my orbitals: gradient, Hessian, gradient of the Laplacian
-            A g1[3][E], h2[6][E], d3[3][E];
-            A u0[E], lam[E];   // Bloch: value of u and of the Laplacian table, for the phase term
+        __syncthreads();
+        // one vector atomic per 16-byte chunk of every touched row of the block
+        A* dc = static_cast<A*>(b.dcoef);
+        A* dl = static_cast<A*>(b.dcoef_lap);
+        for (int i = threadIdx.x; i < kBinPoints * NT * CH; i += kBinnedThreads) {
+            const int c = i % CH, t = (i / CH) % NT, pt = i / (CH * NT);
+            const int o0 = (slice * CH + c) * E;
+            if (o0 >= n_orb) continue;
+            const float* a0 = acc + ((size_t)pt * NT + t) * E * CH + c;
+            A v[E];
+            bool any = false;
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                for (int i = 0; i < 3; ++i) g1[i][e] = d3[i][e] = A(0);
-                for (int i = 0; i < 6; ++i) h2[i][e] = A(0);
-                u0[e] = lam[e] = A(0);
+                v[e] = a0[e * CH];
+                any = any || v[e] != 0.f;
             }
-            const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
-            const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb
-                                    : nullptr;
-            for (int l = 0; l < 4; ++l)
-                for (int m = 0; m < 4; ++m) {
-                    const size_t col = (size_t)(xs[l] * p.ny + ys[m]) * colb;
-                    A a[4][E], al[2][E];
-#pragma unroll
-                    for (int e = 0; e < E; ++e) a[0][e] = a[1][e] = a[2][e] = a[3][e] = al[0][e] = al[1][e] = A(0);
-#pragma unroll
-                    for (int n = 0; n < 4; ++n) {
-                        A c[E];
-                        unpack<T>(ldg_table(p, t0 + col + n * rowb), c);
-#pragma unroll
-                        for (int e = 0; e < E; ++e) {
-                            a[0][e] = fma(w[2][n], c[e], a[0][e]);
-                            a[1][e] = fma(dw[2][n], c[e], a[1][e]);
-                            a[2][e] = fma(d2w[2][n], c[e], a[2][e]);
-                            a[3][e] = fma(d3w[n], c[e], a[3][e]);
-                        }
-                        if (LAPTAB) {
-                            unpack<T>(ldg_table(p, t1 + col + n * rowb), c);
-#pragma unroll
-                            for (int e = 0; e < E; ++e) {
-                                al[0][e] = fma(w[2][n], c[e], al[0][e]);
-                                al[1][e] = fma(dw[2][n], c[e], al[1][e]);
-                            }
-                        }
-                    }
-                    const A bx = w[0][l], dbx = dw[0][l], d2bx = d2w[0][l], d3bx = d3w[l];
-                    const A by = w[1][m], dby = dw[1][m], d2by = d2w[1][m], d3by = d3w[m];
-                    // third-derivative weights contracted with the Laplacian metric
-                    const A x0 = ml0 * d3bx * by + ml1 * dbx * d2by + ml3 * d2bx * dby;
-                    const A x1 = ml4 * d2bx * by + ml5 * dbx * dby;
-                    const A x2 = ml2 * dbx * by;
-                    const A y0 = ml0 * d2bx * dby + ml1 * bx * d3by + ml3 * dbx * d2by;
-                    const A y1 = ml4 * dbx * dby + ml5 * bx * d2by;
-                    const A y2 = ml2 * bx * dby;
-                    const A z1 = ml0 * d2bx * by + ml1 * bx * d2by + ml3 * dbx * dby;
-                    const A z2 = ml4 * dbx * by + ml5 * bx * dby;
-                    const A z3 = ml2 * bx * by;
-                    if constexpr (BLOCH) {
-#pragma unroll
-                        for (int e = 0; e < E; ++e) {
-                            u0[e] += bx * by * a[0][e];
-                            if (LAPTAB) lam[e] += bx * by * al[0][e];
-                        }
-                    }
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        g1[0][e] += dbx * by * a[0][e];
-                        g1[1][e] += bx * dby * a[0][e];
-                        g1[2][e] += bx * by * a[1][e];
-                        h2[0][e] += d2bx * by * a[0][e];
-                        h2[1][e] += bx * d2by * a[0][e];
-                        h2[2][e] += bx * by * a[2][e];
-                        h2[3][e] += dbx * dby * a[0][e];
-                        h2[4][e] += dbx * by * a[1][e];
-                        h2[5][e] += bx * dby * a[1][e];
-                        if (LAPTAB) {
-                            d3[0][e] += dbx * by * al[0][e];
-                            d3[1][e] += bx * dby * al[0][e];
-                            d3[2][e] += bx * by * al[1][e];
-                        } else {
-                            d3[0][e] += x0 * a[0][e] + x1 * a[1][e] + x2 * a[2][e];
-                            d3[1][e] += y0 * a[0][e] + y1 * a[1][e] + y2 * a[2][e];
-                            d3[2][e] += z1 * a[1][e] + z2 * a[2][e] + z3 * a[3][e];
-                        }
-                    }
-                }
-            // u_i = wv g_i + sum_j H_ij g~_j + wl d3_i, summed over my orbitals (in FP64)
-            double u[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const A hxx = h2[0][e], hyy = h2[1][e], hzz = h2[2][e];
-                const A hxy = h2[3][e], hxz = h2[4][e], hyz = h2[5][e];
-                u[0] += (double)(wv[e] * g1[0][e] + hxx * gt[0][e] + hxy * gt[1][e] + hxz * gt[2][e] + wl[e] * d3[0][e]);
-                u[1] += (double)(wv[e] * g1[1][e] + hxy * gt[0][e] + hyy * gt[1][e] + hyz * gt[2][e] + wl[e] * d3[1][e]);
-                u[2] += (double)(wv[e] * g1[2][e] + hxz * gt[0][e] + hyz * gt[1][e] + hzz * gt[2][e] + wl[e] * d3[2][e]);
-            }
-            // Bloch: the phase term, sum over outputs z of Im(conj(h_z) w_z) with the bracket w
-            double sph = 0.0;
-            if constexpr (BLOCH) sph = bloch_phase_sum<A, E, LAPTAB>(p, u0, g1, h2, lam, hv, hg, hl);
-            // sum over the lanes of the group (all lanes of the warp take part)
-            for (int off = L >> 1; off > 0; off >>= 1) {
-#pragma unroll
-                for (int i = 0; i < 3; ++i) u[i] += __shfl_xor_sync(kFullMask, u[i], off);
-                sph += __shfl_xor_sync(kFullMask, sph, off);
-            }
-            if (active && sub == 0) {
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    const double d = p.mg[3 * a] * u[0] + p.mg[3 * a + 1] * u[1] + p.mg[3 * a + 2] * u[2] -
-                                     p.kc[a] * sph;
-                    atomicAdd(b.dpos + 3 * ip + a, d);
-                }
-            }
+            if (!any) continue;
+            const int lz = pt % kBinSide, ly = (pt / kBinSide) % kBinSide, lx = pt / (kBinSide * kBinSide);
+            const size_t row = (((size_t)wrap1(4 * bx - 1 + lx, p.nx) * p.ny + wrap1(4 * by - 1 + ly, p.ny)) * p.nz +
+                                wrap1(4 * bz - 1 + lz, p.nz)) * n_orb + o0;
+            atomic_run<A, E>((t ? dl : dc) + row, v, o0, n_orb, vec);
         }
     }
 }
@@ -289,6 +408,19 @@ int launch_one(const BwdArgs& a, cudaStream_t st)
     if (blocks < 1) blocks = 1;
     bspline_bwd_kernel<T, LAPTAB, BLOCH><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "bspline_bwd_kernel launch");
+}
+
+template <typename T, bool LAPTAB>
+int launch_binned(const BwdArgs& a, const BinnedArgs& g, cudaStream_t st)
+{
+    constexpr size_t smem = binned_smem_bytes<T, LAPTAB>();
+    cudaError_t e = cudaFuncSetAttribute(bspline_bwd_binned_kernel<T, LAPTAB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "binned adjoint shared memory");
+    const int items = g.n_bins * g.n_slices;
+    const int blocks = items < sm_count() ? items : sm_count();
+    bspline_bwd_binned_kernel<T, LAPTAB><<<blocks > 0 ? blocks : 1, kBinnedThreads, smem, st>>>(a, g);
+    return cuda_error(cudaGetLastError(), "bspline_bwd_binned_kernel launch");
 }
 
 template <typename T, bool LAPTAB>
@@ -787,10 +919,30 @@ int launch_bspline_backward(Handle* h, const double* pos, long long n_pos, const
     // FP64 reduction in the kernel
     if (use_cell_order(h, n_pos)) {
         Prepared pr;
+        const BinGeometry g = bin_geometry(h);
         const int rc = prepare_positions(h, pos, n_pos, true, &pr, st);
         if (rc != QMCSPL_OK) return rc;
         a.e.perm = pr.perm;
         a.e.rec = h->storage == QMCSPL_DF64 ? nullptr : pr.rec;
+        // float and bfloat16 tables of real orbitals with bins of 4 cells per edge: the coefficient
+        // adjoint summed per bin in shared memory
+        const bool edge4 = g.edge[0] == 4 && g.edge[1] == 4 && g.edge[2] == 4;
+        if (dcoef && edge4 && !h->bloch && (h->storage == QMCSPL_F32 || h->storage == QMCSPL_BF16)) {
+            BinnedArgs ba;
+            ba.bin_end = pr.bin_end;
+            for (int i = 0; i < 3; ++i) ba.nb[i] = g.nb[i];
+            ba.n_bins = g.n_bins;
+            const bool lt = h->separate_lap != 0;
+            const int S = lt ? BinnedSlice<true>::S : BinnedSlice<false>::S;
+            ba.n_slices = (h->n_orb_p + S - 1) / S;
+            int rc2;
+            if (h->storage == QMCSPL_F32)
+                rc2 = lt ? launch_binned<float, true>(a, ba, st) : launch_binned<float, false>(a, ba, st);
+            else
+                rc2 = lt ? launch_binned<__nv_bfloat16, true>(a, ba, st) : launch_binned<__nv_bfloat16, false>(a, ba, st);
+            if (rc2 != QMCSPL_OK || !dpos) return rc2;
+            a.dcoef = a.dcoef_lap = nullptr;   // the position adjoint alone, below
+        }
     }
     const bool lt = h->separate_lap != 0;
     switch (h->storage) {
