@@ -66,10 +66,9 @@ __device__ __forceinline__ void bwd_coords(const EvalArgs& p, long long ip, int 
 // 16-byte chunk `chunk` of every stored row, E orbitals from o0 = chunk E): the coefficient adjoint's
 // 64 stencil-point rows go to scatter(ix, iy, iz, l, m, n, o0, v, vl) (v for the value table, vl for
 // the Laplacian table), the position adjoint is summed over the group and added to dpos[ip] by lane
-// sub = 0 (POS = false leaves the position adjoint out).  first_part: this group's part is the one
-// that reports a non-finite position.  All 32 lanes of the warp must call it (the group reductions
-// shuffle).
-template <typename T, bool LAPTAB, bool BLOCH, typename Scatter, bool POS = true>
+// sub = 0.  first_part: this group's part is the one that reports a non-finite position.  All 32
+// lanes of the warp must call it (the group reductions shuffle).
+template <typename T, bool LAPTAB, bool BLOCH, typename Scatter>
 __device__ __forceinline__ void bwd_position(const BwdArgs& b, long long ip, bool active, bool first_part, int chunk,
                                              int L, int sub, int gbase, Scatter&& scatter)
 {
@@ -147,8 +146,8 @@ __device__ __forceinline__ void bwd_position(const BwdArgs& b, long long ip, boo
                 }
     }
 
-    // ---- position adjoint (POS = false: the caller computes it elsewhere) ----
-    if (POS && b.dpos) {
+    // ---- position adjoint ----
+    if (b.dpos) {
         // reduced derivatives of my orbitals: gradient, Hessian, gradient of the Laplacian
         A g1[3][E], h2[6][E], d3[3][E];
         A u0[E], lam[E];   // Bloch: value of u and of the Laplacian table, for the phase term
@@ -295,102 +294,6 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
     }
 }
 
-// ---- coefficient adjoint aggregated per bin of cells (many positions, cell order) ----
-// With positions sorted into bins of 4 x 4 x 4 grid cells, the positions of one bin scatter into a
-// block of only 7 x 7 x 7 stencil points, each touched by many of them.  One thread block takes one
-// (bin, orbital slice): it sums the bin's contributions to those 343 rows of the slice in shared
-// memory (shared-memory atomics), then adds each row to the coefficient gradient with one vector
-// atomic per 16-byte chunk -- instead of one global atomic per position and stencil point.  The
-// position adjoint, which needs the table rows and far more registers, is left to the plain kernel
-// in a second launch over the same cell order.
-constexpr int kBinnedThreads = 512;
-constexpr int kBinSide = 7;                           // stencil points per axis of a 4-cell bin edge
-constexpr int kBinPoints = kBinSide * kBinSide * kBinSide;
-
-template <bool LAPTAB> struct BinnedSlice {
-    static constexpr int S = LAPTAB ? 64 : 128;      // orbitals per slice: 343 x S x tables x 4 B of shared memory
-};
-
-template <typename T, bool LAPTAB>
-constexpr size_t binned_smem_bytes()
-{
-    return (size_t)kBinPoints * (LAPTAB ? 2 : 1) * BinnedSlice<LAPTAB>::S * sizeof(float);
-}
-
-struct BinnedArgs {
-    const int* bin_end;       // one past the last sorted position of every bin
-    int nb[3];                // bins per axis (bins of 4 cells per edge)
-    int n_bins, n_slices;
-};
-
-template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(kBinnedThreads, 1) bspline_bwd_binned_kernel(const BwdArgs b, const BinnedArgs g)
-{
-    using A = typename Traits<T>::A;                  // float (float and bfloat16 tables)
-    constexpr int E = Traits<T>::E;                   // orbitals per 16-byte chunk
-    constexpr int S = BinnedSlice<LAPTAB>::S;
-    constexpr int CH = S / E;                         // chunks of a slice = lanes per position
-    constexpr int GPW = 32 / CH;                      // positions per warp
-    constexpr int NT = LAPTAB ? 2 : 1;
-    constexpr int WARPS = kBinnedThreads / 32;
-    // acc[((point * NT + table) * E + e) * CH + chunk]: the CH lanes of a position hit consecutive words
-    extern __shared__ float acc[];
-    const EvalArgs& p = b.e;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int sub = lane & (CH - 1), gbase = lane & ~(CH - 1), grp = lane / CH;
-    const int n_orb = p.n_orb;
-    const bool vec = b.vec_atomic != 0;
-    const int items = g.n_bins * g.n_slices;
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
-        const int bin = item / g.n_slices, slice = item - bin * g.n_slices;
-        const int start = bin ? g.bin_end[bin - 1] : 0, end = g.bin_end[bin];
-        if (start >= end) continue;                   // the same for the whole block
-        const int bz = bin % g.nb[2], by = (bin / g.nb[2]) % g.nb[1], bx = bin / (g.nb[2] * g.nb[1]);
-        __syncthreads();                              // the previous item's flush has read acc
-        for (int i = threadIdx.x; i < kBinPoints * NT * E * CH; i += kBinnedThreads) acc[i] = 0.f;
-        __syncthreads();
-        auto scatter = [&](int ix, int iy, int iz, int l, int m, int n, int, const A* v, const A* vl) {
-            const int pt = ((ix - 4 * bx + l) * kBinSide + (iy - 4 * by + m)) * kBinSide + (iz - 4 * bz + n);
-            float* a0 = acc + (size_t)pt * NT * E * CH + sub;
-#pragma unroll
-            for (int e = 0; e < E; ++e) atomicAdd(a0 + e * CH, v[e]);
-            if (LAPTAB) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) atomicAdd(a0 + (E + e) * CH, vl[e]);
-            }
-        };
-        for (int q0 = start + warp * GPW; q0 < end; q0 += WARPS * GPW) {   // warp-uniform bound
-            const int q = q0 + grp;
-            const bool active = q < end;
-            const long long ip = active ? order_index(p, q) : order_index(p, start);
-            bwd_position<T, LAPTAB, false, decltype(scatter)&, false>(b, ip, active, slice == 0, slice * CH + sub, CH,
-                                                                     sub, gbase, scatter);
-        }
-        __syncthreads();
-        // one vector atomic per 16-byte chunk of every touched row of the block
-        A* dc = static_cast<A*>(b.dcoef);
-        A* dl = static_cast<A*>(b.dcoef_lap);
-        for (int i = threadIdx.x; i < kBinPoints * NT * CH; i += kBinnedThreads) {
-            const int c = i % CH, t = (i / CH) % NT, pt = i / (CH * NT);
-            const int o0 = (slice * CH + c) * E;
-            if (o0 >= n_orb) continue;
-            const float* a0 = acc + ((size_t)pt * NT + t) * E * CH + c;
-            A v[E];
-            bool any = false;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                v[e] = a0[e * CH];
-                any = any || v[e] != 0.f;
-            }
-            if (!any) continue;
-            const int lz = pt % kBinSide, ly = (pt / kBinSide) % kBinSide, lx = pt / (kBinSide * kBinSide);
-            const size_t row = (((size_t)wrap1(4 * bx - 1 + lx, p.nx) * p.ny + wrap1(4 * by - 1 + ly, p.ny)) * p.nz +
-                                wrap1(4 * bz - 1 + lz, p.nz)) * n_orb + o0;
-            atomic_run<A, E>((t ? dl : dc) + row, v, o0, n_orb, vec);
-        }
-    }
-}
-
 template <typename T, bool LAPTAB, bool BLOCH>
 int launch_one(const BwdArgs& a, cudaStream_t st)
 {
@@ -408,19 +311,6 @@ int launch_one(const BwdArgs& a, cudaStream_t st)
     if (blocks < 1) blocks = 1;
     bspline_bwd_kernel<T, LAPTAB, BLOCH><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "bspline_bwd_kernel launch");
-}
-
-template <typename T, bool LAPTAB>
-int launch_binned(const BwdArgs& a, const BinnedArgs& g, cudaStream_t st)
-{
-    constexpr size_t smem = binned_smem_bytes<T, LAPTAB>();
-    cudaError_t e = cudaFuncSetAttribute(bspline_bwd_binned_kernel<T, LAPTAB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "binned adjoint shared memory");
-    const int items = g.n_bins * g.n_slices;
-    const int blocks = items < sm_count() ? items : sm_count();
-    bspline_bwd_binned_kernel<T, LAPTAB><<<blocks > 0 ? blocks : 1, kBinnedThreads, smem, st>>>(a, g);
-    return cuda_error(cudaGetLastError(), "bspline_bwd_binned_kernel launch");
 }
 
 template <typename T, bool LAPTAB>
@@ -919,30 +809,10 @@ int launch_bspline_backward(Handle* h, const double* pos, long long n_pos, const
     // FP64 reduction in the kernel
     if (use_cell_order(h, n_pos)) {
         Prepared pr;
-        const BinGeometry g = bin_geometry(h);
         const int rc = prepare_positions(h, pos, n_pos, true, &pr, st);
         if (rc != QMCSPL_OK) return rc;
         a.e.perm = pr.perm;
         a.e.rec = h->storage == QMCSPL_DF64 ? nullptr : pr.rec;
-        // float and bfloat16 tables of real orbitals with bins of 4 cells per edge: the coefficient
-        // adjoint summed per bin in shared memory
-        const bool edge4 = g.edge[0] == 4 && g.edge[1] == 4 && g.edge[2] == 4;
-        if (dcoef && edge4 && !h->bloch && (h->storage == QMCSPL_F32 || h->storage == QMCSPL_BF16)) {
-            BinnedArgs ba;
-            ba.bin_end = pr.bin_end;
-            for (int i = 0; i < 3; ++i) ba.nb[i] = g.nb[i];
-            ba.n_bins = g.n_bins;
-            const bool lt = h->separate_lap != 0;
-            const int S = lt ? BinnedSlice<true>::S : BinnedSlice<false>::S;
-            ba.n_slices = (h->n_orb_p + S - 1) / S;
-            int rc2;
-            if (h->storage == QMCSPL_F32)
-                rc2 = lt ? launch_binned<float, true>(a, ba, st) : launch_binned<float, false>(a, ba, st);
-            else
-                rc2 = lt ? launch_binned<__nv_bfloat16, true>(a, ba, st) : launch_binned<__nv_bfloat16, false>(a, ba, st);
-            if (rc2 != QMCSPL_OK || !dpos) return rc2;
-            a.dcoef = a.dcoef_lap = nullptr;   // the position adjoint alone, below
-        }
     }
     const bool lt = h->separate_lap != 0;
     switch (h->storage) {
