@@ -796,6 +796,27 @@ def run_ours(args):
     e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e_value = replicas.job_throughput(evals_per_step * e2e_steps, ws, e2e_s)
     d2h = sum(o.numel() * o.element_size() for o in host_out)
+    # the same through qmcspl_eval_vgl_host_ex with bfloat16 outputs (converted on the device: half
+    # the bytes over the link); reported beside the full-precision e2e, which stays the headline
+    e2e_16 = None
+    if args.storage in ("f32", "bf16"):
+        host16 = tuple(torch.empty(o.shape, dtype=torch.bfloat16).pin_memory() for o in outs)
+        step16 = lambda: spl.eval_vgl_host(pos_h, out=host16, out_dtype=torch.bfloat16)
+        for _ in range(max(1, args.warmup)):
+            step16()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            step16()
+        torch.cuda.synchronize()
+        s16 = replicas.max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e_16 = {"value": replicas.job_throughput(evals_per_step * e2e_steps, ws, s16), "unit": UNIT,
+                  "out_dtype": "bf16", "h2d_bytes_per_step": int(pos_h.numel() * 8),
+                  "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in host16)),
+                  "api": "qmcspl_eval_vgl_host_ex (QMCSPL_OUT_BF16)"}
+        del host16
 
     # roofline of the dominant kernel, from its own CUDA-event launch times
     hbm, peak_kind = load_peaks()
@@ -896,6 +917,7 @@ def run_ours(args):
         "parity": parity,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pos_h.numel() * 8),
                 "d2h_bytes_per_step": int(d2h)},
+        "e2e_bf16_outputs": e2e_16,
         "gpu_launches": args.steps * kernels_per_step,
         "clocks": clocks,
         "setup_s": setup_s,

@@ -252,6 +252,34 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
                          void* grad_host, void* lap_host, void* stream);
 
 /*
+ * qmcspl_eval_vgl_host_ex -- qmcspl_eval_vgl_host with a choice of output type.
+ *
+ * Not in the paper.  The host-buffer evaluation moves every output across the host link, which
+ * bounds it (about 180 GB/s device-to-host, against the kernels' rate of some TB/s).  With a
+ * 16-bit output type each chunk of outputs is converted on the device (round to nearest even)
+ * before it is copied, halving the bytes:
+ *   opts->out_type  QMCSPL_OUT_NATIVE: the output dtype of qmcspl_eval_vgl (opts = NULL too);
+ *                   QMCSPL_OUT_BF16: bfloat16 (8 significant bits: relative rounding 2^-9, the
+ *                   float exponent range); QMCSPL_OUT_F16: IEEE half (11 significant bits:
+ *                   relative 2^-12, but magnitudes above 65504 become infinities)
+ *   val_host, grad_host, lap_host  host buffers in the usual layouts, 2-byte elements for the
+ *                   16-bit types; any may be NULL to skip that output (no conversion, no copy)
+ * The 16-bit types are for real orbitals with float or bfloat16 tables (else
+ * QMCSPL_ERR_UNSUPPORTED).  The device staging buffers for the converted chunks (2 x 5 x 65536 x
+ * n_orb x 2 bytes) are allocated on first use and kept by the handle.
+ */
+enum qmcspl_out_type {
+    QMCSPL_OUT_NATIVE = 0,
+    QMCSPL_OUT_BF16 = 1,
+    QMCSPL_OUT_F16 = 2
+};
+typedef struct {
+    int out_type;    /* enum qmcspl_out_type */
+} qmcspl_host_opts;
+int qmcspl_eval_vgl_host_ex(qmcspl_t h, const double* pos_host, long long n_pos, void* val_host,
+                            void* grad_host, void* lap_host, const qmcspl_host_opts* opts, void* stream);
+
+/*
  * qmcspl_eval_vgl_backward -- adjoint of qmcspl_eval_vgl (every method, degree and grid).
  *
  * Not in the paper: for a scalar loss L with upstream gradients gv = dL/dval,

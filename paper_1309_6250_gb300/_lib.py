@@ -69,6 +69,13 @@ class Info(ctypes.Structure):
                 ("block_threads", ctypes.c_int)]
 
 
+class HostOpts(ctypes.Structure):
+    _fields_ = [("out_type", ctypes.c_int)]
+
+
+OUT_TYPE = {"native": 0, "bf16": 1, "f16": 2}
+
+
 class BatchOpts(ctypes.Structure):
     _fields_ = [("launch", ctypes.c_int), ("threads", ctypes.c_int)]
 
@@ -96,6 +103,7 @@ PROTOTYPES = [
     ("qmcspl_info", I, [VP, ctypes.POINTER(Info)]),
     ("qmcspl_eval_vgl", I, [VP, VP, LL, VP, VP, VP, VP]),
     ("qmcspl_eval_vgl_host", I, [VP, VP, LL, VP, VP, VP, VP]),
+    ("qmcspl_eval_vgl_host_ex", I, [VP, VP, LL, VP, VP, VP, ctypes.POINTER(HostOpts), VP]),
     ("qmcspl_eval_vgl_noalloc", I, [VP, VP, LL, VP, VP, VP, VP]),
     ("qmcspl_eval_vgl_backward", I, [VP, VP, LL, VP, VP, VP, VP, VP, VP, VP]),
     ("qmcspl_eval_batched", I, [I, VP, VP, VP, VP, VP, VP, VP]),

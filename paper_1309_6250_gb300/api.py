@@ -214,20 +214,27 @@ class OrbitalSplines:
                 _ptr(grad if want[1] else None), _ptr(lap if want[2] else None), _stream_handle(stream)))
         return val, grad, lap
 
-    def eval_vgl_host(self, pos: torch.Tensor, out=None, stream=None):
-        """Same computation from and to host memory (pinned tensors for full speed)."""
+    def eval_vgl_host(self, pos: torch.Tensor, out=None, stream=None, out_dtype=None):
+        """Same computation from and to host memory (pinned tensors for full speed).  out_dtype
+        torch.bfloat16 or torch.float16 returns 16-bit outputs, converted on the device before the
+        copy (real orbitals, float or bfloat16 tables)."""
         if pos.device.type != "cpu" or pos.dtype != torch.float64:
             raise ValueError("positions must be a float64 CPU tensor")
         pos = pos.reshape(-1, 3).contiguous()
         n = pos.shape[0]
+        code = {None: "native", torch.bfloat16: "bf16", torch.float16: "f16"}[out_dtype]
+        dt = self.result_dtype if out_dtype is None else out_dtype
         if out is None:
-            out = (torch.empty((n, self.n_orb), dtype=self.result_dtype),
-                   torch.empty((n, 3, self.n_orb), dtype=self.result_dtype),
-                   torch.empty((n, self.n_orb), dtype=self.result_dtype))
+            out = (torch.empty((n, self.n_orb), dtype=dt), torch.empty((n, 3, self.n_orb), dtype=dt),
+                   torch.empty((n, self.n_orb), dtype=dt))
         val, grad, lap = out
+        for t in out:
+            if t is not None and t.dtype != dt:
+                raise ValueError("output tensors must be %s" % dt)
+        opts = _lib.HostOpts(_lib.OUT_TYPE[code])
         with torch.cuda.device(self.device):
-            _lib.check(self.lib.qmcspl_eval_vgl_host(self.handle, _ptr(pos), n, _ptr(val), _ptr(grad),
-                                                     _ptr(lap), _stream_handle(stream)))
+            _lib.check(self.lib.qmcspl_eval_vgl_host_ex(self.handle, _ptr(pos), n, _ptr(val), _ptr(grad),
+                                                        _ptr(lap), ctypes.byref(opts), _stream_handle(stream)))
         return val, grad, lap
 
     def backward(self, pos: torch.Tensor, gv=None, gg=None, gl=None, dcoef=None, dcoef_lap=None,

@@ -276,6 +276,7 @@ void free_handle(Handle* h)
     for (int b = 0; b < 2; ++b) {
         if (h->st_pos[b]) cudaFree(h->st_pos[b]);
         if (h->st_out[b]) cudaFree(h->st_out[b]);
+        if (h->st_half[b]) cudaFree(h->st_half[b]);
         if (h->st_stream[b]) cudaStreamDestroy(h->st_stream[b]);
     }
     if (h->st_ready)
@@ -560,18 +561,24 @@ int qmcspl_eval_vgl(qmcspl_t h, const double* pos, long long n_pos, void* val, v
     return eval_dispatch(h, pos, n_pos, val, grad, lap, static_cast<cudaStream_t>(stream));
 }
 
-int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, void* val_host,
-                         void* grad_host, void* lap_host, void* stream)
+int qmcspl_eval_vgl_host_ex(qmcspl_t h, const double* pos_host, long long n_pos, void* val_host,
+                            void* grad_host, void* lap_host, const qmcspl_host_opts* opts, void* stream)
 {
     g_err.clear();
     if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
     if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
+    const int out_type = opts ? opts->out_type : QMCSPL_OUT_NATIVE;
+    if (out_type < QMCSPL_OUT_NATIVE || out_type > QMCSPL_OUT_F16) return set_error(QMCSPL_ERR_ARG, "unknown out_type");
+    const bool reduced = out_type != QMCSPL_OUT_NATIVE;
+    if (reduced && (h->storage == QMCSPL_F64 || h->storage == QMCSPL_DF64 || h->bloch))
+        return set_error(QMCSPL_ERR_UNSUPPORTED, "16-bit outputs are for real orbitals with float or bfloat16 tables");
     if (n_pos == 0) return QMCSPL_OK;
     if (!pos_host) return set_error(QMCSPL_ERR_ARG, "pos_host is NULL");
     DeviceGuard dg(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const size_t ob = (h->storage == QMCSPL_F64 || h->storage == QMCSPL_DF64) ? 8 : 4;
-    const size_t row = (size_t)h->n_orb * ob;          // bytes of one output row
+    const size_t row = (size_t)h->n_orb * ob;          // bytes of one output row on the device
+    const size_t hrow = reduced ? (size_t)h->n_orb * 2 : row;   // ... and in the host buffers
     const long long cap = 1LL << 16;                   // positions per chunk
     cudaError_t e;
     if (!h->st_ready) {
@@ -610,6 +617,17 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
         h->st_cap = cap;
         h->st_ready = true;
     }
+    if (reduced && !h->st_half[0]) {
+        void* sh[2] = {nullptr, nullptr};
+        e = dev_malloc(&sh[0], (size_t)h->n_orb * 2 * 5 * h->st_cap);
+        if (e == cudaSuccess) e = dev_malloc(&sh[1], (size_t)h->n_orb * 2 * 5 * h->st_cap);
+        if (e != cudaSuccess) {
+            if (sh[0]) cudaFree(sh[0]);
+            return cuda_error(e, "16-bit output staging");
+        }
+        h->st_half[0] = sh[0];
+        h->st_half[1] = sh[1];
+    }
     cudaStream_t s_in = h->st_stream[0], s_out = h->st_stream[1];
     cudaEvent_t* ev_in = h->st_ev;          // positions of buffer b are on the device
     cudaEvent_t* ev_done = h->st_ev + 2;    // kernel writing buffer b finished
@@ -631,6 +649,10 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
         char* dv = static_cast<char*>(h->st_out[b]);
         char* dg_ = dv + row * n;
         char* dl = dg_ + row * 3 * n;
+        // what the host copies come from: the outputs, or their 16-bit conversion (same layout)
+        char* cv = reduced ? static_cast<char*>(h->st_half[b]) : dv;
+        char* cg = cv + hrow * n;
+        char* cl = cg + hrow * 3 * n;
         if ((e = cudaStreamWaitEvent(s_in, ev_free[b], 0)) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(h->st_pos[b], pos_host + 3 * p0, sizeof(double) * 3 * n,
                                  cudaMemcpyHostToDevice, s_in)) != cudaSuccess) break;
@@ -639,11 +661,18 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
         rc = eval_dispatch(h, h->st_pos[b], n, hv ? dv : nullptr, hg ? dg_ : nullptr,
                            hl ? dl : nullptr, st);
         if (rc != QMCSPL_OK) break;
+        if (reduced) {   // the requested outputs of the chunk, converted on the device
+            const bool bf = out_type == QMCSPL_OUT_BF16;
+            const long long m = n * (long long)h->n_orb;
+            if (hv && (rc = launch_convert_outputs(reinterpret_cast<const float*>(dv), cv, m, bf, st)) != QMCSPL_OK) break;
+            if (hg && (rc = launch_convert_outputs(reinterpret_cast<const float*>(dg_), cg, 3 * m, bf, st)) != QMCSPL_OK) break;
+            if (hl && (rc = launch_convert_outputs(reinterpret_cast<const float*>(dl), cl, m, bf, st)) != QMCSPL_OK) break;
+        }
         if ((e = cudaEventRecord(ev_done[b], st)) != cudaSuccess) break;
         if ((e = cudaStreamWaitEvent(s_out, ev_done[b], 0)) != cudaSuccess) break;
-        if (hv && (e = cudaMemcpyAsync(hv + row * p0, dv, row * n, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) break;
-        if (hg && (e = cudaMemcpyAsync(hg + row * 3 * p0, dg_, row * 3 * n, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) break;
-        if (hl && (e = cudaMemcpyAsync(hl + row * p0, dl, row * n, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) break;
+        if (hv && (e = cudaMemcpyAsync(hv + hrow * p0, cv, hrow * n, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) break;
+        if (hg && (e = cudaMemcpyAsync(hg + hrow * 3 * p0, cg, hrow * 3 * n, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) break;
+        if (hl && (e = cudaMemcpyAsync(hl + hrow * p0, cl, hrow * n, cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) break;
         if ((e = cudaEventRecord(ev_free[b], s_out)) != cudaSuccess) break;
     }
     if (rc == QMCSPL_OK && e != cudaSuccess) rc = cuda_error(e, "host staging pipeline");
@@ -652,6 +681,12 @@ int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, vo
     if (rc == QMCSPL_OK && e2 != cudaSuccess) rc = cuda_error(e2, "host staging copy-out");
     if (rc == QMCSPL_OK && e3 != cudaSuccess) rc = cuda_error(e3, "host staging kernels");
     return rc;
+}
+
+int qmcspl_eval_vgl_host(qmcspl_t h, const double* pos_host, long long n_pos, void* val_host,
+                         void* grad_host, void* lap_host, void* stream)
+{
+    return qmcspl_eval_vgl_host_ex(h, pos_host, n_pos, val_host, grad_host, lap_host, nullptr, stream);
 }
 
 int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, const void* gv,

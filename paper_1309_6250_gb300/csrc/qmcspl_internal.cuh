@@ -124,6 +124,7 @@ struct qmcspl_s {
     // staging for qmcspl_eval_vgl_host
     double* st_pos[2] = {nullptr, nullptr};
     void* st_out[2] = {nullptr, nullptr};
+    void* st_half[2] = {nullptr, nullptr};   // 16-bit copies of st_out (reduced output types)
     long long st_cap = 0;     // positions per staging chunk
     cudaStream_t st_stream[2] = {nullptr, nullptr};
     cudaEvent_t st_ev[6] = {};
@@ -235,6 +236,9 @@ int build_records(const Handle* h, const double* pos, long long n_pos, void* rec
 // handle's scratch: bins of the handle's bin_geometry, or of `geom` when given.
 int prepare_positions(Handle* h, const double* pos, long long n_pos, bool sort, Prepared* out,
                       cudaStream_t stream, const BinGeometry* geom = nullptr);
+
+// Convert n float outputs to bfloat16 (to_bf16) or IEEE half, round to nearest even.
+int launch_convert_outputs(const float* src, void* dst, long long n, bool to_bf16, cudaStream_t stream);
 
 // Allocate (once) and fill the device grid-point buffer of a non-uniform handle.
 int upload_grid_points(Handle* h, cudaStream_t stream);
