@@ -245,9 +245,14 @@ def cpu_baseline(w, storage, sep, budget_s=12.0, tables=None):
             "single_thread": {"value": n1 * n_orb / dt1, "sample": "%d positions" % n1, "seconds": dt1}}
 
 
-def workload_config(w, ws=1):
+def method_label(method="smooth", sep=True):
+    return "%s B-spline%s" % ({"smooth": "smoothing", "interp": "interpolating"}[method],
+                              " + separate Laplacian table" if sep else " (Laplacian from the Hessian)")
+
+
+def workload_config(w, ws=1, method="smooth", sep=True):
     """The benchmark's workload, the same dict for both arms (no launch details)."""
-    return {"workload": w.cell.name, "method": "smoothing B-spline + separate Laplacian table",
+    return {"workload": w.cell.name, "method": method_label(method, sep),
             "n_orb": int(w.coef.shape[0]), "grid": list(w.cell.grid), "walkers": w.cell.n_walkers,
             "electrons": w.cell.n_elec, "positions": int(w.pos.shape[0]),
             "l2": "table and outputs larger than L2 (no flush needed)",
@@ -488,7 +493,7 @@ def bench_backward_c3(args, dev, stream, l1=None):
     import torch
     import oracle
     from paper_1309_6250_gb300.api import OrbitalSplines
-    w = inputs.make_workload("c3")
+    w = inputs.make_workload("c3", n_pos=args.n_pos)
     n, o = w.pos.shape[0], w.coef.shape[0]
     spl = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth", storage="f32",
                          separate_lap=True, device=dev)
@@ -723,8 +728,8 @@ def run_ours(args):
 
     def build(storage, order):
         t0 = time.perf_counter()
-        s = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method="smooth",
-                           storage=storage, separate_lap=True, device=dev)
+        s = OrbitalSplines(w.lattice, w.cell.grid, w.miller, w.coef, method=args.method,
+                           storage=storage, separate_lap=bool(args.separate_lap), device=dev)
         s.set_order(order)
         return s, time.perf_counter() - t0
 
@@ -825,6 +830,8 @@ def run_ours(args):
     launch_s = prof["eval_ms"] * 1e-3 / max(1, prof["launches"])
     achieved = bpe * evals_per_step / launch_s / 1e9
     key = "%s/%s/%s/%s" % (kernel_name.replace("_kernel", ""), w.cell.name, args.storage, order_name)
+    if args.method != "smooth" or not args.separate_lap:
+        key += "/%s%s" % (args.method, "+lap" if args.separate_lap else "")
     traffic = load_traffic(key)
 
     variants, var_got = {}, {}
@@ -875,8 +882,9 @@ def run_ours(args):
     cpu = parity = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
-        tables = oracle.smoothing_tables(w.lattice, w.miller, w.coef, w.cell.grid, laplacian=True)
-        cpu = cpu_baseline(w, args.storage, True, tables=tables)
+        build_tables = oracle.smoothing_tables if args.method == "smooth" else oracle.interpolating_tables
+        tables = build_tables(w.lattice, w.miller, w.coef, w.cell.grid, laplacian=bool(args.separate_lap))
+        cpu = cpu_baseline(w, args.storage, bool(args.separate_lap), tables=tables)
         parity = {args.storage: bspline_precision(w, args.storage, par_sample, par_got, tables)}
         for st, got in var_got.items():
             parity[st] = bspline_precision(w, st, par_sample, got, tables)
@@ -907,7 +915,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": workload_config(w, ws),
+        "config": workload_config(w, ws, args.method, bool(args.separate_lap)),
         "launch": {"storage": args.storage,
                    "accumulate": {"f64": "f64", "df64": "double-float (f32 pairs)"}.get(args.storage, "f32"),
                    "order": order_name, "table_bytes": info["table_bytes"], "lanes": info["lanes"],
@@ -947,6 +955,10 @@ def main():
     ap.add_argument("--workload", default="c3")
     ap.add_argument("--storage", default="f32", choices=["f64", "df64", "f32", "bf16"])
     ap.add_argument("--order", default="auto", choices=["auto", "input", "cell", "pencil"])
+    ap.add_argument("--method", default="smooth", choices=["smooth", "interp"],
+                    help="B-spline of the main leg (profiling other kernels)")
+    ap.add_argument("--separate-lap", type=int, default=1, choices=[0, 1],
+                    help="0: the Laplacian of the spline itself (one table)")
     ap.add_argument("--ref-sample", type=int, default=2048)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
