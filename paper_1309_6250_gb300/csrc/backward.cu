@@ -294,6 +294,164 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
     }
 }
 
+// ---- coefficient adjoint gathered per bin of cells (many positions, cell order) ----
+// With positions sorted into bins of 4 x 4 x 4 grid cells, the positions of one bin touch only the
+// 7 x 7 x 7 stencil points around the bin, each one by many of them.  One thread block takes one
+// (bin, orbital slice): it stages a batch of the bin's positions in shared memory (local cell,
+// 1-D weights, the upstream weights of the slice with the chain rule transposed), then each warp
+// takes one of the 343 points at a time, finds the batch's positions whose stencil holds it (a
+// ballot), sums their contributions in registers -- lane c owning the c-th 16-byte chunk of the
+// slice -- and adds the point's row to the coefficient gradient with one vector atomic per chunk.
+// No shared-memory atomics, and one global reduction per point row and batch instead of one per
+// position and stencil point.  The table is not read; the position adjoint is left to the plain
+// kernel in a second launch over the same cell order.
+constexpr int kGatherThreads = 512;
+constexpr int kGatherBatch = 64;                      // positions staged at a time
+constexpr int kGatherSide = 7;                        // stencil points per axis of a 4-cell bin edge
+constexpr int kGatherPoints = kGatherSide * kGatherSide * kGatherSide;
+
+struct GatherArgs {
+    const int* bin_end;       // one past the last sorted position of every bin
+    int nb[3];                // bins per axis (4 cells per edge)
+    int n_bins, n_slices;
+};
+
+// staged data of one batch (dynamic shared memory)
+template <typename A>
+struct GatherStage {
+    static constexpr int EA = 16 / sizeof(A);        // upstream values per 16-byte chunk
+    A w[kGatherBatch][3][12];                        // per axis b[4], b'[4], b''[4]
+    int cell[kGatherBatch];                          // local cell cx | cy << 8 | cz << 16, -1: none
+    uint4 up[kGatherBatch][5][32];                   // wv, g~x, g~y, g~z, wl chunks of the slice
+};
+
+template <typename A, bool LAPTAB>
+__global__ void __launch_bounds__(kGatherThreads, 1) bspline_bwd_gather_kernel(const BwdArgs b, const GatherArgs g)
+{
+    constexpr int EA = GatherStage<A>::EA;
+    constexpr int WARPS = kGatherThreads / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GatherStage<A>& S = *reinterpret_cast<GatherStage<A>*>(smem_raw);
+    const EvalArgs& p = b.e;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n_orb = p.n_orb;
+    const bool vec = b.vec_atomic != 0;
+    A* dc = static_cast<A*>(b.dcoef);
+    A* dl = static_cast<A*>(b.dcoef_lap);
+    const A* gvp = static_cast<const A*>(b.gv);
+    const A* ggp = static_cast<const A*>(b.gg);
+    const A* glp = static_cast<const A*>(b.gl);
+    const A ml0 = (A)p.ml[0], ml1 = (A)p.ml[1], ml2 = (A)p.ml[2];
+    const A ml3 = (A)p.ml[3], ml4 = (A)p.ml[4], ml5 = (A)p.ml[5];
+    const int items = g.n_bins * g.n_slices;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int bin = item / g.n_slices, slice = item - bin * g.n_slices;
+        const int start = bin ? g.bin_end[bin - 1] : 0, end = g.bin_end[bin];
+        const int bz = bin % g.nb[2], by = (bin / g.nb[2]) % g.nb[1], bx = bin / (g.nb[2] * g.nb[1]);
+        const int o0 = (slice * 32 + lane) * EA;     // this lane's first orbital of the slice
+        for (int b0 = start; b0 < end; b0 += kGatherBatch) {
+            const int nbat = min(kGatherBatch, end - b0);
+            __syncthreads();                          // the previous batch is no longer read
+            // ---- stage: warp w takes positions w, w + WARPS, ... of the batch ----
+            for (int j = warp; j < nbat; j += WARPS) {
+                const long long ip = order_index(p, b0 + j);
+                int ix, iy, iz;
+                A t[3];
+                bool ok;
+                bwd_coords<A>(p, ip, 32, lane, 0, ix, iy, iz, t[0], t[1], t[2], ok);
+                if (lane < 3) {
+                    A wv[4], dw[4], d2w[4];
+                    bspline_weights<A>(t[lane], wv, dw, d2w);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        S.w[j][lane][k] = wv[k];
+                        S.w[j][lane][4 + k] = dw[k];
+                        S.w[j][lane][8 + k] = d2w[k];
+                    }
+                }
+                if (lane == 0)
+                    S.cell[j] = ok ? ((ix - 4 * bx) | ((iy - 4 * by) << 8) | ((iz - 4 * bz) << 16)) : -1;
+                A wv[EA], wl[EA], wg[3][EA], gt[3][EA];
+                const bool use = ok && o0 < n_orb;
+                load_run<A>(use && gvp ? gvp + ip * n_orb + o0 : nullptr, wv, o0, n_orb, EA);
+                load_run<A>(use && glp ? glp + ip * n_orb + o0 : nullptr, wl, o0, n_orb, EA);
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    load_run<A>(use && ggp ? ggp + (ip * 3 + a) * n_orb + o0 : nullptr, wg[a], o0, n_orb, EA);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int e = 0; e < EA; ++e)
+                        gt[i][e] = (A)p.mg[i] * wg[0][e] + (A)p.mg[3 + i] * wg[1][e] + (A)p.mg[6 + i] * wg[2][e];
+                auto put = [&](int q, const A* v) {
+                    A* d = reinterpret_cast<A*>(&S.up[j][q][lane]);
+#pragma unroll
+                    for (int e = 0; e < EA; ++e) d[e] = v[e];
+                };
+                put(0, wv);
+                put(1, gt[0]);
+                put(2, gt[1]);
+                put(3, gt[2]);
+                put(4, wl);
+            }
+            __syncthreads();
+            // ---- gather: warp w takes points w, w + WARPS, ... of the 7 x 7 x 7 block ----
+            for (int pt = warp; pt < kGatherPoints; pt += WARPS) {
+                const int lx = pt / (kGatherSide * kGatherSide), ly = (pt / kGatherSide) % kGatherSide,
+                          lz = pt % kGatherSide;
+                A acc[EA], accl[EA];
+#pragma unroll
+                for (int e = 0; e < EA; ++e) acc[e] = accl[e] = A(0);
+                bool any = false;
+                for (int jb = 0; jb < nbat; jb += 32) {
+                    const int jj = jb + lane;
+                    bool member = false;
+                    if (jj < nbat) {
+                        const int c = S.cell[jj];
+                        const int l = lx - (c & 255), m = ly - ((c >> 8) & 255), n = lz - (c >> 16);
+                        member = c >= 0 && (unsigned)l < 4u && (unsigned)m < 4u && (unsigned)n < 4u;
+                    }
+                    unsigned mask = __ballot_sync(kFullMask, member);
+                    any = any || mask != 0u;
+                    while (mask) {
+                        const int j = jb + __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const int c = S.cell[j];
+                        const int l = lx - (c & 255), m = ly - ((c >> 8) & 255), n = lz - (c >> 16);
+                        const A bxl = S.w[j][0][l], dbxl = S.w[j][0][4 + l];
+                        const A bym = S.w[j][1][m], dbym = S.w[j][1][4 + m];
+                        const A bzn = S.w[j][2][n], dbzn = S.w[j][2][4 + n];
+                        const A B = bxl * bym * bzn;
+                        const A Bx = dbxl * bym * bzn, By = bxl * dbym * bzn, Bz = bxl * bym * dbzn;
+                        A lapB = A(0);
+                        if (!LAPTAB) {
+                            const A d2bxl = S.w[j][0][8 + l], d2bym = S.w[j][1][8 + m], d2bzn = S.w[j][2][8 + n];
+                            lapB = ml0 * d2bxl * bym * bzn + ml1 * bxl * d2bym * bzn + ml2 * bxl * bym * d2bzn +
+                                   ml3 * dbxl * dbym * bzn + ml4 * dbxl * bym * dbzn + ml5 * bxl * dbym * dbzn;
+                        }
+                        const A* u0 = reinterpret_cast<const A*>(&S.up[j][0][lane]);
+                        const A* u1 = reinterpret_cast<const A*>(&S.up[j][1][lane]);
+                        const A* u2 = reinterpret_cast<const A*>(&S.up[j][2][lane]);
+                        const A* u3 = reinterpret_cast<const A*>(&S.up[j][3][lane]);
+                        const A* u4 = reinterpret_cast<const A*>(&S.up[j][4][lane]);
+#pragma unroll
+                        for (int e = 0; e < EA; ++e) {
+                            acc[e] += u0[e] * B + u1[e] * Bx + u2[e] * By + u3[e] * Bz;
+                            if (LAPTAB) accl[e] += u4[e] * B;
+                            else acc[e] += u4[e] * lapB;
+                        }
+                    }
+                }
+                if (!any || o0 >= n_orb) continue;    // no position of the batch touches the point
+                const size_t row = (((size_t)wrap1(4 * bx - 1 + lx, p.nx) * p.ny + wrap1(4 * by - 1 + ly, p.ny)) * p.nz +
+                                    wrap1(4 * bz - 1 + lz, p.nz)) * n_orb + o0;
+                atomic_run<A, EA>(dc + row, acc, o0, n_orb, vec);
+                if (LAPTAB) atomic_run<A, EA>(dl + row, accl, o0, n_orb, vec);
+            }
+        }
+    }
+}
+
 template <typename T, bool LAPTAB, bool BLOCH>
 int launch_one(const BwdArgs& a, cudaStream_t st)
 {
@@ -311,6 +469,19 @@ int launch_one(const BwdArgs& a, cudaStream_t st)
     if (blocks < 1) blocks = 1;
     bspline_bwd_kernel<T, LAPTAB, BLOCH><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "bspline_bwd_kernel launch");
+}
+
+template <typename A, bool LAPTAB>
+int launch_gather(const BwdArgs& a, const GatherArgs& g, cudaStream_t st)
+{
+    constexpr size_t smem = sizeof(GatherStage<A>);
+    cudaError_t e = cudaFuncSetAttribute(bspline_bwd_gather_kernel<A, LAPTAB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "gathered adjoint shared memory");
+    const int items = g.n_bins * g.n_slices;
+    const int blocks = items < sm_count() ? items : sm_count();
+    bspline_bwd_gather_kernel<A, LAPTAB><<<blocks > 0 ? blocks : 1, kGatherThreads, smem, st>>>(a, g);
+    return cuda_error(cudaGetLastError(), "bspline_bwd_gather_kernel launch");
 }
 
 template <typename T, bool LAPTAB>
@@ -809,10 +980,31 @@ int launch_bspline_backward(Handle* h, const double* pos, long long n_pos, const
     // FP64 reduction in the kernel
     if (use_cell_order(h, n_pos)) {
         Prepared pr;
+        const BinGeometry g = bin_geometry(h);
         const int rc = prepare_positions(h, pos, n_pos, true, &pr, st);
         if (rc != QMCSPL_OK) return rc;
         a.e.perm = pr.perm;
         a.e.rec = h->storage == QMCSPL_DF64 ? nullptr : pr.rec;
+        // real orbitals, bins of 4 cells per edge: the coefficient adjoint gathered per bin
+        // (bspline_bwd_gather_kernel), then the position adjoint alone in the plain kernel
+        const bool edge4 = g.edge[0] == 4 && g.edge[1] == 4 && g.edge[2] == 4;
+        if (dcoef && edge4 && !h->bloch && h->storage != QMCSPL_DF64) {
+            GatherArgs ga;
+            ga.bin_end = pr.bin_end;
+            for (int i = 0; i < 3; ++i) ga.nb[i] = g.nb[i];
+            ga.n_bins = g.n_bins;
+            const bool lt = h->separate_lap != 0;
+            int rc2;
+            if (h->storage == QMCSPL_F64) {
+                ga.n_slices = (h->n_orb + 64 - 1) / 64;      // 32 lanes x 2 doubles
+                rc2 = lt ? launch_gather<double, true>(a, ga, st) : launch_gather<double, false>(a, ga, st);
+            } else {
+                ga.n_slices = (h->n_orb + 128 - 1) / 128;    // 32 lanes x 4 floats
+                rc2 = lt ? launch_gather<float, true>(a, ga, st) : launch_gather<float, false>(a, ga, st);
+            }
+            if (rc2 != QMCSPL_OK || !dpos) return rc2;
+            a.dcoef = a.dcoef_lap = nullptr;   // the position adjoint alone, below
+        }
     }
     const bool lt = h->separate_lap != 0;
     switch (h->storage) {

@@ -559,3 +559,40 @@ def test_c3_mgo64_backward_full_size():
     assert e_pos < TOL["f32"]
     assert abs(lin - ref) <= 2e-6 * scale
     spl.close()
+
+
+@pytest.mark.parametrize("storage,n_orb,sep", [("f32", 150, True), ("f32", 40, False), ("f64", 70, True),
+                                               ("bf16", 24, True)])
+def test_gathered_adjoint_clustered_positions_and_ragged_slices(storage, n_orb, sep):
+    """The coefficient adjoint gathered per 4^3-cell bin: half the positions packed into a few
+    bins (hundreds per bin: several staged batches per bin), the rest spread out; orbital counts
+    that need two slices (150 float, 70 double) or leave a slice ragged; against input order
+    (the plain per-position kernel) and the oracle adjoint on the oracle's tables."""
+    dims = (12, 13, 14)
+    lat, mil, coef = inputs.random_cell(3300 + n_orb, dims, n_orb, 6.0, 5.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=sep)
+    rng = np.random.default_rng(3301)
+    spread = inputs.positions(lat, 6000, 3302, -1, 2)
+    # 6000 positions inside two bins' worth of cells (crystal coordinates in 0.05 .. 0.30)
+    cluster = rng.uniform(0.05, 0.30, size=(6000, 3)) @ lat.T
+    pos = np.ascontiguousarray(np.concatenate([spread, cluster])[rng.permutation(12000)])
+    n = pos.shape[0]
+    gv, gg, gl = inputs.upstream_weights(n, n_orb, 3303)
+    if storage != "f64":
+        gv, gg, gl = (x.astype(np.float32).astype(np.float64) for x in (gv, gg, gl))
+    out = {}
+    for order in ("input", "cell"):
+        spl.set_order(order)
+        out[order] = gpu_backward(spl, pos, gv, gg, gl)
+    tol = 1e-12 if storage == "f64" else TOL["f32"]
+    for a, b in zip(out["cell"], out["input"]):
+        if a is not None:
+            assert oracle.relative_error(a, b) < (1e-13 if storage == "f64" else 2e-6)
+    beta, blap = oracle_tables(lat, mil, coef, dims, "smooth", storage, sep)
+    rdc, rdcl, rdpos = oracle.bspline_adjoint(beta, lat, pos, gv, gg, gl, beta_lap=blap)
+    dc, dcl, dpos = out["cell"]
+    assert oracle.relative_error(dc, rdc) < tol
+    if sep:
+        assert oracle.relative_error(dcl, rdcl) < tol
+    assert oracle.relative_error(dpos, rdpos) < tol
+    spl.close()
