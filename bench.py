@@ -520,6 +520,15 @@ def bench_backward_c3(args, dev, stream, l1=None):
         if l1 is not None:
             r["roofline_l1"] = l1_roofline(bpe * n * o, t * 1e-3, l1)
         res["orders"][order] = r
+    # the two halves alone, in cell order: the coefficient adjoint (dL/dbeta only) and the
+    # position adjoint (dL/dr only)
+    spl.set_order("cell")
+    for name, kw in (("cell_coef_only", dict(dcoef=dc, dcoef_lap=dcl, want_dpos=False)),
+                     ("cell_pos_only", dict(want_dpos=True))):
+        step = lambda: spl.backward(pos, gv, gg, gl, **kw)
+        ms = time_steps(step, max(5, args.steps // 40), 2, torch, stream)
+        spl.sync()
+        res["orders"][name] = {"ms_per_step": sum(ms) / len(ms)}
     res["value"] = res["orders"]["cell"]["value"]
     res["ms_per_step"] = res["orders"]["cell"]["ms_per_step"]
     # dL/dr of sampled positions against the oracle adjoint (FP64, on the oracle's FP32-rounded tables)

@@ -66,9 +66,10 @@ __device__ __forceinline__ void bwd_coords(const EvalArgs& p, long long ip, int 
 // 16-byte chunk `chunk` of every stored row, E orbitals from o0 = chunk E): the coefficient adjoint's
 // 64 stencil-point rows go to scatter(ix, iy, iz, l, m, n, o0, v, vl) (v for the value table, vl for
 // the Laplacian table), the position adjoint is summed over the group and added to dpos[ip] by lane
-// sub = 0.  first_part: this group's part is the one that reports a non-finite position.  All 32
-// lanes of the warp must call it (the group reductions shuffle).
-template <typename T, bool LAPTAB, bool BLOCH, typename Scatter>
+// sub = 0.  COEF = false leaves the coefficient adjoint out (fewer registers for a pass that
+// computes dL/dr alone).  first_part: this group's part is the one that reports a non-finite
+// position.  All 32 lanes of the warp must call it (the group reductions shuffle).
+template <typename T, bool LAPTAB, bool BLOCH, bool COEF, typename Scatter>
 __device__ __forceinline__ void bwd_position(const BwdArgs& b, long long ip, bool active, bool first_part, int chunk,
                                              int L, int sub, int gbase, Scatter&& scatter)
 {
@@ -122,7 +123,7 @@ __device__ __forceinline__ void bwd_position(const BwdArgs& b, long long ip, boo
 
     // ---- coefficient adjoint: the weights of the 64 stencil points, handed to `scatter` ----
     // (a non-finite position adds nothing; its dL/dr comes out NaN)
-    if (b.dcoef && active && ok && o0 < n_orb) {
+    if (COEF && b.dcoef && active && ok && o0 < n_orb) {
         for (int l = 0; l < 4; ++l)
             for (int m = 0; m < 4; ++m)
                 for (int n = 0; n < 4; ++n) {
@@ -259,7 +260,7 @@ __device__ __forceinline__ void bwd_position(const BwdArgs& b, long long ip, boo
     }
 }
 
-template <typename T, bool LAPTAB, bool BLOCH>
+template <typename T, bool LAPTAB, bool BLOCH, bool COEF>
 __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs b)
 {
     using A = typename Traits<T>::A;
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
         const long long q = active ? gid / p.tiles : 0;
         const int tile = active ? (int)(gid - q * p.tiles) : 0;
         const long long ip = active ? order_index(p, q) : 0;   // through the cell order, if any
-        bwd_position<T, LAPTAB, BLOCH>(b, ip, active, tile == 0, tile * L + sub, L, sub, gbase, scatter);
+        bwd_position<T, LAPTAB, BLOCH, COEF>(b, ip, active, tile == 0, tile * L + sub, L, sub, gbase, scatter);
     }
 }
 
@@ -452,23 +453,30 @@ __global__ void __launch_bounds__(kGatherThreads, 1) bspline_bwd_gather_kernel(c
     }
 }
 
-template <typename T, bool LAPTAB, bool BLOCH>
-int launch_one(const BwdArgs& a, cudaStream_t st)
+template <typename T, bool LAPTAB, bool BLOCH, bool COEF>
+int launch_one_kind(const BwdArgs& a, cudaStream_t st)
 {
     const int gpw = 32 >> a.e.lanes_log2;
     const long long groups = a.e.n_pos * a.e.tiles;
     const long long warps = (groups + gpw - 1) / gpw;
     long long blocks = (warps + kEvalThreads / 32 - 1) / (kEvalThreads / 32);
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bspline_bwd_kernel<T, LAPTAB, BLOCH>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bspline_bwd_kernel<T, LAPTAB, BLOCH, COEF>,
                                                                   kEvalThreads, 0);
     if (e != cudaSuccess) return cuda_error(e, "occupancy query");
     if (per_sm < 1) per_sm = 1;
     const long long cap = (long long)sm_count() * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    bspline_bwd_kernel<T, LAPTAB, BLOCH><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
+    bspline_bwd_kernel<T, LAPTAB, BLOCH, COEF><<<(unsigned)blocks, kEvalThreads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "bspline_bwd_kernel launch");
+}
+
+// the coefficient adjoint and the position adjoint in one pass, or (no dcoef) the position alone
+template <typename T, bool LAPTAB, bool BLOCH>
+int launch_one(const BwdArgs& a, cudaStream_t st)
+{
+    return a.dcoef ? launch_one_kind<T, LAPTAB, BLOCH, true>(a, st) : launch_one_kind<T, LAPTAB, BLOCH, false>(a, st);
 }
 
 template <typename A, bool LAPTAB>

@@ -585,9 +585,11 @@ def test_gathered_adjoint_clustered_positions_and_ragged_slices(storage, n_orb, 
         spl.set_order(order)
         out[order] = gpu_backward(spl, pos, gv, gg, gl)
     tol = 1e-12 if storage == "f64" else TOL["f32"]
+    # two FP32 summation orders over up to hundreds of contributions per row: each within the
+    # 2e-6 tolerance of the oracle, so within twice that of each other
     for a, b in zip(out["cell"], out["input"]):
         if a is not None:
-            assert oracle.relative_error(a, b) < (1e-13 if storage == "f64" else 2e-6)
+            assert oracle.relative_error(a, b) < (1e-13 if storage == "f64" else 2 * TOL["f32"])
     beta, blap = oracle_tables(lat, mil, coef, dims, "smooth", storage, sep)
     rdc, rdcl, rdpos = oracle.bspline_adjoint(beta, lat, pos, gv, gg, gl, beta_lap=blap)
     dc, dcl, dpos = out["cell"]
