@@ -295,6 +295,230 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
     }
 }
 
+// ---- position adjoint alone, float tables of real orbitals ----
+// u_i = dL/dt_i = sum over the lane's orbitals of wv d_i phi + sum_j g~_j d_i d_j phi + wl d_i lap,
+// with phi = sum over the 4 x 4 stencil columns (l, m) of bx_l by_m (sum_n bz_n c_n).  The upstream
+// weights are contracted with each column's z sums first: with a_k = sum_n bz^(k)_n c_n (k-th
+// derivative weights in z) and al_k the same for the Laplacian table, the column adds
+//   u_x += bx' by (wv.a0 + wl.al0) + bx'' by (g~x.a0) + bx' by' (g~y.a0) + bx' by (g~z.a1)
+//   u_y += bx by' (wv.a0 + wl.al0) + bx' by' (g~x.a0) + bx by'' (g~y.a0) + bx by' (g~z.a1)
+//   u_z += bx by (wv.a1 + wl.al1) + bx' by (g~x.a1) + bx by' (g~y.a1) + bx by (g~z.a2)
+// (without the Laplacian table the wl terms are the metric-weighted third derivatives of the
+// Hessian Laplacian instead, from wl.a0 .. wl.a3), where "." sums over the lane's orbitals --
+// eight or twelve dot products per column instead of twelve running sums per orbital.  Packed
+// FP32 pairs, the next column's rows loaded while this one is contracted, as in the evaluation.
+template <typename T, bool LAPTAB>
+__device__ __forceinline__ void dpos_task_x2(const BwdArgs& b, long long w0, int lane)
+{
+    const EvalArgs& p = b.e;
+    constexpr int E = Traits<T>::E;
+    constexpr int NP = Pairs<T>::N;
+    constexpr int R = LAPTAB ? 8 : 4;
+    const int L = 1 << p.lanes_log2;
+    const int sub = lane & (L - 1);
+    const int gbase = lane & ~(L - 1);
+    const long long total = p.n_pos * p.tiles;
+    const size_t rowb = (size_t)p.row_stride * sizeof(T);
+    const size_t colb = (size_t)p.col_stride * sizeof(T);
+    const int n_orb = p.n_orb;
+
+    const long long gid = w0 + (lane >> p.lanes_log2);
+    const bool active = gid < total;
+    const long long q = active ? gid / p.tiles : 0;
+    const int tile = active ? (int)(gid - q * p.tiles) : 0;
+    const long long ip = active ? order_index(p, q) : q;
+    int ix, iy, iz;
+    float tx, ty, tz;
+    bool ok;
+    coords_float(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    if (active && !ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
+
+    float bx[4], dbx[4], d2bx[4], by[4], dby[4], d2by[4], bz[4], dbz[4], d2bz[4];
+    bspline_weights<float>(tx, bx, dbx, d2bx);
+    bspline_weights<float>(ty, by, dby, d2by);
+    bspline_weights<float>(tz, bz, dbz, d2bz);
+    const float d3w[4] = {-1.5f, 4.5f, -4.5f, 1.5f};
+    f32x2 bz2[4], dbz2[4], d2bz2[4], d3z2[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        bz2[n] = pack2(bz[n], bz[n]);
+        dbz2[n] = pack2(dbz[n], dbz[n]);
+        d2bz2[n] = pack2(d2bz[n], d2bz[n]);
+        if (!LAPTAB) d3z2[n] = pack2(d3w[n], d3w[n]);
+    }
+    // the lane's upstream weights, the gradient's through the transposed chain rule, as pairs
+    const int chunk = tile * L + sub;
+    const int o0 = chunk * E;
+    f32x2 WV[NP], WL[NP], GX[NP], GY[NP], GZ[NP];
+    {
+        float wv[E], wl[E], wg[3][E];
+        const float* gvp = static_cast<const float*>(b.gv);
+        const float* ggp = static_cast<const float*>(b.gg);
+        const float* glp = static_cast<const float*>(b.gl);
+        const bool use = active && o0 < n_orb;
+        load_run<float>(use && gvp ? gvp + ip * n_orb + o0 : nullptr, wv, o0, n_orb, E);
+        load_run<float>(use && glp ? glp + ip * n_orb + o0 : nullptr, wl, o0, n_orb, E);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            load_run<float>(use && ggp ? ggp + (ip * 3 + a) * n_orb + o0 : nullptr, wg[a], o0, n_orb, E);
+        float gt[3][E];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                gt[i][e] = (float)p.mg[i] * wg[0][e] + (float)p.mg[3 + i] * wg[1][e] + (float)p.mg[6 + i] * wg[2][e];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            WV[j] = pack2(wv[2 * j], wv[2 * j + 1]);
+            WL[j] = pack2(wl[2 * j], wl[2 * j + 1]);
+            GX[j] = pack2(gt[0][2 * j], gt[0][2 * j + 1]);
+            GY[j] = pack2(gt[1][2 * j], gt[1][2 * j + 1]);
+            GZ[j] = pack2(gt[2][2 * j], gt[2][2 * j + 1]);
+        }
+    }
+    const float ml0 = p.mlf[0], ml1 = p.mlf[1], ml2 = p.mlf[2];
+    const float ml3 = p.mlf[3], ml4 = p.mlf[4], ml5 = p.mlf[5];
+    int xs[4], ys[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        xs[j] = wrap1(ix + j - 1, p.nx);
+        ys[j] = wrap1(iy + j - 1, p.ny);
+    }
+    const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
+    const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb : nullptr;
+    auto hsum = [](f32x2 v) {
+        float lo, hi;
+        unpack2(v, lo, hi);
+        return lo + hi;
+    };
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    uint4 cur[R], nxt[R];
+    {
+        const size_t col = (size_t)(xs[0] * p.ny + ys[0]) * colb;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) cur[n] = ldg_table(p, t0 + col + n * rowb);
+        if (LAPTAB) {
+#pragma unroll
+            for (int n = 0; n < 4; ++n) cur[4 + n] = ldg_table(p, t1 + col + n * rowb);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 16; ++c) {
+        const int l = c >> 2, m = c & 3;
+        if (c < 15) {
+            const int ln = (c + 1) >> 2, mn = (c + 1) & 3;
+            const size_t col = (size_t)(xs[ln] * p.ny + ys[mn]) * colb;
+#pragma unroll
+            for (int n = 0; n < 4; ++n) nxt[n] = ldg_table(p, t0 + col + n * rowb);
+            if (LAPTAB) {
+#pragma unroll
+                for (int n = 0; n < 4; ++n) nxt[4 + n] = ldg_table(p, t1 + col + n * rowb);
+            }
+        }
+        // z sums of the column (value table; the Laplacian table's with the value weights)
+        f32x2 A0[NP], A1[NP], A2[NP], A3[NP], AL0[NP], AL1[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) A0[j] = A1[j] = A2[j] = A3[j] = AL0[j] = AL1[j] = 0ull;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+            f32x2 cv[NP];
+            Pairs<T>::get(cur[n], cv);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                A0[j] = ffma2(bz2[n], cv[j], A0[j]);
+                A1[j] = ffma2(dbz2[n], cv[j], A1[j]);
+                A2[j] = ffma2(d2bz2[n], cv[j], A2[j]);
+                if (!LAPTAB) A3[j] = ffma2(d3z2[n], cv[j], A3[j]);
+            }
+            if (LAPTAB) {
+                Pairs<T>::get(cur[4 + n], cv);
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    AL0[j] = ffma2(bz2[n], cv[j], AL0[j]);
+                    AL1[j] = ffma2(dbz2[n], cv[j], AL1[j]);
+                }
+            }
+        }
+        // the upstream against the z sums (pair accumulators, then the two halves added)
+        f32x2 s0 = 0ull, s1 = 0ull, x0p = 0ull, x1p = 0ull, y0p = 0ull, y1p = 0ull, z1p = 0ull, z2p = 0ull;
+        f32x2 w0p = 0ull, w1p = 0ull, w2p = 0ull, w3p = 0ull;
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            s0 = ffma2(WV[j], A0[j], s0);
+            s1 = ffma2(WV[j], A1[j], s1);
+            if (LAPTAB) {
+                s0 = ffma2(WL[j], AL0[j], s0);
+                s1 = ffma2(WL[j], AL1[j], s1);
+            } else {
+                w0p = ffma2(WL[j], A0[j], w0p);
+                w1p = ffma2(WL[j], A1[j], w1p);
+                w2p = ffma2(WL[j], A2[j], w2p);
+                w3p = ffma2(WL[j], A3[j], w3p);
+            }
+            x0p = ffma2(GX[j], A0[j], x0p);
+            x1p = ffma2(GX[j], A1[j], x1p);
+            y0p = ffma2(GY[j], A0[j], y0p);
+            y1p = ffma2(GY[j], A1[j], y1p);
+            z1p = ffma2(GZ[j], A1[j], z1p);
+            z2p = ffma2(GZ[j], A2[j], z2p);
+        }
+        const float S0 = hsum(s0), S1 = hsum(s1), X0 = hsum(x0p), X1 = hsum(x1p);
+        const float Y0 = hsum(y0p), Y1 = hsum(y1p), Z1 = hsum(z1p), Z2 = hsum(z2p);
+        const float bxl = bx[l], dbxl = dbx[l], d2bxl = d2bx[l];
+        const float bym = by[m], dbym = dby[m], d2bym = d2by[m];
+        ux += dbxl * bym * (S0 + Z1) + d2bxl * bym * X0 + dbxl * dbym * Y0;
+        uy += bxl * dbym * (S0 + Z1) + dbxl * dbym * X0 + bxl * d2bym * Y0;
+        uz += bxl * bym * (S1 + Z2) + dbxl * bym * X1 + bxl * dbym * Y1;
+        if (!LAPTAB) {
+            // d_i of the Hessian Laplacian: metric-weighted third derivatives
+            const float W0 = hsum(w0p), W1 = hsum(w1p), W2 = hsum(w2p), W3 = hsum(w3p);
+            const float d3bxl = d3w[l], d3bym = d3w[m];
+            const float xx0 = ml0 * d3bxl * bym + ml1 * dbxl * d2bym + ml3 * d2bxl * dbym;
+            const float xx1 = ml4 * d2bxl * bym + ml5 * dbxl * dbym;
+            const float xx2 = ml2 * dbxl * bym;
+            const float yy0 = ml0 * d2bxl * dbym + ml1 * bxl * d3bym + ml3 * dbxl * d2bym;
+            const float yy1 = ml4 * dbxl * dbym + ml5 * bxl * d2bym;
+            const float yy2 = ml2 * bxl * dbym;
+            const float zz1 = ml0 * d2bxl * bym + ml1 * bxl * d2bym + ml3 * dbxl * dbym;
+            const float zz2 = ml4 * dbxl * bym + ml5 * bxl * dbym;
+            const float zz3 = ml2 * bxl * bym;
+            ux += xx0 * W0 + xx1 * W1 + xx2 * W2;
+            uy += yy0 * W0 + yy1 * W1 + yy2 * W2;
+            uz += zz1 * W1 + zz2 * W2 + zz3 * W3;
+        }
+        if (c < 15) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) cur[k] = nxt[k];
+        }
+    }
+    // sum over the lanes of the group in FP64 (all lanes of the warp take part)
+    double u[3] = {(double)ux, (double)uy, (double)uz};
+    for (int off = L >> 1; off > 0; off >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) u[i] += __shfl_xor_sync(kFullMask, u[i], off);
+    }
+    if (active && sub == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            atomicAdd(b.dpos + 3 * ip + a, p.mg[3 * a] * u[0] + p.mg[3 * a + 1] * u[1] + p.mg[3 * a + 2] * u[2]);
+    }
+}
+
+constexpr int kDposThreads = 512;
+
+template <typename T, bool LAPTAB>
+__global__ void __launch_bounds__(kDposThreads, 1) bspline_dpos_kernel(const BwdArgs b)
+{
+    constexpr int WPB = kDposThreads / 32;
+    const EvalArgs& p = b.e;
+    const int lane = threadIdx.x & 31;
+    const int gpw = 32 >> p.lanes_log2;
+    const long long total = p.n_pos * p.tiles;
+    const long long warp = (long long)blockIdx.x * WPB + (threadIdx.x >> 5);
+    const long long wstride = (long long)gridDim.x * WPB;
+    for (long long w0 = warp * gpw; w0 < total; w0 += wstride * gpw) dpos_task_x2<T, LAPTAB>(b, w0, lane);
+}
+
 // ---- coefficient adjoint gathered per bin of cells (many positions, cell order) ----
 // With positions sorted into bins of 4 x 4 x 4 grid cells, the positions of one bin touch only the
 // 7 x 7 x 7 stencil points around the bin, each one by many of them.  One thread block takes one
@@ -477,6 +701,18 @@ template <typename T, bool LAPTAB, bool BLOCH>
 int launch_one(const BwdArgs& a, cudaStream_t st)
 {
     return a.dcoef ? launch_one_kind<T, LAPTAB, BLOCH, true>(a, st) : launch_one_kind<T, LAPTAB, BLOCH, false>(a, st);
+}
+
+template <typename T, bool LAPTAB>
+int launch_dpos(const BwdArgs& a, cudaStream_t st)
+{
+    const int gpw = 32 >> a.e.lanes_log2;
+    const long long warps = (a.e.n_pos * a.e.tiles + gpw - 1) / gpw;
+    long long blocks = (warps + kDposThreads / 32 - 1) / (kDposThreads / 32);
+    if (blocks > sm_count()) blocks = sm_count();
+    if (blocks < 1) blocks = 1;
+    bspline_dpos_kernel<T, LAPTAB><<<(unsigned)blocks, kDposThreads, 0, st>>>(a);
+    return cuda_error(cudaGetLastError(), "bspline_dpos_kernel launch");
 }
 
 template <typename A, bool LAPTAB>
@@ -1015,6 +1251,10 @@ int launch_bspline_backward(Handle* h, const double* pos, long long n_pos, const
         }
     }
     const bool lt = h->separate_lap != 0;
+    // the position adjoint alone, float tables of real orbitals: its own kernel (bfloat16 tables
+    // need four packed pairs per lane and would spill at 128 registers; they keep the general one)
+    if (!a.dcoef && !h->bloch && h->storage == QMCSPL_F32)
+        return lt ? launch_dpos<float, true>(a, st) : launch_dpos<float, false>(a, st);
     switch (h->storage) {
     case QMCSPL_F64: return lt ? launch_typed<double, true>(a, st) : launch_typed<double, false>(a, st);
     case QMCSPL_F32: return lt ? launch_typed<float, true>(a, st) : launch_typed<float, false>(a, st);
