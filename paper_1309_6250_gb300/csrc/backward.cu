@@ -491,13 +491,14 @@ __device__ __forceinline__ void dpos_task_x2(const BwdArgs& b, long long w0, int
             for (int k = 0; k < R; ++k) cur[k] = nxt[k];
         }
     }
-    // sum over the lanes of the group in FP64 (all lanes of the warp take part)
-    double u[3] = {(double)ux, (double)uy, (double)uz};
+    // sum over the lanes of the group (all lanes of the warp take part), FP32 pairwise
     for (int off = L >> 1; off > 0; off >>= 1) {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) u[i] += __shfl_xor_sync(kFullMask, u[i], off);
+        ux += __shfl_xor_sync(kFullMask, ux, off);
+        uy += __shfl_xor_sync(kFullMask, uy, off);
+        uz += __shfl_xor_sync(kFullMask, uz, off);
     }
     if (active && sub == 0) {
+        const double u[3] = {(double)ux, (double)uy, (double)uz};
 #pragma unroll
         for (int a = 0; a < 3; ++a)
             atomicAdd(b.dpos + 3 * ip + a, p.mg[3 * a] * u[0] + p.mg[3 * a + 1] * u[1] + p.mg[3 * a + 2] * u[2]);
