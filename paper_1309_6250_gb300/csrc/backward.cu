@@ -525,16 +525,75 @@ __global__ void __launch_bounds__(kDposThreads, 1) bspline_dpos_kernel(const Bwd
 // 7 x 7 x 7 stencil points around the bin, each one by many of them.  One thread block takes one
 // (bin, orbital slice): it stages a batch of the bin's positions in shared memory (local cell,
 // 1-D weights, the upstream weights of the slice with the chain rule transposed), then each warp
-// takes one of the 343 points at a time, finds the batch's positions whose stencil holds it (a
-// ballot), sums their contributions in registers -- lane c owning the c-th 16-byte chunk of the
-// slice -- and adds the point's row to the coefficient gradient with one vector atomic per chunk.
-// No shared-memory atomics, and one global reduction per point row and batch instead of one per
-// position and stencil point.  The table is not read; the position adjoint is left to the plain
-// kernel in a second launch over the same cell order.
+// takes one (x, y) column of the block at a time and keeps the column's 7 z points in registers,
+// lane c owning the c-th 16-byte chunk of the slice.  A position whose 4 x 4 (x, y) footprint holds
+// the column (a ballot) adds to 4 consecutive z points of it; the product of its tensor weights
+// factors as bz_n V + bz'_n W (+ bz''_n X for the Laplacian from the Hessian), with V, W, X sums of
+// upstream weights scaled by the column's x and y weights, so the upstream chunks and the x/y
+// products are read and formed once per column instead of once per point.  Each touched point
+// row then goes to the coefficient gradient with one vector atomic per chunk: no shared-memory
+// atomics, one global reduction per point row and batch.  The table is not read; the position
+// adjoint is left to a second launch over the same cell order.
 constexpr int kGatherThreads = 512;
 constexpr int kGatherBatch = 64;                      // positions staged at a time
 constexpr int kGatherSide = 7;                        // stencil points per axis of a 4-cell bin edge
-constexpr int kGatherPoints = kGatherSide * kGatherSide * kGatherSide;
+constexpr int kGatherColumns = kGatherSide * kGatherSide;
+
+// The (x, y) columns of the block in decreasing order of the cell columns of a bin that touch
+// them, (4 - |lx - 3|) (4 - |ly - 3|) of 16, so that warps taking columns in turn finish together.
+struct GatherColumnOrder {
+    unsigned char c[kGatherColumns];
+};
+constexpr int gather_column_weight(int col)
+{
+    const int dx = col / kGatherSide - 3, dy = col % kGatherSide - 3;
+    return (4 - (dx < 0 ? -dx : dx)) * (4 - (dy < 0 ? -dy : dy));
+}
+constexpr GatherColumnOrder make_gather_column_order()
+{
+    GatherColumnOrder r{};
+    int n = 0;
+    for (int w = 16; w >= 1; --w)
+        for (int col = 0; col < kGatherColumns; ++col)
+            if (gather_column_weight(col) == w) r.c[n++] = (unsigned char)col;
+    return r;
+}
+__constant__ GatherColumnOrder kGatherColumnOrder = make_gather_column_order();
+
+// four consecutive A values from 16-byte aligned shared memory
+template <typename A>
+__device__ __forceinline__ void lds4(const A* q, A (&v)[4])
+{
+    if constexpr (sizeof(A) == 4) {
+        const float4 r = *reinterpret_cast<const float4*>(q);
+        v[0] = r.x, v[1] = r.y, v[2] = r.z, v[3] = r.w;
+    } else {
+        const double2 r0 = reinterpret_cast<const double2*>(q)[0], r1 = reinterpret_cast<const double2*>(q)[1];
+        v[0] = r0.x, v[1] = r0.y, v[2] = r1.x, v[3] = r1.y;
+    }
+}
+
+// one position's share of a column: z points CZ .. CZ + 3 of the 7 (wz: bz[4], bz'[4], bz''[4])
+template <typename A, int EA, bool LAPTAB, int CZ>
+__device__ __forceinline__ void gather_column_add(A (&acc)[kGatherSide][EA], A (&accl)[kGatherSide][EA], const A* wz,
+                                                  const A (&V)[EA], const A (&W)[EA], const A (&X)[EA], const A (&L)[EA])
+{
+    A bz[4], dbz[4], d2bz[4];
+    lds4<A>(wz, bz);
+    lds4<A>(wz + 4, dbz);
+    if (!LAPTAB) lds4<A>(wz + 8, d2bz);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+#pragma unroll
+        for (int e = 0; e < EA; ++e) {
+            A t = acc[CZ + n][e] + bz[n] * V[e];
+            t = t + dbz[n] * W[e];
+            if (!LAPTAB) t = t + d2bz[n] * X[e];
+            acc[CZ + n][e] = t;
+            if (LAPTAB) accl[CZ + n][e] = accl[CZ + n][e] + bz[n] * L[e];
+        }
+    }
+}
 
 struct GatherArgs {
     const int* bin_end;       // one past the last sorted position of every bin
@@ -549,6 +608,7 @@ struct GatherStage {
     A w[kGatherBatch][3][12];                        // per axis b[4], b'[4], b''[4]
     int cell[kGatherBatch];                          // local cell cx | cy << 8 | cz << 16, -1: none
     uint4 up[kGatherBatch][5][32];                   // wv, g~x, g~y, g~z, wl chunks of the slice
+    int next;                                        // next column of the batch to take
 };
 
 template <typename A, bool LAPTAB>
@@ -578,6 +638,7 @@ __global__ void __launch_bounds__(kGatherThreads, 1) bspline_bwd_gather_kernel(c
         for (int b0 = start; b0 < end; b0 += kGatherBatch) {
             const int nbat = min(kGatherBatch, end - b0);
             __syncthreads();                          // the previous batch is no longer read
+            if (threadIdx.x == 0) S.next = 0;
             // ---- stage: warp w takes positions w, w + WARPS, ... of the batch ----
             for (int j = warp; j < nbat; j += WARPS) {
                 const long long ip = order_index(p, b0 + j);
@@ -621,58 +682,85 @@ __global__ void __launch_bounds__(kGatherThreads, 1) bspline_bwd_gather_kernel(c
                 put(4, wl);
             }
             __syncthreads();
-            // ---- gather: warp w takes points w, w + WARPS, ... of the 7 x 7 x 7 block ----
-            for (int pt = warp; pt < kGatherPoints; pt += WARPS) {
-                const int lx = pt / (kGatherSide * kGatherSide), ly = (pt / kGatherSide) % kGatherSide,
-                          lz = pt % kGatherSide;
-                A acc[EA], accl[EA];
+            // ---- gather: each warp takes (x, y) columns of the 7 x 7 x 7 block, heaviest first ----
+            for (;;) {
+                int k = 0;
+                if (lane == 0) k = atomicAdd(&S.next, 1);
+                k = __shfl_sync(kFullMask, k, 0);
+                if (k >= kGatherSide * kGatherSide) break;
+                const int col = kGatherColumnOrder.c[k];
+                const int lx = col / kGatherSide, ly = col - lx * kGatherSide;
+                A acc[kGatherSide][EA], accl[kGatherSide][EA];
 #pragma unroll
-                for (int e = 0; e < EA; ++e) acc[e] = accl[e] = A(0);
-                bool any = false;
+                for (int z = 0; z < kGatherSide; ++z)
+#pragma unroll
+                    for (int e = 0; e < EA; ++e) acc[z][e] = accl[z][e] = A(0);
+                unsigned zmask = 0u;                  // z points of the column some position touches
                 for (int jb = 0; jb < nbat; jb += 32) {
                     const int jj = jb + lane;
                     bool member = false;
                     if (jj < nbat) {
                         const int c = S.cell[jj];
-                        const int l = lx - (c & 255), m = ly - ((c >> 8) & 255), n = lz - (c >> 16);
-                        member = c >= 0 && (unsigned)l < 4u && (unsigned)m < 4u && (unsigned)n < 4u;
+                        member = c >= 0 && (unsigned)(lx - (c & 255)) < 4u && (unsigned)(ly - ((c >> 8) & 255)) < 4u &&
+                                 (c >> 16) < 4;
                     }
                     unsigned mask = __ballot_sync(kFullMask, member);
-                    any = any || mask != 0u;
                     while (mask) {
                         const int j = jb + __ffs(mask) - 1;
                         mask &= mask - 1;
                         const int c = S.cell[j];
-                        const int l = lx - (c & 255), m = ly - ((c >> 8) & 255), n = lz - (c >> 16);
+                        const int l = lx - (c & 255), m = ly - ((c >> 8) & 255), cz = c >> 16;
+                        zmask |= 15u << cz;
                         const A bxl = S.w[j][0][l], dbxl = S.w[j][0][4 + l];
                         const A bym = S.w[j][1][m], dbym = S.w[j][1][4 + m];
-                        const A bzn = S.w[j][2][n], dbzn = S.w[j][2][4 + n];
-                        const A B = bxl * bym * bzn;
-                        const A Bx = dbxl * bym * bzn, By = bxl * dbym * bzn, Bz = bxl * bym * dbzn;
-                        A lapB = A(0);
-                        if (!LAPTAB) {
-                            const A d2bxl = S.w[j][0][8 + l], d2bym = S.w[j][1][8 + m], d2bzn = S.w[j][2][8 + n];
-                            lapB = ml0 * d2bxl * bym * bzn + ml1 * bxl * d2bym * bzn + ml2 * bxl * bym * d2bzn +
-                                   ml3 * dbxl * dbym * bzn + ml4 * dbxl * bym * dbzn + ml5 * bxl * dbym * dbzn;
-                        }
+                        const A bxby = bxl * bym, dxby = dbxl * bym, bxdy = bxl * dbym;
+                        // the column's share of the position's rows: bz_n V + bz'_n W (+ bz''_n X),
+                        // Laplacian table bz_n L
+                        A V[EA], W[EA], X[EA], L[EA];
                         const A* u0 = reinterpret_cast<const A*>(&S.up[j][0][lane]);
                         const A* u1 = reinterpret_cast<const A*>(&S.up[j][1][lane]);
                         const A* u2 = reinterpret_cast<const A*>(&S.up[j][2][lane]);
                         const A* u3 = reinterpret_cast<const A*>(&S.up[j][3][lane]);
                         const A* u4 = reinterpret_cast<const A*>(&S.up[j][4][lane]);
+                        if (LAPTAB) {
 #pragma unroll
-                        for (int e = 0; e < EA; ++e) {
-                            acc[e] += u0[e] * B + u1[e] * Bx + u2[e] * By + u3[e] * Bz;
-                            if (LAPTAB) accl[e] += u4[e] * B;
-                            else acc[e] += u4[e] * lapB;
+                            for (int e = 0; e < EA; ++e) {
+                                V[e] = u0[e] * bxby + u1[e] * dxby + u2[e] * bxdy;
+                                W[e] = u3[e] * bxby;
+                                L[e] = u4[e] * bxby;
+                                X[e] = A(0);
+                            }
+                        } else {
+                            const A d2bxl = S.w[j][0][8 + l], d2bym = S.w[j][1][8 + m];
+                            const A al = ml0 * d2bxl * bym + ml1 * bxl * d2bym + ml3 * dbxl * dbym;
+                            const A be = ml2 * bxby;
+                            const A ga = ml4 * dxby + ml5 * bxdy;
+#pragma unroll
+                            for (int e = 0; e < EA; ++e) {
+                                V[e] = u0[e] * bxby + u1[e] * dxby + u2[e] * bxdy + u4[e] * al;
+                                W[e] = u3[e] * bxby + u4[e] * ga;
+                                X[e] = u4[e] * be;
+                                L[e] = A(0);
+                            }
+                        }
+                        const A* wz = &S.w[j][2][0];
+                        switch (cz) {
+                        case 0: gather_column_add<A, EA, LAPTAB, 0>(acc, accl, wz, V, W, X, L); break;
+                        case 1: gather_column_add<A, EA, LAPTAB, 1>(acc, accl, wz, V, W, X, L); break;
+                        case 2: gather_column_add<A, EA, LAPTAB, 2>(acc, accl, wz, V, W, X, L); break;
+                        default: gather_column_add<A, EA, LAPTAB, 3>(acc, accl, wz, V, W, X, L); break;
                         }
                     }
                 }
-                if (!any || o0 >= n_orb) continue;    // no position of the batch touches the point
-                const size_t row = (((size_t)wrap1(4 * bx - 1 + lx, p.nx) * p.ny + wrap1(4 * by - 1 + ly, p.ny)) * p.nz +
-                                    wrap1(4 * bz - 1 + lz, p.nz)) * n_orb + o0;
-                atomic_run<A, EA>(dc + row, acc, o0, n_orb, vec);
-                if (LAPTAB) atomic_run<A, EA>(dl + row, accl, o0, n_orb, vec);
+                if (o0 >= n_orb) continue;
+                const size_t col_row = ((size_t)wrap1(4 * bx - 1 + lx, p.nx) * p.ny + wrap1(4 * by - 1 + ly, p.ny)) * p.nz;
+#pragma unroll
+                for (int z = 0; z < kGatherSide; ++z) {
+                    if (!(zmask & (1u << z))) continue;
+                    const size_t row = (col_row + wrap1(4 * bz - 1 + z, p.nz)) * n_orb + o0;
+                    atomic_run<A, EA>(dc + row, acc[z], o0, n_orb, vec);
+                    if (LAPTAB) atomic_run<A, EA>(dl + row, accl[z], o0, n_orb, vec);
+                }
             }
         }
     }
