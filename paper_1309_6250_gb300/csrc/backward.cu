@@ -306,7 +306,11 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
 // (without the Laplacian table the wl terms are the metric-weighted third derivatives of the
 // Hessian Laplacian instead, from wl.a0 .. wl.a3), where "." sums over the lane's orbitals --
 // eight or twelve dot products per column instead of twelve running sums per orbital.  Packed
-// FP32 pairs, the next column's rows loaded while this one is contracted, as in the evaluation.
+// FP32 pairs.  The rows of the next two columns are in flight while one is contracted (the
+// first two issued before the upstream weights are read): with 16 warps per SM one column
+// ahead left the kernel waiting on its loads (4.2 ms against 2.2 ms on 524,288 positions x 128
+// orbitals).
+constexpr int kDposDepth = 2;
 template <typename T, bool LAPTAB>
 __device__ __forceinline__ void dpos_task_x2(const BwdArgs& b, long long w0, int lane)
 {
@@ -346,9 +350,40 @@ __device__ __forceinline__ void dpos_task_x2(const BwdArgs& b, long long w0, int
         d2bz2[n] = pack2(d2bz[n], d2bz[n]);
         if (!LAPTAB) d3z2[n] = pack2(d3w[n], d3w[n]);
     }
-    // the lane's upstream weights, the gradient's through the transposed chain rule, as pairs
     const int chunk = tile * L + sub;
     const int o0 = chunk * E;
+    const float ml0 = p.mlf[0], ml1 = p.mlf[1], ml2 = p.mlf[2];
+    const float ml3 = p.mlf[3], ml4 = p.mlf[4], ml5 = p.mlf[5];
+    int xs[4], ys[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        xs[j] = wrap1(ix + j - 1, p.nx);
+        ys[j] = wrap1(iy + j - 1, p.ny);
+    }
+    const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
+    const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb : nullptr;
+    auto hsum = [](f32x2 v) {
+        float lo, hi;
+        unpack2(v, lo, hi);
+        return lo + hi;
+    };
+    float ux = 0.f, uy = 0.f, uz = 0.f;
+    // a ring of D + 1 columns of rows: column c + D is loaded while column c is contracted
+    constexpr int D = kDposDepth;
+    uint4 ring[D + 1][R];
+    auto load_column = [&](int c, uint4 (&dst)[R]) {
+        const size_t col = (size_t)(xs[c >> 2] * p.ny + ys[c & 3]) * colb;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) dst[n] = ldg_table(p, t0 + col + n * rowb);
+        if (LAPTAB) {
+#pragma unroll
+            for (int n = 0; n < 4; ++n) dst[4 + n] = ldg_table(p, t1 + col + n * rowb);
+        }
+    };
+#pragma unroll
+    for (int c = 0; c < D; ++c) load_column(c, ring[c]);
+    // the lane's upstream weights (loaded while the first column's rows are in flight), the
+    // gradient's through the transposed chain rule, as pairs
     f32x2 WV[NP], WL[NP], GX[NP], GY[NP], GZ[NP];
     {
         float wv[E], wl[E], wg[3][E];
@@ -376,45 +411,11 @@ __device__ __forceinline__ void dpos_task_x2(const BwdArgs& b, long long w0, int
             GZ[j] = pack2(gt[2][2 * j], gt[2][2 * j + 1]);
         }
     }
-    const float ml0 = p.mlf[0], ml1 = p.mlf[1], ml2 = p.mlf[2];
-    const float ml3 = p.mlf[3], ml4 = p.mlf[4], ml5 = p.mlf[5];
-    int xs[4], ys[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        xs[j] = wrap1(ix + j - 1, p.nx);
-        ys[j] = wrap1(iy + j - 1, p.ny);
-    }
-    const char* t0 = static_cast<const char*>(p.tab[0]) + (size_t)chunk * 16 + (size_t)iz * rowb;
-    const char* t1 = LAPTAB ? static_cast<const char*>(p.tab[1]) + (size_t)chunk * 16 + (size_t)iz * rowb : nullptr;
-    auto hsum = [](f32x2 v) {
-        float lo, hi;
-        unpack2(v, lo, hi);
-        return lo + hi;
-    };
-    float ux = 0.f, uy = 0.f, uz = 0.f;
-    uint4 cur[R], nxt[R];
-    {
-        const size_t col = (size_t)(xs[0] * p.ny + ys[0]) * colb;
-#pragma unroll
-        for (int n = 0; n < 4; ++n) cur[n] = ldg_table(p, t0 + col + n * rowb);
-        if (LAPTAB) {
-#pragma unroll
-            for (int n = 0; n < 4; ++n) cur[4 + n] = ldg_table(p, t1 + col + n * rowb);
-        }
-    }
 #pragma unroll
     for (int c = 0; c < 16; ++c) {
         const int l = c >> 2, m = c & 3;
-        if (c < 15) {
-            const int ln = (c + 1) >> 2, mn = (c + 1) & 3;
-            const size_t col = (size_t)(xs[ln] * p.ny + ys[mn]) * colb;
-#pragma unroll
-            for (int n = 0; n < 4; ++n) nxt[n] = ldg_table(p, t0 + col + n * rowb);
-            if (LAPTAB) {
-#pragma unroll
-                for (int n = 0; n < 4; ++n) nxt[4 + n] = ldg_table(p, t1 + col + n * rowb);
-            }
-        }
+        if (c + D < 16) load_column(c + D, ring[(c + D) % (D + 1)]);
+        const uint4 (&cur)[R] = ring[c % (D + 1)];
         // z sums of the column (value table; the Laplacian table's with the value weights)
         f32x2 A0[NP], A1[NP], A2[NP], A3[NP], AL0[NP], AL1[NP];
 #pragma unroll
@@ -485,10 +486,6 @@ __device__ __forceinline__ void dpos_task_x2(const BwdArgs& b, long long w0, int
             ux += xx0 * W0 + xx1 * W1 + xx2 * W2;
             uy += yy0 * W0 + yy1 * W1 + yy2 * W2;
             uz += zz1 * W1 + zz2 * W2 + zz3 * W3;
-        }
-        if (c < 15) {
-#pragma unroll
-            for (int k = 0; k < R; ++k) cur[k] = nxt[k];
         }
     }
     // sum over the lanes of the group (all lanes of the warp take part), FP32 pairwise
