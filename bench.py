@@ -520,15 +520,30 @@ def bench_backward_c3(args, dev, stream, l1=None):
         if l1 is not None:
             r["roofline_l1"] = l1_roofline(bpe * n * o, t * 1e-3, l1)
         res["orders"][order] = r
-    # the two halves alone, in cell order: the coefficient adjoint (dL/dbeta only) and the
-    # position adjoint (dL/dr only)
+    # the two passes alone, in cell order: the coefficient adjoint (dL/dbeta only, gathered per
+    # bin of cells) and the position adjoint (dL/dr only).  The first is held to its compulsory
+    # DRAM bytes (both dbeta tables read and written once, the upstream weights and positions
+    # read once) against the HBM copy rate, the second to its gathered bytes (64 rows of both
+    # tables, the upstream weights and the position per orbital-evaluation) against the L1 rate.
+    hbm, hbm_kind = load_peaks()
+    coef_bytes = 2 * 2 * dc.numel() * 4 + n * o * 5 * 4 + n * 24
+    pos_bpe = 2 * 64 * 4 + 5 * 4 + 48.0 / o
     spl.set_order("cell")
     for name, kw in (("cell_coef_only", dict(dcoef=dc, dcoef_lap=dcl, want_dpos=False)),
                      ("cell_pos_only", dict(want_dpos=True))):
         step = lambda: spl.backward(pos, gv, gg, gl, **kw)
         ms = time_steps(step, max(5, args.steps // 40), 2, torch, stream)
         spl.sync()
-        res["orders"][name] = {"ms_per_step": sum(ms) / len(ms)}
+        t = sum(ms) / len(ms)
+        r = {"ms_per_step": t}
+        if name == "cell_coef_only":
+            a = coef_bytes / (t * 1e-3) / 1e9
+            r["roofline_hbm"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                                 "compulsory_bytes": coef_bytes, "peak_kind": hbm_kind}
+        elif l1 is not None:
+            r["bytes_per_eval"] = pos_bpe
+            r["roofline_l1"] = l1_roofline(pos_bpe * n * o, t * 1e-3, l1)
+        res["orders"][name] = r
     res["value"] = res["orders"]["cell"]["value"]
     res["ms_per_step"] = res["orders"]["cell"]["ms_per_step"]
     # dL/dr of sampled positions against the oracle adjoint (FP64, on the oracle's FP32-rounded tables)
