@@ -95,12 +95,13 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.t = None
+        self.first = threading.Event()
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return
@@ -110,6 +111,12 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.first.set()
+
+    def wait_first(self, timeout=5.0):
+        """Block until nvidia-smi has printed its first sample (it takes a while to start)."""
+        if self.proc is not None:
+            self.first.wait(timeout)
 
     def stop(self):
         if self.proc is None:
@@ -791,8 +798,18 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    sampler.wait_first()
     ms = time_steps(step, args.steps, 0, torch, stream)
+    # a short timed region holds few samples: keep the same step running, untimed, for another
+    # half second before the sampler stops
+    t_tail = time.perf_counter()
+    while time.perf_counter() - t_tail < 0.5:
+        for _ in range(8):
+            step()
+        torch.cuda.synchronize()
     clocks = sampler.stop()
+    if clocks is not None:
+        clocks["window"] = "timed region + 0.5 s of the same step, untimed"
     spl.sync()
     # the evaluation kernel's own launch time, from the library's CUDA events (eager calls)
     spl.profile(True)
@@ -808,41 +825,33 @@ def run_ours(args):
     par_got = [t[par_idx].double().cpu().numpy() for t in outs]
     value = replicas.job_throughput(evals_per_step * args.steps, ws, total_ms * 1e-3)
 
-    # end to end through the host-buffer entry point: pinned positions in, outputs back
+    # end to end through the host-buffer entry point: pinned positions in, outputs back; the same
+    # through qmcspl_eval_vgl_host_ex with bfloat16 outputs (converted on the device: half the
+    # bytes over the link) is reported beside the full-precision e2e, which stays the headline
     pos_h = torch.from_numpy(w.pos).pin_memory()
-    host_out = tuple(torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs)
-    e2e_step = lambda: spl.eval_vgl_host(pos_h, out=host_out)
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
     e2e_steps = max(3, args.steps // 4)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize()
-    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, dist, dev)
-    e2e_value = replicas.job_throughput(evals_per_step * e2e_steps, ws, e2e_s)
-    d2h = sum(o.numel() * o.element_size() for o in host_out)
-    # the same through qmcspl_eval_vgl_host_ex with bfloat16 outputs (converted on the device: half
-    # the bytes over the link); reported beside the full-precision e2e, which stays the headline
-    e2e_16 = None
-    if args.storage in ("f32", "bf16"):
-        host16 = tuple(torch.empty(o.shape, dtype=torch.bfloat16).pin_memory() for o in outs)
-        step16 = lambda: spl.eval_vgl_host(pos_h, out=host16, out_dtype=torch.bfloat16)
+
+    def time_e2e(fn):
         for _ in range(max(1, args.warmup)):
-            step16()
+            fn()
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            step16()
+            fn()
         torch.cuda.synchronize()
-        s16 = replicas.max_over_ranks(time.perf_counter() - t0, dist, dev)
-        e2e_16 = {"value": replicas.job_throughput(evals_per_step * e2e_steps, ws, s16), "unit": UNIT,
-                  "out_dtype": "bf16", "h2d_bytes_per_step": int(pos_h.numel() * 8),
+        return replicas.job_throughput(evals_per_step * e2e_steps, ws,
+                                       replicas.max_over_ranks(time.perf_counter() - t0, dist, dev))
+
+    host_out = tuple(torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs)
+    e2e_value = time_e2e(lambda: spl.eval_vgl_host(pos_h, out=host_out))
+    d2h = sum(o.numel() * o.element_size() for o in host_out)
+    e2e_16 = None
+    if args.storage in ("f32", "bf16"):
+        host16 = tuple(torch.empty(o.shape, dtype=torch.bfloat16).pin_memory() for o in outs)
+        e2e_16 = {"value": time_e2e(lambda: spl.eval_vgl_host(pos_h, out=host16, out_dtype=torch.bfloat16)),
+                  "unit": UNIT, "out_dtype": "bf16", "h2d_bytes_per_step": int(pos_h.numel() * 8),
                   "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in host16)),
                   "api": "qmcspl_eval_vgl_host_ex (QMCSPL_OUT_BF16)"}
         del host16
@@ -948,7 +957,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "parity": parity,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pos_h.numel() * 8),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h), "api": "qmcspl_eval_vgl_host"},
         "e2e_bf16_outputs": e2e_16,
         "gpu_launches": args.steps * kernels_per_step,
         "clocks": clocks,
