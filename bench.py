@@ -495,7 +495,7 @@ def bench_backward_c3(args, dev, stream, l1=None):
     """Both adjoints (coefficient scatter and position gradient) at the many-walker scale: the
     MgO-like 64-atom cell, 128 orbitals on 96^3, FP32 smoothing + Laplacian tables, 2048 walkers x
     256 electrons, upstream weights N(0,1) on value, gradient and Laplacian (seeded device
-    generator).  Cell order (the default from 8192 positions) against input order; dL/dr of every
+    generator).  Cell order (the automatic choice here) against input order; dL/dr of every
     512th position against the oracle adjoint."""
     import torch
     import oracle
@@ -784,11 +784,12 @@ def run_ours(args):
         torch.cuda.synchronize()
         step = graph.replay    # replays on the current (timed) stream
     # the path qmcspl_eval_vgl takes (the rule of qmcspl_set_order)
-    staged = bool(info["staged"]) and args.order == "pencil"
-    cell_order = staged or args.order in ("cell", "pencil") or (args.order == "auto" and n_pos >= 8192)
-    order_name = "pencil" if staged else ("cell" if cell_order else "input")
+    order_name = spl.resolved_order(n_pos)     # the library's rule (qmcspl_get_order)
+    staged = order_name == "pencil"
     kernel_name = "bspline_vgl_staged_kernel" if staged else "bspline_vgl_kernel"
-    kernels_per_step = 4 if cell_order else 1     # records/bins, scan, place + evaluation
+    # sorted: records/bins, scan, place + evaluation; input order: a records pass from 8192
+    # positions on (Bloch handles: always, for the phases) + evaluation
+    kernels_per_step = 4 if order_name != "input" else (2 if n_pos >= 8192 or info["bloch"] else 1)
 
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     for _ in range(args.warmup):

@@ -434,8 +434,12 @@ int qmcspl_set_table(qmcspl_t h, int table, const void* src, int src_dtype, void
  * BF16 orbitals); other handles, the batched call and qmcspl_eval_vgl_noalloc take cell
  * order instead.  On GB300 cell order is the faster of the two for every workload measured,
  * so pencil order is never chosen automatically.
- *   mode  QMCSPL_ORDER_AUTO (default: cell order for 8192 positions or more),
- *         QMCSPL_ORDER_INPUT, QMCSPL_ORDER_CELL or QMCSPL_ORDER_PENCIL
+ *   mode  QMCSPL_ORDER_AUTO (default: cell order from 8192 positions on when the tables are
+ *         larger than the L2 cache; for tables that fit in L2, once the positions per bin of
+ *         4 x 4 x 4 cells reach 8, 32 or 192 for tables filling more than 60 %, more than 30 %
+ *         or at most 30 % of L2 -- below that the table is gathered from L2 in input order
+ *         about as fast, without the sort), QMCSPL_ORDER_INPUT, QMCSPL_ORDER_CELL or
+ *         QMCSPL_ORDER_PENCIL
  * A staged evaluation whose pipeline stalls for about a second (a fault of this library,
  * not of the input) gives up; qmcspl_sync then returns QMCSPL_ERR_TIMEOUT.
  */
@@ -446,6 +450,15 @@ enum qmcspl_order {
     QMCSPL_ORDER_PENCIL = 3
 };
 int qmcspl_set_order(qmcspl_t h, int mode);
+
+/*
+ * qmcspl_get_order -- the order in which qmcspl_eval_vgl (and the backward pass) would visit
+ * n_pos positions: QMCSPL_ORDER_INPUT, QMCSPL_ORDER_CELL or QMCSPL_ORDER_PENCIL, with
+ * QMCSPL_ORDER_AUTO resolved.  Not in the paper.
+ *   order  host int receiving the order
+ * QMCSPL_ERR_ARG for a NULL handle or order or n_pos < 0.  No device work.
+ */
+int qmcspl_get_order(qmcspl_t h, long long n_pos, int* order);
 
 /*
  * qmcspl_eval_vgl_noalloc -- qmcspl_eval_vgl in cell order, allocating nothing.

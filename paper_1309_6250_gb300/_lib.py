@@ -112,6 +112,7 @@ PROTOTYPES = [
     ("qmcspl_get_table", I, [VP, I, VP, VP]),
     ("qmcspl_set_table", I, [VP, I, VP, I, VP]),
     ("qmcspl_set_order", I, [VP, I]),
+    ("qmcspl_get_order", I, [VP, LL, ctypes.POINTER(I)]),
     ("qmcspl_profile", I, [VP, I]),
     ("qmcspl_profile_read", I, [VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_longlong)]),

@@ -171,6 +171,13 @@ class OrbitalSplines:
                 "pencil": _lib.ORDER_PENCIL}[mode]
         _lib.check(self.lib.qmcspl_set_order(self.handle, code))
 
+    def resolved_order(self, n_pos: int) -> str:
+        """The order eval_vgl takes for n_pos positions ('input', 'cell' or 'pencil'), with 'auto'
+        resolved by the library's rule."""
+        o = ctypes.c_int(0)
+        _lib.check(self.lib.qmcspl_get_order(self.handle, int(n_pos), ctypes.byref(o)))
+        return {_lib.ORDER_INPUT: "input", _lib.ORDER_CELL: "cell", _lib.ORDER_PENCIL: "pencil"}[o.value]
+
     def profile(self, enable: bool = True) -> None:
         """Start (and clear) or stop CUDA-event timing of this handle's kernels."""
         _lib.check(self.lib.qmcspl_profile(self.handle, int(bool(enable))))

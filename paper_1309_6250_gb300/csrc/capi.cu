@@ -81,6 +81,19 @@ int sm_count()
     return cached[dev];
 }
 
+long long l2_cache_bytes()
+{
+    static long long cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 128LL << 20;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrL2CacheSize, dev);
+        cached[dev] = n > 0 ? n : (128LL << 20);
+    }
+    return cached[dev];
+}
+
 void fill_eval_args(const Handle* h, EvalArgs* a)
 {
     std::memset(a, 0, sizeof(*a));
@@ -891,6 +904,20 @@ int qmcspl_set_order(qmcspl_t h, int mode)
     if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
     if (mode < QMCSPL_ORDER_AUTO || mode > QMCSPL_ORDER_PENCIL) return set_error(QMCSPL_ERR_ARG, "unknown order mode");
     h->order_mode = mode;
+    return QMCSPL_OK;
+}
+
+int qmcspl_get_order(qmcspl_t h, long long n_pos, int* order)
+{
+    g_err.clear();
+    if (!h) return set_error(QMCSPL_ERR_ARG, "NULL handle");
+    if (!order) return set_error(QMCSPL_ERR_ARG, "order is NULL");
+    if (n_pos < 0) return set_error(QMCSPL_ERR_ARG, "n_pos < 0");
+    DeviceGuard dg(h->device);
+    BinGeometry g;
+    StagedArgs sa;
+    if (n_pos > 0 && use_staged(h, n_pos) && staged_plan(h, n_pos, &g, &sa)) *order = QMCSPL_ORDER_PENCIL;
+    else *order = n_pos > 0 && use_cell_order(h, n_pos) ? QMCSPL_ORDER_CELL : QMCSPL_ORDER_INPUT;
     return QMCSPL_OK;
 }
 

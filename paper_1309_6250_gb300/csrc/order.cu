@@ -232,6 +232,14 @@ BinGeometry bin_geometry(const Handle* h)
     }
 }
 
+// QMCSPL_ORDER_AUTO.  Cell order costs three short kernels (bin counts, scan, placement) and pays
+// back through the L1 reuse of stencil rows among neighbouring positions.  A table larger than L2
+// is re-read from HBM in input order, and sorting wins from 8192 positions on.  A table that fits
+// in L2 is gathered from there in input order too, so sorting pays only once enough positions
+// share each bin of cells -- the fewer, the more of L2 the table takes.  Break-even points
+// measured on GB300 (FP32 tables with the Laplacian table, 16 to 128 orbitals, 48^3 to 96^3
+// grids): about 170 positions per 4^3-cell bin for a table filling 11% of L2, 25 to 30 at 45 to
+// 50%, 7 at 75%; tables of 400 MB and more (3 to 7 times L2) were faster sorted from 8192.
 bool use_cell_order(const Handle* h, long long n_pos)
 {
     if (n_pos >= (1LL << 31) - 1) return false;
@@ -239,7 +247,13 @@ bool use_cell_order(const Handle* h, long long n_pos)
     case QMCSPL_ORDER_INPUT: return false;
     case QMCSPL_ORDER_CELL:
     case QMCSPL_ORDER_PENCIL: return true;   // pencil order where staged evaluation does not apply
-    default: return n_pos >= 8192;
+    default: {
+        if (n_pos < 8192) return false;
+        const double share = (double)h->table_elems * h->elem_bytes * h->n_tables / (double)l2_cache_bytes();
+        if (share > 1.0) return true;
+        const double per_bin = (double)n_pos / bin_geometry(h).n_bins;
+        return per_bin >= (share > 0.6 ? 8.0 : share > 0.3 ? 32.0 : 192.0);
+    }
     }
 }
 

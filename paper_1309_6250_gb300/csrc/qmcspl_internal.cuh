@@ -248,5 +248,6 @@ void fill_eval_args(const Handle* h, EvalArgs* a);
 
 // number of SMs of the current device (cached)
 int sm_count();
+long long l2_cache_bytes();   // L2 size of the current device
 
 }  // namespace qmcspl

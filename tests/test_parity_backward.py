@@ -498,7 +498,7 @@ def test_general_backward_nonfinite_position_and_empty_call():
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
 def test_cell_ordered_backward_matches_input_order_and_oracle(storage):
     """32,768 positions on the Si-like 8-atom cell (16 orbitals, 48^3, smoothing + Laplacian
-    table): the cell-ordered adjoint (the default from 8192 positions) against input order and
+    table): the cell-ordered adjoint against input order and
     against the oracle adjoint on the oracle's tables rounded as stored."""
     w = inputs.make_workload("c2")
     dims = w.cell.grid
