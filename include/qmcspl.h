@@ -324,7 +324,8 @@ int qmcspl_eval_vgl_backward(qmcspl_t h, const double* pos, long long n_pos, con
  * storage type, the same separate_lap setting and the same bloch setting (k points may
  * differ per cell).
  *   n_cells   1..QMCSPL_MAX_BATCH
- *   h         host array of n_cells handles
+ *   h         host array of n_cells distinct handles (a cell's visiting order is kept in its
+ *             handle's scratch, so a handle given twice is refused with QMCSPL_ERR_ARG)
  *   pos, val, grad, lap   host arrays of n_cells DEVICE pointers (layouts as above;
  *             val/grad/lap entries may be NULL)
  *   n_pos     host array of n_cells position counts

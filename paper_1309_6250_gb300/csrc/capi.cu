@@ -750,6 +750,10 @@ int qmcspl_eval_batched_ex(int n_cells, const qmcspl_t* hs, const double* const*
     }
     if (threads == 640 && hs[0]->storage != QMCSPL_F32 && hs[0]->storage != QMCSPL_BF16)
         return set_error(QMCSPL_ERR_UNSUPPORTED, "640-thread blocks are for float and bfloat16 tables");
+    // each cell's order lives in its handle's scratch: a handle twice would overwrite its own
+    for (int c = 0; c < n_cells; ++c)
+        for (int d = 0; d < c; ++d)
+            if (hs[d] == hs[c]) return set_error(QMCSPL_ERR_ARG, "a handle appears twice in the batch");
     DeviceGuard dg(hs[0]->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Prepared prs[QMCSPL_MAX_BATCH];

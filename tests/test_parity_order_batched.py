@@ -244,3 +244,30 @@ def test_launch_plans_and_block_shapes_give_the_same_bits(storage):
         with pytest.raises(_lib.QmcsplError) as ei:
             eval_batched(spls, pos, plan={"launch": "single", "threads": 640})
         assert ei.value.code == _lib.ERR_UNSUPPORTED
+
+
+
+def test_batched_refuses_a_handle_twice():
+    """Each cell's visiting order lives in its handle's scratch, so a handle may appear only once
+    in a batch; cells of 8192 positions or more (records, and the sort for the first and last)
+    give the bytes of per-cell eval_vgl."""
+    from paper_1309_6250_gb300 import _lib
+    from paper_1309_6250_gb300.api import eval_batched
+    spec = (((16, 16, 16), 8, 40_000), ((20, 18, 16), 24, 9_000), ((12, 12, 12), 5, 20_000))
+    spls, pos = [], []
+    for i, (dims, n_orb, n) in enumerate(spec):
+        lat, mil, coef = inputs.random_cell(2450 + i, dims, n_orb, 6.0, 5.0, NONORTHO)
+        spls.append(splines(lat, dims, mil, coef, method="smooth", storage="f32", separate_lap=True))
+        pos.append(torch.from_numpy(inputs.positions(lat, n, 2460 + i, -1, 2)).to(dev()))
+    assert [s.resolved_order(p.shape[0]) for s, p in zip(spls, pos)] == ["cell", "input", "cell"]
+    ref = [s.eval_vgl(p) for s, p in zip(spls, pos)]
+    got = eval_batched(spls, pos)
+    torch.cuda.synchronize()
+    for a, b in zip(got, ref):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)
+    with pytest.raises(_lib.QmcsplError) as ei:
+        eval_batched([spls[0], spls[1], spls[0]], [pos[0], pos[1], pos[0]])
+    assert ei.value.code == _lib.ERR_ARG
+    for s in spls:
+        s.close()
