@@ -848,6 +848,19 @@ def run_ours(args):
     host_out = tuple(torch.empty(o.shape, dtype=o.dtype).pin_memory() for o in outs)
     e2e_value = time_e2e(lambda: spl.eval_vgl_host(pos_h, out=host_out))
     d2h = sum(o.numel() * o.element_size() for o in host_out)
+    # the link's own rate for the same bytes: device outputs copied into the pinned host tensors
+    # (cudaMemcpyAsync on one stream), the bound of the end-to-end number
+    def copy_out():
+        for h_, o_ in zip(host_out, outs):
+            h_.copy_(o_, non_blocking=True)
+    copy_out()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        copy_out()
+    torch.cuda.synchronize()
+    link_gbs = 3 * d2h / (time.perf_counter() - t0) / 1e9
+    e2e_gbs = d2h * e2e_value / evals_per_step / 1e9 / ws
     e2e_16 = None
     if args.storage in ("f32", "bf16"):
         host16 = tuple(torch.empty(o.shape, dtype=torch.bfloat16).pin_memory() for o in outs)
@@ -958,7 +971,10 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "parity": parity,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(pos_h.numel() * 8),
-                "d2h_bytes_per_step": int(d2h), "api": "qmcspl_eval_vgl_host"},
+                "d2h_bytes_per_step": int(d2h), "api": "qmcspl_eval_vgl_host",
+                "link": {"bound": "d2h", "achieved": e2e_gbs, "peak": link_gbs, "unit": "GB/s",
+                         "frac": e2e_gbs / link_gbs,
+                         "peak_kind": "measured in this run: the same output bytes copied device to pinned host"}},
         "e2e_bf16_outputs": e2e_16,
         "gpu_launches": args.steps * kernels_per_step,
         "clocks": clocks,
