@@ -317,6 +317,41 @@ def probe_cache(dev, level):
                    "best of 5 CUDA-event-timed launches" % (level, how)}
 
 
+def probe_fma(dev, packed=1):
+    """The SMs' FP32 multiply-add rate, measured on this GPU by the library's probe
+    (qmcspl_probe_fma): TFLOP/s over all SMs (2 FLOPs per multiply-add), FLOPs per SM clock, the
+    SM clock it ran at."""
+    import ctypes
+    import torch
+    from paper_1309_6250_gb300 import _lib
+    lib = _lib.load()
+    t, f, m = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    with torch.cuda.device(dev):
+        _lib.check(lib.qmcspl_probe_fma(int(packed), ctypes.byref(t), ctypes.byref(f), ctypes.byref(m),
+                                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return {"tflops": t.value, "flops_per_clk_per_sm": f.value, "sm_mhz": m.value,
+            "how": "qmcspl_probe_fma(%d): 2 x 1024 threads per SM, 8 independent chains of %s per thread, "
+                   "best of 5 CUDA-event-timed launches" % (packed, "fma.rn.f32x2" if packed else "fma.rn.f32")}
+
+
+# FP32 multiply-adds per orbital-evaluation as the kernels form them (z sums of the 4 rows of each
+# stencil column or pp unit, the column's weighted accumulations, then the 3 x 3 chain rule of
+# the gradient): interpolating/smoothing B-spline with the Laplacian table 16 x (2 x 4 + 4 + 5) + 9;
+# with the Laplacian from the Hessian 16 x (3 x 4 + 7) + 9, and the same for the pp-spline's 16
+# units (2 x 2 corner columns x 4 labels); five tables (Lagrange, separate gradient tables)
+# 80 x (4 + 1) + 9.
+FMA_PER_EVAL = {"interp_lap": 281, "smooth_lap": 281, "smooth": 313, "pp": 313, "lagrange": 409,
+                "smooth_sep_grad": 409}
+
+
+def alu_roofline(fma_per_eval, evals, launch_s, fma):
+    """Multiply-add FLOPs of one launch against the probe's packed FP32 rate."""
+    achieved = 2.0 * fma_per_eval * evals / launch_s / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": fma["tflops"], "unit": "TFLOP/s",
+            "frac": achieved / fma["tflops"], "fma_per_eval": fma_per_eval,
+            "peak_kind": "measured in this run (qmcspl_probe_fma, packed fma.rn.f32x2)"}
+
+
 def l1_roofline(gather_bytes, launch_s, l1):
     """Every gathered stencil byte is requested from the SM's L1 data path (hits there, misses
     continue to L2).  Peak: the probe's measured L1 rate."""
@@ -417,10 +452,11 @@ def method_oracle(name, lat, mil, coef, dims, pos, storage):
     return ev(t), ev(tuple(rounded_table(x, storage) for x in t))
 
 
-def bench_methods_c3(args, dev, stream, l1):
+def bench_methods_c3(args, dev, stream, l1, fma=None):
     """The paper's bases at the 128-orbital scale: MgO-like 64-atom cell, 96^3, 2048 walkers x
     256 electrons, FP32 tables, cell order.  Per method the evaluation kernel's own time
-    (library CUDA events) and its gathered bytes against the measured L1 data-path peak:
+    (library CUDA events), its gathered bytes against the measured L1 data-path peak and its
+    multiply-adds against the measured FP32 multiply-add rate:
     smoothing without the Laplacian table (Hessian Laplacian, 1 table), interpolating with it
     (2 tables), Lagrange and B-splines with separate gradient tables (5 tables each), pp (8
     points x 8 entries = 64 values, as one table).  Per method also the error of the first 16
@@ -456,6 +492,8 @@ def bench_methods_c3(args, dev, stream, l1):
                      "eval_kernel_ms": k_s * 1e3, "tables": n_tab, "bytes_per_eval": bpe,
                      "table_bytes": spl.info()["table_bytes"],
                      "roofline_l1": l1_roofline(bpe * evals, k_s, l1)}
+        if fma is not None:
+            out[name]["roofline_alu"] = alu_roofline(FMA_PER_EVAL[name], evals, k_s, fma)
         del o
         spl.close()
         torch.cuda.empty_cache()
@@ -873,6 +911,7 @@ def run_ours(args):
     # roofline of the dominant kernel, from its own CUDA-event launch times
     hbm, peak_kind = load_peaks()
     l1, l2 = probe_cache(dev, 1), probe_cache(dev, 2)
+    fma = probe_fma(dev, 1)
     bpe = algorithmic_bytes_per_eval(args.storage, info["n_tables"], n_orb)
     launch_s = prof["eval_ms"] * 1e-3 / max(1, prof["launches"])
     achieved = bpe * evals_per_step / launch_s / 1e9
@@ -919,7 +958,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         batched = bench_batched(args, dev, stream, l1)
         methods = bench_methods(args, dev, stream)
-        methods_c3 = bench_methods_c3(args, dev, stream, l1)
+        methods_c3 = bench_methods_c3(args, dev, stream, l1, fma)
         backward = bench_backward(args, dev, stream)
         backward_c3 = bench_backward_c3(args, dev, stream, l1)
         bloch = bench_bloch(args, dev, stream)
@@ -942,6 +981,10 @@ def run_ours(args):
     l2_b = traffic["l2"] if traffic else None
     inorder = variants.get("%s_input" % args.storage)
     roofline, levels = cache_rooflines(bpe * evals_per_step, l2_b, dram_b, launch_s, l1, l2, hbm, peak_kind)
+    if args.storage in ("f32", "bf16"):   # the packed FP32 arithmetic of the float and bfloat16 kernels
+        levels["alu"] = alu_roofline(FMA_PER_EVAL["smooth_lap" if args.separate_lap else "smooth"],
+                                     evals_per_step, launch_s, fma)
+        roofline = dict(max(levels.values(), key=lambda r: r["frac"]))
     roofline.update({
         "traffic": dram_b,
         "traffic_source": ("stored: ncu dram__bytes_read.sum + dram__bytes_write.sum (and lts__t_bytes.sum) "
@@ -949,7 +992,7 @@ def run_ours(args):
         "kernel": kernel_name, "bytes_per_eval": bpe, "kernel_ms": launch_s * 1e3,
         "order_kernels_ms": prof["order_ms"] / max(1, prof["launches"]),
         "levels": levels,
-        "probes": {"l1": l1, "l2": l2},
+        "probes": {"l1": l1, "l2": l2, "fma": fma},
         "reuse_factor": (bpe * evals_per_step / dram_b) if dram_b else None,
         "reuse_factor_note": "algorithmic (gathered) bytes per DRAM byte: stencil rows shared by neighbouring "
                              "positions in cell order are read from HBM about once",
@@ -1025,10 +1068,11 @@ def main():
         import torch
         dev = torch.device("cuda", torch.cuda.current_device())
         leg = {"bloch": bench_bloch, "consumer": bench_consumer, "general": bench_general,
-               "methods": bench_methods, "methods_c3": lambda a, d, s: bench_methods_c3(a, d, s, probe_cache(d, 1)),
+               "methods": bench_methods, "methods_c3": lambda a, d, s: bench_methods_c3(a, d, s, probe_cache(d, 1), probe_fma(d, 1)),
                "batched": lambda a, d, s: bench_batched(a, d, s, probe_cache(d, 1)), "backward": bench_backward,
                "backward_c3": lambda a, d, s: bench_backward_c3(a, d, s, probe_cache(d, 1)),
-               "probes": lambda a, d, s: {"l1": probe_cache(d, 1), "l2": probe_cache(d, 2)}}[args.only]
+               "probes": lambda a, d, s: {"l1": probe_cache(d, 1), "l2": probe_cache(d, 2),
+                                           "fma": probe_fma(d, 1), "fma_scalar": probe_fma(d, 0)}}[args.only]
         print(json.dumps({"leg": args.only, **leg(args, dev, torch.cuda.current_stream())}), flush=True)
     else:
         run_ours(args)

@@ -609,6 +609,25 @@ int qmcspl_load(qmcspl_t* out, const char* path, void* stream);
  */
 int qmcspl_probe_cache(int level, double* gbs, double* bytes_per_clk, double* sm_mhz, void* stream);
 
+/*
+ * qmcspl_probe_fma -- measured FP32 multiply-add throughput of the SMs (not in the paper).
+ *
+ * Where positions share their stencil rows on chip, the kernels that also form the Hessian or
+ * the pp-spline derivatives spend their time in multiply-adds (z sums and column weights per
+ * orbital, Eq. (b-splineapproximation)), and the rate that bounds them is that of the FP32
+ * pipe.  This call measures it on the current device: two 1024-thread blocks per SM, each thread
+ * eight independent chains of 4096 multiply-adds, timed with CUDA events on `stream`, best of five
+ * after one warm-up.
+ *   packed         0: fma.rn.f32 (one multiply-add per lane and instruction);
+ *                  1: fma.rn.f32x2 (two per lane and instruction, the form the kernels use)
+ *   tflops         [out] multiply-add FLOPs per second (2 per multiply-add), 10^12
+ *   flops_per_clk  [out] the same per SM and per SM clock cycle
+ *   sm_mhz         [out] the SM clock of the best launch (clock64 cycles / event time)
+ * Any output may be NULL.  Blocking; allocates a few KB for the call; changes no device
+ * setting.  QMCSPL_ERR_ARG for another value of packed.
+ */
+int qmcspl_probe_fma(int packed, double* tflops, double* flops_per_clk, double* sm_mhz, void* stream);
+
 /* qmcspl_sync -- synchronise `stream` and report (then clear) any device-side error the
  * handle's kernels recorded: QMCSPL_ERR_DEVICE for non-finite positions. */
 int qmcspl_sync(qmcspl_t h, void* stream);

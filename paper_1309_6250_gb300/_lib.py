@@ -123,6 +123,8 @@ PROTOTYPES = [
     ("qmcspl_debug_stall_pipeline", I, [I]),
     ("qmcspl_probe_cache", I, [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double), VP]),
+    ("qmcspl_probe_fma", I, [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), VP]),
     ("qmcspl_sync", I, [VP, VP]),
     ("qmcspl_last_error", ctypes.c_char_p, []),
     ("qmcspl_version", I, []),

@@ -1,5 +1,5 @@
-// probe.cu -- measured throughput of the SMs' L1 and L2 data paths for 16-byte loads (not in
-// the paper).
+// probe.cu -- measured throughput of the SMs' L1 and L2 data paths for 16-byte loads and of their
+// FP32 fused multiply-add pipes (not in the paper).
 //
 // With positions in cell order, neighbouring positions share most of the 64 stencil rows of
 // Eq. (b-splineapproximation): the evaluation kernels find those rows in the SM's L1 cache or,
@@ -13,6 +13,7 @@
 //            each block sweeping its own 128 KB window per iteration so that all L2 slices of
 //            both dies serve the SMs.
 #include "qmcspl_internal.cuh"
+#include "eval_common.cuh"
 
 namespace qmcspl {
 namespace {
@@ -74,10 +75,105 @@ __global__ void __launch_bounds__(kProbeThreads) cache_probe_kernel(const uint4*
     if ((acc.x & acc.y & acc.z & acc.w) == 0xffffffffu) sink[blockIdx.x] = acc;
 }
 
+// FP32 multiply-add throughput: every thread runs kFmaChains independent chains of
+// fma.rn.f32 (PACKED = false) or fma.rn.f32x2 (PACKED = true: two lanes of FP32 per
+// instruction), kFmaIters steps each.  m and a come from the host so that nothing folds.
+constexpr int kFmaChains = 8;
+constexpr int kFmaIters = 4096;
+
+template <bool PACKED>
+__global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(float m, float a, long long* cycles, float* sink)
+{
+    __syncthreads();
+    const long long t0 = clock64();
+    float out = 0.f;
+    if (PACKED) {
+        f32x2 acc[kFmaChains];
+        const f32x2 m2 = pack2(m, m), a2 = pack2(a, a);
+#pragma unroll
+        for (int i = 0; i < kFmaChains; ++i) acc[i] = pack2((float)(threadIdx.x + i), (float)i);
+        for (int k = 0; k < kFmaIters; ++k) {
+#pragma unroll
+            for (int i = 0; i < kFmaChains; ++i) acc[i] = ffma2(acc[i], m2, a2);
+        }
+#pragma unroll
+        for (int i = 0; i < kFmaChains; ++i) {
+            float lo, hi;
+            unpack2(acc[i], lo, hi);
+            out += lo + hi;
+        }
+    } else {
+        float acc[kFmaChains];
+#pragma unroll
+        for (int i = 0; i < kFmaChains; ++i) acc[i] = (float)(threadIdx.x + i);
+        for (int k = 0; k < kFmaIters; ++k) {
+#pragma unroll
+            for (int i = 0; i < kFmaChains; ++i) asm("fma.rn.f32 %0, %0, %1, %2;" : "+f"(acc[i]) : "f"(m), "f"(a));
+        }
+#pragma unroll
+        for (int i = 0; i < kFmaChains; ++i) out += acc[i];
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+    if (out == -1.0f) sink[blockIdx.x] = out;   // keeps the chains live; m = 1, a = 0 never gives -1
+}
+
 }  // namespace
 }  // namespace qmcspl
 
 using namespace qmcspl;
+
+extern "C" int qmcspl_probe_fma(int packed, double* tflops, double* flops_per_clk, double* sm_mhz, void* stream)
+{
+    clear_error();
+    if (packed != 0 && packed != 1) return set_error(QMCSPL_ERR_ARG, "qmcspl_probe_fma: packed must be 0 or 1");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int sms = sm_count();
+    const int blocks = kProbeBlocksPerSm * sms;
+    float* sink = nullptr;
+    long long* cyc = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    double best_ms = 0.0;
+    long long best_cycles = 0;
+    const int nc = blocks < 1024 ? blocks : 1024;
+    long long c[1024];
+    cudaError_t e = dev_malloc((void**)&sink, sizeof(float) * (size_t)blocks);
+    if (e == cudaSuccess) e = dev_malloc((void**)&cyc, sizeof(long long) * (size_t)blocks);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    for (int run = 0; run <= kProbeRuns && e == cudaSuccess; ++run) {   // run 0 warms up
+        e = cudaEventRecord(ev[0], st);
+        if (e != cudaSuccess) break;
+        if (packed) fma_probe_kernel<true><<<blocks, kProbeThreads, 0, st>>>(1.0f, 0.0f, cyc, sink);
+        else fma_probe_kernel<false><<<blocks, kProbeThreads, 0, st>>>(1.0f, 0.0f, cyc, sink);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e == cudaSuccess) e = cudaMemcpy(c, cyc, sizeof(long long) * (size_t)nc, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess || run == 0) continue;
+        long long cmax = 0;
+        for (int i = 0; i < nc; ++i) cmax = c[i] > cmax ? c[i] : cmax;
+        if (best_ms == 0.0 || ms < best_ms) {
+            best_ms = ms;
+            best_cycles = cmax;
+        }
+    }
+    if (ev[0]) cudaEventDestroy(ev[0]);
+    if (ev[1]) cudaEventDestroy(ev[1]);
+    if (sink) cudaFree(sink);
+    if (cyc) cudaFree(cyc);
+    if (e != cudaSuccess) return cuda_error(e, "qmcspl_probe_fma");
+    const double flops = (double)blocks * kProbeThreads * kFmaIters * kFmaChains * 2.0 * (packed ? 2.0 : 1.0);
+    const double mhz = best_ms > 0.0 ? (double)best_cycles / (best_ms * 1e3) : 0.0;
+    const double rate = best_ms > 0.0 ? flops / (best_ms * 1e-3) / 1e12 : 0.0;
+    if (tflops) *tflops = rate;
+    if (sm_mhz) *sm_mhz = mhz;
+    if (flops_per_clk) *flops_per_clk = mhz > 0.0 ? rate * 1e12 / ((double)sms * mhz * 1e6) : 0.0;
+    return QMCSPL_OK;
+}
 
 extern "C" int qmcspl_probe_cache(int level, double* gbs, double* bytes_per_clk, double* sm_mhz, void* stream)
 {
