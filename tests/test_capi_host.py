@@ -94,6 +94,8 @@ def test_validation_without_gpu(lib):
     assert lib.qmcspl_sync(None, None) == _lib.ERR_ARG
     assert lib.qmcspl_set_table(None, 0, None, _lib.F64, None) == _lib.ERR_ARG
     assert lib.qmcspl_set_block(None, 512) == _lib.ERR_ARG
+    assert lib.qmcspl_probe_cache(3, None, None, None, None) == _lib.ERR_ARG
+    assert lib.qmcspl_probe_fma(2, None, None, None, None) == _lib.ERR_ARG
     order = ctypes.c_int(-1)
     assert lib.qmcspl_get_order(None, 100, ctypes.byref(order)) == _lib.ERR_ARG and order.value == -1
     assert lib.qmcspl_eval_vgl_host_ex(None, None, 0, None, None, None, ctypes.byref(_lib.HostOpts(1)), None) == _lib.ERR_ARG
