@@ -183,7 +183,9 @@ __device__ __forceinline__ void bspline_warp_task_x2(const EvalArgs& p, long lon
     int ix, iy, iz;
     float tx, ty, tz;
     bool ok;
-    coords_float(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
+    // (the bfloat16 kernel runs fastest with the rolled form of the reduction, the float one with
+    // the written-out form; both give the same bits)
+    coords_float<std::is_same<T, __nv_bfloat16>::value>(p, ip, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
     if (!active) return;
     if (!ok && sub == 0 && tile == 0) atomicOr(p.err, 1);
 

@@ -155,6 +155,15 @@ __device__ __forceinline__ void unpack_cell(int c, int& ix, int& iy, int& iz, bo
     iz = (cc >> 20) & 1023;
 }
 
+// the reduced coordinates of float and bfloat16 tables (double-float arithmetic), defined below
+template <bool ROLLED>
+__device__ __forceinline__ void reduced_coordinates_df(const EvalArgs& p, const double* r, int L, int sub,
+                                                       int gbase, int& ix, int& iy, int& iz, float& tx,
+                                                       float& ty, float& tz, bool& ok);
+
+// ROLLED: the form of the reduction without records (see reduced_coordinates_df); both forms give
+// the same bits
+template <bool ROLLED = false>
 __device__ __forceinline__ void coords_float(const EvalArgs& p, long long ip, int L, int sub, int gbase,
                                              int& ix, int& iy, int& iz, float& tx, float& ty, float& tz,
                                              bool& ok)
@@ -167,11 +176,7 @@ __device__ __forceinline__ void coords_float(const EvalArgs& p, long long ip, in
         tz = q.w;
     } else {
         const double r[3] = {p.pos[3 * ip], p.pos[3 * ip + 1], p.pos[3 * ip + 2]};
-        double dx, dy, dz;
-        reduced_coordinates(p, r, L, sub, gbase, ix, iy, iz, dx, dy, dz, ok);
-        tx = (float)dx;
-        ty = (float)dy;
-        tz = (float)dz;
+        reduced_coordinates_df<ROLLED>(p, r, L, sub, gbase, ix, iy, iz, tx, ty, tz, ok);
     }
 }
 
@@ -331,6 +336,154 @@ __device__ __forceinline__ dfloat df_add(dfloat a, dfloat b)
     return df_norm(s, e);
 }
 __device__ __forceinline__ dfloat df_neg(dfloat a) { return {-a.h, -a.l}; }
+
+// floor of a double-float value (|l| <= ulp(h)/2): that of h, one less where h is an integer
+// and the value lies just below it
+__device__ __forceinline__ float df_floor(dfloat x)
+{
+    const float f = floorf(x.h);
+    return (f == x.h && x.l < 0.0f) ? f - 1.0f : f;
+}
+
+// Reduced coordinate of one axis for float and bfloat16 tables (Eq. reducedcoordinate, the
+// steps of reduce_axis) in double-float arithmetic on the FP32 pipe: crystal coordinate
+// s = sum_j a^-1_ij r_j, wrap to [0, 1), scale by N, split into cell i and offset t, the offset
+// rounded to float at the end.  About 48 significant bits, enough for t to 2^-40 within
+// |s| < 1024 cells; a position further out takes the FP64 steps.  rh, rl: the position as
+// double-float pairs; ah, al: row `ax` of a^-1 as double-float pairs.
+__device__ __forceinline__ void reduce_axis_df(const double* r, const float* rh, const float* rl, const double* ad,
+                                               const float* ah, const float* al, int N, int& i, float& t, bool& ok)
+{
+    dfloat s = df_mul({ah[0], al[0]}, {rh[0], rl[0]});
+    s = df_add(s, df_mul({ah[1], al[1]}, {rh[1], rl[1]}));
+    s = df_add(s, df_mul({ah[2], al[2]}, {rh[2], rl[2]}));
+    if (!(fabsf(s.h) < 1024.0f)) {   // far outside the cell, or not finite
+        double td;
+        reduce_axis(crystal(ad[0], ad[1], ad[2], r), N, i, td, ok);
+        t = (float)td;
+        return;
+    }
+    ok = true;
+    const dfloat f = df_add(s, {-df_floor(s), 0.0f});
+    const dfloat u = df_mulf(f, (float)N);
+    const float fl = df_floor(u);
+    const dfloat d = df_add(u, {-fl, 0.0f});
+    t = __fadd_rn(d.h, d.l);
+    int k = (int)fl;
+    if (k >= N) k -= N;
+    i = k;
+}
+
+// a row of a^-1 as double-float pairs: the same split as df_from_double, so that the host's split
+// of the same doubles (the records' arguments) gives the same floats
+__device__ __forceinline__ void df_row(const double* ad, float* ah, float* al)
+{
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const dfloat d = df_from_double(ad[j]);
+        ah[j] = d.h;
+        al[j] = d.l;
+    }
+}
+
+// reduced_coordinates() for float and bfloat16 tables, with reduce_axis_df per axis: with L >= 4
+// lane j < 3 of the group takes axis j (the results broadcast by shuffles), smaller groups reduce
+// all three axes in every lane.  Two forms of the same arithmetic, chosen per kernel by what its
+// code layout runs fastest with: the axes written out (ROLLED = false), or one copy of the steps
+// in a loop over the axes (ROLLED = true).
+template <bool ROLLED>
+__device__ __forceinline__ void reduced_coordinates_df(const EvalArgs& p, const double* r, int L, int sub,
+                                                       int gbase, int& ix, int& iy, int& iz, float& tx,
+                                                       float& ty, float& tz, bool& ok)
+{
+    float rh[3], rl[3];
+    df_row(r, rh, rl);
+    const bool shared = L >= 4;
+    if (!ROLLED) {
+        if (shared) {
+            const int ax = sub < 3 ? sub : 2;
+            const double ad[3] = {ax == 0 ? p.ainv[0] : (ax == 1 ? p.ainv[3] : p.ainv[6]),
+                                  ax == 0 ? p.ainv[1] : (ax == 1 ? p.ainv[4] : p.ainv[7]),
+                                  ax == 0 ? p.ainv[2] : (ax == 1 ? p.ainv[5] : p.ainv[8])};
+            const int N = ax == 0 ? p.nx : (ax == 1 ? p.ny : p.nz);
+            float ah[3], al[3];
+            df_row(ad, ah, al);
+            int i;
+            float t;
+            bool o;
+            reduce_axis_df(r, rh, rl, ad, ah, al, N, i, t, o);
+            ix = __shfl_sync(kFullMask, i, gbase);
+            iy = __shfl_sync(kFullMask, i, gbase + 1);
+            iz = __shfl_sync(kFullMask, i, gbase + 2);
+            tx = __shfl_sync(kFullMask, t, gbase);
+            ty = __shfl_sync(kFullMask, t, gbase + 1);
+            tz = __shfl_sync(kFullMask, t, gbase + 2);
+            const int okb = o ? 1 : 0;
+            ok = (__shfl_sync(kFullMask, okb, gbase) & __shfl_sync(kFullMask, okb, gbase + 1) &
+                  __shfl_sync(kFullMask, okb, gbase + 2)) != 0;
+        } else {
+            bool o0, o1, o2;
+            float ah[9], al[9];
+            df_row(p.ainv, ah, al);
+            df_row(p.ainv + 3, ah + 3, al + 3);
+            df_row(p.ainv + 6, ah + 6, al + 6);
+            reduce_axis_df(r, rh, rl, p.ainv, ah, al, p.nx, ix, tx, o0);
+            reduce_axis_df(r, rh, rl, p.ainv + 3, ah + 3, al + 3, p.ny, iy, ty, o1);
+            reduce_axis_df(r, rh, rl, p.ainv + 6, ah + 6, al + 6, p.nz, iz, tz, o2);
+            ok = o0 && o1 && o2;
+        }
+        return;
+    }
+    int i0 = 0, i1 = 0, i2 = 0;
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+    bool o0 = true, o1 = true, o2 = true;
+#pragma unroll 1
+    for (int k = 0; k < (shared ? 1 : 3); ++k) {
+        const int ax = shared ? (sub < 3 ? sub : 2) : k;
+        const double ad[3] = {ax == 0 ? p.ainv[0] : (ax == 1 ? p.ainv[3] : p.ainv[6]),
+                              ax == 0 ? p.ainv[1] : (ax == 1 ? p.ainv[4] : p.ainv[7]),
+                              ax == 0 ? p.ainv[2] : (ax == 1 ? p.ainv[5] : p.ainv[8])};
+        const int N = ax == 0 ? p.nx : (ax == 1 ? p.ny : p.nz);
+        float ah[3], al[3];
+        df_row(ad, ah, al);
+        int i;
+        float t;
+        bool o;
+        reduce_axis_df(r, rh, rl, ad, ah, al, N, i, t, o);
+        if (k == 0) {
+            i0 = i;
+            t0 = t;
+            o0 = o;
+        } else if (k == 1) {
+            i1 = i;
+            t1 = t;
+            o1 = o;
+        } else {
+            i2 = i;
+            t2 = t;
+            o2 = o;
+        }
+    }
+    if (shared) {
+        ix = __shfl_sync(kFullMask, i0, gbase);
+        iy = __shfl_sync(kFullMask, i0, gbase + 1);
+        iz = __shfl_sync(kFullMask, i0, gbase + 2);
+        tx = __shfl_sync(kFullMask, t0, gbase);
+        ty = __shfl_sync(kFullMask, t0, gbase + 1);
+        tz = __shfl_sync(kFullMask, t0, gbase + 2);
+        const int okb = o0 ? 1 : 0;
+        ok = (__shfl_sync(kFullMask, okb, gbase) & __shfl_sync(kFullMask, okb, gbase + 1) &
+              __shfl_sync(kFullMask, okb, gbase + 2)) != 0;
+    } else {
+        ix = i0;
+        iy = i1;
+        iz = i2;
+        tx = t0;
+        ty = t1;
+        tz = t2;
+        ok = o0 && o1 && o2;
+    }
+}
 
 // Cubic B-spline weights (Eq. b-splinebasis) and first derivatives in double-float
 // from a reduced coordinate given in double.

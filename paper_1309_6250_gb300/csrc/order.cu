@@ -1,7 +1,9 @@
 // order.cu -- per-position preparation before evaluation (not in the paper).
 //
-// 1. Coordinate records.  Eq. (reducedcoordinate) needs FP64 (an FP32 product N*s
-//    loses ~N*6e-8 of t), and GB300 runs FP64 at a small fraction of its FP32 rate.
+// 1. Coordinate records.  Eq. (reducedcoordinate) needs more than FP32 (an FP32 product N*s
+//    loses ~N*6e-8 of t), and GB300 runs FP64 at a small fraction of its FP32 rate: the
+//    records of float and bfloat16 tables (kind 1) are reduced in double-float arithmetic
+//    on the FP32 pipe (reduce_axis_df, about 48 bits), the others in FP64.
 //    Inside the evaluation kernels a group of lanes shares one position, so a warp-wide
 //    FP64 instruction there serves one position; here one thread reduces one position,
 //    so the same instruction serves 32.  The result (grid cell and t, see
@@ -31,6 +33,7 @@ struct PrepArgs {
     const double* pos;
     long long n;
     double ainv[9];
+    float ainv_h[9], ainv_l[9];   // a^-1 as double-float pairs (records of kind 1)
     int dims[3];
     int edge[3];              // grid cells per bin edge, per axis
     int nb[3];
@@ -51,6 +54,21 @@ __device__ __forceinline__ void reduce_position(const PrepArgs& a, long long i, 
     reduce_axis(crystal(a.ainv[0], a.ainv[1], a.ainv[2], r), a.dims[0], ix, tx, o0);
     reduce_axis(crystal(a.ainv[3], a.ainv[4], a.ainv[5], r), a.dims[1], iy, ty, o1);
     reduce_axis(crystal(a.ainv[6], a.ainv[7], a.ainv[8], r), a.dims[2], iz, tz, o2);
+    ok = o0 && o1 && o2;
+}
+
+// Float records (kind 1): the double-float steps of the float kernels' own reduction
+// (reduced_coordinates_df), so that a record holds the bits those kernels would compute.
+__device__ __forceinline__ void reduce_position_df(const PrepArgs& a, long long i, int& ix, int& iy, int& iz,
+                                                   float& tx, float& ty, float& tz, bool& ok)
+{
+    const double r[3] = {a.pos[3 * i], a.pos[3 * i + 1], a.pos[3 * i + 2]};
+    float rh[3], rl[3];
+    df_row(r, rh, rl);
+    bool o0, o1, o2;
+    reduce_axis_df(r, rh, rl, a.ainv, a.ainv_h, a.ainv_l, a.dims[0], ix, tx, o0);
+    reduce_axis_df(r, rh, rl, a.ainv + 3, a.ainv_h + 3, a.ainv_l + 3, a.dims[1], iy, ty, o1);
+    reduce_axis_df(r, rh, rl, a.ainv + 6, a.ainv_h + 6, a.ainv_l + 6, a.dims[2], iz, tz, o2);
     ok = o0 && o1 && o2;
 }
 
@@ -91,14 +109,18 @@ __global__ void prepare_kernel(const PrepArgs a)
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     int ix, iy, iz;
-    double tx, ty, tz;
+    double tx = 0.0, ty = 0.0, tz = 0.0;
+    float fx = 0.f, fy = 0.f, fz = 0.f;
     bool ok;
     // kinds 4, 5 and binning alone (kind 0) on a non-uniform grid: the grid interval that holds
     // the position, so that bins group positions by the knot intervals they evaluate in
     if (KIND >= 4 || (KIND == 0 && a.knots)) locate_position(a, i, ix, iy, iz, tx, ty, tz, ok);
+    else if (KIND == 1) reduce_position_df(a, i, ix, iy, iz, fx, fy, fz, ok);
     else reduce_position(a, i, ix, iy, iz, tx, ty, tz, ok);
     const int cell = ok ? (ix | (iy << 10) | (iz << 20)) : -1;
-    if (KIND == 1 || KIND == 4) {
+    if (KIND == 1) {
+        static_cast<float4*>(a.rec)[i] = make_float4(__int_as_float(cell), fx, fy, fz);
+    } else if (KIND == 4) {
         static_cast<float4*>(a.rec)[i] = make_float4(__int_as_float(cell), (float)tx, (float)ty, (float)tz);
     } else if (KIND == 2 || KIND == 5) {
         double2* q = static_cast<double2*>(a.rec) + 2 * i;
@@ -185,7 +207,11 @@ PrepArgs prep_args(const Handle* h, const double* pos, long long n, void* rec, d
     a.phase = phase;
     a.knots = h->nonuniform ? h->d_knots : nullptr;
     for (int i = 0; i < 3; ++i) a.kred[i] = h->kred[i];
-    for (int i = 0; i < 9; ++i) a.ainv[i] = h->ainv[i];
+    for (int i = 0; i < 9; ++i) {
+        a.ainv[i] = h->ainv[i];
+        a.ainv_h[i] = (float)h->ainv[i];
+        a.ainv_l[i] = (float)(h->ainv[i] - (double)a.ainv_h[i]);
+    }
     for (int i = 0; i < 3; ++i) {
         a.dims[i] = h->dims[i];
         a.nb[i] = g ? g->nb[i] : 1;
