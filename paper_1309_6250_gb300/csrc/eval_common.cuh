@@ -348,8 +348,9 @@ __device__ __forceinline__ float df_floor(dfloat x)
 // Reduced coordinate of one axis for float and bfloat16 tables (Eq. reducedcoordinate, the
 // steps of reduce_axis) in double-float arithmetic on the FP32 pipe: crystal coordinate
 // s = sum_j a^-1_ij r_j, wrap to [0, 1), scale by N, split into cell i and offset t, the offset
-// rounded to float at the end.  About 48 significant bits, enough for t to 2^-40 within
-// |s| < 1024 cells; a position further out takes the FP64 steps.  rh, rl: the position as
+// rounded to float at the end.  About 48 significant bits: t to about N 2^-38 within 1024 lattice
+// vectors of the origin (|s| < 1024), far below the float it is rounded to; a position further
+// out takes the FP64 steps.  rh, rl: the position as
 // double-float pairs; ah, al: row `ax` of a^-1 as double-float pairs.
 __device__ __forceinline__ void reduce_axis_df(const double* r, const float* rh, const float* rl, const double* ad,
                                                const float* ah, const float* al, int N, int& i, float& t, bool& ok)

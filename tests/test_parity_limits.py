@@ -108,3 +108,34 @@ def test_tiny_grids_every_method(dims, method, storage, sep):
     v, g, l = gpu_eval(spl, many)
     assert_parity((v[:60], g[:60], l[:60]), ref, TOL[storage], "tiny cell order")
     spl.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_far_positions_take_the_fp64_reduction(storage):
+    """Float and bfloat16 tables reduce coordinates in double-float arithmetic within 1024 lattice
+    vectors of the origin (|s| < 1024) and in FP64 beyond: positions up to 3,000 lattice vectors
+    away, on both sides of that limit, through the no-record path (< 8192 positions) and the
+    record path in input and cell order, against the oracle and bit for bit against each other."""
+    dims = (12, 13, 14)
+    lat, mil, coef = inputs.random_cell(2470, dims, 8, 6.0, 5.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="smooth", storage=storage, separate_lap=True)
+    rng = np.random.default_rng(2471)
+    frac = rng.uniform(0.0, 1.0, size=(600, 3))
+    # lattice shifts: well inside the double-float range, straddling |s| = 1024, and far beyond
+    # it, in every octant
+    shifts = np.concatenate([rng.integers(-5, 6, size=(200, 3)),
+                             rng.choice([-1, 1], size=(200, 3)) * rng.integers(1000, 1050, size=(200, 3)),
+                             rng.integers(-3000, 3001, size=(200, 3))])
+    pos = np.ascontiguousarray((frac + shifts) @ lat.T)
+    beta, blap = oracle_tables(lat, mil, coef, dims, "smooth", storage, True)
+    ref = oracle.bspline_eval(beta, lat, pos, beta_lap=blap)
+    few = gpu_eval(spl, pos)                          # no records
+    assert_parity(few, ref, TOL[storage], "far positions, no records " + storage)
+    many = np.concatenate([pos] * 14)                 # 8,400 positions: records
+    outs = {}
+    for order in ("input", "cell"):
+        spl.set_order(order)
+        outs[order] = gpu_eval(spl, many)
+        for a, b in zip(outs[order], few):
+            assert np.array_equal(a[:pos.shape[0]], b), order
+    spl.close()
