@@ -1316,7 +1316,8 @@ int launch_bspline_backward(Handle* h, const double* pos, long long n_pos, const
         a.e.perm = pr.perm;
         a.e.rec = h->storage == QMCSPL_DF64 ? nullptr : pr.rec;
         // real orbitals, bins of 4 cells per edge: the coefficient adjoint gathered per bin
-        // (bspline_bwd_gather_kernel), then the position adjoint alone in the plain kernel
+        // (bspline_bwd_gather_kernel), then the position adjoint alone (below: its own kernel for
+        // float tables, the one-pass kernel without the coefficient part otherwise)
         const bool edge4 = g.edge[0] == 4 && g.edge[1] == 4 && g.edge[2] == 4;
         if (dcoef && edge4 && !h->bloch && h->storage != QMCSPL_DF64) {
             GatherArgs ga;
