@@ -36,6 +36,8 @@ from paper_1309_6250_gb300 import inputs  # noqa: E402
 METRIC = "orbital x position evals/s (val+grad+lap)"
 UNIT = "evals/s"
 KERNEL_SOURCES = ["paper_1309_6250_gb300/csrc/eval_bspline.cu", "paper_1309_6250_gb300/csrc/eval_common.cuh"]
+# the 128-orbital method legs run kernels of both evaluation files
+METHOD_SOURCES = KERNEL_SOURCES + ["paper_1309_6250_gb300/csrc/eval_variants.cu"]
 
 
 def out_bytes(storage):
@@ -52,9 +54,9 @@ def algorithmic_bytes_per_eval(storage, n_tables, n_orb):
     return n_tables * 64 * elem_bytes(storage) + 5 * out_bytes(storage) + 24.0 / n_orb
 
 
-def kernel_source_hash():
+def kernel_source_hash(sources=None):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -69,7 +71,7 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def load_traffic(key):
+def load_traffic(key, sources=None):
     """Bytes per launch from the committed ncu capture, if it was taken on the current kernel
     source: {'dram': DRAM read + write bytes, 'l2': L2 bytes or None}; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
@@ -78,7 +80,7 @@ def load_traffic(key):
     with open(p) as f:
         d = json.load(f)
     e = d.get(key)
-    if not e or e.get("kernel_source_sha") != kernel_source_hash():
+    if not e or e.get("kernel_source_sha") != kernel_source_hash(sources):
         return None
     return {"dram": e.get("dram_bytes_per_launch"), "l2": e.get("l2_bytes_per_launch")}
 
@@ -494,6 +496,15 @@ def bench_methods_c3(args, dev, stream, l1, fma=None):
                      "roofline_l1": l1_roofline(bpe * evals, k_s, l1)}
         if fma is not None:
             out[name]["roofline_alu"] = alu_roofline(FMA_PER_EVAL[name], evals, k_s, fma)
+        # DRAM bytes of the launch from the stored ncu capture of this source, against HBM
+        tr = load_traffic("methods_c3/" + name, METHOD_SOURCES)
+        if tr and tr["dram"]:
+            hbm, hbm_kind = load_peaks()
+            a = tr["dram"] / k_s / 1e9
+            out[name]["roofline_hbm"] = {"bound": "hbm", "achieved": a, "peak": hbm, "unit": "GB/s",
+                                         "frac": a / hbm, "bytes_per_launch": tr["dram"], "peak_kind": hbm_kind,
+                                         "traffic_source": "stored: ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                                                           "of this kernel source, profiles/traffic.json"}
         del o
         spl.close()
         torch.cuda.empty_cache()

@@ -115,6 +115,6 @@ def test_traffic_is_dropped_when_the_kernel_source_changes(monkeypatch):
     key, entry = next(iter(entries.items()))
     if entry["kernel_source_sha"] == bench.kernel_source_hash():
         assert bench.load_traffic(key)["dram"] == entry["dram_bytes_per_launch"]
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda sources=None: "0000000000000000")
     assert bench.load_traffic(key) is None
     assert bench.load_traffic("no/such/key") is None
