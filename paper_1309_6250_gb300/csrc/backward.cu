@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kEvalThreads) bspline_bwd_kernel(const BwdArgs
     }
 }
 
-// ---- position adjoint alone, float tables of real orbitals ----
+// ---- position adjoint alone, float and bfloat16 tables of real orbitals ----
 // u_i = dL/dt_i = sum over the lane's orbitals of wv d_i phi + sum_j g~_j d_i d_j phi + wl d_i lap,
 // with phi = sum over the 4 x 4 stencil columns (l, m) of bx_l by_m (sum_n bz_n c_n).  The upstream
 // weights are contracted with each column's z sums first: with a_k = sum_n bz^(k)_n c_n (k-th
@@ -502,12 +502,16 @@ __device__ __forceinline__ void dpos_task_x2(const BwdArgs& b, long long w0, int
     }
 }
 
-constexpr int kDposThreads = 512;
+// threads per block: 512 for float tables (128 registers); bfloat16 tables carry eight orbitals per
+// lane (twice the upstream and z-sum pairs) and run 384 (168 registers; at 512 they spill)
+template <typename T> struct DposShape {
+    static constexpr int threads = sizeof(T) == 2 ? 384 : 512;
+};
 
 template <typename T, bool LAPTAB>
-__global__ void __launch_bounds__(kDposThreads, 1) bspline_dpos_kernel(const BwdArgs b)
+__global__ void __launch_bounds__(DposShape<T>::threads, 1) bspline_dpos_kernel(const BwdArgs b)
 {
-    constexpr int WPB = kDposThreads / 32;
+    constexpr int WPB = DposShape<T>::threads / 32;
     const EvalArgs& p = b.e;
     const int lane = threadIdx.x & 31;
     const int gpw = 32 >> p.lanes_log2;
@@ -794,10 +798,11 @@ int launch_dpos(const BwdArgs& a, cudaStream_t st)
 {
     const int gpw = 32 >> a.e.lanes_log2;
     const long long warps = (a.e.n_pos * a.e.tiles + gpw - 1) / gpw;
-    long long blocks = (warps + kDposThreads / 32 - 1) / (kDposThreads / 32);
+    constexpr int threads = DposShape<T>::threads;
+    long long blocks = (warps + threads / 32 - 1) / (threads / 32);
     if (blocks > sm_count()) blocks = sm_count();
     if (blocks < 1) blocks = 1;
-    bspline_dpos_kernel<T, LAPTAB><<<(unsigned)blocks, kDposThreads, 0, st>>>(a);
+    bspline_dpos_kernel<T, LAPTAB><<<(unsigned)blocks, threads, 0, st>>>(a);
     return cuda_error(cudaGetLastError(), "bspline_dpos_kernel launch");
 }
 
@@ -1338,10 +1343,11 @@ int launch_bspline_backward(Handle* h, const double* pos, long long n_pos, const
         }
     }
     const bool lt = h->separate_lap != 0;
-    // the position adjoint alone, float tables of real orbitals: its own kernel (bfloat16 tables
-    // need four packed pairs per lane and would spill at 128 registers; they keep the general one)
+    // the position adjoint alone, float and bfloat16 tables of real orbitals: its own kernel
     if (!a.dcoef && !h->bloch && h->storage == QMCSPL_F32)
         return lt ? launch_dpos<float, true>(a, st) : launch_dpos<float, false>(a, st);
+    if (!a.dcoef && !h->bloch && h->storage == QMCSPL_BF16)
+        return lt ? launch_dpos<__nv_bfloat16, true>(a, st) : launch_dpos<__nv_bfloat16, false>(a, st);
     switch (h->storage) {
     case QMCSPL_F64: return lt ? launch_typed<double, true>(a, st) : launch_typed<double, false>(a, st);
     case QMCSPL_F32: return lt ? launch_typed<float, true>(a, st) : launch_typed<float, false>(a, st);
