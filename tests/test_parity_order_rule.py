@@ -50,3 +50,18 @@ def test_automatic_order_follows_the_rule(dims, n_orb):
     for x, y in zip(a, b):
         assert torch.equal(x, y)
     spl.close()
+
+
+@pytest.mark.parametrize("n_orb,staged", [(32, True), (16, False)])
+def test_pencil_order_is_reported_where_the_staged_kernel_applies(n_orb, staged):
+    """Pencil order takes the shared-memory-staged kernel only for cubic B-splines whose rows
+    are 128, 256 or 512 bytes (32 FP32 orbitals here); other handles evaluate in cell order,
+    and qmcspl_get_order says which."""
+    dims = (16, 16, 16)
+    lat, mil, coef = inputs.random_cell(2480 + n_orb, dims, n_orb, 3.0, 4.0, NONORTHO)
+    spl = splines(lat, dims, mil, coef, method="smooth", storage="f32", separate_lap=True)
+    assert bool(spl.info()["staged"]) == staged
+    spl.set_order("pencil")
+    assert spl.resolved_order(20000) == ("pencil" if staged else "cell")
+    assert spl.resolved_order(0) == "input"
+    spl.close()
