@@ -271,3 +271,31 @@ def test_batched_refuses_a_handle_twice():
     assert ei.value.code == _lib.ERR_ARG
     for s in spls:
         s.close()
+
+
+def test_batched_with_an_empty_cell():
+    """A cell of no positions in the middle of a batch (its pointers may be NULL) changes nothing
+    for the others under every launch plan; the host-buffer call with no positions is a no-op."""
+    from paper_1309_6250_gb300.api import eval_batched
+    spec = (((16, 16, 16), 8, 20_000), ((10, 11, 12), 5, 0), ((12, 12, 12), 6, 1_000))
+    spls, pos = [], []
+    for i, (dims, n_orb, n) in enumerate(spec):
+        lat, mil, coef = inputs.random_cell(2490 + i, dims, n_orb, 6.0, 5.0, NONORTHO)
+        spls.append(splines(lat, dims, mil, coef, method="smooth", storage="f32", separate_lap=True))
+        p = inputs.positions(lat, max(n, 1), 2495 + i, -1, 2)[:n]
+        pos.append(torch.from_numpy(np.ascontiguousarray(p)).to(dev()).reshape(-1, 3))
+    ref = [s.eval_vgl(p) if p.shape[0] else None for s, p in zip(spls, pos)]
+    torch.cuda.synchronize()
+    for plan in (None, {"launch": "split"}, {"launch": "single", "threads": 512}):
+        got = eval_batched(spls, pos, plan=plan)
+        torch.cuda.synchronize()
+        for g, r in zip(got, ref):
+            if r is None:
+                assert all(t.shape[0] == 0 for t in g)
+                continue
+            for x, y in zip(g, r):
+                assert torch.equal(x, y), plan
+    v, g_, l = spls[0].eval_vgl_host(torch.zeros((0, 3), dtype=torch.float64))
+    assert v.shape[0] == 0 and g_.shape[0] == 0 and l.shape[0] == 0
+    for s in spls:
+        s.close()
